@@ -1,0 +1,382 @@
+"""FP64 CPU oracle of the unbiased polyspectrum estimator (arXiv 2505.01231).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  The CUDA path never
+calls it, and it shares no code with the CUDA path (only the seeded signal
+generators in ``synth`` feed both).
+
+Every step follows the paper literally, in float64, with no blocking, fusion or
+reordering beyond what the cited formula states:
+
+* frames and window ........ Sec. 3, Eq. 16-17 (z_i, g_i); App. B, Eq. 71 (confined Gaussian)
+* Fourier coefficients ..... Sec. 3, Eq. 18 (a_k with the POSITIVE exponent e^{+2 pi j ik/N},
+                              t0 = 0); App. A, Eq. 63 (sign convention)
+* cumulant estimators ...... Sec. 4.1, Eq. 32 (c2), Eq. 33 (c3), Eq. 34 (c4, raw-moment form);
+                              App. H, Eq. 85 (factorised c4)
+* spectra + normalisation .. Sec. 3, Eq. 23 (S2); Sec. 4, Eq. 28 (S3), Eq. 31 (S4 cut);
+                              Sec. 7, Eq. 47, 48, 50 (multi-channel S2, S3, S4 cut)
+* error bars ............... Sec. 4.2, Eq. 35-36 (variance over N_p parts, standard error)
+
+Notation: ``T`` is the number of samples per frame (the paper's N), ``dt`` the
+sample interval (the paper's T/N), ``M = T/2 + 1`` the number of real-FFT bins,
+``m`` the number of frames per k-statistic sample set ("group") and ``G`` the
+number of groups; the paper's parts N_p are the groups.
+
+With a_k = dt * X_k (X the plain windowed DFT sum), the paper's prefactor N/T
+equals 1/dt, so Eq. 23, 28 and 31 become
+    S2 = dt   c2(X_k, X_k*)                 / sum g^2
+    S3 = dt^2 c3(X_k, X_l, X_{k+l}*)        / sum g^3
+    S4 = dt^3 c4(X_k, X_k*, X_l, X_l*)      / sum g^4.
+For real channels X_{-k} = X_k* (the DFT of a real frame).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "window",
+    "dft_plus",
+    "dft_plus_direct",
+    "frame_groups",
+    "fourier_coefficients",
+    "c2",
+    "c3",
+    "c4",
+    "c4_factorised",
+    "coef",
+    "s2_groups",
+    "s3_groups",
+    "s4_groups",
+    "mean_and_stderr",
+    "s3_domain",
+    "polyspectra",
+    "cross_domain_s3",
+    "cross_polyspectra",
+]
+
+
+# --------------------------------------------------------------------------- window
+def window(T: int, kind: str = "hann", sigma_t: float = 0.14) -> np.ndarray:
+    """Window coefficients g_i, i = 0..T-1 (float64).
+
+    ``hann``: periodic Hann, g_i = 0.5 - 0.5 cos(2 pi i / T).
+    ``acg``: approximate confined Gaussian of App. B, Eq. 71,
+        g_k ~ G(k) - G(-1/2) [G(k+N) + G(k-N)] / [G(-1/2+N) + G(-1/2-N)],
+        G(x) = exp(-(x - (N-1)/2)^2 / (4 N^2 sigma_t^2)), N = T.
+    The estimator is invariant under g -> c g, so no normalisation is applied.
+    """
+    i = np.arange(T, dtype=np.float64)
+    if kind == "hann":
+        return 0.5 - 0.5 * np.cos(2.0 * np.pi * i / T)
+    if kind == "acg":
+        N = float(T)
+
+        def G(x):
+            return np.exp(-((x - (N - 1.0) / 2.0) ** 2) / (4.0 * N * N * sigma_t * sigma_t))
+
+        return G(i) - G(-0.5) * (G(i + N) + G(i - N)) / (G(-0.5 + N) + G(-0.5 - N))
+    raise ValueError(f"unknown window {kind!r}")
+
+
+# --------------------------------------------------------------------------- DFT
+def dft_plus(x: np.ndarray) -> np.ndarray:
+    """X_k = sum_i x_i exp(+2 pi j i k / T), k = 0..T/2, over the last axis.
+
+    Eq. 18 with t0 = 0 and without the dt prefactor.  For real x this is the
+    complex conjugate of numpy's forward real FFT (which uses exp(-2 pi j ik/T)),
+    so the library FFT serves as the summation step.
+    """
+    return np.conj(np.fft.rfft(np.asarray(x, dtype=np.float64), axis=-1))
+
+
+def dft_plus_direct(x: np.ndarray) -> np.ndarray:
+    """The same sum as ``dft_plus`` evaluated term by term, O(T^2) (pinning only)."""
+    x = np.asarray(x, dtype=np.float64)
+    T = x.shape[-1]
+    k = np.arange(T // 2 + 1)
+    i = np.arange(T)
+    w = np.exp(2j * np.pi * np.outer(i, k) / T)
+    return x @ w
+
+
+# --------------------------------------------------------------------------- framing
+def frame_groups(z: np.ndarray, T: int, m: int) -> np.ndarray:
+    """Cut a channel into consecutive frames z_i = z[jT + i] (Eq. 16) and group m frames.
+
+    Returns float64 [G, m, T]; trailing samples that do not fill a whole group
+    are dropped.
+    """
+    z = np.asarray(z)
+    G = z.shape[-1] // (m * T)
+    return z[..., : G * m * T].astype(np.float64).reshape(z.shape[:-1] + (G, m, T))
+
+
+def fourier_coefficients(z: np.ndarray, T: int, m: int, g: np.ndarray) -> np.ndarray:
+    """X[g, j, k] = sum_i g_i z_{(g m + j) T + i} e^{+2 pi j ik/T}: complex128 [G, m, M]."""
+    return dft_plus(frame_groups(z, T, m) * g)
+
+
+# --------------------------------------------------------------------------- k-statistics
+def _mean(v):
+    return v.mean(axis=-1)
+
+
+def c2(x, y):
+    """Eq. 32: m/(m-1) (mean(xy) - mean(x) mean(y)); samples on the last axis."""
+    m = x.shape[-1]
+    return m / (m - 1) * (_mean(x * y) - _mean(x) * _mean(y))
+
+
+def c3(x, y, z):
+    """Eq. 33: m^2/((m-1)(m-2)) (xyz - xy z - xz y - yz x + 2 x y z), bars = sample means."""
+    m = x.shape[-1]
+    mx, my, mz = _mean(x), _mean(y), _mean(z)
+    return m * m / ((m - 1) * (m - 2)) * (
+        _mean(x * y * z)
+        - _mean(x * y) * mz
+        - _mean(x * z) * my
+        - _mean(y * z) * mx
+        + 2.0 * mx * my * mz
+    )
+
+
+def c4(x, y, z, w):
+    """Eq. 34, the raw-moment form of the fourth k-statistic."""
+    m = x.shape[-1]
+    mx, my, mz, mw = _mean(x), _mean(y), _mean(z), _mean(w)
+    xy, xz, xw = _mean(x * y), _mean(x * z), _mean(x * w)
+    yz, yw, zw = _mean(y * z), _mean(y * w), _mean(z * w)
+    xyz, xyw = _mean(x * y * z), _mean(x * y * w)
+    xzw, yzw = _mean(x * z * w), _mean(y * z * w)
+    xyzw = _mean(x * y * z * w)
+    bracket = (
+        (m + 1) * xyzw
+        - (m + 1) * (xyz * mw + xyw * mz + xzw * my + yzw * mx)
+        - (m - 1) * (xy * zw + xz * yw + xw * yz)
+        + 2 * m * (xy * mz * mw + xz * my * mw + xw * my * mz
+                   + yz * mx * mw + yw * mx * mz + zw * mx * my)
+        - 6 * m * mx * my * mz * mw
+    )
+    return m * m / ((m - 1) * (m - 2) * (m - 3)) * bracket
+
+
+def c4_factorised(x, y, z, w):
+    """App. H, Eq. 85: the same statistic written with centred samples."""
+    m = x.shape[-1]
+    dx = x - _mean(x)[..., None]
+    dy = y - _mean(y)[..., None]
+    dz = z - _mean(z)[..., None]
+    dw = w - _mean(w)[..., None]
+    bracket = (m + 1) * _mean(dx * dy * dz * dw) - (m - 1) * (
+        _mean(dx * dy) * _mean(dz * dw)
+        + _mean(dx * dz) * _mean(dy * dw)
+        + _mean(dx * dw) * _mean(dy * dz)
+    )
+    return m * m / ((m - 1) * (m - 2) * (m - 3)) * bracket
+
+
+# --------------------------------------------------------------------------- spectra
+def coef(X: np.ndarray, k) -> np.ndarray:
+    """Coefficients at (possibly negative) bins k: X_{-k} = X_k* for a real channel.
+
+    X: [..., m, M]; returns [..., m, len(k)].
+    """
+    k = np.asarray(k)
+    v = X[..., np.abs(k)]
+    return np.where(k < 0, np.conj(v), v)
+
+
+def _samples_last(v):
+    # [..., m, P] -> [..., P, m] so the k-statistics reduce over the last axis
+    return np.swapaxes(v, -1, -2)
+
+
+def s2_groups(Xa, Xb, dt, g, k=None):
+    """Per-group S2 (Eq. 23 / Eq. 47): dt c2(a_k, b_k*) / sum g^2.  Returns [G, P]."""
+    M = Xa.shape[-1]
+    k = np.arange(M) if k is None else np.asarray(k)
+    x = _samples_last(coef(Xa, k))
+    y = _samples_last(np.conj(coef(Xb, k)))
+    return dt * c2(x, y) / np.sum(g ** 2)
+
+
+def s3_groups(Xa, Xb, Xc, dt, g, k, l):
+    """Per-group S3 (Eq. 28 / Eq. 48): dt^2 c3(a_k, b_l, c_{k+l}*) / sum g^3."""
+    k, l = np.asarray(k), np.asarray(l)
+    x = _samples_last(coef(Xa, k))
+    y = _samples_last(coef(Xb, l))
+    z = _samples_last(np.conj(coef(Xc, k + l)))
+    return dt * dt * c3(x, y, z) / np.sum(g ** 3)
+
+
+def s4_groups(Xa, Xb, Xc, Xd, dt, g, k, l, factorised=False):
+    """Per-group S4 cut (Eq. 31 / Eq. 50): dt^3 c4(a_k, b_k*, c_l, d_l*) / sum g^4."""
+    k, l = np.asarray(k), np.asarray(l)
+    x = _samples_last(coef(Xa, k))
+    y = _samples_last(np.conj(coef(Xb, k)))
+    z = _samples_last(coef(Xc, l))
+    w = _samples_last(np.conj(coef(Xd, l)))
+    f = c4_factorised if factorised else c4
+    return dt ** 3 * f(x, y, z, w) / np.sum(g ** 4)
+
+
+def mean_and_stderr(Sg: np.ndarray):
+    """Average over the N_p = G parts and standard error of Re and Im (Eq. 35-36).
+
+    Var(x) = N_p/(N_p - 1) (mean(x^2) - mean(x)^2), sigma = sqrt(Var / N_p).
+    Returns (mean complex, err_re, err_im), each with the part axis (0) removed.
+    """
+    Np = Sg.shape[0]
+
+    def err(x):
+        var = Np / (Np - 1) * (np.mean(x * x, axis=0) - np.mean(x, axis=0) ** 2)
+        return np.sqrt(np.maximum(var, 0.0) / Np)
+
+    return Sg.mean(axis=0), err(Sg.real), err(Sg.imag)
+
+
+class _Acc:
+    """Running sums over groups of S, Re(S)^2 and Im(S)^2 (float64)."""
+
+    def __init__(self, shape):
+        self.s = np.zeros(shape, np.complex128)
+        self.qr = np.zeros(shape, np.float64)
+        self.qi = np.zeros(shape, np.float64)
+        self.n = 0
+
+    def add(self, Sg):
+        self.s += Sg.sum(axis=0)
+        self.qr += (Sg.real ** 2).sum(axis=0)
+        self.qi += (Sg.imag ** 2).sum(axis=0)
+        self.n += Sg.shape[0]
+
+    def result(self):
+        Np = self.n
+        mean = self.s / Np
+        var_r = Np / (Np - 1) * (self.qr / Np - mean.real ** 2)
+        var_i = Np / (Np - 1) * (self.qi / Np - mean.imag ** 2)
+        return mean, np.sqrt(np.maximum(var_r, 0) / Np), np.sqrt(np.maximum(var_i, 0) / Np)
+
+
+def s3_domain(M: int):
+    """Single-channel bispectrum grid points: 0 <= k, l and k + l <= M - 1 (row-major)."""
+    kk, ll = np.meshgrid(np.arange(M), np.arange(M), indexing="ij")
+    sel = (kk + ll) <= M - 1
+    return kk[sel], ll[sel]
+
+
+def polyspectra(z, T, dt, m, window_kind="hann", sigma_t=0.14, orders=(2, 3, 4),
+                group_chunk=16, max_groups=None, factorised_c4=False):
+    """Single-channel S2 [M], S3 [M, M], S4 [M, M] with standard errors.
+
+    Returns a dict with keys 'S2', 'S2_err', 'S3', 'S3_err', 'S4', 'S4_err', 'G'
+    ('*_err' arrays carry a trailing axis (err_re, err_im)).  S3 is zero outside
+    k + l <= M - 1.  ``max_groups`` limits the record to its first groups.
+    """
+    g = window(T, window_kind, sigma_t)
+    frames = frame_groups(z, T, m)
+    if max_groups is not None:
+        frames = frames[:max_groups]
+    G = frames.shape[0]
+    if G < 2:
+        raise ValueError("need at least two groups for an error estimate")
+    M = T // 2 + 1
+    out = {"G": G}
+    kk3, ll3 = s3_domain(M)
+    kk4, ll4 = [a.ravel() for a in np.meshgrid(np.arange(M), np.arange(M), indexing="ij")]
+    acc = {}
+    if 2 in orders:
+        acc[2] = _Acc((M,))
+    if 3 in orders:
+        acc[3] = _Acc((kk3.size,))
+    if 4 in orders:
+        acc[4] = _Acc((kk4.size,))
+    for g0 in range(0, G, group_chunk):
+        X = dft_plus(frames[g0:g0 + group_chunk] * g)
+        if 2 in orders:
+            acc[2].add(s2_groups(X, X, dt, g))
+        if 3 in orders:
+            acc[3].add(s3_groups(X, X, X, dt, g, kk3, ll3))
+        if 4 in orders:
+            acc[4].add(s4_groups(X, X, X, X, dt, g, kk4, ll4, factorised=factorised_c4))
+    if 2 in orders:
+        mean, er, ei = acc[2].result()
+        out["S2"], out["S2_err"] = mean, np.stack([er, ei], -1)
+    if 3 in orders:
+        mean, er, ei = acc[3].result()
+        S3 = np.zeros((M, M), np.complex128)
+        E3 = np.zeros((M, M, 2))
+        S3[kk3, ll3] = mean
+        E3[kk3, ll3, 0], E3[kk3, ll3, 1] = er, ei
+        out["S3"], out["S3_err"] = S3, E3
+    if 4 in orders:
+        mean, er, ei = acc[4].result()
+        out["S4"] = mean.reshape(M, M)
+        out["S4_err"] = np.stack([er, ei], -1).reshape(M, M, 2)
+    return out
+
+
+# --------------------------------------------------------------------------- multi-channel
+def cross_domain_s3(M: int):
+    """Cross bispectrum grid: k in [-(M-1), M-1], l in [0, M-1], |k + l| <= M - 1.
+
+    Returned as index arrays (k, l) in row-major order of the [2M-1, M] output,
+    whose row r holds k = r - (M - 1).
+    """
+    kk, ll = np.meshgrid(np.arange(-(M - 1), M), np.arange(M), indexing="ij")
+    sel = np.abs(kk + ll) <= M - 1
+    return kk[sel], ll[sel]
+
+
+def cross_polyspectra(zs, T, dt, m, s2_combos=(), s3_combos=(), s4_combos=(),
+                      window_kind="hann", sigma_t=0.14, group_chunk=8, max_groups=None):
+    """Multi-channel spectra (Sec. 7, Eq. 47, 48, 50) for the listed channel combinations.
+
+    zs: [C, n] real channels.  s2_combos: (a, b) pairs -> S2_ab [M] = C2(a_k, b_k*).
+    s3_combos: (a, b, c) -> S3_abc [2M-1, M] = C3(a_k, b_l, c_{k+l}*) on the cross
+    domain of ``cross_domain_s3`` (zero elsewhere).  s4_combos: (a, b, c, d) ->
+    S4_abcd [2M-1, M] = C4(a_k, b_k*, c_l, d_l*), k in [-(M-1), M-1], l in [0, M-1].
+    Returns a dict keyed by ('S2', combo) etc. holding (mean, err[..., 2]), plus 'G'.
+    """
+    g = window(T, window_kind, sigma_t)
+    frames = frame_groups(np.asarray(zs), T, m)  # [C, G, m, T]
+    if max_groups is not None:
+        frames = frames[:, :max_groups]
+    C, G = frames.shape[0], frames.shape[1]
+    M = T // 2 + 1
+    kk3, ll3 = cross_domain_s3(M)
+    kk4, ll4 = [a.ravel() for a in
+                np.meshgrid(np.arange(-(M - 1), M), np.arange(M), indexing="ij")]
+    accs = {}
+    for cmb in s2_combos:
+        accs[("S2", tuple(cmb))] = _Acc((M,))
+    for cmb in s3_combos:
+        accs[("S3", tuple(cmb))] = _Acc((kk3.size,))
+    for cmb in s4_combos:
+        accs[("S4", tuple(cmb))] = _Acc((kk4.size,))
+    for g0 in range(0, G, group_chunk):
+        X = [dft_plus(frames[c, g0:g0 + group_chunk] * g) for c in range(C)]
+        for cmb in s2_combos:
+            a, b = cmb
+            accs[("S2", tuple(cmb))].add(s2_groups(X[a], X[b], dt, g))
+        for cmb in s3_combos:
+            a, b, c = cmb
+            accs[("S3", tuple(cmb))].add(s3_groups(X[a], X[b], X[c], dt, g, kk3, ll3))
+        for cmb in s4_combos:
+            a, b, c, d = cmb
+            accs[("S4", tuple(cmb))].add(s4_groups(X[a], X[b], X[c], X[d], dt, g, kk4, ll4))
+    out = {"G": G}
+    for key, acc in accs.items():
+        mean, er, ei = acc.result()
+        if key[0] == "S2":
+            out[key] = (mean, np.stack([er, ei], -1))
+        elif key[0] == "S3":
+            S = np.zeros((2 * M - 1, M), np.complex128)
+            E = np.zeros((2 * M - 1, M, 2))
+            S[kk3 + M - 1, ll3] = mean
+            E[kk3 + M - 1, ll3, 0], E[kk3 + M - 1, ll3, 1] = er, ei
+            out[key] = (S, E)
+        else:
+            out[key] = (mean.reshape(2 * M - 1, M),
+                        np.stack([er, ei], -1).reshape(2 * M - 1, M, 2))
+    return out
