@@ -1,0 +1,376 @@
+"""Throughput of the polyspectrum hot path (S2 + S3 + S4) on GB300.
+
+One step = one pass of the whole path over one synthetic record: ss_reset,
+ss_accumulate (frame/window/FFT/centre + S2, bispectrum, trispectrum cut) and
+ss_finalize (means and standard errors), through the C ABI.
+
+  value : input samples/s with the record already resident in HBM (device
+          pointers in and out), CUDA events on the plan's stream.
+  e2e   : the same metric through the same C-ABI calls with HOST buffers: the
+          record is read from pinned host memory and all spectra and error
+          bars are copied back to host memory inside the timed region.
+
+Default workload: one channel, 2^28 float32 samples of x = y + 0.3 (y^2 - 1), y an
+AR(1) process (coefficient 0.9, seed 1); frames T = 1024 (513 bins), Hann
+window, groups of m = 10 frames; full S2, S3 and S4 grids.  The record (1 GiB)
+is larger than L2, so no extra L2 flush is done between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank processes its own record (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "input samples/s for S2+S3+S4 at stated T,m; % of HBM/FP32/tensor peak; err vs FP64"
+
+WORKLOADS = {
+    # name: (channels, n samples per channel, T, m, seed)
+    "ar1q-2^28-T1024-m10": dict(channels=1, n=1 << 28, T=1024, m=10, seed=1, phi=0.9),
+    "ar1q-2^20-T256-m10": dict(channels=1, n=1 << 20, T=256, m=10, seed=0, phi=0.9),
+}
+DEFAULT_WORKLOAD = "ar1q-2^28-T1024-m10"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_record(w, rank):
+    import synth
+
+    return synth.ar1_quadratic(w["n"], seed=w["seed"] + rank, phi=w["phi"])
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_peak_tflops(nsm, pk):
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock, at the maximum
+    # SM clock; no FP32 FMA peak is measured, so this is derived from unit counts
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    return nsm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is
+    unchanged since the capture (source hash recorded beside the figure)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2505_01231_gb300", "csrc", rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["bytes_per_launch"] if h == rec["sha256_16"] else None
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    import oracle
+
+    z = make_record(w, 0)
+    T, m = w["T"], w["m"]
+    groups_per_step = args.ref_groups
+    n_step = groups_per_step * m * T
+    ts = []
+    for i in range(args.warmup + args.steps):
+        off = (i * n_step) % max(1, (len(z) - n_step))
+        t0 = time.perf_counter()
+        oracle.polyspectra(z[off:off + n_step], T, 1.0, m, group_chunk=groups_per_step)
+        if i >= args.warmup:
+            ts.append(time.perf_counter() - t0)
+    sec = float(np.mean(ts))
+    value = n_step / sec
+    sample = (f"{groups_per_step} groups ({n_step} samples) of the same record per step, "
+              f"full S2/S3/S4 grids, numpy float64")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "T": T, "m": m, "samples_per_step": n_step},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, z, groups):
+    import oracle
+
+    T, m = w["T"], w["m"]
+    n = groups * m * T
+    t0 = time.perf_counter()
+    oracle.polyspectra(z[:n], T, 1.0, m, group_chunk=groups)
+    sec = time.perf_counter() - t0
+    return {"value": n / sec, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {groups} groups ({n} samples) of the record, full S2/S3/S4 grids, "
+                      f"numpy float64 on one host core, {sec:.1f} s"}
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-groups", type=int, default=24)
+    ap.add_argument("--ref-groups", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    rank, world, local = dist_env()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+
+    import torch
+
+    import paper_2505_01231_gb300 as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    z = make_record(w, rank)
+    n = z.shape[-1]
+    T, m, C = w["T"], w["m"], w["channels"]
+    stream = torch.cuda.current_stream()
+    plan = P.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4), stream=stream)
+    info = P.ss_query(plan.handle)
+    dz = torch.from_numpy(z).cuda()
+    sh = plan.shapes()
+    outs = {k: torch.empty(int(np.prod(v)) * 2, dtype=torch.float64, device="cuda")
+            for k, v in sh.items()}
+    errs = {k: torch.empty_like(v) for k, v in outs.items()}
+
+    def step_device():
+        P.ss_reset(plan.handle)
+        P.ss_accumulate(plan.handle, dz, n)
+        P.ss_finalize(plan.handle, outs["S2"], outs["S3"], outs["S4"], errs["S2"], errs["S3"],
+                      errs["S4"])
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step_device()
+    barrier()
+    P.ss_reset(plan.handle)
+    P.ss_set_timing(plan.handle, 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    stage_ms = np.zeros(5)
+    stage_launches = np.zeros(5)
+    for _ in range(args.steps):
+        step_device()
+        st = P.ss_stats(plan.handle)   # per-stage event times of this step (reset clears)
+        stage_ms += np.array(st.ms[:])
+        stage_launches += np.array(st.launches[:])
+    t1.record(stream)
+    barrier()
+    clock_info = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    P.ss_set_timing(plan.handle, 0)
+    if dist is not None:
+        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ms_per_step = elapsed / args.steps * 1e3
+    G = info.groups if info.groups else (n // (m * T))
+    groups = n // (m * T)
+    value = world * n * args.steps / elapsed
+
+    # ---- roofline of the dominant kernel (live CUDA events on the plan's stream)
+    pk = peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    st = P.ss_stats(plan.handle)
+    frames = groups * m
+    names = ["k1_spectra", "k2_bispec", "k3_trispec", "k4_finalize", "h2d"]
+    dom = int(np.argmax(stage_ms[:3]))
+    n_batches = max(1, int(np.ceil(groups / info.groups_per_batch)))
+    launches = stage_launches[dom]
+    if dom == 0:
+        bytes_per_step = frames * (4 * T * C + 8 * (T // 2 + 1) * C)
+        achieved = bytes_per_step * args.steps / (stage_ms[0] / 1e3) / 1e9
+        peak, unit, bound = float(pk.get("hbm_gbs", 6800.0)), "GB/s", "hbm"
+    elif dom == 1:
+        flops_per_step = 14.0 * st.pairs3 * frames
+        achieved = flops_per_step * args.steps / (stage_ms[1] / 1e3) / 1e12
+        peak, unit, bound = fp32_peak_tflops(nsm, pk), "TFLOP/s", "alu"
+    else:
+        flops_per_step = 10.0 * st.pairs4 * frames
+        achieved = flops_per_step * args.steps / (stage_ms[2] / 1e3) / 1e12
+        peak, unit, bound = fp32_peak_tflops(nsm, pk), "TFLOP/s", "alu"
+    roofline = {"bound": bound, "kernel": names[dom], "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak, "traffic": traffic_for(names[dom]),
+                "peak_source": ("measured (MEASURED_PEAKS.json)" if bound == "hbm" else
+                                "derived: SMs x 128 FP32 lanes x 2 flop x max SM clock"),
+                "stage_ms_per_step": {nm: float(stage_ms[i] / args.steps)
+                                      for i, nm in enumerate(names[:4])},
+                "launch_ms": float(stage_ms[dom] / max(1, launches))}
+    gpu_launches = int(args.steps * (n_batches * (1 + info.n_s3 + info.n_s4) + 3))
+
+    # ---- end to end through the same calls with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hz = torch.from_numpy(z).pin_memory()
+        host_out = {k: np.empty(int(np.prod(v)) * 2, np.float64) for k, v in sh.items()}
+        host_err = {k: np.empty_like(v) for k, v in host_out.items()}
+
+        def step_host():
+            P.ss_reset(plan.handle)
+            P.ss_accumulate(plan.handle, hz, n)
+            P.ss_finalize(plan.handle, host_out["S2"], host_out["S3"], host_out["S4"],
+                          host_err["S2"], host_err["S3"], host_err["S4"])
+
+        for _ in range(2):
+            step_host()
+        barrier()
+        h0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        barrier()
+        he = time.perf_counter() - h0
+        if dist is not None:
+            t = torch.tensor([he], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            he = float(t.item())
+        d2h = sum(v.nbytes for v in host_out.values()) + sum(v.nbytes for v in host_err.values())
+        e2e = {"value": world * n * args.steps / he, "unit": "samples/s",
+               "h2d_bytes_per_step": int(z.nbytes), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, z, args.cpu_groups)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "channels": C, "samples_per_rank": n, "T": T,
+                       "M": T // 2 + 1, "m": m, "groups": groups, "window": "hann",
+                       "orders": "S2+S3+S4 full grids", "s4_precision": "fp32",
+                       "l2": "record of 1 GiB per step is larger than L2; no flush"},
+            "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
+            "cpu_baseline": cpu, "clocks": clock_info,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

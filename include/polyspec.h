@@ -1,0 +1,204 @@
+/*
+ * polyspec.h -- C ABI of the GB300 (sm_103a) unbiased polyspectrum estimator.
+ *
+ * The library estimates the power spectrum S2, the bispectrum S3 and the
+ * two-dimensional trispectrum cut S4 of one or more real signal channels with
+ * the unbiased multivariate k-statistics of arXiv 2505.01231 ("Correct
+ * Estimation of Higher-Order Spectra ... in SignalSnap"):
+ *
+ *   frames ................ Sec. 3, Eq. 16: frame j of a channel is z[jT .. jT+T-1]
+ *   window ................ Sec. 3, Eq. 17; App. B, Eq. 71 (confined Gaussian)
+ *   Fourier coefficients .. Sec. 3, Eq. 18: X_k = sum_i g_i z_i exp(+2 pi j ik/T),
+ *                           k = 0..T/2 (positive exponent, t0 = 0)
+ *   k-statistics .......... Sec. 4.1, Eq. 32-34 over a group of m consecutive frames;
+ *                           the fourth order in the factorised form of App. H, Eq. 85
+ *   spectra ............... Sec. 3, Eq. 23 (S2); Sec. 4, Eq. 28 (S3), Eq. 31 (S4 cut);
+ *                           Sec. 7, Eq. 47, 48, 50 (multi-channel)
+ *   error bars ............ Sec. 4.2, Eq. 35-36 with the parts N_p = the groups
+ *
+ * Notation: T = samples per frame (the paper's N), dt = sample interval (the
+ * paper's T/N), M = T/2 + 1 bins, m = frames per group, G = groups.  With
+ * a_k = dt X_k the normalisations read
+ *   S2 = dt c2(X_k, X_k*) / sum g^2,  S3 = dt^2 c3(X_k, X_l, X_{k+l}*) / sum g^3,
+ *   S4 = dt^3 c4(X_k, X_k*, X_l, X_l*) / sum g^4.
+ * Each group gives one estimate S_g; the result is the mean over groups and
+ * the standard error sqrt(G/(G-1) (mean(x^2) - mean(x)^2) / G) of x = Re S_g and
+ * of x = Im S_g separately.
+ *
+ * Conventions shared by every call:
+ *  - No exception or abort crosses the ABI: every call returns an ss_status and
+ *    ss_last_error() describes the last failure of a plan.
+ *  - A plan owns all of its device memory (window, twiddles, carry-over samples,
+ *    centred-spectrum scratch, FP64 accumulators).  The caller owns every input
+ *    and output buffer it passes.
+ *  - All device work of a plan is ordered on the stream given to ss_plan (NULL =
+ *    the legacy default stream).  A plan must not be used by two host threads at
+ *    the same time.
+ *  - Pointers may be device pointers or host pointers (pinned or pageable); the
+ *    library inspects each pointer with cudaPointerGetAttributes.
+ */
+#ifndef POLYSPEC_H
+#define POLYSPEC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ss_plan_s* ss_plan_t;
+
+typedef enum {
+  SS_OK = 0,
+  SS_EINVAL = -1,       /* an argument is out of range or inconsistent            */
+  SS_ENOMEM = -2,       /* a device or pinned-host allocation failed               */
+  SS_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed             */
+  SS_ESTATE = -4,       /* the call is not valid in the plan's current state       */
+  SS_ETIMEOUT = -5,     /* a bounded device-side wait gave up                      */
+  SS_EUNSUPPORTED = -6  /* valid request that this build does not implement        */
+} ss_status;
+
+/* window kinds (Sec. 3, Eq. 17) */
+enum { SS_WIN_HANN = 0, /* periodic Hann, g_i = 0.5 - 0.5 cos(2 pi i / T)            */
+       SS_WIN_ACG = 1   /* approximate confined Gaussian, App. B, Eq. 71; win_param
+                           is sigma_t (the paper's default is 0.14)                  */ };
+
+/* spectral orders, OR-ed together */
+enum { SS_ORDER2 = 1u << 2, SS_ORDER3 = 1u << 3, SS_ORDER4 = 1u << 4 };
+
+/* sample type of the input chunks */
+enum { SS_F32 = 0, /* float32 samples                                          */
+       SS_I16 = 1  /* int16 ADC samples, converted exactly to float32           */ };
+
+/* arithmetic of the fourth-order moment sums (S4); the rest is always FP32
+   with FP64 cross-group accumulation and an FP64 combine */
+enum { SS_PREC_FP32 = 0,    /* FP32 FMA on CUDA cores                          */
+       SS_PREC_TF32X3 = 1,  /* tensor cores, TF32 hi/lo split, 3 products      */
+       SS_PREC_BF16X3 = 2,  /* tensor cores, BF16 hi/lo split, 3 products      */
+       SS_PREC_BF16 = 3     /* tensor cores, plain BF16 inputs                 */ };
+
+/* Size and layout information of a plan (filled by ss_query). */
+typedef struct {
+  int channels, T, M, m;
+  int n_s2, n_s3, n_s4;      /* number of channel combinations per order          */
+  int rows3, rows4;          /* rows of each S3 / S4 grid: M (one channel) or 2M-1 */
+  long long groups;          /* groups accumulated since the last reset           */
+  long long samples;         /* samples per channel consumed since the last reset */
+  long long carried;         /* samples per channel waiting for a full group      */
+  int groups_per_batch;      /* groups processed per device batch                 */
+  size_t device_bytes;       /* device memory held by the plan                    */
+} ss_info;
+
+/* Per-stage device time, summed over launches since the last reset, measured
+   with CUDA events on the plan's stream when timing is enabled
+   (ss_set_timing).  Index 0: frame/window/FFT/centre + S2 (K1); 1: S3 (K2);
+   2: S4 (K3); 3: finalize (K4); 4: host<->device copies. */
+typedef struct {
+  double ms[5];
+  long long launches[5];
+  long long pairs3;          /* bispectrum grid points evaluated per group        */
+  long long pairs4;          /* trispectrum grid points evaluated per group       */
+} ss_stats_t;
+
+/*
+ * ss_plan -- create a plan.
+ *   out        receives the plan handle (set to NULL on failure).
+ *   channels   number of real channels C, 1 <= C <= 4.
+ *   T          samples per frame, a power of two in [8, 4096] (Eq. 16-18).
+ *   dt         sample interval, > 0 (the paper's T/N).
+ *   m          frames per group (k-statistic sample size, Sec. 4.1); m >= 2 for
+ *              S2, m >= 3 with SS_ORDER3, m >= 4 with SS_ORDER4 (the c3 and c4
+ *              prefactors of Eq. 33-34 divide by m-2 and m-3).
+ *   window     SS_WIN_HANN or SS_WIN_ACG; win_param = sigma_t for SS_WIN_ACG.
+ *   orders     OR of SS_ORDER2/3/4, at least one.
+ *   dtype      SS_F32 or SS_I16.
+ *   precision  SS_PREC_* for the S4 moment sums.
+ *   combos     NULL for the default combinations, else n_combos records of five
+ *              ints {order, c0, c1, c2, c3} (channels c0.. of the cumulant of
+ *              Eq. 47 (order 2: C2(c0_k, c1_k*)), Eq. 48 (order 3:
+ *              C3(c0_k, c1_l, c2_{k+l}*)) or Eq. 50 (order 4:
+ *              C4(c0_k, c1_k*, c2_l, c3_l*)); unused entries are ignored.
+ *              Defaults: one channel -> the auto spectra of each requested
+ *              order; several channels -> every multiset of channels for S2 and
+ *              S3 and every distinct pairing for S4 (ss_query gives the counts;
+ *              ss_combos lists them).
+ *   stream     cudaStream_t on which all device work is ordered (NULL = default).
+ * Errors: SS_EINVAL for out-of-range arguments, SS_ENOMEM, SS_ECUDA,
+ * SS_EUNSUPPORTED for combinations this build does not implement.
+ */
+ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int window,
+                  double win_param, unsigned orders, int dtype, int precision,
+                  const int* combos, int n_combos, void* stream);
+
+/*
+ * ss_accumulate -- feed the next n_samples samples of every channel.
+ *   chunk      [channels][n_samples] samples of the plan's dtype, channel-major
+ *              (channel c starts at element c * n_samples).  Device memory or
+ *              host memory (pinned or pageable).
+ * The record is cut into consecutive frames of T samples and groups of m frames
+ * (Eq. 16; Sec. 10: "m subsequent temporal windows").  Samples that do not yet
+ * complete a group are kept by the plan and prepended to the next chunk, so any
+ * split of a record into chunks gives the same groups and the same result.
+ * Work is enqueued on the plan's stream; a device chunk must stay valid until
+ * that stream has passed the call, a host chunk may be reused when the call
+ * returns.
+ * Errors: SS_EINVAL (NULL chunk with n_samples > 0), SS_ESTATE (after a failed
+ * launch), SS_ECUDA.
+ */
+ss_status ss_accumulate(ss_plan_t plan, const void* chunk, size_t n_samples);
+
+/*
+ * ss_finalize -- write the spectra accumulated since the last reset.
+ * Outputs are complex128 values stored as interleaved (re, im) doubles; each
+ * error array holds (err_re, err_im) pairs in the same layout.  Any pointer may
+ * be NULL to skip that output; any may be host or device memory.
+ *   S2   [n_s2][M]
+ *   S3   [n_s3][rows3][M]; one channel: rows3 = M, element (k, l) for k, l >= 0,
+ *        zero outside k + l <= M-1.  Several channels: rows3 = 2M-1, row r holds
+ *        k = r - (M-1), zero outside |k + l| <= M-1.
+ *   S4   [n_s4][rows4][M]; one channel: rows4 = M, (k, l) for k, l >= 0.
+ *        Several channels: rows4 = 2M-1, row r holds k = r - (M-1).
+ * The plan keeps its sums: more ss_accumulate calls may follow.
+ * Leftover samples that never completed a group do not enter the result.
+ * Errors: SS_ESTATE if fewer than two groups were accumulated (no error bar,
+ * Eq. 35 divides by N_p - 1), SS_ECUDA.  Synchronises the plan's stream.
+ */
+ss_status ss_finalize(ss_plan_t plan, double* S2, double* S3, double* S4,
+                      double* S2_err, double* S3_err, double* S4_err);
+
+/* ss_reset -- zero the accumulators, the carry-over and the statistics. */
+ss_status ss_reset(ss_plan_t plan);
+
+/* ss_query -- sizes and layout of the plan's outputs (see ss_info). */
+ss_status ss_query(ss_plan_t plan, ss_info* info);
+
+/* ss_combos -- copy the plan's combinations, (n_s2 + n_s3 + n_s4) records of
+   five ints {order, c0, c1, c2, c3} in output order; out may hold max_records. */
+ss_status ss_combos(ss_plan_t plan, int* out, int max_records);
+
+/* ss_set_timing -- enable (1) or disable (0) per-stage CUDA-event timing. */
+ss_status ss_set_timing(ss_plan_t plan, int enable);
+
+/* ss_stats -- per-stage device times (synchronises the plan's stream). */
+ss_status ss_stats(ss_plan_t plan, ss_stats_t* stats);
+
+/* ss_set_batch -- cap on groups per device batch (0 = automatic).  Changing it
+   only changes scheduling, never the result.  Valid only right after ss_plan or
+   ss_reset. */
+ss_status ss_set_batch(ss_plan_t plan, int groups_per_batch);
+
+/* ss_destroy -- release every resource of the plan (NULL is accepted). */
+ss_status ss_destroy(ss_plan_t plan);
+
+/* ss_last_error -- text of the last failure of the plan, or of the last failed
+   ss_plan when plan is NULL.  Valid until the next call on the same plan. */
+const char* ss_last_error(ss_plan_t plan);
+
+/* ss_version -- library version string. */
+const char* ss_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYSPEC_H */

@@ -1,0 +1,232 @@
+"""Python binding of the GB300 polyspectrum library (libpolyspec.so, C ABI).
+
+Argument marshalling only: every step of the estimator runs in the library's
+CUDA kernels.  The functions mirror include/polyspec.h one to one
+(``ss_plan``, ``ss_accumulate``, ``ss_finalize``, ...); ``Plan`` is a small
+convenience wrapper over them.  Buffers may be torch tensors (CPU or CUDA),
+numpy arrays or raw integer addresses.
+
+Importing this module loads the compiled library and raises ImportError if it
+is missing: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "SS_OK", "SS_EINVAL", "SS_ENOMEM", "SS_ECUDA", "SS_ESTATE", "SS_ETIMEOUT", "SS_EUNSUPPORTED",
+    "SS_WIN_HANN", "SS_WIN_ACG", "SS_ORDER2", "SS_ORDER3", "SS_ORDER4", "SS_F32", "SS_I16",
+    "SS_PREC_FP32", "SS_PREC_TF32X3", "SS_PREC_BF16X3", "SS_PREC_BF16",
+    "SSError", "ss_info", "ss_stats_t", "lib", "LIB_PATH",
+    "ss_plan", "ss_accumulate", "ss_finalize", "ss_reset", "ss_query", "ss_combos",
+    "ss_set_timing", "ss_stats", "ss_set_batch", "ss_destroy", "ss_last_error", "ss_version",
+    "Plan",
+]
+
+SS_OK, SS_EINVAL, SS_ENOMEM, SS_ECUDA, SS_ESTATE, SS_ETIMEOUT, SS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+SS_WIN_HANN, SS_WIN_ACG = 0, 1
+SS_ORDER2, SS_ORDER3, SS_ORDER4 = 1 << 2, 1 << 3, 1 << 4
+SS_F32, SS_I16 = 0, 1
+SS_PREC_FP32, SS_PREC_TF32X3, SS_PREC_BF16X3, SS_PREC_BF16 = 0, 1, 2, 3
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpolyspec.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it first (python -m paper_2505_01231_gb300.build); "
+        "this package has no CPU fallback")
+lib = ctypes.CDLL(LIB_PATH)
+
+
+class ss_info(ctypes.Structure):
+    _fields_ = [("channels", ctypes.c_int), ("T", ctypes.c_int), ("M", ctypes.c_int),
+                ("m", ctypes.c_int), ("n_s2", ctypes.c_int), ("n_s3", ctypes.c_int),
+                ("n_s4", ctypes.c_int), ("rows3", ctypes.c_int), ("rows4", ctypes.c_int),
+                ("groups", ctypes.c_longlong), ("samples", ctypes.c_longlong),
+                ("carried", ctypes.c_longlong), ("groups_per_batch", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+class ss_stats_t(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_longlong * 5),
+                ("pairs3", ctypes.c_longlong), ("pairs4", ctypes.c_longlong)]
+
+
+_P = ctypes.c_void_p
+_sig = {
+    "ss_plan": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint,
+                               ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P]),
+    "ss_accumulate": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "ss_finalize": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "ss_reset": (ctypes.c_int, [_P]),
+    "ss_query": (ctypes.c_int, [_P, ctypes.POINTER(ss_info)]),
+    "ss_combos": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "ss_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ss_stats": (ctypes.c_int, [_P, ctypes.POINTER(ss_stats_t)]),
+    "ss_set_batch": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ss_destroy": (ctypes.c_int, [_P]),
+    "ss_last_error": (ctypes.c_char_p, [_P]),
+    "ss_version": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class SSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def _addr(buf):
+    """Raw address of a torch tensor, numpy array, int or None."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):
+        return buf.data_ptr()
+    if isinstance(buf, np.ndarray):
+        return buf.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _check(status, handle):
+    if status != SS_OK:
+        raise SSError(status, lib.ss_last_error(handle).decode())
+
+
+def ss_plan(channels, T, dt, m, window=SS_WIN_HANN, win_param=0.14,
+            orders=SS_ORDER2 | SS_ORDER3 | SS_ORDER4, dtype=SS_F32, precision=SS_PREC_FP32,
+            combos=None, stream=None):
+    """Create a plan; returns its handle (int).  ``combos``: list of 5-int records."""
+    h = _P()
+    arr = None
+    if combos is not None:
+        arr = (ctypes.c_int * (5 * len(combos)))(*[int(v) for rec in combos for v in rec])
+    st = lib.ss_plan(ctypes.byref(h), channels, T, float(dt), m, window, float(win_param),
+                     orders, dtype, precision, arr, 0 if combos is None else len(combos),
+                     _addr(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream)
+    _check(st, None)
+    return h.value
+
+
+def ss_accumulate(plan, chunk, n_samples):
+    _check(lib.ss_accumulate(plan, _addr(chunk), n_samples), plan)
+
+
+def ss_finalize(plan, S2=None, S3=None, S4=None, S2_err=None, S3_err=None, S4_err=None):
+    _check(lib.ss_finalize(plan, _addr(S2), _addr(S3), _addr(S4), _addr(S2_err), _addr(S3_err),
+                           _addr(S4_err)), plan)
+
+
+def ss_reset(plan):
+    _check(lib.ss_reset(plan), plan)
+
+
+def ss_query(plan):
+    info = ss_info()
+    _check(lib.ss_query(plan, ctypes.byref(info)), plan)
+    return info
+
+
+def ss_combos(plan):
+    info = ss_query(plan)
+    n = info.n_s2 + info.n_s3 + info.n_s4
+    buf = (ctypes.c_int * (5 * max(n, 1)))()
+    _check(lib.ss_combos(plan, buf, n), plan)
+    return [tuple(buf[5 * i:5 * i + 5]) for i in range(n)]
+
+
+def ss_set_timing(plan, enable):
+    _check(lib.ss_set_timing(plan, int(bool(enable))), plan)
+
+
+def ss_stats(plan):
+    s = ss_stats_t()
+    _check(lib.ss_stats(plan, ctypes.byref(s)), plan)
+    return s
+
+
+def ss_set_batch(plan, groups_per_batch):
+    _check(lib.ss_set_batch(plan, groups_per_batch), plan)
+
+
+def ss_destroy(plan):
+    _check(lib.ss_destroy(plan), None)
+
+
+def ss_last_error(plan=None):
+    return lib.ss_last_error(plan).decode()
+
+
+def ss_version():
+    return lib.ss_version().decode()
+
+
+class Plan:
+    """Convenience wrapper: owns a plan handle, returns spectra as numpy arrays."""
+
+    def __init__(self, channels=1, T=256, dt=1.0, m=10, window="hann", sigma_t=0.14,
+                 orders=(2, 3, 4), dtype="f32", precision="fp32", combos=None, stream=None):
+        win = {"hann": SS_WIN_HANN, "acg": SS_WIN_ACG}[window]
+        ords = 0
+        for o in orders:
+            ords |= 1 << o
+        dt_code = {"f32": SS_F32, "i16": SS_I16}[dtype]
+        prec = {"fp32": SS_PREC_FP32, "tf32x3": SS_PREC_TF32X3, "bf16x3": SS_PREC_BF16X3,
+                "bf16": SS_PREC_BF16}[precision]
+        self.handle = ss_plan(channels, T, dt, m, win, sigma_t, ords, dt_code, prec, combos, stream)
+        self.info = ss_query(self.handle)
+
+    def accumulate(self, chunk, n_samples=None):
+        if n_samples is None:
+            n_samples = chunk.shape[-1]
+        ss_accumulate(self.handle, chunk, n_samples)
+
+    def shapes(self):
+        i = ss_query(self.handle)
+        return {"S2": (i.n_s2, i.M), "S3": (i.n_s3, i.rows3, i.M), "S4": (i.n_s4, i.rows4, i.M)}
+
+    def finalize(self):
+        """Returns dict of complex128 arrays S2/S3/S4 and float64 errors [..., 2]."""
+        sh = self.shapes()
+        out = {}
+        bufs = {}
+        for key in ("S2", "S3", "S4"):
+            n = int(np.prod(sh[key]))
+            bufs[key] = np.zeros(sh[key] + (2,), np.float64) if n else None
+            bufs[key + "_err"] = np.zeros(sh[key] + (2,), np.float64) if n else None
+        ss_finalize(self.handle, bufs["S2"], bufs["S3"], bufs["S4"], bufs["S2_err"],
+                    bufs["S3_err"], bufs["S4_err"])
+        for key in ("S2", "S3", "S4"):
+            if bufs[key] is not None:
+                out[key] = bufs[key][..., 0] + 1j * bufs[key][..., 1]
+                out[key + "_err"] = bufs[key + "_err"]
+        out["G"] = ss_query(self.handle).groups
+        return out
+
+    def reset(self):
+        ss_reset(self.handle)
+
+    def combos(self):
+        return ss_combos(self.handle)
+
+    def stats(self):
+        return ss_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            ss_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

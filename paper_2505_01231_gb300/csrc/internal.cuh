@@ -1,0 +1,76 @@
+// internal.cuh -- definitions shared by the kernels and the host runtime of the
+// polyspectrum library (not part of the public ABI; see include/polyspec.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "polyspec.h"
+
+namespace ss {
+
+// Tile edge of the bispectrum and trispectrum kernels in (k, l) grid points.
+constexpr int kTile = 64;
+// Threads per CTA of the frame/FFT kernel and of the pair kernels.
+constexpr int kThreadsK1 = 256;
+constexpr int kThreadsPair = 256;
+
+// Accumulator planes per grid point: sum Re S_g, sum Im S_g, sum (Re S_g)^2,
+// sum (Im S_g)^2, all float64 (Sec. 4.2, Eq. 35-36 need the first and second
+// power sums over the parts).
+constexpr int kPlanes = 4;
+
+// Where the samples of one batch come from: the plan's carry-over buffer
+// (samples left from earlier chunks) followed by the caller's chunk.  Sample s
+// of channel c in the concatenated record is carry[c*carry_stride + s] for
+// s < carry_n and chunk[c*chunk_stride + s - carry_n] otherwise.
+struct SampleSource {
+  const void* carry;
+  long long carry_n;
+  long long carry_stride;
+  const void* chunk;
+  long long chunk_stride;
+  int dtype;  // SS_F32 or SS_I16
+};
+
+// One channel combination of one order; channels as in the ABI records.
+struct Combo {
+  int order;
+  int c[4];
+};
+
+// Kernel launchers (each returns the launch status; all work on `stream`).
+cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G, int C, int T,
+                              int m, int M, int Mp, const float* win, const float2* tw,
+                              float2* spec, long long spec_chan_stride, const int* s2_auto,
+                              double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream);
+
+cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G, int m, int M,
+                               int Mp, const int4* pairs, int n_pairs, float pref2, double* acc2,
+                               long long plane, int nsm, cudaStream_t stream);
+
+// acc points at the combination's first accumulator plane; `plane` is the
+// distance in doubles between the four planes (sum Re, sum Im, sumsq Re, sumsq Im).
+cudaError_t launch_k2_bispec(const float2* spec_a, const float2* spec_b, const float2* spec_c,
+                             int G, int m, int M, int Mp, const int2* tiles, int n_tiles,
+                             int cross, int group_splits, float pref3, double* acc,
+                             long long plane, int rows, cudaStream_t stream);
+
+cudaError_t launch_k3_trispec(const float2* spec, int G, int m, int M, int Mp, const int2* tiles,
+                              int n_tiles, int group_splits, float pref4a, float pref4b,
+                              double* acc, long long plane, cudaStream_t stream);
+
+cudaError_t launch_k4_finalize(const double* acc, int n_combos, int rows, int M, int layout,
+                               long long G, double norm, double* out, double* err,
+                               cudaStream_t stream);
+
+// Layout codes of launch_k4_finalize.
+enum { kLayoutVector = 0,       // S2: [M]
+       kLayoutS3Single = 1,     // one channel, computed for k <= l, mirrored; k+l <= M-1
+       kLayoutS4Single = 2,     // one channel, computed for k <= l, mirrored
+       kLayoutCross = 3 };      // full [2M-1][M] grid, no mirroring
+
+}  // namespace ss

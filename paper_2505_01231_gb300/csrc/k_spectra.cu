@@ -1,0 +1,288 @@
+// k_spectra.cu -- K1: frame, window, real FFT, group centring and S2.
+//
+// One CTA handles one group of m consecutive frames at a time (persistent loop
+// over groups).  For every channel and frame j of the group it
+//   1. reads the T samples of the frame (Sec. 3, Eq. 16) from the concatenation
+//      carry-over | chunk and multiplies them by the window g_i / sqrt(sum g^2)
+//      (Eq. 17; the scale is undone in the finalize step),
+//   2. packs them as N = T/2 complex points y_n = x_{2n} + j x_{2n+1} and runs a
+//      Stockham autosort FFT with the POSITIVE exponent of Eq. 18 (radix-8/4/2
+//      butterflies in registers, ping-pong buffers in shared memory),
+//   3. splits the half-length transform into the T/2+1 coefficients
+//      X_k = E_k + e^{+2 pi j k/T} O_k of the real frame, and writes them.
+// After the m frames it subtracts the group mean of every bin (the centred
+// samples of the factorised k-statistics, App. H, Eq. 85), and forms the
+// per-group S2 estimate c2 = 1/(m-1) sum_j |dX_jk|^2 (Eq. 32 with y = x*),
+// whose sum and sum of squares over groups are accumulated for Eq. 35-36.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace ss {
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// multiplication by +j
+__device__ __forceinline__ float2 cj(float2 a) { return make_float2(-a.y, a.x); }
+
+// Radix-R DFT with the positive exponent, V_q = sum_r v_r e^{+2 pi j rq/R}.
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+  const float2 s02 = cadd(v0, v2), d02 = csub(v0, v2);
+  const float2 s13 = cadd(v1, v3), d13 = cj(csub(v1, v3));
+  v0 = cadd(s02, s13);
+  v2 = csub(s02, s13);
+  v1 = cadd(d02, d13);
+  v3 = csub(d02, d13);
+}
+
+template <int R>
+__device__ __forceinline__ void dft(float2 (&v)[R]);
+
+template <>
+__device__ __forceinline__ void dft<2>(float2 (&v)[2]) {
+  const float2 a = v[0];
+  v[0] = cadd(a, v[1]);
+  v[1] = csub(a, v[1]);
+}
+
+template <>
+__device__ __forceinline__ void dft<4>(float2 (&v)[4]) {
+  dft4(v[0], v[1], v[2], v[3]);
+}
+
+template <>
+__device__ __forceinline__ void dft<8>(float2 (&v)[8]) {
+  // even/odd split: V_q = E_q + w^q O_q, V_{q+4} = E_q - w^q O_q, w = e^{+2 pi j/8}
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4(e0, e1, e2, e3);
+  dft4(o0, o1, o2, o3);
+  const float h = 0.70710678118654752f;
+  o1 = make_float2((o1.x - o1.y) * h, (o1.x + o1.y) * h);    // * (1 + j)/sqrt 2
+  o2 = cj(o2);                                                // * j
+  o3 = make_float2((-o3.x - o3.y) * h, (o3.x - o3.y) * h);   // * (-1 + j)/sqrt 2
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+// One Stockham pass: sub-transforms of length Ns are combined R at a time into
+// length Ns*R.  x, y: N complex points in shared memory; tw[a] = e^{+2 pi j a/T}.
+template <int R>
+__device__ __forceinline__ void stockham_pass(const float2* __restrict__ x, float2* __restrict__ y,
+                                              int N, int Ns, const float2* __restrict__ tw,
+                                              int T) {
+  const int NR = N / R;
+  const int tw_scale = T / (Ns * R);
+  for (int j = threadIdx.x; j < NR; j += blockDim.x) {
+    const int k = j & (Ns - 1);
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[j + r * NR];
+    if (Ns > 1) {
+      const int step = k * tw_scale;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(&tw[r * step]));
+    }
+    dft<R>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) y[base + q * Ns] = v[q];
+  }
+}
+
+template <int DTYPE>
+__device__ __forceinline__ float load_sample(const SampleSource& s, int c, long long idx) {
+  if (idx < s.carry_n) {
+    const long long o = (long long)c * s.carry_stride + idx;
+    if (DTYPE == SS_F32) return __ldg(static_cast<const float*>(s.carry) + o);
+    return (float)__ldg(static_cast<const short*>(s.carry) + o);
+  }
+  const long long o = (long long)c * s.chunk_stride + (idx - s.carry_n);
+  if (DTYPE == SS_F32) return __ldg(static_cast<const float*>(s.chunk) + o);
+  return (float)__ldg(static_cast<const short*>(s.chunk) + o);
+}
+
+template <int DTYPE>
+__global__ void __launch_bounds__(kThreadsK1)
+k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int M, int Mp,
+           const float* __restrict__ win, const float2* __restrict__ tw,
+           float2* __restrict__ spec, long long chan_stride, const int* __restrict__ s2_auto,
+           double* __restrict__ acc2, int n_s2, float pref2) {
+  extern __shared__ float4 smem_raw[];
+  const int N = T / 2;
+  float2* bufA = reinterpret_cast<float2*>(smem_raw);
+  float2* bufB = bufA + N;
+  float2* gsum = bufB + N;                                        // [M]
+  float* s2sum = reinterpret_cast<float*>(gsum + M);             // [C][M]
+  float* s2sq = s2sum + C * M;                                    // [C][M]
+
+  for (int i = threadIdx.x; i < 2 * C * M; i += blockDim.x) s2sum[i] = 0.f;
+
+  for (int g = blockIdx.x; g < G; g += gridDim.x) {
+    for (int c = 0; c < C; ++c) {
+      float2* grow = spec + (long long)c * chan_stride + (long long)g * m * Mp;
+      for (int k = threadIdx.x; k < M; k += blockDim.x) gsum[k] = make_float2(0.f, 0.f);
+      for (int j = 0; j < m; ++j) {
+        const long long s0 = sample0 + ((long long)g * m + j) * T;
+        __syncthreads();  // bufA is free (previous frame's post-processing done)
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+          const float x0 = load_sample<DTYPE>(src, c, s0 + 2 * n);
+          const float x1 = load_sample<DTYPE>(src, c, s0 + 2 * n + 1);
+          bufA[n] = make_float2(x0 * __ldg(&win[2 * n]), x1 * __ldg(&win[2 * n + 1]));
+        }
+        __syncthreads();
+        float2* x = bufA;
+        float2* y = bufB;
+        int Ns = 1;
+        int rem = N;
+        while (rem > 1) {
+          if (rem % 8 == 0 && rem != 16) {
+            stockham_pass<8>(x, y, N, Ns, tw, T);
+            Ns *= 8; rem /= 8;
+          } else if (rem % 4 == 0) {
+            stockham_pass<4>(x, y, N, Ns, tw, T);
+            Ns *= 4; rem /= 4;
+          } else {
+            stockham_pass<2>(x, y, N, Ns, tw, T);
+            Ns *= 2; rem /= 2;
+          }
+          __syncthreads();
+          float2* t = x; x = y; y = t;
+        }
+        // x holds Y_n; X_k = 1/2 [(Y_k + Y*_{N-k}) - j w^k (Y_k - Y*_{N-k})], w = e^{+2 pi j/T}
+        float2* row = grow + (long long)j * Mp;
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+          const float2 yk = x[k == N ? 0 : k];
+          const float2 yr = x[k == 0 ? 0 : N - k];
+          const float2 yc = make_float2(yr.x, -yr.y);
+          const float2 s = cadd(yk, yc);
+          const float2 wd = cmul(__ldg(&tw[k]), csub(yk, yc));
+          const float2 X = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
+          row[k] = X;
+          gsum[k] = cadd(gsum[k], X);
+        }
+      }
+      // centre each bin over the group and form the per-group S2 estimate
+      const float inv_m = 1.0f / (float)m;
+      const int ia = s2_auto[c];
+      for (int k = threadIdx.x; k < Mp; k += blockDim.x) {
+        if (k >= M) {
+          for (int j = 0; j < m; ++j) grow[(long long)j * Mp + k] = make_float2(0.f, 0.f);
+          continue;
+        }
+        const float2 mean = make_float2(gsum[k].x * inv_m, gsum[k].y * inv_m);
+        float p = 0.f;
+        for (int j = 0; j < m; ++j) {
+          float2* e = grow + (long long)j * Mp + k;
+          const float2 d = csub(*e, mean);
+          *e = d;
+          p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+        }
+        if (ia >= 0) {
+          const float c2 = p * pref2;
+          s2sum[c * M + k] += c2;
+          s2sq[c * M + k] = fmaf(c2, c2, s2sq[c * M + k]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // flush the CTA's float32 partial sums into the float64 accumulators
+  const long long plane = (long long)n_s2 * M;
+  for (int c = 0; c < C; ++c) {
+    const int ia = s2_auto[c];
+    if (ia < 0) continue;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+      atomicAdd(acc2 + 0 * plane + (long long)ia * M + k, (double)s2sum[c * M + k]);
+      atomicAdd(acc2 + 2 * plane + (long long)ia * M + k, (double)s2sq[c * M + k]);
+    }
+  }
+}
+
+// Cross-channel S2 (Sec. 7, Eq. 47): c2(a_k, b_k*) = 1/(m-1) sum_j da_jk db_jk*
+// per group, from the centred spectra K1 wrote.  Thread = (combination, bin);
+// blockIdx.y splits the groups; float32 sums per CTA, float64 accumulation.
+__global__ void k1_cross_s2(const float2* __restrict__ spec, long long chan_stride, int G, int m,
+                            int M, int Mp, const int4* __restrict__ pairs, int groups_per_cta,
+                            float pref2, double* __restrict__ acc2, long long plane) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  const int4 pr = pairs[blockIdx.z];
+  const float2* A = spec + pr.x * chan_stride;
+  const float2* B = spec + pr.y * chan_stride;
+  const int g0 = blockIdx.y * groups_per_cta;
+  const int g1 = min(G, g0 + groups_per_cta);
+  float sr = 0.f, si = 0.f, qr = 0.f, qi = 0.f;
+  for (int g = g0; g < g1; ++g) {
+    float cr = 0.f, ci = 0.f;
+    for (int j = 0; j < m; ++j) {
+      const long long o = ((long long)g * m + j) * Mp + k;
+      const float2 a = A[o], b = B[o];
+      cr = fmaf(a.x, b.x, fmaf(a.y, b.y, cr));
+      ci = fmaf(a.y, b.x, fmaf(-a.x, b.y, ci));
+    }
+    cr *= pref2;
+    ci *= pref2;
+    sr += cr;
+    si += ci;
+    qr = fmaf(cr, cr, qr);
+    qi = fmaf(ci, ci, qi);
+  }
+  const long long o = (long long)pr.z * M + k;
+  atomicAdd(acc2 + o, (double)sr);
+  atomicAdd(acc2 + plane + o, (double)si);
+  atomicAdd(acc2 + 2 * plane + o, (double)qr);
+  atomicAdd(acc2 + 3 * plane + o, (double)qi);
+}
+
+}  // namespace
+
+cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G, int C, int T,
+                              int m, int M, int Mp, const float* win, const float2* tw,
+                              float2* spec, long long spec_chan_stride, const int* s2_auto,
+                              double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream) {
+  if (G <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(T / 2) * 2 * sizeof(float2) + (size_t)M * sizeof(float2) +
+                      (size_t)2 * C * M * sizeof(float);
+  if (grid > G) grid = G;
+  cudaError_t e;
+  if (src.dtype == SS_F32) {
+    e = cudaFuncSetAttribute(k1_spectra<SS_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k1_spectra<SS_F32><<<grid, kThreadsK1, smem, stream>>>(src, sample0, G, C, T, m, M, Mp, win,
+                                                             tw, spec, spec_chan_stride, s2_auto,
+                                                             acc2, n_s2, pref2);
+  } else {
+    e = cudaFuncSetAttribute(k1_spectra<SS_I16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k1_spectra<SS_I16><<<grid, kThreadsK1, smem, stream>>>(src, sample0, G, C, T, m, M, Mp, win,
+                                                             tw, spec, spec_chan_stride, s2_auto,
+                                                             acc2, n_s2, pref2);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G, int m, int M,
+                               int Mp, const int4* pairs, int n_pairs, float pref2, double* acc2,
+                               long long plane, int nsm, cudaStream_t stream) {
+  if (G <= 0 || n_pairs <= 0) return cudaSuccess;
+  const int bx = (M + 127) / 128;
+  int splits = std::max(1, (4 * nsm) / std::max(1, bx * n_pairs));
+  splits = std::min(splits, std::max(1, G / 8));
+  const int gpc = (G + splits - 1) / splits;
+  splits = (G + gpc - 1) / gpc;
+  dim3 grid(bx, splits, n_pairs);
+  k1_cross_s2<<<grid, 128, 0, stream>>>(spec, chan_stride, G, m, M, Mp, pairs, gpc, pref2, acc2,
+                                        plane);
+  return cudaGetLastError();
+}
+
+}  // namespace ss

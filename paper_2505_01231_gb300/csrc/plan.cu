@@ -1,0 +1,745 @@
+// plan.cu -- host runtime behind the C ABI of include/polyspec.h.
+//
+// A plan owns the window and twiddle tables, the carry-over of samples that do
+// not yet complete a group, the scratch of centred spectra for one batch of
+// groups, and the float64 accumulators (sum and sum of squares of every
+// per-group estimate, Sec. 4.2).  ss_accumulate cuts the concatenation
+// carry-over | chunk into whole groups of m frames (Sec. 3, Eq. 16) and runs,
+// batch after batch on the plan's stream,
+//   K1 frame/window/FFT/centre + S2 -> K2 bispectrum (per S3 combination)
+//   -> K3 trispectrum cut (per S4 combination);
+// ss_finalize runs K4 (mean and standard error, Eq. 35-36) and copies out.
+// Host chunks are copied to the device through two staging buffers on a
+// separate copy stream, so the copy of one piece overlaps the kernels of the
+// previous one.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace ss;
+
+namespace {
+
+thread_local std::string g_plan_error;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+}  // namespace
+
+struct ss_plan_s {
+  // configuration
+  int C = 1, T = 0, M = 0, Mp = 0, m = 0, window = 0, dtype = 0, precision = 0;
+  unsigned orders = 0;
+  double dt = 1.0, win_param = 0.14;
+  cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  int device = 0, nsm = 1;
+  size_t elem = 4;
+  std::vector<Combo> c2, c3, c4;
+  int rows3 = 0, rows4 = 0;
+  // normalisation (Eq. 23, 28, 31 with the window scaled by 1/sqrt(sum g^2))
+  double sg2 = 0, sg3 = 0, sg4 = 0, norm2 = 0, norm3 = 0, norm4 = 0;
+  // device tables and buffers
+  float* d_win = nullptr;
+  float2* d_tw = nullptr;
+  void* d_carry = nullptr;
+  long long carry_n = 0;
+  float2* d_spec = nullptr;
+  int Gb_max = 0, Gb_user = 0;
+  double *d_acc2 = nullptr, *d_acc3 = nullptr, *d_acc4 = nullptr;
+  size_t n_acc2 = 0, n_acc3 = 0, n_acc4 = 0;
+  int* d_s2auto = nullptr;
+  int4* d_s2cross = nullptr;
+  int n_s2cross = 0;
+  int2 *d_tiles3 = nullptr, *d_tiles4 = nullptr;
+  int n_tiles3 = 0, n_tiles4 = 0;
+  long long pairs3 = 0, pairs4 = 0;
+  void* d_stage[2] = {nullptr, nullptr};
+  long long stage_n = 0;
+  cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  double* d_out = nullptr;
+  size_t out_doubles = 0;
+  size_t device_bytes = 0;
+  // progress
+  long long groups = 0, samples = 0;
+  // timing
+  bool timing = false;
+  std::vector<EventPair> ev[5];
+  long long launches[5] = {0, 0, 0, 0, 0};
+  // errors
+  bool broken = false;
+  std::string err;
+};
+
+namespace {
+
+ss_status fail(ss_plan_s* p, ss_status st, const std::string& msg) {
+  if (p) {
+    p->err = msg;
+    if (st == SS_ECUDA) p->broken = true;
+  } else {
+    g_plan_error = msg;
+  }
+  return st;
+}
+
+ss_status cuda_fail(ss_plan_s* p, cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a non-sticky error
+  return fail(p, e == cudaErrorMemoryAllocation ? SS_ENOMEM : SS_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SS_TRY(p, call)                                        \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail((p), e_, #call);   \
+  } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(ss_plan_s* p, T** ptr, size_t bytes) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+  if (e == cudaSuccess) p->device_bytes += bytes;
+  return e;
+}
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Default combinations (Sec. 9): every multiset for S2 and S3, every unordered
+// pair of unordered channel pairs for the S4 cut C4(a_k, b_k*, c_l, d_l*).
+void default_combos(ss_plan_s* p) {
+  const int C = p->C;
+  if (p->orders & SS_ORDER2)
+    for (int a = 0; a < C; ++a)
+      for (int b = a; b < C; ++b) p->c2.push_back({2, {a, b, -1, -1}});
+  if (p->orders & SS_ORDER3)
+    for (int a = 0; a < C; ++a)
+      for (int b = a; b < C; ++b)
+        for (int c = b; c < C; ++c) p->c3.push_back({3, {a, b, c, -1}});
+  if (p->orders & SS_ORDER4) {
+    std::vector<std::pair<int, int>> pairs;
+    for (int a = 0; a < C; ++a)
+      for (int b = a; b < C; ++b) pairs.push_back({a, b});
+    for (size_t i = 0; i < pairs.size(); ++i)
+      for (size_t j = i; j < pairs.size(); ++j)
+        p->c4.push_back({4, {pairs[i].first, pairs[i].second, pairs[j].first, pairs[j].second}});
+  }
+}
+
+bool in_domain3(int k, int l, int M, bool cross) {
+  if (cross) return l >= 0 && l < M && k > -M && k < M && k + l < M && k + l > -M;
+  return k >= 0 && k <= l && k + l < M;
+}
+
+void build_tiles(ss_plan_s* p, std::vector<int2>& t3, std::vector<int2>& t4) {
+  const int M = p->M;
+  const bool cross = p->C > 1;
+  p->pairs3 = 0;
+  p->pairs4 = 0;
+  if (!cross) {
+    for (int k0 = 0; k0 < M; k0 += kTile)
+      for (int l0 = k0; l0 < M; l0 += kTile) {
+        if (k0 + l0 <= M - 1) t3.push_back(make_int2(k0, l0));
+        t4.push_back(make_int2(k0, l0));
+      }
+    for (int k = 0; k < M; ++k)
+      for (int l = k; l < M; ++l) {
+        if (k + l < M) ++p->pairs3;
+        ++p->pairs4;
+      }
+  } else {
+    const int kmin = -((M - 1 + kTile - 1) / kTile) * kTile;
+    for (int k0 = kmin; k0 < M; k0 += kTile)
+      for (int l0 = 0; l0 < M; l0 += kTile) {
+        bool any3 = false;
+        for (int a = 0; a < kTile && !any3; ++a)
+          for (int b = 0; b < kTile && !any3; ++b) any3 = in_domain3(k0 + a, l0 + b, M, true);
+        if (any3) t3.push_back(make_int2(k0, l0));
+        if (k0 + kTile > -M) t4.push_back(make_int2(k0, l0));
+      }
+    for (int k = -(M - 1); k < M; ++k)
+      for (int l = 0; l < M; ++l) {
+        if (in_domain3(k, l, M, true)) ++p->pairs3;
+        ++p->pairs4;
+      }
+  }
+}
+
+int group_splits(const ss_plan_s* p, int n_tiles, int G) {
+  if (n_tiles <= 0) return 1;
+  // about four CTAs per SM in total, at least 16 groups per CTA
+  int s = std::max(1, (4 * p->nsm + n_tiles - 1) / n_tiles);
+  s = std::min(s, std::max(1, G / 16));
+  return s;
+}
+
+void record(ss_plan_s* p, int stage, cudaStream_t s, bool start) {
+  if (!p->timing) return;
+  if (start) {
+    EventPair e;
+    cudaEventCreate(&e.a);
+    cudaEventCreate(&e.b);
+    cudaEventRecord(e.a, s);
+    p->ev[stage].push_back(e);
+  } else {
+    cudaEventRecord(p->ev[stage].back().b, s);
+    ++p->launches[stage];
+  }
+}
+
+void clear_events(ss_plan_s* p) {
+  for (auto& v : p->ev) {
+    for (auto& e : v) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    v.clear();
+  }
+  for (auto& l : p->launches) l = 0;
+}
+
+// Process n samples per channel that are already on the device (channel c at
+// ptr + c * stride elements).
+ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long stride) {
+  const long long per_group = (long long)p->m * p->T;
+  const long long total = p->carry_n + n;
+  const long long Gn = total / per_group;
+  const char* base = static_cast<const char*>(ptr);
+  if (Gn > 0) {
+    const long long nb = (Gn + p->Gb_max - 1) / p->Gb_max;
+    const long long gb = (Gn + nb - 1) / nb;
+    SampleSource src;
+    src.carry = p->d_carry;
+    src.carry_n = p->carry_n;
+    src.carry_stride = per_group;
+    src.chunk = ptr;
+    src.chunk_stride = stride;
+    src.dtype = p->dtype;
+    const long long chan_stride = (long long)p->Gb_max * p->m * p->Mp;
+    const float pref2 = 1.0f / (float)(p->m - 1);
+    const double md = p->m;
+    const float pref3 = (float)(md / ((md - 1) * (md - 2)));
+    const float pref4a = (float)(md * (md + 1) / ((md - 1) * (md - 2) * (md - 3)));
+    const float pref4b = (float)(1.0 / ((md - 2) * (md - 3)));
+    for (long long g0 = 0; g0 < Gn; g0 += gb) {
+      const int cnt = (int)std::min(gb, Gn - g0);
+      record(p, 0, p->stream, true);
+      SS_TRY(p, launch_k1_spectra(src, g0 * per_group, cnt, p->C, p->T, p->m, p->M, p->Mp,
+                                  p->d_win, p->d_tw, p->d_spec, chan_stride, p->d_s2auto,
+                                  p->d_acc2, (int)p->c2.size(), pref2, 4 * p->nsm, p->stream));
+      if (p->n_s2cross > 0)
+        SS_TRY(p, launch_k1_cross_s2(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp,
+                                     p->d_s2cross, p->n_s2cross, pref2, p->d_acc2,
+                                     (long long)p->c2.size() * p->M, p->nsm, p->stream));
+      record(p, 0, p->stream, false);
+      if (!p->c3.empty()) {
+        record(p, 1, p->stream, true);
+        const long long plane = (long long)p->c3.size() * p->rows3 * p->M;
+        for (size_t i = 0; i < p->c3.size(); ++i) {
+          const Combo& cb = p->c3[i];
+          SS_TRY(p, launch_k2_bispec(p->d_spec + cb.c[0] * chan_stride,
+                                     p->d_spec + cb.c[1] * chan_stride,
+                                     p->d_spec + cb.c[2] * chan_stride, cnt, p->m, p->M, p->Mp,
+                                     p->d_tiles3, p->n_tiles3, p->C > 1 ? 1 : 0,
+                                     group_splits(p, p->n_tiles3, cnt), pref3,
+                                     p->d_acc3 + (long long)i * p->rows3 * p->M, plane, p->rows3,
+                                     p->stream));
+        }
+        record(p, 1, p->stream, false);
+      }
+      if (!p->c4.empty()) {
+        record(p, 2, p->stream, true);
+        const long long plane = (long long)p->c4.size() * p->rows4 * p->M;
+        for (size_t i = 0; i < p->c4.size(); ++i) {
+          const Combo& cb = p->c4[i];
+          SS_TRY(p, launch_k3_trispec(p->d_spec + cb.c[0] * chan_stride, cnt, p->m, p->M, p->Mp,
+                                      p->d_tiles4, p->n_tiles4,
+                                      group_splits(p, p->n_tiles4, cnt), pref4a, pref4b,
+                                      p->d_acc4 + (long long)i * p->rows4 * p->M, plane,
+                                      p->stream));
+        }
+        record(p, 2, p->stream, false);
+      }
+    }
+  }
+  // keep the samples that do not complete a group
+  const long long left = total - Gn * per_group;
+  const size_t e = p->elem;
+  char* carry = static_cast<char*>(p->d_carry);
+  for (int c = 0; c < p->C; ++c) {
+    char* dst = carry + (size_t)c * per_group * e;
+    const char* src = base + (size_t)c * stride * e;
+    if (Gn == 0) {
+      if (n > 0)
+        SS_TRY(p, cudaMemcpyAsync(dst + p->carry_n * e, src, n * e, cudaMemcpyDeviceToDevice,
+                                  p->stream));
+    } else if (left > 0) {
+      SS_TRY(p, cudaMemcpyAsync(dst, src + (n - left) * e, left * e, cudaMemcpyDeviceToDevice,
+                                p->stream));
+    }
+  }
+  p->carry_n = left;
+  p->groups += Gn;
+  p->samples += n;
+  return SS_OK;
+}
+
+ss_status ensure_stage(ss_plan_s* p) {
+  if (p->d_stage[0]) return SS_OK;
+  // 32 Mi samples per channel per staging buffer
+  p->stage_n = (32ll << 20) / std::max(1, p->C);
+  for (int i = 0; i < 2; ++i) {
+    SS_TRY(p, dev_alloc(p, &p->d_stage[i], (size_t)p->stage_n * p->C * p->elem));
+    SS_TRY(p, cudaEventCreateWithFlags(&p->ev_ready[i], cudaEventDisableTiming));
+    SS_TRY(p, cudaEventCreateWithFlags(&p->ev_free[i], cudaEventDisableTiming));
+  }
+  SS_TRY(p, cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+  return SS_OK;
+}
+
+ss_status process_host(ss_plan_s* p, const void* chunk, long long n) {
+  ss_status st = ensure_stage(p);
+  if (st != SS_OK) return st;
+  const char* src = static_cast<const char*>(chunk);
+  const size_t e = p->elem;
+  int piece = 0;
+  for (long long off = 0; off < n; off += p->stage_n, ++piece) {
+    const int b = piece & 1;
+    const long long len = std::min(p->stage_n, n - off);
+    SS_TRY(p, cudaStreamWaitEvent(p->copy_stream, p->ev_free[b], 0));
+    record(p, 4, p->copy_stream, true);
+    for (int c = 0; c < p->C; ++c)
+      SS_TRY(p, cudaMemcpyAsync(static_cast<char*>(p->d_stage[b]) + (size_t)c * p->stage_n * e,
+                                src + ((size_t)c * n + off) * e, len * e,
+                                cudaMemcpyHostToDevice, p->copy_stream));
+    record(p, 4, p->copy_stream, false);
+    SS_TRY(p, cudaEventRecord(p->ev_ready[b], p->copy_stream));
+    SS_TRY(p, cudaStreamWaitEvent(p->stream, p->ev_ready[b], 0));
+    st = process_device(p, p->d_stage[b], len, p->stage_n);
+    if (st != SS_OK) return st;
+    SS_TRY(p, cudaEventRecord(p->ev_free[b], p->stream));
+  }
+  // the caller may reuse its buffer once every copy out of it has finished
+  SS_TRY(p, cudaStreamSynchronize(p->copy_stream));
+  return SS_OK;
+}
+
+ss_status zero_state(ss_plan_s* p) {
+  if (p->d_acc2) SS_TRY(p, cudaMemsetAsync(p->d_acc2, 0, p->n_acc2 * sizeof(double), p->stream));
+  if (p->d_acc3) SS_TRY(p, cudaMemsetAsync(p->d_acc3, 0, p->n_acc3 * sizeof(double), p->stream));
+  if (p->d_acc4) SS_TRY(p, cudaMemsetAsync(p->d_acc4, 0, p->n_acc4 * sizeof(double), p->stream));
+  p->carry_n = 0;
+  p->groups = 0;
+  p->samples = 0;
+  clear_events(p);
+  return SS_OK;
+}
+
+ss_status alloc_spec(ss_plan_s* p) {
+  if (p->d_spec) {
+    cudaFree(p->d_spec);
+    p->device_bytes -= (size_t)p->C * p->Gb_max * p->m * p->Mp * sizeof(float2);
+    p->d_spec = nullptr;
+  }
+  const size_t per_group = (size_t)p->C * p->m * p->Mp * sizeof(float2);
+  int gb = p->Gb_user;
+  if (gb <= 0) {
+    // about 1.5 GiB of centred spectra per batch, at least one group
+    gb = (int)std::max<size_t>(1, (size_t)(1536ull << 20) / per_group);
+  }
+  p->Gb_max = gb;
+  SS_TRY(p, dev_alloc(p, &p->d_spec, per_group * gb));
+  return SS_OK;
+}
+
+void destroy(ss_plan_s* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->copy_stream) {
+    cudaStreamSynchronize(p->copy_stream);
+    cudaStreamDestroy(p->copy_stream);
+  }
+  clear_events(p);
+  for (int i = 0; i < 2; ++i) {
+    if (p->ev_ready[i]) cudaEventDestroy(p->ev_ready[i]);
+    if (p->ev_free[i]) cudaEventDestroy(p->ev_free[i]);
+    cudaFree(p->d_stage[i]);
+  }
+  cudaFree(p->d_win);
+  cudaFree(p->d_tw);
+  cudaFree(p->d_carry);
+  cudaFree(p->d_spec);
+  cudaFree(p->d_acc2);
+  cudaFree(p->d_acc3);
+  cudaFree(p->d_acc4);
+  cudaFree(p->d_s2auto);
+  cudaFree(p->d_s2cross);
+  cudaFree(p->d_tiles3);
+  cudaFree(p->d_tiles4);
+  cudaFree(p->d_out);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ss_version(void) { return "polyspec-gb300 0.1 (sm_103a)"; }
+
+const char* ss_last_error(ss_plan_t plan) {
+  return plan ? plan->err.c_str() : g_plan_error.c_str();
+}
+
+ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int window,
+                  double win_param, unsigned orders, int dtype, int precision,
+                  const int* combos, int n_combos, void* stream) {
+  if (!out) return fail(nullptr, SS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (channels < 1 || channels > 4) return fail(nullptr, SS_EINVAL, "channels must be 1..4");
+  if (!is_pow2(T) || T < 8 || T > 4096)
+    return fail(nullptr, SS_EINVAL, "T must be a power of two in [8, 4096]");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, SS_EINVAL, "dt must be > 0");
+  if (orders == 0 || (orders & ~(unsigned)(SS_ORDER2 | SS_ORDER3 | SS_ORDER4)))
+    return fail(nullptr, SS_EINVAL, "orders must be a non-empty OR of SS_ORDER2/3/4");
+  if (m < 2) return fail(nullptr, SS_EINVAL, "S2 needs m >= 2 (Eq. 32)");
+  if ((orders & SS_ORDER3) && m < 3) return fail(nullptr, SS_EINVAL, "S3 needs m >= 3 (Eq. 33)");
+  if ((orders & SS_ORDER4) && m < 4) return fail(nullptr, SS_EINVAL, "S4 needs m >= 4 (Eq. 34)");
+  if (window != SS_WIN_HANN && window != SS_WIN_ACG)
+    return fail(nullptr, SS_EINVAL, "unknown window");
+  if (window == SS_WIN_ACG && !(win_param > 0.0 && win_param < 10.0))
+    return fail(nullptr, SS_EINVAL, "sigma_t of the confined Gaussian must be in (0, 10)");
+  if (dtype != SS_F32 && dtype != SS_I16) return fail(nullptr, SS_EINVAL, "unknown dtype");
+  if (precision < SS_PREC_FP32 || precision > SS_PREC_BF16)
+    return fail(nullptr, SS_EINVAL, "unknown precision");
+  if (combos && n_combos <= 0) return fail(nullptr, SS_EINVAL, "n_combos must be > 0");
+
+  ss_plan_s* p = new ss_plan_s();
+  p->C = channels;
+  p->T = T;
+  p->M = T / 2 + 1;
+  p->Mp = (p->M + 3) & ~3;
+  p->m = m;
+  p->dt = dt;
+  p->window = window;
+  p->win_param = win_param;
+  p->orders = orders;
+  p->dtype = dtype;
+  p->precision = precision;
+  p->elem = dtype == SS_F32 ? 4 : 2;
+  p->stream = static_cast<cudaStream_t>(stream);
+
+  if (combos) {
+    for (int i = 0; i < n_combos; ++i) {
+      const int* r = combos + 5 * i;
+      Combo cb{r[0], {r[1], r[2], r[3], r[4]}};
+      const int n = cb.order;
+      if (n < 2 || n > 4 || !(orders & (1u << n))) {
+        delete p;
+        return fail(nullptr, SS_EINVAL, "combination of an order the plan does not compute");
+      }
+      for (int q = 0; q < n; ++q)
+        if (cb.c[q] < 0 || cb.c[q] >= channels) {
+          delete p;
+          return fail(nullptr, SS_EINVAL, "combination names a channel out of range");
+        }
+      (n == 2 ? p->c2 : n == 3 ? p->c3 : p->c4).push_back(cb);
+    }
+  } else {
+    default_combos(p);
+  }
+  if (precision != SS_PREC_FP32 && !p->c4.empty()) {
+    delete p;
+    return fail(nullptr, SS_EUNSUPPORTED, "tensor-core S4 precisions are not built yet");
+  }
+  for (const Combo& cb : p->c4)
+    if (channels > 1 || cb.c[0] != cb.c[1] || cb.c[0] != cb.c[2] || cb.c[0] != cb.c[3]) {
+      delete p;
+      return fail(nullptr, SS_EUNSUPPORTED, "cross-channel S4 is not built yet");
+    }
+  p->rows3 = channels == 1 ? p->M : 2 * p->M - 1;
+  p->rows4 = channels == 1 ? p->M : 2 * p->M - 1;
+
+  ss_status st;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    st = cuda_fail(nullptr, e, "cudaGetDevice");
+    delete p;
+    return st;
+  }
+  cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
+
+  // window (Eq. 17 / App. B) and its power sums, in float64
+  std::vector<double> g(T);
+  for (int i = 0; i < T; ++i) {
+    if (window == SS_WIN_HANN) {
+      g[i] = 0.5 - 0.5 * std::cos(2.0 * M_PI * i / T);
+    } else {
+      const double N = T, s = win_param, c = (N - 1.0) / 2.0;
+      auto G = [&](double x) { return std::exp(-(x - c) * (x - c) / (4.0 * N * N * s * s)); };
+      g[i] = G(i) - G(-0.5) * (G(i + N) + G(i - N)) / (G(-0.5 + N) + G(-0.5 - N));
+    }
+  }
+  for (int i = 0; i < T; ++i) {
+    p->sg2 += g[i] * g[i];
+    p->sg3 += g[i] * g[i] * g[i];
+    p->sg4 += g[i] * g[i] * g[i] * g[i];
+  }
+  p->norm2 = dt;
+  p->norm3 = dt * dt * std::pow(p->sg2, 1.5) / p->sg3;
+  p->norm4 = dt * dt * dt * p->sg2 * p->sg2 / p->sg4;
+  std::vector<float> gw(T);
+  for (int i = 0; i < T; ++i) gw[i] = (float)(g[i] / std::sqrt(p->sg2));
+  std::vector<float2> tw(T);
+  for (int a = 0; a < T; ++a)
+    tw[a] = make_float2((float)std::cos(2.0 * M_PI * a / T), (float)std::sin(2.0 * M_PI * a / T));
+
+  std::vector<int> s2auto(channels, -1);
+  std::vector<int4> s2cross;
+  for (size_t i = 0; i < p->c2.size(); ++i) {
+    const Combo& cb = p->c2[i];
+    if (cb.c[0] == cb.c[1] && s2auto[cb.c[0]] < 0)
+      s2auto[cb.c[0]] = (int)i;
+    else
+      s2cross.push_back(make_int4(cb.c[0], cb.c[1], (int)i, 0));
+  }
+  p->n_s2cross = (int)s2cross.size();
+  std::vector<int2> t3, t4;
+  build_tiles(p, t3, t4);
+  if (p->c3.empty()) t3.clear();
+  if (p->c4.empty()) t4.clear();
+  p->n_tiles3 = (int)t3.size();
+  p->n_tiles4 = (int)t4.size();
+
+#define PLAN_TRY(call)                           \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) {                     \
+      st = cuda_fail(nullptr, e_, #call);        \
+      destroy(p);                                \
+      return st;                                 \
+    }                                            \
+  } while (0)
+
+  PLAN_TRY(dev_alloc(p, &p->d_win, T * sizeof(float)));
+  PLAN_TRY(dev_alloc(p, &p->d_tw, T * sizeof(float2)));
+  PLAN_TRY(dev_alloc(p, &p->d_carry, (size_t)channels * m * T * p->elem));
+  PLAN_TRY(dev_alloc(p, &p->d_s2auto, channels * sizeof(int)));
+  if (!s2cross.empty()) PLAN_TRY(dev_alloc(p, &p->d_s2cross, s2cross.size() * sizeof(int4)));
+  p->n_acc2 = (size_t)kPlanes * p->c2.size() * p->M;
+  p->n_acc3 = (size_t)kPlanes * p->c3.size() * p->rows3 * p->M;
+  p->n_acc4 = (size_t)kPlanes * p->c4.size() * p->rows4 * p->M;
+  if (p->n_acc2) PLAN_TRY(dev_alloc(p, &p->d_acc2, p->n_acc2 * sizeof(double)));
+  if (p->n_acc3) PLAN_TRY(dev_alloc(p, &p->d_acc3, p->n_acc3 * sizeof(double)));
+  if (p->n_acc4) PLAN_TRY(dev_alloc(p, &p->d_acc4, p->n_acc4 * sizeof(double)));
+  if (!t3.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles3, t3.size() * sizeof(int2)));
+  if (!t4.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4, t4.size() * sizeof(int2)));
+  PLAN_TRY(cudaMemcpy(p->d_win, gw.data(), T * sizeof(float), cudaMemcpyHostToDevice));
+  PLAN_TRY(cudaMemcpy(p->d_tw, tw.data(), T * sizeof(float2), cudaMemcpyHostToDevice));
+  PLAN_TRY(cudaMemcpy(p->d_s2auto, s2auto.data(), channels * sizeof(int),
+                      cudaMemcpyHostToDevice));
+  if (!s2cross.empty())
+    PLAN_TRY(cudaMemcpy(p->d_s2cross, s2cross.data(), s2cross.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice));
+  if (!t3.empty())
+    PLAN_TRY(cudaMemcpy(p->d_tiles3, t3.data(), t3.size() * sizeof(int2),
+                        cudaMemcpyHostToDevice));
+  if (!t4.empty())
+    PLAN_TRY(cudaMemcpy(p->d_tiles4, t4.data(), t4.size() * sizeof(int2),
+                        cudaMemcpyHostToDevice));
+  st = alloc_spec(p);
+  if (st != SS_OK) {
+    g_plan_error = p->err;
+    destroy(p);
+    return st;
+  }
+  st = zero_state(p);
+  if (st == SS_OK && p->stream == nullptr) {
+    cudaError_t e2 = cudaStreamSynchronize(nullptr);
+    if (e2 != cudaSuccess) st = cuda_fail(p, e2, "cudaStreamSynchronize");
+  }
+  if (st != SS_OK) {
+    g_plan_error = p->err;
+    destroy(p);
+    return st;
+  }
+#undef PLAN_TRY
+  *out = p;
+  return SS_OK;
+}
+
+ss_status ss_accumulate(ss_plan_t p, const void* chunk, size_t n_samples) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
+  if (n_samples == 0) return SS_OK;
+  if (!chunk) return fail(p, SS_EINVAL, "chunk is NULL");
+  if (n_samples > (size_t)1 << 46) return fail(p, SS_EINVAL, "n_samples too large");
+  DeviceGuard guard(p->device);
+  if (is_device_ptr(chunk)) return process_device(p, chunk, (long long)n_samples,
+                                                  (long long)n_samples);
+  return process_host(p, chunk, (long long)n_samples);
+}
+
+ss_status ss_finalize(ss_plan_t p, double* S2, double* S3, double* S4, double* S2_err,
+                      double* S3_err, double* S4_err) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
+  if (p->groups < 2)
+    return fail(p, SS_ESTATE, "fewer than two groups accumulated: no error estimate (Eq. 35)");
+  DeviceGuard guard(p->device);
+  const size_t n2 = p->c2.size() * p->M * 2;
+  const size_t n3 = p->c3.size() * p->rows3 * p->M * 2;
+  const size_t n4 = p->c4.size() * p->rows4 * p->M * 2;
+  const size_t need = 2 * (n2 + n3 + n4);
+  if (p->out_doubles < need) {
+    if (p->d_out) {
+      cudaFree(p->d_out);
+      p->device_bytes -= p->out_doubles * sizeof(double);
+      p->d_out = nullptr;
+    }
+    SS_TRY(p, dev_alloc(p, &p->d_out, need * sizeof(double)));
+    p->out_doubles = need;
+  }
+  double* o2 = p->d_out;
+  double* e2 = o2 + n2;
+  double* o3 = e2 + n2;
+  double* e3 = o3 + n3;
+  double* o4 = e3 + n3;
+  double* e4 = o4 + n4;
+  const bool single = p->C == 1;
+  record(p, 3, p->stream, true);
+  if (n2)
+    SS_TRY(p, launch_k4_finalize(p->d_acc2, (int)p->c2.size(), 1, p->M, kLayoutVector,
+                                 p->groups, p->norm2, o2, e2, p->stream));
+  if (n3)
+    SS_TRY(p, launch_k4_finalize(p->d_acc3, (int)p->c3.size(), p->rows3, p->M,
+                                 single ? kLayoutS3Single : kLayoutCross, p->groups, p->norm3,
+                                 o3, e3, p->stream));
+  if (n4)
+    SS_TRY(p, launch_k4_finalize(p->d_acc4, (int)p->c4.size(), p->rows4, p->M,
+                                 single ? kLayoutS4Single : kLayoutCross, p->groups, p->norm4,
+                                 o4, e4, p->stream));
+  record(p, 3, p->stream, false);
+  const std::pair<double*, std::pair<const double*, size_t>> copies[6] = {
+      {S2, {o2, n2}}, {S2_err, {e2, n2}}, {S3, {o3, n3}},
+      {S3_err, {e3, n3}}, {S4, {o4, n4}}, {S4_err, {e4, n4}}};
+  for (const auto& c : copies)
+    if (c.first && c.second.second)
+      SS_TRY(p, cudaMemcpyAsync(c.first, c.second.first, c.second.second * sizeof(double),
+                                cudaMemcpyDefault, p->stream));
+  SS_TRY(p, cudaStreamSynchronize(p->stream));
+  return SS_OK;
+}
+
+ss_status ss_reset(ss_plan_t p) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
+  DeviceGuard guard(p->device);
+  SS_TRY(p, cudaStreamSynchronize(p->stream));
+  return zero_state(p);
+}
+
+ss_status ss_query(ss_plan_t p, ss_info* info) {
+  if (!p || !info) return fail(p, SS_EINVAL, "NULL argument");
+  info->channels = p->C;
+  info->T = p->T;
+  info->M = p->M;
+  info->m = p->m;
+  info->n_s2 = (int)p->c2.size();
+  info->n_s3 = (int)p->c3.size();
+  info->n_s4 = (int)p->c4.size();
+  info->rows3 = p->rows3;
+  info->rows4 = p->rows4;
+  info->groups = p->groups;
+  info->samples = p->samples;
+  info->carried = p->carry_n;
+  info->groups_per_batch = p->Gb_max;
+  info->device_bytes = p->device_bytes;
+  return SS_OK;
+}
+
+ss_status ss_combos(ss_plan_t p, int* out, int max_records) {
+  if (!p || (!out && max_records > 0)) return fail(p, SS_EINVAL, "NULL argument");
+  int r = 0;
+  for (const auto* v : {&p->c2, &p->c3, &p->c4})
+    for (const Combo& cb : *v) {
+      if (r >= max_records) return fail(p, SS_EINVAL, "max_records too small");
+      out[5 * r] = cb.order;
+      for (int q = 0; q < 4; ++q) out[5 * r + 1 + q] = q < cb.order ? cb.c[q] : -1;
+      ++r;
+    }
+  return SS_OK;
+}
+
+ss_status ss_set_timing(ss_plan_t p, int enable) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  p->timing = enable != 0;
+  return SS_OK;
+}
+
+ss_status ss_stats(ss_plan_t p, ss_stats_t* s) {
+  if (!p || !s) return fail(p, SS_EINVAL, "NULL argument");
+  DeviceGuard guard(p->device);
+  SS_TRY(p, cudaStreamSynchronize(p->stream));
+  if (p->copy_stream) SS_TRY(p, cudaStreamSynchronize(p->copy_stream));
+  for (int i = 0; i < 5; ++i) {
+    double ms = 0.0;
+    for (const EventPair& e : p->ev[i]) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) ms += t;
+    }
+    s->ms[i] = ms;
+    s->launches[i] = p->launches[i];
+  }
+  s->pairs3 = p->pairs3;
+  s->pairs4 = p->pairs4;
+  return SS_OK;
+}
+
+ss_status ss_set_batch(ss_plan_t p, int groups_per_batch) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (groups_per_batch < 0) return fail(p, SS_EINVAL, "groups_per_batch must be >= 0");
+  if (p->groups != 0 || p->carry_n != 0)
+    return fail(p, SS_ESTATE, "ss_set_batch is valid only before the first ss_accumulate");
+  DeviceGuard guard(p->device);
+  SS_TRY(p, cudaStreamSynchronize(p->stream));
+  p->Gb_user = groups_per_batch;
+  return alloc_spec(p);
+}
+
+ss_status ss_destroy(ss_plan_t p) {
+  if (!p) return SS_OK;
+  DeviceGuard guard(p->device);
+  destroy(p);
+  return SS_OK;
+}
+
+}  // extern "C"

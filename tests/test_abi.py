@@ -1,0 +1,69 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/polyspec.h, and rejects invalid arguments before any CUDA call."""
+import os
+import re
+
+import pytest
+
+import paper_2505_01231_gb300 as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ss_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_symbols()
+    assert "ss_plan" in names and "ss_accumulate" in names and "ss_finalize" in names
+    for n in names:
+        assert hasattr(P.lib, n), n
+
+
+def test_version():
+    assert "sm_103a" in P.ss_version()
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(channels=0), "channels"),
+    (dict(channels=5), "channels"),
+    (dict(T=100), "power of two"),
+    (dict(T=4), "power of two"),
+    (dict(T=8192), "power of two"),
+    (dict(dt=0.0), "dt"),
+    (dict(dt=float("nan")), "dt"),
+    (dict(m=3), "m >= 4"),
+    (dict(m=2, orders=P.SS_ORDER3), "m >= 3"),
+    (dict(m=1, orders=P.SS_ORDER2), "m >= 2"),
+    (dict(orders=0), "orders"),
+    (dict(orders=1), "orders"),
+    (dict(window=7), "window"),
+    (dict(window=P.SS_WIN_ACG, win_param=-1.0), "sigma_t"),
+    (dict(dtype=9), "dtype"),
+    (dict(precision=9), "precision"),
+    (dict(combos=[(3, 0, 0, 0, -1)], orders=P.SS_ORDER2), "order"),
+    (dict(combos=[(2, 0, 3, -1, -1)], channels=2, orders=P.SS_ORDER2), "channel"),
+])
+def test_plan_rejects_invalid_arguments(kw, msg):
+    args = dict(channels=1, T=256, dt=1.0, m=10, window=P.SS_WIN_HANN, win_param=0.14,
+                orders=P.SS_ORDER2 | P.SS_ORDER3 | P.SS_ORDER4, dtype=P.SS_F32,
+                precision=P.SS_PREC_FP32, combos=None)
+    args.update(kw)
+    with pytest.raises(P.SSError) as ei:
+        P.ss_plan(**args)
+    assert ei.value.status == P.SS_EINVAL
+    assert msg in str(ei.value)
+
+
+def test_null_plan_calls_fail_cleanly():
+    assert P.lib.ss_accumulate(None, None, 0) == P.SS_EINVAL
+    assert P.lib.ss_finalize(None, None, None, None, None, None, None) == P.SS_EINVAL
+    assert P.lib.ss_reset(None) == P.SS_EINVAL
+    assert P.lib.ss_destroy(None) == P.SS_OK

@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance (stated for floating point): max |GPU - oracle| <= 1e-5 x max |oracle| for
+every spectrum (the FP32 path), the standard errors within 1e-4 x their maximum.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+TOL_ERR = 1e-4
+
+
+def P():
+    import paper_2505_01231_gb300 as mod
+    return mod
+
+
+def run_gpu(z, T, m, dt=1.0, window="hann", sigma_t=0.14, orders=(2, 3, 4), chunks=None,
+            host=False, batch=0, dtype="f32", channels=1, combos=None):
+    mod = P()
+    plan = mod.Plan(channels=channels, T=T, dt=dt, m=m, window=window, sigma_t=sigma_t,
+                    orders=orders, dtype=dtype, combos=combos)
+    if batch:
+        mod.ss_set_batch(plan.handle, batch)
+    z = np.ascontiguousarray(z)
+    n = z.shape[-1]
+    cuts = [0] + list(chunks or []) + [n]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        piece = np.ascontiguousarray(z[..., a:b])
+        if host:
+            plan.accumulate(piece, b - a)
+        else:
+            t = torch.from_numpy(piece).cuda()
+            plan.accumulate(t, b - a)
+            torch.cuda.synchronize()
+    out = plan.finalize()
+    plan.close()
+    return out
+
+
+def check(gpu, ref, key, tol=TOL):
+    a, b = gpu[key].reshape(ref[key].shape), ref[key]
+    scale = np.max(np.abs(b))
+    err = np.max(np.abs(a - b)) / scale
+    assert err <= tol, f"{key}: max rel err {err:.3e} > {tol}"
+    ea, eb = gpu[key + "_err"].reshape(ref[key + "_err"].shape), ref[key + "_err"]
+    escale = np.max(np.abs(eb))
+    eerr = np.max(np.abs(ea - eb)) / escale
+    assert eerr <= TOL_ERR, f"{key}_err: max rel err {eerr:.3e} > {TOL_ERR}"
+    return err
+
+
+def compare_single(gpu, ref, orders=(2, 3, 4)):
+    assert gpu["G"] == ref["G"]
+    errs = {}
+    for n in orders:
+        key = f"S{n}"
+        g = {key: gpu[key][0], key + "_err": gpu[key + "_err"][0]}
+        errs[key] = check(g, ref, key)
+    return errs
+
+
+@pytest.fixture(scope="module")
+def c1_signal():
+    return synth.ar1_quadratic(1 << 20, seed=0)
+
+
+def test_config1_full_grid(c1_signal):
+    # single channel, 2^20 samples, T=256 (129 bins: three 64-wide tiles, ragged tail
+    # of one bin), Hann, m=10, 409 groups, 6 frames dropped
+    ref = oracle.polyspectra(c1_signal, 256, 1.0, 10, group_chunk=64)
+    gpu = run_gpu(c1_signal, 256, 10)
+    errs = compare_single(gpu, ref)
+    print("config-1 max relative errors", errs)
+
+
+@pytest.mark.parametrize("T,m,G", [(8, 4, 50), (16, 5, 40), (64, 6, 30), (128, 4, 24),
+                                   (512, 7, 9), (4096, 4, 3)])
+def test_sizes_and_ragged_tails(T, m, G):
+    z = synth.ar1_quadratic(T * m * G + 3 * T + 5, seed=T + m)   # partial group dropped
+    ref = oracle.polyspectra(z, T, 0.25, m, group_chunk=8)
+    gpu = run_gpu(z, T, m, dt=0.25)
+    compare_single(gpu, ref)
+
+
+def test_streaming_chunks_match_one_call(c1_signal):
+    z = c1_signal[: 256 * 10 * 40 + 77]
+    ref = oracle.polyspectra(z, 256, 1.0, 10)
+    # chunks of odd sizes, smaller and larger than a group, one empty
+    cuts = [1, 1000, 1000, 2561, 9999, 30000, 65000, 65001, 70000]
+    gpu = run_gpu(z, 256, 10, chunks=cuts)
+    compare_single(gpu, ref)
+
+
+def test_host_chunks_match_device_chunks(c1_signal):
+    z = c1_signal[: 256 * 10 * 60]
+    a = run_gpu(z, 256, 10, host=True, chunks=[12345, 50000])
+    b = run_gpu(z, 256, 10)
+    for key in ("S2", "S3", "S4"):
+        scale = np.max(np.abs(b[key]))
+        assert np.max(np.abs(a[key] - b[key])) <= 1e-6 * scale
+
+
+def test_small_batches_match(c1_signal):
+    z = c1_signal[: 256 * 10 * 50]
+    ref = oracle.polyspectra(z, 256, 1.0, 10)
+    gpu = run_gpu(z, 256, 10, batch=7)
+    compare_single(gpu, ref)
+
+
+def test_confined_gaussian_window_and_dt():
+    z = synth.ar1_quadratic(128 * 6 * 40, seed=5)
+    ref = oracle.polyspectra(z, 128, 1e-3, 6, window_kind="acg", sigma_t=0.14)
+    gpu = run_gpu(z, 128, 6, dt=1e-3, window="acg", sigma_t=0.14)
+    compare_single(gpu, ref)
+
+
+def test_int16_input():
+    x, _ = synth.adc_telegraph_int16(256 * 10 * 30, seed=3)
+    ref = oracle.polyspectra(x, 256, 1.0, 10)
+    gpu = run_gpu(x, 256, 10, dtype="i16")
+    compare_single(gpu, ref)
+
+
+def test_order_subsets_and_minimum_m():
+    z = synth.ar1_quadratic(64 * 3 * 50, seed=8)
+    ref = oracle.polyspectra(z, 64, 1.0, 3, orders=(2, 3))
+    gpu = run_gpu(z, 64, 3, orders=(2, 3))
+    assert "S4" not in gpu or gpu["S4"].size == 0
+    compare_single(gpu, ref, orders=(2, 3))
+
+
+def test_multichannel_s2_s3():
+    zs = synth.multichannel_shared(3, 64 * 5 * 40, seed=12)
+    combos2 = [(0, 0), (0, 1), (1, 2), (2, 0)]
+    combos3 = [(0, 0, 0), (0, 1, 1), (1, 1, 0), (0, 1, 2)]
+    recs = [(2, *c, -1, -1) for c in combos2] + [(3, *c, -1) for c in combos3]
+    gpu = run_gpu(zs, 64, 5, orders=(2, 3), channels=3, combos=recs)
+    ref = oracle.cross_polyspectra(zs, 64, 1.0, 5, s2_combos=combos2, s3_combos=combos3)
+    for i, c in enumerate(combos2):
+        check({"S2": gpu["S2"][i], "S2_err": gpu["S2_err"][i]},
+              {"S2": ref[("S2", c)][0], "S2_err": ref[("S2", c)][1]}, "S2")
+    for i, c in enumerate(combos3):
+        check({"S3": gpu["S3"][i], "S3_err": gpu["S3_err"][i]},
+              {"S3": ref[("S3", c)][0], "S3_err": ref[("S3", c)][1]}, "S3")
+
+
+def test_fewer_than_two_groups_is_a_state_error():
+    mod = P()
+    plan = mod.Plan(T=64, m=4)
+    z = torch.from_numpy(synth.ar1_quadratic(64 * 4 + 10, seed=1)).cuda()
+    plan.accumulate(z)
+    with pytest.raises(mod.SSError) as ei:
+        plan.finalize()
+    assert ei.value.status == mod.SS_ESTATE
+    info = mod.ss_query(plan.handle)
+    assert info.groups == 1 and info.carried == 10
+    plan.close()
+
+
+def test_reset_gives_identical_results(c1_signal):
+    mod = P()
+    z = torch.from_numpy(c1_signal[: 256 * 10 * 20]).cuda()
+    plan = mod.Plan(T=256, m=10)
+    plan.accumulate(z)
+    a = plan.finalize()
+    plan.reset()
+    plan.accumulate(z)
+    b = plan.finalize()
+    plan.close()
+    for key in ("S2", "S3", "S4"):
+        assert np.array_equal(a[key], b[key]) or \
+            np.max(np.abs(a[key] - b[key])) <= 1e-6 * np.max(np.abs(a[key]))
+
+
+# ---------------------------------------------------------------- full size
+def sampled_points(M, rng):
+    lo = [(k, l) for k in range(6) for l in range(k, 6)]
+    kk3, ll3 = oracle.s3_domain(M)
+    half = kk3 <= ll3
+    idx = rng.choice(np.flatnonzero(half), 40, replace=False)
+    s3 = lo + [(int(kk3[i]), int(ll3[i])) for i in idx] + [(0, M - 1), ((M - 1) // 2, (M - 1) // 2)]
+    s4 = lo + [(int(a), int(b)) for a, b in rng.integers(0, M, size=(40, 2))] + \
+        [(M - 1, M - 1), (0, M - 1)]
+    return s3, s4
+
+
+def oracle_points(z, T, m, dt, s3pts, s4pts, chunk=2048):
+    g = oracle.window(T)
+    frames = oracle.frame_groups(z, T, m)
+    G = frames.shape[0]
+    k3, l3 = np.array(s3pts).T
+    k4, l4 = np.array(s4pts).T
+    v2, v3, v4 = [], [], []
+    for g0 in range(0, G, chunk):
+        X = oracle.dft_plus(frames[g0:g0 + chunk] * g)
+        v2.append(oracle.s2_groups(X, X, dt, g))
+        v3.append(oracle.s3_groups(X, X, X, dt, g, k3, l3))
+        v4.append(oracle.s4_groups(X, X, X, X, dt, g, k4, l4))
+    return [oracle.mean_and_stderr(np.concatenate(v)) for v in (v2, v3, v4)], G
+
+
+def test_config2_full_size_sampled_points():
+    # 2^28 samples, T=1024 (513 bins), m=10, 26214 groups, launched as bench.py does
+    T, m, n = 1024, 10, 1 << 28
+    z = synth.ar1_quadratic(n, seed=1)
+    gpu = run_gpu(z, T, m)
+    M = T // 2 + 1
+    s3, s4 = sampled_points(M, np.random.default_rng(0))
+    (r2, r3, r4), G = oracle_points(z, T, m, 1.0, s3, s4)
+    assert gpu["G"] == G == 26214
+    S2 = gpu["S2"][0]
+    assert np.max(np.abs(S2 - r2[0])) <= TOL * np.max(np.abs(r2[0]))
+    for (S, E), ref, pts in (((gpu["S3"][0], gpu["S3_err"][0]), r3, s3),
+                             ((gpu["S4"][0], gpu["S4_err"][0]), r4, s4)):
+        k, l = np.array(pts).T
+        scale = np.max(np.abs(ref[0]))
+        # the spectrum's peak lies in the sampled low-frequency block
+        assert np.max(np.abs(S)) <= 1.001 * scale
+        assert np.max(np.abs(S[k, l] - ref[0])) <= TOL * scale
+        assert np.max(np.abs(E[k, l, 0] - ref[1])) <= TOL_ERR * np.max(ref[1])
+        assert np.max(np.abs(E[k, l, 1] - ref[2])) <= TOL_ERR * max(np.max(ref[1]), np.max(ref[2]))
+    # estimator-level symmetries of the whole grid (Sec. 9)
+    S3, S4 = gpu["S3"][0], gpu["S4"][0]
+    assert np.array_equal(S3, S3.T)
+    assert np.array_equal(S4, S4.T)
+    assert np.max(np.abs(S4.imag)) == 0.0
