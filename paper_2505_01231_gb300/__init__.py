@@ -35,7 +35,7 @@ SS_PREC_FP32, SS_PREC_TF32X3, SS_PREC_BF16X3, SS_PREC_BF16 = 0, 1, 2, 3
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpolyspec.so")
 if not os.path.exists(LIB_PATH):
     raise ImportError(
-        f"{LIB_PATH} is missing: build it first (python -m paper_2505_01231_gb300.build); "
+        f"{LIB_PATH} is missing: build it first (python paper_2505_01231_gb300/build.py); "
         "this package has no CPU fallback")
 lib = ctypes.CDLL(LIB_PATH)
 

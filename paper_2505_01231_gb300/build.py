@@ -3,7 +3,8 @@
 Every translation unit under ``csrc/`` is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a`` and linked into
 ``paper_2505_01231_gb300/libpolyspec.so`` (in-tree; git-ignored).
-Run as ``python -m paper_2505_01231_gb300.build`` or call ``build()``.
+Run as ``python paper_2505_01231_gb300/build.py`` (the package itself cannot be
+imported before the library exists) or call ``__graft_entry__.build()``.
 """
 from __future__ import annotations
 
