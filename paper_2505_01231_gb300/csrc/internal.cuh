@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "pipeline.cuh"
 #include "polyspec.h"
 
 namespace ss {
@@ -52,16 +53,20 @@ cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G,
                                int Mp, const int4* pairs, int n_pairs, float pref2, double* acc2,
                                long long plane, int nsm, cudaStream_t stream);
 
-// acc points at the combination's first accumulator plane; `plane` is the
-// distance in doubles between the four planes (sum Re, sum Im, sumsq Re, sumsq Im).
+// Pair kernels run persistent grids of nsm x (resident CTAs per SM) CTAs over a
+// balanced schedule of the tiles (see pipeline.cuh).  acc points at the
+// combination's first accumulator plane; `plane` is the distance in doubles
+// between the four planes (sum Re, sum Im, sumsq Re, sumsq Im).  `status` is
+// the plan's device status word (a bounded wait that gives up writes to it).
 cudaError_t launch_k2_bispec(const float2* spec_a, const float2* spec_b, const float2* spec_c,
-                             int G, int m, int M, int Mp, const int2* tiles, int n_tiles,
-                             int cross, int group_splits, float pref3, double* acc,
-                             long long plane, int rows, cudaStream_t stream);
+                             int G, int m, int M, int Mp, const TileInfo* tiles, int n_tiles,
+                             int cross, float pref3, double* acc, long long plane, int rows,
+                             int nsm, int* status, cudaStream_t stream);
 
-cudaError_t launch_k3_trispec(const float2* spec, int G, int m, int M, int Mp, const int2* tiles,
-                              int n_tiles, int group_splits, float pref4a, float pref4b,
-                              double* acc, long long plane, cudaStream_t stream);
+cudaError_t launch_k3_trispec(const float2* spec, int G, int m, int M, int Mp,
+                              const TileInfo* tiles, int n_tiles, float pref4a, float pref4b,
+                              double* acc, long long plane, int nsm, int* status,
+                              cudaStream_t stream);
 
 cudaError_t launch_k4_finalize(const double* acc, int n_combos, int rows, int M, int layout,
                                long long G, double norm, double* out, double* err,

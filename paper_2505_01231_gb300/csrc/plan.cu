@@ -74,7 +74,8 @@ struct ss_plan_s {
   int* d_s2auto = nullptr;
   int4* d_s2cross = nullptr;
   int n_s2cross = 0;
-  int2 *d_tiles3 = nullptr, *d_tiles4 = nullptr;
+  TileInfo *d_tiles3 = nullptr, *d_tiles4 = nullptr;
+  int* d_status = nullptr;
   int n_tiles3 = 0, n_tiles4 = 0;
   long long pairs3 = 0, pairs4 = 0;
   void* d_stage[2] = {nullptr, nullptr};
@@ -160,46 +161,48 @@ bool in_domain3(int k, int l, int M, bool cross) {
   return k >= 0 && k <= l && k + l < M;
 }
 
-void build_tiles(ss_plan_s* p, std::vector<int2>& t3, std::vector<int2>& t4) {
+// Tiles of 64 x 64 grid points that touch the domain, each weighted by the
+// number of its 32 x 16 warp sub-tiles that touch the domain (the kernels skip
+// the others), with prefix sums for the balanced schedule.
+void build_tiles(ss_plan_s* p, std::vector<TileInfo>& t3, std::vector<TileInfo>& t4) {
   const int M = p->M;
   const bool cross = p->C > 1;
   p->pairs3 = 0;
   p->pairs4 = 0;
-  if (!cross) {
-    for (int k0 = 0; k0 < M; k0 += kTile)
-      for (int l0 = k0; l0 < M; l0 += kTile) {
-        if (k0 + l0 <= M - 1) t3.push_back(make_int2(k0, l0));
-        t4.push_back(make_int2(k0, l0));
-      }
-    for (int k = 0; k < M; ++k)
-      for (int l = k; l < M; ++l) {
-        if (k + l < M) ++p->pairs3;
-        ++p->pairs4;
-      }
-  } else {
-    const int kmin = -((M - 1 + kTile - 1) / kTile) * kTile;
-    for (int k0 = kmin; k0 < M; k0 += kTile)
-      for (int l0 = 0; l0 < M; l0 += kTile) {
-        bool any3 = false;
-        for (int a = 0; a < kTile && !any3; ++a)
-          for (int b = 0; b < kTile && !any3; ++b) any3 = in_domain3(k0 + a, l0 + b, M, true);
-        if (any3) t3.push_back(make_int2(k0, l0));
-        if (k0 + kTile > -M) t4.push_back(make_int2(k0, l0));
-      }
-    for (int k = -(M - 1); k < M; ++k)
-      for (int l = 0; l < M; ++l) {
-        if (in_domain3(k, l, M, true)) ++p->pairs3;
-        ++p->pairs4;
-      }
+  auto warps = [&](int k0, int l0, auto in_dom) {
+    int w = 0;
+    for (int wi = 0; wi < kThreadsPair / 32; ++wi) {
+      const int kw = k0 + 32 * (wi & 1), lw = l0 + 16 * (wi >> 1);
+      bool any = false;
+      for (int a = 0; a < 32 && !any; ++a)
+        for (int b = 0; b < 16 && !any; ++b) any = in_dom(kw + a, lw + b);
+      w += any ? 1 : 0;
+    }
+    return w;
+  };
+  auto dom3 = [&](int k, int l) { return in_domain3(k, l, M, cross); };
+  auto dom4 = [&](int k, int l) {
+    return cross ? (l >= 0 && l < M && k > -M && k < M) : (k >= 0 && k <= l && l < M);
+  };
+  const int kmin = cross ? -((M - 1 + kTile - 1) / kTile) * kTile : 0;
+  for (int k0 = kmin; k0 < M; k0 += kTile)
+    for (int l0 = 0; l0 < M; l0 += kTile) {
+      const int w3 = warps(k0, l0, dom3), w4 = warps(k0, l0, dom4);
+      if (w3) t3.push_back(TileInfo{k0, l0, w3, 0});
+      if (w4) t4.push_back(TileInfo{k0, l0, w4, 0});
+    }
+  for (auto* v : {&t3, &t4}) {
+    int acc = 0;
+    for (TileInfo& t : *v) {
+      t.prefix = acc;
+      acc += t.weight;
+    }
   }
-}
-
-int group_splits(const ss_plan_s* p, int n_tiles, int G) {
-  if (n_tiles <= 0) return 1;
-  // about four CTAs per SM in total, at least 16 groups per CTA
-  int s = std::max(1, (4 * p->nsm + n_tiles - 1) / n_tiles);
-  s = std::min(s, std::max(1, G / 16));
-  return s;
+  for (int k = -(M - 1); k < M; ++k)
+    for (int l = 0; l < M; ++l) {
+      if (dom3(k, l)) ++p->pairs3;
+      if (dom4(k, l)) ++p->pairs4;
+    }
 }
 
 void record(ss_plan_s* p, int stage, cudaStream_t s, bool start) {
@@ -269,10 +272,9 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
           SS_TRY(p, launch_k2_bispec(p->d_spec + cb.c[0] * chan_stride,
                                      p->d_spec + cb.c[1] * chan_stride,
                                      p->d_spec + cb.c[2] * chan_stride, cnt, p->m, p->M, p->Mp,
-                                     p->d_tiles3, p->n_tiles3, p->C > 1 ? 1 : 0,
-                                     group_splits(p, p->n_tiles3, cnt), pref3,
+                                     p->d_tiles3, p->n_tiles3, p->C > 1 ? 1 : 0, pref3,
                                      p->d_acc3 + (long long)i * p->rows3 * p->M, plane, p->rows3,
-                                     p->stream));
+                                     p->nsm, p->d_status, p->stream));
         }
         record(p, 1, p->stream, false);
       }
@@ -282,10 +284,9 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
         for (size_t i = 0; i < p->c4.size(); ++i) {
           const Combo& cb = p->c4[i];
           SS_TRY(p, launch_k3_trispec(p->d_spec + cb.c[0] * chan_stride, cnt, p->m, p->M, p->Mp,
-                                      p->d_tiles4, p->n_tiles4,
-                                      group_splits(p, p->n_tiles4, cnt), pref4a, pref4b,
-                                      p->d_acc4 + (long long)i * p->rows4 * p->M, plane,
-                                      p->stream));
+                                      p->d_tiles4, p->n_tiles4, pref4a, pref4b,
+                                      p->d_acc4 + (long long)i * p->rows4 * p->M, plane, p->nsm,
+                                      p->d_status, p->stream));
         }
         record(p, 2, p->stream, false);
       }
@@ -310,6 +311,18 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
   p->carry_n = left;
   p->groups += Gn;
   p->samples += n;
+  return SS_OK;
+}
+
+// A kernel whose bounded wait gave up leaves a non-zero device status; the
+// sums of that launch are incomplete, so the plan is marked unusable.
+ss_status check_status(ss_plan_s* p) {
+  int st = 0;
+  SS_TRY(p, cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != kStatusOk) {
+    p->broken = true;
+    return fail(p, SS_ETIMEOUT, "a device-side wait for staged data gave up; results discarded");
+  }
   return SS_OK;
 }
 
@@ -354,6 +367,7 @@ ss_status process_host(ss_plan_s* p, const void* chunk, long long n) {
 }
 
 ss_status zero_state(ss_plan_s* p) {
+  if (p->d_status) SS_TRY(p, cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   if (p->d_acc2) SS_TRY(p, cudaMemsetAsync(p->d_acc2, 0, p->n_acc2 * sizeof(double), p->stream));
   if (p->d_acc3) SS_TRY(p, cudaMemsetAsync(p->d_acc3, 0, p->n_acc3 * sizeof(double), p->stream));
   if (p->d_acc4) SS_TRY(p, cudaMemsetAsync(p->d_acc4, 0, p->n_acc4 * sizeof(double), p->stream));
@@ -405,6 +419,7 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_s2cross);
   cudaFree(p->d_tiles3);
   cudaFree(p->d_tiles4);
+  cudaFree(p->d_status);
   cudaFree(p->d_out);
   delete p;
 }
@@ -532,7 +547,7 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
       s2cross.push_back(make_int4(cb.c[0], cb.c[1], (int)i, 0));
   }
   p->n_s2cross = (int)s2cross.size();
-  std::vector<int2> t3, t4;
+  std::vector<TileInfo> t3, t4;
   build_tiles(p, t3, t4);
   if (p->c3.empty()) t3.clear();
   if (p->c4.empty()) t4.clear();
@@ -560,8 +575,9 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   if (p->n_acc2) PLAN_TRY(dev_alloc(p, &p->d_acc2, p->n_acc2 * sizeof(double)));
   if (p->n_acc3) PLAN_TRY(dev_alloc(p, &p->d_acc3, p->n_acc3 * sizeof(double)));
   if (p->n_acc4) PLAN_TRY(dev_alloc(p, &p->d_acc4, p->n_acc4 * sizeof(double)));
-  if (!t3.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles3, t3.size() * sizeof(int2)));
-  if (!t4.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4, t4.size() * sizeof(int2)));
+  if (!t3.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles3, t3.size() * sizeof(TileInfo)));
+  if (!t4.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4, t4.size() * sizeof(TileInfo)));
+  PLAN_TRY(dev_alloc(p, &p->d_status, sizeof(int)));
   PLAN_TRY(cudaMemcpy(p->d_win, gw.data(), T * sizeof(float), cudaMemcpyHostToDevice));
   PLAN_TRY(cudaMemcpy(p->d_tw, tw.data(), T * sizeof(float2), cudaMemcpyHostToDevice));
   PLAN_TRY(cudaMemcpy(p->d_s2auto, s2auto.data(), channels * sizeof(int),
@@ -570,10 +586,10 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
     PLAN_TRY(cudaMemcpy(p->d_s2cross, s2cross.data(), s2cross.size() * sizeof(int4),
                         cudaMemcpyHostToDevice));
   if (!t3.empty())
-    PLAN_TRY(cudaMemcpy(p->d_tiles3, t3.data(), t3.size() * sizeof(int2),
+    PLAN_TRY(cudaMemcpy(p->d_tiles3, t3.data(), t3.size() * sizeof(TileInfo),
                         cudaMemcpyHostToDevice));
   if (!t4.empty())
-    PLAN_TRY(cudaMemcpy(p->d_tiles4, t4.data(), t4.size() * sizeof(int2),
+    PLAN_TRY(cudaMemcpy(p->d_tiles4, t4.data(), t4.size() * sizeof(TileInfo),
                         cudaMemcpyHostToDevice));
   st = alloc_spec(p);
   if (st != SS_OK) {
@@ -656,7 +672,7 @@ ss_status ss_finalize(ss_plan_t p, double* S2, double* S3, double* S4, double* S
       SS_TRY(p, cudaMemcpyAsync(c.first, c.second.first, c.second.second * sizeof(double),
                                 cudaMemcpyDefault, p->stream));
   SS_TRY(p, cudaStreamSynchronize(p->stream));
-  return SS_OK;
+  return check_status(p);
 }
 
 ss_status ss_reset(ss_plan_t p) {
