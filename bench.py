@@ -41,6 +41,8 @@ WORKLOADS = {
     # name: (channels, n samples per channel, T, m, seed)
     "ar1q-2^28-T1024-m10": dict(channels=1, n=1 << 28, T=1024, m=10, seed=1, phi=0.9),
     "ar1q-2^20-T256-m10": dict(channels=1, n=1 << 20, T=256, m=10, seed=0, phi=0.9),
+    # same shapes as the default at 1/8 of the length (profiling captures)
+    "ar1q-2^25-T1024-m10": dict(channels=1, n=1 << 25, T=1024, m=10, seed=1, phi=0.9),
 }
 DEFAULT_WORKLOAD = "ar1q-2^28-T1024-m10"
 
