@@ -58,15 +58,21 @@ cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G,
 // combination's first accumulator plane; `plane` is the distance in doubles
 // between the four planes (sum Re, sum Im, sumsq Re, sumsq Im).  `status` is
 // the plan's device status word (a bounded wait that gives up writes to it).
-cudaError_t launch_k2_bispec(const float2* spec_a, const float2* spec_b, const float2* spec_c,
-                             int G, int m, int M, int Mp, const TileInfo* tiles, int n_tiles,
-                             int cross, float pref3, double* acc, long long plane, int rows,
-                             int nsm, int* status, cudaStream_t stream);
+cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
+                             const float2* spec_a, const float2* spec_b, const float2* spec_c,
+                             int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
+                             const TileInfo* tiles, int n_tiles, int cross, float pref3,
+                             double* acc, long long plane, int rows, int nsm, int* status,
+                             cudaStream_t stream);
 
-cudaError_t launch_k3_trispec(const float2* spec, int G, int m, int M, int Mp,
+cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, int FC, int M,
                               const TileInfo* tiles, int n_tiles, float pref4a, float pref4b,
                               double* acc, long long plane, int nsm, int* status,
                               cudaStream_t stream);
+
+// dynamic shared memory of the pair kernels for FC frames per stage
+size_t k2_smem_bytes(int FC);
+size_t k3_smem_bytes(int FC);
 
 cudaError_t launch_k4_finalize(const double* acc, int n_combos, int rows, int M, int layout,
                                long long G, double norm, double* out, double* err,

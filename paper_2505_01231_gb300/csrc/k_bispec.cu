@@ -9,14 +9,15 @@
 // applied by the finalize kernel.
 //
 // Work split: a persistent CTA walks a balanced list of (64 x 64 tile of (k, l),
-// range of groups) segments.  Per group, one thread issues 1-D TMA bulk copies
-// of the m frames' coefficients at k0..k0+63, l0..l0+63 and k0+l0..k0+l0+127
-// into one of two shared-memory stages (mbarrier completion, bounded waits), so
-// the copy of group g+2 overlaps the arithmetic of group g+1.  Each thread
-// evaluates a 4 x 4 micro-tile of grid points with 128-bit shared loads,
-// looping over the frames; its float32 sums over the segment's groups are added
-// to the float64 accumulators when the segment ends.  Warps whose 32 x 16
-// sub-tile lies outside the domain skip the arithmetic.
+// range of groups) segments.  A group's frames are taken in chunks of FC frames;
+// for each chunk one thread issues three 2-D TMA box loads (FC frames x 64 bins
+// at k0, at l0, and FC x 128 bins at k0 + l0; bins past the spectrum read as
+// zero) into one of kStages shared-memory stages, so loads run kStages-1 chunks
+// ahead of the arithmetic.  Each thread evaluates a 4 x 4 micro-tile of grid
+// points with 128-bit shared loads; its float32 sums over the segment's groups
+// are added to the float64 accumulators when the segment ends.  Warps whose
+// 32 x 16 sub-tile lies outside the domain skip the arithmetic.  All waits on
+// the stage barriers are bounded.
 //
 // Domains: one channel (cross = 0): 0 <= k <= l, k + l <= M-1 (the rest follows
 // from S3(k, l) = S3(l, k), Sec. 9).  Several channels (cross = 1):
@@ -27,6 +28,8 @@
 
 namespace ss {
 namespace {
+
+constexpr int kStages = 4;
 
 __device__ __forceinline__ float2 coef(const float2* __restrict__ row, int k, int M) {
   if (k >= 0) return k < M ? row[k] : make_float2(0.f, 0.f);
@@ -42,46 +45,31 @@ __device__ __forceinline__ bool in_domain3(int k, int l, int M, int cross) {
   return k >= 0 && k <= l && k + l < M;
 }
 
-struct Stage {
-  float2* a;  // [m][64]
-  float2* b;  // [m][64]
-  float2* c;  // [m][128]
-};
-
-__device__ __forceinline__ Stage stage_ptr(float2* base, int s, int m) {
-  float2* p = base + (size_t)s * m * 4 * kTile;
-  return Stage{p, p + m * kTile, p + 2 * m * kTile};
-}
-
-// bytes of a bulk copy of n coefficients starting at bin k0 of a row of Mp
-__device__ __forceinline__ uint32_t seg_bytes(int k0, int n, int Mp) {
-  const int len = min(n, Mp - k0);
-  return len > 0 ? (uint32_t)len * sizeof(float2) : 0u;
-}
-
 __global__ void __launch_bounds__(kThreadsPair, 1)
-k2_bispec(const float2* __restrict__ sa, const float2* __restrict__ sb,
-          const float2* __restrict__ sc, int G, int m, int M, int Mp,
-          const TileInfo* __restrict__ tiles, int n_tiles, int cross, float pref3,
+k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUtensorMap tm128,
+          const float2* __restrict__ sa, const float2* __restrict__ sb,
+          const float2* __restrict__ sc, int rowA, int rowB, int rowC, int G, int m, int FC,
+          int M, int Mp, const TileInfo* __restrict__ tiles, int n_tiles, int cross, float pref3,
           double* __restrict__ acc, long long plane, int koff, int* __restrict__ status) {
-  extern __shared__ __align__(128) float4 smem_raw[];
-  __shared__ __align__(8) uint64_t full[2];
-  float2* sbase = reinterpret_cast<float2*>(smem_raw);
+  extern __shared__ __align__(128) float4 smem_raw[];  // + 128 spare bytes for alignment
+  __shared__ __align__(8) uint64_t full[kStages];
+  float2* sbase = align128<float2>(smem_raw);
+  const int stage_elems = FC * 4 * kTile;  // [FC][64] at k, [FC][64] at l, [FC][128] at k+l
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int tx = (warp & 1) * 8 + (lane & 7);     // 16 threads along k
   const int ty = (warp >> 1) * 4 + (lane >> 3);   // 16 threads along l
   const int kt = 4 * tx, lt = 4 * ty;
+  const int nch = (m + FC - 1) / FC;
 
   if (tid == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
+    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
-  for (int i = tid; i < 2 * m * 4 * kTile; i += blockDim.x) sbase[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < kStages * stage_elems; i += blockDim.x) sbase[i] = make_float2(0.f, 0.f);
   fence_async_smem();
   __syncthreads();
-  uint32_t phase = 0;  // bit s = parity of the next wait on stage s
+  uint32_t qbase = 0;  // TMA steps consumed so far (stage = q % kStages)
   bool aborted = false;
 
   for_each_segment(tiles, n_tiles, G, blockIdx.x, gridDim.x, [&](int t, int ga, int gb) {
@@ -92,57 +80,57 @@ k2_bispec(const float2* __restrict__ sa, const float2* __restrict__ sb,
     bool active = false;
     for (int a = 0; a < 32 && !active; ++a)
       for (int b = 0; b < 16 && !active; ++b) active = in_domain3(kw + a, lw + b, M, cross);
-
-    const uint32_t ba = seg_bytes(k0, kTile, Mp), bb = seg_bytes(l0, kTile, Mp);
-    const uint32_t bc = use_tma ? seg_bytes(k0 + l0, 2 * kTile, Mp) : 0u;
-    auto issue = [&](int s, int g) {
-      const Stage st = stage_ptr(sbase, s, m);
-      mbar_arrive_expect_tx(&full[s], (uint32_t)m * (ba + bb + bc));
-      for (int j = 0; j < m; ++j) {
-        const long long r = ((long long)g * m + j) * Mp;
-        if (ba) tma_load_1d(st.a + j * kTile, sa + r + k0, ba, &full[s]);
-        if (bb) tma_load_1d(st.b + j * kTile, sb + r + l0, bb, &full[s]);
-        if (bc) tma_load_1d(st.c + j * 2 * kTile, sc + r + k0 + l0, bc, &full[s]);
-      }
+    const int nsteps = (gb - ga) * nch;
+    auto issue = [&](int i) {
+      const int s = (int)((qbase + i) % kStages);
+      const int g = ga + i / nch, j0 = (i % nch) * FC;
+      float2* st = sbase + (size_t)s * stage_elems;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_elems * sizeof(float2)));
+      tma_load_2d(st, &tm64, k0, rowA + g * m + j0, &full[s]);
+      tma_load_2d(st + FC * kTile, &tm64, l0, rowB + g * m + j0, &full[s]);
+      tma_load_2d(st + 2 * FC * kTile, &tm128, k0 + l0, rowC + g * m + j0, &full[s]);
     };
 
-    float sr[16], si[16], qr[16], qi[16];
+    float sr[16], si[16], qr[16], qi[16], ar[16], ai[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) sr[i] = si[i] = qr[i] = qi[i] = 0.f;
+    for (int i = 0; i < 16; ++i) sr[i] = si[i] = qr[i] = qi[i] = ar[i] = ai[i] = 0.f;
 
     if (use_tma && tid == 0) {
       fence_async_smem();
-      issue(0, ga);
-      if (ga + 1 < gb) issue(1, ga + 1);
+      for (int i = 0; i < kStages && i < nsteps; ++i) issue(i);
     }
-    for (int g = ga; g < gb; ++g) {
-      const int s = (g - ga) & 1;
-      const Stage st = stage_ptr(sbase, s, m);
+    for (int i = 0; i < nsteps; ++i) {
+      const int g = ga + i / nch, ch = i % nch, j0 = ch * FC;
+      const int nf = min(FC, m - j0);
+      const int s = use_tma ? (int)((qbase + i) % kStages) : (i & 1);
+      const float2* sA = sbase + (size_t)s * stage_elems;
+      const float2* sB = sA + FC * kTile;
+      const float2* sC = sB + FC * kTile;
       bool ok = true;
       if (use_tma) {
-        ok = mbar_wait_bounded(&full[s], (phase >> s) & 1u, status);
-        phase ^= 1u << s;
+        ok = mbar_wait_bounded(&full[s], ((qbase + i) / kStages) & 1u, status);
       } else {
-        const long long gbase = (long long)g * m * Mp;
-        for (int idx = tid; idx < m * 4 * kTile; idx += blockDim.x) {
+        float2* w = sbase + (size_t)s * stage_elems;
+        for (int idx = tid; idx < nf * 4 * kTile; idx += blockDim.x) {
           const int j = idx / (4 * kTile);
           const int e = idx - j * 4 * kTile;
-          const long long r = gbase + (long long)j * Mp;
-          if (e < kTile) st.a[j * kTile + e] = coef(sa + r, k0 + e, M);
-          else if (e < 2 * kTile) st.b[j * kTile + e - kTile] = coef(sb + r, l0 + e - kTile, M);
-          else st.c[j * 2 * kTile + e - 2 * kTile] = coef(sc + r, k0 + l0 + e - 2 * kTile, M);
+          const long long r = ((long long)g * m + j0 + j) * Mp;
+          if (e < kTile)
+            w[j * kTile + e] = coef(sa + r, k0 + e, M);
+          else if (e < 2 * kTile)
+            w[FC * kTile + j * kTile + e - kTile] = coef(sb + r, l0 + e - kTile, M);
+          else
+            w[2 * FC * kTile + j * 2 * kTile + e - 2 * kTile] =
+                coef(sc + r, k0 + l0 + e - 2 * kTile, M);
         }
         __syncthreads();
       }
       if (active) {
-        float ar[16], ai[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) ar[i] = ai[i] = 0.f;
 #pragma unroll 2
-        for (int j = 0; j < m; ++j) {
-          const float4* pa = reinterpret_cast<const float4*>(st.a + j * kTile + kt);
-          const float4* pb = reinterpret_cast<const float4*>(st.b + j * kTile + lt);
-          const float4* pc = reinterpret_cast<const float4*>(st.c + j * 2 * kTile + kt + lt);
+        for (int j = 0; j < nf; ++j) {
+          const float4* pa = reinterpret_cast<const float4*>(sA + j * kTile + kt);
+          const float4* pb = reinterpret_cast<const float4*>(sB + j * kTile + lt);
+          const float4* pc = reinterpret_cast<const float4*>(sC + j * 2 * kTile + kt + lt);
           const float4 a01 = pa[0], a23 = pa[1], b01 = pb[0], b23 = pb[1];
           const float4 c01 = pc[0], c23 = pc[1], c45 = pc[2], c67 = pc[3];
           const float2 ak[4] = {{a01.x, a01.y}, {a01.z, a01.w}, {a23.x, a23.y}, {a23.z, a23.w}};
@@ -162,27 +150,32 @@ k2_bispec(const float2* __restrict__ sa, const float2* __restrict__ sb,
             }
           }
         }
+        if (ch == nch - 1) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float vr = ar[i] * pref3, vi = ai[i] * pref3;
-          sr[i] += vr;
-          si[i] += vi;
-          qr[i] = fmaf(vr, vr, qr[i]);
-          qi[i] = fmaf(vi, vi, qi[i]);
+          for (int q = 0; q < 16; ++q) {
+            const float vr = ar[q] * pref3, vi = ai[q] * pref3;
+            sr[q] += vr;
+            si[q] += vi;
+            qr[q] = fmaf(vr, vr, qr[q]);
+            qi[q] = fmaf(vi, vi, qi[q]);
+            ar[q] = ai[q] = 0.f;
+          }
         }
       }
       // every thread is done with stage s; a failed wait anywhere stops the CTA
       if (__syncthreads_or(!ok)) {
-        // drain the other stage's copy, if one is in flight, then give up
-        if (use_tma && g + 1 < gb) mbar_wait_bounded(&full[s ^ 1], (phase >> (s ^ 1)) & 1u, status);
+        if (use_tma)  // drain copies still in flight before giving up
+          for (int r = i + 1; r < nsteps && r < i + kStages; ++r)
+            mbar_wait_bounded(&full[(qbase + r) % kStages], ((qbase + r) / kStages) & 1u, status);
         aborted = true;
         return;
       }
-      if (use_tma && tid == 0 && g + 2 < gb) {
+      if (use_tma && tid == 0 && i + kStages < nsteps) {
         fence_async_smem();
-        issue(s, g + 2);
+        issue(i + kStages);
       }
     }
+    if (use_tma) qbase += nsteps;
     if (!active) return;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -191,11 +184,11 @@ k2_bispec(const float2* __restrict__ sa, const float2* __restrict__ sb,
         const int k = k0 + kt + a, l = l0 + lt + b;
         if (!in_domain3(k, l, M, cross)) continue;
         const long long o = (long long)(k + koff) * M + l;
-        const int i = a * 4 + b;
-        atomicAdd(acc + o, (double)sr[i]);
-        atomicAdd(acc + plane + o, (double)si[i]);
-        atomicAdd(acc + 2 * plane + o, (double)qr[i]);
-        atomicAdd(acc + 3 * plane + o, (double)qi[i]);
+        const int q = a * 4 + b;
+        atomicAdd(acc + o, (double)sr[q]);
+        atomicAdd(acc + plane + o, (double)si[q]);
+        atomicAdd(acc + 2 * plane + o, (double)qr[q]);
+        atomicAdd(acc + 3 * plane + o, (double)qi[q]);
       }
     }
   });
@@ -203,12 +196,16 @@ k2_bispec(const float2* __restrict__ sa, const float2* __restrict__ sb,
 
 }  // namespace
 
-cudaError_t launch_k2_bispec(const float2* spec_a, const float2* spec_b, const float2* spec_c,
-                             int G, int m, int M, int Mp, const TileInfo* tiles, int n_tiles,
-                             int cross, float pref3, double* acc, long long plane, int rows,
-                             int nsm, int* status, cudaStream_t stream) {
+size_t k2_smem_bytes(int FC) { return (size_t)kStages * FC * 4 * kTile * sizeof(float2) + 128; }
+
+cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
+                             const float2* spec_a, const float2* spec_b, const float2* spec_c,
+                             int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
+                             const TileInfo* tiles, int n_tiles, int cross, float pref3,
+                             double* acc, long long plane, int rows, int nsm, int* status,
+                             cudaStream_t stream) {
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
-  const size_t smem = (size_t)2 * m * 4 * kTile * sizeof(float2);
+  const size_t smem = k2_smem_bytes(FC);
   cudaError_t e = cudaFuncSetAttribute(k2_bispec, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -217,9 +214,9 @@ cudaError_t launch_k2_bispec(const float2* spec_a, const float2* spec_b, const f
   if (e != cudaSuccess) return e;
   const int n_cta = nsm * (occ > 0 ? occ : 1);
   const int koff = (rows == M) ? 0 : (M - 1);
-  k2_bispec<<<n_cta, kThreadsPair, smem, stream>>>(spec_a, spec_b, spec_c, G, m, M, Mp, tiles,
-                                                   n_tiles, cross, pref3, acc, plane, koff,
-                                                   status);
+  k2_bispec<<<n_cta, kThreadsPair, smem, stream>>>(tm64, tm128, spec_a, spec_b, spec_c, rowA,
+                                                   rowB, rowC, G, m, FC, M, Mp, tiles, n_tiles,
+                                                   cross, pref3, acc, plane, koff, status);
   return cudaGetLastError();
 }
 

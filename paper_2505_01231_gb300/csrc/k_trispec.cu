@@ -17,43 +17,41 @@
 // This is the plain FP32 CUDA-core form of the fourth-order moment sums: five
 // length-m dot products per grid point and group.  Work split as in K2: a
 // persistent CTA walks balanced (64 x 64 tile of the upper triangle k <= l,
-// group range) segments; the m frames' coefficients at k0.. and l0.. arrive by
-// 1-D TMA bulk copies into two shared-memory stages; 4 x 4 micro-tiles.
+// group range) segments; chunks of FC frames of the coefficients at k0.. and
+// l0.. arrive by 2-D TMA box loads into kStages shared-memory stages, |da|^2 is
+// formed once per staged chunk, and each thread evaluates a 4 x 4 micro-tile.
 #include "internal.cuh"
 #include "pipeline.cuh"
 
 namespace ss {
 namespace {
 
-__device__ __forceinline__ uint32_t seg_bytes(int k0, int n, int Mp) {
-  const int len = min(n, Mp - k0);
-  return len > 0 ? (uint32_t)len * sizeof(float2) : 0u;
-}
+constexpr int kStages = 4;
 
 __global__ void __launch_bounds__(kThreadsPair, 1)
-k3_trispec(const float2* __restrict__ spec, int G, int m, int M, int Mp,
+k3_trispec(const __grid_constant__ CUtensorMap tm64, int row0, int G, int m, int FC, int M,
            const TileInfo* __restrict__ tiles, int n_tiles, float pref_a, float pref_b,
            double* __restrict__ acc, long long plane, int* __restrict__ status) {
-  extern __shared__ __align__(128) float4 smem_raw[];
-  __shared__ __align__(8) uint64_t full[2];
-  float2* sbase = reinterpret_cast<float2*>(smem_raw);       // 2 stages x [2][m][64] float2
-  float* pA = reinterpret_cast<float*>(sbase + 2 * 2 * m * kTile);  // [m][64]
-  float* pB = pA + m * kTile;                                        // [m][64]
+  extern __shared__ __align__(128) float4 smem_raw[];  // + 128 spare bytes for alignment
+  __shared__ __align__(8) uint64_t full[kStages];
+  float2* sbase = align128<float2>(smem_raw);   // kStages x [2][FC][64] float2
+  const int stage_elems = 2 * FC * kTile;
+  float* pA = reinterpret_cast<float*>(sbase + kStages * stage_elems);  // [FC][64]
+  float* pB = pA + FC * kTile;                                           // [FC][64]
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int tx = (warp & 1) * 8 + (lane & 7);
   const int ty = (warp >> 1) * 4 + (lane >> 3);
   const int kt = 4 * tx, lt = 4 * ty;
+  const int nch = (m + FC - 1) / FC;
 
   if (tid == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
+    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
-  for (int i = tid; i < 2 * 2 * m * kTile; i += blockDim.x) sbase[i] = make_float2(0.f, 0.f);
   fence_async_smem();
   __syncthreads();
-  uint32_t phase = 0;
+  uint32_t qbase = 0;
   bool aborted = false;
 
   for_each_segment(tiles, n_tiles, G, blockIdx.x, gridDim.x, [&](int t, int ga, int gb) {
@@ -61,46 +59,41 @@ k3_trispec(const float2* __restrict__ spec, int G, int m, int M, int Mp,
     const int k0 = tiles[t].k0, l0 = tiles[t].l0;
     const int kw = k0 + 32 * (warp & 1), lw = l0 + 16 * (warp >> 1);
     const bool active = (kw <= lw + 15) && (lw < M) && (kw < M);
-    const uint32_t ba = seg_bytes(k0, kTile, Mp), bb = seg_bytes(l0, kTile, Mp);
-    auto issue = [&](int s, int g) {
-      float2* sa = sbase + (size_t)s * 2 * m * kTile;
-      float2* sb = sa + m * kTile;
-      mbar_arrive_expect_tx(&full[s], (uint32_t)m * (ba + bb));
-      for (int j = 0; j < m; ++j) {
-        const long long r = ((long long)g * m + j) * Mp;
-        if (ba) tma_load_1d(sa + j * kTile, spec + r + k0, ba, &full[s]);
-        if (bb) tma_load_1d(sb + j * kTile, spec + r + l0, bb, &full[s]);
-      }
+    const int nsteps = (gb - ga) * nch;
+    auto issue = [&](int i) {
+      const int s = (int)((qbase + i) % kStages);
+      const int g = ga + i / nch, j0 = (i % nch) * FC;
+      float2* st = sbase + (size_t)s * stage_elems;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_elems * sizeof(float2)));
+      tma_load_2d(st, &tm64, k0, row0 + g * m + j0, &full[s]);
+      tma_load_2d(st + FC * kTile, &tm64, l0, row0 + g * m + j0, &full[s]);
     };
 
-    float sum[16], sq[16];
+    float sum[16], sq[16], q[16], rr[16], ii[16], xx[16], xt[16], sk[4], sl[4];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) sum[i] = sq[i] = 0.f;
+    for (int i = 0; i < 16; ++i) sum[i] = sq[i] = q[i] = rr[i] = ii[i] = xx[i] = xt[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sk[i] = sl[i] = 0.f;
     if (tid == 0) {
       fence_async_smem();
-      issue(0, ga);
-      if (ga + 1 < gb) issue(1, ga + 1);
+      for (int i = 0; i < kStages && i < nsteps; ++i) issue(i);
     }
-    for (int g = ga; g < gb; ++g) {
-      const int s = (g - ga) & 1;
-      const float2* sA = sbase + (size_t)s * 2 * m * kTile;
-      const float2* sB = sA + m * kTile;
-      const bool ok = mbar_wait_bounded(&full[s], (phase >> s) & 1u, status);
-      phase ^= 1u << s;
-      for (int i = tid; i < 2 * m * kTile; i += blockDim.x) {
-        const float2 v = sA[i];  // sA and sB are contiguous: [2][m][64]
+    for (int i = 0; i < nsteps; ++i) {
+      const int ch = i % nch;
+      const int nf = min(FC, m - ch * FC);
+      const int s = (int)((qbase + i) % kStages);
+      const float2* sA = sbase + (size_t)s * stage_elems;
+      const float2* sB = sA + FC * kTile;
+      const bool ok = mbar_wait_bounded(&full[s], ((qbase + i) / kStages) & 1u, status);
+      for (int e = tid; e < 2 * FC * kTile; e += blockDim.x) {
+        const float2 v = sA[e];  // sA and sB are contiguous: [2][FC][64]
         const float p = fmaf(v.x, v.x, v.y * v.y);
-        if (i < m * kTile) pA[i] = p; else pB[i - m * kTile] = p;
+        if (e < FC * kTile) pA[e] = p; else pB[e - FC * kTile] = p;
       }
       __syncthreads();
       if (active) {
-        float q[16], rr[16], ii[16], xx[16], xt[16], sk[4], sl[4];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) q[i] = rr[i] = ii[i] = xx[i] = xt[i] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) sk[i] = sl[i] = 0.f;
 #pragma unroll 2
-        for (int j = 0; j < m; ++j) {
+        for (int j = 0; j < nf; ++j) {
           const float4* a4 = reinterpret_cast<const float4*>(sA + j * kTile + kt);
           const float4* b4 = reinterpret_cast<const float4*>(sB + j * kTile + lt);
           const float4 a01 = a4[0], a23 = a4[1], b01 = b4[0], b23 = b4[1];
@@ -119,40 +112,47 @@ k3_trispec(const float2* __restrict__ spec, int G, int m, int M, int Mp,
           for (int a = 0; a < 4; ++a) {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-              const int i = a * 4 + b;
-              q[i] = fmaf(pk[a], pl[b], q[i]);
-              rr[i] = fmaf(ak[a].x, al[b].x, rr[i]);
-              ii[i] = fmaf(ak[a].y, al[b].y, ii[i]);
-              xx[i] = fmaf(ak[a].x, al[b].y, xx[i]);
-              xt[i] = fmaf(ak[a].y, al[b].x, xt[i]);
+              const int r = a * 4 + b;
+              q[r] = fmaf(pk[a], pl[b], q[r]);
+              rr[r] = fmaf(ak[a].x, al[b].x, rr[r]);
+              ii[r] = fmaf(ak[a].y, al[b].y, ii[r]);
+              xx[r] = fmaf(ak[a].x, al[b].y, xx[r]);
+              xt[r] = fmaf(ak[a].y, al[b].x, xt[r]);
             }
           }
         }
+        if (ch == nch - 1) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+          for (int a = 0; a < 4; ++a) {
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int i = a * 4 + b;
-            float uv = fmaf(rr[i], rr[i], ii[i] * ii[i]);
-            uv = fmaf(xx[i], xx[i], uv);
-            uv = fmaf(xt[i], xt[i], uv);
-            const float pair = fmaf(2.f, uv, sk[a] * sl[b]);
-            const float c4 = fmaf(pref_a, q[i], -pref_b * pair);
-            sum[i] += c4;
-            sq[i] = fmaf(c4, c4, sq[i]);
+            for (int b = 0; b < 4; ++b) {
+              const int r = a * 4 + b;
+              float uv = fmaf(rr[r], rr[r], ii[r] * ii[r]);
+              uv = fmaf(xx[r], xx[r], uv);
+              uv = fmaf(xt[r], xt[r], uv);
+              const float pair = fmaf(2.f, uv, sk[a] * sl[b]);
+              const float c4 = fmaf(pref_a, q[r], -pref_b * pair);
+              sum[r] += c4;
+              sq[r] = fmaf(c4, c4, sq[r]);
+              q[r] = rr[r] = ii[r] = xx[r] = xt[r] = 0.f;
+            }
           }
+#pragma unroll
+          for (int a = 0; a < 4; ++a) sk[a] = sl[a] = 0.f;
         }
       }
       if (__syncthreads_or(!ok)) {
-        if (g + 1 < gb) mbar_wait_bounded(&full[s ^ 1], (phase >> (s ^ 1)) & 1u, status);
+        for (int r = i + 1; r < nsteps && r < i + kStages; ++r)
+          mbar_wait_bounded(&full[(qbase + r) % kStages], ((qbase + r) / kStages) & 1u, status);
         aborted = true;
         return;
       }
-      if (tid == 0 && g + 2 < gb) {
+      if (tid == 0 && i + kStages < nsteps) {
         fence_async_smem();
-        issue(s, g + 2);
+        issue(i + kStages);
       }
     }
+    qbase += nsteps;
     if (!active) return;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -170,13 +170,17 @@ k3_trispec(const float2* __restrict__ spec, int G, int m, int M, int Mp,
 
 }  // namespace
 
-cudaError_t launch_k3_trispec(const float2* spec, int G, int m, int M, int Mp,
+size_t k3_smem_bytes(int FC) {
+  return (size_t)kStages * 2 * FC * kTile * sizeof(float2) + (size_t)2 * FC * kTile * sizeof(float) +
+         128;
+}
+
+cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, int FC, int M,
                               const TileInfo* tiles, int n_tiles, float pref4a, float pref4b,
                               double* acc, long long plane, int nsm, int* status,
                               cudaStream_t stream) {
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
-  const size_t smem = (size_t)2 * 2 * m * kTile * sizeof(float2) +
-                      (size_t)2 * m * kTile * sizeof(float);
+  const size_t smem = k3_smem_bytes(FC);
   cudaError_t e = cudaFuncSetAttribute(k3_trispec, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -184,8 +188,8 @@ cudaError_t launch_k3_trispec(const float2* spec, int G, int m, int M, int Mp,
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_trispec, kThreadsPair, smem);
   if (e != cudaSuccess) return e;
   const int n_cta = nsm * (occ > 0 ? occ : 1);
-  k3_trispec<<<n_cta, kThreadsPair, smem, stream>>>(spec, G, m, M, Mp, tiles, n_tiles, pref4a,
-                                                    pref4b, acc, plane, status);
+  k3_trispec<<<n_cta, kThreadsPair, smem, stream>>>(tm64, row0, G, m, FC, M, tiles, n_tiles,
+                                                    pref4a, pref4b, acc, plane, status);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 // schedule of (tile, group range) work used by the persistent pair kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,6 +17,14 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// First 128-byte aligned address at or after p in shared memory (tiled TMA
+// destinations need 128-byte alignment; kernels reserve 128 spare bytes).
+template <typename T>
+__device__ __forceinline__ T* align128(void* p) {
+  const uint32_t a = smem_addr(p);
+  return reinterpret_cast<T*>(static_cast<char*>(p) + ((128u - (a & 127u)) & 127u));
 }
 
 __device__ __forceinline__ unsigned long long global_timer_ns() {
@@ -55,6 +64,18 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
       : "memory");
 }
 
+// 2-D tiled TMA load of one box of a tensor map (coordinates {x, y}, x the
+// innermost; x * element size must be a multiple of 16 bytes); bins outside the
+// tensor are filled with zeros.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -80,6 +101,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
   return true;
 }
+
+// Scheduling cost of one (tile, group) unit: the warps of the CTA whose
+// sub-tile touches the domain, plus a fixed part for staging and barriers that
+// every group pays whatever the tile's shape.
+constexpr int kTileFixedCost = 3;
 
 // Work description of one tile of (k, l) grid points: origin and per-group
 // weight (number of warps of the CTA whose sub-tile touches the domain).

@@ -21,6 +21,8 @@
 #include <utility>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "internal.cuh"
 
 using namespace ss;
@@ -76,6 +78,8 @@ struct ss_plan_s {
   int n_s2cross = 0;
   TileInfo *d_tiles3 = nullptr, *d_tiles4 = nullptr;
   int* d_status = nullptr;
+  int FC = 0;                      // frames per staged chunk of the pair kernels
+  CUtensorMap tm64{}, tm128{};     // 2-D views [rows = C*Gb_max*m][M] of the spectra
   int n_tiles3 = 0, n_tiles4 = 0;
   long long pairs3 = 0, pairs4 = 0;
   void* d_stage[2] = {nullptr, nullptr};
@@ -163,7 +167,8 @@ bool in_domain3(int k, int l, int M, bool cross) {
 
 // Tiles of 64 x 64 grid points that touch the domain, each weighted by the
 // number of its 32 x 16 warp sub-tiles that touch the domain (the kernels skip
-// the others), with prefix sums for the balanced schedule.
+// the others) plus the fixed per-group cost, with prefix sums for the balanced
+// schedule.
 void build_tiles(ss_plan_s* p, std::vector<TileInfo>& t3, std::vector<TileInfo>& t4) {
   const int M = p->M;
   const bool cross = p->C > 1;
@@ -188,8 +193,8 @@ void build_tiles(ss_plan_s* p, std::vector<TileInfo>& t3, std::vector<TileInfo>&
   for (int k0 = kmin; k0 < M; k0 += kTile)
     for (int l0 = 0; l0 < M; l0 += kTile) {
       const int w3 = warps(k0, l0, dom3), w4 = warps(k0, l0, dom4);
-      if (w3) t3.push_back(TileInfo{k0, l0, w3, 0});
-      if (w4) t4.push_back(TileInfo{k0, l0, w4, 0});
+      if (w3) t3.push_back(TileInfo{k0, l0, w3 + kTileFixedCost, 0});
+      if (w4) t4.push_back(TileInfo{k0, l0, w4 + kTileFixedCost, 0});
     }
   for (auto* v : {&t3, &t4}) {
     int acc = 0;
@@ -269,10 +274,13 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
         const long long plane = (long long)p->c3.size() * p->rows3 * p->M;
         for (size_t i = 0; i < p->c3.size(); ++i) {
           const Combo& cb = p->c3[i];
-          SS_TRY(p, launch_k2_bispec(p->d_spec + cb.c[0] * chan_stride,
+          const int row_stride = p->Gb_max * p->m;
+          SS_TRY(p, launch_k2_bispec(p->tm64, p->tm128, p->d_spec + cb.c[0] * chan_stride,
                                      p->d_spec + cb.c[1] * chan_stride,
-                                     p->d_spec + cb.c[2] * chan_stride, cnt, p->m, p->M, p->Mp,
-                                     p->d_tiles3, p->n_tiles3, p->C > 1 ? 1 : 0, pref3,
+                                     p->d_spec + cb.c[2] * chan_stride, cb.c[0] * row_stride,
+                                     cb.c[1] * row_stride, cb.c[2] * row_stride, cnt, p->m,
+                                     p->FC, p->M, p->Mp, p->d_tiles3, p->n_tiles3,
+                                     p->C > 1 ? 1 : 0, pref3,
                                      p->d_acc3 + (long long)i * p->rows3 * p->M, plane, p->rows3,
                                      p->nsm, p->d_status, p->stream));
         }
@@ -283,8 +291,8 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
         const long long plane = (long long)p->c4.size() * p->rows4 * p->M;
         for (size_t i = 0; i < p->c4.size(); ++i) {
           const Combo& cb = p->c4[i];
-          SS_TRY(p, launch_k3_trispec(p->d_spec + cb.c[0] * chan_stride, cnt, p->m, p->M, p->Mp,
-                                      p->d_tiles4, p->n_tiles4, pref4a, pref4b,
+          SS_TRY(p, launch_k3_trispec(p->tm64, cb.c[0] * p->Gb_max * p->m, cnt, p->m, p->FC,
+                                      p->M, p->d_tiles4, p->n_tiles4, pref4a, pref4b,
                                       p->d_acc4 + (long long)i * p->rows4 * p->M, plane, p->nsm,
                                       p->d_status, p->stream));
         }
@@ -378,6 +386,36 @@ ss_status zero_state(ss_plan_s* p) {
   return SS_OK;
 }
 
+// 2-D tensor maps over the centred spectra, one row per frame: element (x, y)
+// is bin x of frame row y (rows of channel c start at c * Gb_max * m); boxes of
+// FC rows by 64 or 128 bins; bins >= M read as zero.
+ss_status encode_maps(ss_plan_s* p) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(p, SS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t rows = (cuuint64_t)p->C * p->Gb_max * p->m;
+  const cuuint64_t dims[2] = {(cuuint64_t)p->M, rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)p->Mp * sizeof(float2)};
+  const cuuint32_t estr[2] = {1, 1};
+  for (int w : {64, 128}) {
+    const cuuint32_t box[2] = {(cuuint32_t)w, (cuuint32_t)p->FC};
+    CUresult r = encode(w == 64 ? &p->tm64 : &p->tm128, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                        p->d_spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(p, SS_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string(r));
+  }
+  return SS_OK;
+}
+
 ss_status alloc_spec(ss_plan_s* p) {
   if (p->d_spec) {
     cudaFree(p->d_spec);
@@ -390,9 +428,12 @@ ss_status alloc_spec(ss_plan_s* p) {
     // about 1.5 GiB of centred spectra per batch, at least one group
     gb = (int)std::max<size_t>(1, (size_t)(1536ull << 20) / per_group);
   }
+  // the 2-D views index rows with 32-bit coordinates
+  const long long max_rows = (1ll << 31) - 1;
+  if ((long long)p->C * gb * p->m > max_rows) gb = (int)(max_rows / ((long long)p->C * p->m));
   p->Gb_max = gb;
   SS_TRY(p, dev_alloc(p, &p->d_spec, per_group * gb));
-  return SS_OK;
+  return encode_maps(p);
 }
 
 void destroy(ss_plan_s* p) {
@@ -470,6 +511,10 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   p->dtype = dtype;
   p->precision = precision;
   p->elem = dtype == SS_F32 ? 4 : 2;
+  {
+    const int nch = (m + 15) / 16;
+    p->FC = (m + nch - 1) / nch;  // chunks of at most 16 frames, as even as possible
+  }
   p->stream = static_cast<cudaStream_t>(stream);
 
   if (combos) {

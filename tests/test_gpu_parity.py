@@ -81,7 +81,9 @@ def test_config1_full_grid(c1_signal):
 
 
 @pytest.mark.parametrize("T,m,G", [(8, 4, 50), (16, 5, 40), (64, 6, 30), (128, 4, 24),
-                                   (512, 7, 9), (4096, 4, 3)])
+                                   (512, 7, 9), (4096, 4, 3),
+                                   # groups longer than one staged chunk of frames
+                                   (64, 17, 12), (32, 40, 8), (16, 300, 4)])
 def test_sizes_and_ragged_tails(T, m, G):
     z = synth.ar1_quadratic(T * m * G + 3 * T + 5, seed=T + m)   # partial group dropped
     ref = oracle.polyspectra(z, T, 0.25, m, group_chunk=8)
