@@ -136,7 +136,7 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
  *              (channel c starts at element c * n_samples).  Device memory or
  *              host memory (pinned or pageable).
  * The record is cut into consecutive frames of T samples and groups of m frames
- * (Eq. 16; Sec. 10: "m subsequent temporal windows").  Samples that do not yet
+ * (Eq. 16; Sec. 10 estimates from m consecutive windows).  Samples that do not yet
  * complete a group are kept by the plan and prepended to the next chunk, so any
  * split of a record into chunks gives the same groups and the same result.
  * Work is enqueued on the plan's stream; a device chunk must stay valid until
@@ -196,6 +196,43 @@ const char* ss_last_error(ss_plan_t plan);
 
 /* ss_version -- library version string. */
 const char* ss_version(void);
+
+/*
+ * ss_s2_noalloc -- power spectrum S2 of one float32 channel, without allocating
+ * any device memory.  The paper has no counterpart to this entry point; it
+ * exists for callers that cannot call cudaMalloc: processes whose device memory
+ * is owned up front by a framework's caching allocator or by a fixed budget,
+ * and latency-critical loops that must neither wait for an allocation
+ * (cudaMalloc can synchronise the device) nor handle its failure.
+ *
+ * It computes the same S2 as a one-channel plan with SS_ORDER2 fed the whole
+ * record in one ss_accumulate call (Sec. 3, Eq. 23; Sec. 4.1, Eq. 32; error
+ * bars Sec. 4.2, Eq. 35-36), with every intermediate (window and twiddle tables,
+ * centred spectra, float64 sums) kept in one static device array of
+ * SS_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the library holds
+ * until the process exits.
+ *   d_signal   device pointer to n_samples float32 samples.
+ *   T, dt, m, window, win_param   as for ss_plan (m >= 2).
+ *   d_S2       device output, [M] complex128 as interleaved (re, im) doubles.
+ *   d_S2_err   device output [M] (err_re, err_im), or NULL.
+ *   stream     cudaStream_t; the work is enqueued on it and the call returns
+ *              without waiting (outputs are ready when the stream passes it).
+ * Limit: the centred spectra of all groups must fit the scratch array,
+ * floor(n_samples / (m T)) * m * (M rounded up to a multiple of 4) * 8 bytes
+ * <= SS_NOALLOC_SCRATCH_BYTES - 128 KiB; longer inputs return SS_EINVAL.
+ * Fewer than two groups return SS_ESTATE.  ss_noalloc_last_error() describes
+ * the last failure of the calling thread.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  All calls share the one array: calls whose work
+ * overlaps on the GPU (concurrent streams, or several host threads) race on it
+ * and give wrong results; order them on one stream or serialise them.
+ */
+#define SS_NOALLOC_SCRATCH_BYTES (32u << 20)
+ss_status ss_s2_noalloc(const float* d_signal, size_t n_samples, int T, double dt, int m,
+                        int window, double win_param, double* d_S2, double* d_S2_err,
+                        void* stream);
+const char* ss_noalloc_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,7 @@ __all__ = [
     "SSError", "ss_info", "ss_stats_t", "lib", "LIB_PATH",
     "ss_plan", "ss_accumulate", "ss_finalize", "ss_reset", "ss_query", "ss_combos",
     "ss_set_timing", "ss_stats", "ss_set_batch", "ss_destroy", "ss_last_error", "ss_version",
-    "Plan",
+    "ss_s2_noalloc", "Plan",
 ]
 
 SS_OK, SS_EINVAL, SS_ENOMEM, SS_ECUDA, SS_ESTATE, SS_ETIMEOUT, SS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
@@ -70,6 +70,9 @@ _sig = {
     "ss_destroy": (ctypes.c_int, [_P]),
     "ss_last_error": (ctypes.c_char_p, [_P]),
     "ss_version": (ctypes.c_char_p, []),
+    "ss_s2_noalloc": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P]),
+    "ss_noalloc_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -167,6 +170,17 @@ def ss_last_error(plan=None):
 
 def ss_version():
     return lib.ss_version().decode()
+
+
+def ss_s2_noalloc(d_signal, n_samples, T, dt, m, window=SS_WIN_HANN, win_param=0.14,
+                  d_S2=None, d_S2_err=None, stream=None):
+    """Power spectrum of one device-resident float32 channel with no device allocation
+    (see include/polyspec.h).  Outputs are device buffers; the call is stream-ordered."""
+    st = lib.ss_s2_noalloc(_addr(d_signal), n_samples, T, float(dt), m, window,
+                           float(win_param), _addr(d_S2), _addr(d_S2_err),
+                           _addr(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream)
+    if st != SS_OK:
+        raise SSError(st, lib.ss_noalloc_last_error().decode())
 
 
 class Plan:

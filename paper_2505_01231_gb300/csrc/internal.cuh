@@ -13,6 +13,9 @@
 
 namespace ss {
 
+// Size of the static scratch array of ss_s2_noalloc.
+constexpr size_t kNoallocScratchBytes = SS_NOALLOC_SCRATCH_BYTES;
+
 // Tile edge of the bispectrum and trispectrum kernels in (k, l) grid points.
 constexpr int kTile = 64;
 // Threads per CTA of the frame/FFT kernel and of the pair kernels.
