@@ -56,22 +56,35 @@ cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G,
                                int Mp, const int4* pairs, int n_pairs, float pref2, double* acc2,
                                long long plane, int nsm, cudaStream_t stream);
 
-// Pair kernels run persistent grids of nsm x (resident CTAs per SM) CTAs over a
-// balanced schedule of the tiles (see pipeline.cuh).  acc points at the
+// Pair kernels run persistent grids of nsm x (resident CTAs per SM) CTAs that
+// take (group chunk, tile) items from a queue (see pipeline.cuh); `counter` is
+// a device int the launcher zeroes on the stream.  acc points at the
 // combination's first accumulator plane; `plane` is the distance in doubles
 // between the four planes (sum Re, sum Im, sumsq Re, sumsq Im).  `status` is
 // the plan's device status word (a bounded wait that gives up writes to it).
+// The tensor maps view the centred spectra as [rows][Mp/16][16] float2 with
+// 128-byte swizzling; tm64 has boxes of 4 blocks (64 bins), tm128 of 8.
 cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
                              const float2* spec_a, const float2* spec_b, const float2* spec_c,
                              int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
                              const TileInfo* tiles, int n_tiles, int cross, float pref3,
-                             double* acc, long long plane, int rows, int nsm, int* status,
-                             cudaStream_t stream);
+                             double* acc, long long plane, int rows, int nsm, int* counter,
+                             int* status, cudaStream_t stream);
 
 cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, int FC, int M,
                               const TileInfo* tiles, int n_tiles, float pref4a, float pref4b,
-                              double* acc, long long plane, int nsm, int* status,
+                              double* acc, long long plane, int nsm, int* counter, int* status,
                               cudaStream_t stream);
+
+// Groups per work item: about 16 items per CTA, whole groups, at least one.
+inline int work_group_chunk(int G, int n_tiles, int n_cta) {
+  const long long units = (long long)G * n_tiles;
+  const long long target = 16ll * n_cta;
+  long long gc = (units + target - 1) / target;
+  if (gc < 1) gc = 1;
+  if (gc > G) gc = G;
+  return (int)gc;
+}
 
 // dynamic shared memory of the pair kernels for FC frames per stage
 size_t k2_smem_bytes(int FC);

@@ -8,16 +8,18 @@
 // (Sec. 4.2, Eq. 35-36).  The window and dt normalisation (Eq. 28, Eq. 48) is
 // applied by the finalize kernel.
 //
-// Work split: a persistent CTA walks a balanced list of (64 x 64 tile of (k, l),
-// range of groups) segments.  A group's frames are taken in chunks of FC frames;
-// for each chunk one thread issues three 2-D TMA box loads (FC frames x 64 bins
-// at k0, at l0, and FC x 128 bins at k0 + l0; bins past the spectrum read as
-// zero) into one of kStages shared-memory stages, so loads run kStages-1 chunks
-// ahead of the arithmetic.  Each thread evaluates a 4 x 4 micro-tile of grid
-// points with 128-bit shared loads; its float32 sums over the segment's groups
-// are added to the float64 accumulators when the segment ends.  Warps whose
-// 32 x 16 sub-tile lies outside the domain skip the arithmetic.  All waits on
-// the stage barriers are bounded.
+// Work split: persistent CTAs take (group chunk, 64 x 64 tile of (k, l)) items
+// from a group-major work queue.  A group's frames are taken in chunks of FC
+// frames; for each chunk one thread issues three 3-D TMA box loads (FC frames x
+// 64 bins at k0, at l0, and FC x 128 bins at k0 + l0, as 128-byte blocks of 16
+// bins with 128-byte swizzling; bins past the spectrum read as zero) into one of
+// kStages shared-memory stages, so loads run kStages-1 chunks ahead of the
+// arithmetic.  Each thread evaluates a 4 x 4 micro-tile of grid points with
+// 128-bit shared loads; the thread layout (a quarter-warp covers 4 k-threads x
+// 2 l-threads) together with the swizzle keeps every quarter-warp on distinct
+// banks.  Per-item float32 sums over groups are added to the float64
+// accumulators when the item ends.  Warps whose 32 x 16 sub-tile lies outside
+// the domain skip the arithmetic.  All waits on the stage barriers are bounded.
 //
 // Domains: one channel (cross = 0): 0 <= k <= l, k + l <= M-1 (the rest follows
 // from S3(k, l) = S3(l, k), Sec. 9).  Several channels (cross = 1):
@@ -45,35 +47,58 @@ __device__ __forceinline__ bool in_domain3(int k, int l, int M, int cross) {
   return k >= 0 && k <= l && k + l < M;
 }
 
+// bytes of one [FC][64] float2 array rounded up to the 1024-byte swizzle atom
+__host__ __device__ __forceinline__ uint32_t arr64_bytes(int FC) {
+  return ((uint32_t)FC * 512u + 1023u) & ~1023u;
+}
+__host__ __device__ __forceinline__ uint32_t stage_bytes(int FC) {
+  return 2u * arr64_bytes(FC) + (uint32_t)FC * 1024u;
+}
+
+__device__ __forceinline__ float4 lds128(const unsigned char* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+
 __global__ void __launch_bounds__(kThreadsPair, 1)
 k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUtensorMap tm128,
           const float2* __restrict__ sa, const float2* __restrict__ sb,
           const float2* __restrict__ sc, int rowA, int rowB, int rowC, int G, int m, int FC,
-          int M, int Mp, const TileInfo* __restrict__ tiles, int n_tiles, int cross, float pref3,
-          double* __restrict__ acc, long long plane, int koff, int* __restrict__ status) {
-  extern __shared__ __align__(128) float4 smem_raw[];  // + 128 spare bytes for alignment
+          int M, int Mp, const TileInfo* __restrict__ tiles, WorkQueue wq, int cross,
+          float pref3, double* __restrict__ acc, long long plane, int koff,
+          int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
   __shared__ __align__(8) uint64_t full[kStages];
-  float2* sbase = align128<float2>(smem_raw);
-  const int stage_elems = FC * 4 * kTile;  // [FC][64] at k, [FC][64] at l, [FC][128] at k+l
+  __shared__ int s_item;
+  unsigned char* sbase = align1024<unsigned char>(smem_raw);
+  const uint32_t sbytes = stage_bytes(FC), a64 = arr64_bytes(FC);
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int tx = (warp & 1) * 8 + (lane & 7);     // 16 threads along k
-  const int ty = (warp >> 1) * 4 + (lane >> 3);   // 16 threads along l
+  const int qw = lane >> 3, r8 = lane & 7;
+  const int tx = (warp & 1) * 8 + (r8 & 3) + 4 * (qw & 1);    // 16 threads along k
+  const int ty = (warp >> 1) * 4 + (r8 >> 2) + 2 * (qw >> 1);  // 16 threads along l
   const int kt = 4 * tx, lt = 4 * ty;
   const int nch = (m + FC - 1) / FC;
+  // swizzled byte offsets of this thread's operands (even / odd frame of a pair)
+  const uint32_t oA0 = swz128(kt * 8), oA1 = swz128(kt * 8 + 16);
+  const uint32_t oA0o = swz128(512 + kt * 8), oA1o = swz128(512 + kt * 8 + 16);
+  const uint32_t oB0 = swz128(lt * 8), oB1 = swz128(lt * 8 + 16);
+  const uint32_t oB0o = swz128(512 + lt * 8), oB1o = swz128(512 + lt * 8 + 16);
+  uint32_t oC[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) oC[d] = swz128((kt + lt) * 8 + 16 * d);
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
-  for (int i = tid; i < kStages * stage_elems; i += blockDim.x) sbase[i] = make_float2(0.f, 0.f);
   fence_async_smem();
   __syncthreads();
   uint32_t qbase = 0;  // TMA steps consumed so far (stage = q % kStages)
-  bool aborted = false;
 
-  for_each_segment(tiles, n_tiles, G, blockIdx.x, gridDim.x, [&](int t, int ga, int gb) {
-    if (aborted) return;
+  for (int item; (item = next_item(wq, &s_item)) >= 0;) {
+    const int t = item % wq.n_tiles;
+    const int ga = (item / wq.n_tiles) * wq.group_chunk;
+    const int gb = min(G, ga + wq.group_chunk);
     const int k0 = tiles[t].k0, l0 = tiles[t].l0;
     const bool use_tma = k0 >= 0 && k0 + l0 >= 0;
     const int kw = k0 + 32 * (warp & 1), lw = l0 + 16 * (warp >> 1);
@@ -84,11 +109,11 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
     auto issue = [&](int i) {
       const int s = (int)((qbase + i) % kStages);
       const int g = ga + i / nch, j0 = (i % nch) * FC;
-      float2* st = sbase + (size_t)s * stage_elems;
-      mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_elems * sizeof(float2)));
-      tma_load_2d(st, &tm64, k0, rowA + g * m + j0, &full[s]);
-      tma_load_2d(st + FC * kTile, &tm64, l0, rowB + g * m + j0, &full[s]);
-      tma_load_2d(st + 2 * FC * kTile, &tm128, k0 + l0, rowC + g * m + j0, &full[s]);
+      unsigned char* st = sbase + (size_t)s * sbytes;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)FC * 256u * 8u);
+      tma_load_3d(st, &tm64, 0, k0 >> 4, rowA + g * m + j0, &full[s]);
+      tma_load_3d(st + a64, &tm64, 0, l0 >> 4, rowB + g * m + j0, &full[s]);
+      tma_load_3d(st + 2 * a64, &tm128, 0, (k0 + l0) >> 4, rowC + g * m + j0, &full[s]);
     };
 
     float sr[16], si[16], qr[16], qi[16], ar[16], ai[16];
@@ -99,40 +124,47 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
       fence_async_smem();
       for (int i = 0; i < kStages && i < nsteps; ++i) issue(i);
     }
+    bool ok = true;
     for (int i = 0; i < nsteps; ++i) {
       const int g = ga + i / nch, ch = i % nch, j0 = ch * FC;
       const int nf = min(FC, m - j0);
       const int s = use_tma ? (int)((qbase + i) % kStages) : (i & 1);
-      const float2* sA = sbase + (size_t)s * stage_elems;
-      const float2* sB = sA + FC * kTile;
-      const float2* sC = sB + FC * kTile;
-      bool ok = true;
+      const unsigned char* sA = sbase + (size_t)s * sbytes;
+      const unsigned char* sB = sA + a64;
+      const unsigned char* sC = sA + 2 * a64;
       if (use_tma) {
         ok = mbar_wait_bounded(&full[s], ((qbase + i) / kStages) & 1u, status);
       } else {
-        float2* w = sbase + (size_t)s * stage_elems;
+        unsigned char* w = sbase + (size_t)s * sbytes;
         for (int idx = tid; idx < nf * 4 * kTile; idx += blockDim.x) {
           const int j = idx / (4 * kTile);
           const int e = idx - j * 4 * kTile;
-          const long long r = ((long long)g * m + j0 + j) * Mp;
-          if (e < kTile)
-            w[j * kTile + e] = coef(sa + r, k0 + e, M);
-          else if (e < 2 * kTile)
-            w[FC * kTile + j * kTile + e - kTile] = coef(sb + r, l0 + e - kTile, M);
-          else
-            w[2 * FC * kTile + j * 2 * kTile + e - 2 * kTile] =
-                coef(sc + r, k0 + l0 + e - 2 * kTile, M);
+          const long long rr = ((long long)g * m + j0 + j) * Mp;
+          float2 v;
+          uint32_t off;
+          if (e < kTile) {
+            v = coef(sa + rr, k0 + e, M);
+            off = swz128(j * 512 + e * 8);
+          } else if (e < 2 * kTile) {
+            v = coef(sb + rr, l0 + e - kTile, M);
+            off = a64 + swz128(j * 512 + (e - kTile) * 8);
+          } else {
+            v = coef(sc + rr, k0 + l0 + e - 2 * kTile, M);
+            off = 2 * a64 + swz128(j * 1024 + (e - 2 * kTile) * 8);
+          }
+          *reinterpret_cast<float2*>(w + off) = v;
         }
         __syncthreads();
       }
       if (active) {
-#pragma unroll 2
-        for (int j = 0; j < nf; ++j) {
-          const float4* pa = reinterpret_cast<const float4*>(sA + j * kTile + kt);
-          const float4* pb = reinterpret_cast<const float4*>(sB + j * kTile + lt);
-          const float4* pc = reinterpret_cast<const float4*>(sC + j * 2 * kTile + kt + lt);
-          const float4 a01 = pa[0], a23 = pa[1], b01 = pb[0], b23 = pb[1];
-          const float4 c01 = pc[0], c23 = pc[1], c45 = pc[2], c67 = pc[3];
+        auto frame = [&](int j, uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1) {
+          const unsigned char* pa = sA + (j & ~1) * 512;
+          const unsigned char* pb = sB + (j & ~1) * 512;
+          const unsigned char* pc = sC + j * 1024;
+          const float4 a01 = lds128(pa + a0), a23 = lds128(pa + a1);
+          const float4 b01 = lds128(pb + b0), b23 = lds128(pb + b1);
+          const float4 c01 = lds128(pc + oC[0]), c23 = lds128(pc + oC[1]);
+          const float4 c45 = lds128(pc + oC[2]), c67 = lds128(pc + oC[3]);
           const float2 ak[4] = {{a01.x, a01.y}, {a01.z, a01.w}, {a23.x, a23.y}, {a23.z, a23.w}};
           const float2 al[4] = {{b01.x, b01.y}, {b01.z, b01.w}, {b23.x, b23.y}, {b23.z, b23.w}};
           const float2 ac[7] = {{c01.x, c01.y}, {c01.z, c01.w}, {c23.x, c23.y}, {c23.z, c23.w},
@@ -149,7 +181,13 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
               ai[a * 4 + b] = fmaf(py, c.x, fmaf(-px, c.y, ai[a * 4 + b]));
             }
           }
+        };
+        int j = 0;
+        for (; j + 1 < nf; j += 2) {
+          frame(j, oA0, oA1, oB0, oB1);
+          frame(j + 1, oA0o, oA1o, oB0o, oB1o);
         }
+        if (j < nf) frame(j, oA0, oA1, oB0, oB1);
         if (ch == nch - 1) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
@@ -165,9 +203,8 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
       // every thread is done with stage s; a failed wait anywhere stops the CTA
       if (__syncthreads_or(!ok)) {
         if (use_tma)  // drain copies still in flight before giving up
-          for (int r = i + 1; r < nsteps && r < i + kStages; ++r)
-            mbar_wait_bounded(&full[(qbase + r) % kStages], ((qbase + r) / kStages) & 1u, status);
-        aborted = true;
+          for (int q = i + 1; q < nsteps && q < i + kStages; ++q)
+            mbar_wait_bounded(&full[(qbase + q) % kStages], ((qbase + q) / kStages) & 1u, status);
         return;
       }
       if (use_tma && tid == 0 && i + kStages < nsteps) {
@@ -176,7 +213,7 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
       }
     }
     if (use_tma) qbase += nsteps;
-    if (!active) return;
+    if (!active) continue;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
 #pragma unroll
@@ -191,19 +228,19 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
         atomicAdd(acc + 3 * plane + o, (double)qi[q]);
       }
     }
-  });
+  }
 }
 
 }  // namespace
 
-size_t k2_smem_bytes(int FC) { return (size_t)kStages * FC * 4 * kTile * sizeof(float2) + 128; }
+size_t k2_smem_bytes(int FC) { return (size_t)kStages * stage_bytes(FC) + 1024; }
 
 cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
                              const float2* spec_a, const float2* spec_b, const float2* spec_c,
                              int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
                              const TileInfo* tiles, int n_tiles, int cross, float pref3,
-                             double* acc, long long plane, int rows, int nsm, int* status,
-                             cudaStream_t stream) {
+                             double* acc, long long plane, int rows, int nsm, int* counter,
+                             int* status, cudaStream_t stream) {
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
   const size_t smem = k2_smem_bytes(FC);
   cudaError_t e = cudaFuncSetAttribute(k2_bispec, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -213,9 +250,16 @@ cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_bispec, kThreadsPair, smem);
   if (e != cudaSuccess) return e;
   const int n_cta = nsm * (occ > 0 ? occ : 1);
+  WorkQueue wq;
+  wq.counter = counter;
+  wq.n_tiles = n_tiles;
+  wq.group_chunk = work_group_chunk(G, n_tiles, n_cta);
+  wq.n_items = n_tiles * ((G + wq.group_chunk - 1) / wq.group_chunk);
+  e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
   const int koff = (rows == M) ? 0 : (M - 1);
   k2_bispec<<<n_cta, kThreadsPair, smem, stream>>>(tm64, tm128, spec_a, spec_b, spec_c, rowA,
-                                                   rowB, rowC, G, m, FC, M, Mp, tiles, n_tiles,
+                                                   rowB, rowC, G, m, FC, M, Mp, tiles, wq,
                                                    cross, pref3, acc, plane, koff, status);
   return cudaGetLastError();
 }

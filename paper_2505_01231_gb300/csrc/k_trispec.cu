@@ -15,11 +15,12 @@
 // and its sum of squares over groups are accumulated (Eq. 35-36).
 //
 // This is the plain FP32 CUDA-core form of the fourth-order moment sums: five
-// length-m dot products per grid point and group.  Work split as in K2: a
-// persistent CTA walks balanced (64 x 64 tile of the upper triangle k <= l,
-// group range) segments; chunks of FC frames of the coefficients at k0.. and
-// l0.. arrive by 2-D TMA box loads into kStages shared-memory stages, |da|^2 is
-// formed once per staged chunk, and each thread evaluates a 4 x 4 micro-tile.
+// length-m dot products per grid point and group.  Work split as in K2:
+// persistent CTAs take (group chunk, 64 x 64 tile of the upper triangle k <= l)
+// items from a group-major queue; chunks of FC frames of the coefficients at
+// k0.. and l0.. arrive by 128-byte-swizzled 3-D TMA box loads into kStages
+// shared-memory stages, |da|^2 is formed once per staged chunk, and each thread
+// evaluates a 4 x 4 micro-tile (quarter-warps of 4 k-threads x 2 l-threads).
 #include "internal.cuh"
 #include "pipeline.cuh"
 
@@ -28,22 +29,36 @@ namespace {
 
 constexpr int kStages = 4;
 
+__host__ __device__ __forceinline__ uint32_t arr64_bytes(int FC) {
+  return ((uint32_t)FC * 512u + 1023u) & ~1023u;
+}
+
+__device__ __forceinline__ float4 lds128(const void* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+
 __global__ void __launch_bounds__(kThreadsPair, 1)
 k3_trispec(const __grid_constant__ CUtensorMap tm64, int row0, int G, int m, int FC, int M,
-           const TileInfo* __restrict__ tiles, int n_tiles, float pref_a, float pref_b,
+           const TileInfo* __restrict__ tiles, WorkQueue wq, float pref_a, float pref_b,
            double* __restrict__ acc, long long plane, int* __restrict__ status) {
-  extern __shared__ __align__(128) float4 smem_raw[];  // + 128 spare bytes for alignment
+  extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
   __shared__ __align__(8) uint64_t full[kStages];
-  float2* sbase = align128<float2>(smem_raw);   // kStages x [2][FC][64] float2
-  const int stage_elems = 2 * FC * kTile;
-  float* pA = reinterpret_cast<float*>(sbase + kStages * stage_elems);  // [FC][64]
-  float* pB = pA + FC * kTile;                                           // [FC][64]
+  __shared__ int s_item;
+  unsigned char* sbase = align1024<unsigned char>(smem_raw);
+  const uint32_t a64 = arr64_bytes(FC), sbytes = 2 * a64;   // stage: [FC][64] at k, at l
+  float* pA = reinterpret_cast<float*>(sbase + kStages * sbytes);  // [FC][64] |da_k|^2
+  float* pB = pA + FC * kTile;                                      // [FC][64] |da_l|^2
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int tx = (warp & 1) * 8 + (lane & 7);
-  const int ty = (warp >> 1) * 4 + (lane >> 3);
+  const int qw = lane >> 3, r8 = lane & 7;
+  const int tx = (warp & 1) * 8 + (r8 & 3) + 4 * (qw & 1);
+  const int ty = (warp >> 1) * 4 + (r8 >> 2) + 2 * (qw >> 1);
   const int kt = 4 * tx, lt = 4 * ty;
   const int nch = (m + FC - 1) / FC;
+  const uint32_t oA0 = swz128(kt * 8), oA1 = swz128(kt * 8 + 16);
+  const uint32_t oA0o = swz128(512 + kt * 8), oA1o = swz128(512 + kt * 8 + 16);
+  const uint32_t oB0 = swz128(lt * 8), oB1 = swz128(lt * 8 + 16);
+  const uint32_t oB0o = swz128(512 + lt * 8), oB1o = swz128(512 + lt * 8 + 16);
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
@@ -52,10 +67,11 @@ k3_trispec(const __grid_constant__ CUtensorMap tm64, int row0, int G, int m, int
   fence_async_smem();
   __syncthreads();
   uint32_t qbase = 0;
-  bool aborted = false;
 
-  for_each_segment(tiles, n_tiles, G, blockIdx.x, gridDim.x, [&](int t, int ga, int gb) {
-    if (aborted) return;
+  for (int item; (item = next_item(wq, &s_item)) >= 0;) {
+    const int t = item % wq.n_tiles;
+    const int ga = (item / wq.n_tiles) * wq.group_chunk;
+    const int gb = min(G, ga + wq.group_chunk);
     const int k0 = tiles[t].k0, l0 = tiles[t].l0;
     const int kw = k0 + 32 * (warp & 1), lw = l0 + 16 * (warp >> 1);
     const bool active = (kw <= lw + 15) && (lw < M) && (kw < M);
@@ -63,10 +79,10 @@ k3_trispec(const __grid_constant__ CUtensorMap tm64, int row0, int G, int m, int
     auto issue = [&](int i) {
       const int s = (int)((qbase + i) % kStages);
       const int g = ga + i / nch, j0 = (i % nch) * FC;
-      float2* st = sbase + (size_t)s * stage_elems;
-      mbar_arrive_expect_tx(&full[s], (uint32_t)(stage_elems * sizeof(float2)));
-      tma_load_2d(st, &tm64, k0, row0 + g * m + j0, &full[s]);
-      tma_load_2d(st + FC * kTile, &tm64, l0, row0 + g * m + j0, &full[s]);
+      unsigned char* st = sbase + (size_t)s * sbytes;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)FC * 128u * 8u);
+      tma_load_3d(st, &tm64, 0, k0 >> 4, row0 + g * m + j0, &full[s]);
+      tma_load_3d(st + a64, &tm64, 0, l0 >> 4, row0 + g * m + j0, &full[s]);
     };
 
     float sum[16], sq[16], q[16], rr[16], ii[16], xx[16], xt[16], sk[4], sl[4];
@@ -82,23 +98,25 @@ k3_trispec(const __grid_constant__ CUtensorMap tm64, int row0, int G, int m, int
       const int ch = i % nch;
       const int nf = min(FC, m - ch * FC);
       const int s = (int)((qbase + i) % kStages);
-      const float2* sA = sbase + (size_t)s * stage_elems;
-      const float2* sB = sA + FC * kTile;
+      const unsigned char* sA = sbase + (size_t)s * sbytes;
+      const unsigned char* sB = sA + a64;
       const bool ok = mbar_wait_bounded(&full[s], ((qbase + i) / kStages) & 1u, status);
       for (int e = tid; e < 2 * FC * kTile; e += blockDim.x) {
-        const float2 v = sA[e];  // sA and sB are contiguous: [2][FC][64]
-        const float p = fmaf(v.x, v.x, v.y * v.y);
-        if (e < FC * kTile) pA[e] = p; else pB[e - FC * kTile] = p;
+        const int arr = e >= FC * kTile;
+        const int rem = e - arr * FC * kTile;
+        const int j = rem >> 6, bin = rem & 63;
+        const float2 v = *reinterpret_cast<const float2*>(sA + arr * a64 + swz128(j * 512 + bin * 8));
+        (arr ? pB : pA)[rem] = fmaf(v.x, v.x, v.y * v.y);
       }
       __syncthreads();
       if (active) {
-#pragma unroll 2
-        for (int j = 0; j < nf; ++j) {
-          const float4* a4 = reinterpret_cast<const float4*>(sA + j * kTile + kt);
-          const float4* b4 = reinterpret_cast<const float4*>(sB + j * kTile + lt);
-          const float4 a01 = a4[0], a23 = a4[1], b01 = b4[0], b23 = b4[1];
-          const float4 pk4 = *reinterpret_cast<const float4*>(pA + j * kTile + kt);
-          const float4 pl4 = *reinterpret_cast<const float4*>(pB + j * kTile + lt);
+        auto frame = [&](int j, uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1) {
+          const unsigned char* pa = sA + (j & ~1) * 512;
+          const unsigned char* pb = sB + (j & ~1) * 512;
+          const float4 a01 = lds128(pa + a0), a23 = lds128(pa + a1);
+          const float4 b01 = lds128(pb + b0), b23 = lds128(pb + b1);
+          const float4 pk4 = lds128(pA + j * kTile + kt);
+          const float4 pl4 = lds128(pB + j * kTile + lt);
           const float2 ak[4] = {{a01.x, a01.y}, {a01.z, a01.w}, {a23.x, a23.y}, {a23.z, a23.w}};
           const float2 al[4] = {{b01.x, b01.y}, {b01.z, b01.w}, {b23.x, b23.y}, {b23.z, b23.w}};
           const float pk[4] = {pk4.x, pk4.y, pk4.z, pk4.w};
@@ -120,7 +138,13 @@ k3_trispec(const __grid_constant__ CUtensorMap tm64, int row0, int G, int m, int
               xt[r] = fmaf(ak[a].y, al[b].x, xt[r]);
             }
           }
+        };
+        int j = 0;
+        for (; j + 1 < nf; j += 2) {
+          frame(j, oA0, oA1, oB0, oB1);
+          frame(j + 1, oA0o, oA1o, oB0o, oB1o);
         }
+        if (j < nf) frame(j, oA0, oA1, oB0, oB1);
         if (ch == nch - 1) {
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
@@ -144,7 +168,6 @@ k3_trispec(const __grid_constant__ CUtensorMap tm64, int row0, int G, int m, int
       if (__syncthreads_or(!ok)) {
         for (int r = i + 1; r < nsteps && r < i + kStages; ++r)
           mbar_wait_bounded(&full[(qbase + r) % kStages], ((qbase + r) / kStages) & 1u, status);
-        aborted = true;
         return;
       }
       if (tid == 0 && i + kStages < nsteps) {
@@ -153,7 +176,7 @@ k3_trispec(const __grid_constant__ CUtensorMap tm64, int row0, int G, int m, int
       }
     }
     qbase += nsteps;
-    if (!active) return;
+    if (!active) continue;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
 #pragma unroll
@@ -165,19 +188,18 @@ k3_trispec(const __grid_constant__ CUtensorMap tm64, int row0, int G, int m, int
         atomicAdd(acc + 2 * plane + o, (double)sq[a * 4 + b]);
       }
     }
-  });
+  }
 }
 
 }  // namespace
 
 size_t k3_smem_bytes(int FC) {
-  return (size_t)kStages * 2 * FC * kTile * sizeof(float2) + (size_t)2 * FC * kTile * sizeof(float) +
-         128;
+  return (size_t)kStages * 2 * arr64_bytes(FC) + (size_t)2 * FC * kTile * sizeof(float) + 1024;
 }
 
 cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, int FC, int M,
                               const TileInfo* tiles, int n_tiles, float pref4a, float pref4b,
-                              double* acc, long long plane, int nsm, int* status,
+                              double* acc, long long plane, int nsm, int* counter, int* status,
                               cudaStream_t stream) {
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
   const size_t smem = k3_smem_bytes(FC);
@@ -188,8 +210,15 @@ cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, i
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_trispec, kThreadsPair, smem);
   if (e != cudaSuccess) return e;
   const int n_cta = nsm * (occ > 0 ? occ : 1);
-  k3_trispec<<<n_cta, kThreadsPair, smem, stream>>>(tm64, row0, G, m, FC, M, tiles, n_tiles,
-                                                    pref4a, pref4b, acc, plane, status);
+  WorkQueue wq;
+  wq.counter = counter;
+  wq.n_tiles = n_tiles;
+  wq.group_chunk = work_group_chunk(G, n_tiles, n_cta);
+  wq.n_items = n_tiles * ((G + wq.group_chunk - 1) / wq.group_chunk);
+  e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  k3_trispec<<<n_cta, kThreadsPair, smem, stream>>>(tm64, row0, G, m, FC, M, tiles, wq, pref4a,
+                                                    pref4b, acc, plane, status);
   return cudaGetLastError();
 }
 

@@ -19,12 +19,12 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// First 128-byte aligned address at or after p in shared memory (tiled TMA
-// destinations need 128-byte alignment; kernels reserve 128 spare bytes).
+// First 1024-byte aligned address at or after p in shared memory (destinations
+// of 128-byte-swizzled TMA loads; kernels reserve 1024 spare bytes).
 template <typename T>
-__device__ __forceinline__ T* align128(void* p) {
+__device__ __forceinline__ T* align1024(void* p) {
   const uint32_t a = smem_addr(p);
-  return reinterpret_cast<T*>(static_cast<char*>(p) + ((128u - (a & 127u)) & 127u));
+  return reinterpret_cast<T*>(static_cast<char*>(p) + ((1024u - (a & 1023u)) & 1023u));
 }
 
 __device__ __forceinline__ unsigned long long global_timer_ns() {
@@ -76,6 +76,23 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// 3-D tiled TMA load (coordinates {x, y, z}).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Byte offset, inside a 1024-byte aligned shared buffer written by a TMA load
+// with 128-byte swizzling, of the 16-byte chunk holding logical offset `off`:
+// the chunk index (bits 4-6) is XOR-ed with the 128-byte row index (bits 7-9).
+__device__ __forceinline__ uint32_t swz128(uint32_t off) {
+  return off ^ (((off >> 7) & 7u) << 4);
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -102,42 +119,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// Scheduling cost of one (tile, group) unit: the warps of the CTA whose
-// sub-tile touches the domain, plus a fixed part for staging and barriers that
-// every group pays whatever the tile's shape.
-constexpr int kTileFixedCost = 3;
-
-// Work description of one tile of (k, l) grid points: origin and per-group
-// weight (number of warps of the CTA whose sub-tile touches the domain).
-// `prefix` is the sum of the weights of all earlier tiles.
+// Work description of one tile of (k, l) grid points: its origin and how many
+// of the CTA's eight 32 x 16 warp sub-tiles touch the domain.
 struct TileInfo {
-  int k0, l0, weight, prefix;
+  int k0, l0, active_warps, pad;
 };
 
-// Balanced static schedule: the work units are (tile t, group g) with weight
-// w_t each, laid out tile-major; CTA c of n takes the weight range
-// [c W / n, (c+1) W / n).  Group g of tile t belongs to the CTA whose range holds
-// the unit's first weight position P_t G + g w_t, so every unit is taken once.
-// Calls f(tile_index, g_begin, g_end) for each tile segment of the CTA's range.
-template <typename F>
-__device__ __forceinline__ void for_each_segment(const TileInfo* __restrict__ tiles, int n_tiles,
-                                                 int G, int cta, int n_cta, F&& f) {
-  const long long total_w = (long long)(tiles[n_tiles - 1].prefix + tiles[n_tiles - 1].weight) * G;
-  const long long x0 = total_w * cta / n_cta;
-  const long long x1 = total_w * (cta + 1) / n_cta;
-  for (int t = 0; t < n_tiles; ++t) {
-    const long long w = tiles[t].weight;
-    if (w == 0) continue;
-    const long long p0 = (long long)tiles[t].prefix * G;
-    const long long p1 = p0 + w * G;
-    if (p1 <= x0) continue;
-    if (p0 >= x1) break;
-    const long long a = x0 > p0 ? x0 - p0 : 0;
-    const long long b = (x1 < p1 ? x1 : p1) - p0;
-    const int ga = (int)((a + w - 1) / w);
-    const int gb = (int)((b + w - 1) / w);
-    if (gb > ga) f(t, ga, gb);
-  }
+// Dynamic work queue of the persistent pair kernels.  Item i is (group chunk
+// i / n_tiles, tile i % n_tiles): group-major, so the CTAs working at the same
+// time share one chunk of centred spectra in L2.  A CTA takes the next item
+// with one atomicAdd on a counter that the host zeroes before the launch.
+struct WorkQueue {
+  int* counter;
+  int n_tiles;
+  int group_chunk;
+  int n_items;
+};
+
+// Returns the next item for the calling CTA (all threads receive it) or -1.
+__device__ __forceinline__ int next_item(const WorkQueue& q, int* s_slot) {
+  __syncthreads();  // the previous item's readers of *s_slot are done
+  if (threadIdx.x == 0) *s_slot = atomicAdd(q.counter, 1);
+  __syncthreads();
+  const int it = *s_slot;
+  return it < q.n_items ? it : -1;
 }
 
 }  // namespace ss

@@ -78,8 +78,9 @@ struct ss_plan_s {
   int n_s2cross = 0;
   TileInfo *d_tiles3 = nullptr, *d_tiles4 = nullptr;
   int* d_status = nullptr;
+  int* d_counter = nullptr;        // work-queue counter of the pair kernels
   int FC = 0;                      // frames per staged chunk of the pair kernels
-  CUtensorMap tm64{}, tm128{};     // 2-D views [rows = C*Gb_max*m][M] of the spectra
+  CUtensorMap tm64{}, tm128{};     // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
   int n_tiles3 = 0, n_tiles4 = 0;
   long long pairs3 = 0, pairs4 = 0;
   void* d_stage[2] = {nullptr, nullptr};
@@ -165,10 +166,8 @@ bool in_domain3(int k, int l, int M, bool cross) {
   return k >= 0 && k <= l && k + l < M;
 }
 
-// Tiles of 64 x 64 grid points that touch the domain, each weighted by the
-// number of its 32 x 16 warp sub-tiles that touch the domain (the kernels skip
-// the others) plus the fixed per-group cost, with prefix sums for the balanced
-// schedule.
+// Tiles of 64 x 64 grid points that touch the domain, with the number of
+// their 32 x 16 warp sub-tiles that touch it (the kernels skip the others).
 void build_tiles(ss_plan_s* p, std::vector<TileInfo>& t3, std::vector<TileInfo>& t4) {
   const int M = p->M;
   const bool cross = p->C > 1;
@@ -193,16 +192,9 @@ void build_tiles(ss_plan_s* p, std::vector<TileInfo>& t3, std::vector<TileInfo>&
   for (int k0 = kmin; k0 < M; k0 += kTile)
     for (int l0 = 0; l0 < M; l0 += kTile) {
       const int w3 = warps(k0, l0, dom3), w4 = warps(k0, l0, dom4);
-      if (w3) t3.push_back(TileInfo{k0, l0, w3 + kTileFixedCost, 0});
-      if (w4) t4.push_back(TileInfo{k0, l0, w4 + kTileFixedCost, 0});
+      if (w3) t3.push_back(TileInfo{k0, l0, w3, 0});
+      if (w4) t4.push_back(TileInfo{k0, l0, w4, 0});
     }
-  for (auto* v : {&t3, &t4}) {
-    int acc = 0;
-    for (TileInfo& t : *v) {
-      t.prefix = acc;
-      acc += t.weight;
-    }
-  }
   for (int k = -(M - 1); k < M; ++k)
     for (int l = 0; l < M; ++l) {
       if (dom3(k, l)) ++p->pairs3;
@@ -282,7 +274,7 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
                                      p->FC, p->M, p->Mp, p->d_tiles3, p->n_tiles3,
                                      p->C > 1 ? 1 : 0, pref3,
                                      p->d_acc3 + (long long)i * p->rows3 * p->M, plane, p->rows3,
-                                     p->nsm, p->d_status, p->stream));
+                                     p->nsm, p->d_counter, p->d_status, p->stream));
         }
         record(p, 1, p->stream, false);
       }
@@ -294,7 +286,7 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
           SS_TRY(p, launch_k3_trispec(p->tm64, cb.c[0] * p->Gb_max * p->m, cnt, p->m, p->FC,
                                       p->M, p->d_tiles4, p->n_tiles4, pref4a, pref4b,
                                       p->d_acc4 + (long long)i * p->rows4 * p->M, plane, p->nsm,
-                                      p->d_status, p->stream));
+                                      p->d_counter, p->d_status, p->stream));
         }
         record(p, 2, p->stream, false);
       }
@@ -386,9 +378,10 @@ ss_status zero_state(ss_plan_s* p) {
   return SS_OK;
 }
 
-// 2-D tensor maps over the centred spectra, one row per frame: element (x, y)
-// is bin x of frame row y (rows of channel c start at c * Gb_max * m); boxes of
-// FC rows by 64 or 128 bins; bins >= M read as zero.
+// 3-D tensor maps over the centred spectra: element (x, y, z) is bin 16 y + x of
+// frame row z (rows of channel c start at c * Gb_max * m).  Boxes are 16 bins x
+// 4 or 8 blocks x FC rows, written to shared memory with 128-byte swizzling;
+// blocks past the row read as zero.
 ss_status encode_maps(ss_plan_s* p) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -401,14 +394,14 @@ ss_status encode_maps(ss_plan_s* p) {
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   const cuuint64_t rows = (cuuint64_t)p->C * p->Gb_max * p->m;
-  const cuuint64_t dims[2] = {(cuuint64_t)p->M, rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)p->Mp * sizeof(float2)};
-  const cuuint32_t estr[2] = {1, 1};
-  for (int w : {64, 128}) {
-    const cuuint32_t box[2] = {(cuuint32_t)w, (cuuint32_t)p->FC};
-    CUresult r = encode(w == 64 ? &p->tm64 : &p->tm128, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+  const cuuint64_t dims[3] = {16, (cuuint64_t)p->Mp / 16, rows};
+  const cuuint64_t strides[2] = {16 * sizeof(float2), (cuuint64_t)p->Mp * sizeof(float2)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int blocks : {4, 8}) {
+    const cuuint32_t box[3] = {16, (cuuint32_t)blocks, (cuuint32_t)p->FC};
+    CUresult r = encode(blocks == 4 ? &p->tm64 : &p->tm128, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
                         p->d_spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
       return fail(p, SS_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string(r));
@@ -461,6 +454,7 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_tiles3);
   cudaFree(p->d_tiles4);
   cudaFree(p->d_status);
+  cudaFree(p->d_counter);
   cudaFree(p->d_out);
   delete p;
 }
@@ -502,7 +496,7 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   p->C = channels;
   p->T = T;
   p->M = T / 2 + 1;
-  p->Mp = (p->M + 3) & ~3;
+  p->Mp = (p->M + 15) & ~15;  // whole 128-byte blocks of 16 bins per row
   p->m = m;
   p->dt = dt;
   p->window = window;
@@ -623,6 +617,7 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   if (!t3.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles3, t3.size() * sizeof(TileInfo)));
   if (!t4.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4, t4.size() * sizeof(TileInfo)));
   PLAN_TRY(dev_alloc(p, &p->d_status, sizeof(int)));
+  PLAN_TRY(dev_alloc(p, &p->d_counter, sizeof(int)));
   PLAN_TRY(cudaMemcpy(p->d_win, gw.data(), T * sizeof(float), cudaMemcpyHostToDevice));
   PLAN_TRY(cudaMemcpy(p->d_tw, tw.data(), T * sizeof(float2), cudaMemcpyHostToDevice));
   PLAN_TRY(cudaMemcpy(p->d_s2auto, s2auto.data(), channels * sizeof(int),
