@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--ref-groups", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3", "bf16"],
+                    help="arithmetic of the S4 moment sums")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     rank, world, local = dist_env()
@@ -240,7 +242,8 @@ def main():
     n = z.shape[-1]
     T, m, C = w["T"], w["m"], w["channels"]
     stream = torch.cuda.current_stream()
-    plan = P.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4), stream=stream)
+    plan = P.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4), stream=stream,
+                  precision=args.precision)
     info = P.ss_query(plan.handle)
     dz = torch.from_numpy(z).cuda()
     sh = plan.shapes()
@@ -363,7 +366,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "channels": C, "samples_per_rank": n, "T": T,
                        "M": T // 2 + 1, "m": m, "groups": groups, "window": "hann",
-                       "orders": "S2+S3+S4 full grids", "s4_precision": "fp32",
+                       "orders": "S2+S3+S4 full grids", "s4_precision": args.precision,
                        "l2": "record of 1 GiB per step is larger than L2; no flush"},
             "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
             "cpu_baseline": cpu, "clocks": clock_info,

@@ -76,6 +76,16 @@ cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, i
                               double* acc, long long plane, int nsm, int* counter, int* status,
                               cudaStream_t stream);
 
+// Tensor-core form of K3 (SS_PREC_TF32X3, SS_PREC_BF16X3, SS_PREC_BF16): tiles of
+// 128 k-bins x 48 l-bins; tm128 / tm48 are the spectra views with boxes of 8 and
+// 3 blocks of 16 bins.
+constexpr int kTcTileM = 128, kTcTileN = 48;
+cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm128, const CUtensorMap& tm48, int row0,
+                                 int G, int m, int FC, int M, const TileInfo* tiles, int n_tiles,
+                                 int precision, double* acc, long long plane, int nsm,
+                                 int* counter, int* status, cudaStream_t stream);
+size_t k3tc_smem_bytes(int FC, int precision);
+
 // Groups per work item: about 16 items per CTA, whole groups, at least one.
 inline int work_group_chunk(int G, int n_tiles, int n_cta) {
   const long long units = (long long)G * n_tiles;

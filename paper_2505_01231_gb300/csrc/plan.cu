@@ -80,7 +80,9 @@ struct ss_plan_s {
   int* d_status = nullptr;
   int* d_counter = nullptr;        // work-queue counter of the pair kernels
   int FC = 0;                      // frames per staged chunk of the pair kernels
-  CUtensorMap tm64{}, tm128{};     // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
+  CUtensorMap tm64{}, tm128{}, tm48{};  // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
+  TileInfo* d_tiles4tc = nullptr;  // 128 x 48 tiles of the tensor-core S4 kernel
+  int n_tiles4tc = 0;
   int n_tiles3 = 0, n_tiles4 = 0;
   long long pairs3 = 0, pairs4 = 0;
   void* d_stage[2] = {nullptr, nullptr};
@@ -164,6 +166,16 @@ void default_combos(ss_plan_s* p) {
 bool in_domain3(int k, int l, int M, bool cross) {
   if (cross) return l >= 0 && l < M && k > -M && k < M && k + l < M && k + l > -M;
   return k >= 0 && k <= l && k + l < M;
+}
+
+// Tiles of 128 x 48 grid points of the tensor-core S4 kernel that touch the
+// upper triangle k <= l < M.
+std::vector<TileInfo> build_tc_tiles(int M) {
+  std::vector<TileInfo> t;
+  for (int k0 = 0; k0 < M; k0 += kTcTileM)
+    for (int l0 = 0; l0 < M; l0 += kTcTileN)
+      if (k0 <= l0 + kTcTileN - 1) t.push_back(TileInfo{k0, l0, 8, 0});
+  return t;
 }
 
 // Tiles of 64 x 64 grid points that touch the domain, with the number of
@@ -283,10 +295,17 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
         const long long plane = (long long)p->c4.size() * p->rows4 * p->M;
         for (size_t i = 0; i < p->c4.size(); ++i) {
           const Combo& cb = p->c4[i];
-          SS_TRY(p, launch_k3_trispec(p->tm64, cb.c[0] * p->Gb_max * p->m, cnt, p->m, p->FC,
-                                      p->M, p->d_tiles4, p->n_tiles4, pref4a, pref4b,
-                                      p->d_acc4 + (long long)i * p->rows4 * p->M, plane, p->nsm,
-                                      p->d_counter, p->d_status, p->stream));
+          if (p->precision == SS_PREC_FP32)
+            SS_TRY(p, launch_k3_trispec(p->tm64, cb.c[0] * p->Gb_max * p->m, cnt, p->m, p->FC,
+                                        p->M, p->d_tiles4, p->n_tiles4, pref4a, pref4b,
+                                        p->d_acc4 + (long long)i * p->rows4 * p->M, plane,
+                                        p->nsm, p->d_counter, p->d_status, p->stream));
+          else
+            SS_TRY(p, launch_k3_trispec_tc(p->tm128, p->tm48, cb.c[0] * p->Gb_max * p->m, cnt,
+                                           p->m, p->FC, p->M, p->d_tiles4tc, p->n_tiles4tc,
+                                           p->precision,
+                                           p->d_acc4 + (long long)i * p->rows4 * p->M, plane,
+                                           p->nsm, p->d_counter, p->d_status, p->stream));
         }
         record(p, 2, p->stream, false);
       }
@@ -397,9 +416,10 @@ ss_status encode_maps(ss_plan_s* p) {
   const cuuint64_t dims[3] = {16, (cuuint64_t)p->Mp / 16, rows};
   const cuuint64_t strides[2] = {16 * sizeof(float2), (cuuint64_t)p->Mp * sizeof(float2)};
   const cuuint32_t estr[3] = {1, 1, 1};
-  for (int blocks : {4, 8}) {
+  for (int blocks : {3, 4, 8}) {
     const cuuint32_t box[3] = {16, (cuuint32_t)blocks, (cuuint32_t)p->FC};
-    CUresult r = encode(blocks == 4 ? &p->tm64 : &p->tm128, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+    CUtensorMap* map = blocks == 3 ? &p->tm48 : blocks == 4 ? &p->tm64 : &p->tm128;
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
                         p->d_spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -453,6 +473,7 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_s2cross);
   cudaFree(p->d_tiles3);
   cudaFree(p->d_tiles4);
+  cudaFree(p->d_tiles4tc);
   cudaFree(p->d_status);
   cudaFree(p->d_counter);
   cudaFree(p->d_out);
@@ -530,10 +551,6 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   } else {
     default_combos(p);
   }
-  if (precision != SS_PREC_FP32 && !p->c4.empty()) {
-    delete p;
-    return fail(nullptr, SS_EUNSUPPORTED, "tensor-core S4 precisions are not built yet");
-  }
   for (const Combo& cb : p->c4)
     if (channels > 1 || cb.c[0] != cb.c[1] || cb.c[0] != cb.c[2] || cb.c[0] != cb.c[3]) {
       delete p;
@@ -588,6 +605,9 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   p->n_s2cross = (int)s2cross.size();
   std::vector<TileInfo> t3, t4;
   build_tiles(p, t3, t4);
+  std::vector<TileInfo> t4tc;
+  if (!p->c4.empty() && precision != SS_PREC_FP32) t4tc = build_tc_tiles(p->M);
+  p->n_tiles4tc = (int)t4tc.size();
   if (p->c3.empty()) t3.clear();
   if (p->c4.empty()) t4.clear();
   p->n_tiles3 = (int)t3.size();
@@ -616,6 +636,7 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   if (p->n_acc4) PLAN_TRY(dev_alloc(p, &p->d_acc4, p->n_acc4 * sizeof(double)));
   if (!t3.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles3, t3.size() * sizeof(TileInfo)));
   if (!t4.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4, t4.size() * sizeof(TileInfo)));
+  if (!t4tc.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4tc, t4tc.size() * sizeof(TileInfo)));
   PLAN_TRY(dev_alloc(p, &p->d_status, sizeof(int)));
   PLAN_TRY(dev_alloc(p, &p->d_counter, sizeof(int)));
   PLAN_TRY(cudaMemcpy(p->d_win, gw.data(), T * sizeof(float), cudaMemcpyHostToDevice));
@@ -630,6 +651,9 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
                         cudaMemcpyHostToDevice));
   if (!t4.empty())
     PLAN_TRY(cudaMemcpy(p->d_tiles4, t4.data(), t4.size() * sizeof(TileInfo),
+                        cudaMemcpyHostToDevice));
+  if (!t4tc.empty())
+    PLAN_TRY(cudaMemcpy(p->d_tiles4tc, t4tc.data(), t4tc.size() * sizeof(TileInfo),
                         cudaMemcpyHostToDevice));
   st = alloc_spec(p);
   if (st != SS_OK) {

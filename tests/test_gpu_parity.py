@@ -22,10 +22,10 @@ def P():
 
 
 def run_gpu(z, T, m, dt=1.0, window="hann", sigma_t=0.14, orders=(2, 3, 4), chunks=None,
-            host=False, batch=0, dtype="f32", channels=1, combos=None):
+            host=False, batch=0, dtype="f32", channels=1, combos=None, precision="fp32"):
     mod = P()
     plan = mod.Plan(channels=channels, T=T, dt=dt, m=m, window=window, sigma_t=sigma_t,
-                    orders=orders, dtype=dtype, combos=combos)
+                    orders=orders, dtype=dtype, combos=combos, precision=precision)
     if batch:
         mod.ss_set_batch(plan.handle, batch)
     z = np.ascontiguousarray(z)
@@ -44,7 +44,7 @@ def run_gpu(z, T, m, dt=1.0, window="hann", sigma_t=0.14, orders=(2, 3, 4), chun
     return out
 
 
-def check(gpu, ref, key, tol=TOL):
+def check(gpu, ref, key, tol=TOL, tol_err=TOL_ERR):
     a, b = gpu[key].reshape(ref[key].shape), ref[key]
     scale = np.max(np.abs(b))
     err = np.max(np.abs(a - b)) / scale
@@ -52,17 +52,18 @@ def check(gpu, ref, key, tol=TOL):
     ea, eb = gpu[key + "_err"].reshape(ref[key + "_err"].shape), ref[key + "_err"]
     escale = np.max(np.abs(eb))
     eerr = np.max(np.abs(ea - eb)) / escale
-    assert eerr <= TOL_ERR, f"{key}_err: max rel err {eerr:.3e} > {TOL_ERR}"
+    assert eerr <= tol_err, f"{key}_err: max rel err {eerr:.3e} > {tol_err}"
     return err
 
 
-def compare_single(gpu, ref, orders=(2, 3, 4)):
+def compare_single(gpu, ref, orders=(2, 3, 4), tol4=TOL, tol4_err=TOL_ERR):
     assert gpu["G"] == ref["G"]
     errs = {}
     for n in orders:
         key = f"S{n}"
         g = {key: gpu[key][0], key + "_err": gpu[key + "_err"][0]}
-        errs[key] = check(g, ref, key)
+        errs[key] = check(g, ref, key, tol=tol4 if n == 4 else TOL,
+                          tol_err=tol4_err if n == 4 else TOL_ERR)
     return errs
 
 
@@ -89,6 +90,30 @@ def test_sizes_and_ragged_tails(T, m, G):
     ref = oracle.polyspectra(z, T, 0.25, m, group_chunk=8)
     gpu = run_gpu(z, T, m, dt=0.25)
     compare_single(gpu, ref)
+
+
+# tensor-core S4: TF32 3-pass split meets the FP32 bar; BF16 3-pass and plain
+# BF16 are held to the bars their operand precision allows (2^-17 and 2^-9 per
+# product before averaging)
+PREC_TOL = {"tf32x3": (TOL, TOL_ERR), "bf16x3": (5e-5, 5e-4), "bf16": (2e-2, 2e-1)}
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3", "bf16"])
+def test_config1_tensor_core_s4(c1_signal, precision):
+    ref = oracle.polyspectra(c1_signal, 256, 1.0, 10, orders=(4,), group_chunk=64)
+    gpu = run_gpu(c1_signal, 256, 10, orders=(4,), precision=precision)
+    tol, tol_err = PREC_TOL[precision]
+    errs = compare_single(gpu, ref, orders=(4,), tol4=tol, tol4_err=tol_err)
+    print(f"config-1 S4 {precision} max relative error", errs)
+
+
+@pytest.mark.parametrize("T,m,G", [(16, 4, 40), (64, 6, 30), (512, 10, 9), (128, 17, 10),
+                                   (64, 40, 6), (4096, 5, 3)])
+def test_tensor_core_s4_sizes(T, m, G):
+    z = synth.ar1_quadratic(T * m * G + 2 * T + 3, seed=T + 7 * m)
+    ref = oracle.polyspectra(z, T, 0.5, m, orders=(2, 4), group_chunk=8)
+    gpu = run_gpu(z, T, m, dt=0.5, orders=(2, 4), precision="tf32x3")
+    compare_single(gpu, ref, orders=(2, 4))
 
 
 def test_streaming_chunks_match_one_call(c1_signal):
