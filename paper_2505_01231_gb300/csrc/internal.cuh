@@ -46,11 +46,31 @@ struct Combo {
   int c[4];
 };
 
+// Optional second output of K1 for the tensor-core S4 kernel: per channel,
+// group and chunk of FC frames (zero-padded to 16), the hi/lo split of Re, Im
+// and |.|^2 of the centred coefficients, laid out as the tensor cores read
+// K-major operands: rows (bins) in groups of 8; for each row group the six
+// matrices (Re hi, Re lo, Im hi, Im lo, P hi, P lo) of `CB` bytes each, where a
+// matrix holds the row group's core matrices (8 rows x 16 bytes) for
+// consecutive 16-byte frame groups, 128 bytes apart (TF32: 4 frame groups,
+// CB = 512; BF16: 2, CB = 256).  ps holds sum_j |.|^2 / sqrt 2 per bin.
+enum { kImageNone = 0, kImageTF32 = 1, kImageBF16 = 2 };
+struct OperandImage {
+  void* img = nullptr;
+  float* ps = nullptr;
+  int fmt = kImageNone;
+  int FC = 0, nch = 0;
+  long long chunk_bytes = 0;  // (Mp / 8) * 6 * CB
+  long long chan_bytes = 0;   // Gb_max * nch * chunk_bytes
+  long long chan_ps = 0;      // Gb_max * Mp floats
+};
+
 // Kernel launchers (each returns the launch status; all work on `stream`).
 cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G, int C, int T,
                               int m, int M, int Mp, const float* win, const float2* tw,
                               float2* spec, long long spec_chan_stride, const int* s2_auto,
-                              double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream);
+                              double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream,
+                              const OperandImage& oi = OperandImage());
 
 cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G, int m, int M,
                                int Mp, const int4* pairs, int n_pairs, float pref2, double* acc2,
@@ -77,14 +97,13 @@ cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, i
                               cudaStream_t stream);
 
 // Tensor-core form of K3 (SS_PREC_TF32X3, SS_PREC_BF16X3, SS_PREC_BF16): tiles of
-// 128 k-bins x 48 l-bins; tm128 / tm48 are the spectra views with boxes of 8 and
-// 3 blocks of 16 bins.
+// 128 k-bins x 48 l-bins fed from K1's operand image of `channel`.
 constexpr int kTcTileM = 128, kTcTileN = 48;
-cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm128, const CUtensorMap& tm48, int row0,
-                                 int G, int m, int FC, int M, const TileInfo* tiles, int n_tiles,
-                                 int precision, double* acc, long long plane, int nsm,
-                                 int* counter, int* status, cudaStream_t stream);
-size_t k3tc_smem_bytes(int FC, int precision);
+cudaError_t launch_k3_trispec_tc(const OperandImage& oi, int channel, int G, int m, int M, int Mp,
+                                 const TileInfo* tiles, int n_tiles, int precision, double* acc,
+                                 long long plane, int nsm, int* counter, int* status,
+                                 cudaStream_t stream);
+size_t k3tc_smem_bytes(int precision);
 
 // Groups per work item: about 16 items per CTA, whole groups, at least one.
 inline int work_group_chunk(int G, int n_tiles, int n_cta) {

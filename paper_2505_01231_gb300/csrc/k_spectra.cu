@@ -14,6 +14,8 @@
 // samples of the factorised k-statistics, App. H, Eq. 85), and forms the
 // per-group S2 estimate c2 = 1/(m-1) sum_j |dX_jk|^2 (Eq. 32 with y = x*),
 // whose sum and sum of squares over groups are accumulated for Eq. 35-36.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "internal.cuh"
@@ -96,6 +98,76 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ x, floa
   }
 }
 
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t t;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+  return t;
+}
+
+// Write one bin's row of one frame chunk (16 frames, zero-padded) of the
+// operand image: the hi and lo parts of Re, Im and |.|^2 of the centred
+// coefficients in the K-major core-matrix layout the tensor cores read
+// (8 rows x 16 bytes per core matrix, frame groups of 16 bytes 128 bytes apart).
+template <int FMT>
+__device__ __forceinline__ void write_image_row(unsigned char* base, int k, const float (&re)[16],
+                                                const float (&im)[16]) {
+  constexpr uint32_t CB = FMT == kImageTF32 ? 512u : 256u;
+  unsigned char* row = base + (size_t)(k >> 3) * 6 * CB + (k & 7) * 16;
+  if constexpr (FMT == kImageTF32) {
+#pragma unroll
+    for (int kg = 0; kg < 4; ++kg) {
+      uint32_t w[6][4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float x = re[4 * kg + e], y = im[4 * kg + e];
+        const float p = fmaf(x, x, y * y);
+        w[0][e] = to_tf32(x);
+        w[1][e] = to_tf32(x - __uint_as_float(w[0][e]));
+        w[2][e] = to_tf32(y);
+        w[3][e] = to_tf32(y - __uint_as_float(w[2][e]));
+        w[4][e] = to_tf32(p);
+        w[5][e] = to_tf32(p - __uint_as_float(w[4][e]));
+      }
+#pragma unroll
+      for (int mt = 0; mt < 6; ++mt)
+        *reinterpret_cast<uint4*>(row + mt * CB + kg * 128) =
+            make_uint4(w[mt][0], w[mt][1], w[mt][2], w[mt][3]);
+    }
+  } else {
+#pragma unroll
+    for (int kg = 0; kg < 2; ++kg) {
+      uint32_t w[6][4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        uint32_t hh[6], ll[6];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const float x = re[8 * kg + e + u], y = im[8 * kg + e + u];
+          const float v[3] = {x, y, fmaf(x, x, y * y)};
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v[q]);
+            const __nv_bfloat16 l = __float2bfloat16_rn(v[q] - __bfloat162float(h));
+            if (u == 0) {
+              hh[2 * q] = __bfloat16_as_ushort(h);
+              hh[2 * q + 1] = __bfloat16_as_ushort(l);
+            } else {
+              ll[2 * q] = __bfloat16_as_ushort(h);
+              ll[2 * q + 1] = __bfloat16_as_ushort(l);
+            }
+          }
+        }
+#pragma unroll
+        for (int mt = 0; mt < 6; ++mt) w[mt][e / 2] = hh[mt] | (ll[mt] << 16);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 6; ++mt)
+        *reinterpret_cast<uint4*>(row + mt * CB + kg * 128) =
+            make_uint4(w[mt][0], w[mt][1], w[mt][2], w[mt][3]);
+    }
+  }
+}
+
 template <int DTYPE>
 __device__ __forceinline__ float load_sample(const SampleSource& s, int c, long long idx) {
   if (idx < s.carry_n) {
@@ -108,12 +180,12 @@ __device__ __forceinline__ float load_sample(const SampleSource& s, int c, long 
   return (float)__ldg(static_cast<const short*>(s.chunk) + o);
 }
 
-template <int DTYPE>
+template <int DTYPE, int FMT>
 __global__ void __launch_bounds__(kThreadsK1)
 k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int M, int Mp,
            const float* __restrict__ win, const float2* __restrict__ tw,
            float2* __restrict__ spec, long long chan_stride, const int* __restrict__ s2_auto,
-           double* __restrict__ acc2, int n_s2, float pref2) {
+           double* __restrict__ acc2, int n_s2, float pref2, OperandImage oi) {
   extern __shared__ float4 smem_raw[];
   const int N = T / 2;
   float2* bufA = reinterpret_cast<float2*>(smem_raw);
@@ -168,23 +240,49 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
           gsum[k] = cadd(gsum[k], X);
         }
       }
-      // centre each bin over the group and form the per-group S2 estimate
+      // centre each bin over the group and form the per-group S2 estimate; with an
+      // operand image, also write the split tensor-core operands chunk by chunk
       const float inv_m = 1.0f / (float)m;
       const int ia = s2_auto[c];
+      const int nch = FMT != kImageNone ? oi.nch : 1;
+      const int FC = FMT != kImageNone ? oi.FC : m;
       for (int k = threadIdx.x; k < Mp; k += blockDim.x) {
-        if (k >= M) {
-          for (int j = 0; j < m; ++j) grow[(long long)j * Mp + k] = make_float2(0.f, 0.f);
-          continue;
-        }
-        const float2 mean = make_float2(gsum[k].x * inv_m, gsum[k].y * inv_m);
+        const bool valid = k < M;
+        const float2 mean = valid ? make_float2(gsum[k].x * inv_m, gsum[k].y * inv_m)
+                                  : make_float2(0.f, 0.f);
         float p = 0.f;
-        for (int j = 0; j < m; ++j) {
-          float2* e = grow + (long long)j * Mp + k;
-          const float2 d = csub(*e, mean);
-          *e = d;
-          p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+        if constexpr (FMT == kImageNone) {
+          for (int j = 0; j < m; ++j) {
+            float2* e = grow + (long long)j * Mp + k;
+            const float2 d = valid ? csub(*e, mean) : make_float2(0.f, 0.f);
+            *e = d;
+            p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+          }
+        } else {
+          for (int ch = 0; ch < nch; ++ch) {
+            const int j0 = ch * FC;
+            const int nfc = min(FC, m - j0);
+            float re[16], im[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              float2 d = make_float2(0.f, 0.f);
+              if (e < nfc) {
+                float2* ep = grow + (long long)(j0 + e) * Mp + k;
+                if (valid) d = csub(*ep, mean);
+                *ep = d;
+              }
+              re[e] = d.x;
+              im[e] = d.y;
+              p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+            }
+            unsigned char* base = static_cast<unsigned char*>(oi.img) +
+                                  (size_t)c * oi.chan_bytes +
+                                  ((size_t)g * nch + ch) * oi.chunk_bytes;
+            write_image_row<FMT>(base, k, re, im);
+          }
+          oi.ps[(long long)c * oi.chan_ps + (long long)g * Mp + k] = p * 0.70710678118654752f;
         }
-        if (ia >= 0) {
+        if (valid && ia >= 0) {
           const float c2 = p * pref2;
           s2sum[c * M + k] += c2;
           s2sq[c * M + k] = fmaf(c2, c2, s2sq[c * M + k]);
@@ -243,31 +341,54 @@ __global__ void k1_cross_s2(const float2* __restrict__ spec, long long chan_stri
 
 }  // namespace
 
+template <int DTYPE, int FMT>
+cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C, int T, int m,
+                        int M, int Mp, const float* win, const float2* tw, float2* spec,
+                        long long spec_chan_stride, const int* s2_auto, double* acc2, int n_s2,
+                        float pref2, const OperandImage& oi, int grid, size_t smem,
+                        cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(k1_spectra<DTYPE, FMT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k1_spectra<DTYPE, FMT><<<grid, kThreadsK1, smem, stream>>>(src, sample0, G, C, T, m, M, Mp, win,
+                                                             tw, spec, spec_chan_stride, s2_auto,
+                                                             acc2, n_s2, pref2, oi);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G, int C, int T,
                               int m, int M, int Mp, const float* win, const float2* tw,
                               float2* spec, long long spec_chan_stride, const int* s2_auto,
-                              double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream) {
+                              double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream,
+                              const OperandImage& oi) {
   if (G <= 0) return cudaSuccess;
   const size_t smem = (size_t)(T / 2) * 2 * sizeof(float2) + (size_t)M * sizeof(float2) +
                       (size_t)2 * C * M * sizeof(float);
   if (grid > G) grid = G;
-  cudaError_t e;
-  if (src.dtype == SS_F32) {
-    e = cudaFuncSetAttribute(k1_spectra<SS_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k1_spectra<SS_F32><<<grid, kThreadsK1, smem, stream>>>(src, sample0, G, C, T, m, M, Mp, win,
-                                                             tw, spec, spec_chan_stride, s2_auto,
-                                                             acc2, n_s2, pref2);
-  } else {
-    e = cudaFuncSetAttribute(k1_spectra<SS_I16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k1_spectra<SS_I16><<<grid, kThreadsK1, smem, stream>>>(src, sample0, G, C, T, m, M, Mp, win,
-                                                             tw, spec, spec_chan_stride, s2_auto,
-                                                             acc2, n_s2, pref2);
+  const bool f32 = src.dtype == SS_F32;
+  switch (oi.fmt) {
+    case kImageTF32:
+      return f32 ? launch_k1_t<SS_F32, kImageTF32>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
+                                                   oi, grid, smem, stream)
+                 : launch_k1_t<SS_I16, kImageTF32>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
+                                                   oi, grid, smem, stream);
+    case kImageBF16:
+      return f32 ? launch_k1_t<SS_F32, kImageBF16>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
+                                                   oi, grid, smem, stream)
+                 : launch_k1_t<SS_I16, kImageBF16>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
+                                                   oi, grid, smem, stream);
+    default:
+      return f32 ? launch_k1_t<SS_F32, kImageNone>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
+                                                   oi, grid, smem, stream)
+                 : launch_k1_t<SS_I16, kImageNone>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
+                                                   oi, grid, smem, stream);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G, int m, int M,

@@ -17,16 +17,21 @@
 // product is formed from three MMAs hi*hi + hi*lo + lo*hi accumulated in FP32
 // in TMEM (one MMA per product in the plain BF16 mode).
 //
-// Pipeline of a CTA over its (group chunk, tile) items, per step = (group,
-// chunk of <= 16 frames):
-//   TMA loads of the complex coefficients (128 bins at k0, 48 at l0) into one
-//   of two stages -> all threads convert them into K-major split operands in
-//   one of two operand buffers -> one thread issues the 30 (or 10 / 5) MMAs into
-//   the group's TMEM buffer (two buffers of 5 x 48 columns) and commits them to
-//   an mbarrier -> while those run, all threads read the previous group's
-//   accumulators from TMEM (tcgen05.ld), form c4 and update the float32 sums of
-//   their 24 grid points.  Every wait is bounded; a CTA that gives up drains
-//   its copies and products and frees its TMEM before returning.
+// The operands come ready-made: K1 writes, once per group and chunk of <= 16
+// frames, the hi/lo parts of Re, Im and |.|^2 in the K-major core-matrix layout
+// the tensor cores read (the "operand image", see OperandImage), and the sums
+// sum_j |.|^2 / sqrt2 per bin.  Pipeline of a CTA over its (group chunk, tile)
+// items, per step = (group, chunk):
+//   1-D TMA bulk copies of the image rows of the 128 bins at k0 and the 48 at
+//   l0 into one of kTcStages stages -> one thread issues the 30 (or 15 / 5)
+//   MMAs straight from the stage into the group's TMEM buffer (two buffers of
+//   5 x 48 columns) and commits them to the stage's mbarrier -> when the
+//   products of the previous step are complete its stage is refilled, and, at a
+//   group boundary, all threads read the finished group's accumulators from
+//   TMEM (tcgen05.ld), form c4 and update the float32 sums of their 24 grid
+//   points while the tensor cores work on the next group.  Every wait is
+//   bounded; a CTA that gives up drains its copies and products and frees its
+//   TMEM before returning.
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -36,34 +41,28 @@ namespace ss {
 namespace {
 
 constexpr int kTM = 128, kTN = 48, kKpad = 16, kTcThreads = 256;
-constexpr int kTcStages = 2;
+constexpr int kTcStages = 3;
 constexpr uint32_t kTmemCols = 512;  // two buffers of 5 x 48 fp32 columns
 
+// Operand formats.  A matrix of a row group is CB bytes: its core matrices
+// (8 rows x 16 bytes) for consecutive 16-byte frame groups, 128 bytes apart
+// (LBO); consecutive row groups are 6 CB apart (SBO, the six matrices of a row
+// group are adjacent).
 template <bool kBF16>
 struct OpFmt;
 
 template <>
 struct OpFmt<false> {  // TF32 operands, K = 8 per MMA
-  static constexpr uint32_t kMatK = kTM * kKpad * 4, kMatL = kTN * kKpad * 4;
-  static constexpr uint32_t kLBO = 128, kSBO = 512, kKstepBytes = 256;
+  static constexpr uint32_t kCB = 512, kLBO = 128, kSBO = 6 * 512, kKstepBytes = 256;
   static constexpr int kKsteps = 2;
   static constexpr uint32_t kIdescAB = (2u << 7) | (2u << 10);
-  // byte offset of element (row r, frame k) in the no-swizzle K-major layout of
-  // 8-row x 16-byte core matrices, K-adjacent cores 128 bytes apart
-  __device__ static uint32_t off(int r, int k) {
-    return ((r >> 3) * 4 + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4;
-  }
 };
 
 template <>
 struct OpFmt<true> {  // BF16 operands, K = 16 per MMA
-  static constexpr uint32_t kMatK = kTM * kKpad * 2, kMatL = kTN * kKpad * 2;
-  static constexpr uint32_t kLBO = 128, kSBO = 256, kKstepBytes = 0;
+  static constexpr uint32_t kCB = 256, kLBO = 128, kSBO = 6 * 256, kKstepBytes = 0;
   static constexpr int kKsteps = 1;
   static constexpr uint32_t kIdescAB = (1u << 7) | (1u << 10);
-  __device__ static uint32_t off(int r, int k) {
-    return ((r >> 3) * 2 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
-  }
 };
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -108,66 +107,31 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t t;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
-  return t;
-}
-
-// split x = hi + lo in the operand format; returns the bits of (hi, lo)
-template <bool kBF16>
-__device__ __forceinline__ void split(float x, uint32_t& hi, uint32_t& lo) {
-  if constexpr (kBF16) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-    hi = __bfloat16_as_ushort(h);
-    lo = __bfloat16_as_ushort(l);
-  } else {
-    hi = to_tf32(x);
-    lo = to_tf32(x - __uint_as_float(hi));
-  }
-}
-
-struct TcSmem {
-  unsigned char* stage[kTcStages];  // [FC][8][16] float2 at k0 | [FC][3][16] float2 at l0
-  uint32_t lside_off;               // offset of the l-side box inside a stage
-  unsigned char* ops[2];            // split operands: 6 k-side then 6 l-side matrices
-  float* sk;                        // [2][128] sum_j P / sqrt 2 per TMEM buffer
-  float* sl;                        // [2][48]
-};
-
 template <bool kBF16>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k3_trispec_tc(const __grid_constant__ CUtensorMap tm128, const __grid_constant__ CUtensorMap tm48,
-              int row0, int G, int m, int FC, int M, const TileInfo* __restrict__ tiles,
-              WorkQueue wq, float alpha, float scale2pb, int passes,
-              double* __restrict__ acc, long long plane, int* __restrict__ status) {
+k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ ps, int G, int m,
+              int nch, int M, int Mp, long long chunk_bytes, const TileInfo* __restrict__ tiles,
+              WorkQueue wq, float alpha, float scale2pb, int passes, double* __restrict__ acc,
+              long long plane, int* __restrict__ status) {
   using F = OpFmt<kBF16>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
   __shared__ __align__(8) uint64_t full[kTcStages];
-  __shared__ __align__(8) uint64_t mma_bar[2];
+  __shared__ __align__(8) uint64_t mma_bar[kTcStages];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_item;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
+  constexpr uint32_t kRowGroupBytes = 6 * F::kCB;
+  constexpr uint32_t kKBytes = (kTM / 8) * kRowGroupBytes;   // 16 row groups at k0
+  constexpr uint32_t kLBytes = (kTN / 8) * kRowGroupBytes;   // 6 row groups at l0
+  constexpr uint32_t kStageBytes = kKBytes + kLBytes;
   unsigned char* base = align1024<unsigned char>(smem_raw);
-  const uint32_t k_bytes = (uint32_t)FC * 1024u;
-  const uint32_t l_bytes = ((uint32_t)FC * 384u + 1023u) & ~1023u;
-  const uint32_t stage_bytes = k_bytes + l_bytes;
-  const uint32_t op_bytes = 6 * F::kMatK + 6 * F::kMatL;  // multiples of 1024
-  TcSmem S;
-  S.stage[0] = base;
-  S.stage[1] = base + stage_bytes;
-  S.lside_off = k_bytes;
-  S.ops[0] = base + 2 * stage_bytes;
-  S.ops[1] = S.ops[0] + op_bytes;
-  S.sk = reinterpret_cast<float*>(S.ops[1] + op_bytes);
-  S.sl = S.sk + 2 * kTM;
+  const int R = Mp / 8;  // row groups per chunk of the image
 
   if (tid == 0) {
-    for (int s = 0; s < kTcStages; ++s) mbar_init(&full[s], 1);
-    mbar_init(&mma_bar[0], 1);
-    mbar_init(&mma_bar[1], 1);
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&mma_bar[s], 1);
+    }
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -183,15 +147,12 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm128, const __grid_constant__
   const uint32_t taddr = tmem_slot;
   const uint32_t idesc = (1u << 4) | F::kIdescAB | ((uint32_t)(kTN >> 3) << 17) |
                          ((uint32_t)(kTM >> 4) << 24);
-  const int nch = (m + FC - 1) / FC;
-  // epilogue role: TMEM lane quadrant q (rows 32q..32q+31), column half h
-  const int q = warp & 3, h = warp >> 2;
-  uint32_t qs = 0;   // running step counter: TMA stage q % 2, mbarrier parities
-  uint32_t gcnt = 0; // running group counter: TMEM / sk buffer gcnt % 2
+  const int q = warp & 3, h = warp >> 2;  // epilogue: TMEM lane quadrant, column half
+  uint32_t qs = 0;    // running step counter: stage qs % kTcStages, barrier parities
+  uint32_t gcnt = 0;  // running group counter: TMEM buffer gcnt % 2
   bool failed = false;
-  // for a bounded drain after a failure: last committed step per product
-  // barrier, and the TMA steps issued but not yet waited for
-  long long last_commit[2] = {-1, -1};
+  long long last_commit[kTcStages];
+  for (int s = 0; s < kTcStages; ++s) last_commit[s] = -1;
   uint32_t tma_next = 0, tma_issued = 0;
 
   for (int item; !failed && (item = next_item(wq, &s_item)) >= 0;) {
@@ -200,6 +161,8 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm128, const __grid_constant__
     const int gb = min(G, ga + wq.group_chunk);
     const int k0 = tiles[t].k0, l0 = tiles[t].l0;
     const int nsteps = (gb - ga) * nch;
+    const uint32_t kb = (uint32_t)min(kTM / 8, R - (k0 >> 3)) * kRowGroupBytes;
+    const uint32_t lb = (uint32_t)min(kTN / 8, R - (l0 >> 3)) * kRowGroupBytes;
     float sum[24], sq[24];
 #pragma unroll
     for (int i = 0; i < 24; ++i) sum[i] = sq[i] = 0.f;
@@ -207,24 +170,33 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm128, const __grid_constant__
     auto issue_tma = [&](int i) {
       const uint32_t Q = qs + i;
       const int s = Q % kTcStages;
-      const int g = ga + i / nch, j0 = (i % nch) * FC;
-      mbar_arrive_expect_tx(&full[s], (uint32_t)FC * (1024u + 384u));
-      tma_load_3d(S.stage[s], &tm128, 0, k0 >> 4, row0 + g * m + j0, &full[s]);
-      tma_load_3d(S.stage[s] + S.lside_off, &tm48, 0, l0 >> 4, row0 + g * m + j0, &full[s]);
+      const int g = ga + i / nch, ch = i % nch;
+      const unsigned char* src = img + ((size_t)g * nch + ch) * (size_t)chunk_bytes;
+      unsigned char* st = base + (size_t)s * kStageBytes;
+      mbar_arrive_expect_tx(&full[s], kb + lb);
+      tma_load_1d(st, src + (size_t)(k0 >> 3) * kRowGroupBytes, kb, &full[s]);
+      tma_load_1d(st + kKBytes, src + (size_t)(l0 >> 3) * kRowGroupBytes, lb, &full[s]);
     };
-    // epilogue of the group held in TMEM buffer b (its products are complete)
-    auto epilogue = [&](int b) {
+    // epilogue of group g held in TMEM buffer b (its products are complete)
+    auto epilogue = [&](int g, uint32_t b) {
+      const float* psg = ps + (long long)g * Mp;
+      const int kr = k0 + 32 * q + lane;
+      const float skr = kr < Mp ? __ldg(psg + kr) : 0.f;
       tc_fence_after();
-      const float skr = S.sk[b * kTM + 32 * q + lane];
-      const uint32_t tb = taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)b * 5 * kTN + 24 * h;
+      const uint32_t tb = taddr + ((uint32_t)(32 * q) << 16) + b * 5 * kTN + 24 * h;
 #pragma unroll
       for (int c0 = 0; c0 < 24; c0 += 8) {
-        float rr[8], ii[8], xx[8], xt[8], qq[8];
+        float rr[8], ii[8], xx[8], xt[8], qq[8], sl[8];
         tmem_ld8(tb + 0 * kTN + c0, rr);
         tmem_ld8(tb + 1 * kTN + c0, ii);
         tmem_ld8(tb + 2 * kTN + c0, xx);
         tmem_ld8(tb + 3 * kTN + c0, xt);
         tmem_ld8(tb + 4 * kTN + c0, qq);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int lc = l0 + 24 * h + c0 + i;
+          sl[i] = lc < Mp ? __ldg(psg + lc) : 0.f;
+        }
         tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -232,8 +204,8 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm128, const __grid_constant__
           u = fmaf(ii[i], ii[i], u);
           u = fmaf(xx[i], xx[i], u);
           u = fmaf(xt[i], xt[i], u);
-          u = fmaf(skr, S.sl[b * kTN + 24 * h + c0 + i], u);
-          const float c = qq[i] - u;
+          u = fmaf(skr, sl[i], u);
+          const float c = fmaf(alpha, qq[i], -u);
           sum[c0 + i] += c;
           sq[c0 + i] = fmaf(c, c, sq[c0 + i]);
         }
@@ -247,117 +219,70 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm128, const __grid_constant__
     }
     tma_next = qs;
     tma_issued = qs + (uint32_t)min(kTcStages, nsteps);
-    for (int i = 0; i < nsteps && !failed; ++i) {
+    for (int i = 0; i < nsteps; ++i) {
       const uint32_t Q = qs + i;
       const int s = Q % kTcStages;
       const int gi = i / nch, ch = i % nch;
-      const int nf = min(FC, m - ch * FC);
-      const uint32_t tb = (gcnt + gi) & 1u;  // TMEM / sk buffer of this group
-      bool ok = mbar_wait_bounded(&full[s], (Q / kTcStages) & 1u, status);
+      const uint32_t tb = (gcnt + gi) & 1u;
+      const bool ok = mbar_wait_bounded(&full[s], (Q / kTcStages) & 1u, status);
       tma_next = Q + 1;
-      // operand buffer Q % 2 is free once the products of step Q-2 are complete
-      if (ok && Q >= 2 && i >= 2) ok = mbar_wait_bounded(&mma_bar[Q & 1], ((Q - 2) >> 1) & 1u, status);
-      // ---- convert: complex coefficients -> K-major split operands
-      unsigned char* ops = S.ops[Q & 1];
-      const unsigned char* st = S.stage[s];
-      if (tid < kTM + kTN) {
-        const bool kside = tid < kTM;
-        const int r = kside ? tid : tid - kTM;
-        const uint32_t rowb = kside ? 1024u : 384u;
-        const unsigned char* src = st + (kside ? 0u : S.lside_off);
-        unsigned char* dst = ops + (kside ? 0u : 6 * F::kMatK);
-        const uint32_t mat = kside ? F::kMatK : F::kMatL;
-        const float sc = kside ? alpha : 1.f;
-        float psum = 0.f;
-        constexpr int kPer = kBF16 ? 8 : 4;  // K elements per 16-byte core-matrix row
-#pragma unroll
-        for (int kg = 0; kg < kKpad / kPer; ++kg) {
-          uint32_t w[6][kPer];
-#pragma unroll
-          for (int e = 0; e < kPer; ++e) {
-            const int j = kg * kPer + e;
-            float re = 0.f, im = 0.f;
-            if (j < nf) {
-              const float2 v = *reinterpret_cast<const float2*>(src + swz128(j * rowb + r * 8));
-              re = v.x;
-              im = v.y;
-            }
-            const float p = fmaf(re, re, im * im);
-            psum += p;
-            split<kBF16>(re, w[0][e], w[1][e]);
-            split<kBF16>(im, w[2][e], w[3][e]);
-            split<kBF16>(p * sc, w[4][e], w[5][e]);
-          }
-#pragma unroll
-          for (int mt = 0; mt < 6; ++mt) {
-            uint4 pk;
-            if constexpr (kBF16) {
-              pk = make_uint4(w[mt][0] | (w[mt][1] << 16), w[mt][2] | (w[mt][3] << 16),
-                              w[mt][4] | (w[mt][5] << 16), w[mt][6] | (w[mt][7] << 16));
-            } else {
-              pk = make_uint4(w[mt][0], w[mt][1], w[mt][2], w[mt][3]);
-            }
-            *reinterpret_cast<uint4*>(dst + mt * mat + F::off(r, kg * kPer)) = pk;
-          }
-        }
-        float* sx = kside ? &S.sk[tb * kTM + r] : &S.sl[tb * kTN + r];
-        const float v = psum * 0.70710678118654752f;
-        *sx = (ch == 0) ? v : *sx + v;
-      }
-      fence_async_smem();
-      // a failed wait anywhere stops the CTA (after this barrier all agree)
+      // all threads are past the previous epilogue (TMEM reads done) and agree on success
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
       }
       tc_fence_after();
-      last_commit[Q & 1] = Q;
-      if (i + kTcStages < nsteps) tma_issued = Q + kTcStages + 1;
+      last_commit[s] = Q;
       if (tid == 0) {
-        // refill the TMA stage just consumed
-        if (i + kTcStages < nsteps) issue_tma(i + kTcStages);
         const uint32_t d0 = taddr + tb * 5 * kTN;
-        const uint32_t ka = smem_addr(ops), la = ka + 6 * F::kMatK;
-        // products: (k-side matrix, l-side matrix) = RR (Ar,Ar), II (Ai,Ai), X (Ar,Ai),
-        // Xt (Ai,Ar), Q (P,P); matrices are ordered hi, lo for Ar, Ai, P
+        const uint32_t ka = smem_addr(base + (size_t)s * kStageBytes), la = ka + kKBytes;
+        // products: (k-side, l-side) = RR (Re,Re), II (Im,Im), X (Re,Im), Xt (Im,Re),
+        // Q (P,P); the six matrices of a row group are Re hi, Re lo, Im hi, Im lo,
+        // P hi, P lo
 #pragma unroll
         for (int pr = 0; pr < 5; ++pr) {
-          const int pa = pr < 4 ? (pr & 1) : 2;              // Ar, Ai, Ar, Ai, P
-          const int pl = pr < 4 ? ((pr ^ (pr >> 1)) & 1) : 2;  // Ar, Ai, Ai, Ar, P
-          for (int ps = 0; ps < passes; ++ps) {
-            const int ha = (ps == 2) ? 1 : 0, hb = (ps == 1) ? 1 : 0;
+          const int pa = pr < 4 ? (pr & 1) : 2;
+          const int pl = pr < 4 ? ((pr ^ (pr >> 1)) & 1) : 2;
+          for (int ps_ = 0; ps_ < passes; ++ps_) {
+            const int ha = (ps_ == 2) ? 1 : 0, hb = (ps_ == 1) ? 1 : 0;
 #pragma unroll
             for (int kst = 0; kst < F::kKsteps; ++kst) {
-              const uint64_t ad = smem_desc(ka + (pa * 2 + ha) * F::kMatK + kst * F::kKstepBytes,
+              const uint64_t ad = smem_desc(ka + (pa * 2 + ha) * F::kCB + kst * F::kKstepBytes,
                                             F::kLBO, F::kSBO);
-              const uint64_t bd = smem_desc(la + (pl * 2 + hb) * F::kMatL + kst * F::kKstepBytes,
+              const uint64_t bd = smem_desc(la + (pl * 2 + hb) * F::kCB + kst * F::kKstepBytes,
                                             F::kLBO, F::kSBO);
-              const bool accum = !(ch == 0 && ps == 0 && kst == 0);
+              const bool accum = !(ch == 0 && ps_ == 0 && kst == 0);
               mma_issue(d0 + pr * kTN, ad, bd, idesc, accum, kBF16);
             }
           }
         }
-        mma_commit(&mma_bar[Q & 1]);
+        mma_commit(&mma_bar[s]);
       }
-      // epilogue of the previous group while this step's products run
-      if (ch == 0 && gi > 0) {
-        const uint32_t Qp = Q - 1;  // last step of the previous group
-        const bool okp = mbar_wait_bounded(&mma_bar[Qp & 1], (Qp >> 1) & 1u, status);
+      if (i > 0) {
+        // the previous step's products are complete: refill its stage, and if it
+        // closed a group, run that group's epilogue while this step's products run
+        const uint32_t Qp = Q - 1;
+        const int sp = Qp % kTcStages;
+        const bool okp = mbar_wait_bounded(&mma_bar[sp], (Qp / kTcStages) & 1u, status);
         if (__syncthreads_or(!okp)) {
           failed = true;
           break;
         }
-        epilogue((gcnt + gi - 1) & 1u);
+        if (tid == 0 && (i - 1) + kTcStages < nsteps) {
+          fence_async_smem();
+          issue_tma((i - 1) + kTcStages);
+        }
+        if ((i - 1) + kTcStages < nsteps) tma_issued = Qp + kTcStages + 1;
+        if (ch == 0) epilogue(ga + gi - 1, (gcnt + gi - 1) & 1u);
       }
     }
     if (!failed && nsteps > 0) {
       const uint32_t Ql = qs + nsteps - 1;
-      const bool okl = mbar_wait_bounded(&mma_bar[Ql & 1], (Ql >> 1) & 1u, status);
-      if (__syncthreads_or(!okl)) {
+      const bool okl = mbar_wait_bounded(&mma_bar[Ql % kTcStages], (Ql / kTcStages) & 1u, status);
+      if (__syncthreads_or(!okl))
         failed = true;
-      } else {
-        epilogue((gcnt + (gb - ga) - 1) & 1u);
-      }
+      else
+        epilogue(gb - 1, (gcnt + (gb - ga) - 1) & 1u);
     }
     if (failed) break;
     qs += nsteps;
@@ -376,9 +301,9 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm128, const __grid_constant__
   if (failed && tid == 0) {
     // drain with bounded waits: the last products committed on each barrier and
     // the copies issued but not consumed, before the TMEM is freed
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < kTcStages; ++b)
       if (last_commit[b] >= 0)
-        mbar_wait_bounded(&mma_bar[b], ((uint32_t)last_commit[b] >> 1) & 1u, nullptr);
+        mbar_wait_bounded(&mma_bar[b], ((uint32_t)last_commit[b] / kTcStages) & 1u, nullptr);
     for (uint32_t Q = tma_next; Q < tma_issued; ++Q)
       mbar_wait_bounded(&full[Q % kTcStages], (Q / kTcStages) & 1u, nullptr);
   }
@@ -391,29 +316,23 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm128, const __grid_constant__
   }
 }
 
-size_t tc_smem_bytes(int FC, bool bf16) {
-  const size_t k_bytes = (size_t)FC * 1024;
-  const size_t l_bytes = ((size_t)FC * 384 + 1023) & ~(size_t)1023;
-  const size_t mk = bf16 ? OpFmt<true>::kMatK : OpFmt<false>::kMatK;
-  const size_t ml = bf16 ? OpFmt<true>::kMatL : OpFmt<false>::kMatL;
-  return 2 * (k_bytes + l_bytes) + 2 * (6 * mk + 6 * ml) + (2 * kTM + 2 * kTN) * sizeof(float) +
-         1024;
+size_t tc_smem_bytes(bool bf16) {
+  const size_t cb = bf16 ? OpFmt<true>::kCB : OpFmt<false>::kCB;
+  return (size_t)kTcStages * (kTM / 8 + kTN / 8) * 6 * cb + 1024;
 }
 
 }  // namespace
 
-size_t k3tc_smem_bytes(int FC, int precision) {
-  return tc_smem_bytes(FC, precision != SS_PREC_TF32X3);
-}
+size_t k3tc_smem_bytes(int precision) { return tc_smem_bytes(precision != SS_PREC_TF32X3); }
 
-cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm128, const CUtensorMap& tm48, int row0,
-                                 int G, int m, int FC, int M, const TileInfo* tiles, int n_tiles,
-                                 int precision, double* acc, long long plane, int nsm,
-                                 int* counter, int* status, cudaStream_t stream) {
+cudaError_t launch_k3_trispec_tc(const OperandImage& oi, int channel, int G, int m, int M, int Mp,
+                                 const TileInfo* tiles, int n_tiles, int precision, double* acc,
+                                 long long plane, int nsm, int* counter, int* status,
+                                 cudaStream_t stream) {
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
   const bool bf16 = precision != SS_PREC_TF32X3;
   const int passes = precision == SS_PREC_BF16 ? 1 : 3;
-  const size_t smem = tc_smem_bytes(FC, bf16);
+  const size_t smem = tc_smem_bytes(bf16);
   auto kern = bf16 ? k3_trispec_tc<true> : k3_trispec_tc<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -429,8 +348,10 @@ cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm128, const CUtensorMap& tm
   const double md = m;
   const float alpha = (float)(md * (md + 1.0) / (2.0 * (md - 1.0)));
   const float scale2pb = (float)(2.0 / ((md - 2.0) * (md - 3.0)));
-  kern<<<n_cta, kTcThreads, smem, stream>>>(tm128, tm48, row0, G, m, FC, M, tiles, wq, alpha,
-                                            scale2pb, passes, acc, plane, status);
+  const unsigned char* img = static_cast<const unsigned char*>(oi.img) + (size_t)channel * oi.chan_bytes;
+  const float* ps = oi.ps + (size_t)channel * oi.chan_ps;
+  kern<<<n_cta, kTcThreads, smem, stream>>>(img, ps, G, m, oi.nch, M, Mp, oi.chunk_bytes, tiles, wq,
+                                            alpha, scale2pb, passes, acc, plane, status);
   return cudaGetLastError();
 }
 

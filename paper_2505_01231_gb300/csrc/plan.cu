@@ -83,6 +83,7 @@ struct ss_plan_s {
   CUtensorMap tm64{}, tm128{}, tm48{};  // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
   TileInfo* d_tiles4tc = nullptr;  // 128 x 48 tiles of the tensor-core S4 kernel
   int n_tiles4tc = 0;
+  OperandImage oi;                 // K1's second output for the tensor-core S4 kernel
   int n_tiles3 = 0, n_tiles4 = 0;
   long long pairs3 = 0, pairs4 = 0;
   void* d_stage[2] = {nullptr, nullptr};
@@ -267,7 +268,8 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
       record(p, 0, p->stream, true);
       SS_TRY(p, launch_k1_spectra(src, g0 * per_group, cnt, p->C, p->T, p->m, p->M, p->Mp,
                                   p->d_win, p->d_tw, p->d_spec, chan_stride, p->d_s2auto,
-                                  p->d_acc2, (int)p->c2.size(), pref2, 4 * p->nsm, p->stream));
+                                  p->d_acc2, (int)p->c2.size(), pref2, 4 * p->nsm, p->stream,
+                                  p->oi));
       if (p->n_s2cross > 0)
         SS_TRY(p, launch_k1_cross_s2(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp,
                                      p->d_s2cross, p->n_s2cross, pref2, p->d_acc2,
@@ -301,9 +303,8 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
                                         p->d_acc4 + (long long)i * p->rows4 * p->M, plane,
                                         p->nsm, p->d_counter, p->d_status, p->stream));
           else
-            SS_TRY(p, launch_k3_trispec_tc(p->tm128, p->tm48, cb.c[0] * p->Gb_max * p->m, cnt,
-                                           p->m, p->FC, p->M, p->d_tiles4tc, p->n_tiles4tc,
-                                           p->precision,
+            SS_TRY(p, launch_k3_trispec_tc(p->oi, cb.c[0], cnt, p->m, p->M, p->Mp,
+                                           p->d_tiles4tc, p->n_tiles4tc, p->precision,
                                            p->d_acc4 + (long long)i * p->rows4 * p->M, plane,
                                            p->nsm, p->d_counter, p->d_status, p->stream));
         }
@@ -430,22 +431,51 @@ ss_status encode_maps(ss_plan_s* p) {
 }
 
 ss_status alloc_spec(ss_plan_s* p) {
-  if (p->d_spec) {
-    cudaFree(p->d_spec);
-    p->device_bytes -= (size_t)p->C * p->Gb_max * p->m * p->Mp * sizeof(float2);
+  auto release = [&](void*& ptr, size_t bytes) {
+    if (ptr) {
+      cudaFree(ptr);
+      p->device_bytes -= bytes;
+      ptr = nullptr;
+    }
+  };
+  const size_t spec_group = (size_t)p->C * p->m * p->Mp * sizeof(float2);
+  const bool image = !p->c4.empty() && p->precision != SS_PREC_FP32;
+  const int nch = (p->m + p->FC - 1) / p->FC;
+  const size_t cb = p->precision == SS_PREC_TF32X3 ? 512 : 256;
+  const size_t chunk_bytes = (size_t)(p->Mp / 8) * 6 * cb;
+  const size_t img_group = image ? (size_t)p->C * nch * chunk_bytes : 0;
+  const size_t ps_group = image ? (size_t)p->C * p->Mp * sizeof(float) : 0;
+  {
+    void* v = p->d_spec;
+    release(v, spec_group * p->Gb_max);
     p->d_spec = nullptr;
+    release(p->oi.img, img_group * p->Gb_max);
+    void* w = p->oi.ps;
+    release(w, ps_group * p->Gb_max);
+    p->oi.ps = nullptr;
   }
-  const size_t per_group = (size_t)p->C * p->m * p->Mp * sizeof(float2);
+  const size_t per_group = spec_group + img_group + ps_group;
   int gb = p->Gb_user;
   if (gb <= 0) {
-    // about 1.5 GiB of centred spectra per batch, at least one group
-    gb = (int)std::max<size_t>(1, (size_t)(1536ull << 20) / per_group);
+    // about 4 GiB of per-batch scratch, at least one group
+    gb = (int)std::max<size_t>(1, (size_t)(4096ull << 20) / per_group);
   }
-  // the 2-D views index rows with 32-bit coordinates
+  // the 3-D views index rows with 32-bit coordinates
   const long long max_rows = (1ll << 31) - 1;
   if ((long long)p->C * gb * p->m > max_rows) gb = (int)(max_rows / ((long long)p->C * p->m));
   p->Gb_max = gb;
-  SS_TRY(p, dev_alloc(p, &p->d_spec, per_group * gb));
+  SS_TRY(p, dev_alloc(p, &p->d_spec, spec_group * gb));
+  p->oi = OperandImage();
+  if (image) {
+    SS_TRY(p, dev_alloc(p, &p->oi.img, img_group * gb));
+    SS_TRY(p, dev_alloc(p, &p->oi.ps, ps_group * gb));
+    p->oi.fmt = p->precision == SS_PREC_TF32X3 ? kImageTF32 : kImageBF16;
+    p->oi.FC = p->FC;
+    p->oi.nch = nch;
+    p->oi.chunk_bytes = (long long)chunk_bytes;
+    p->oi.chan_bytes = (long long)gb * nch * chunk_bytes;
+    p->oi.chan_ps = (long long)gb * p->Mp;
+  }
   return encode_maps(p);
 }
 
@@ -466,6 +496,8 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_tw);
   cudaFree(p->d_carry);
   cudaFree(p->d_spec);
+  cudaFree(p->oi.img);
+  cudaFree(p->oi.ps);
   cudaFree(p->d_acc2);
   cudaFree(p->d_acc3);
   cudaFree(p->d_acc4);
