@@ -20,18 +20,23 @@
 // The operands come ready-made: K1 writes, once per group and chunk of <= 16
 // frames, the hi/lo parts of Re, Im and |.|^2 in the K-major core-matrix layout
 // the tensor cores read (the "operand image", see OperandImage), and the sums
-// sum_j |.|^2 / sqrt2 per bin.  Pipeline of a CTA over its (group chunk, tile)
-// items, per step = (group, chunk):
-//   1-D TMA bulk copies of the image rows of the 128 bins at k0 and the 48 at
-//   l0 into one of kTcStages stages -> one thread issues the 30 (or 15 / 5)
-//   MMAs straight from the stage into the group's TMEM buffer (two buffers of
-//   5 x 48 columns) and commits them to the stage's mbarrier -> when the
-//   products of the previous step are complete its stage is refilled, and, at a
-//   group boundary, all threads read the finished group's accumulators from
-//   TMEM (tcgen05.ld), form c4 and update the float32 sums of their 24 grid
-//   points while the tensor cores work on the next group.  Every wait is
-//   bounded; a CTA that gives up drains its copies and products and frees its
-//   TMEM before returning.
+// sum_j |.|^2 / sqrt2 per bin.
+//
+// Warp roles (288 threads).  Warp 8, the producer: takes (group chunk, tile)
+// items from the queue; for every step = (group, chunk of <= 16 frames) it
+// issues 1-D TMA bulk copies of the image rows of the 128 bins at k0 and the 48
+// at l0 into one of kTcStages stages, then the 30 (or 15 / 5) MMAs straight
+// from the stage into the group's TMEM buffer (two buffers of 5 x 48 columns),
+// commits them to the stage's mbarrier (stage reuse) and, after the group's last
+// chunk, to the buffer's "full" mbarrier with a record of the group in shared
+// memory.  Warps 0-7, the epilogue: for each group in order they wait for its
+// buffer, read the five accumulators from TMEM (tcgen05.ld, TMEM lane quadrant
+// = warp % 4, column half = warp / 4), form c4 and update the float32 sums of
+// their 24 grid points, release the buffer, and at the end of an item add the
+// sums to the float64 accumulators.  Producer and epilogue meet only on
+// mbarriers, so copies, products and epilogue of consecutive groups overlap.
+// Every wait is bounded; on a failure the CTA stops, drains its copies and
+// products and frees its TMEM before returning.
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -40,7 +45,7 @@
 namespace ss {
 namespace {
 
-constexpr int kTM = 128, kTN = 48, kKpad = 16, kTcThreads = 256;
+constexpr int kTM = 128, kTN = 48, kKpad = 16, kTcThreads = 288, kEpiWarps = 8;
 constexpr int kTcStages = 3;
 constexpr uint32_t kTmemCols = 512;  // two buffers of 5 x 48 fp32 columns
 
@@ -103,9 +108,22 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+struct GroupRec {
+  int k0, l0, g, flags;  // flags: 1 = last group of its item, 2 = stop
+};
 
 template <bool kBF16>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -115,10 +133,13 @@ k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ p
               long long plane, int* __restrict__ status) {
   using F = OpFmt<kBF16>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
-  __shared__ __align__(8) uint64_t full[kTcStages];
-  __shared__ __align__(8) uint64_t mma_bar[kTcStages];
+  __shared__ __align__(8) uint64_t full[kTcStages];       // stage loaded (TMA)
+  __shared__ __align__(8) uint64_t sdone[kTcStages];      // stage's products complete
+  __shared__ __align__(8) uint64_t afull[2];              // TMEM buffer holds a finished group
+  __shared__ __align__(8) uint64_t aempty[2];             // TMEM buffer read by the epilogue
+  __shared__ GroupRec rec[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_item;
+  __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr uint32_t kRowGroupBytes = 6 * F::kCB;
   constexpr uint32_t kKBytes = (kTM / 8) * kRowGroupBytes;   // 16 row groups at k0
@@ -130,8 +151,13 @@ k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ p
   if (tid == 0) {
     for (int s = 0; s < kTcStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&mma_bar[s], 1);
+      mbar_init(&sdone[s], 1);
     }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&afull[b], 2);  // the products' commit + the producer's record arrive
+      mbar_init(&aempty[b], kEpiWarps);
+    }
+    s_fail = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -145,167 +171,207 @@ k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ p
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = tmem_slot;
-  const uint32_t idesc = (1u << 4) | F::kIdescAB | ((uint32_t)(kTN >> 3) << 17) |
-                         ((uint32_t)(kTM >> 4) << 24);
-  const int q = warp & 3, h = warp >> 2;  // epilogue: TMEM lane quadrant, column half
-  uint32_t qs = 0;    // running step counter: stage qs % kTcStages, barrier parities
-  uint32_t gcnt = 0;  // running group counter: TMEM buffer gcnt % 2
-  bool failed = false;
-  long long last_commit[kTcStages];
-  for (int s = 0; s < kTcStages; ++s) last_commit[s] = -1;
-  uint32_t tma_next = 0, tma_issued = 0;
 
-  for (int item; !failed && (item = next_item(wq, &s_item)) >= 0;) {
-    const int t = item % wq.n_tiles;
-    const int ga = (item / wq.n_tiles) * wq.group_chunk;
-    const int gb = min(G, ga + wq.group_chunk);
-    const int k0 = tiles[t].k0, l0 = tiles[t].l0;
-    const int nsteps = (gb - ga) * nch;
-    const uint32_t kb = (uint32_t)min(kTM / 8, R - (k0 >> 3)) * kRowGroupBytes;
-    const uint32_t lb = (uint32_t)min(kTN / 8, R - (l0 >> 3)) * kRowGroupBytes;
+  if (warp == kEpiWarps) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | F::kIdescAB | ((uint32_t)(kTN >> 3) << 17) |
+                             ((uint32_t)(kTM >> 4) << 24);
+      uint32_t Q = 0;      // steps issued (stage Q % kTcStages)
+      uint32_t gc = 0;     // groups issued (TMEM buffer gc % 2)
+      bool ok = true;
+      // per stage: the step last loaded into it (for the stage-reuse wait)
+      long long stage_step[kTcStages];
+      for (int s = 0; s < kTcStages; ++s) stage_step[s] = -1;
+      auto load_step = [&](uint32_t q, int k0, int l0, int g, int ch) -> bool {
+        const int s = q % kTcStages;
+        if (stage_step[s] >= 0 &&  // the stage's previous products must be complete
+            !mbar_wait_bounded(&sdone[s], ((uint32_t)stage_step[s] / kTcStages) & 1u, status))
+          return false;
+        stage_step[s] = q;
+        const uint32_t kb = (uint32_t)min(kTM / 8, R - (k0 >> 3)) * kRowGroupBytes;
+        const uint32_t lb = (uint32_t)min(kTN / 8, R - (l0 >> 3)) * kRowGroupBytes;
+        const unsigned char* src = img + ((size_t)g * nch + ch) * (size_t)chunk_bytes;
+        unsigned char* st = base + (size_t)s * kStageBytes;
+        fence_async_smem();
+        mbar_arrive_expect_tx(&full[s], kb + lb);
+        tma_load_1d(st, src + (size_t)(k0 >> 3) * kRowGroupBytes, kb, &full[s]);
+        tma_load_1d(st + kKBytes, src + (size_t)(l0 >> 3) * kRowGroupBytes, lb, &full[s]);
+        return true;
+      };
+      for (;;) {
+        const int item = atomicAdd(wq.counter, 1);
+        if (item >= wq.n_items || *(volatile int*)&s_fail) break;
+        const int t = item % wq.n_tiles;
+        const int ga = (item / wq.n_tiles) * wq.group_chunk;
+        const int gb = min(G, ga + wq.group_chunk);
+        const int k0 = tiles[t].k0, l0 = tiles[t].l0;
+        const int nsteps = (gb - ga) * nch;
+        // keep kTcStages - 1 steps of copies ahead of the products
+        int loaded = 0;
+        for (; loaded < nsteps && loaded < kTcStages - 1 && ok; ++loaded)
+          ok = load_step(Q + loaded, k0, l0, ga + loaded / nch, loaded % nch);
+        for (int i = 0; i < nsteps && ok; ++i) {
+          const uint32_t q = Q + i;
+          const int s = q % kTcStages;
+          const int ch = i % nch, gi = i / nch;
+          const uint32_t b = (gc + gi) & 1u;
+          if (ch == 0) {
+            // the TMEM buffer is free once the epilogue has read the group before last
+            const uint32_t use = (gc + gi) >> 1;  // earlier uses of buffer b
+            if (use > 0 && !mbar_wait_bounded(&aempty[b], (use - 1) & 1u, status)) {
+              ok = false;
+              break;
+            }
+          }
+          if (!mbar_wait_bounded(&full[s], (q / kTcStages) & 1u, status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d0 = taddr + b * 5 * kTN;
+          const uint32_t ka = smem_addr(base + (size_t)s * kStageBytes), la = ka + kKBytes;
+          // products (k-side, l-side): RR (Re,Re), II (Im,Im), X (Re,Im), Xt (Im,Re),
+          // Q (P,P); a row group's six matrices are Re hi, Re lo, Im hi, Im lo, P hi, P lo
+#pragma unroll
+          for (int pr = 0; pr < 5; ++pr) {
+            const int pa = pr < 4 ? (pr & 1) : 2;
+            const int pl = pr < 4 ? ((pr ^ (pr >> 1)) & 1) : 2;
+            for (int ps_ = 0; ps_ < passes; ++ps_) {
+              const int ha = (ps_ == 2) ? 1 : 0, hb = (ps_ == 1) ? 1 : 0;
+#pragma unroll
+              for (int kst = 0; kst < F::kKsteps; ++kst) {
+                const uint64_t ad = smem_desc(ka + (pa * 2 + ha) * F::kCB + kst * F::kKstepBytes,
+                                              F::kLBO, F::kSBO);
+                const uint64_t bd = smem_desc(la + (pl * 2 + hb) * F::kCB + kst * F::kKstepBytes,
+                                              F::kLBO, F::kSBO);
+                mma_issue(d0 + pr * kTN, ad, bd, idesc, !(ch == 0 && ps_ == 0 && kst == 0),
+                          kBF16);
+              }
+            }
+          }
+          mma_commit(&sdone[s]);
+          if (ch == nch - 1) {
+            const int g = ga + gi;
+            rec[b].k0 = k0;
+            rec[b].l0 = l0;
+            rec[b].g = g;
+            rec[b].flags = (g == gb - 1) ? 1 : 0;
+            mma_commit(&afull[b]);  // arrives when the group's products are complete
+            asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
+                             smem_addr(&afull[b]))
+                         : "memory");
+          }
+          // refill the stage freed by the previous step while this step's products run
+          if (loaded < nsteps) {
+            ok = load_step(Q + loaded, k0, l0, ga + loaded / nch, loaded % nch);
+            ++loaded;
+          }
+        }
+        if (!ok) break;
+        Q += nsteps;
+        gc += gb - ga;
+      }
+      if (!ok) {
+        atomicExch(&s_fail, 1);
+        // drain: every stage's last copy and products, with bounded waits
+        for (int s = 0; s < kTcStages; ++s)
+          if (stage_step[s] >= 0) {
+            mbar_wait_bounded(&full[s], ((uint32_t)stage_step[s] / kTcStages) & 1u, nullptr);
+          }
+      }
+      // stop record: wait until the next buffer is free, then release it without products
+      const uint32_t b = gc & 1u, use = gc >> 1;
+      if (use > 0) mbar_wait_bounded(&aempty[b], (use - 1) & 1u, nullptr);
+      rec[b].flags = 2;
+      asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0], 2;" ::"r"(
+                       smem_addr(&afull[b]))
+                   : "memory");
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3, h = warp >> 2;
     float sum[24], sq[24];
 #pragma unroll
     for (int i = 0; i < 24; ++i) sum[i] = sq[i] = 0.f;
-
-    auto issue_tma = [&](int i) {
-      const uint32_t Q = qs + i;
-      const int s = Q % kTcStages;
-      const int g = ga + i / nch, ch = i % nch;
-      const unsigned char* src = img + ((size_t)g * nch + ch) * (size_t)chunk_bytes;
-      unsigned char* st = base + (size_t)s * kStageBytes;
-      mbar_arrive_expect_tx(&full[s], kb + lb);
-      tma_load_1d(st, src + (size_t)(k0 >> 3) * kRowGroupBytes, kb, &full[s]);
-      tma_load_1d(st + kKBytes, src + (size_t)(l0 >> 3) * kRowGroupBytes, lb, &full[s]);
-    };
-    // epilogue of group g held in TMEM buffer b (its products are complete)
-    auto epilogue = [&](int g, uint32_t b) {
-      const float* psg = ps + (long long)g * Mp;
-      const int kr = k0 + 32 * q + lane;
-      const float skr = kr < Mp ? __ldg(psg + kr) : 0.f;
-      tc_fence_after();
-      const uint32_t tb = taddr + ((uint32_t)(32 * q) << 16) + b * 5 * kTN + 24 * h;
-#pragma unroll
-      for (int c0 = 0; c0 < 24; c0 += 8) {
-        float rr[8], ii[8], xx[8], xt[8], qq[8], sl[8];
-        tmem_ld8(tb + 0 * kTN + c0, rr);
-        tmem_ld8(tb + 1 * kTN + c0, ii);
-        tmem_ld8(tb + 2 * kTN + c0, xx);
-        tmem_ld8(tb + 3 * kTN + c0, xt);
-        tmem_ld8(tb + 4 * kTN + c0, qq);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int lc = l0 + 24 * h + c0 + i;
-          sl[i] = lc < Mp ? __ldg(psg + lc) : 0.f;
-        }
-        tmem_wait_ld();
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float u = rr[i] * rr[i];
-          u = fmaf(ii[i], ii[i], u);
-          u = fmaf(xx[i], xx[i], u);
-          u = fmaf(xt[i], xt[i], u);
-          u = fmaf(skr, sl[i], u);
-          const float c = fmaf(alpha, qq[i], -u);
-          sum[c0 + i] += c;
-          sq[c0 + i] = fmaf(c, c, sq[c0 + i]);
-        }
-      }
-      tc_fence_before();
-    };
-
-    if (tid == 0) {
-      fence_async_smem();
-      for (int i = 0; i < kTcStages && i < nsteps; ++i) issue_tma(i);
-    }
-    tma_next = qs;
-    tma_issued = qs + (uint32_t)min(kTcStages, nsteps);
-    for (int i = 0; i < nsteps; ++i) {
-      const uint32_t Q = qs + i;
-      const int s = Q % kTcStages;
-      const int gi = i / nch, ch = i % nch;
-      const uint32_t tb = (gcnt + gi) & 1u;
-      const bool ok = mbar_wait_bounded(&full[s], (Q / kTcStages) & 1u, status);
-      tma_next = Q + 1;
-      // all threads are past the previous epilogue (TMEM reads done) and agree on success
-      if (__syncthreads_or(!ok)) {
-        failed = true;
+    for (uint32_t gc = 0;; ++gc) {
+      const uint32_t b = gc & 1u;
+      if (!mbar_wait_bounded(&afull[b], (gc >> 1) & 1u, status)) {
+        atomicExch(&s_fail, 1);
         break;
       }
+      const GroupRec r = rec[b];
+      if (r.flags & 2) break;
       tc_fence_after();
-      last_commit[s] = Q;
-      if (tid == 0) {
-        const uint32_t d0 = taddr + tb * 5 * kTN;
-        const uint32_t ka = smem_addr(base + (size_t)s * kStageBytes), la = ka + kKBytes;
-        // products: (k-side, l-side) = RR (Re,Re), II (Im,Im), X (Re,Im), Xt (Im,Re),
-        // Q (P,P); the six matrices of a row group are Re hi, Re lo, Im hi, Im lo,
-        // P hi, P lo
+      const uint32_t tb = taddr + ((uint32_t)(32 * q) << 16) + b * 5 * kTN + 24 * h;
+      const float* psg = ps + (long long)r.g * Mp;
+      const int kr = r.k0 + 32 * q + lane;
+      const int lc0 = r.l0 + 24 * h;
+      const float skr = kr < Mp ? __ldg(psg + kr) : 0.f;
+      // two rounds of 12 columns keep the live accumulator values within the
+      // register budget of three warps per scheduler
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int cb = 12 * half;
+        float v[5][12];
 #pragma unroll
         for (int pr = 0; pr < 5; ++pr) {
-          const int pa = pr < 4 ? (pr & 1) : 2;
-          const int pl = pr < 4 ? ((pr ^ (pr >> 1)) & 1) : 2;
-          for (int ps_ = 0; ps_ < passes; ++ps_) {
-            const int ha = (ps_ == 2) ? 1 : 0, hb = (ps_ == 1) ? 1 : 0;
+          float t8[8], t4[4];
+          tmem_ld8(tb + pr * kTN + cb, t8);
+          tmem_ld4(tb + pr * kTN + cb + 8, t4);
 #pragma unroll
-            for (int kst = 0; kst < F::kKsteps; ++kst) {
-              const uint64_t ad = smem_desc(ka + (pa * 2 + ha) * F::kCB + kst * F::kKstepBytes,
-                                            F::kLBO, F::kSBO);
-              const uint64_t bd = smem_desc(la + (pl * 2 + hb) * F::kCB + kst * F::kKstepBytes,
-                                            F::kLBO, F::kSBO);
-              const bool accum = !(ch == 0 && ps_ == 0 && kst == 0);
-              mma_issue(d0 + pr * kTN, ad, bd, idesc, accum, kBF16);
-            }
+          for (int e = 0; e < 8; ++e) v[pr][e] = t8[e];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[pr][8 + e] = t4[e];
+        }
+        // sums of |.|^2 / sqrt 2 of the 12 columns (the same for the whole warp)
+        float sl[12];
+#pragma unroll
+        for (int c = 0; c < 12; c += 4) {
+          const int lc = lc0 + cb + c;
+          if (lc + 3 < Mp) {
+            const float4 w = __ldg(reinterpret_cast<const float4*>(psg + lc));
+            sl[c] = w.x; sl[c + 1] = w.y; sl[c + 2] = w.z; sl[c + 3] = w.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sl[c + e] = (lc + e < Mp) ? __ldg(psg + lc + e) : 0.f;
           }
         }
-        mma_commit(&mma_bar[s]);
-      }
-      if (i > 0) {
-        // the previous step's products are complete: refill its stage, and if it
-        // closed a group, run that group's epilogue while this step's products run
-        const uint32_t Qp = Q - 1;
-        const int sp = Qp % kTcStages;
-        const bool okp = mbar_wait_bounded(&mma_bar[sp], (Qp / kTcStages) & 1u, status);
-        if (__syncthreads_or(!okp)) {
-          failed = true;
-          break;
+        tmem_wait_ld();
+        if (half == 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0)  // this warp has read the buffer
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&aempty[b]))
+                         : "memory");
         }
-        if (tid == 0 && (i - 1) + kTcStages < nsteps) {
-          fence_async_smem();
-          issue_tma((i - 1) + kTcStages);
-        }
-        if ((i - 1) + kTcStages < nsteps) tma_issued = Qp + kTcStages + 1;
-        if (ch == 0) epilogue(ga + gi - 1, (gcnt + gi - 1) & 1u);
-      }
-    }
-    if (!failed && nsteps > 0) {
-      const uint32_t Ql = qs + nsteps - 1;
-      const bool okl = mbar_wait_bounded(&mma_bar[Ql % kTcStages], (Ql / kTcStages) & 1u, status);
-      if (__syncthreads_or(!okl))
-        failed = true;
-      else
-        epilogue(gb - 1, (gcnt + (gb - ga) - 1) & 1u);
-    }
-    if (failed) break;
-    qs += nsteps;
-    gcnt += gb - ga;
-    // flush the item's sums (scaled back by 2 pb) into the float64 accumulators
-    const int k = k0 + 32 * q + lane;
 #pragma unroll
-    for (int c = 0; c < 24; ++c) {
-      const int l = l0 + 24 * h + c;
-      if (k > l || l >= M) continue;
-      const long long o = (long long)k * M + l;
-      atomicAdd(acc + o, (double)sum[c] * scale2pb);
-      atomicAdd(acc + 2 * plane + o, (double)sq[c] * scale2pb * scale2pb);
+        for (int i = 0; i < 12; ++i) {
+          float u = v[0][i] * v[0][i];
+          u = fmaf(v[1][i], v[1][i], u);
+          u = fmaf(v[2][i], v[2][i], u);
+          u = fmaf(v[3][i], v[3][i], u);
+          u = fmaf(skr, sl[i], u);
+          const float c = fmaf(alpha, v[4][i], -u);
+          sum[cb + i] += c;
+          sq[cb + i] = fmaf(c, c, sq[cb + i]);
+        }
+      }
+      if (r.flags & 1) {
+        // end of the item: add the sums (scaled back by 2 pb) to the float64 accumulators
+#pragma unroll
+        for (int c = 0; c < 24; ++c) {
+          const int l = lc0 + c;
+          if (kr <= l && l < M) {
+            const long long o = (long long)kr * M + l;
+            atomicAdd(acc + o, (double)sum[c] * scale2pb);
+            atomicAdd(acc + 2 * plane + o, (double)sq[c] * scale2pb * scale2pb);
+          }
+          sum[c] = sq[c] = 0.f;
+        }
+      }
     }
-  }
-  if (failed && tid == 0) {
-    // drain with bounded waits: the last products committed on each barrier and
-    // the copies issued but not consumed, before the TMEM is freed
-    for (int b = 0; b < kTcStages; ++b)
-      if (last_commit[b] >= 0)
-        mbar_wait_bounded(&mma_bar[b], ((uint32_t)last_commit[b] / kTcStages) & 1u, nullptr);
-    for (uint32_t Q = tma_next; Q < tma_issued; ++Q)
-      mbar_wait_bounded(&full[Q % kTcStages], (Q / kTcStages) & 1u, nullptr);
   }
   tc_fence_before();
   __syncthreads();
