@@ -138,6 +138,8 @@ k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ p
   __shared__ __align__(8) uint64_t afull[2];              // TMEM buffer holds a finished group
   __shared__ __align__(8) uint64_t aempty[2];             // TMEM buffer read by the epilogue
   __shared__ GroupRec rec[2];
+  // sums of |.|^2 / sqrt 2 of the group in each TMEM buffer: 128 k-bins, then 48 l-bins
+  __shared__ __align__(16) float psb[2][kTM + kTN];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -217,12 +219,22 @@ k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ p
           const int ch = i % nch, gi = i / nch;
           const uint32_t b = (gc + gi) & 1u;
           if (ch == 0) {
-            // the TMEM buffer is free once the epilogue has read the group before last
+            // the TMEM buffer (and its slot of P sums) is free once the epilogue has
+            // read the group before last
             const uint32_t use = (gc + gi) >> 1;  // earlier uses of buffer b
             if (use > 0 && !mbar_wait_bounded(&aempty[b], (use - 1) & 1u, status)) {
               ok = false;
               break;
             }
+            // stage the group's P sums for the epilogue; the copies count on afull[b]
+            const float* psg = ps + (long long)(ga + gi) * Mp;
+            const uint32_t pk = (uint32_t)min(kTM, Mp - k0) * 4u, pl = (uint32_t)min(kTN, Mp - l0) * 4u;
+            asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(
+                             smem_addr(&afull[b])),
+                         "r"(pk + pl)
+                         : "memory");
+            tma_load_1d(&psb[b][0], psg + k0, pk, &afull[b]);
+            tma_load_1d(&psb[b][kTM], psg + l0, pl, &afull[b]);
           }
           if (!mbar_wait_bounded(&full[s], (q / kTcStages) & 1u, status)) {
             ok = false;
@@ -305,10 +317,9 @@ k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ p
       if (r.flags & 2) break;
       tc_fence_after();
       const uint32_t tb = taddr + ((uint32_t)(32 * q) << 16) + b * 5 * kTN + 24 * h;
-      const float* psg = ps + (long long)r.g * Mp;
       const int kr = r.k0 + 32 * q + lane;
       const int lc0 = r.l0 + 24 * h;
-      const float skr = kr < Mp ? __ldg(psg + kr) : 0.f;
+      const float skr = psb[b][32 * q + lane];
       // two rounds of 12 columns keep the live accumulator values within the
       // register budget of three warps per scheduler
 #pragma unroll
@@ -329,14 +340,8 @@ k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ p
         float sl[12];
 #pragma unroll
         for (int c = 0; c < 12; c += 4) {
-          const int lc = lc0 + cb + c;
-          if (lc + 3 < Mp) {
-            const float4 w = __ldg(reinterpret_cast<const float4*>(psg + lc));
-            sl[c] = w.x; sl[c + 1] = w.y; sl[c + 2] = w.z; sl[c + 3] = w.w;
-          } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) sl[c + e] = (lc + e < Mp) ? __ldg(psg + lc + e) : 0.f;
-          }
+          const float4 w = *reinterpret_cast<const float4*>(&psb[b][kTM + 24 * h + cb + c]);
+          sl[c] = w.x; sl[c + 1] = w.y; sl[c + 2] = w.z; sl[c + 3] = w.w;
         }
         tmem_wait_ld();
         if (half == 1) {
