@@ -46,22 +46,35 @@ struct Combo {
   int c[4];
 };
 
-// Optional second output of K1 for the tensor-core S4 kernel: per channel,
-// group and chunk of FC frames (zero-padded to 16), the hi/lo split of Re, Im
-// and |.|^2 of the centred coefficients, laid out as the tensor cores read
-// K-major operands: rows (bins) in groups of 8; for each row group the six
-// matrices (Re hi, Re lo, Im hi, Im lo, P hi, P lo) of `CB` bytes each, where a
-// matrix holds the row group's core matrices (8 rows x 16 bytes) for
-// consecutive 16-byte frame groups, 128 bytes apart (TF32: 4 frame groups,
-// CB = 512; BF16: 2, CB = 256).  ps holds sum_j |.|^2 / sqrt 2 per bin.
-enum { kImageNone = 0, kImageTF32 = 1, kImageBF16 = 2 };
+// Optional second output of K1 for the tensor-core S4 kernel: the operand
+// image of the weighted frame Gram of every bin.  With centred coefficients d_j
+// of a group, G_jj' = Re(d_j d_j'*), the bracket of the factorised fourth
+// k-statistic (App. H, Eq. 85) for the cut (a_k, a_k*, a_l, a_l*) is
+//   m(m+1) Q - (m-1)(|U|^2 + |V|^2) = sum_{j<=j'} w_jj' G^k_jj' G^l_jj',
+//   w_jj = m^2 - m + 2,  w_jj' = -4(m-1) (j < j'),
+// one real contraction over K = m(m+1)/2, and c4 = r [that - (m-1) Sk Sl] with
+// r = 1/((m-1)(m-2)(m-3)), Sk = sum_j |d_jk|^2.  The K entries come in chunks
+// of 16: the diagonal chunks first, scaled by sd = sqrt(w_jj r), then the pairs
+// j < j' in lexicographic order, scaled by so = sqrt(4(m-1) r) (the
+// tensor-core kernel negates the pair chunks), zero-padded.  Each entry is
+// split hi + lo.  Layout per channel and group: rows (bins) in groups of 8;
+// per row group, for each chunk, a hi block and a lo block of CB bytes, each
+// holding the row group's core matrices (8 rows x 16 bytes) of the chunk's
+// 16-byte entry groups 128 bytes apart (TF32: CB = 512; BF16: CB = 256).  So a
+// chunk of a row group is 2 CB bytes, a row group rg_bytes = nkc * 2 CB, a
+// group group_bytes = (Mp / 8) * rg_bytes.  ps holds sp * Sk per bin,
+// sp = sqrt((m-1) r), so that the contraction minus ps_k ps_l is c4.
+enum { kImageNone = 0, kImageGramTF32 = 1, kImageGramBF16 = 2 };
+constexpr int kMaxGramM = 32;  // largest m of the tensor-core S4 path
 struct OperandImage {
   void* img = nullptr;
   float* ps = nullptr;
   int fmt = kImageNone;
-  int FC = 0, nch = 0;
-  long long chunk_bytes = 0;  // (Mp / 8) * 6 * CB
-  long long chan_bytes = 0;   // Gb_max * nch * chunk_bytes
+  int nkc = 0, ndc = 0;       // K chunks, of which diagonal
+  float sd = 0.f, so = 0.f, sp = 0.f;
+  long long rg_bytes = 0;     // nkc * 2 * CB
+  long long group_bytes = 0;  // (Mp / 8) * rg_bytes
+  long long chan_bytes = 0;   // Gb_max * group_bytes
   long long chan_ps = 0;      // Gb_max * Mp floats
 };
 
@@ -97,13 +110,18 @@ cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, i
                               cudaStream_t stream);
 
 // Tensor-core form of K3 (SS_PREC_TF32X3, SS_PREC_BF16X3, SS_PREC_BF16): tiles of
-// 128 k-bins x 48 l-bins fed from K1's operand image of `channel`.
-constexpr int kTcTileM = 128, kTcTileN = 48;
-cudaError_t launch_k3_trispec_tc(const OperandImage& oi, int channel, int G, int m, int M, int Mp,
+// 128 x 128 (k, l) bins, the weighted frame-Gram contraction fed from K1's
+// operand image of `channel` through tm_img, a 4-D view of that channel's
+// image [group][row group][chunk][2 CB bytes] in 8-byte elements with boxes of
+// k3tc_stage_chunks(precision) chunks x 16 row groups; needs 4 <= m <= kMaxGramM.
+constexpr int kTcTileM = 128, kTcTileN = 128;
+cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm_img, const OperandImage& oi, int channel,
+                                 int G, int m, int M, int Mp,
                                  const TileInfo* tiles, int n_tiles, int precision, double* acc,
                                  long long plane, int nsm, int* counter, int* status,
                                  cudaStream_t stream);
 size_t k3tc_smem_bytes(int precision);
+int k3tc_stage_chunks(int precision);
 
 // Groups per work item: about 16 items per CTA, whole groups, at least one.
 inline int work_group_chunk(int G, int n_tiles, int n_cta) {
@@ -127,6 +145,7 @@ cudaError_t launch_k4_finalize(const double* acc, int n_combos, int rows, int M,
 enum { kLayoutVector = 0,       // S2: [M]
        kLayoutS3Single = 1,     // one channel, computed for k <= l, mirrored; k+l <= M-1
        kLayoutS4Single = 2,     // one channel, computed for k <= l, mirrored
-       kLayoutCross = 3 };      // full [2M-1][M] grid, no mirroring
+       kLayoutCross = 3,        // full [2M-1][M] grid, no mirroring
+       kLayoutS4Lower = 4 };    // one channel, point (k, l), k <= l, stored at [l][k]
 
 }  // namespace ss

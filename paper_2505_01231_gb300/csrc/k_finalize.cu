@@ -6,8 +6,9 @@
 //   mean = norm sum / G
 //   err  = sqrt( G/(G-1) (norm^2 sumsq / G - mean^2) / G )   (Eq. 35-36)
 // for the real and the imaginary part.  One-channel grids that were computed
-// on the k <= l half are mirrored with S(k, l) = S(l, k) (Sec. 9); bispectrum
-// points with k + l > M-1 are set to zero.
+// on the k <= l half are mirrored with S(k, l) = S(l, k) (Sec. 9), whether the
+// sums of (k, l) are stored at [k][l] or at [l][k]; bispectrum points with
+// k + l > M-1 are set to zero.
 #include "internal.cuh"
 
 namespace ss {
@@ -32,6 +33,8 @@ __global__ void k4_finalize(const double* __restrict__ acc, int n_combos, int ro
       if (r > l) { const int t = r; r = l; l = t; }
     } else if (layout == kLayoutS4Single) {
       if (r > l) { const int t = r; r = l; l = t; }
+    } else if (layout == kLayoutS4Lower) {
+      if (r < l) { const int t = r; r = l; l = t; }
     }
     double mr = 0.0, mi = 0.0, er = 0.0, ei = 0.0;
     if (!zero) {

@@ -104,66 +104,46 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return t;
 }
 
-// Write one bin's row of one frame chunk (16 frames, zero-padded) of the
-// operand image: the hi and lo parts of Re, Im and |.|^2 of the centred
-// coefficients in the K-major core-matrix layout the tensor cores read
-// (8 rows x 16 bytes per core matrix, frame groups of 16 bytes 128 bytes apart).
+// Write one bin's row of one K chunk (16 entries) of the Gram operand image:
+// the hi and lo parts of the entries, in the K-major core-matrix layout the
+// tensor cores read (8 rows x 16 bytes per core matrix, 16-byte entry groups
+// 128 bytes apart; the hi block of a row group's chunk is followed by its lo
+// block).  `row` is the bin's 16-byte slot in the chunk's first hi matrix.
 template <int FMT>
-__device__ __forceinline__ void write_image_row(unsigned char* base, int k, const float (&re)[16],
-                                                const float (&im)[16]) {
-  constexpr uint32_t CB = FMT == kImageTF32 ? 512u : 256u;
-  unsigned char* row = base + (size_t)(k >> 3) * 6 * CB + (k & 7) * 16;
-  if constexpr (FMT == kImageTF32) {
+__device__ __forceinline__ void write_gram_row(unsigned char* row, const float (&e)[16]) {
+  constexpr uint32_t CB = FMT == kImageGramTF32 ? 512u : 256u;
+  if constexpr (FMT == kImageGramTF32) {
 #pragma unroll
     for (int kg = 0; kg < 4; ++kg) {
-      uint32_t w[6][4];
+      uint32_t hi[4], lo[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float x = re[4 * kg + e], y = im[4 * kg + e];
-        const float p = fmaf(x, x, y * y);
-        w[0][e] = to_tf32(x);
-        w[1][e] = to_tf32(x - __uint_as_float(w[0][e]));
-        w[2][e] = to_tf32(y);
-        w[3][e] = to_tf32(y - __uint_as_float(w[2][e]));
-        w[4][e] = to_tf32(p);
-        w[5][e] = to_tf32(p - __uint_as_float(w[4][e]));
+      for (int t = 0; t < 4; ++t) {
+        hi[t] = to_tf32(e[4 * kg + t]);
+        lo[t] = to_tf32(e[4 * kg + t] - __uint_as_float(hi[t]));
       }
-#pragma unroll
-      for (int mt = 0; mt < 6; ++mt)
-        *reinterpret_cast<uint4*>(row + mt * CB + kg * 128) =
-            make_uint4(w[mt][0], w[mt][1], w[mt][2], w[mt][3]);
+      *reinterpret_cast<uint4*>(row + kg * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(row + CB + kg * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
   } else {
 #pragma unroll
     for (int kg = 0; kg < 2; ++kg) {
-      uint32_t w[6][4];
+      uint32_t hi[4], lo[4];
 #pragma unroll
-      for (int e = 0; e < 8; e += 2) {
-        uint32_t hh[6], ll[6];
+      for (int t = 0; t < 4; ++t) {
+        uint32_t h2[2], l2[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          const float x = re[8 * kg + e + u], y = im[8 * kg + e + u];
-          const float v[3] = {x, y, fmaf(x, x, y * y)};
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(v[q]);
-            const __nv_bfloat16 l = __float2bfloat16_rn(v[q] - __bfloat162float(h));
-            if (u == 0) {
-              hh[2 * q] = __bfloat16_as_ushort(h);
-              hh[2 * q + 1] = __bfloat16_as_ushort(l);
-            } else {
-              ll[2 * q] = __bfloat16_as_ushort(h);
-              ll[2 * q + 1] = __bfloat16_as_ushort(l);
-            }
-          }
+          const float v = e[8 * kg + 2 * t + u];
+          const __nv_bfloat16 h = __float2bfloat16_rn(v);
+          const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+          h2[u] = __bfloat16_as_ushort(h);
+          l2[u] = __bfloat16_as_ushort(l);
         }
-#pragma unroll
-        for (int mt = 0; mt < 6; ++mt) w[mt][e / 2] = hh[mt] | (ll[mt] << 16);
+        hi[t] = h2[0] | (h2[1] << 16);
+        lo[t] = l2[0] | (l2[1] << 16);
       }
-#pragma unroll
-      for (int mt = 0; mt < 6; ++mt)
-        *reinterpret_cast<uint4*>(row + mt * CB + kg * 128) =
-            make_uint4(w[mt][0], w[mt][1], w[mt][2], w[mt][3]);
+      *reinterpret_cast<uint4*>(row + kg * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(row + CB + kg * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
   }
 }
@@ -244,8 +224,6 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
       // operand image, also write the split tensor-core operands chunk by chunk
       const float inv_m = 1.0f / (float)m;
       const int ia = s2_auto[c];
-      const int nch = FMT != kImageNone ? oi.nch : 1;
-      const int FC = FMT != kImageNone ? oi.FC : m;
       for (int k = threadIdx.x; k < Mp; k += blockDim.x) {
         const bool valid = k < M;
         const float2 mean = valid ? make_float2(gsum[k].x * inv_m, gsum[k].y * inv_m)
@@ -259,28 +237,50 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
             p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
           }
         } else {
-          for (int ch = 0; ch < nch; ++ch) {
-            const int j0 = ch * FC;
-            const int nfc = min(FC, m - j0);
-            float re[16], im[16];
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              float2 d = make_float2(0.f, 0.f);
-              if (e < nfc) {
-                float2* ep = grow + (long long)(j0 + e) * Mp + k;
-                if (valid) d = csub(*ep, mean);
-                *ep = d;
-              }
-              re[e] = d.x;
-              im[e] = d.y;
-              p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
-            }
-            unsigned char* base = static_cast<unsigned char*>(oi.img) +
-                                  (size_t)c * oi.chan_bytes +
-                                  ((size_t)g * nch + ch) * oi.chunk_bytes;
-            write_image_row<FMT>(base, k, re, im);
+          // centred samples of this bin, then the weighted Gram entries in K order:
+          // diagonal chunks (sqrt(m^2-m+2) |d_j|^2), then the pairs j < j'
+          // (sqrt(4(m-1)) Re(d_j d_j'*)), 16 per chunk, zero-padded
+          float dr[kMaxGramM], di[kMaxGramM];
+          for (int j = 0; j < m; ++j) {
+            float2* ep = grow + (long long)j * Mp + k;
+            const float2 d = valid ? csub(*ep, mean) : make_float2(0.f, 0.f);
+            *ep = d;
+            dr[j] = d.x;
+            di[j] = d.y;
+            p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
           }
-          oi.ps[(long long)c * oi.chan_ps + (long long)g * Mp + k] = p * 0.70710678118654752f;
+          const int npair = m * (m - 1) / 2;
+          int pj = 0, pk = 1;  // next off-diagonal pair (j, j'), lexicographic
+          constexpr int kChunkBytes = FMT == kImageGramTF32 ? 1024 : 512;  // 2 CB
+          unsigned char* rbase = static_cast<unsigned char*>(oi.img) + (size_t)c * oi.chan_bytes +
+                                 (size_t)g * oi.group_bytes + (size_t)(k >> 3) * oi.rg_bytes +
+                                 (k & 7) * 16;
+          for (int ch = 0; ch < oi.nkc; ++ch) {
+            float e[16];
+            if (ch < oi.ndc) {
+#pragma unroll
+              for (int t = 0; t < 16; ++t) {
+                const int j = ch * 16 + t;
+                e[t] = j < m ? oi.sd * fmaf(dr[j], dr[j], di[j] * di[j]) : 0.f;
+              }
+            } else {
+              const int p0 = (ch - oi.ndc) * 16;
+#pragma unroll
+              for (int t = 0; t < 16; ++t) {
+                if (p0 + t < npair) {
+                  e[t] = oi.so * fmaf(dr[pj], dr[pk], di[pj] * di[pk]);
+                  if (++pk == m) {
+                    ++pj;
+                    pk = pj + 1;
+                  }
+                } else {
+                  e[t] = 0.f;
+                }
+              }
+            }
+            write_gram_row<FMT>(rbase + ch * kChunkBytes, e);
+          }
+          oi.ps[(long long)c * oi.chan_ps + (long long)g * Mp + k] = oi.sp * p;
         }
         if (valid && ia >= 0) {
           const float c2 = p * pref2;
@@ -367,18 +367,18 @@ cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G,
   if (grid > G) grid = G;
   const bool f32 = src.dtype == SS_F32;
   switch (oi.fmt) {
-    case kImageTF32:
-      return f32 ? launch_k1_t<SS_F32, kImageTF32>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+    case kImageGramTF32:
+      return f32 ? launch_k1_t<SS_F32, kImageGramTF32>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
                                                    spec_chan_stride, s2_auto, acc2, n_s2, pref2,
                                                    oi, grid, smem, stream)
-                 : launch_k1_t<SS_I16, kImageTF32>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+                 : launch_k1_t<SS_I16, kImageGramTF32>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
                                                    spec_chan_stride, s2_auto, acc2, n_s2, pref2,
                                                    oi, grid, smem, stream);
-    case kImageBF16:
-      return f32 ? launch_k1_t<SS_F32, kImageBF16>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+    case kImageGramBF16:
+      return f32 ? launch_k1_t<SS_F32, kImageGramBF16>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
                                                    spec_chan_stride, s2_auto, acc2, n_s2, pref2,
                                                    oi, grid, smem, stream)
-                 : launch_k1_t<SS_I16, kImageBF16>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+                 : launch_k1_t<SS_I16, kImageGramBF16>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
                                                    spec_chan_stride, s2_auto, acc2, n_s2, pref2,
                                                    oi, grid, smem, stream);
     default:

@@ -1,85 +1,80 @@
-// k_trispec_tc.cu -- K3 on the tensor cores: the fourth-order moment sums of the
-// trispectrum cut (Eq. 31, factorised estimator of App. H, Eq. 85) as tcgen05
-// matrix products with accumulators in TMEM.
+// k_trispec_tc.cu -- K3 on the tensor cores: the trispectrum cut (Eq. 31) with
+// the factorised fourth k-statistic (App. H, Eq. 85) as one tcgen05 contraction
+// per group, with accumulators and running sums in TMEM.
 //
-// Per group and per 128 x 48 tile of (k, l), with centred coefficients
-// da = ar + j ai and P = |da|^2 over the group's frames j (the K dimension):
-//   RR = Ar_k^T Ar_l, II = Ai_k^T Ai_l, X = Ar_k^T Ai_l, Xt = Ai_k^T Ar_l,
-//   Q' = (alpha P_k)^T P_l,  alpha = m(m+1) / (2(m-1)),
-// five real products of [128 x K] by [K x 48].  Then
-//   c4 / (2 pb) = Q' - (Sk/sqrt2)(Sl/sqrt2) - (RR^2 + II^2 + X^2 + Xt^2),
-// pb = 1/((m-2)(m-3)), Sk = sum_j P_jk, which is the factorised c4 of Eq. 85
-// (the same algebra as the CUDA-core kernel k_trispec.cu, with the prefactors
-// folded into the operands); the 2 pb factor is applied when the sums are
-// flushed.
+// With the centred coefficients d_j of a group and the frame Gram of bin k,
+// G^k_jj' = Re(d_jk d_j'k*), the bracket of Eq. 85 for (a_k, a_k*, a_l, a_l*) is
+//   B(k, l) = m(m+1) sum_j P_jk P_jl - (m-1)(|U|^2 + |V|^2)
+//           = sum_{j<=j'} w_jj' G^k_jj' G^l_jj',
+//   w_jj = m^2 - m + 2,  w_jj' = -4(m-1) for j < j',
+// with P = |d|^2, U = sum_j d_jk d_jl, V = sum_j d_jk d_jl* (the cross terms of
+// |U|^2 + |V|^2 regroup as 2 sum_{j,j'} G^k_jj' G^l_jj'), and
+//   c4 = [B(k, l) - (m-1) Sk Sl] / ((m-1)(m-2)(m-3)),  Sk = sum_j P_jk.
+// K1 writes the operand image of sqrt(|w| r) G (K = m(m+1)/2 entries in
+// chunks of 16, see OperandImage), r = 1/((m-1)(m-2)(m-3)), and
+// ps = sqrt((m-1) r) Sk, so that D - ps_k ps_l is c4 itself.  This kernel forms
+// D = A_k A_l^T over K for every 128 x 128 tile of (k, l), negating the pair
+// chunks through the MMA's negate-A bit, in FP32 accumulators in TMEM.
+// Operands are split hi + lo (TF32 or BF16) and each chunk takes three MMAs
+// hi*hi + hi*lo + lo*hi (one in the plain BF16 mode).
 //
-// Precision: operands are split as x = hi + lo in TF32 (or BF16) and each
-// product is formed from three MMAs hi*hi + hi*lo + lo*hi accumulated in FP32
-// in TMEM (one MMA per product in the plain BF16 mode).
-//
-// The operands come ready-made: K1 writes, once per group and chunk of <= 16
-// frames, the hi/lo parts of Re, Im and |.|^2 in the K-major core-matrix layout
-// the tensor cores read (the "operand image", see OperandImage), and the sums
-// sum_j |.|^2 / sqrt2 per bin.
-//
-// Warp roles (288 threads).  Warp 8, the producer: takes (group chunk, tile)
-// items from the queue; for every step = (group, chunk of <= 16 frames) it
-// issues 1-D TMA bulk copies of the image rows of the 128 bins at k0 and the 48
-// at l0 into one of kTcStages stages, then the 30 (or 15 / 5) MMAs straight
-// from the stage into the group's TMEM buffer (two buffers of 5 x 48 columns),
-// commits them to the stage's mbarrier (stage reuse) and, after the group's last
-// chunk, to the buffer's "full" mbarrier with a record of the group in shared
-// memory.  Warps 0-7, the epilogue: for each group in order they wait for its
-// buffer, read the five accumulators from TMEM (tcgen05.ld, TMEM lane quadrant
-// = warp % 4, column half = warp / 4), form c4 and update the float32 sums of
-// their 24 grid points, release the buffer, and at the end of an item add the
-// sums to the float64 accumulators.  Producer and epilogue meet only on
-// mbarriers, so copies, products and epilogue of consecutive groups overlap.
-// Every wait is bounded; on a failure the CTA stops, drains its copies and
-// products and frees its TMEM before returning.
-#include <cuda_bf16.h>
-
+// Warp roles (320 threads), coupled only by mbarriers.  Warp 8, TMA: takes
+// (group chunk, tile) items from the queue; per group it loads the group's ps
+// values for the tile into a ring of kPsSlots slots with a record of the group,
+// and per stage (group, kChunks consecutive K chunks) it loads two boxes of the
+// operand image through a 4-D tensor map: the 16 row groups of the k-block and
+// the 16 of the l-block.  Warp 9, MMA: per stage it issues the MMAs of its
+// chunks into the group's TMEM buffer (two buffers of 128 columns), commits
+// them to the stage's barrier (the stage is then free for the next load) and,
+// after the group's last stage, to the buffer's barrier.  Warps 0-7, the
+// epilogue: TMEM lane quadrant warp % 4, column half warp / 4.  For each group
+// they read D, form c4 and update the running sum and sum of squares of their
+// 64 grid points, which stay in TMEM columns 256-511; at the end of an item they
+// add them to the float64 accumulators.  Tiles of the last l-block are as
+// narrow as the bins left (N a multiple of 16).  Every wait is bounded; on a
+// failure the CTA stops, drains its copies and products and frees its TMEM.
 #include "internal.cuh"
 #include "pipeline.cuh"
 
 namespace ss {
 namespace {
 
-constexpr int kTM = 128, kTN = 48, kKpad = 16, kTcThreads = 288, kEpiWarps = 8;
-constexpr int kTcStages = 3;
-constexpr uint32_t kTmemCols = 512;  // two buffers of 5 x 48 fp32 columns
+constexpr int kTM = 128, kTN = 128, kEpiWarps = 8, kTcThreads = 32 * (kEpiWarps + 2);
+constexpr uint32_t kTmemCols = 512;  // D0 | D1 | running sum | running sum of squares
+constexpr uint32_t kColSum = 256, kColSq = 384;
 
-// Operand formats.  A matrix of a row group is CB bytes: its core matrices
-// (8 rows x 16 bytes) for consecutive 16-byte frame groups, 128 bytes apart
-// (LBO); consecutive row groups are 6 CB apart (SBO, the six matrices of a row
-// group are adjacent).
+// Operand formats.  In the image and in a stage, a row group (8 bins) holds,
+// per K chunk, a hi block and a lo block of CB bytes; a block holds the core
+// matrices (8 rows x 16 bytes) of the chunk's 16-byte entry groups, 128 bytes
+// apart (LBO).  A stage holds kChunks chunks of 16 row groups, so row groups
+// are kChunks * 2 CB apart (SBO).  Every stage is 64 KB.
 template <bool kBF16>
 struct OpFmt;
 
 template <>
-struct OpFmt<false> {  // TF32 operands, K = 8 per MMA
-  static constexpr uint32_t kCB = 512, kLBO = 128, kSBO = 6 * 512, kKstepBytes = 256;
-  static constexpr int kKsteps = 2;
+struct OpFmt<false> {  // TF32: K = 8 per MMA, two K steps of two core matrices
+  static constexpr uint32_t kCB = 512, kKstepBytes = 256;
+  static constexpr int kKsteps = 2, kChunks = 2, kStages = 3;
   static constexpr uint32_t kIdescAB = (2u << 7) | (2u << 10);
 };
 
 template <>
-struct OpFmt<true> {  // BF16 operands, K = 16 per MMA
-  static constexpr uint32_t kCB = 256, kLBO = 128, kSBO = 6 * 256, kKstepBytes = 0;
-  static constexpr int kKsteps = 1;
+struct OpFmt<true> {  // BF16: K = 16 per MMA, one K step
+  static constexpr uint32_t kCB = 256, kKstepBytes = 0;
+  static constexpr int kKsteps = 1, kChunks = 4, kStages = 3;
   static constexpr uint32_t kIdescAB = (1u << 7) | (1u << 10);
 };
 
+// Shared-memory matrix descriptor, no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  // start address, leading / stride byte offsets (>> 4), descriptor version 1,
-  // no swizzle
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
          ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
 
+template <bool kBF16>
 __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                          bool accumulate, bool bf16) {
-  if (bf16)
+                                          bool accumulate) {
+  if constexpr (kBF16)
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -98,65 +93,89 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                 "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
-  uint32_t r[4];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Record of a group for the epilogue, delivered with its ps values.
 struct GroupRec {
-  int k0, l0, g, flags;  // flags: 1 = last group of its item, 2 = stop
+  int k0, l0, n, flags;  // n = tile columns; flags: 1 = last group of its item, 2 = stop
 };
+
+constexpr int kPsSlots = 8;  // ring of per-group ps values and records (a power of two)
 
 template <bool kBF16>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ ps, int G, int m,
-              int nch, int M, int Mp, long long chunk_bytes, const TileInfo* __restrict__ tiles,
-              WorkQueue wq, float alpha, float scale2pb, int passes, double* __restrict__ acc,
-              long long plane, int* __restrict__ status) {
+k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restrict__ ps, int G,
+              int nkc, int ndc, int M, int Mp, const TileInfo* __restrict__ tiles, WorkQueue wq,
+              int passes, double* __restrict__ acc, long long plane, int* __restrict__ status) {
   using F = OpFmt<kBF16>;
+  constexpr int S = F::kStages, KC = F::kChunks;
+  constexpr uint32_t kChunkBytes = 2 * F::kCB;               // hi and lo blocks of a chunk
+  constexpr uint32_t kRowGroupBytes = KC * kChunkBytes;      // a row group in a stage
+  constexpr uint32_t kABytes = (kTM / 8) * kRowGroupBytes;   // box of 16 row groups
+  constexpr uint32_t kStageBytes = 2 * kABytes;
   extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
-  __shared__ __align__(8) uint64_t full[kTcStages];       // stage loaded (TMA)
-  __shared__ __align__(8) uint64_t sdone[kTcStages];      // stage's products complete
-  __shared__ __align__(8) uint64_t afull[2];              // TMEM buffer holds a finished group
-  __shared__ __align__(8) uint64_t aempty[2];             // TMEM buffer read by the epilogue
-  __shared__ GroupRec rec[2];
-  // sums of |.|^2 / sqrt 2 of the group in each TMEM buffer: 128 k-bins, then 48 l-bins
-  __shared__ __align__(16) float psb[2][kTM + kTN];
+  __shared__ __align__(8) uint64_t full[S];             // stage loaded (TMA)
+  __shared__ __align__(8) uint64_t sdone[S];            // stage's products complete
+  __shared__ __align__(8) uint64_t psfull[kPsSlots];    // ps slot loaded (TMA)
+  __shared__ __align__(8) uint64_t psempty[kPsSlots];   // ps slot read by the epilogue
+  __shared__ __align__(8) uint64_t afull[2];            // TMEM buffer holds a finished group
+  __shared__ __align__(8) uint64_t aempty[2];           // TMEM buffer read by the epilogue
+  __shared__ int sinfo[S];  // stage record: first K chunk | tile columns << 16; -1 = stop
+  __shared__ GroupRec prec[kPsSlots];
+  __shared__ __align__(16) float psr[kPsSlots][kTM + kTN];  // ps: k rows, then l columns
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr uint32_t kRowGroupBytes = 6 * F::kCB;
-  constexpr uint32_t kKBytes = (kTM / 8) * kRowGroupBytes;   // 16 row groups at k0
-  constexpr uint32_t kLBytes = (kTN / 8) * kRowGroupBytes;   // 6 row groups at l0
-  constexpr uint32_t kStageBytes = kKBytes + kLBytes;
   unsigned char* base = align1024<unsigned char>(smem_raw);
-  const int R = Mp / 8;  // row groups per chunk of the image
 
   if (tid == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&sdone[s], 1);
     }
+    for (int p = 0; p < kPsSlots; ++p) {
+      mbar_init(&psfull[p], 1);
+      mbar_init(&psempty[p], kEpiWarps);
+    }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&afull[b], 2);  // the products' commit + the producer's record arrive
+      mbar_init(&afull[b], 1);
       mbar_init(&aempty[b], kEpiWarps);
     }
     s_fail = 0;
@@ -175,208 +194,242 @@ k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ p
   const uint32_t taddr = tmem_slot;
 
   if (warp == kEpiWarps) {
-    // ------------------------------------------------------------ producer
+    // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | F::kIdescAB | ((uint32_t)(kTN >> 3) << 17) |
-                             ((uint32_t)(kTM >> 4) << 24);
-      uint32_t Q = 0;      // steps issued (stage Q % kTcStages)
-      uint32_t gc = 0;     // groups issued (TMEM buffer gc % 2)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_img))
+                   : "memory");
+      uint32_t q = 0, gq = 0;  // stages and groups issued
+      int s = 0;               // stage of load q
+      uint32_t ph = 0;         // parity of stage s's current use
       bool ok = true;
-      // per stage: the step last loaded into it (for the stage-reuse wait)
-      long long stage_step[kTcStages];
-      for (int s = 0; s < kTcStages; ++s) stage_step[s] = -1;
-      auto load_step = [&](uint32_t q, int k0, int l0, int g, int ch) -> bool {
-        const int s = q % kTcStages;
-        if (stage_step[s] >= 0 &&  // the stage's previous products must be complete
-            !mbar_wait_bounded(&sdone[s], ((uint32_t)stage_step[s] / kTcStages) & 1u, status))
-          return false;
-        stage_step[s] = q;
-        const uint32_t kb = (uint32_t)min(kTM / 8, R - (k0 >> 3)) * kRowGroupBytes;
-        const uint32_t lb = (uint32_t)min(kTN / 8, R - (l0 >> 3)) * kRowGroupBytes;
-        const unsigned char* src = img + ((size_t)g * nch + ch) * (size_t)chunk_bytes;
-        unsigned char* st = base + (size_t)s * kStageBytes;
-        fence_async_smem();
-        mbar_arrive_expect_tx(&full[s], kb + lb);
-        tma_load_1d(st, src + (size_t)(k0 >> 3) * kRowGroupBytes, kb, &full[s]);
-        tma_load_1d(st + kKBytes, src + (size_t)(l0 >> 3) * kRowGroupBytes, lb, &full[s]);
-        return true;
-      };
       for (;;) {
         const int item = atomicAdd(wq.counter, 1);
         if (item >= wq.n_items || *(volatile int*)&s_fail) break;
         const int t = item % wq.n_tiles;
         const int ga = (item / wq.n_tiles) * wq.group_chunk;
         const int gb = min(G, ga + wq.group_chunk);
-        const int k0 = tiles[t].k0, l0 = tiles[t].l0;
-        const int nsteps = (gb - ga) * nch;
-        // keep kTcStages - 1 steps of copies ahead of the products
-        int loaded = 0;
-        for (; loaded < nsteps && loaded < kTcStages - 1 && ok; ++loaded)
-          ok = load_step(Q + loaded, k0, l0, ga + loaded / nch, loaded % nch);
-        for (int i = 0; i < nsteps && ok; ++i) {
-          const uint32_t q = Q + i;
-          const int s = q % kTcStages;
-          const int ch = i % nch, gi = i / nch;
-          const uint32_t b = (gc + gi) & 1u;
-          if (ch == 0) {
-            // the TMEM buffer (and its slot of P sums) is free once the epilogue has
-            // read the group before last
-            const uint32_t use = (gc + gi) >> 1;  // earlier uses of buffer b
-            if (use > 0 && !mbar_wait_bounded(&aempty[b], (use - 1) & 1u, status)) {
-              ok = false;
-              break;
-            }
-            // stage the group's P sums for the epilogue; the copies count on afull[b]
-            const float* psg = ps + (long long)(ga + gi) * Mp;
-            const uint32_t pk = (uint32_t)min(kTM, Mp - k0) * 4u, pl = (uint32_t)min(kTN, Mp - l0) * 4u;
-            asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(
-                             smem_addr(&afull[b])),
-                         "r"(pk + pl)
-                         : "memory");
-            tma_load_1d(&psb[b][0], psg + k0, pk, &afull[b]);
-            tma_load_1d(&psb[b][kTM], psg + l0, pl, &afull[b]);
-          }
-          if (!mbar_wait_bounded(&full[s], (q / kTcStages) & 1u, status)) {
+        const TileInfo ti = tiles[t];
+        const uint32_t pk = (uint32_t)min(kTM, Mp - ti.k0) * 4u;
+        const uint32_t pl = (uint32_t)min(ti.ncols, Mp - ti.l0) * 4u;
+        const int info0 = ti.ncols << 16;
+        for (int g = ga; g < gb && ok; ++g) {
+          // the group's ps values and record
+          const int p = gq & (kPsSlots - 1);
+          if (gq >= kPsSlots &&
+              !mbar_wait_bounded(&psempty[p], ((gq / kPsSlots) - 1) & 1u, status)) {
             ok = false;
             break;
           }
-          tc_fence_after();
-          const uint32_t d0 = taddr + b * 5 * kTN;
-          const uint32_t ka = smem_addr(base + (size_t)s * kStageBytes), la = ka + kKBytes;
-          // products (k-side, l-side): RR (Re,Re), II (Im,Im), X (Re,Im), Xt (Im,Re),
-          // Q (P,P); a row group's six matrices are Re hi, Re lo, Im hi, Im lo, P hi, P lo
-#pragma unroll
-          for (int pr = 0; pr < 5; ++pr) {
-            const int pa = pr < 4 ? (pr & 1) : 2;
-            const int pl = pr < 4 ? ((pr ^ (pr >> 1)) & 1) : 2;
-            for (int ps_ = 0; ps_ < passes; ++ps_) {
-              const int ha = (ps_ == 2) ? 1 : 0, hb = (ps_ == 1) ? 1 : 0;
-#pragma unroll
-              for (int kst = 0; kst < F::kKsteps; ++kst) {
-                const uint64_t ad = smem_desc(ka + (pa * 2 + ha) * F::kCB + kst * F::kKstepBytes,
-                                              F::kLBO, F::kSBO);
-                const uint64_t bd = smem_desc(la + (pl * 2 + hb) * F::kCB + kst * F::kKstepBytes,
-                                              F::kLBO, F::kSBO);
-                mma_issue(d0 + pr * kTN, ad, bd, idesc, !(ch == 0 && ps_ == 0 && kst == 0),
-                          kBF16);
-              }
+          prec[p] = GroupRec{ti.k0, ti.l0, ti.ncols, (g == gb - 1) ? 1 : 0};
+          const float* psg = ps + (long long)g * Mp;
+          mbar_arrive_expect_tx(&psfull[p], pk + pl);
+          tma_load_1d(&psr[p][0], psg + ti.k0, pk, &psfull[p]);
+          tma_load_1d(&psr[p][kTM], psg + ti.l0, pl, &psfull[p]);
+          ++gq;
+          // its stages of KC chunks (chunks past nkc and rows past Mp read as zeros)
+          for (int kc0 = 0; kc0 < nkc; kc0 += KC) {
+            if (q >= (uint32_t)S && !mbar_wait_bounded(&sdone[s], ph ^ 1u, status)) {
+              ok = false;
+              break;
             }
-          }
-          mma_commit(&sdone[s]);
-          if (ch == nch - 1) {
-            const int g = ga + gi;
-            rec[b].k0 = k0;
-            rec[b].l0 = l0;
-            rec[b].g = g;
-            rec[b].flags = (g == gb - 1) ? 1 : 0;
-            mma_commit(&afull[b]);  // arrives when the group's products are complete
-            asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
-                             smem_addr(&afull[b]))
-                         : "memory");
-          }
-          // refill the stage freed by the previous step while this step's products run
-          if (loaded < nsteps) {
-            ok = load_step(Q + loaded, k0, l0, ga + loaded / nch, loaded % nch);
-            ++loaded;
+            sinfo[s] = info0 | kc0;
+            unsigned char* st = base + (size_t)s * kStageBytes;
+            mbar_arrive_expect_tx(&full[s], kStageBytes);
+            tma_load_4d(st, &tm_img, 0, kc0, ti.k0 >> 3, g, &full[s]);
+            tma_load_4d(st + kABytes, &tm_img, 0, kc0, ti.l0 >> 3, g, &full[s]);
+            ++q;
+            if (++s == S) {
+              s = 0;
+              ph ^= 1u;
+            }
           }
         }
         if (!ok) break;
-        Q += nsteps;
-        gc += gb - ga;
       }
-      if (!ok) {
-        atomicExch(&s_fail, 1);
-        // drain: every stage's last copy and products, with bounded waits
-        for (int s = 0; s < kTcStages; ++s)
-          if (stage_step[s] >= 0) {
-            mbar_wait_bounded(&full[s], ((uint32_t)stage_step[s] / kTcStages) & 1u, nullptr);
-          }
-      }
-      // stop record: wait until the next buffer is free, then release it without products
-      const uint32_t b = gc & 1u, use = gc >> 1;
-      if (use > 0) mbar_wait_bounded(&aempty[b], (use - 1) & 1u, nullptr);
-      rec[b].flags = 2;
-      asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0], 2;" ::"r"(
-                       smem_addr(&afull[b]))
+      if (!ok) atomicExch(&s_fail, 1);
+      // every copy this warp issued has landed before the CTA may exit (waited
+      // before the stop records below move the barriers to their next phase)
+      for (uint32_t i = q > (uint32_t)S ? q - S : 0; i < q; ++i)
+        mbar_wait_bounded(&full[i % S], (i / S) & 1u, status);
+      for (uint32_t i = gq > (uint32_t)kPsSlots ? gq - kPsSlots : 0; i < gq; ++i)
+        mbar_wait_bounded(&psfull[i % kPsSlots], (i / kPsSlots) & 1u, status);
+      // stop records for the MMA warp and the epilogue (plain arrivals, no bytes)
+      if (q >= (uint32_t)S) mbar_wait_bounded(&sdone[s], ph ^ 1u, status);
+      sinfo[s] = -1;
+      asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
+                       smem_addr(&full[s]))
                    : "memory");
+      const int p = gq & (kPsSlots - 1);
+      if (gq >= kPsSlots) mbar_wait_bounded(&psempty[p], ((gq / kPsSlots) - 1) & 1u, status);
+      prec[p].flags = 2;
+      asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
+                       smem_addr(&psfull[p]))
+                   : "memory");
+    }
+    __syncwarp();
+  } else if (warp == kEpiWarps + 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc0 = (1u << 4) | F::kIdescAB | ((uint32_t)(kTM >> 4) << 24);
+      // descriptors of stage 0; a stage adds kStageBytes >> 4 to the address field
+      const uint64_t a_desc0 = smem_desc(smem_addr(base), 128, kRowGroupBytes);
+      const uint64_t b_desc0 = smem_desc(smem_addr(base) + kABytes, 128, kRowGroupBytes);
+      int s = 0;
+      uint32_t ph = 0;
+      int last_s = -1;
+      uint32_t last_ph = 0;
+      for (uint32_t gc = 0;; ++gc) {
+        const uint32_t b = gc & 1u;
+        const uint32_t d = taddr + b * kTN;
+        uint32_t idesc = 0;
+        bool stop = false;
+        for (int kc0 = 0; kc0 < nkc; kc0 += KC) {
+          if (!mbar_wait_bounded(&full[s], ph, status)) {
+            stop = true;
+            break;
+          }
+          if (kc0 == 0) {
+            const int info = sinfo[s];
+            if (info < 0) {
+              stop = true;
+              break;
+            }
+            idesc = idesc0 | ((uint32_t)((info >> 16) >> 3) << 17);
+            // the buffer is free once the epilogue has read the group before last
+            if (gc >= 2 && !mbar_wait_bounded(&aempty[b], ((gc >> 1) - 1) & 1u, status)) {
+              stop = true;
+              break;
+            }
+          }
+          tc_fence_after();
+          const uint64_t so = (uint64_t)((s * kStageBytes) >> 4);
+          const int nck = min(KC, nkc - kc0);
+          for (int j = 0; j < nck; ++j) {
+            const int kc = kc0 + j;
+            const uint32_t id = kc < ndc ? idesc : (idesc | (1u << 13));  // negate A: pairs
+            const uint64_t co = so + ((j * kChunkBytes) >> 4);
+            for (int pa = 0; pa < passes; ++pa) {
+              const uint64_t ha = (pa == 2) ? (F::kCB >> 4) : 0u;
+              const uint64_t hb = (pa == 1) ? (F::kCB >> 4) : 0u;
+#pragma unroll
+              for (int kst = 0; kst < F::kKsteps; ++kst)
+                mma_issue<kBF16>(d, a_desc0 + co + ha + kst * (F::kKstepBytes >> 4),
+                                 b_desc0 + co + hb + kst * (F::kKstepBytes >> 4), id,
+                                 kc > 0 || pa > 0 || kst > 0);
+            }
+          }
+          mma_commit(&sdone[s]);
+          last_s = s;
+          last_ph = ph;
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (stop) break;
+        mma_commit(&afull[b]);  // arrives when the group's products are complete
+      }
+      if (*(volatile int*)status != 0) atomicExch(&s_fail, 1);
+      // the products issued must be complete before the TMEM is freed
+      if (last_s >= 0) mbar_wait_bounded(&sdone[last_s], last_ph, status);
     }
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3, h = warp >> 2;
-    float sum[24], sq[24];
+    const uint32_t lane_addr = taddr + ((uint32_t)(32 * q) << 16);
+    const int col0 = 64 * h;  // this warp's 64 columns of the tile
+    {
+      float z[32];
 #pragma unroll
-    for (int i = 0; i < 24; ++i) sum[i] = sq[i] = 0.f;
+      for (int i = 0; i < 32; ++i) z[i] = 0.f;
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        tmem_st32(lane_addr + kColSum + col0 + 32 * cc, z);
+        tmem_st32(lane_addr + kColSq + col0 + 32 * cc, z);
+      }
+    }
     for (uint32_t gc = 0;; ++gc) {
+      const int p = gc & (kPsSlots - 1);
       const uint32_t b = gc & 1u;
-      if (!mbar_wait_bounded(&afull[b], (gc >> 1) & 1u, status)) {
-        atomicExch(&s_fail, 1);
+      // one verdict per warp: the TMEM accesses below are warp-collective
+      if (!__all_sync(0xffffffffu,
+                      mbar_wait_bounded(&psfull[p], (gc / kPsSlots) & 1u, status))) {
+        if (lane == 0) atomicExch(&s_fail, 1);
         break;
       }
-      const GroupRec r = rec[b];
+      const GroupRec r = prec[p];
       if (r.flags & 2) break;
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&afull[b], (gc >> 1) & 1u, status))) {
+        if (lane == 0) atomicExch(&s_fail, 1);
+        break;
+      }
       tc_fence_after();
-      const uint32_t tb = taddr + ((uint32_t)(32 * q) << 16) + b * 5 * kTN + 24 * h;
-      const int kr = r.k0 + 32 * q + lane;
-      const int lc0 = r.l0 + 24 * h;
-      const float skr = psb[b][32 * q + lane];
-      // two rounds of 12 columns keep the live accumulator values within the
-      // register budget of three warps per scheduler
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int cb = 12 * half;
-        float v[5][12];
-#pragma unroll
-        for (int pr = 0; pr < 5; ++pr) {
-          float t8[8], t4[4];
-          tmem_ld8(tb + pr * kTN + cb, t8);
-          tmem_ld4(tb + pr * kTN + cb + 8, t4);
-#pragma unroll
-          for (int e = 0; e < 8; ++e) v[pr][e] = t8[e];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) v[pr][8 + e] = t4[e];
-        }
-        // sums of |.|^2 / sqrt 2 of the 12 columns (the same for the whole warp)
-        float sl[12];
-#pragma unroll
-        for (int c = 0; c < 12; c += 4) {
-          const float4 w = *reinterpret_cast<const float4*>(&psb[b][kTM + 24 * h + cb + c]);
-          sl[c] = w.x; sl[c + 1] = w.y; sl[c + 2] = w.z; sl[c + 3] = w.w;
-        }
+      tmem_wait_st();  // the previous group's running sums are stored
+      const float skr = psr[p][32 * q + lane];
+      // 32-column blocks of this warp that meet the tile (columns past its width
+      // hold no products; their sums are never flushed)
+      const int ncc = min(2, max(0, (r.n - col0 + 31) >> 5));
+#pragma unroll 1
+      for (int cc = 0; cc < ncc; ++cc) {
+        const uint32_t col = col0 + 32 * cc;
+        float d[32], sm[32], sq[32];
+        tmem_ld32(lane_addr + b * kTN + col, d);
+        tmem_ld32(lane_addr + kColSum + col, sm);
+        tmem_ld32(lane_addr + kColSq + col, sq);
         tmem_wait_ld();
-        if (half == 1) {
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0)  // this warp has read the buffer
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&aempty[b]))
-                         : "memory");
-        }
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
-          float u = v[0][i] * v[0][i];
-          u = fmaf(v[1][i], v[1][i], u);
-          u = fmaf(v[2][i], v[2][i], u);
-          u = fmaf(v[3][i], v[3][i], u);
-          u = fmaf(skr, sl[i], u);
-          const float c = fmaf(alpha, v[4][i], -u);
-          sum[cb + i] += c;
-          sq[cb + i] = fmaf(c, c, sq[cb + i]);
+        for (int c = 0; c < 32; c += 4) {
+          const float4 w = *reinterpret_cast<const float4*>(&psr[p][kTM + col + c]);
+          const float sl[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float v = fmaf(-skr, sl[i], d[c + i]);  // c4 = r (B(k, l) - (m-1) Sk Sl)
+            sm[c + i] += v;
+            sq[c + i] = fmaf(v, v, sq[c + i]);
+          }
         }
+        tmem_st32(lane_addr + kColSum + col, sm);
+        tmem_st32(lane_addr + kColSq + col, sq);
+      }
+      // this warp has read its part of the buffer and of the ps slot
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&aempty[b]))
+                     : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&psempty[p]))
+                     : "memory");
       }
       if (r.flags & 1) {
-        // end of the item: add the sums (scaled back by 2 pb) to the float64 accumulators
+        // end of an item: add the sums to the float64 accumulators.  Point (k, l),
+        // k <= l, is stored at [l][k], so a warp's 32 rows k are 32 consecutive
+        // doubles.
+        tmem_wait_st();
+        const int k = r.k0 + 32 * q + lane;
+#pragma unroll 1
+        for (int cc = 0; cc < ncc; ++cc) {
+          const uint32_t col = col0 + 32 * cc;
+          float sm[32], sq[32];
+          tmem_ld32(lane_addr + kColSum + col, sm);
+          tmem_ld32(lane_addr + kColSq + col, sq);
+          tmem_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 24; ++c) {
-          const int l = lc0 + c;
-          if (kr <= l && l < M) {
-            const long long o = (long long)kr * M + l;
-            atomicAdd(acc + o, (double)sum[c] * scale2pb);
-            atomicAdd(acc + 2 * plane + o, (double)sq[c] * scale2pb * scale2pb);
+          for (int i = 0; i < 32; ++i) {
+            const int l = r.l0 + (int)col + i;
+            if (k <= l && l < M) {
+              const long long o = (long long)l * M + k;
+              atomicAdd(acc + o, (double)sm[i]);
+              atomicAdd(acc + 2 * plane + o, (double)sq[i]);
+            }
+            sm[i] = 0.f;
           }
-          sum[c] = sq[c] = 0.f;
+          tmem_st32(lane_addr + kColSum + col, sm);
+          tmem_st32(lane_addr + kColSq + col, sm);
         }
       }
     }
+    tmem_wait_st();
   }
   tc_fence_before();
   __syncthreads();
@@ -387,23 +440,31 @@ k3_trispec_tc(const unsigned char* __restrict__ img, const float* __restrict__ p
   }
 }
 
-size_t tc_smem_bytes(bool bf16) {
-  const size_t cb = bf16 ? OpFmt<true>::kCB : OpFmt<false>::kCB;
-  return (size_t)kTcStages * (kTM / 8 + kTN / 8) * 6 * cb + 1024;
+template <bool kBF16>
+size_t tc_smem_bytes_t() {
+  using F = OpFmt<kBF16>;
+  return (size_t)F::kStages * 2 * (kTM / 8) * F::kChunks * 2 * F::kCB + 1024;
 }
 
 }  // namespace
 
-size_t k3tc_smem_bytes(int precision) { return tc_smem_bytes(precision != SS_PREC_TF32X3); }
+size_t k3tc_smem_bytes(int precision) {
+  return precision == SS_PREC_TF32X3 ? tc_smem_bytes_t<false>() : tc_smem_bytes_t<true>();
+}
 
-cudaError_t launch_k3_trispec_tc(const OperandImage& oi, int channel, int G, int m, int M, int Mp,
-                                 const TileInfo* tiles, int n_tiles, int precision, double* acc,
-                                 long long plane, int nsm, int* counter, int* status,
-                                 cudaStream_t stream) {
+int k3tc_stage_chunks(int precision) {
+  return precision == SS_PREC_TF32X3 ? OpFmt<false>::kChunks : OpFmt<true>::kChunks;
+}
+
+cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm_img, const OperandImage& oi, int channel,
+                                 int G, int m, int M, int Mp, const TileInfo* tiles, int n_tiles,
+                                 int precision, double* acc, long long plane, int nsm,
+                                 int* counter, int* status, cudaStream_t stream) {
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
+  if (m < 4 || m > kMaxGramM || (Mp & 15)) return cudaErrorInvalidValue;
   const bool bf16 = precision != SS_PREC_TF32X3;
   const int passes = precision == SS_PREC_BF16 ? 1 : 3;
-  const size_t smem = tc_smem_bytes(bf16);
+  const size_t smem = k3tc_smem_bytes(precision);
   auto kern = bf16 ? k3_trispec_tc<true> : k3_trispec_tc<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -416,13 +477,9 @@ cudaError_t launch_k3_trispec_tc(const OperandImage& oi, int channel, int G, int
   wq.n_items = n_tiles * ((G + wq.group_chunk - 1) / wq.group_chunk);
   e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
-  const double md = m;
-  const float alpha = (float)(md * (md + 1.0) / (2.0 * (md - 1.0)));
-  const float scale2pb = (float)(2.0 / ((md - 2.0) * (md - 3.0)));
-  const unsigned char* img = static_cast<const unsigned char*>(oi.img) + (size_t)channel * oi.chan_bytes;
   const float* ps = oi.ps + (size_t)channel * oi.chan_ps;
-  kern<<<n_cta, kTcThreads, smem, stream>>>(img, ps, G, m, oi.nch, M, Mp, oi.chunk_bytes, tiles, wq,
-                                            alpha, scale2pb, passes, acc, plane, status);
+  kern<<<n_cta, kTcThreads, smem, stream>>>(tm_img, ps, G, oi.nkc, oi.ndc, M, Mp, tiles, wq,
+                                            passes, acc, plane, status);
   return cudaGetLastError();
 }
 

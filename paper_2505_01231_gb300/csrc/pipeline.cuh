@@ -86,6 +86,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// 4-D tiled TMA load (coordinates {x, y, z, w}).
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            int w, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_addr(bar))
+      : "memory");
+}
+
 // Byte offset, inside a 1024-byte aligned shared buffer written by a TMA load
 // with 128-byte swizzling, of the 16-byte chunk holding logical offset `off`:
 // the chunk index (bits 4-6) is XOR-ed with the 128-byte row index (bits 7-9).
@@ -119,10 +129,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// Work description of one tile of (k, l) grid points: its origin and how many
-// of the CTA's eight 32 x 16 warp sub-tiles touch the domain.
+// Work description of one tile of (k, l) grid points: its origin, how many of
+// the CTA's eight 32 x 16 warp sub-tiles touch the domain (CUDA-core kernels)
+// and its number of l columns (tensor-core kernel, a multiple of 16).
 struct TileInfo {
-  int k0, l0, active_warps, pad;
+  int k0, l0, active_warps, ncols;
 };
 
 // Dynamic work queue of the persistent pair kernels.  Item i is (group chunk

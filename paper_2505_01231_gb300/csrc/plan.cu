@@ -81,6 +81,7 @@ struct ss_plan_s {
   int* d_counter = nullptr;        // work-queue counter of the pair kernels
   int FC = 0;                      // frames per staged chunk of the pair kernels
   CUtensorMap tm64{}, tm128{}, tm48{};  // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
+  CUtensorMap tm_img[4]{};               // 4-D views of each channel's Gram operand image
   TileInfo* d_tiles4tc = nullptr;  // 128 x 48 tiles of the tensor-core S4 kernel
   int n_tiles4tc = 0;
   OperandImage oi;                 // K1's second output for the tensor-core S4 kernel
@@ -169,13 +170,16 @@ bool in_domain3(int k, int l, int M, bool cross) {
   return k >= 0 && k <= l && k + l < M;
 }
 
-// Tiles of 128 x 48 grid points of the tensor-core S4 kernel that touch the
-// upper triangle k <= l < M.
+// Tiles of the tensor-core S4 kernel that touch the upper triangle k <= l < M:
+// 128 k-bins by up to 128 l-bins; the last l-block is cut to the bins left,
+// rounded up to the 16-column granule of the MMA.
 std::vector<TileInfo> build_tc_tiles(int M) {
   std::vector<TileInfo> t;
   for (int k0 = 0; k0 < M; k0 += kTcTileM)
-    for (int l0 = 0; l0 < M; l0 += kTcTileN)
-      if (k0 <= l0 + kTcTileN - 1) t.push_back(TileInfo{k0, l0, 8, 0});
+    for (int l0 = 0; l0 < M; l0 += kTcTileN) {
+      const int n = std::min(kTcTileN, (M - l0 + 15) & ~15);
+      if (k0 <= l0 + n - 1) t.push_back(TileInfo{k0, l0, 8, n});
+    }
   return t;
 }
 
@@ -303,7 +307,8 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
                                         p->d_acc4 + (long long)i * p->rows4 * p->M, plane,
                                         p->nsm, p->d_counter, p->d_status, p->stream));
           else
-            SS_TRY(p, launch_k3_trispec_tc(p->oi, cb.c[0], cnt, p->m, p->M, p->Mp,
+            SS_TRY(p, launch_k3_trispec_tc(p->tm_img[cb.c[0]], p->oi, cb.c[0], cnt, p->m, p->M,
+                                           p->Mp,
                                            p->d_tiles4tc, p->n_tiles4tc, p->precision,
                                            p->d_acc4 + (long long)i * p->rows4 * p->M, plane,
                                            p->nsm, p->d_counter, p->d_status, p->stream));
@@ -427,6 +432,28 @@ ss_status encode_maps(ss_plan_s* p) {
     if (r != CUDA_SUCCESS)
       return fail(p, SS_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string(r));
   }
+  if (p->oi.img) {
+    // Gram operand image of each channel as [group][row group][chunk][2 CB bytes]
+    // in 8-byte elements; a box is the stage's chunks of 16 row groups of one group
+    const cuuint64_t cbytes = p->oi.rg_bytes / p->oi.nkc;  // 2 CB
+    const cuuint64_t idims[4] = {cbytes / 8, (cuuint64_t)p->oi.nkc, (cuuint64_t)p->Mp / 8,
+                                 (cuuint64_t)p->Gb_max};
+    const cuuint64_t istr[3] = {cbytes, (cuuint64_t)p->oi.rg_bytes,
+                                (cuuint64_t)p->oi.group_bytes};
+    const cuuint32_t ibox[4] = {(cuuint32_t)(cbytes / 8),
+                                (cuuint32_t)k3tc_stage_chunks(p->precision), 16, 1};
+    const cuuint32_t iestr[4] = {1, 1, 1, 1};
+    for (int c = 0; c < p->C; ++c) {
+      CUresult r = encode(&p->tm_img[c], CU_TENSOR_MAP_DATA_TYPE_UINT64, 4,
+                          static_cast<char*>(p->oi.img) + (size_t)c * p->oi.chan_bytes, idims,
+                          istr, ibox, iestr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(p, SS_ECUDA,
+                    "cuTensorMapEncodeTiled (operand image) failed with code " + std::to_string(r));
+    }
+  }
   return SS_OK;
 }
 
@@ -440,10 +467,13 @@ ss_status alloc_spec(ss_plan_s* p) {
   };
   const size_t spec_group = (size_t)p->C * p->m * p->Mp * sizeof(float2);
   const bool image = !p->c4.empty() && p->precision != SS_PREC_FP32;
-  const int nch = (p->m + p->FC - 1) / p->FC;
+  // Gram image: ceil(m/16) diagonal chunks, then ceil(m(m-1)/2 / 16) pair chunks
+  const int ndc = (p->m + 15) / 16;
+  const int nkc = ndc + (p->m * (p->m - 1) / 2 + 15) / 16;
   const size_t cb = p->precision == SS_PREC_TF32X3 ? 512 : 256;
-  const size_t chunk_bytes = (size_t)(p->Mp / 8) * 6 * cb;
-  const size_t img_group = image ? (size_t)p->C * nch * chunk_bytes : 0;
+  const size_t rg_bytes = (size_t)nkc * 2 * cb;
+  const size_t group_bytes = (size_t)(p->Mp / 8) * rg_bytes;
+  const size_t img_group = image ? (size_t)p->C * group_bytes : 0;
   const size_t ps_group = image ? (size_t)p->C * p->Mp * sizeof(float) : 0;
   {
     void* v = p->d_spec;
@@ -469,11 +499,17 @@ ss_status alloc_spec(ss_plan_s* p) {
   if (image) {
     SS_TRY(p, dev_alloc(p, &p->oi.img, img_group * gb));
     SS_TRY(p, dev_alloc(p, &p->oi.ps, ps_group * gb));
-    p->oi.fmt = p->precision == SS_PREC_TF32X3 ? kImageTF32 : kImageBF16;
-    p->oi.FC = p->FC;
-    p->oi.nch = nch;
-    p->oi.chunk_bytes = (long long)chunk_bytes;
-    p->oi.chan_bytes = (long long)gb * nch * chunk_bytes;
+    p->oi.fmt = p->precision == SS_PREC_TF32X3 ? kImageGramTF32 : kImageGramBF16;
+    p->oi.nkc = nkc;
+    p->oi.ndc = ndc;
+    // weights of the Gram contraction with r = 1/((m-1)(m-2)(m-3)) folded in
+    const double md = p->m, r = 1.0 / ((md - 1.0) * (md - 2.0) * (md - 3.0));
+    p->oi.sd = (float)std::sqrt((md * md - md + 2.0) * r);
+    p->oi.so = (float)std::sqrt(4.0 * (md - 1.0) * r);
+    p->oi.sp = (float)std::sqrt((md - 1.0) * r);
+    p->oi.rg_bytes = (long long)rg_bytes;
+    p->oi.group_bytes = (long long)group_bytes;
+    p->oi.chan_bytes = (long long)gb * group_bytes;
     p->oi.chan_ps = (long long)gb * p->Mp;
   }
   return encode_maps(p);
@@ -588,6 +624,11 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
       delete p;
       return fail(nullptr, SS_EUNSUPPORTED, "cross-channel S4 is not built yet");
     }
+  if (!p->c4.empty() && precision != SS_PREC_FP32 && m > kMaxGramM) {
+    delete p;
+    return fail(nullptr, SS_EUNSUPPORTED,
+                "the tensor-core S4 precisions take m <= 32 frames per group; use fp32");
+  }
   p->rows3 = channels == 1 ? p->M : 2 * p->M - 1;
   p->rows4 = channels == 1 ? p->M : 2 * p->M - 1;
 
@@ -757,7 +798,9 @@ ss_status ss_finalize(ss_plan_t p, double* S2, double* S3, double* S4, double* S
                                  o3, e3, p->stream));
   if (n4)
     SS_TRY(p, launch_k4_finalize(p->d_acc4, (int)p->c4.size(), p->rows4, p->M,
-                                 single ? kLayoutS4Single : kLayoutCross, p->groups, p->norm4,
+                                 !single ? kLayoutCross
+                                 : p->precision == SS_PREC_FP32 ? kLayoutS4Single : kLayoutS4Lower,
+                                 p->groups, p->norm4,
                                  o4, e4, p->stream));
   record(p, 3, p->stream, false);
   const std::pair<double*, std::pair<const double*, size_t>> copies[6] = {

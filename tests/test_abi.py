@@ -67,3 +67,15 @@ def test_null_plan_calls_fail_cleanly():
     assert P.lib.ss_finalize(None, None, None, None, None, None, None) == P.SS_EINVAL
     assert P.lib.ss_reset(None) == P.SS_EINVAL
     assert P.lib.ss_destroy(None) == P.SS_OK
+
+
+@pytest.mark.parametrize("precision", ["SS_PREC_TF32X3", "SS_PREC_BF16X3", "SS_PREC_BF16"])
+def test_tensor_core_s4_rejects_more_than_32_frames(precision):
+    # the Gram contraction holds m(m+1)/2 products per bin: m <= 32 on the tensor cores
+    args = dict(channels=1, T=256, dt=1.0, m=33, window=P.SS_WIN_HANN, win_param=0.14,
+                orders=P.SS_ORDER2 | P.SS_ORDER4, dtype=P.SS_F32,
+                precision=getattr(P, precision), combos=None)
+    with pytest.raises(P.SSError) as ei:
+        P.ss_plan(**args)
+    assert ei.value.status == P.SS_EUNSUPPORTED
+    assert "m <= 32" in str(ei.value)

@@ -107,13 +107,18 @@ def test_config1_tensor_core_s4(c1_signal, precision):
     print(f"config-1 S4 {precision} max relative error", errs)
 
 
-@pytest.mark.parametrize("T,m,G", [(16, 4, 40), (64, 6, 30), (512, 10, 9), (128, 17, 10),
-                                   (64, 40, 6), (4096, 5, 3)])
-def test_tensor_core_s4_sizes(T, m, G):
+# m from the smallest S4 group to the largest the Gram contraction takes: one
+# diagonal K chunk and a ragged pair chunk (m = 4, 6, 10), exactly 16 frames,
+# two diagonal chunks (m = 17, 32); grids from one ragged 128-bin tile to 17 x 17
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("T,m,G", [(16, 4, 40), (64, 6, 30), (512, 10, 9), (32, 16, 12),
+                                   (128, 17, 10), (64, 32, 6), (4096, 5, 3)])
+def test_tensor_core_s4_sizes(T, m, G, precision):
     z = synth.ar1_quadratic(T * m * G + 2 * T + 3, seed=T + 7 * m)
     ref = oracle.polyspectra(z, T, 0.5, m, orders=(2, 4), group_chunk=8)
-    gpu = run_gpu(z, T, m, dt=0.5, orders=(2, 4), precision="tf32x3")
-    compare_single(gpu, ref, orders=(2, 4))
+    gpu = run_gpu(z, T, m, dt=0.5, orders=(2, 4), precision=precision)
+    tol, tol_err = PREC_TOL[precision]
+    compare_single(gpu, ref, orders=(2, 4), tol4=tol, tol4_err=tol_err)
 
 
 def test_streaming_chunks_match_one_call(c1_signal):
