@@ -192,16 +192,38 @@ def run_reference(args, w, rank, world):
 
 
 def cpu_baseline(w, z, groups):
+    """Time the FP64 oracle on a prefix of the record; return the line and its spectra."""
     import oracle
 
     T, m = w["T"], w["m"]
     n = groups * m * T
     t0 = time.perf_counter()
-    oracle.polyspectra(z[:n], T, 1.0, m, group_chunk=groups)
+    ref = oracle.polyspectra(z[:n], T, 1.0, m, group_chunk=groups)
     sec = time.perf_counter() - t0
-    return {"value": n / sec, "unit": "samples/s", "cores": 1, "kind": "oracle",
+    line = {"value": n / sec, "unit": "samples/s", "cores": 1, "kind": "oracle",
             "sample": f"first {groups} groups ({n} samples) of the record, full S2/S3/S4 grids, "
                       f"numpy float64 on one host core, {sec:.1f} s"}
+    return line, ref
+
+
+def error_vs_oracle(P, w, z, ref, groups, precision):
+    """max |GPU - oracle| / max |oracle| per spectrum on the oracle's prefix, through the
+    same C-ABI path and precision as the timed run."""
+    import torch
+
+    T, m = w["T"], w["m"]
+    n = groups * m * T
+    plan = P.Plan(channels=1, T=T, dt=1.0, m=m, orders=(2, 3, 4), precision=precision)
+    plan.accumulate(torch.from_numpy(np.ascontiguousarray(z[:n])).cuda(), n)
+    out = plan.finalize()
+    plan.close()
+    errs = {}
+    for key in ("S2", "S3", "S4"):
+        a, b = out[key][0].reshape(ref[key].shape), ref[key]
+        errs[key] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    errs["groups"] = groups
+    errs["precision"] = precision
+    return errs
 
 
 # ------------------------------------------------------------------ our arm
@@ -216,7 +238,7 @@ def main():
     ap.add_argument("--ref-groups", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3", "bf16"],
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3", "bf16"],
                     help="arithmetic of the S4 moment sums")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -325,6 +347,32 @@ def main():
                 "launch_ms": float(stage_ms[dom] / max(1, launches))}
     gpu_launches = int(args.steps * (n_batches * (1 + info.n_s3 + info.n_s4) + 3))
 
+    # ---- the S4 stage against its own bound: the tensor pipe in the split modes
+    # (useful products of the Gram contraction, K = m(m+1)/2 per grid point and
+    # group, times the hi/lo passes), the FP32 pipe otherwise
+    s4_ms = stage_ms[2] / args.steps
+    if args.precision == "fp32":
+        s4_flops = 10.0 * st.pairs4 * frames
+        s4_peak, s4_unit, s4_bound = fp32_peak_tflops(nsm, pk), "TFLOP/s", "alu"
+        s4_src = "derived: SMs x 128 FP32 lanes x 2 flop x max SM clock"
+    else:
+        passes = 1 if args.precision == "bf16" else 3
+        s4_flops = float(st.pairs4) * groups * m * (m + 1) * passes
+        bf16_peak = float(pk.get("bf16_tflops", 1900.0))
+        if args.precision == "tf32x3":
+            s4_peak = bf16_peak * 1.1 / 2.25
+            s4_src = "measured bf16 x nominal tf32/bf16 dense ratio (1.1/2.25 PFLOP/s)"
+        else:
+            s4_peak, s4_src = bf16_peak, "measured (MEASURED_PEAKS.json, bf16 burst)"
+        s4_unit, s4_bound = "TFLOP/s", "tensor"
+    s4_ach = s4_flops / (s4_ms / 1e3) / 1e12 if s4_ms > 0 else None
+    roofline_s4 = {"bound": s4_bound, "kernel": "k3_trispec", "achieved": s4_ach,
+                   "peak": s4_peak, "unit": s4_unit,
+                   "frac": (s4_ach / s4_peak) if s4_ach else None,
+                   "traffic": traffic_for("k3_trispec_tc" if args.precision != "fp32"
+                                          else "k3_trispec"),
+                   "peak_source": s4_src, "ms_per_step": s4_ms}
+
     # ---- end to end through the same calls with host buffers
     e2e = None
     if not args.no_e2e:
@@ -354,9 +402,10 @@ def main():
         e2e = {"value": world * n * args.steps / he, "unit": "samples/s",
                "h2d_bytes_per_step": int(z.nbytes), "d2h_bytes_per_step": int(d2h)}
 
-    cpu = None
+    cpu, err_fp64 = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, z, args.cpu_groups)
+        cpu, ref = cpu_baseline(w, z, args.cpu_groups)
+        err_fp64 = error_vs_oracle(P, w, z, ref, args.cpu_groups, args.precision)
 
     if rank == 0:
         line = {
@@ -369,6 +418,7 @@ def main():
                        "orders": "S2+S3+S4 full grids", "s4_precision": args.precision,
                        "l2": "record of 1 GiB per step is larger than L2; no flush"},
             "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
+            "roofline_s4": roofline_s4, "err_vs_fp64": err_fp64,
             "cpu_baseline": cpu, "clocks": clock_info,
         }
         print(json.dumps(line), flush=True)
