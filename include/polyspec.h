@@ -192,6 +192,37 @@ ss_status ss_stats(ss_plan_t plan, ss_stats_t* stats);
    ss_reset. */
 ss_status ss_set_batch(ss_plan_t plan, int groups_per_batch);
 
+/*
+ * Sharding a record across GPUs or processes (Sec. 4.2: the estimate and its
+ * error bar of Eq. 35-36 are built from sums over groups of the per-group
+ * spectra S_g and of (Re S_g)^2, (Im S_g)^2, so plans that saw disjoint sets of
+ * whole groups combine by adding those sums).
+ *
+ * A state is SS_STATE_HEADER doubles followed by the plan's float64 sums.
+ * Header words 0..13 describe the configuration (channels, T, m, orders,
+ * precision, window, sigma_t, dt, the number of S2/S3/S4 combinations, a
+ * 52-bit hash of the combination list, a layout version, 0) and must match
+ * between plans that are merged; word 14 is the number of groups, word 15
+ * the number of samples per channel in them.
+ * Samples carried over towards an incomplete group are not part of a state.
+ *
+ * ss_state_size   -- number of doubles of the plan's state (header included).
+ * ss_export_state -- write the state to dst (host or device memory, at least
+ *                    ss_state_size doubles).  Synchronises the plan's stream.
+ * ss_merge_state  -- add a state written by ss_export_state of a plan with the
+ *                    same configuration (host or device memory): its group
+ *                    sums, groups and samples are added to this plan's.  A
+ *                    configuration mismatch returns SS_EINVAL and changes
+ *                    nothing.  Stream-ordered; a host src is copied before the
+ *                    call returns.
+ * Adding exported states element-wise (e.g. an all-reduce sum) and merging
+ * the total into a reset plan gives the state of the union of the groups.
+ */
+#define SS_STATE_HEADER 16
+ss_status ss_state_size(ss_plan_t plan, size_t* n_doubles);
+ss_status ss_export_state(ss_plan_t plan, double* dst);
+ss_status ss_merge_state(ss_plan_t plan, const double* src);
+
 /* ss_destroy -- release every resource of the plan (NULL is accepted). */
 ss_status ss_destroy(ss_plan_t plan);
 

@@ -31,6 +31,7 @@ SS_WIN_HANN, SS_WIN_ACG = 0, 1
 SS_ORDER2, SS_ORDER3, SS_ORDER4 = 1 << 2, 1 << 3, 1 << 4
 SS_F32, SS_I16 = 0, 1
 SS_PREC_FP32, SS_PREC_TF32X3, SS_PREC_BF16X3, SS_PREC_BF16 = 0, 1, 2, 3
+SS_STATE_HEADER = 16
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpolyspec.so")
 if not os.path.exists(LIB_PATH):
@@ -73,6 +74,9 @@ _sig = {
     "ss_s2_noalloc": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P]),
     "ss_noalloc_last_error": (ctypes.c_char_p, []),
+    "ss_state_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "ss_export_state": (ctypes.c_int, [_P, _P]),
+    "ss_merge_state": (ctypes.c_int, [_P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -172,6 +176,20 @@ def ss_version():
     return lib.ss_version().decode()
 
 
+def ss_state_size(plan):
+    n = ctypes.c_size_t()
+    _check(lib.ss_state_size(plan, ctypes.byref(n)), plan)
+    return n.value
+
+
+def ss_export_state(plan, dst):
+    _check(lib.ss_export_state(plan, _addr(dst)), plan)
+
+
+def ss_merge_state(plan, src):
+    _check(lib.ss_merge_state(plan, _addr(src)), plan)
+
+
 def ss_s2_noalloc(d_signal, n_samples, T, dt, m, window=SS_WIN_HANN, win_param=0.14,
                   d_S2=None, d_S2_err=None, stream=None):
     """Power spectrum of one device-resident float32 channel with no device allocation
@@ -227,6 +245,18 @@ class Plan:
 
     def reset(self):
         ss_reset(self.handle)
+
+    def export_state(self, out=None):
+        """The plan's group sums with their header (float64); a new host array unless
+        ``out`` (host or device, ss_state_size doubles) is given."""
+        if out is None:
+            out = np.empty(ss_state_size(self.handle), np.float64)
+        ss_export_state(self.handle, out)
+        return out
+
+    def merge_state(self, src):
+        """Add a state exported by an identically configured plan."""
+        ss_merge_state(self.handle, src)
 
     def combos(self):
         return ss_combos(self.handle)

@@ -141,6 +141,9 @@ cudaError_t launch_k4_finalize(const double* acc, int n_combos, int rows, int M,
                                long long G, double norm, double* out, double* err,
                                cudaStream_t stream);
 
+// dst[i] += src[i], i < n (device pointers): merges exported group sums.
+cudaError_t launch_add_f64(double* dst, const double* src, long long n, cudaStream_t stream);
+
 // Layout codes of launch_k4_finalize.
 enum { kLayoutVector = 0,       // S2: [M]
        kLayoutS3Single = 1,     // one channel, computed for k <= l, mirrored; k+l <= M-1

@@ -1,4 +1,5 @@
-// k_finalize.cu -- K4: mean over groups and standard errors, in float64.
+// k_finalize.cu -- K4: mean over groups and standard errors, in float64; and the
+// element-wise float64 addition that merges the group sums of two plans.
 //
 // For every output grid point it reads the float64 sums over the G groups of
 // S_g (real and imaginary part) and of their squares, applies the window and
@@ -51,7 +52,21 @@ __global__ void k4_finalize(const double* __restrict__ acc, int n_combos, int ro
   }
 }
 
+__global__ void k_add_f64(double* __restrict__ dst, const double* __restrict__ src, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] += src[i];
+}
+
 }  // namespace
+
+cudaError_t launch_add_f64(double* dst, const double* src, long long n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  long long grid = (n + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  k_add_f64<<<(int)grid, 256, 0, stream>>>(dst, src, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_k4_finalize(const double* acc, int n_combos, int rows, int M, int layout,
                                long long G, double norm, double* out, double* err,

@@ -890,6 +890,123 @@ ss_status ss_set_batch(ss_plan_t p, int groups_per_batch) {
   return alloc_spec(p);
 }
 
+namespace {
+
+constexpr double kStateLayoutVersion = 1.0;
+constexpr int kStateCfgWords = 14;  // header words that must match; 14 = groups, 15 = samples
+
+// FNV-1a over the combination records, cut to 52 bits (exact in a double)
+double combos_hash(const ss_plan_s* p) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](int v) {
+    for (int b = 0; b < 4; ++b) {
+      h ^= (uint64_t)((v >> (8 * b)) & 0xff);
+      h *= 1099511628211ull;
+    }
+  };
+  for (const auto* list : {&p->c2, &p->c3, &p->c4})
+    for (const Combo& c : *list) {
+      mix(c.order);
+      for (int q = 0; q < 4; ++q) mix(q < c.order ? c.c[q] : -1);
+    }
+  return (double)(h & ((1ull << 52) - 1));
+}
+
+void state_header(const ss_plan_s* p, double* h) {
+  for (int i = 0; i < SS_STATE_HEADER; ++i) h[i] = 0.0;
+  h[0] = p->C;
+  h[1] = p->T;
+  h[2] = p->m;
+  h[3] = p->orders;
+  h[4] = p->precision;
+  h[5] = p->window;
+  h[6] = p->window == SS_WIN_ACG ? p->win_param : 0.0;
+  h[7] = p->dt;
+  h[8] = (double)p->c2.size();
+  h[9] = (double)p->c3.size();
+  h[10] = (double)p->c4.size();
+  h[11] = combos_hash(p);
+  h[12] = kStateLayoutVersion;
+  h[14] = (double)p->groups;
+  h[15] = (double)p->samples;
+}
+
+}  // namespace
+
+ss_status ss_state_size(ss_plan_t p, size_t* n) {
+  if (!p || !n) return fail(p, SS_EINVAL, "NULL argument");
+  *n = SS_STATE_HEADER + p->n_acc2 + p->n_acc3 + p->n_acc4;
+  return SS_OK;
+}
+
+ss_status ss_export_state(ss_plan_t p, double* dst) {
+  if (!p || !dst) return fail(p, SS_EINVAL, "NULL argument");
+  if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
+  DeviceGuard guard(p->device);
+  ss_status st = check_status(p);
+  if (st != SS_OK) return st;
+  double h[SS_STATE_HEADER];
+  state_header(p, h);
+  SS_TRY(p, cudaMemcpyAsync(dst, h, sizeof(h), cudaMemcpyDefault, p->stream));
+  double* o = dst + SS_STATE_HEADER;
+  const std::pair<const double*, size_t> parts[3] = {
+      {p->d_acc2, p->n_acc2}, {p->d_acc3, p->n_acc3}, {p->d_acc4, p->n_acc4}};
+  for (const auto& pr : parts) {
+    if (pr.second)
+      SS_TRY(p, cudaMemcpyAsync(o, pr.first, pr.second * sizeof(double), cudaMemcpyDefault,
+                                p->stream));
+    o += pr.second;
+  }
+  SS_TRY(p, cudaStreamSynchronize(p->stream));
+  return SS_OK;
+}
+
+ss_status ss_merge_state(ss_plan_t p, const double* src) {
+  if (!p || !src) return fail(p, SS_EINVAL, "NULL argument");
+  if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
+  DeviceGuard guard(p->device);
+  double mine[SS_STATE_HEADER], theirs[SS_STATE_HEADER];
+  state_header(p, mine);
+  SS_TRY(p, cudaMemcpyAsync(theirs, src, sizeof(theirs), cudaMemcpyDefault, p->stream));
+  SS_TRY(p, cudaStreamSynchronize(p->stream));
+  for (int i = 0; i < kStateCfgWords; ++i)
+    if (mine[i] != theirs[i])
+      return fail(p, SS_EINVAL, "state of a plan with another configuration (header word " +
+                                    std::to_string(i) + ")");
+  if (!(theirs[14] >= 0.0) || !(theirs[15] >= 0.0))
+    return fail(p, SS_EINVAL, "state with a negative group or sample count");
+  const size_t n = p->n_acc2 + p->n_acc3 + p->n_acc4;
+  const double* payload = src + SS_STATE_HEADER;
+  if (n) {
+    const double* dsrc = payload;
+    if (!is_device_ptr(src)) {
+      if (p->out_doubles < n) {  // the finalize buffer doubles as the staging buffer
+        if (p->d_out) {
+          cudaFree(p->d_out);
+          p->device_bytes -= p->out_doubles * sizeof(double);
+          p->d_out = nullptr;
+          p->out_doubles = 0;
+        }
+        SS_TRY(p, dev_alloc(p, &p->d_out, n * sizeof(double)));
+        p->out_doubles = n;
+      }
+      SS_TRY(p, cudaMemcpyAsync(p->d_out, payload, n * sizeof(double), cudaMemcpyHostToDevice,
+                                p->stream));
+      dsrc = p->d_out;
+    }
+    const std::pair<double*, size_t> parts[3] = {
+        {p->d_acc2, p->n_acc2}, {p->d_acc3, p->n_acc3}, {p->d_acc4, p->n_acc4}};
+    for (const auto& pr : parts) {
+      if (pr.second) SS_TRY(p, launch_add_f64(pr.first, dsrc, (long long)pr.second, p->stream));
+      dsrc += pr.second;
+    }
+    SS_TRY(p, cudaStreamSynchronize(p->stream));  // a host src may be reused on return
+  }
+  p->groups += (long long)theirs[14];
+  p->samples += (long long)theirs[15];
+  return SS_OK;
+}
+
 ss_status ss_destroy(ss_plan_t p) {
   if (!p) return SS_OK;
   DeviceGuard guard(p->device);

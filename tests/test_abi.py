@@ -66,6 +66,9 @@ def test_null_plan_calls_fail_cleanly():
     assert P.lib.ss_accumulate(None, None, 0) == P.SS_EINVAL
     assert P.lib.ss_finalize(None, None, None, None, None, None, None) == P.SS_EINVAL
     assert P.lib.ss_reset(None) == P.SS_EINVAL
+    assert P.lib.ss_state_size(None, None) == P.SS_EINVAL
+    assert P.lib.ss_export_state(None, None) == P.SS_EINVAL
+    assert P.lib.ss_merge_state(None, None) == P.SS_EINVAL
     assert P.lib.ss_destroy(None) == P.SS_OK
 
 
