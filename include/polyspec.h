@@ -77,8 +77,10 @@ enum { SS_PREC_FP32 = 0,    /* FP32 FMA on CUDA cores                          *
        SS_PREC_BF16X3 = 2,  /* tensor cores, BF16 hi/lo split, 3 products      */
        SS_PREC_BF16 = 3     /* tensor cores, plain BF16 inputs                 */ };
 /* The tensor-core precisions contract the weighted frame Gram of each bin
-   (m(m+1)/2 products per grid point and group) and take m <= 32 when the plan
-   computes S4; ss_plan returns SS_EUNSUPPORTED for larger m.  All precisions
+   (m(m+1)/2 products per grid point and group) and take m <= 32 when a
+   one-channel plan computes S4; ss_plan returns SS_EUNSUPPORTED for larger m.
+   Plans of several channels compute every S4 combination in FP32 on CUDA
+   cores, whatever the precision.  All precisions
    keep the per-group c4 values and their per-item sums in FP32: inputs whose
    |c4| exceeds about 1e18 overflow the sum of squares. */
 

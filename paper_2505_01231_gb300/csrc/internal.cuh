@@ -121,6 +121,13 @@ cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm_img, const OperandImage& 
                                  long long plane, int nsm, int* counter, int* status,
                                  cudaStream_t stream);
 size_t k3tc_smem_bytes(int precision);
+
+// K3 for several channels (FP32 CUDA cores): C4(a_k, b_k*, c_l, d_l*) of every
+// combination (combos: device array of n_combos (a, b, c, d)) on the grid
+// k in [-(M-1), M-1] x l in [0, M-1], accumulated at acc[plane][combo][k+M-1][l].
+cudaError_t launch_k3_trispec_cross(const float2* spec, long long chan_stride, int G, int m, int M,
+                                    int Mp, const int4* combos, int n_combos, double* acc,
+                                    long long plane, int nsm, cudaStream_t stream);
 int k3tc_stage_chunks(int precision);
 
 // Groups per work item: about 16 items per CTA, whole groups, at least one.

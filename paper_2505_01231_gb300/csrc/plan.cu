@@ -82,7 +82,8 @@ struct ss_plan_s {
   int FC = 0;                      // frames per staged chunk of the pair kernels
   CUtensorMap tm64{}, tm128{}, tm48{};  // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
   CUtensorMap tm_img[4]{};               // 4-D views of each channel's Gram operand image
-  TileInfo* d_tiles4tc = nullptr;  // 128 x 48 tiles of the tensor-core S4 kernel
+  TileInfo* d_tiles4tc = nullptr;  // tiles of the tensor-core S4 kernel (one channel)
+  int4* d_c4cross = nullptr;       // (a, b, c, d) of each S4 combination (several channels)
   int n_tiles4tc = 0;
   OperandImage oi;                 // K1's second output for the tensor-core S4 kernel
   int n_tiles3 = 0, n_tiles4 = 0;
@@ -299,7 +300,11 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
       if (!p->c4.empty()) {
         record(p, 2, p->stream, true);
         const long long plane = (long long)p->c4.size() * p->rows4 * p->M;
-        for (size_t i = 0; i < p->c4.size(); ++i) {
+        if (p->C > 1)
+          SS_TRY(p, launch_k3_trispec_cross(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp,
+                                            p->d_c4cross, (int)p->c4.size(), p->d_acc4, plane,
+                                            p->nsm, p->stream));
+        for (size_t i = 0; i < p->c4.size() && p->C == 1; ++i) {
           const Combo& cb = p->c4[i];
           if (p->precision == SS_PREC_FP32)
             SS_TRY(p, launch_k3_trispec(p->tm64, cb.c[0] * p->Gb_max * p->m, cnt, p->m, p->FC,
@@ -466,7 +471,7 @@ ss_status alloc_spec(ss_plan_s* p) {
     }
   };
   const size_t spec_group = (size_t)p->C * p->m * p->Mp * sizeof(float2);
-  const bool image = !p->c4.empty() && p->precision != SS_PREC_FP32;
+  const bool image = p->C == 1 && !p->c4.empty() && p->precision != SS_PREC_FP32;
   // Gram image: ceil(m/16) diagonal chunks, then ceil(m(m-1)/2 / 16) pair chunks
   const int ndc = (p->m + 15) / 16;
   const int nkc = ndc + (p->m * (p->m - 1) / 2 + 15) / 16;
@@ -542,6 +547,7 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_tiles3);
   cudaFree(p->d_tiles4);
   cudaFree(p->d_tiles4tc);
+  cudaFree(p->d_c4cross);
   cudaFree(p->d_status);
   cudaFree(p->d_counter);
   cudaFree(p->d_out);
@@ -619,12 +625,7 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   } else {
     default_combos(p);
   }
-  for (const Combo& cb : p->c4)
-    if (channels > 1 || cb.c[0] != cb.c[1] || cb.c[0] != cb.c[2] || cb.c[0] != cb.c[3]) {
-      delete p;
-      return fail(nullptr, SS_EUNSUPPORTED, "cross-channel S4 is not built yet");
-    }
-  if (!p->c4.empty() && precision != SS_PREC_FP32 && m > kMaxGramM) {
+  if (channels == 1 && !p->c4.empty() && precision != SS_PREC_FP32 && m > kMaxGramM) {
     delete p;
     return fail(nullptr, SS_EUNSUPPORTED,
                 "the tensor-core S4 precisions take m <= 32 frames per group; use fp32");
@@ -679,10 +680,10 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   std::vector<TileInfo> t3, t4;
   build_tiles(p, t3, t4);
   std::vector<TileInfo> t4tc;
-  if (!p->c4.empty() && precision != SS_PREC_FP32) t4tc = build_tc_tiles(p->M);
+  if (channels == 1 && !p->c4.empty() && precision != SS_PREC_FP32) t4tc = build_tc_tiles(p->M);
   p->n_tiles4tc = (int)t4tc.size();
   if (p->c3.empty()) t3.clear();
-  if (p->c4.empty()) t4.clear();
+  if (p->c4.empty() || channels > 1) t4.clear();  // several channels: k3_trispec_cross
   p->n_tiles3 = (int)t3.size();
   p->n_tiles4 = (int)t4.size();
 
@@ -710,6 +711,14 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   if (!t3.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles3, t3.size() * sizeof(TileInfo)));
   if (!t4.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4, t4.size() * sizeof(TileInfo)));
   if (!t4tc.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4tc, t4tc.size() * sizeof(TileInfo)));
+  std::vector<int4> c4x;
+  if (channels > 1)
+    for (const Combo& cb : p->c4) c4x.push_back(make_int4(cb.c[0], cb.c[1], cb.c[2], cb.c[3]));
+  if (!c4x.empty()) {
+    PLAN_TRY(dev_alloc(p, &p->d_c4cross, c4x.size() * sizeof(int4)));
+    PLAN_TRY(cudaMemcpy(p->d_c4cross, c4x.data(), c4x.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice));
+  }
   PLAN_TRY(dev_alloc(p, &p->d_status, sizeof(int)));
   PLAN_TRY(dev_alloc(p, &p->d_counter, sizeof(int)));
   PLAN_TRY(cudaMemcpy(p->d_win, gw.data(), T * sizeof(float), cudaMemcpyHostToDevice));

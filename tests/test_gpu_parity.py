@@ -183,6 +183,44 @@ def test_multichannel_s2_s3():
               {"S3": ref[("S3", c)][0], "S3_err": ref[("S3", c)][1]}, "S3")
 
 
+# cross-channel S4, C4(a_k, b_k*, c_l, d_l*) on k in [-(M-1), M-1] x l in [0, M-1]:
+# pairings that exercise every role (all equal, one distinct, two pairs, all
+# distinct, the order of the pairs), m across one and two staged frame chunks,
+# a grid with ragged row and column tiles; every precision runs it in FP32
+@pytest.mark.parametrize("T,m,G,precision", [(64, 5, 40, "fp32"), (32, 20, 12, "fp32"),
+                                             (128, 6, 16, "tf32x3")])
+def test_multichannel_s4(T, m, G, precision):
+    zs = synth.multichannel_shared(4, T * m * G + 7, seed=13 + m)
+    combos4 = [(0, 0, 0, 0), (0, 0, 1, 1), (0, 1, 0, 1), (0, 1, 1, 0), (0, 0, 1, 2),
+               (1, 2, 0, 0), (0, 1, 2, 3), (3, 2, 1, 0), (2, 2, 2, 3)]
+    recs = [(4, *c) for c in combos4]
+    gpu = run_gpu(zs, T, m, dt=0.5, orders=(4,), channels=4, combos=recs, precision=precision)
+    ref = oracle.cross_polyspectra(zs, T, 0.5, m, s4_combos=combos4)
+    assert gpu["G"] == ref["G"] == G
+    for i, c in enumerate(combos4):
+        check({"S4": gpu["S4"][i], "S4_err": gpu["S4_err"][i]},
+              {"S4": ref[("S4", c)][0], "S4_err": ref[("S4", c)][1]}, "S4")
+
+
+def test_multichannel_default_combinations_all_orders():
+    # three channels, the default combination lists of every order in one plan
+    mod = P()
+    zs = synth.multichannel_shared(3, 64 * 6 * 20, seed=21)
+    plan = mod.Plan(channels=3, T=64, dt=1.0, m=6, orders=(2, 3, 4))
+    recs = plan.combos()
+    plan.close()
+    c2 = [tuple(r[1:3]) for r in recs if r[0] == 2]
+    c3 = [tuple(r[1:4]) for r in recs if r[0] == 3]
+    c4 = [tuple(r[1:5]) for r in recs if r[0] == 4]
+    assert (len(c2), len(c3), len(c4)) == (6, 10, 21)
+    gpu = run_gpu(zs, 64, 6, channels=3)
+    ref = oracle.cross_polyspectra(zs, 64, 1.0, 6, s2_combos=c2, s3_combos=c3, s4_combos=c4)
+    for key, lst in (("S2", c2), ("S3", c3), ("S4", c4)):
+        for i, c in enumerate(lst):
+            check({key: gpu[key][i], key + "_err": gpu[key + "_err"][i]},
+                  {key: ref[(key, c)][0], key + "_err": ref[(key, c)][1]}, key)
+
+
 def test_fewer_than_two_groups_is_a_state_error():
     mod = P()
     plan = mod.Plan(T=64, m=4)
