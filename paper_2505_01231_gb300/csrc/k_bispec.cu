@@ -17,14 +17,19 @@
 // arithmetic.  Each thread evaluates a 4 x 4 micro-tile of grid points with
 // 128-bit shared loads; the thread layout (a quarter-warp covers 4 k-threads x
 // 2 l-threads) together with the swizzle keeps every quarter-warp on distinct
-// banks.  Per-item float32 sums over groups are added to the float64
-// accumulators when the item ends.  Warps whose 32 x 16 sub-tile lies outside
+// banks.  The per-item float32 sums over groups of the four parts (Re, Im and
+// their squares) live in tensor memory, 128 columns per CTA (warp w: TMEM lane
+// quadrant w % 4, columns 64 (w / 4) ..), read and written with tcgen05.ld/st
+// once per group, which keeps the kernel within 128 registers and two CTAs per
+// SM; they are added to the float64 accumulators when the item ends.  Warps whose 32 x 16 sub-tile lies outside
 // the domain skip the arithmetic.  All waits on the stage barriers are bounded.
 //
 // Domains: one channel (cross = 0): 0 <= k <= l, k + l <= M-1 (the rest follows
 // from S3(k, l) = S3(l, k), Sec. 9).  Several channels (cross = 1):
 // -(M-1) <= k <= M-1, 0 <= l <= M-1, |k + l| <= M-1, using X_{-k} = X_k*; tiles
 // that reach negative bins are staged by the threads (conjugated), not by TMA.
+#include <algorithm>
+
 #include "internal.cuh"
 #include "pipeline.cuh"
 
@@ -59,7 +64,37 @@ __device__ __forceinline__ float4 lds128(const unsigned char* p) {
   return *reinterpret_cast<const float4*>(p);
 }
 
-__global__ void __launch_bounds__(kThreadsPair, 1)
+constexpr uint32_t kTmemCols = 128;  // per CTA: 2 warps per lane quadrant x 64 columns
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsPair, 2)
 k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUtensorMap tm128,
           const float2* __restrict__ sa, const float2* __restrict__ sb,
           const float2* __restrict__ sc, int rowA, int rowB, int rowC, int G, int m, int FC,
@@ -69,6 +104,7 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
   extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ int s_item;
+  __shared__ uint32_t tmem_slot;
   unsigned char* sbase = align1024<unsigned char>(smem_raw);
   const uint32_t sbytes = stage_bytes(FC), a64 = arr64_bytes(FC);
   const int tid = threadIdx.x;
@@ -91,11 +127,29 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
   fence_async_smem();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // this warp's 64 columns of per-item sums: Re, Im, Re^2, Im^2 of 16 points
+  const uint32_t tsum = tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (warp >> 2);
+  {
+    float z[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = 0.f;
+#pragma unroll
+    for (int part = 0; part < 4; ++part) tmem_st16(tsum + 16 * part, z);
+  }
   uint32_t qbase = 0;  // TMA steps consumed so far (stage = q % kStages)
+  bool failed = false;
 
-  for (int item; (item = next_item(wq, &s_item)) >= 0;) {
+  for (int item; !failed && (item = next_item(wq, &s_item)) >= 0;) {
     const int t = item % wq.n_tiles;
     const int ga = (item / wq.n_tiles) * wq.group_chunk;
     const int gb = min(G, ga + wq.group_chunk);
@@ -116,9 +170,9 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
       tma_load_3d(st + 2 * a64, &tm128, 0, (k0 + l0) >> 4, rowC + g * m + j0, &full[s]);
     };
 
-    float sr[16], si[16], qr[16], qi[16], ar[16], ai[16];
+    float ar[16], ai[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) sr[i] = si[i] = qr[i] = qi[i] = ar[i] = ai[i] = 0.f;
+    for (int i = 0; i < 16; ++i) ar[i] = ai[i] = 0.f;
 
     if (use_tma && tid == 0) {
       fence_async_smem();
@@ -188,16 +242,31 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
           frame(j + 1, oA0o, oA1o, oB0o, oB1o);
         }
         if (j < nf) frame(j, oA0, oA1, oB0, oB1);
-        if (ch == nch - 1) {
+        if (ch == nch - 1) {  // end of a group: c3 into the per-item sums
+          float t[16];
+          tmem_ld16(tsum, t);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) t[q] = fmaf(ar[q], pref3, t[q]);
+          tmem_st16(tsum, t);
+          tmem_ld16(tsum + 16, t);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) t[q] = fmaf(ai[q], pref3, t[q]);
+          tmem_st16(tsum + 16, t);
+          tmem_ld16(tsum + 32, t);
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
-            const float vr = ar[q] * pref3, vi = ai[q] * pref3;
-            sr[q] += vr;
-            si[q] += vi;
-            qr[q] = fmaf(vr, vr, qr[q]);
-            qi[q] = fmaf(vi, vi, qi[q]);
+            const float v = ar[q] * pref3;
+            t[q] = fmaf(v, v, t[q]);
+          }
+          tmem_st16(tsum + 32, t);
+          tmem_ld16(tsum + 48, t);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float v = ai[q] * pref3;
+            t[q] = fmaf(v, v, t[q]);
             ar[q] = ai[q] = 0.f;
           }
+          tmem_st16(tsum + 48, t);
         }
       }
       // every thread is done with stage s; a failed wait anywhere stops the CTA
@@ -205,29 +274,39 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
         if (use_tma)  // drain copies still in flight before giving up
           for (int q = i + 1; q < nsteps && q < i + kStages; ++q)
             mbar_wait_bounded(&full[(qbase + q) % kStages], ((qbase + q) / kStages) & 1u, status);
-        return;
+        failed = true;
+        break;
       }
       if (use_tma && tid == 0 && i + kStages < nsteps) {
         fence_async_smem();
         issue(i + kStages);
       }
     }
+    if (failed) break;
     if (use_tma) qbase += nsteps;
     if (!active) continue;
+    // end of the item: the sums of each part go to the float64 accumulators
+#pragma unroll 1
+    for (int part = 0; part < 4; ++part) {
+      float t[16], z[16];
+      tmem_ld16(tsum + 16 * part, t);
+      double* dst = acc + (long long)part * plane;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int k = k0 + kt + a, l = l0 + lt + b;
-        if (!in_domain3(k, l, M, cross)) continue;
-        const long long o = (long long)(k + koff) * M + l;
-        const int q = a * 4 + b;
-        atomicAdd(acc + o, (double)sr[q]);
-        atomicAdd(acc + plane + o, (double)si[q]);
-        atomicAdd(acc + 2 * plane + o, (double)qr[q]);
-        atomicAdd(acc + 3 * plane + o, (double)qi[q]);
+      for (int q = 0; q < 16; ++q) {
+        const int k = k0 + kt + (q >> 2), l = l0 + lt + (q & 3);
+        if (in_domain3(k, l, M, cross))
+          atomicAdd(dst + (long long)(k + koff) * M + l, (double)t[q]);
+        z[q] = 0.f;
       }
+      tmem_st16(tsum + 16 * part, z);
     }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot),
+                 "r"(kTmemCols));
   }
 }
 
@@ -246,10 +325,31 @@ cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
   cudaError_t e = cudaFuncSetAttribute(k2_bispec, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_bispec, kThreadsPair, smem);
+  // the whole unified L1 as shared memory, so that two CTAs fit per SM
+  e = cudaFuncSetAttribute(k2_bispec, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  const int n_cta = nsm * (occ > 0 ? occ : 1);
+  // resident CTAs per SM from the kernel's registers and shared memory (the
+  // occupancy query reports one for this kernel although both limits allow two)
+  static int occ = 0;
+  if (occ == 0) {
+    cudaFuncAttributes fa;
+    int dev = 0, sm_smem = 0, sm_regs = 0, rsv = 0;
+    e = cudaFuncGetAttributes(&fa, k2_bispec);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e != cudaSuccess) return e;
+    const int regs = ((fa.numRegs + 7) & ~7) * kThreadsPair;
+    const int by_regs = regs > 0 ? sm_regs / regs : 1;
+    const int by_smem = sm_smem / (int)(smem + fa.sharedSizeBytes + rsv);
+    occ = std::max(1, std::min(2, std::min(by_regs, by_smem)));
+  }
+  const int n_cta = nsm * occ;
   WorkQueue wq;
   wq.counter = counter;
   wq.n_tiles = n_tiles;
