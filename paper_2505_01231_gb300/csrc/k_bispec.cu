@@ -94,10 +94,13 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// kFC > 0: the frames per staged chunk fixed at compile time (the frame loop of a
+// full chunk is unrolled with constant shared-memory offsets); 0: taken from FC.
+template <int kFC>
 __global__ void __launch_bounds__(kThreadsPair, 2)
 k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUtensorMap tm128,
           const float2* __restrict__ sa, const float2* __restrict__ sb,
-          const float2* __restrict__ sc, int rowA, int rowB, int rowC, int G, int m, int FC,
+          const float2* __restrict__ sc, int rowA, int rowB, int rowC, int G, int m, int FC_rt,
           int M, int Mp, const TileInfo* __restrict__ tiles, WorkQueue wq, int cross,
           float pref3, double* __restrict__ acc, long long plane, int koff,
           int* __restrict__ status) {
@@ -106,6 +109,7 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
   __shared__ int s_item;
   __shared__ uint32_t tmem_slot;
   unsigned char* sbase = align1024<unsigned char>(smem_raw);
+  const int FC = kFC > 0 ? kFC : FC_rt;
   const uint32_t sbytes = stage_bytes(FC), a64 = arr64_bytes(FC);
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -236,12 +240,20 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
             }
           }
         };
-        int j = 0;
-        for (; j + 1 < nf; j += 2) {
-          frame(j, oA0, oA1, oB0, oB1);
-          frame(j + 1, oA0o, oA1o, oB0o, oB1o);
+        if (kFC > 0 && nf == kFC) {
+#pragma unroll
+          for (int j = 0; j < kFC; j += 2) {
+            frame(j, oA0, oA1, oB0, oB1);
+            if (j + 1 < kFC) frame(j + 1, oA0o, oA1o, oB0o, oB1o);
+          }
+        } else {
+          int j = 0;
+          for (; j + 1 < nf; j += 2) {
+            frame(j, oA0, oA1, oB0, oB1);
+            frame(j + 1, oA0o, oA1o, oB0o, oB1o);
+          }
+          if (j < nf) frame(j, oA0, oA1, oB0, oB1);
         }
-        if (j < nf) frame(j, oA0, oA1, oB0, oB1);
         if (ch == nch - 1) {  // end of a group: c3 into the per-item sums
           float t[16];
           tmem_ld16(tsum, t);
@@ -314,28 +326,18 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
 
 size_t k2_smem_bytes(int FC) { return (size_t)kStages * stage_bytes(FC) + 1024; }
 
-cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
-                             const float2* spec_a, const float2* spec_b, const float2* spec_c,
-                             int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
-                             const TileInfo* tiles, int n_tiles, int cross, float pref3,
-                             double* acc, long long plane, int rows, int nsm, int* counter,
-                             int* status, cudaStream_t stream) {
-  if (G <= 0 || n_tiles <= 0) return cudaSuccess;
-  const size_t smem = k2_smem_bytes(FC);
-  cudaError_t e = cudaFuncSetAttribute(k2_bispec, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  // the whole unified L1 as shared memory, so that two CTAs fit per SM
-  e = cudaFuncSetAttribute(k2_bispec, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
-  // resident CTAs per SM from the kernel's registers and shared memory (the
-  // occupancy query reports one for this kernel although both limits allow two)
-  static int occ = 0;
-  if (occ == 0) {
+namespace {
+
+// resident CTAs per SM of one instantiation, from its registers and shared
+// memory (the occupancy query reports one for these kernels although both
+// limits allow two)
+template <int kFC>
+cudaError_t k2_ctas_per_sm(size_t smem, int* occ_out) {
+  int occ = 0;
+  {
     cudaFuncAttributes fa;
     int dev = 0, sm_smem = 0, sm_regs = 0, rsv = 0;
-    e = cudaFuncGetAttributes(&fa, k2_bispec);
+    cudaError_t e = cudaFuncGetAttributes(&fa, k2_bispec<kFC>);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
       e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -349,6 +351,27 @@ cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
     const int by_smem = sm_smem / (int)(smem + fa.sharedSizeBytes + rsv);
     occ = std::max(1, std::min(2, std::min(by_regs, by_smem)));
   }
+  *occ_out = occ;
+  return cudaSuccess;
+}
+
+template <int kFC>
+cudaError_t launch_k2_t(const CUtensorMap& tm64, const CUtensorMap& tm128, const float2* spec_a,
+                        const float2* spec_b, const float2* spec_c, int rowA, int rowB, int rowC,
+                        int G, int m, int FC, int M, int Mp, const TileInfo* tiles, int n_tiles,
+                        int cross, float pref3, double* acc, long long plane, int rows, int nsm,
+                        int* counter, int* status, cudaStream_t stream) {
+  const size_t smem = k2_smem_bytes(FC);
+  cudaError_t e = cudaFuncSetAttribute(k2_bispec<kFC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // the whole unified L1 as shared memory, so that two CTAs fit per SM
+  e = cudaFuncSetAttribute(k2_bispec<kFC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  int occ = 1;
+  e = k2_ctas_per_sm<kFC>(smem, &occ);
+  if (e != cudaSuccess) return e;
   const int n_cta = nsm * occ;
   WorkQueue wq;
   wq.counter = counter;
@@ -358,10 +381,31 @@ cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
   e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
   const int koff = (rows == M) ? 0 : (M - 1);
-  k2_bispec<<<n_cta, kThreadsPair, smem, stream>>>(tm64, tm128, spec_a, spec_b, spec_c, rowA,
-                                                   rowB, rowC, G, m, FC, M, Mp, tiles, wq,
-                                                   cross, pref3, acc, plane, koff, status);
+  k2_bispec<kFC><<<n_cta, kThreadsPair, smem, stream>>>(tm64, tm128, spec_a, spec_b, spec_c,
+                                                        rowA, rowB, rowC, G, m, FC, M, Mp, tiles,
+                                                        wq, cross, pref3, acc, plane, koff,
+                                                        status);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
+                             const float2* spec_a, const float2* spec_b, const float2* spec_c,
+                             int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
+                             const TileInfo* tiles, int n_tiles, int cross, float pref3,
+                             double* acc, long long plane, int rows, int nsm, int* counter,
+                             int* status, cudaStream_t stream) {
+  if (G <= 0 || n_tiles <= 0) return cudaSuccess;
+#define K2_ARGS tm64, tm128, spec_a, spec_b, spec_c, rowA, rowB, rowC, G, m, FC, M, Mp, tiles, \
+                n_tiles, cross, pref3, acc, plane, rows, nsm, counter, status, stream
+  switch (FC) {
+    case 8: return launch_k2_t<8>(K2_ARGS);
+    case 10: return launch_k2_t<10>(K2_ARGS);
+    case 16: return launch_k2_t<16>(K2_ARGS);
+    default: return launch_k2_t<0>(K2_ARGS);
+  }
+#undef K2_ARGS
 }
 
 }  // namespace ss
