@@ -43,6 +43,9 @@ WORKLOADS = {
     "ar1q-2^20-T256-m10": dict(channels=1, n=1 << 20, T=256, m=10, seed=0, phi=0.9),
     # same shapes as the default at 1/8 of the length (profiling captures)
     "ar1q-2^25-T1024-m10": dict(channels=1, n=1 << 25, T=1024, m=10, seed=1, phi=0.9),
+    # 64 independent recordings, lengths log-uniform in [2^20, 2^26], T from
+    # {128, 256, 512, 1024}, AR coefficients uniform in [0.5, 0.98], one CUDA graph
+    "many64-2^20..2^26-m10": dict(channels=1, many=64, m=10, seed=100),
 }
 DEFAULT_WORKLOAD = "ar1q-2^28-T1024-m10"
 
@@ -162,7 +165,13 @@ def run_reference(args, w, rank, world):
         return
     import oracle
 
-    z = make_record(w, 0)
+    if "many" in w:  # a bounded sample: the first recording's process, T = 512
+        import synth
+
+        z = synth.ar1_quadratic(1 << 20, seed=w["seed"] + 1, phi=0.74)
+        w = dict(w, T=512)
+    else:
+        z = make_record(w, 0)
     T, m = w["T"], w["m"]
     groups_per_step = args.ref_groups
     n_step = groups_per_step * m * T
@@ -226,6 +235,76 @@ def error_vs_oracle(P, w, z, ref, groups, precision):
     return errs
 
 
+def make_many(w):
+    """Lengths, frame lengths and AR coefficients of the batched workload, then the
+    records (one seed per recording)."""
+    import synth
+
+    k = w["many"]
+    u = synth.uniform(3 * k, seed=w["seed"])
+    lens = [int(2.0 ** (20 + 6 * u[i])) for i in range(k)]
+    Ts = [(128, 256, 512, 1024)[min(3, int(4 * u[k + i]))] for i in range(k)]
+    phis = [0.5 + 0.48 * u[2 * k + i] for i in range(k)]
+    jobs = [(n, w["seed"] + 1 + i, phi) for i, (n, phi) in enumerate(zip(lens, phis))]
+    import multiprocessing as mp
+
+    # records generated in parallel, in spawned processes, before any CUDA call
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        zs = pool.starmap(_ar1q_job, jobs)
+    return Ts, zs
+
+
+def _ar1q_job(n, seed, phi):
+    import synth
+
+    return synth.ar1_quadratic(n, seed=seed, phi=phi)
+
+
+def run_many(args, w, rank, world):
+    """The batched-recordings workload: every step is one replay of the graph that
+    processes all recordings (reset, accumulate, finalize each)."""
+    Ts, zs = make_many(w)
+    import torch
+
+    import paper_2505_01231_gb300 as P
+
+    torch.cuda.set_device(0)
+    total = sum(len(z) for z in zs)
+    stream = torch.cuda.current_stream()
+    many = P.ManyPlan(Ts, [len(z) for z in zs], m=w["m"], precision=args.precision,
+                      stream=stream)
+    dz = [torch.from_numpy(z).cuda() for z in zs]
+    for _ in range(args.warmup):
+        many.run(dz)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        many.run(dz)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    line = {
+        "metric": METRIC, "value": total * args.steps / elapsed, "unit": "samples/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "recordings": len(zs), "samples": total,
+                   "T_counts": {str(t): Ts.count(t) for t in (128, 256, 512, 1024)},
+                   "m": w["m"], "s4_precision": args.precision,
+                   "l2": f"records of {4 * total / 2**30:.1f} GiB per step are larger than L2"},
+        "e2e": None, "gpu_launches": None, "roofline": None, "cpu_baseline": None,
+        "clocks": clock_info,
+    }
+    print(json.dumps(line), flush=True)
+    many.close()
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     ap = argparse.ArgumentParser()
@@ -247,6 +326,10 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, w, rank, world)
+        return
+    if "many" in w:
+        if rank == 0:
+            run_many(args, w, rank, world)
         return
 
     import torch

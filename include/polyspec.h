@@ -47,6 +47,7 @@ extern "C" {
 #endif
 
 typedef struct ss_plan_s* ss_plan_t;
+typedef struct ss_many_s* ss_many_t;
 
 typedef enum {
   SS_OK = 0,
@@ -224,6 +225,45 @@ ss_status ss_set_batch(ss_plan_t plan, int groups_per_batch);
 ss_status ss_state_size(ss_plan_t plan, size_t* n_doubles);
 ss_status ss_export_state(ss_plan_t plan, double* dst);
 ss_status ss_merge_state(ss_plan_t plan, const double* src);
+
+/*
+ * Many independent recordings in one CUDA graph (Sec. 3, Eq. 16-18 per
+ * recording; the estimate of each recording is the same as a one-channel
+ * ss_plan's).  Each recording has its own frame length and length and gets
+ * its own S2, S3 and S4 with error bars.
+ *
+ * ss_plan_many -- one-channel plans for n_rec recordings: T[i] is recording
+ *     i's frame length (a power of two in [8, 4096]), max_samples[i] the most
+ *     samples it will be given (at least two groups, m T[i] each); dt, m,
+ *     window, win_param, orders and precision are shared and mean what they
+ *     mean for ss_plan; stream is the cudaStream_t the runs are ordered on.
+ *     The device scratch of all recordings together is about 6 GiB; longer
+ *     recordings are processed in several batches inside the graph.
+ * ss_run_many -- for every recording i: reset, accumulate the n_samples[i]
+ *     float32 samples at chunks[i] (device memory) and finalize into S2[i],
+ *     S3[i], S4[i] and the *_err[i] (layouts as for ss_finalize of a
+ *     one-channel plan; device or page-locked host memory; a NULL list or
+ *     entry skips that output).  The first call captures all of it as one CUDA
+ *     graph (the recordings spread over four forked streams, longest first) and
+ *     launches it; later calls with the same chunks, n_samples and outputs
+ *     replay the graph, other arguments capture a new one.  Synchronises the
+ *     stream; returns SS_ETIMEOUT if a device-side wait of any recording gave
+ *     up.  The arrays are host arrays of n_rec entries.
+ * ss_many_plan -- the plan of recording i (owned by the handle; ss_query,
+ *     ss_stats, ss_export_state work on it; do not destroy it).
+ * ss_destroy_many -- release everything (NULL is accepted).
+ * ss_many_last_error -- text of the handle's last failure (or of the last
+ *     failed ss_plan_many when NULL).
+ */
+ss_status ss_plan_many(ss_many_t* out, int n_rec, const int* T, const size_t* max_samples,
+                       double dt, int m, int window, double win_param, unsigned orders,
+                       int precision, void* stream);
+ss_status ss_run_many(ss_many_t many, const void* const* chunks, const size_t* n_samples,
+                      double* const* S2, double* const* S3, double* const* S4,
+                      double* const* S2_err, double* const* S3_err, double* const* S4_err);
+ss_status ss_many_plan(ss_many_t many, int i, ss_plan_t* plan);
+ss_status ss_destroy_many(ss_many_t many);
+const char* ss_many_last_error(ss_many_t many);
 
 /* ss_destroy -- release every resource of the plan (NULL is accepted). */
 ss_status ss_destroy(ss_plan_t plan);

@@ -77,6 +77,13 @@ _sig = {
     "ss_state_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "ss_export_state": (ctypes.c_int, [_P, _P]),
     "ss_merge_state": (ctypes.c_int, [_P, _P]),
+    "ss_plan_many": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint,
+                                    ctypes.c_int, _P]),
+    "ss_run_many": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ss_many_plan": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "ss_destroy_many": (ctypes.c_int, [_P]),
+    "ss_many_last_error": (ctypes.c_char_p, [_P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -190,6 +197,50 @@ def ss_merge_state(plan, src):
     _check(lib.ss_merge_state(plan, _addr(src)), plan)
 
 
+def _check_many(status, handle):
+    if status != SS_OK:
+        raise SSError(status, lib.ss_many_last_error(handle).decode())
+
+
+def ss_plan_many(T_list, max_samples, dt, m, window=SS_WIN_HANN, win_param=0.14,
+                 orders=SS_ORDER2 | SS_ORDER3 | SS_ORDER4, precision=SS_PREC_FP32, stream=None):
+    """One-channel plans for many recordings; returns the handle (int)."""
+    n = len(T_list)
+    t = (ctypes.c_int * n)(*[int(v) for v in T_list])
+    ms = (ctypes.c_size_t * n)(*[int(v) for v in max_samples])
+    h = _P()
+    st = lib.ss_plan_many(ctypes.byref(h), n, t, ms, float(dt), m, window, float(win_param),
+                          orders, precision,
+                          _addr(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream)
+    _check_many(st, None)
+    return h.value
+
+
+def _ptr_array(bufs):
+    if bufs is None:
+        return None
+    return (_P * len(bufs))(*[_addr(b) for b in bufs])
+
+
+def ss_run_many(handle, chunks, n_samples, S2=None, S3=None, S4=None, S2_err=None,
+                S3_err=None, S4_err=None):
+    n = len(chunks)
+    ns = (ctypes.c_size_t * n)(*[int(v) for v in n_samples])
+    _check_many(lib.ss_run_many(handle, _ptr_array(chunks), ns, _ptr_array(S2), _ptr_array(S3),
+                                _ptr_array(S4), _ptr_array(S2_err), _ptr_array(S3_err),
+                                _ptr_array(S4_err)), handle)
+
+
+def ss_many_plan(handle, i):
+    h = _P()
+    _check_many(lib.ss_many_plan(handle, i, ctypes.byref(h)), handle)
+    return h.value
+
+
+def ss_destroy_many(handle):
+    _check_many(lib.ss_destroy_many(handle), handle)
+
+
 def ss_s2_noalloc(d_signal, n_samples, T, dt, m, window=SS_WIN_HANN, win_param=0.14,
                   d_S2=None, d_S2_err=None, stream=None):
     """Power spectrum of one device-resident float32 channel with no device allocation
@@ -199,6 +250,71 @@ def ss_s2_noalloc(d_signal, n_samples, T, dt, m, window=SS_WIN_HANN, win_param=0
                            _addr(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream)
     if st != SS_OK:
         raise SSError(st, lib.ss_noalloc_last_error().decode())
+
+
+class ManyPlan:
+    """Many one-channel recordings in one CUDA graph (ss_plan_many / ss_run_many).
+    Keeps device output buffers per recording, so repeated runs on the same input
+    tensors replay the captured graph."""
+
+    def __init__(self, T_list, max_samples, dt=1.0, m=10, window="hann", sigma_t=0.14,
+                 orders=(2, 3, 4), precision="fp32", stream=None):
+        import torch
+
+        win = {"hann": SS_WIN_HANN, "acg": SS_WIN_ACG}[window]
+        ords = 0
+        for o in orders:
+            ords |= 1 << o
+        prec = {"fp32": SS_PREC_FP32, "tf32x3": SS_PREC_TF32X3, "bf16x3": SS_PREC_BF16X3,
+                "bf16": SS_PREC_BF16}[precision]
+        self.handle = ss_plan_many(T_list, max_samples, dt, m, win, sigma_t, ords, prec, stream)
+        self.n = len(T_list)
+        self.outs = {}
+        for key in ("S2", "S3", "S4"):
+            self.outs[key], self.outs[key + "_err"] = [], []
+            for i in range(self.n):
+                info = ss_query(ss_many_plan(self.handle, i))
+                shape = {"S2": (info.n_s2, info.M), "S3": (info.n_s3, info.rows3, info.M),
+                         "S4": (info.n_s4, info.rows4, info.M)}[key]
+                cnt = int(np.prod(shape)) * 2
+                for k2 in (key, key + "_err"):
+                    self.outs[k2].append(torch.empty(max(cnt, 1), dtype=torch.float64,
+                                                     device="cuda") if cnt else None)
+
+    def plan(self, i):
+        return ss_many_plan(self.handle, i)
+
+    def run(self, chunks, n_samples=None):
+        if n_samples is None:
+            n_samples = [c.shape[-1] for c in chunks]
+        o = self.outs
+        ss_run_many(self.handle, chunks, n_samples, o["S2"], o["S3"], o["S4"], o["S2_err"],
+                    o["S3_err"], o["S4_err"])
+
+    def results(self, i):
+        """Spectra of recording i as numpy arrays (as Plan.finalize returns them)."""
+        info = ss_query(ss_many_plan(self.handle, i))
+        shapes = {"S2": (info.n_s2, info.M), "S3": (info.n_s3, info.rows3, info.M),
+                  "S4": (info.n_s4, info.rows4, info.M)}
+        out = {"G": info.groups}
+        for key, sh in shapes.items():
+            if self.outs[key][i] is None:
+                continue
+            v = self.outs[key][i].cpu().numpy().reshape(sh + (2,))
+            out[key] = v[..., 0] + 1j * v[..., 1]
+            out[key + "_err"] = self.outs[key + "_err"][i].cpu().numpy().reshape(sh + (2,))
+        return out
+
+    def close(self):
+        if self.handle:
+            ss_destroy_many(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

@@ -564,9 +564,11 @@ const char* ss_last_error(ss_plan_t plan) {
   return plan ? plan->err.c_str() : g_plan_error.c_str();
 }
 
-ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int window,
-                  double win_param, unsigned orders, int dtype, int precision,
-                  const int* combos, int n_combos, void* stream) {
+// ss_plan with a cap on groups per device batch applied before the scratch is
+// allocated (0 = automatic).
+static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int m, int window,
+                             double win_param, unsigned orders, int dtype, int precision,
+                             const int* combos, int n_combos, void* stream, int batch) {
   if (!out) return fail(nullptr, SS_EINVAL, "out is NULL");
   *out = nullptr;
   if (channels < 1 || channels > 4) return fail(nullptr, SS_EINVAL, "channels must be 1..4");
@@ -737,6 +739,7 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   if (!t4tc.empty())
     PLAN_TRY(cudaMemcpy(p->d_tiles4tc, t4tc.data(), t4tc.size() * sizeof(TileInfo),
                         cudaMemcpyHostToDevice));
+  p->Gb_user = batch;
   st = alloc_spec(p);
   if (st != SS_OK) {
     g_plan_error = p->err;
@@ -758,6 +761,13 @@ ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int win
   return SS_OK;
 }
 
+ss_status ss_plan(ss_plan_t* out, int channels, int T, double dt, int m, int window,
+                  double win_param, unsigned orders, int dtype, int precision,
+                  const int* combos, int n_combos, void* stream) {
+  return plan_create(out, channels, T, dt, m, window, win_param, orders, dtype, precision,
+                     combos, n_combos, stream, 0);
+}
+
 ss_status ss_accumulate(ss_plan_t p, const void* chunk, size_t n_samples) {
   if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
   if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
@@ -770,13 +780,8 @@ ss_status ss_accumulate(ss_plan_t p, const void* chunk, size_t n_samples) {
   return process_host(p, chunk, (long long)n_samples);
 }
 
-ss_status ss_finalize(ss_plan_t p, double* S2, double* S3, double* S4, double* S2_err,
-                      double* S3_err, double* S4_err) {
-  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
-  if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
-  if (p->groups < 2)
-    return fail(p, SS_ESTATE, "fewer than two groups accumulated: no error estimate (Eq. 35)");
-  DeviceGuard guard(p->device);
+// The finalize buffer: means and errors of every spectrum (complex doubles).
+static ss_status ensure_out(ss_plan_s* p) {
   const size_t n2 = p->c2.size() * p->M * 2;
   const size_t n3 = p->c3.size() * p->rows3 * p->M * 2;
   const size_t n4 = p->c4.size() * p->rows4 * p->M * 2;
@@ -786,10 +791,22 @@ ss_status ss_finalize(ss_plan_t p, double* S2, double* S3, double* S4, double* S
       cudaFree(p->d_out);
       p->device_bytes -= p->out_doubles * sizeof(double);
       p->d_out = nullptr;
+      p->out_doubles = 0;
     }
     SS_TRY(p, dev_alloc(p, &p->d_out, need * sizeof(double)));
     p->out_doubles = need;
   }
+  return SS_OK;
+}
+
+// K4 and the copies to the caller's buffers, stream-ordered (no synchronisation).
+static ss_status finalize_launch(ss_plan_s* p, double* S2, double* S3, double* S4,
+                                 double* S2_err, double* S3_err, double* S4_err) {
+  ss_status st0 = ensure_out(p);
+  if (st0 != SS_OK) return st0;
+  const size_t n2 = p->c2.size() * p->M * 2;
+  const size_t n3 = p->c3.size() * p->rows3 * p->M * 2;
+  const size_t n4 = p->c4.size() * p->rows4 * p->M * 2;
   double* o2 = p->d_out;
   double* e2 = o2 + n2;
   double* o3 = e2 + n2;
@@ -819,6 +836,18 @@ ss_status ss_finalize(ss_plan_t p, double* S2, double* S3, double* S4, double* S
     if (c.first && c.second.second)
       SS_TRY(p, cudaMemcpyAsync(c.first, c.second.first, c.second.second * sizeof(double),
                                 cudaMemcpyDefault, p->stream));
+  return SS_OK;
+}
+
+ss_status ss_finalize(ss_plan_t p, double* S2, double* S3, double* S4, double* S2_err,
+                      double* S3_err, double* S4_err) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
+  if (p->groups < 2)
+    return fail(p, SS_ESTATE, "fewer than two groups accumulated: no error estimate (Eq. 35)");
+  DeviceGuard guard(p->device);
+  ss_status st = finalize_launch(p, S2, S3, S4, S2_err, S3_err, S4_err);
+  if (st != SS_OK) return st;
   SS_TRY(p, cudaStreamSynchronize(p->stream));
   return check_status(p);
 }
@@ -1021,6 +1050,252 @@ ss_status ss_destroy(ss_plan_t p) {
   DeviceGuard guard(p->device);
   destroy(p);
   return SS_OK;
+}
+
+// ------------------------------------------------------------------------
+// Many independent recordings (single channel each, frame lengths and record
+// lengths of their own) processed as one CUDA graph: per recording ss_reset,
+// ss_accumulate of the whole record from device memory and ss_finalize into
+// device buffers, the recordings spread over kBranches forked streams so that
+// small ones overlap.  The graph is captured on the first ss_run_many and
+// replayed while the inputs and outputs stay the same.
+}  // extern "C"
+
+namespace {
+constexpr int kBranches = 4;
+constexpr size_t kManyScratch = 6ull << 30;  // per-batch scratch of all recordings together
+thread_local std::string g_many_error;
+}  // namespace
+
+struct ss_many_s {
+  std::vector<ss_plan_s*> plans;
+  std::vector<long long> max_n;
+  std::vector<int> order;  // recordings by decreasing length (branch assignment)
+  cudaStream_t stream = nullptr;   // the caller's: the graph is launched on it
+  cudaStream_t cap = nullptr;      // own stream the graph is captured on
+  cudaStream_t branch[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> cap_in;
+  std::vector<size_t> cap_n;
+  std::vector<double*> cap_out;  // 6 per recording
+  int device = 0;
+  std::string err;
+};
+
+namespace {
+
+ss_status many_fail(ss_many_s* mp, ss_status st, const std::string& msg) {
+  if (mp)
+    mp->err = msg;
+  else
+    g_many_error = msg;
+  return st;
+}
+
+void many_release(ss_many_s* mp) {
+  if (!mp) return;
+  if (mp->exec) cudaGraphExecDestroy(mp->exec);
+  if (mp->graph) cudaGraphDestroy(mp->graph);
+  mp->exec = nullptr;
+  mp->graph = nullptr;
+  for (ss_plan_s* p : mp->plans) destroy(p);
+  mp->plans.clear();
+  for (int b = 0; b < kBranches; ++b) {
+    if (mp->branch[b]) cudaStreamDestroy(mp->branch[b]);
+    if (mp->join[b]) cudaEventDestroy(mp->join[b]);
+  }
+  if (mp->fork) cudaEventDestroy(mp->fork);
+  if (mp->cap) cudaStreamDestroy(mp->cap);
+}
+
+bool device_or_pinned(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
+         a.type == cudaMemoryTypeHost;
+}
+
+}  // namespace
+
+extern "C" {
+
+ss_status ss_plan_many(ss_many_t* out, int n_rec, const int* T, const size_t* max_samples,
+                       double dt, int m, int window, double win_param, unsigned orders,
+                       int precision, void* stream) {
+  if (!out) return many_fail(nullptr, SS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_rec < 1 || !T || !max_samples)
+    return many_fail(nullptr, SS_EINVAL, "need n_rec >= 1 and the T and max_samples arrays");
+  std::vector<long long> groups(n_rec);
+  double total = 0.0;
+  for (int i = 0; i < n_rec; ++i) {
+    if (T[i] < 8 || T[i] > 4096 || (T[i] & (T[i] - 1)))
+      return many_fail(nullptr, SS_EINVAL,
+                       "recording " + std::to_string(i) + ": T must be a power of two in [8, 4096]");
+    if (m < 2) return many_fail(nullptr, SS_EINVAL, "m >= 2 required");
+    groups[i] = (long long)(max_samples[i] / ((size_t)m * T[i]));
+    if (groups[i] < 2)
+      return many_fail(nullptr, SS_EINVAL,
+                       "recording " + std::to_string(i) + " holds fewer than two groups");
+    const int Mp = ((T[i] / 2 + 1) + 15) & ~15;
+    total += (double)groups[i] * m * Mp * 8.0 * (precision == SS_PREC_FP32 ? 1.0 : 5.0);
+  }
+  ss_many_s* mp = new ss_many_s();
+  mp->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&mp->device);
+  for (int i = 0; i < n_rec; ++i) {
+    // the scratch budget is shared in proportion to each recording's groups
+    long long gb = groups[i];
+    if (total > (double)kManyScratch)
+      gb = std::max(1ll, (long long)((double)groups[i] * (double)kManyScratch / total));
+    ss_plan_t p = nullptr;
+    ss_status st = plan_create(&p, 1, T[i], dt, m, window, win_param, orders, SS_F32, precision,
+                               nullptr, 0, stream, (int)std::min<long long>(gb, 1 << 30));
+    if (st == SS_OK) st = ensure_out(p);
+    if (st != SS_OK) {
+      const std::string why = p ? p->err : g_plan_error;
+      if (p) destroy(p);
+      many_release(mp);
+      delete mp;
+      return many_fail(nullptr, st, "recording " + std::to_string(i) + ": " + why);
+    }
+    mp->plans.push_back(p);
+    mp->max_n.push_back((long long)max_samples[i]);
+  }
+  mp->order.resize(n_rec);
+  for (int i = 0; i < n_rec; ++i) mp->order[i] = i;
+  std::stable_sort(mp->order.begin(), mp->order.end(),
+                   [&](int a, int b) { return max_samples[a] > max_samples[b]; });
+  cudaError_t e = cudaEventCreateWithFlags(&mp->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mp->cap, cudaStreamNonBlocking);
+  for (int b = 0; b < kBranches && e == cudaSuccess; ++b) {
+    e = cudaStreamCreateWithFlags(&mp->branch[b], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&mp->join[b], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    many_release(mp);
+    delete mp;
+    return many_fail(nullptr, SS_ECUDA, std::string("stream set-up: ") + cudaGetErrorString(e));
+  }
+  *out = mp;
+  return SS_OK;
+}
+
+ss_status ss_run_many(ss_many_t mp, const void* const* chunks, const size_t* n_samples,
+                      double* const* S2, double* const* S3, double* const* S4,
+                      double* const* S2_err, double* const* S3_err, double* const* S4_err) {
+  if (!mp) return many_fail(nullptr, SS_EINVAL, "handle is NULL");
+  if (!chunks || !n_samples) return many_fail(mp, SS_EINVAL, "chunks and n_samples are required");
+  DeviceGuard guard(mp->device);
+  const int n = (int)mp->plans.size();
+  std::vector<double*> outs(6 * (size_t)n, nullptr);
+  double* const* lists[6] = {S2, S2_err, S3, S3_err, S4, S4_err};
+  for (int i = 0; i < n; ++i) {
+    ss_plan_s* p = mp->plans[i];
+    if (p->broken) return many_fail(mp, SS_ESTATE, "recording " + std::to_string(i) + ": " + p->err);
+    if (!chunks[i] || !is_device_ptr(chunks[i]))
+      return many_fail(mp, SS_EINVAL, "recording " + std::to_string(i) + ": chunk must be device memory");
+    if ((long long)n_samples[i] > mp->max_n[i])
+      return many_fail(mp, SS_EINVAL, "recording " + std::to_string(i) + ": more samples than planned");
+    if ((long long)(n_samples[i] / ((size_t)p->m * p->T)) < 2)
+      return many_fail(mp, SS_EINVAL, "recording " + std::to_string(i) + ": fewer than two groups");
+    for (int k = 0; k < 6; ++k) {
+      double* o = lists[k] ? lists[k][i] : nullptr;
+      if (o && !device_or_pinned(o))
+        return many_fail(mp, SS_EINVAL, "recording " + std::to_string(i) +
+                                            ": outputs must be device or page-locked host memory");
+      outs[6 * (size_t)i + k] = o;
+    }
+  }
+  const bool same = mp->exec && mp->cap_n.size() == (size_t)n &&
+                    std::equal(mp->cap_n.begin(), mp->cap_n.end(), n_samples) &&
+                    std::equal(mp->cap_in.begin(), mp->cap_in.end(), chunks) &&
+                    mp->cap_out == outs;
+  if (!same) {
+    if (mp->exec) cudaGraphExecDestroy(mp->exec);
+    if (mp->graph) cudaGraphDestroy(mp->graph);
+    mp->exec = nullptr;
+    mp->graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(mp->cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess)
+      return many_fail(mp, SS_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    ss_status st = SS_OK;
+    e = cudaEventRecord(mp->fork, mp->cap);
+    for (int b = 0; b < kBranches && e == cudaSuccess; ++b)
+      e = cudaStreamWaitEvent(mp->branch[b], mp->fork, 0);
+    if (e != cudaSuccess) st = many_fail(mp, SS_ECUDA, cudaGetErrorString(e));
+    for (int r = 0; r < n && st == SS_OK; ++r) {
+      const int i = mp->order[r];
+      ss_plan_s* p = mp->plans[i];
+      const cudaStream_t own = p->stream;
+      p->stream = mp->branch[r % kBranches];
+      st = zero_state(p);
+      if (st == SS_OK) st = process_device(p, chunks[i], (long long)n_samples[i], (long long)n_samples[i]);
+      if (st == SS_OK)
+        st = finalize_launch(p, outs[6 * i + 0], outs[6 * i + 2], outs[6 * i + 4],
+                             outs[6 * i + 1], outs[6 * i + 3], outs[6 * i + 5]);
+      p->stream = own;
+      if (st != SS_OK) st = many_fail(mp, st, "recording " + std::to_string(i) + ": " + p->err);
+    }
+    for (int b = 0; b < kBranches && st == SS_OK; ++b) {
+      e = cudaEventRecord(mp->join[b], mp->branch[b]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(mp->cap, mp->join[b], 0);
+      if (e != cudaSuccess) st = many_fail(mp, SS_ECUDA, cudaGetErrorString(e));
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(mp->cap, &g);
+    if (st != SS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess)
+      return many_fail(mp, SS_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    mp->graph = g;
+    e = cudaGraphInstantiate(&mp->exec, g, 0);
+    if (e != cudaSuccess) {
+      mp->exec = nullptr;
+      return many_fail(mp, SS_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    mp->cap_in.assign(chunks, chunks + n);
+    mp->cap_n.assign(n_samples, n_samples + n);
+    mp->cap_out = outs;
+  }
+  cudaError_t e = cudaGraphLaunch(mp->exec, mp->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(mp->stream);
+  if (e != cudaSuccess)
+    return many_fail(mp, SS_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  for (int i = 0; i < n; ++i) {
+    ss_status st = check_status(mp->plans[i]);
+    if (st != SS_OK)
+      return many_fail(mp, st, "recording " + std::to_string(i) + ": " + mp->plans[i]->err);
+  }
+  mp->err.clear();
+  return SS_OK;
+}
+
+ss_status ss_many_plan(ss_many_t mp, int i, ss_plan_t* plan) {
+  if (!mp || !plan) return many_fail(mp, SS_EINVAL, "NULL argument");
+  if (i < 0 || i >= (int)mp->plans.size()) return many_fail(mp, SS_EINVAL, "index out of range");
+  *plan = mp->plans[i];
+  return SS_OK;
+}
+
+ss_status ss_destroy_many(ss_many_t mp) {
+  if (!mp) return SS_OK;
+  DeviceGuard guard(mp->device);
+  if (mp->stream) cudaStreamSynchronize(mp->stream);
+  many_release(mp);
+  delete mp;
+  return SS_OK;
+}
+
+const char* ss_many_last_error(ss_many_t mp) {
+  return mp ? mp->err.c_str() : g_many_error.c_str();
 }
 
 }  // extern "C"

@@ -69,6 +69,9 @@ def test_null_plan_calls_fail_cleanly():
     assert P.lib.ss_state_size(None, None) == P.SS_EINVAL
     assert P.lib.ss_export_state(None, None) == P.SS_EINVAL
     assert P.lib.ss_merge_state(None, None) == P.SS_EINVAL
+    assert P.lib.ss_run_many(None, None, None, None, None, None, None, None, None) == P.SS_EINVAL
+    assert P.lib.ss_many_plan(None, 0, None) == P.SS_EINVAL
+    assert P.lib.ss_destroy_many(None) == P.SS_OK
     assert P.lib.ss_destroy(None) == P.SS_OK
 
 
@@ -82,3 +85,13 @@ def test_tensor_core_s4_rejects_more_than_32_frames(precision):
         P.ss_plan(**args)
     assert ei.value.status == P.SS_EUNSUPPORTED
     assert "m <= 32" in str(ei.value)
+
+
+@pytest.mark.parametrize("Ts,lens,msg", [([100, 64], [10000, 10000], "power of two"),
+                                         ([64, 64], [10000, 700], "fewer than two groups"),
+                                         ([], [], "n_rec")])
+def test_plan_many_rejects_invalid_arguments(Ts, lens, msg):
+    with pytest.raises(P.SSError) as ei:
+        P.ss_plan_many(Ts, lens, 1.0, 6)
+    assert ei.value.status == P.SS_EINVAL
+    assert msg in str(ei.value)
