@@ -160,6 +160,74 @@ __device__ __forceinline__ float load_sample(const SampleSource& s, int c, long 
   return (float)__ldg(static_cast<const short*>(s.chunk) + o);
 }
 
+// Centre bin k over the group's m frames (subtract the mean, the samples of the
+// factorised k-statistics, App. H, Eq. 85), store the centred coefficients,
+// add the per-group S2 estimate c2 = 1/(m-1) sum_j |d_j|^2 (Eq. 32) to the
+// CTA's float32 sums, and, with an operand image, write the bin's weighted Gram
+// products (diagonal chunks sqrt(w_jj r) |d_j|^2, then the pairs j < j' in
+// lexicographic order, sqrt(4(m-1) r) Re(d_j d_j'*), 16 per chunk, zero-padded)
+// and its ps value.  fetch(j) gives frame j's coefficient, store(j, d) keeps the
+// centred one.
+template <int FMT, class Fetch, class Store>
+__device__ __forceinline__ void centre_bin(int k, bool valid, float2 mean, int m, int c, int g,
+                                           int Mp, const OperandImage& oi, Fetch fetch,
+                                           Store store, float* s2sum, float* s2sq, float pref2) {
+  float p = 0.f;
+  if constexpr (FMT == kImageNone) {
+    for (int j = 0; j < m; ++j) {
+      const float2 d = valid ? csub(fetch(j), mean) : make_float2(0.f, 0.f);
+      store(j, d);
+      p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+    }
+  } else {
+    float dr[kMaxGramM], di[kMaxGramM];
+    for (int j = 0; j < m; ++j) {
+      const float2 d = valid ? csub(fetch(j), mean) : make_float2(0.f, 0.f);
+      store(j, d);
+      dr[j] = d.x;
+      di[j] = d.y;
+      p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+    }
+    const int npair = m * (m - 1) / 2;
+    int pj = 0, pk = 1;  // next off-diagonal pair (j, j'), lexicographic
+    constexpr int kChunkBytes = FMT == kImageGramTF32 ? 1024 : 512;  // 2 CB
+    unsigned char* rbase = static_cast<unsigned char*>(oi.img) + (size_t)c * oi.chan_bytes +
+                           (size_t)g * oi.group_bytes + (size_t)(k >> 3) * oi.rg_bytes +
+                           (k & 7) * 16;
+    for (int ch = 0; ch < oi.nkc; ++ch) {
+      float e[16];
+      if (ch < oi.ndc) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int j = ch * 16 + t;
+          e[t] = j < m ? oi.sd * fmaf(dr[j], dr[j], di[j] * di[j]) : 0.f;
+        }
+      } else {
+        const int p0 = (ch - oi.ndc) * 16;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          if (p0 + t < npair) {
+            e[t] = oi.so * fmaf(dr[pj], dr[pk], di[pj] * di[pk]);
+            if (++pk == m) {
+              ++pj;
+              pk = pj + 1;
+            }
+          } else {
+            e[t] = 0.f;
+          }
+        }
+      }
+      write_gram_row<FMT>(rbase + ch * kChunkBytes, e);
+    }
+    oi.ps[(long long)c * oi.chan_ps + (long long)g * Mp + k] = oi.sp * p;
+  }
+  if (valid && s2sum) {
+    const float c2 = p * pref2;
+    s2sum[k] += c2;
+    s2sq[k] = fmaf(c2, c2, s2sq[k]);
+  }
+}
+
 template <int DTYPE, int FMT>
 __global__ void __launch_bounds__(kThreadsK1)
 k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int M, int Mp,
@@ -228,50 +296,199 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
         const bool valid = k < M;
         const float2 mean = valid ? make_float2(gsum[k].x * inv_m, gsum[k].y * inv_m)
                                   : make_float2(0.f, 0.f);
-        float p = 0.f;
-        if constexpr (FMT == kImageNone) {
-          for (int j = 0; j < m; ++j) {
-            float2* e = grow + (long long)j * Mp + k;
-            const float2 d = valid ? csub(*e, mean) : make_float2(0.f, 0.f);
-            *e = d;
-            p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+        centre_bin<FMT>(
+            k, valid, mean, m, c, g, Mp, oi,
+            [&](int j) { return grow[(long long)j * Mp + k]; },
+            [&](int j, float2 d) { grow[(long long)j * Mp + k] = d; },
+            ia >= 0 ? s2sum + c * M : nullptr, ia >= 0 ? s2sq + c * M : nullptr, pref2);
+      }
+    }
+  }
+  __syncthreads();
+  // flush the CTA's float32 partial sums into the float64 accumulators
+  const long long plane = (long long)n_s2 * M;
+  for (int c = 0; c < C; ++c) {
+    const int ia = s2_auto[c];
+    if (ia < 0) continue;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+      atomicAdd(acc2 + 0 * plane + (long long)ia * M + k, (double)s2sum[c * M + k]);
+      atomicAdd(acc2 + 2 * plane + (long long)ia * M + k, (double)s2sq[c * M + k]);
+    }
+  }
+}
+
+// Stockham pass over a batch of FB frames of N points (frame f at x + f N);
+// all threads share the FB * N/R butterflies of the pass.
+template <int R>
+__device__ __forceinline__ void stockham_pass_batch(const float2* __restrict__ x,
+                                                    float2* __restrict__ y, int N, int Ns,
+                                                    const float2* __restrict__ tw, int T, int FB) {
+  const int NR = N / R;
+  const int lg = __ffs(NR) - 1;  // NR is a power of two
+  const int tw_scale = T / (Ns * R);
+  for (int idx = threadIdx.x; idx < FB * NR; idx += blockDim.x) {
+    const int f = idx >> lg, j = idx & (NR - 1);
+    const float2* xf = x + f * N;
+    float2* yf = y + f * N;
+    const int k = j & (Ns - 1);
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = xf[j + r * NR];
+    if (Ns > 1) {
+      const int step = k * tw_scale;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * step]);
+    }
+    dft<R>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) yf[base + q * Ns] = v[q];
+  }
+}
+
+// K1 for groups whose coefficients fit in shared memory: the group's m frames
+// are transformed FB at a time (every Stockham pass covers all FB frames, so a
+// frame costs a fraction of the barriers), the coefficients X_jk stay in shared
+// memory, and the centred coefficients are written to the spectra once.  Same
+// results as k1_spectra; the samples of a batch are contiguous and are read
+// with 16-byte (float32) or 8-byte (int16) loads when aligned.
+template <int DTYPE, int FMT>
+__global__ void __launch_bounds__(kThreadsK1)
+k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, int M, int Mp,
+               int FB, const float* __restrict__ win, const float2* __restrict__ tw,
+               float2* __restrict__ spec, long long chan_stride, const int* __restrict__ s2_auto,
+               double* __restrict__ acc2, int n_s2, float pref2, OperandImage oi) {
+  extern __shared__ float4 smem_raw[];
+  const int N = T / 2;
+  float2* bufA = reinterpret_cast<float2*>(smem_raw);  // [FB][N]
+  float2* bufB = bufA + FB * N;                        // [FB][N]
+  float2* Xs = bufB + FB * N;                          // [m][Mp]
+  float2* tws = Xs + m * Mp;                           // [T] twiddles e^{+2 pi j a/T}
+  float* wins = reinterpret_cast<float*>(tws + T);     // [T] window / sqrt(sum g^2)
+  float* s2sum = wins + T;                             // [C][M]
+  float* s2sq = s2sum + C * M;                         // [C][M]
+  constexpr int kVec = DTYPE == SS_F32 ? 16 : 8;        // bytes per vector load (4 samples)
+
+  for (int i = threadIdx.x; i < 2 * C * M; i += blockDim.x) s2sum[i] = 0.f;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    tws[i] = __ldg(&tw[i]);
+    wins[i] = __ldg(&win[i]);
+  }
+
+  for (int g = blockIdx.x; g < G; g += gridDim.x) {
+    for (int c = 0; c < C; ++c) {
+      float2* grow = spec + (long long)c * chan_stride + (long long)g * m * Mp;
+      for (int j0 = 0; j0 < m; j0 += FB) {
+        const int nf = min(FB, m - j0);
+        const long long s0 = sample0 + ((long long)g * m + j0) * T;  // first sample of the batch
+        __syncthreads();  // the buffers are free (previous batch split, previous group centred)
+        const long long off = s0 - src.carry_n;
+        const char* cbase = static_cast<const char*>(src.chunk) +
+                            ((long long)c * src.chunk_stride + off) * (DTYPE == SS_F32 ? 4 : 2);
+        if (off >= 0 && ((uintptr_t)cbase % kVec) == 0) {
+          for (int q = threadIdx.x; q < nf * T / 4; q += blockDim.x) {
+            const int i = (4 * q) & (T - 1), f = (4 * q) / T;
+            float x0, x1, x2, x3;
+            if constexpr (DTYPE == SS_F32) {
+              const float4 v = __ldg(reinterpret_cast<const float4*>(cbase) + q);
+              x0 = v.x; x1 = v.y; x2 = v.z; x3 = v.w;
+            } else {
+              const short4 v = __ldg(reinterpret_cast<const short4*>(cbase) + q);
+              x0 = v.x; x1 = v.y; x2 = v.z; x3 = v.w;
+            }
+            const float4 w = *reinterpret_cast<const float4*>(wins + i);
+            float2* d = bufA + f * N + i / 2;
+            d[0] = make_float2(x0 * w.x, x1 * w.y);
+            d[1] = make_float2(x2 * w.z, x3 * w.w);
           }
         } else {
-          // centred samples of this bin, then the weighted Gram entries in K order:
-          // diagonal chunks (sqrt(m^2-m+2) |d_j|^2), then the pairs j < j'
-          // (sqrt(4(m-1)) Re(d_j d_j'*)), 16 per chunk, zero-padded
-          float dr[kMaxGramM], di[kMaxGramM];
-          for (int j = 0; j < m; ++j) {
-            float2* ep = grow + (long long)j * Mp + k;
-            const float2 d = valid ? csub(*ep, mean) : make_float2(0.f, 0.f);
-            *ep = d;
-            dr[j] = d.x;
-            di[j] = d.y;
-            p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+          for (int q = threadIdx.x; q < nf * N; q += blockDim.x) {
+            const int f = q / N, n = q - f * N;
+            const long long si = s0 + (long long)f * T + 2 * n;
+            bufA[q] = make_float2(load_sample<DTYPE>(src, c, si) * wins[2 * n],
+                                  load_sample<DTYPE>(src, c, si + 1) * wins[2 * n + 1]);
           }
+        }
+        __syncthreads();
+        float2* x = bufA;
+        float2* y = bufB;
+        int Ns = 1;
+        int rem = N;
+        while (rem > 1) {
+          if (rem % 8 == 0 && rem != 16) {
+            stockham_pass_batch<8>(x, y, N, Ns, tws, T, nf);
+            Ns *= 8; rem /= 8;
+          } else if (rem % 4 == 0) {
+            stockham_pass_batch<4>(x, y, N, Ns, tws, T, nf);
+            Ns *= 4; rem /= 4;
+          } else {
+            stockham_pass_batch<2>(x, y, N, Ns, tws, T, nf);
+            Ns *= 2; rem /= 2;
+          }
+          __syncthreads();
+          float2* t = x; x = y; y = t;
+        }
+        // X_k = 1/2 [(Y_k + Y*_{N-k}) - j w^k (Y_k - Y*_{N-k})], w = e^{+2 pi j/T}
+        for (int f = 0; f < nf; ++f) {
+          const float2* xf = x + f * N;
+          float2* xr = Xs + (j0 + f) * Mp;
+          for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            const float2 yk = xf[k == N ? 0 : k];
+            const float2 yr = xf[k == 0 ? 0 : N - k];
+            const float2 yc = make_float2(yr.x, -yr.y);
+            const float2 sm = cadd(yk, yc);
+            const float2 wd = cmul(tws[k], csub(yk, yc));
+            xr[k] = make_float2(0.5f * (sm.x + wd.y), 0.5f * (sm.y - wd.x));
+          }
+        }
+      }
+      __syncthreads();  // the group's coefficients are in shared memory
+      const float inv_m = 1.0f / (float)m;
+      const int ia = s2_auto[c];
+      for (int k = threadIdx.x; k < Mp; k += blockDim.x) {
+        // thread = bin: centre the column in place, write it out once
+        const bool valid = k < M;
+        float2 mean = make_float2(0.f, 0.f);
+        if (valid) {
+          for (int j = 0; j < m; ++j) mean = cadd(mean, Xs[j * Mp + k]);
+          mean = make_float2(mean.x * inv_m, mean.y * inv_m);
+        }
+        float p = 0.f;
+        for (int j = 0; j < m; ++j) {
+          const float2 d = valid ? csub(Xs[j * Mp + k], mean) : make_float2(0.f, 0.f);
+          Xs[j * Mp + k] = d;
+          grow[(long long)j * Mp + k] = d;
+          p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+        }
+        if constexpr (FMT != kImageNone) {
+          // weighted Gram products of the bin in K order, read from the centred column
           const int npair = m * (m - 1) / 2;
-          int pj = 0, pk = 1;  // next off-diagonal pair (j, j'), lexicographic
+          int pj = 0, pk = 1;
+          float2 dj = Xs[k];
           constexpr int kChunkBytes = FMT == kImageGramTF32 ? 1024 : 512;  // 2 CB
-          unsigned char* rbase = static_cast<unsigned char*>(oi.img) + (size_t)c * oi.chan_bytes +
-                                 (size_t)g * oi.group_bytes + (size_t)(k >> 3) * oi.rg_bytes +
-                                 (k & 7) * 16;
+          unsigned char* rbase = static_cast<unsigned char*>(oi.img) +
+                                 (size_t)c * oi.chan_bytes + (size_t)g * oi.group_bytes +
+                                 (size_t)(k >> 3) * oi.rg_bytes + (k & 7) * 16;
           for (int ch = 0; ch < oi.nkc; ++ch) {
             float e[16];
             if (ch < oi.ndc) {
 #pragma unroll
               for (int t = 0; t < 16; ++t) {
                 const int j = ch * 16 + t;
-                e[t] = j < m ? oi.sd * fmaf(dr[j], dr[j], di[j] * di[j]) : 0.f;
+                const float2 d = j < m ? Xs[j * Mp + k] : make_float2(0.f, 0.f);
+                e[t] = oi.sd * fmaf(d.x, d.x, d.y * d.y);
               }
             } else {
               const int p0 = (ch - oi.ndc) * 16;
 #pragma unroll
               for (int t = 0; t < 16; ++t) {
                 if (p0 + t < npair) {
-                  e[t] = oi.so * fmaf(dr[pj], dr[pk], di[pj] * di[pk]);
+                  const float2 d2 = Xs[pk * Mp + k];
+                  e[t] = oi.so * fmaf(dj.x, d2.x, dj.y * d2.y);
                   if (++pk == m) {
                     ++pj;
                     pk = pj + 1;
+                    dj = Xs[pj * Mp + k];
                   }
                 } else {
                   e[t] = 0.f;
@@ -291,7 +508,6 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
     }
   }
   __syncthreads();
-  // flush the CTA's float32 partial sums into the float64 accumulators
   const long long plane = (long long)n_s2 * M;
   for (int c = 0; c < C; ++c) {
     const int ia = s2_auto[c];
@@ -347,6 +563,30 @@ cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C
                         long long spec_chan_stride, const int* s2_auto, double* acc2, int n_s2,
                         float pref2, const OperandImage& oi, int grid, size_t smem,
                         cudaStream_t stream) {
+  // a group whose coefficients fit beside a batch of FFT buffers stays resident
+  const size_t fixed = (size_t)m * Mp * sizeof(float2) + (size_t)2 * C * M * sizeof(float) +
+                       (size_t)T * (sizeof(float2) + sizeof(float));  // + twiddles and window
+  const size_t per_frame = (size_t)T * sizeof(float2);  // two buffers of T/2 points
+  if (fixed + per_frame <= kK1ResidentBytes) {
+    const int FB = (int)std::min<size_t>((size_t)m, (kK1ResidentBytes - fixed) / per_frame);
+    const size_t rsmem = fixed + (size_t)FB * per_frame;
+    cudaError_t e = cudaFuncSetAttribute(k1_spectra_res<DTYPE, FMT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+    if (e != cudaSuccess) return e;
+    // one wave: as many CTAs as are resident at once
+    int dev = 0, nsm = 1, occ = 1;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k1_spectra_res<DTYPE, FMT>,
+                                                        kThreadsK1, rsmem);
+    if (e != cudaSuccess) return e;
+    const int rgrid = std::max(1, std::min(G, nsm * std::max(1, occ)));
+    k1_spectra_res<DTYPE, FMT><<<rgrid, kThreadsK1, rsmem, stream>>>(
+        src, sample0, G, C, T, m, M, Mp, FB, win, tw, spec, spec_chan_stride, s2_auto, acc2, n_s2,
+        pref2, oi);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaFuncSetAttribute(k1_spectra<DTYPE, FMT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
