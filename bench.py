@@ -448,6 +448,25 @@ def main():
         else:
             s4_peak, s4_src = bf16_peak, "measured (MEASURED_PEAKS.json, bf16 burst)"
         s4_unit, s4_bound = "TFLOP/s", "tensor"
+    # ---- K1 against HBM: algorithmic bytes = samples in (4 B), centred spectra out
+    # (8 B per bin and frame, bins padded to a multiple of 16) and, in the split
+    # modes, the operand image (hi and lo of ceil(m/16) + ceil(m(m-1)/2 / 16) chunks of
+    # 16 products per bin, TF32 4 B, BF16 2 B each part) and the ps values (4 B per bin)
+    Mp = ((T // 2 + 1) + 15) // 16 * 16
+    k1_bytes = groups * (m * T * 4 * C + m * Mp * 8 * C)
+    if args.precision != "fp32":
+        nkc = (m + 15) // 16 + (m * (m - 1) // 2 + 15) // 16
+        k1_bytes += groups * C * Mp * (nkc * 16 * 2 * (4 if args.precision == "tf32x3" else 2) + 4)
+    k1_ms = stage_ms[0] / args.steps
+    k1_ach = k1_bytes / (k1_ms / 1e3) / 1e9 if k1_ms > 0 else None
+    roofline_k1 = {"bound": "hbm", "kernel": "k1_spectra", "achieved": k1_ach,
+                   "peak": float(pk.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                   "frac": (k1_ach / float(pk.get("hbm_gbs", 6800.0))) if k1_ach else None,
+                   "traffic": traffic_for("k1_spectra_" + args.precision),
+                   "traffic_note": "DRAM bytes per launch (ncu); a step is "
+                                   f"{n_batches} launches",
+                   "algorithmic_bytes_per_step": k1_bytes,
+                   "peak_source": "measured (MEASURED_PEAKS.json)", "ms_per_step": k1_ms}
     s4_ach = s4_flops / (s4_ms / 1e3) / 1e12 if s4_ms > 0 else None
     roofline_s4 = {"bound": s4_bound, "kernel": "k3_trispec", "achieved": s4_ach,
                    "peak": s4_peak, "unit": s4_unit,
@@ -501,7 +520,7 @@ def main():
                        "orders": "S2+S3+S4 full grids", "s4_precision": args.precision,
                        "l2": "record of 1 GiB per step is larger than L2; no flush"},
             "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
-            "roofline_s4": roofline_s4, "err_vs_fp64": err_fp64,
+            "roofline_s4": roofline_s4, "roofline_k1": roofline_k1, "err_vs_fp64": err_fp64,
             "cpu_baseline": cpu, "clocks": clock_info,
         }
         print(json.dumps(line), flush=True)
