@@ -139,11 +139,12 @@ struct GroupRec {
 
 constexpr int kPsSlots = 8;  // ring of per-group ps values and records (a power of two)
 
-template <bool kBF16>
+// kPasses: 3 (hi*hi + hi*lo + lo*hi) or 1 (hi*hi, plain BF16)
+template <bool kBF16, int kPasses>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restrict__ ps, int G,
               int nkc, int ndc, int M, int Mp, const TileInfo* __restrict__ tiles, WorkQueue wq,
-              int passes, double* __restrict__ acc, long long plane, int* __restrict__ status) {
+              double* __restrict__ acc, long long plane, int* __restrict__ status) {
   using F = OpFmt<kBF16>;
   constexpr int S = F::kStages, KC = F::kChunks;
   constexpr uint32_t kChunkBytes = 2 * F::kCB;               // hi and lo blocks of a chunk
@@ -300,22 +301,31 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
               stop = true;
               break;
             }
+            // order the group's products after the epilogue's reads of the buffer;
+            // the staged operands need no fence (TMA writes and MMA reads are both
+            // async-proxy accesses ordered by the stage barrier)
+            tc_fence_after();
           }
-          tc_fence_after();
-          const uint64_t so = (uint64_t)((s * kStageBytes) >> 4);
+          // descriptors of the stage; every MMA adds a compile-time offset
+          const uint64_t sa = a_desc0 + (uint64_t)((s * kStageBytes) >> 4);
+          const uint64_t sb = b_desc0 + (uint64_t)((s * kStageBytes) >> 4);
           const int nck = min(KC, nkc - kc0);
-          for (int j = 0; j < nck; ++j) {
-            const int kc = kc0 + j;
-            const uint32_t id = kc < ndc ? idesc : (idesc | (1u << 13));  // negate A: pairs
-            const uint64_t co = so + ((j * kChunkBytes) >> 4);
-            for (int pa = 0; pa < passes; ++pa) {
-              const uint64_t ha = (pa == 2) ? (F::kCB >> 4) : 0u;
-              const uint64_t hb = (pa == 1) ? (F::kCB >> 4) : 0u;
 #pragma unroll
-              for (int kst = 0; kst < F::kKsteps; ++kst)
-                mma_issue<kBF16>(d, a_desc0 + co + ha + kst * (F::kKstepBytes >> 4),
-                                 b_desc0 + co + hb + kst * (F::kKstepBytes >> 4), id,
-                                 kc > 0 || pa > 0 || kst > 0);
+          for (int j = 0; j < KC; ++j) {
+            if (j < nck) {
+              const int kc = kc0 + j;
+              const uint32_t id = kc < ndc ? idesc : (idesc | (1u << 13));  // negate A: pairs
+#pragma unroll
+              for (int pa = 0; pa < kPasses; ++pa) {
+                constexpr uint64_t kLo = F::kCB >> 4;
+#pragma unroll
+                for (int kst = 0; kst < F::kKsteps; ++kst) {
+                  const uint64_t off = (uint64_t)((j * kChunkBytes + kst * F::kKstepBytes) >> 4);
+                  mma_issue<kBF16>(d, sa + off + (pa == 2 ? kLo : 0u),
+                                   sb + off + (pa == 1 ? kLo : 0u), id,
+                                   kc > 0 || pa > 0 || kst > 0);
+                }
+              }
             }
           }
           mma_commit(&sdone[s]);
@@ -462,10 +472,10 @@ cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm_img, const OperandImage& 
                                  int* counter, int* status, cudaStream_t stream) {
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
   if (m < 4 || m > kMaxGramM || (Mp & 15)) return cudaErrorInvalidValue;
-  const bool bf16 = precision != SS_PREC_TF32X3;
-  const int passes = precision == SS_PREC_BF16 ? 1 : 3;
   const size_t smem = k3tc_smem_bytes(precision);
-  auto kern = bf16 ? k3_trispec_tc<true> : k3_trispec_tc<false>;
+  auto kern = precision == SS_PREC_TF32X3 ? k3_trispec_tc<false, 3>
+              : precision == SS_PREC_BF16X3 ? k3_trispec_tc<true, 3>
+                                            : k3_trispec_tc<true, 1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // one CTA per SM: each CTA allocates all 512 TMEM columns
@@ -478,8 +488,8 @@ cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm_img, const OperandImage& 
   e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
   const float* ps = oi.ps + (size_t)channel * oi.chan_ps;
-  kern<<<n_cta, kTcThreads, smem, stream>>>(tm_img, ps, G, oi.nkc, oi.ndc, M, Mp, tiles, wq,
-                                            passes, acc, plane, status);
+  kern<<<n_cta, kTcThreads, smem, stream>>>(tm_img, ps, G, oi.nkc, oi.ndc, M, Mp, tiles, wq, acc,
+                                            plane, status);
   return cudaGetLastError();
 }
 
