@@ -18,15 +18,17 @@
 // Operands are split hi + lo (TF32 or BF16) and each chunk takes three MMAs
 // hi*hi + hi*lo + lo*hi (one in the plain BF16 mode).
 //
-// Warp roles (320 threads), coupled only by mbarriers.  Warp 8, TMA: takes
+// Warp roles (352 threads), coupled only by mbarriers.  Warp 8, TMA: takes
 // (group chunk, tile) items from the queue; per group it loads the group's ps
 // values for the tile into a ring of kPsSlots slots with a record of the group,
 // and per stage (group, kChunks consecutive K chunks) it loads two boxes of the
 // operand image through a 4-D tensor map: the 16 row groups of the k-block and
-// the 16 of the l-block.  Warp 9, MMA: per stage it issues the MMAs of its
-// chunks into the group's TMEM buffer (two buffers of 128 columns), commits
+// the 16 of the l-block.  Warps 9 and 10, MMA: warp 9 + w takes every other
+// group (w = group index mod 2, TMEM buffer w of 128 columns), reads the group's
+// record from the ring, and per stage issues the MMAs of its chunks, commits
 // them to the stage's barrier (the stage is then free for the next load) and,
-// after the group's last stage, to the buffer's barrier.  Warps 0-7, the
+// after the group's last stage, to the buffer's barrier; one warp's waits and
+// commits overlap the other's products.  Warps 0-7, the
 // epilogue: TMEM lane quadrant warp % 4, column half warp / 4.  For each group
 // they read D, form c4 and update the running sum and sum of squares of their
 // 64 grid points, which stay in TMEM columns 256-511; at the end of an item they
@@ -39,7 +41,8 @@
 namespace ss {
 namespace {
 
-constexpr int kTM = 128, kTN = 128, kEpiWarps = 8, kTcThreads = 32 * (kEpiWarps + 2);
+constexpr int kTM = 128, kTN = 128, kEpiWarps = 8, kMmaWarps = 2;
+constexpr int kTcThreads = 32 * (kEpiWarps + 1 + kMmaWarps);
 constexpr uint32_t kTmemCols = 512;  // D0 | D1 | running sum | running sum of squares
 constexpr uint32_t kColSum = 256, kColSq = 384;
 
@@ -158,7 +161,6 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
   __shared__ __align__(8) uint64_t psempty[kPsSlots];   // ps slot read by the epilogue
   __shared__ __align__(8) uint64_t afull[2];            // TMEM buffer holds a finished group
   __shared__ __align__(8) uint64_t aempty[2];           // TMEM buffer read by the epilogue
-  __shared__ int sinfo[S];  // stage record: first K chunk | tile columns << 16; -1 = stop
   __shared__ GroupRec prec[kPsSlots];
   __shared__ __align__(16) float psr[kPsSlots][kTM + kTN];  // ps: k rows, then l columns
   __shared__ uint32_t tmem_slot;
@@ -212,7 +214,6 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
         const TileInfo ti = tiles[t];
         const uint32_t pk = (uint32_t)min(kTM, Mp - ti.k0) * 4u;
         const uint32_t pl = (uint32_t)min(ti.ncols, Mp - ti.l0) * 4u;
-        const int info0 = ti.ncols << 16;
         for (int g = ga; g < gb && ok; ++g) {
           // the group's ps values and record
           const int p = gq & (kPsSlots - 1);
@@ -233,7 +234,6 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
               ok = false;
               break;
             }
-            sinfo[s] = info0 | kc0;
             unsigned char* st = base + (size_t)s * kStageBytes;
             mbar_arrive_expect_tx(&full[s], kStageBytes);
             tma_load_4d(st, &tm_img, 0, kc0, ti.k0 >> 3, g, &full[s]);
@@ -254,58 +254,57 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
         mbar_wait_bounded(&full[i % S], (i / S) & 1u, status);
       for (uint32_t i = gq > (uint32_t)kPsSlots ? gq - kPsSlots : 0; i < gq; ++i)
         mbar_wait_bounded(&psfull[i % kPsSlots], (i / kPsSlots) & 1u, status);
-      // stop records for the MMA warp and the epilogue (plain arrivals, no bytes)
-      if (q >= (uint32_t)S) mbar_wait_bounded(&sdone[s], ph ^ 1u, status);
-      sinfo[s] = -1;
-      asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
-                       smem_addr(&full[s]))
-                   : "memory");
-      const int p = gq & (kPsSlots - 1);
-      if (gq >= kPsSlots) mbar_wait_bounded(&psempty[p], ((gq / kPsSlots) - 1) & 1u, status);
-      prec[p].flags = 2;
-      asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
-                       smem_addr(&psfull[p]))
-                   : "memory");
+      // stop records (plain arrivals, no bytes) in the next two group slots: the
+      // epilogue reads the first, each MMA warp the one of its next group
+      for (uint32_t gs = gq; gs < gq + kMmaWarps; ++gs) {
+        const int p = gs & (kPsSlots - 1);
+        if (gs >= kPsSlots) mbar_wait_bounded(&psempty[p], ((gs / kPsSlots) - 1) & 1u, status);
+        prec[p].flags = 2;
+        asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
+                         smem_addr(&psfull[p]))
+                     : "memory");
+      }
     }
     __syncwarp();
-  } else if (warp == kEpiWarps + 1) {
-    // ------------------------------------------------------------ MMA issuer
+  } else if (warp > kEpiWarps) {
+    // ------------------------------------------------------------ MMA issuers
+    // MMA warp w takes the groups gc = w, w + 2, ... (TMEM buffer w), so that one
+    // warp's waits and commits overlap the other's products
     if (lane == 0) {
+      const uint32_t w = (uint32_t)(warp - kEpiWarps - 1);
       const uint32_t idesc0 = (1u << 4) | F::kIdescAB | ((uint32_t)(kTM >> 4) << 24);
       // descriptors of stage 0; a stage adds kStageBytes >> 4 to the address field
       const uint64_t a_desc0 = smem_desc(smem_addr(base), 128, kRowGroupBytes);
       const uint64_t b_desc0 = smem_desc(smem_addr(base) + kABytes, 128, kRowGroupBytes);
-      int s = 0;
-      uint32_t ph = 0;
+      const uint32_t nst = (uint32_t)((nkc + KC - 1) / KC);  // stages per group
       int last_s = -1;
       uint32_t last_ph = 0;
-      for (uint32_t gc = 0;; ++gc) {
-        const uint32_t b = gc & 1u;
-        const uint32_t d = taddr + b * kTN;
-        uint32_t idesc = 0;
+      for (uint32_t gc = w;; gc += kMmaWarps) {
+        // the group's record (tile columns, or stop)
+        const int p = gc & (kPsSlots - 1);
+        if (!mbar_wait_bounded(&psfull[p], (gc / kPsSlots) & 1u, status)) break;
+        const GroupRec r = prec[p];
+        if (r.flags & 2) break;
+        const uint32_t d = taddr + w * kTN;
+        const uint32_t idesc = idesc0 | ((uint32_t)(r.n >> 3) << 17);
+        // the buffer is free once the epilogue has read this warp's previous group
+        if (gc >= kMmaWarps &&
+            !mbar_wait_bounded(&aempty[w], ((gc / kMmaWarps) - 1) & 1u, status))
+          break;
+        // order the group's products after the epilogue's reads of the buffer; the
+        // staged operands need no fence (TMA writes and MMA reads are both
+        // async-proxy accesses ordered by the stage barrier)
+        tc_fence_after();
         bool stop = false;
-        for (int kc0 = 0; kc0 < nkc; kc0 += KC) {
+        for (uint32_t i = 0; i < nst; ++i) {
+          const uint32_t q = gc * nst + i;  // the group's stages are loaded in order
+          const int s = (int)(q % S);
+          const uint32_t ph = (q / S) & 1u;
           if (!mbar_wait_bounded(&full[s], ph, status)) {
             stop = true;
             break;
           }
-          if (kc0 == 0) {
-            const int info = sinfo[s];
-            if (info < 0) {
-              stop = true;
-              break;
-            }
-            idesc = idesc0 | ((uint32_t)((info >> 16) >> 3) << 17);
-            // the buffer is free once the epilogue has read the group before last
-            if (gc >= 2 && !mbar_wait_bounded(&aempty[b], ((gc >> 1) - 1) & 1u, status)) {
-              stop = true;
-              break;
-            }
-            // order the group's products after the epilogue's reads of the buffer;
-            // the staged operands need no fence (TMA writes and MMA reads are both
-            // async-proxy accesses ordered by the stage barrier)
-            tc_fence_after();
-          }
+          const int kc0 = (int)i * KC;
           // descriptors of the stage; every MMA adds a compile-time offset
           const uint64_t sa = a_desc0 + (uint64_t)((s * kStageBytes) >> 4);
           const uint64_t sb = b_desc0 + (uint64_t)((s * kStageBytes) >> 4);
@@ -331,13 +330,9 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
           mma_commit(&sdone[s]);
           last_s = s;
           last_ph = ph;
-          if (++s == S) {
-            s = 0;
-            ph ^= 1u;
-          }
         }
         if (stop) break;
-        mma_commit(&afull[b]);  // arrives when the group's products are complete
+        mma_commit(&afull[w]);  // arrives when the group's products are complete
       }
       if (*(volatile int*)status != 0) atomicExch(&s_fail, 1);
       // the products issued must be complete before the TMEM is freed
