@@ -46,6 +46,10 @@ WORKLOADS = {
     # 64 independent recordings, lengths log-uniform in [2^20, 2^26], T from
     # {128, 256, 512, 1024}, AR coefficients uniform in [0.5, 0.98], one CUDA graph
     "many64-2^20..2^26-m10": dict(channels=1, many=64, m=10, seed=100),
+    # int16 ADC record (low-passed telegraph plus noise) streamed from page-locked
+    # host memory in 256 MiB chunks; 1/16 of the 2^34-sample streamed configuration
+    "adc16-2^30-T4096-m10": dict(channels=1, n=1 << 30, T=4096, m=10, seed=5, dtype="i16",
+                                 chunk=1 << 27, cpu_groups=3),
 }
 DEFAULT_WORKLOAD = "ar1q-2^28-T1024-m10"
 
@@ -59,6 +63,10 @@ def dist_env():
 
 def make_record(w, rank):
     import synth
+
+    if w.get("dtype") == "i16":
+        return synth.adc_telegraph_int16_parallel(w["n"], seed=w["seed"] + rank,
+                                                  processes=min(16, os.cpu_count() or 1))
 
     return synth.ar1_quadratic(w["n"], seed=w["seed"] + rank, phi=w["phi"])
 
@@ -222,7 +230,8 @@ def error_vs_oracle(P, w, z, ref, groups, precision):
 
     T, m = w["T"], w["m"]
     n = groups * m * T
-    plan = P.Plan(channels=1, T=T, dt=1.0, m=m, orders=(2, 3, 4), precision=precision)
+    plan = P.Plan(channels=1, T=T, dt=1.0, m=m, orders=(2, 3, 4), precision=precision,
+                  dtype=w.get("dtype", "f32"))
     plan.accumulate(torch.from_numpy(np.ascontiguousarray(z[:n])).cuda(), n)
     out = plan.finalize()
     plan.close()
@@ -348,6 +357,7 @@ def main():
     T, m, C = w["T"], w["m"], w["channels"]
     stream = torch.cuda.current_stream()
     plan = P.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4), stream=stream,
+                  dtype=w.get("dtype", "f32"),
                   precision=args.precision)
     info = P.ss_query(plan.handle)
     dz = torch.from_numpy(z).cuda()
@@ -453,7 +463,7 @@ def main():
     # modes, the operand image (hi and lo of ceil(m/16) + ceil(m(m-1)/2 / 16) chunks of
     # 16 products per bin, TF32 4 B, BF16 2 B each part) and the ps values (4 B per bin)
     Mp = ((T // 2 + 1) + 15) // 16 * 16
-    k1_bytes = groups * (m * T * 4 * C + m * Mp * 8 * C)
+    k1_bytes = groups * (m * T * z.itemsize * C + m * Mp * 8 * C)
     if args.precision != "fp32":
         nkc = (m + 15) // 16 + (m * (m - 1) // 2 + 15) // 16
         k1_bytes += groups * C * Mp * (nkc * 16 * 2 * (4 if args.precision == "tf32x3" else 2) + 4)
@@ -482,9 +492,12 @@ def main():
         host_out = {k: np.empty(int(np.prod(v)) * 2, np.float64) for k, v in sh.items()}
         host_err = {k: np.empty_like(v) for k, v in host_out.items()}
 
+        chunk = w.get("chunk", n)  # samples per ss_accumulate call (a streaming caller)
+
         def step_host():
             P.ss_reset(plan.handle)
-            P.ss_accumulate(plan.handle, hz, n)
+            for a in range(0, n, chunk):
+                P.ss_accumulate(plan.handle, hz[..., a:a + chunk], min(chunk, n - a))
             P.ss_finalize(plan.handle, host_out["S2"], host_out["S3"], host_out["S4"],
                           host_err["S2"], host_err["S3"], host_err["S4"])
 
@@ -506,8 +519,9 @@ def main():
 
     cpu, err_fp64 = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, ref = cpu_baseline(w, z, args.cpu_groups)
-        err_fp64 = error_vs_oracle(P, w, z, ref, args.cpu_groups, args.precision)
+        cg = w.get("cpu_groups", args.cpu_groups)
+        cpu, ref = cpu_baseline(w, z, cg)
+        err_fp64 = error_vs_oracle(P, w, z, ref, cg, args.precision)
 
     if rank == 0:
         line = {
@@ -518,7 +532,9 @@ def main():
             "config": {"workload": args.workload, "channels": C, "samples_per_rank": n, "T": T,
                        "M": T // 2 + 1, "m": m, "groups": groups, "window": "hann",
                        "orders": "S2+S3+S4 full grids", "s4_precision": args.precision,
-                       "l2": "record of 1 GiB per step is larger than L2; no flush"},
+                       "dtype_in": w.get("dtype", "f32"),
+                       "l2": f"record of {z.nbytes / 2**30:.0f} GiB per step is larger than L2; "
+                             "no flush"},
             "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
             "roofline_s4": roofline_s4, "roofline_k1": roofline_k1, "err_vs_fp64": err_fp64,
             "cpu_baseline": cpu, "clocks": clock_info,

@@ -358,8 +358,10 @@ ss_status check_status(ss_plan_s* p) {
 
 ss_status ensure_stage(ss_plan_s* p) {
   if (p->d_stage[0]) return SS_OK;
-  // 32 Mi samples per channel per staging buffer
-  p->stage_n = (32ll << 20) / std::max(1, p->C);
+  // one device batch of samples per staging buffer (within 32 Mi and 256 Mi
+  // samples per channel), so a staged piece runs as one full batch of groups
+  const long long batch = (long long)p->Gb_max * p->m * p->T;
+  p->stage_n = std::max(32ll << 20, std::min(256ll << 20, batch)) / std::max(1, p->C);
   for (int i = 0; i < 2; ++i) {
     SS_TRY(p, dev_alloc(p, &p->d_stage[i], (size_t)p->stage_n * p->C * p->elem));
     SS_TRY(p, cudaEventCreateWithFlags(&p->ev_ready[i], cudaEventDisableTiming));

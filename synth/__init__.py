@@ -37,6 +37,7 @@ __all__ = [
     "telegraph",
     "multichannel_shared",
     "adc_telegraph_int16",
+    "adc_telegraph_int16_parallel",
     "iid_frames_ar1",
     "uneven_recordings",
 ]
@@ -153,6 +154,49 @@ def adc_telegraph_int16(n: int, seed: int, start: int = 0, state=None, p: float 
     y, zf = lfilter(b, a, s, zi=zi)
     v = np.rint(gain * y + sigma * normal(n, seed, 12, start))
     return np.clip(v, -32768, 32767).astype(np.int16), (zf, float(s[-1]))
+
+
+def _adc_flips(n, seed, start, p):
+    return np.flatnonzero(uniform(n, seed, 11, start) < p)
+
+
+def _adc_noise(y, seed, start, gain, sigma):
+    v = np.rint(gain * y + sigma * normal(len(y), seed, 12, start))
+    return np.clip(v, -32768, 32767).astype(np.int16)
+
+
+def adc_telegraph_int16_parallel(n: int, seed: int, p: float = 1e-4, gain: float = 2000.0,
+                                 sigma: float = 800.0, cutoff: float = 0.05,
+                                 piece: int = 1 << 24, processes: int = 8) -> np.ndarray:
+    """The record ``adc_telegraph_int16(n, seed)`` returns, produced with a process
+    pool: the telegraph's flip positions and the noise are drawn in parallel
+    pieces (the generator is counter based), the low-pass filter runs over the
+    pieces in order with its state carried across.  The pool uses the ``spawn``
+    start method, so it may be created after CUDA has been initialised."""
+    import multiprocessing as mp
+
+    from scipy.signal import butter, lfilter, lfilter_zi
+
+    starts = list(range(0, n, piece))
+    lens = [min(piece, n - a) for a in starts]
+    with mp.get_context("spawn").Pool(processes) as pool:
+        flips = pool.starmap(_adc_flips, [(ln, seed, a, p) for a, ln in zip(starts, lens)])
+        b, a_coef = butter(4, 2.0 * cutoff)
+        out = np.empty(n, np.int16)
+        sign, zi, pending = 1.0, None, []
+        for a, ln, fl in zip(starts, lens, flips):
+            cnt = np.zeros(ln, np.int64)
+            cnt[fl] = 1
+            s = sign * (1.0 - 2.0 * (np.cumsum(cnt) & 1).astype(np.float64))
+            if zi is None:
+                zi = lfilter_zi(b, a_coef) * s[0]
+            y, zi = lfilter(b, a_coef, s, zi=zi)
+            sign = float(s[-1])
+            pending.append((a, pool.apply_async(_adc_noise, (y, seed, a, gain, sigma))))
+        for a, r in pending:
+            v = r.get()
+            out[a:a + len(v)] = v
+    return out
 
 
 def iid_frames_ar1(n_frames: int, T: int, phi: float, seed: int,

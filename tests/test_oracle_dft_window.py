@@ -73,3 +73,4 @@ def test_frame_groups_layout_and_drop():
     f = oracle.frame_groups(z, 4, 3)
     assert f.shape == (2, 3, 4)
     assert f[1, 2, 3] == (1 * 3 + 2) * 4 + 3
+
