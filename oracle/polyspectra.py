@@ -16,6 +16,10 @@ reordering beyond what the cited formula states:
 * spectra + normalisation .. Sec. 3, Eq. 23 (S2); Sec. 4, Eq. 28 (S3), Eq. 31 (S4 cut);
                               Sec. 7, Eq. 47, 48, 50 (multi-channel S2, S3, S4 cut)
 * error bars ............... Sec. 4.2, Eq. 35-36 (variance over N_p parts, standard error)
+* first-order spectrum ..... Sec. 4, S1 = N C1(a_0) / (T sum g); App. G
+* natural (biased) estimators, for the paper's unbiased-vs-biased comparison
+                              (Sec. 4.1, Fig. 6): the cumulants of the m samples'
+                              own empirical distribution, from their central moments
 
 Notation: ``T`` is the number of samples per frame (the paper's N), ``dt`` the
 sample interval (the paper's T/N), ``M = T/2 + 1`` the number of real-FFT bins,
@@ -43,10 +47,14 @@ __all__ = [
     "c3",
     "c4",
     "c4_factorised",
+    "c2_natural",
+    "c3_natural",
+    "c4_natural",
     "coef",
     "s2_groups",
     "s3_groups",
     "s4_groups",
+    "s1_groups",
     "mean_and_stderr",
     "s3_domain",
     "polyspectra",
@@ -176,6 +184,39 @@ def c4_factorised(x, y, z, w):
 
 
 # --------------------------------------------------------------------------- spectra
+def _central(v):
+    return v - _mean(v)[..., None]
+
+
+def c2_natural(x, y):
+    """Second cumulant of the samples' empirical distribution: the mean product of
+    the centred samples (no m/(m-1) correction; biased)."""
+    return _mean(_central(x) * _central(y))
+
+
+def c3_natural(x, y, z):
+    """Third cumulant of the empirical distribution: the mean triple product of the
+    centred samples (biased)."""
+    return _mean(_central(x) * _central(y) * _central(z))
+
+
+def c4_natural(x, y, z, w):
+    """Fourth cumulant of the empirical distribution: the fourth central moment
+    minus the three pairings of second central moments (biased)."""
+    dx, dy, dz, dw = _central(x), _central(y), _central(z), _central(w)
+    return _mean(dx * dy * dz * dw) - (
+        _mean(dx * dy) * _mean(dz * dw)
+        + _mean(dx * dz) * _mean(dy * dw)
+        + _mean(dx * dw) * _mean(dy * dz)
+    )
+
+
+_ESTIMATORS = {
+    "unbiased": (None, None, None),
+    "natural": (c2_natural, c3_natural, c4_natural),
+}
+
+
 def coef(X: np.ndarray, k) -> np.ndarray:
     """Coefficients at (possibly negative) bins k: X_{-k} = X_k* for a real channel.
 
@@ -191,33 +232,42 @@ def _samples_last(v):
     return np.swapaxes(v, -1, -2)
 
 
-def s2_groups(Xa, Xb, dt, g, k=None):
+def s2_groups(Xa, Xb, dt, g, k=None, estimator="unbiased"):
     """Per-group S2 (Eq. 23 / Eq. 47): dt c2(a_k, b_k*) / sum g^2.  Returns [G, P]."""
     M = Xa.shape[-1]
     k = np.arange(M) if k is None else np.asarray(k)
     x = _samples_last(coef(Xa, k))
     y = _samples_last(np.conj(coef(Xb, k)))
-    return dt * c2(x, y) / np.sum(g ** 2)
+    f = _ESTIMATORS[estimator][0] or c2
+    return dt * f(x, y) / np.sum(g ** 2)
 
 
-def s3_groups(Xa, Xb, Xc, dt, g, k, l):
+def s3_groups(Xa, Xb, Xc, dt, g, k, l, estimator="unbiased"):
     """Per-group S3 (Eq. 28 / Eq. 48): dt^2 c3(a_k, b_l, c_{k+l}*) / sum g^3."""
     k, l = np.asarray(k), np.asarray(l)
     x = _samples_last(coef(Xa, k))
     y = _samples_last(coef(Xb, l))
     z = _samples_last(np.conj(coef(Xc, k + l)))
-    return dt * dt * c3(x, y, z) / np.sum(g ** 3)
+    f = _ESTIMATORS[estimator][1] or c3
+    return dt * dt * f(x, y, z) / np.sum(g ** 3)
 
 
-def s4_groups(Xa, Xb, Xc, Xd, dt, g, k, l, factorised=False):
+def s4_groups(Xa, Xb, Xc, Xd, dt, g, k, l, factorised=False, estimator="unbiased"):
     """Per-group S4 cut (Eq. 31 / Eq. 50): dt^3 c4(a_k, b_k*, c_l, d_l*) / sum g^4."""
     k, l = np.asarray(k), np.asarray(l)
     x = _samples_last(coef(Xa, k))
     y = _samples_last(np.conj(coef(Xb, k)))
     z = _samples_last(coef(Xc, l))
     w = _samples_last(np.conj(coef(Xd, l)))
-    f = c4_factorised if factorised else c4
+    f = _ESTIMATORS[estimator][2] or (c4_factorised if factorised else c4)
     return dt ** 3 * f(x, y, z, w) / np.sum(g ** 4)
+
+
+def s1_groups(X, g):
+    """Per-group first-order spectrum S1 = N C1(a_0) / (T sum g) = mean_j X_j0 / sum g
+    (a_0 = dt X_0 and N/T = 1/dt); C1 is the plain mean, the same for both
+    estimators.  Returns [G]."""
+    return _mean(_samples_last(X[..., 0:1]))[..., 0] / np.sum(g)
 
 
 def mean_and_stderr(Sg: np.ndarray):
@@ -266,12 +316,14 @@ def s3_domain(M: int):
 
 
 def polyspectra(z, T, dt, m, window_kind="hann", sigma_t=0.14, orders=(2, 3, 4),
-                group_chunk=16, max_groups=None, factorised_c4=False):
-    """Single-channel S2 [M], S3 [M, M], S4 [M, M] with standard errors.
+                group_chunk=16, max_groups=None, factorised_c4=False, estimator="unbiased"):
+    """Single-channel S1 (a number), S2 [M], S3 [M, M], S4 [M, M] with standard errors.
 
     Returns a dict with keys 'S2', 'S2_err', 'S3', 'S3_err', 'S4', 'S4_err', 'G'
-    ('*_err' arrays carry a trailing axis (err_re, err_im)).  S3 is zero outside
-    k + l <= M - 1.  ``max_groups`` limits the record to its first groups.
+    (and 'S1', 'S1_err' with order 1; '*_err' arrays carry a trailing axis
+    (err_re, err_im)).  S3 is zero outside k + l <= M - 1.  ``max_groups`` limits
+    the record to its first groups.  ``estimator``: "unbiased" (k-statistics,
+    Eq. 32-34) or "natural" (cumulants of each group's empirical distribution).
     """
     g = window(T, window_kind, sigma_t)
     frames = frame_groups(z, T, m)
@@ -285,6 +337,8 @@ def polyspectra(z, T, dt, m, window_kind="hann", sigma_t=0.14, orders=(2, 3, 4),
     kk3, ll3 = s3_domain(M)
     kk4, ll4 = [a.ravel() for a in np.meshgrid(np.arange(M), np.arange(M), indexing="ij")]
     acc = {}
+    if 1 in orders:
+        acc[1] = _Acc(())
     if 2 in orders:
         acc[2] = _Acc((M,))
     if 3 in orders:
@@ -293,12 +347,18 @@ def polyspectra(z, T, dt, m, window_kind="hann", sigma_t=0.14, orders=(2, 3, 4),
         acc[4] = _Acc((kk4.size,))
     for g0 in range(0, G, group_chunk):
         X = dft_plus(frames[g0:g0 + group_chunk] * g)
+        if 1 in orders:
+            acc[1].add(s1_groups(X, g))
         if 2 in orders:
-            acc[2].add(s2_groups(X, X, dt, g))
+            acc[2].add(s2_groups(X, X, dt, g, estimator=estimator))
         if 3 in orders:
-            acc[3].add(s3_groups(X, X, X, dt, g, kk3, ll3))
+            acc[3].add(s3_groups(X, X, X, dt, g, kk3, ll3, estimator=estimator))
         if 4 in orders:
-            acc[4].add(s4_groups(X, X, X, X, dt, g, kk4, ll4, factorised=factorised_c4))
+            acc[4].add(s4_groups(X, X, X, X, dt, g, kk4, ll4, factorised=factorised_c4,
+                                 estimator=estimator))
+    if 1 in orders:
+        mean, er, ei = acc[1].result()
+        out["S1"], out["S1_err"] = mean, np.stack([er, ei], -1)
     if 2 in orders:
         mean, er, ei = acc[2].result()
         out["S2"], out["S2_err"] = mean, np.stack([er, ei], -1)
@@ -329,7 +389,8 @@ def cross_domain_s3(M: int):
 
 
 def cross_polyspectra(zs, T, dt, m, s2_combos=(), s3_combos=(), s4_combos=(),
-                      window_kind="hann", sigma_t=0.14, group_chunk=8, max_groups=None):
+                      window_kind="hann", sigma_t=0.14, group_chunk=8, max_groups=None,
+                      estimator="unbiased"):
     """Multi-channel spectra (Sec. 7, Eq. 47, 48, 50) for the listed channel combinations.
 
     zs: [C, n] real channels.  s2_combos: (a, b) pairs -> S2_ab [M] = C2(a_k, b_k*).
@@ -358,13 +419,15 @@ def cross_polyspectra(zs, T, dt, m, s2_combos=(), s3_combos=(), s4_combos=(),
         X = [dft_plus(frames[c, g0:g0 + group_chunk] * g) for c in range(C)]
         for cmb in s2_combos:
             a, b = cmb
-            accs[("S2", tuple(cmb))].add(s2_groups(X[a], X[b], dt, g))
+            accs[("S2", tuple(cmb))].add(s2_groups(X[a], X[b], dt, g, estimator=estimator))
         for cmb in s3_combos:
             a, b, c = cmb
-            accs[("S3", tuple(cmb))].add(s3_groups(X[a], X[b], X[c], dt, g, kk3, ll3))
+            accs[("S3", tuple(cmb))].add(s3_groups(X[a], X[b], X[c], dt, g, kk3, ll3,
+                                                   estimator=estimator))
         for cmb in s4_combos:
             a, b, c, d = cmb
-            accs[("S4", tuple(cmb))].add(s4_groups(X[a], X[b], X[c], X[d], dt, g, kk4, ll4))
+            accs[("S4", tuple(cmb))].add(s4_groups(X[a], X[b], X[c], X[d], dt, g, kk4, ll4,
+                                                   estimator=estimator))
     out = {"G": G}
     for key, acc in accs.items():
         mean, er, ei = acc.result()

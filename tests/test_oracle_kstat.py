@@ -130,3 +130,66 @@ def test_translation_invariance_and_multilinearity():
     lhs = oracle.c3(v[0] + 2.0 * u, v[1], v[2])
     rhs = oracle.c3(v[0], v[1], v[2]) + 2.0 * oracle.c3(u, v[1], v[2])
     assert np.allclose(lhs, rhs, atol=1e-11)
+
+
+# ---------------------------------------------------------------- natural estimators
+def _complex_samples(rng, m, n=4):
+    return [rng.normal(size=m) + 1j * rng.normal(size=m) + 0.3 * i for i in range(n)]
+
+
+@pytest.mark.parametrize("m", [3, 5, 11])
+def test_natural_c2_c3_are_the_k_statistics_rescaled(m):
+    # the empirical cumulants of orders 2 and 3 are the central moments, which differ
+    # from the k-statistics by (m-1)/m and (m-1)(m-2)/m^2
+    x, y, z, _ = _complex_samples(np.random.default_rng(m), m)
+    assert np.isclose(oracle.c2_natural(x, y), (m - 1) / m * oracle.c2(x, y), rtol=1e-13)
+    assert np.isclose(oracle.c3_natural(x, y, z), (m - 1) * (m - 2) / m ** 2 * oracle.c3(x, y, z),
+                      rtol=1e-12)
+
+
+@pytest.mark.parametrize("m", [4, 9, 30])
+def test_natural_univariate_c4_equals_scipy_central_moments(m):
+    x = np.random.default_rng(10 + m).gamma(2.0, size=m) - 1.1
+    want = stats.moment(x, 4) - 3.0 * stats.moment(x, 2) ** 2
+    assert np.isclose(oracle.c4_natural(x, x, x, x), want, rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("m", [4, 6, 13])
+def test_natural_estimators_are_the_cumulants_of_the_empirical_distribution(m):
+    # the set-partition formula with raw empirical moments (each sample weight 1/m)
+    # is an independent route to the same numbers, for complex multivariate data
+    cols = _complex_samples(np.random.default_rng(20 + m), m)
+    support = np.stack(cols, axis=1)
+    probs = np.full(m, 1.0 / m)
+    for fn, c in ((oracle.c2_natural, (0, 1)), (oracle.c3_natural, (0, 1, 2)),
+                  (oracle.c4_natural, (0, 1, 2, 3)), (oracle.c4_natural, (2, 0, 3, 0))):
+        got = fn(*[cols[i] for i in c])
+        assert np.isclose(got, joint_cumulant(c, support, probs), rtol=1e-10, atol=1e-12)
+
+
+def test_natural_estimator_bias_by_enumeration(distribution):
+    # with m draws, the expected empirical c2 is (m-1)/m kappa2: the bias the
+    # paper's comparison shows (the k-statistic removes it)
+    support, probs = distribution
+    m = 4
+    kappa = joint_cumulant((0, 1), support, probs)
+    e = brute_expectation(oracle.c2_natural, (0, 1), support, probs, m)
+    assert np.isclose(e, (m - 1) / m * kappa, rtol=1e-12, atol=1e-14)
+
+
+def test_first_order_spectrum_of_a_constant_and_of_a_shift():
+    # S1 is the window-weighted mean of the signal: c for a constant record, and a
+    # constant added to any record adds itself
+    T, m = 32, 4
+    z = np.full(T * m * 5, 2.5)
+    r = oracle.polyspectra(z, T, 0.1, m, orders=(1,))
+    assert np.isclose(r["S1"], 2.5) and np.allclose(r["S1_err"], 0.0)
+    y = np.random.default_rng(3).normal(size=T * m * 7)
+    a = oracle.polyspectra(y, T, 0.1, m, orders=(1,), window_kind="acg")
+    b = oracle.polyspectra(y + 0.75, T, 0.1, m, orders=(1,), window_kind="acg")
+    assert np.isclose(b["S1"], a["S1"] + 0.75, rtol=0, atol=1e-12)
+    # and the groups' plain weighted means give it directly
+    g = oracle.window(T, "acg")
+    fr = y[: (len(y) // (T * m)) * T * m].reshape(-1, m, T)
+    want = np.mean(np.sum(fr * g, axis=-1) / np.sum(g))
+    assert np.isclose(a["S1"].real, want, rtol=1e-12)
