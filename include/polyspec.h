@@ -64,8 +64,16 @@ enum { SS_WIN_HANN = 0, /* periodic Hann, g_i = 0.5 - 0.5 cos(2 pi i / T)       
        SS_WIN_ACG = 1   /* approximate confined Gaussian, App. B, Eq. 71; win_param
                            is sigma_t (the paper's default is 0.14)                  */ };
 
-/* spectral orders, OR-ed together */
-enum { SS_ORDER2 = 1u << 2, SS_ORDER3 = 1u << 3, SS_ORDER4 = 1u << 4 };
+/* spectral orders, OR-ed together; SS_ORDER1 is the first-order spectrum of
+   each channel, S1 = N C1(a_0) / (T sum g) (Sec. 4, App. G), read with
+   ss_finalize_s1 */
+enum { SS_ORDER1 = 1u << 1, SS_ORDER2 = 1u << 2, SS_ORDER3 = 1u << 3, SS_ORDER4 = 1u << 4 };
+
+/* cumulant estimators (ss_set_estimator): the unbiased k-statistics of Sec. 4.1
+   (Eq. 32-34, the default), or the natural estimators the paper compares them
+   with (Sec. 4.1, Fig. 6): the cumulants of each group's m samples taken as a
+   distribution of their own, biased for finite m */
+enum { SS_EST_UNBIASED = 0, SS_EST_NATURAL = 1 };
 
 /* sample type of the input chunks */
 enum { SS_F32 = 0, /* float32 samples                                          */
@@ -118,7 +126,7 @@ typedef struct {
  *              S2, m >= 3 with SS_ORDER3, m >= 4 with SS_ORDER4 (the c3 and c4
  *              prefactors of Eq. 33-34 divide by m-2 and m-3).
  *   window     SS_WIN_HANN or SS_WIN_ACG; win_param = sigma_t for SS_WIN_ACG.
- *   orders     OR of SS_ORDER2/3/4, at least one.
+ *   orders     OR of SS_ORDER1/2/3/4, at least one.
  *   dtype      SS_F32 or SS_I16.
  *   precision  SS_PREC_* for the S4 moment sums.
  *   combos     NULL for the default combinations, else n_combos records of five
@@ -174,6 +182,24 @@ ss_status ss_accumulate(ss_plan_t plan, const void* chunk, size_t n_samples);
 ss_status ss_finalize(ss_plan_t plan, double* S2, double* S3, double* S4,
                       double* S2_err, double* S3_err, double* S4_err);
 
+/*
+ * ss_finalize_s1 -- first-order spectrum of every channel (a plan made with
+ *   SS_ORDER1): S1 [channels] complex128 interleaved (re, im) and S1_err
+ *   [channels][2] (standard errors of Re and Im over the groups, Eq. 35-36),
+ *   host or device memory; either may be NULL.  S1 is the group-averaged mean
+ *   of the zero-frequency coefficient divided by sum g, i.e. the window-
+ *   weighted mean of the signal.  SS_ESTATE with fewer than two groups or
+ *   without SS_ORDER1.  Synchronises the plan's stream.
+ */
+ss_status ss_finalize_s1(ss_plan_t plan, double* S1, double* S1_err);
+
+/*
+ * ss_set_estimator -- SS_EST_UNBIASED (default) or SS_EST_NATURAL for every
+ *   order of the plan.  Valid only before the first ss_accumulate (or after
+ *   ss_reset); SS_ESTATE otherwise, SS_EINVAL for another value.
+ */
+ss_status ss_set_estimator(ss_plan_t plan, int estimator);
+
 /* ss_reset -- zero the accumulators, the carry-over and the statistics. */
 ss_status ss_reset(ss_plan_t plan);
 
@@ -204,9 +230,9 @@ ss_status ss_set_batch(ss_plan_t plan, int groups_per_batch);
  * A state is SS_STATE_HEADER doubles followed by the plan's float64 sums.
  * Header words 0..13 describe the configuration (channels, T, m, orders,
  * precision, window, sigma_t, dt, the number of S2/S3/S4 combinations, a
- * 52-bit hash of the combination list, a layout version, 0) and must match
- * between plans that are merged; word 14 is the number of groups, word 15
- * the number of samples per channel in them.
+ * 52-bit hash of the combination list, a layout version, the estimator) and
+ * must match between plans that are merged; word 14 is the number of groups,
+ * word 15 the number of samples per channel in them.
  * Samples carried over towards an incomplete group are not part of a state.
  *
  * ss_state_size   -- number of doubles of the plan's state (header included).

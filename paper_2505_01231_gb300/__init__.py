@@ -28,7 +28,8 @@ __all__ = [
 
 SS_OK, SS_EINVAL, SS_ENOMEM, SS_ECUDA, SS_ESTATE, SS_ETIMEOUT, SS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 SS_WIN_HANN, SS_WIN_ACG = 0, 1
-SS_ORDER2, SS_ORDER3, SS_ORDER4 = 1 << 2, 1 << 3, 1 << 4
+SS_ORDER1, SS_ORDER2, SS_ORDER3, SS_ORDER4 = 1 << 1, 1 << 2, 1 << 3, 1 << 4
+SS_EST_UNBIASED, SS_EST_NATURAL = 0, 1
 SS_F32, SS_I16 = 0, 1
 SS_PREC_FP32, SS_PREC_TF32X3, SS_PREC_BF16X3, SS_PREC_BF16 = 0, 1, 2, 3
 SS_STATE_HEADER = 16
@@ -75,6 +76,8 @@ _sig = {
                                      ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P]),
     "ss_noalloc_last_error": (ctypes.c_char_p, []),
     "ss_state_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "ss_finalize_s1": (ctypes.c_int, [_P, _P, _P]),
+    "ss_set_estimator": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_export_state": (ctypes.c_int, [_P, _P]),
     "ss_merge_state": (ctypes.c_int, [_P, _P]),
     "ss_plan_many": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_double,
@@ -137,6 +140,14 @@ def ss_accumulate(plan, chunk, n_samples):
 def ss_finalize(plan, S2=None, S3=None, S4=None, S2_err=None, S3_err=None, S4_err=None):
     _check(lib.ss_finalize(plan, _addr(S2), _addr(S3), _addr(S4), _addr(S2_err), _addr(S3_err),
                            _addr(S4_err)), plan)
+
+
+def ss_finalize_s1(plan, S1=None, S1_err=None):
+    _check(lib.ss_finalize_s1(plan, _addr(S1), _addr(S1_err)), plan)
+
+
+def ss_set_estimator(plan, estimator):
+    _check(lib.ss_set_estimator(plan, estimator), plan)
 
 
 def ss_reset(plan):
@@ -321,7 +332,8 @@ class Plan:
     """Convenience wrapper: owns a plan handle, returns spectra as numpy arrays."""
 
     def __init__(self, channels=1, T=256, dt=1.0, m=10, window="hann", sigma_t=0.14,
-                 orders=(2, 3, 4), dtype="f32", precision="fp32", combos=None, stream=None):
+                 orders=(2, 3, 4), dtype="f32", precision="fp32", combos=None, stream=None,
+                 estimator="unbiased"):
         win = {"hann": SS_WIN_HANN, "acg": SS_WIN_ACG}[window]
         ords = 0
         for o in orders:
@@ -330,6 +342,10 @@ class Plan:
         prec = {"fp32": SS_PREC_FP32, "tf32x3": SS_PREC_TF32X3, "bf16x3": SS_PREC_BF16X3,
                 "bf16": SS_PREC_BF16}[precision]
         self.handle = ss_plan(channels, T, dt, m, win, sigma_t, ords, dt_code, prec, combos, stream)
+        self.orders = tuple(orders)
+        if estimator != "unbiased":
+            ss_set_estimator(self.handle, {"unbiased": SS_EST_UNBIASED,
+                                           "natural": SS_EST_NATURAL}[estimator])
         self.info = ss_query(self.handle)
 
     def accumulate(self, chunk, n_samples=None):
@@ -356,6 +372,13 @@ class Plan:
             if bufs[key] is not None:
                 out[key] = bufs[key][..., 0] + 1j * bufs[key][..., 1]
                 out[key + "_err"] = bufs[key + "_err"]
+        if 1 in self.orders:
+            C = ss_query(self.handle).channels
+            s1 = np.zeros((C, 2), np.float64)
+            e1 = np.zeros((C, 2), np.float64)
+            ss_finalize_s1(self.handle, s1, e1)
+            out["S1"] = s1[:, 0] + 1j * s1[:, 1]
+            out["S1_err"] = e1
         out["G"] = ss_query(self.handle).groups
         return out
 

@@ -85,7 +85,7 @@ cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G,
                               int m, int M, int Mp, const float* win, const float2* tw,
                               float2* spec, long long spec_chan_stride, const int* s2_auto,
                               double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream,
-                              const OperandImage& oi = OperandImage());
+                              const OperandImage& oi = OperandImage(), double* acc1 = nullptr);
 
 cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G, int m, int M,
                                int Mp, const int4* pairs, int n_pairs, float pref2, double* acc2,
@@ -129,7 +129,7 @@ size_t k3tc_smem_bytes(int precision);
 // k in [-(M-1), M-1] x l in [0, M-1], accumulated at acc[plane][combo][k+M-1][l].
 cudaError_t launch_k3_trispec_cross(const float2* spec, long long chan_stride, int G, int m, int M,
                                     int Mp, const int4* combos, int n_combos, double* acc,
-                                    long long plane, int nsm, cudaStream_t stream);
+                                    long long plane, int nsm, bool natural, cudaStream_t stream);
 int k3tc_stage_chunks(int precision);
 
 // Groups per work item: about 16 items per CTA, whole groups, at least one.

@@ -160,6 +160,16 @@ __device__ __forceinline__ float load_sample(const SampleSource& s, int c, long 
   return (float)__ldg(static_cast<const short*>(s.chunk) + o);
 }
 
+// First-order spectrum of one group (Sec. 4, App. G): the group mean of the
+// zero-frequency coefficient (divided by sum g at finalize); its sum and sums of
+// squares over the CTA's groups.  Called by the thread that centres bin 0.
+__device__ __forceinline__ void add_s1(float* s1, float2 mean) {
+  s1[0] += mean.x;
+  s1[1] += mean.y;
+  s1[2] = fmaf(mean.x, mean.x, s1[2]);
+  s1[3] = fmaf(mean.y, mean.y, s1[3]);
+}
+
 // Centre bin k over the group's m frames (subtract the mean, the samples of the
 // factorised k-statistics, App. H, Eq. 85), store the centred coefficients,
 // add the per-group S2 estimate c2 = 1/(m-1) sum_j |d_j|^2 (Eq. 32) to the
@@ -233,7 +243,8 @@ __global__ void __launch_bounds__(kThreadsK1)
 k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int M, int Mp,
            const float* __restrict__ win, const float2* __restrict__ tw,
            float2* __restrict__ spec, long long chan_stride, const int* __restrict__ s2_auto,
-           double* __restrict__ acc2, int n_s2, float pref2, OperandImage oi) {
+           double* __restrict__ acc2, int n_s2, float pref2, OperandImage oi,
+           double* __restrict__ acc1) {
   extern __shared__ float4 smem_raw[];
   const int N = T / 2;
   float2* bufA = reinterpret_cast<float2*>(smem_raw);
@@ -242,7 +253,9 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
   float* s2sum = reinterpret_cast<float*>(gsum + M);             // [C][M]
   float* s2sq = s2sum + C * M;                                    // [C][M]
 
+  __shared__ float s1s[4][4];  // per channel: sums of Re, Im, Re^2, Im^2 of S1 (thread 0)
   for (int i = threadIdx.x; i < 2 * C * M; i += blockDim.x) s2sum[i] = 0.f;
+  if (threadIdx.x < 16) s1s[threadIdx.x >> 2][threadIdx.x & 3] = 0.f;
 
   for (int g = blockIdx.x; g < G; g += gridDim.x) {
     for (int c = 0; c < C; ++c) {
@@ -296,6 +309,7 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
         const bool valid = k < M;
         const float2 mean = valid ? make_float2(gsum[k].x * inv_m, gsum[k].y * inv_m)
                                   : make_float2(0.f, 0.f);
+        if (k == 0) add_s1(s1s[c], mean);
         centre_bin<FMT>(
             k, valid, mean, m, c, g, Mp, oi,
             [&](int j) { return grow[(long long)j * Mp + k]; },
@@ -315,6 +329,9 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
       atomicAdd(acc2 + 2 * plane + (long long)ia * M + k, (double)s2sq[c * M + k]);
     }
   }
+  if (acc1 && threadIdx.x == 0)  // S1 sums: planes of C values
+    for (int c = 0; c < C; ++c)
+      for (int q = 0; q < 4; ++q) atomicAdd(acc1 + q * C + c, (double)s1s[c][q]);
 }
 
 // Stockham pass over a batch of FB frames of N points (frame f at x + f N);
@@ -357,7 +374,8 @@ __global__ void __launch_bounds__(kThreadsK1)
 k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, int M, int Mp,
                int FB, const float* __restrict__ win, const float2* __restrict__ tw,
                float2* __restrict__ spec, long long chan_stride, const int* __restrict__ s2_auto,
-               double* __restrict__ acc2, int n_s2, float pref2, OperandImage oi) {
+               double* __restrict__ acc2, int n_s2, float pref2, OperandImage oi,
+           double* __restrict__ acc1) {
   extern __shared__ float4 smem_raw[];
   const int N = T / 2;
   float2* bufA = reinterpret_cast<float2*>(smem_raw);  // [FB][N]
@@ -369,7 +387,9 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
   float* s2sq = s2sum + C * M;                         // [C][M]
   constexpr int kVec = DTYPE == SS_F32 ? 16 : 8;        // bytes per vector load (4 samples)
 
+  __shared__ float s1s[4][4];  // per channel: sums of Re, Im, Re^2, Im^2 of S1 (thread 0)
   for (int i = threadIdx.x; i < 2 * C * M; i += blockDim.x) s2sum[i] = 0.f;
+  if (threadIdx.x < 16) s1s[threadIdx.x >> 2][threadIdx.x & 3] = 0.f;
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     tws[i] = __ldg(&tw[i]);
     wins[i] = __ldg(&win[i]);
@@ -453,6 +473,7 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
           for (int j = 0; j < m; ++j) mean = cadd(mean, Xs[j * Mp + k]);
           mean = make_float2(mean.x * inv_m, mean.y * inv_m);
         }
+        if (k == 0) add_s1(s1s[c], mean);
         float p = 0.f;
         for (int j = 0; j < m; ++j) {
           const float2 d = valid ? csub(Xs[j * Mp + k], mean) : make_float2(0.f, 0.f);
@@ -517,6 +538,9 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
       atomicAdd(acc2 + 2 * plane + (long long)ia * M + k, (double)s2sq[c * M + k]);
     }
   }
+  if (acc1 && threadIdx.x == 0)  // S1 sums: planes of C values
+    for (int c = 0; c < C; ++c)
+      for (int q = 0; q < 4; ++q) atomicAdd(acc1 + q * C + c, (double)s1s[c][q]);
 }
 
 // Cross-channel S2 (Sec. 7, Eq. 47): c2(a_k, b_k*) = 1/(m-1) sum_j da_jk db_jk*
@@ -562,7 +586,7 @@ cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C
                         int M, int Mp, const float* win, const float2* tw, float2* spec,
                         long long spec_chan_stride, const int* s2_auto, double* acc2, int n_s2,
                         float pref2, const OperandImage& oi, int grid, size_t smem,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, double* acc1) {
   // a group whose coefficients fit beside a batch of FFT buffers stays resident
   const size_t fixed = (size_t)m * Mp * sizeof(float2) + (size_t)2 * C * M * sizeof(float) +
                        (size_t)T * (sizeof(float2) + sizeof(float));  // + twiddles and window
@@ -584,7 +608,7 @@ cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C
     const int rgrid = std::max(1, std::min(G, nsm * std::max(1, occ)));
     k1_spectra_res<DTYPE, FMT><<<rgrid, kThreadsK1, rsmem, stream>>>(
         src, sample0, G, C, T, m, M, Mp, FB, win, tw, spec, spec_chan_stride, s2_auto, acc2, n_s2,
-        pref2, oi);
+        pref2, oi, acc1);
     return cudaGetLastError();
   }
   cudaError_t e = cudaFuncSetAttribute(k1_spectra<DTYPE, FMT>,
@@ -592,7 +616,7 @@ cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C
   if (e != cudaSuccess) return e;
   k1_spectra<DTYPE, FMT><<<grid, kThreadsK1, smem, stream>>>(src, sample0, G, C, T, m, M, Mp, win,
                                                              tw, spec, spec_chan_stride, s2_auto,
-                                                             acc2, n_s2, pref2, oi);
+                                                             acc2, n_s2, pref2, oi, acc1);
   return cudaGetLastError();
 }
 
@@ -600,7 +624,7 @@ cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G,
                               int m, int M, int Mp, const float* win, const float2* tw,
                               float2* spec, long long spec_chan_stride, const int* s2_auto,
                               double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream,
-                              const OperandImage& oi) {
+                              const OperandImage& oi, double* acc1) {
   if (G <= 0) return cudaSuccess;
   const size_t smem = (size_t)(T / 2) * 2 * sizeof(float2) + (size_t)M * sizeof(float2) +
                       (size_t)2 * C * M * sizeof(float);
@@ -610,24 +634,24 @@ cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G,
     case kImageGramTF32:
       return f32 ? launch_k1_t<SS_F32, kImageGramTF32>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
                                                    spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream)
+                                                   oi, grid, smem, stream, acc1)
                  : launch_k1_t<SS_I16, kImageGramTF32>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
                                                    spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream);
+                                                   oi, grid, smem, stream, acc1);
     case kImageGramBF16:
       return f32 ? launch_k1_t<SS_F32, kImageGramBF16>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
                                                    spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream)
+                                                   oi, grid, smem, stream, acc1)
                  : launch_k1_t<SS_I16, kImageGramBF16>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
                                                    spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream);
+                                                   oi, grid, smem, stream, acc1);
     default:
       return f32 ? launch_k1_t<SS_F32, kImageNone>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
                                                    spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream)
+                                                   oi, grid, smem, stream, acc1)
                  : launch_k1_t<SS_I16, kImageNone>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
                                                    spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream);
+                                                   oi, grid, smem, stream, acc1);
   }
 }
 

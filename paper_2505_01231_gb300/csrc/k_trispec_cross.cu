@@ -38,7 +38,8 @@ __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.
 __global__ void __launch_bounds__(kThreads, 2)
 k3_trispec_cross(const float2* __restrict__ spec, long long chan_stride, int G, int m, int M,
                  int Mp, const int4* __restrict__ combos, int tiles_l, int groups_per_cta,
-                 float pref, double* __restrict__ acc, long long plane, long long combo_stride) {
+                 float pref, float fmm, float fm1, double* __restrict__ acc, long long plane,
+                 long long combo_stride) {
   __shared__ __align__(16) float2 sx[kFrames][kRT], sy[kFrames][kRT], sxy[kFrames][kRT];
   __shared__ __align__(16) float2 sz[kFrames][kLT], sw[kFrames][kLT], szw[kFrames][kLT];
   const int tid = threadIdx.x;
@@ -55,7 +56,6 @@ k3_trispec_cross(const float2* __restrict__ spec, long long chan_stride, int G, 
   const int rows = 2 * M - 1;
   const int ti = tid & (kRT - 1), tj = tid >> 4;  // row ti, columns 4 tj .. 4 tj + 3
   const int r = r0 + ti, lc = l0 + 4 * tj;
-  const float fm1 = (float)(m - 1), fmm = (float)m * (float)(m + 1);
 
   float sre[4], sim[4], qre[4], qim[4];
 #pragma unroll
@@ -175,7 +175,7 @@ k3_trispec_cross(const float2* __restrict__ spec, long long chan_stride, int G, 
 
 cudaError_t launch_k3_trispec_cross(const float2* spec, long long chan_stride, int G, int m, int M,
                                     int Mp, const int4* combos, int n_combos, double* acc,
-                                    long long plane, int nsm, cudaStream_t stream) {
+                                    long long plane, int nsm, bool natural, cudaStream_t stream) {
   if (G <= 0 || n_combos <= 0) return cudaSuccess;
   const int rows = 2 * M - 1;
   const int tiles_r = (rows + kRT - 1) / kRT, tiles_l = (M + kLT - 1) / kLT;
@@ -189,10 +189,16 @@ cudaError_t launch_k3_trispec_cross(const float2* spec, long long chan_stride, i
   chunks = (G + gpc - 1) / gpc;
   if (tiles > 0x7fffffffll || n_combos > 65535) return cudaErrorInvalidValue;
   const double md = m;
-  const float pref = (float)(1.0 / ((md - 1.0) * (md - 2.0) * (md - 3.0)));
+  // c4 = pref [fmm sum xyzw - fm1 (sum xy sum zw + ...)]: the k-statistic (Eq. 85),
+  // or the natural estimator 1/m sum xyzw - 1/m^2 (...)
+  const float pref =
+      (float)(natural ? 1.0 / (md * md) : 1.0 / ((md - 1.0) * (md - 2.0) * (md - 3.0)));
+  const float fmm = (float)(natural ? md : md * (md + 1.0));
+  const float fm1 = (float)(natural ? 1.0 : md - 1.0);
   dim3 grid((unsigned)tiles, (unsigned)chunks, (unsigned)n_combos);
   k3_trispec_cross<<<grid, kThreads, 0, stream>>>(spec, chan_stride, G, m, M, Mp, combos, tiles_l,
-                                                  gpc, pref, acc, plane, (long long)rows * M);
+                                                  gpc, pref, fmm, fm1, acc, plane,
+                                                  (long long)rows * M);
   return cudaGetLastError();
 }
 

@@ -71,8 +71,10 @@ struct ss_plan_s {
   long long carry_n = 0;
   float2* d_spec = nullptr;
   int Gb_max = 0, Gb_user = 0;
-  double *d_acc2 = nullptr, *d_acc3 = nullptr, *d_acc4 = nullptr;
-  size_t n_acc2 = 0, n_acc3 = 0, n_acc4 = 0;
+  double *d_acc1 = nullptr, *d_acc2 = nullptr, *d_acc3 = nullptr, *d_acc4 = nullptr;
+  size_t n_acc1 = 0, n_acc2 = 0, n_acc3 = 0, n_acc4 = 0;
+  int estimator = SS_EST_UNBIASED;
+  double sg1 = 0, norm1 = 0;  // sum g and the S1 scale sqrt(sum g^2) / sum g
   int* d_s2auto = nullptr;
   int4* d_s2cross = nullptr;
   int n_s2cross = 0;
@@ -263,18 +265,22 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
     src.chunk_stride = stride;
     src.dtype = p->dtype;
     const long long chan_stride = (long long)p->Gb_max * p->m * p->Mp;
-    const float pref2 = 1.0f / (float)(p->m - 1);
+    // prefactors of c2, c3 and the two parts of c4 over the centred sums: the
+    // k-statistics (Eq. 32-34, 85) or the natural estimators
     const double md = p->m;
-    const float pref3 = (float)(md / ((md - 1) * (md - 2)));
-    const float pref4a = (float)(md * (md + 1) / ((md - 1) * (md - 2) * (md - 3)));
-    const float pref4b = (float)(1.0 / ((md - 2) * (md - 3)));
+    const bool nat = p->estimator == SS_EST_NATURAL;
+    const float pref2 = (float)(nat ? 1.0 / md : 1.0 / (md - 1));
+    const float pref3 = (float)(nat ? 1.0 / md : md / ((md - 1) * (md - 2)));
+    const float pref4a =
+        (float)(nat ? 1.0 / md : md * (md + 1) / ((md - 1) * (md - 2) * (md - 3)));
+    const float pref4b = (float)(nat ? 1.0 / (md * md) : 1.0 / ((md - 2) * (md - 3)));
     for (long long g0 = 0; g0 < Gn; g0 += gb) {
       const int cnt = (int)std::min(gb, Gn - g0);
       record(p, 0, p->stream, true);
       SS_TRY(p, launch_k1_spectra(src, g0 * per_group, cnt, p->C, p->T, p->m, p->M, p->Mp,
                                   p->d_win, p->d_tw, p->d_spec, chan_stride, p->d_s2auto,
                                   p->d_acc2, (int)p->c2.size(), pref2, 4 * p->nsm, p->stream,
-                                  p->oi));
+                                  p->oi, p->d_acc1));
       if (p->n_s2cross > 0)
         SS_TRY(p, launch_k1_cross_s2(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp,
                                      p->d_s2cross, p->n_s2cross, pref2, p->d_acc2,
@@ -303,7 +309,7 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
         if (p->C > 1)
           SS_TRY(p, launch_k3_trispec_cross(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp,
                                             p->d_c4cross, (int)p->c4.size(), p->d_acc4, plane,
-                                            p->nsm, p->stream));
+                                            p->nsm, nat, p->stream));
         for (size_t i = 0; i < p->c4.size() && p->C == 1; ++i) {
           const Combo& cb = p->c4[i];
           if (p->precision == SS_PREC_FP32)
@@ -400,6 +406,7 @@ ss_status process_host(ss_plan_s* p, const void* chunk, long long n) {
 
 ss_status zero_state(ss_plan_s* p) {
   if (p->d_status) SS_TRY(p, cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
+  if (p->d_acc1) SS_TRY(p, cudaMemsetAsync(p->d_acc1, 0, p->n_acc1 * sizeof(double), p->stream));
   if (p->d_acc2) SS_TRY(p, cudaMemsetAsync(p->d_acc2, 0, p->n_acc2 * sizeof(double), p->stream));
   if (p->d_acc3) SS_TRY(p, cudaMemsetAsync(p->d_acc3, 0, p->n_acc3 * sizeof(double), p->stream));
   if (p->d_acc4) SS_TRY(p, cudaMemsetAsync(p->d_acc4, 0, p->n_acc4 * sizeof(double), p->stream));
@@ -464,6 +471,27 @@ ss_status encode_maps(ss_plan_s* p) {
   return SS_OK;
 }
 
+// Weights of the Gram contraction of the tensor-core S4 with the prefactor r
+// folded in (see OperandImage): for the k-statistic (Eq. 85) w_jj = m^2 - m + 2,
+// w_jj' = -4(m-1), S_k S_l weight m-1, r = 1/((m-1)(m-2)(m-3)); for the natural
+// estimator, c4 = [(m-2) sum_j P_jk P_jl - 4 sum_{j<j'} G G - S_k S_l] / m^2
+// (the same regrouping of |U|^2 + |V|^2), so w_jj = m-2, w_jj' = -4, weight 1,
+// r = 1/m^2.
+void set_image_scales(ss_plan_s* p) {
+  const double md = p->m;
+  if (p->estimator == SS_EST_NATURAL) {
+    const double r = 1.0 / (md * md);
+    p->oi.sd = (float)std::sqrt((md - 2.0) * r);
+    p->oi.so = (float)std::sqrt(4.0 * r);
+    p->oi.sp = (float)std::sqrt(r);
+  } else {
+    const double r = 1.0 / ((md - 1.0) * (md - 2.0) * (md - 3.0));
+    p->oi.sd = (float)std::sqrt((md * md - md + 2.0) * r);
+    p->oi.so = (float)std::sqrt(4.0 * (md - 1.0) * r);
+    p->oi.sp = (float)std::sqrt((md - 1.0) * r);
+  }
+}
+
 ss_status alloc_spec(ss_plan_s* p) {
   auto release = [&](void*& ptr, size_t bytes) {
     if (ptr) {
@@ -509,11 +537,7 @@ ss_status alloc_spec(ss_plan_s* p) {
     p->oi.fmt = p->precision == SS_PREC_TF32X3 ? kImageGramTF32 : kImageGramBF16;
     p->oi.nkc = nkc;
     p->oi.ndc = ndc;
-    // weights of the Gram contraction with r = 1/((m-1)(m-2)(m-3)) folded in
-    const double md = p->m, r = 1.0 / ((md - 1.0) * (md - 2.0) * (md - 3.0));
-    p->oi.sd = (float)std::sqrt((md * md - md + 2.0) * r);
-    p->oi.so = (float)std::sqrt(4.0 * (md - 1.0) * r);
-    p->oi.sp = (float)std::sqrt((md - 1.0) * r);
+    set_image_scales(p);
     p->oi.rg_bytes = (long long)rg_bytes;
     p->oi.group_bytes = (long long)group_bytes;
     p->oi.chan_bytes = (long long)gb * group_bytes;
@@ -541,6 +565,7 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_spec);
   cudaFree(p->oi.img);
   cudaFree(p->oi.ps);
+  cudaFree(p->d_acc1);
   cudaFree(p->d_acc2);
   cudaFree(p->d_acc3);
   cudaFree(p->d_acc4);
@@ -577,8 +602,8 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
   if (!is_pow2(T) || T < 8 || T > 4096)
     return fail(nullptr, SS_EINVAL, "T must be a power of two in [8, 4096]");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, SS_EINVAL, "dt must be > 0");
-  if (orders == 0 || (orders & ~(unsigned)(SS_ORDER2 | SS_ORDER3 | SS_ORDER4)))
-    return fail(nullptr, SS_EINVAL, "orders must be a non-empty OR of SS_ORDER2/3/4");
+  if (orders == 0 || (orders & ~(unsigned)(SS_ORDER1 | SS_ORDER2 | SS_ORDER3 | SS_ORDER4)))
+    return fail(nullptr, SS_EINVAL, "orders must be a non-empty OR of SS_ORDER1/2/3/4");
   if (m < 2) return fail(nullptr, SS_EINVAL, "S2 needs m >= 2 (Eq. 32)");
   if ((orders & SS_ORDER3) && m < 3) return fail(nullptr, SS_EINVAL, "S3 needs m >= 3 (Eq. 33)");
   if ((orders & SS_ORDER4) && m < 4) return fail(nullptr, SS_EINVAL, "S4 needs m >= 4 (Eq. 34)");
@@ -658,10 +683,13 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
     }
   }
   for (int i = 0; i < T; ++i) {
+    p->sg1 += g[i];
     p->sg2 += g[i] * g[i];
     p->sg3 += g[i] * g[i] * g[i];
     p->sg4 += g[i] * g[i] * g[i] * g[i];
   }
+  // S1 = mean X_0 / sum g with the kernels' window scaled by 1/sqrt(sum g^2)
+  p->norm1 = std::sqrt(p->sg2) / p->sg1;
   p->norm2 = dt;
   p->norm3 = dt * dt * std::pow(p->sg2, 1.5) / p->sg3;
   p->norm4 = dt * dt * dt * p->sg2 * p->sg2 / p->sg4;
@@ -706,9 +734,11 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
   PLAN_TRY(dev_alloc(p, &p->d_carry, (size_t)channels * m * T * p->elem));
   PLAN_TRY(dev_alloc(p, &p->d_s2auto, channels * sizeof(int)));
   if (!s2cross.empty()) PLAN_TRY(dev_alloc(p, &p->d_s2cross, s2cross.size() * sizeof(int4)));
+  p->n_acc1 = (orders & SS_ORDER1) ? (size_t)kPlanes * channels : 0;
   p->n_acc2 = (size_t)kPlanes * p->c2.size() * p->M;
   p->n_acc3 = (size_t)kPlanes * p->c3.size() * p->rows3 * p->M;
   p->n_acc4 = (size_t)kPlanes * p->c4.size() * p->rows4 * p->M;
+  if (p->n_acc1) PLAN_TRY(dev_alloc(p, &p->d_acc1, p->n_acc1 * sizeof(double)));
   if (p->n_acc2) PLAN_TRY(dev_alloc(p, &p->d_acc2, p->n_acc2 * sizeof(double)));
   if (p->n_acc3) PLAN_TRY(dev_alloc(p, &p->d_acc3, p->n_acc3 * sizeof(double)));
   if (p->n_acc4) PLAN_TRY(dev_alloc(p, &p->d_acc4, p->n_acc4 * sizeof(double)));
@@ -854,6 +884,38 @@ ss_status ss_finalize(ss_plan_t p, double* S2, double* S3, double* S4, double* S
   return check_status(p);
 }
 
+ss_status ss_finalize_s1(ss_plan_t p, double* S1, double* S1_err) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
+  if (!p->d_acc1) return fail(p, SS_ESTATE, "the plan was made without SS_ORDER1");
+  if (p->groups < 2)
+    return fail(p, SS_ESTATE, "fewer than two groups accumulated: no error estimate (Eq. 35)");
+  DeviceGuard guard(p->device);
+  ss_status st = ensure_out(p);
+  if (st != SS_OK) return st;
+  const size_t n1 = (size_t)p->C * 2;
+  double* o1 = p->d_out;
+  double* e1 = o1 + n1;
+  SS_TRY(p, launch_k4_finalize(p->d_acc1, p->C, 1, 1, kLayoutVector, p->groups, p->norm1, o1,
+                               e1, p->stream));
+  if (S1) SS_TRY(p, cudaMemcpyAsync(S1, o1, n1 * sizeof(double), cudaMemcpyDefault, p->stream));
+  if (S1_err)
+    SS_TRY(p, cudaMemcpyAsync(S1_err, e1, n1 * sizeof(double), cudaMemcpyDefault, p->stream));
+  SS_TRY(p, cudaStreamSynchronize(p->stream));
+  return check_status(p);
+}
+
+ss_status ss_set_estimator(ss_plan_t p, int estimator) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (estimator != SS_EST_UNBIASED && estimator != SS_EST_NATURAL)
+    return fail(p, SS_EINVAL, "unknown estimator");
+  if (p->groups != 0 || p->carry_n != 0)
+    return fail(p, SS_ESTATE, "ss_set_estimator is valid only before the first ss_accumulate");
+  p->estimator = estimator;
+  if (p->oi.img) set_image_scales(p);
+  return SS_OK;
+}
+
 ss_status ss_reset(ss_plan_t p) {
   if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
   if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
@@ -932,7 +994,7 @@ ss_status ss_set_batch(ss_plan_t p, int groups_per_batch) {
 
 namespace {
 
-constexpr double kStateLayoutVersion = 1.0;
+constexpr double kStateLayoutVersion = 2.0;  // 2: S1 sums before the S2 sums
 constexpr int kStateCfgWords = 14;  // header words that must match; 14 = groups, 15 = samples
 
 // FNV-1a over the combination records, cut to 52 bits (exact in a double)
@@ -967,6 +1029,7 @@ void state_header(const ss_plan_s* p, double* h) {
   h[10] = (double)p->c4.size();
   h[11] = combos_hash(p);
   h[12] = kStateLayoutVersion;
+  h[13] = p->estimator;
   h[14] = (double)p->groups;
   h[15] = (double)p->samples;
 }
@@ -975,7 +1038,7 @@ void state_header(const ss_plan_s* p, double* h) {
 
 ss_status ss_state_size(ss_plan_t p, size_t* n) {
   if (!p || !n) return fail(p, SS_EINVAL, "NULL argument");
-  *n = SS_STATE_HEADER + p->n_acc2 + p->n_acc3 + p->n_acc4;
+  *n = SS_STATE_HEADER + p->n_acc1 + p->n_acc2 + p->n_acc3 + p->n_acc4;
   return SS_OK;
 }
 
@@ -989,8 +1052,9 @@ ss_status ss_export_state(ss_plan_t p, double* dst) {
   state_header(p, h);
   SS_TRY(p, cudaMemcpyAsync(dst, h, sizeof(h), cudaMemcpyDefault, p->stream));
   double* o = dst + SS_STATE_HEADER;
-  const std::pair<const double*, size_t> parts[3] = {
-      {p->d_acc2, p->n_acc2}, {p->d_acc3, p->n_acc3}, {p->d_acc4, p->n_acc4}};
+  const std::pair<const double*, size_t> parts[4] = {
+      {p->d_acc1, p->n_acc1}, {p->d_acc2, p->n_acc2}, {p->d_acc3, p->n_acc3},
+      {p->d_acc4, p->n_acc4}};
   for (const auto& pr : parts) {
     if (pr.second)
       SS_TRY(p, cudaMemcpyAsync(o, pr.first, pr.second * sizeof(double), cudaMemcpyDefault,
@@ -1015,7 +1079,7 @@ ss_status ss_merge_state(ss_plan_t p, const double* src) {
                                     std::to_string(i) + ")");
   if (!(theirs[14] >= 0.0) || !(theirs[15] >= 0.0))
     return fail(p, SS_EINVAL, "state with a negative group or sample count");
-  const size_t n = p->n_acc2 + p->n_acc3 + p->n_acc4;
+  const size_t n = p->n_acc1 + p->n_acc2 + p->n_acc3 + p->n_acc4;
   const double* payload = src + SS_STATE_HEADER;
   if (n) {
     const double* dsrc = payload;
@@ -1034,8 +1098,9 @@ ss_status ss_merge_state(ss_plan_t p, const double* src) {
                                 p->stream));
       dsrc = p->d_out;
     }
-    const std::pair<double*, size_t> parts[3] = {
-        {p->d_acc2, p->n_acc2}, {p->d_acc3, p->n_acc3}, {p->d_acc4, p->n_acc4}};
+    const std::pair<double*, size_t> parts[4] = {
+        {p->d_acc1, p->n_acc1}, {p->d_acc2, p->n_acc2}, {p->d_acc3, p->n_acc3},
+        {p->d_acc4, p->n_acc4}};
     for (const auto& pr : parts) {
       if (pr.second) SS_TRY(p, launch_add_f64(pr.first, dsrc, (long long)pr.second, p->stream));
       dsrc += pr.second;

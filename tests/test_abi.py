@@ -44,6 +44,7 @@ def test_version():
     (dict(m=1, orders=P.SS_ORDER2), "m >= 2"),
     (dict(orders=0), "orders"),
     (dict(orders=1), "orders"),
+    (dict(orders=1 << 5), "orders"),
     (dict(window=7), "window"),
     (dict(window=P.SS_WIN_ACG, win_param=-1.0), "sigma_t"),
     (dict(dtype=9), "dtype"),
@@ -72,6 +73,8 @@ def test_null_plan_calls_fail_cleanly():
     assert P.lib.ss_run_many(None, None, None, None, None, None, None, None, None) == P.SS_EINVAL
     assert P.lib.ss_many_plan(None, 0, None) == P.SS_EINVAL
     assert P.lib.ss_destroy_many(None) == P.SS_OK
+    assert P.lib.ss_set_estimator(None, 0) == P.SS_EINVAL
+    assert P.lib.ss_finalize_s1(None, None, None) == P.SS_EINVAL
     assert P.lib.ss_destroy(None) == P.SS_OK
 
 

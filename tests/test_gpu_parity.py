@@ -301,3 +301,74 @@ def test_config2_full_size_sampled_points():
     assert np.array_equal(S3, S3.T)
     assert np.array_equal(S4, S4.T)
     assert np.max(np.abs(S4.imag)) == 0.0
+
+
+# ---------------------------------------------------------------- S1 and natural estimators
+def check_s1(gpu_s1, gpu_e1, ref):
+    assert abs(gpu_s1 - ref["S1"]) <= TOL * abs(ref["S1"])
+    assert np.max(np.abs(gpu_e1 - ref["S1_err"])) <= TOL_ERR * np.max(np.abs(ref["S1_err"]))
+
+
+@pytest.mark.parametrize("estimator", ["unbiased", "natural"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16x3"])
+def test_first_order_and_natural_estimators_single_channel(estimator, precision):
+    T, m, G = 128, 6, 30
+    z = synth.ar1_quadratic(T * m * G + 17, seed=41)
+    ref = oracle.polyspectra(z, T, 0.5, m, orders=(1, 2, 3, 4), group_chunk=8,
+                             estimator=estimator)
+    mod = P()
+    plan = mod.Plan(T=T, dt=0.5, m=m, orders=(1, 2, 3, 4), precision=precision,
+                    estimator=estimator)
+    plan.accumulate(torch.from_numpy(z).cuda())
+    out = plan.finalize()
+    plan.close()
+    tol4, tol4_err = PREC_TOL.get(precision, (TOL, TOL_ERR))
+    compare_single(out, ref, tol4=tol4, tol4_err=tol4_err)
+    check_s1(out["S1"][0], out["S1_err"][0], ref)
+
+
+def test_natural_estimators_several_channels():
+    zs = synth.multichannel_shared(3, 64 * 5 * 30 + 9, seed=43)
+    combos2 = [(0, 0), (0, 2)]
+    combos3 = [(0, 1, 2), (1, 1, 0)]
+    combos4 = [(0, 0, 1, 1), (0, 1, 2, 0)]
+    recs = ([(2, *c, -1, -1) for c in combos2] + [(3, *c, -1) for c in combos3]
+            + [(4, *c) for c in combos4])
+    mod = P()
+    plan = mod.Plan(channels=3, T=64, dt=1.0, m=5, orders=(1, 2, 3, 4), combos=recs,
+                    estimator="natural")
+    plan.accumulate(torch.from_numpy(np.ascontiguousarray(zs)).cuda())
+    out = plan.finalize()
+    plan.close()
+    ref = oracle.cross_polyspectra(zs, 64, 1.0, 5, s2_combos=combos2, s3_combos=combos3,
+                                   s4_combos=combos4, estimator="natural")
+    for key, lst in (("S2", combos2), ("S3", combos3), ("S4", combos4)):
+        for i, c in enumerate(lst):
+            check({key: out[key][i], key + "_err": out[key + "_err"][i]},
+                  {key: ref[(key, c)][0], key + "_err": ref[(key, c)][1]}, key)
+    for c in range(3):  # S1 of each channel is that channel's own
+        r1 = oracle.polyspectra(zs[c], 64, 1.0, 5, orders=(1,))
+        check_s1(out["S1"][c], out["S1_err"][c], r1)
+
+
+def test_estimator_is_fixed_once_data_arrived_and_states_must_agree():
+    mod = P()
+    z = torch.from_numpy(synth.ar1_quadratic(64 * 6 * 4, seed=3)).cuda()
+    a = mod.Plan(T=64, m=6)
+    a.accumulate(z)
+    with pytest.raises(mod.SSError) as ei:
+        mod.ss_set_estimator(a.handle, mod.SS_EST_NATURAL)
+    assert ei.value.status == mod.SS_ESTATE
+    with pytest.raises(mod.SSError) as ei:
+        mod.ss_set_estimator(a.handle, 7)
+    assert ei.value.status == mod.SS_EINVAL
+    b = mod.Plan(T=64, m=6, estimator="natural")
+    b.accumulate(z)
+    with pytest.raises(mod.SSError) as ei:
+        a.merge_state(b.export_state())
+    assert ei.value.status == mod.SS_EINVAL
+    with pytest.raises(mod.SSError) as ei:  # no S1 without SS_ORDER1
+        mod.ss_finalize_s1(a.handle, np.zeros(2), np.zeros(2))
+    assert ei.value.status == mod.SS_ESTATE
+    a.close()
+    b.close()
