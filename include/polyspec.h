@@ -200,6 +200,18 @@ ss_status ss_finalize_s1(ss_plan_t plan, double* S1, double* S1_err);
  */
 ss_status ss_set_estimator(ss_plan_t plan, int estimator);
 
+/*
+ * ss_set_interlace -- on (1) or off (0): interlaced spectra (Sec. 3).  The plan
+ *   also frames the record from its sample T/2 on (windows shifted by half a
+ *   frame, so the middle of one window set covers the edges of the other) and
+ *   pools the groups of both window sets in every estimate and error bar; with
+ *   as many groups in each set, the estimate is the average of the two spectra.
+ *   Doubles the work and the device memory.  Valid only before the first
+ *   ss_accumulate (or after ss_reset); SS_ESTATE otherwise.  ss_query reports
+ *   the pooled groups; ss_export_state writes the pooled sums.
+ */
+ss_status ss_set_interlace(ss_plan_t plan, int on);
+
 /* ss_reset -- zero the accumulators, the carry-over and the statistics. */
 ss_status ss_reset(ss_plan_t plan);
 

@@ -17,6 +17,8 @@ reordering beyond what the cited formula states:
                               Sec. 7, Eq. 47, 48, 50 (multi-channel S2, S3, S4 cut)
 * error bars ............... Sec. 4.2, Eq. 35-36 (variance over N_p parts, standard error)
 * first-order spectrum ..... Sec. 4, S1 = N C1(a_0) / (T sum g); App. G
+* interlaced spectra ....... Sec. 3: the same estimate from windows shifted by T/2, pooled with
+                              the unshifted one (the groups of both window sets are the parts)
 * natural (biased) estimators, for the paper's unbiased-vs-biased comparison
                               (Sec. 4.1, Fig. 6): the cumulants of the m samples'
                               own empirical distribution, from their central moments
@@ -316,7 +318,8 @@ def s3_domain(M: int):
 
 
 def polyspectra(z, T, dt, m, window_kind="hann", sigma_t=0.14, orders=(2, 3, 4),
-                group_chunk=16, max_groups=None, factorised_c4=False, estimator="unbiased"):
+                group_chunk=16, max_groups=None, factorised_c4=False, estimator="unbiased",
+                interlaced=False):
     """Single-channel S1 (a number), S2 [M], S3 [M, M], S4 [M, M] with standard errors.
 
     Returns a dict with keys 'S2', 'S2_err', 'S3', 'S3_err', 'S4', 'S4_err', 'G'
@@ -324,11 +327,17 @@ def polyspectra(z, T, dt, m, window_kind="hann", sigma_t=0.14, orders=(2, 3, 4),
     (err_re, err_im)).  S3 is zero outside k + l <= M - 1.  ``max_groups`` limits
     the record to its first groups.  ``estimator``: "unbiased" (k-statistics,
     Eq. 32-34) or "natural" (cumulants of each group's empirical distribution).
+    ``interlaced``: add the groups of the frames that start T/2 samples later.
     """
     g = window(T, window_kind, sigma_t)
     frames = frame_groups(z, T, m)
     if max_groups is not None:
         frames = frames[:max_groups]
+    if interlaced:
+        shifted = frame_groups(np.asarray(z)[T // 2:], T, m)
+        if max_groups is not None:
+            shifted = shifted[:max_groups]
+        frames = np.concatenate([frames, shifted], axis=0)
     G = frames.shape[0]
     if G < 2:
         raise ValueError("need at least two groups for an error estimate")

@@ -78,6 +78,7 @@ _sig = {
     "ss_state_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "ss_finalize_s1": (ctypes.c_int, [_P, _P, _P]),
     "ss_set_estimator": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ss_set_interlace": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_export_state": (ctypes.c_int, [_P, _P]),
     "ss_merge_state": (ctypes.c_int, [_P, _P]),
     "ss_plan_many": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_double,
@@ -148,6 +149,10 @@ def ss_finalize_s1(plan, S1=None, S1_err=None):
 
 def ss_set_estimator(plan, estimator):
     _check(lib.ss_set_estimator(plan, estimator), plan)
+
+
+def ss_set_interlace(plan, on):
+    _check(lib.ss_set_interlace(plan, int(on)), plan)
 
 
 def ss_reset(plan):
@@ -333,7 +338,7 @@ class Plan:
 
     def __init__(self, channels=1, T=256, dt=1.0, m=10, window="hann", sigma_t=0.14,
                  orders=(2, 3, 4), dtype="f32", precision="fp32", combos=None, stream=None,
-                 estimator="unbiased"):
+                 estimator="unbiased", interlaced=False):
         win = {"hann": SS_WIN_HANN, "acg": SS_WIN_ACG}[window]
         ords = 0
         for o in orders:
@@ -346,6 +351,8 @@ class Plan:
         if estimator != "unbiased":
             ss_set_estimator(self.handle, {"unbiased": SS_EST_UNBIASED,
                                            "natural": SS_EST_NATURAL}[estimator])
+        if interlaced:
+            ss_set_interlace(self.handle, 1)
         self.info = ss_query(self.handle)
 
     def accumulate(self, chunk, n_samples=None):

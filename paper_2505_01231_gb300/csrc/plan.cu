@@ -74,6 +74,11 @@ struct ss_plan_s {
   double *d_acc1 = nullptr, *d_acc2 = nullptr, *d_acc3 = nullptr, *d_acc4 = nullptr;
   size_t n_acc1 = 0, n_acc2 = 0, n_acc3 = 0, n_acc4 = 0;
   int estimator = SS_EST_UNBIASED;
+  // interlaced spectra (Sec. 3): a plan fed the same record without its first
+  // T/2 samples, whose groups are pooled with this plan's at finalize
+  ss_plan_s* shadow = nullptr;
+  long long skip = 0;       // samples still to drop (in the shadow plan)
+  double* d_pool = nullptr;  // pooled accumulators of the two plans
   double sg1 = 0, norm1 = 0;  // sum g and the S1 scale sqrt(sum g^2) / sum g
   int* d_s2auto = nullptr;
   int4* d_s2cross = nullptr;
@@ -354,6 +359,13 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
 // sums of that launch are incomplete, so the plan is marked unusable.
 ss_status check_status(ss_plan_s* p) {
   int st = 0;
+  if (p->shadow) {
+    SS_TRY(p, cudaMemcpy(&st, p->shadow->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != kStatusOk) {
+      p->broken = true;
+      return fail(p, SS_ETIMEOUT, "a device-side wait for staged data gave up; results discarded");
+    }
+  }
   SS_TRY(p, cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st != kStatusOk) {
     p->broken = true;
@@ -377,6 +389,20 @@ ss_status ensure_stage(ss_plan_s* p) {
   return SS_OK;
 }
 
+// Pass samples on to the interlaced window set: the same stream, less its
+// first T/2 samples.
+ss_status feed_shadow(ss_plan_s* p, const void* ptr, long long n, long long stride) {
+  ss_plan_s* s = p->shadow;
+  if (!s || n <= 0) return SS_OK;
+  const long long skip = std::min(s->skip, n);
+  s->skip -= skip;
+  if (n - skip <= 0) return SS_OK;
+  ss_status st = process_device(s, static_cast<const char*>(ptr) + (size_t)skip * s->elem,
+                                n - skip, stride);
+  if (st != SS_OK) return fail(p, st, "interlaced window set: " + s->err);
+  return SS_OK;
+}
+
 ss_status process_host(ss_plan_s* p, const void* chunk, long long n) {
   ss_status st = ensure_stage(p);
   if (st != SS_OK) return st;
@@ -396,6 +422,7 @@ ss_status process_host(ss_plan_s* p, const void* chunk, long long n) {
     SS_TRY(p, cudaEventRecord(p->ev_ready[b], p->copy_stream));
     SS_TRY(p, cudaStreamWaitEvent(p->stream, p->ev_ready[b], 0));
     st = process_device(p, p->d_stage[b], len, p->stage_n);
+    if (st == SS_OK) st = feed_shadow(p, p->d_stage[b], len, p->stage_n);
     if (st != SS_OK) return st;
     SS_TRY(p, cudaEventRecord(p->ev_free[b], p->stream));
   }
@@ -548,6 +575,9 @@ ss_status alloc_spec(ss_plan_s* p) {
 
 void destroy(ss_plan_s* p) {
   if (!p) return;
+  if (p->shadow) destroy(p->shadow);
+  p->shadow = nullptr;
+  cudaFree(p->d_pool);
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->copy_stream) {
     cudaStreamSynchronize(p->copy_stream);
@@ -807,9 +837,43 @@ ss_status ss_accumulate(ss_plan_t p, const void* chunk, size_t n_samples) {
   if (!chunk) return fail(p, SS_EINVAL, "chunk is NULL");
   if (n_samples > (size_t)1 << 46) return fail(p, SS_EINVAL, "n_samples too large");
   DeviceGuard guard(p->device);
-  if (is_device_ptr(chunk)) return process_device(p, chunk, (long long)n_samples,
-                                                  (long long)n_samples);
+  if (is_device_ptr(chunk)) {
+    ss_status st = process_device(p, chunk, (long long)n_samples, (long long)n_samples);
+    if (st == SS_OK) st = feed_shadow(p, chunk, (long long)n_samples, (long long)n_samples);
+    return st;
+  }
   return process_host(p, chunk, (long long)n_samples);
+}
+
+// The sums to finalize or export: the plan's own, or with an interlaced window
+// set the element-wise sum of both plans' sums and groups.
+struct Pooled {
+  double *a1, *a2, *a3, *a4;
+  long long groups, samples;
+};
+
+static ss_status pooled(ss_plan_s* p, Pooled* out) {
+  *out = Pooled{p->d_acc1, p->d_acc2, p->d_acc3, p->d_acc4, p->groups, p->samples};
+  ss_plan_s* s = p->shadow;
+  if (!s) return SS_OK;
+  const size_t n = p->n_acc1 + p->n_acc2 + p->n_acc3 + p->n_acc4;
+  if (!p->d_pool) SS_TRY(p, dev_alloc(p, &p->d_pool, n * sizeof(double)));
+  double* q = p->d_pool;
+  double** dst[4] = {&out->a1, &out->a2, &out->a3, &out->a4};
+  const double* mine[4] = {p->d_acc1, p->d_acc2, p->d_acc3, p->d_acc4};
+  const double* theirs[4] = {s->d_acc1, s->d_acc2, s->d_acc3, s->d_acc4};
+  const size_t cnt[4] = {p->n_acc1, p->n_acc2, p->n_acc3, p->n_acc4};
+  for (int i = 0; i < 4; ++i) {
+    if (!cnt[i]) continue;
+    SS_TRY(p, cudaMemcpyAsync(q, mine[i], cnt[i] * sizeof(double), cudaMemcpyDeviceToDevice,
+                              p->stream));
+    SS_TRY(p, launch_add_f64(q, theirs[i], (long long)cnt[i], p->stream));
+    *dst[i] = q;
+    q += cnt[i];
+  }
+  out->groups += s->groups;
+  out->samples += s->samples;
+  return SS_OK;
 }
 
 // The finalize buffer: means and errors of every spectrum (complex doubles).
@@ -836,6 +900,9 @@ static ss_status finalize_launch(ss_plan_s* p, double* S2, double* S3, double* S
                                  double* S2_err, double* S3_err, double* S4_err) {
   ss_status st0 = ensure_out(p);
   if (st0 != SS_OK) return st0;
+  Pooled pl;
+  st0 = pooled(p, &pl);
+  if (st0 != SS_OK) return st0;
   const size_t n2 = p->c2.size() * p->M * 2;
   const size_t n3 = p->c3.size() * p->rows3 * p->M * 2;
   const size_t n4 = p->c4.size() * p->rows4 * p->M * 2;
@@ -848,17 +915,17 @@ static ss_status finalize_launch(ss_plan_s* p, double* S2, double* S3, double* S
   const bool single = p->C == 1;
   record(p, 3, p->stream, true);
   if (n2)
-    SS_TRY(p, launch_k4_finalize(p->d_acc2, (int)p->c2.size(), 1, p->M, kLayoutVector,
-                                 p->groups, p->norm2, o2, e2, p->stream));
+    SS_TRY(p, launch_k4_finalize(pl.a2, (int)p->c2.size(), 1, p->M, kLayoutVector,
+                                 pl.groups, p->norm2, o2, e2, p->stream));
   if (n3)
-    SS_TRY(p, launch_k4_finalize(p->d_acc3, (int)p->c3.size(), p->rows3, p->M,
-                                 single ? kLayoutS3Single : kLayoutCross, p->groups, p->norm3,
+    SS_TRY(p, launch_k4_finalize(pl.a3, (int)p->c3.size(), p->rows3, p->M,
+                                 single ? kLayoutS3Single : kLayoutCross, pl.groups, p->norm3,
                                  o3, e3, p->stream));
   if (n4)
-    SS_TRY(p, launch_k4_finalize(p->d_acc4, (int)p->c4.size(), p->rows4, p->M,
+    SS_TRY(p, launch_k4_finalize(pl.a4, (int)p->c4.size(), p->rows4, p->M,
                                  !single ? kLayoutCross
                                  : p->precision == SS_PREC_FP32 ? kLayoutS4Single : kLayoutS4Lower,
-                                 p->groups, p->norm4,
+                                 pl.groups, p->norm4,
                                  o4, e4, p->stream));
   record(p, 3, p->stream, false);
   const std::pair<double*, std::pair<const double*, size_t>> copies[6] = {
@@ -875,7 +942,7 @@ ss_status ss_finalize(ss_plan_t p, double* S2, double* S3, double* S4, double* S
                       double* S3_err, double* S4_err) {
   if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
   if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
-  if (p->groups < 2)
+  if (p->groups + (p->shadow ? p->shadow->groups : 0) < 2)
     return fail(p, SS_ESTATE, "fewer than two groups accumulated: no error estimate (Eq. 35)");
   DeviceGuard guard(p->device);
   ss_status st = finalize_launch(p, S2, S3, S4, S2_err, S3_err, S4_err);
@@ -888,15 +955,18 @@ ss_status ss_finalize_s1(ss_plan_t p, double* S1, double* S1_err) {
   if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
   if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
   if (!p->d_acc1) return fail(p, SS_ESTATE, "the plan was made without SS_ORDER1");
-  if (p->groups < 2)
+  if (p->groups + (p->shadow ? p->shadow->groups : 0) < 2)
     return fail(p, SS_ESTATE, "fewer than two groups accumulated: no error estimate (Eq. 35)");
   DeviceGuard guard(p->device);
   ss_status st = ensure_out(p);
   if (st != SS_OK) return st;
+  Pooled pl;
+  st = pooled(p, &pl);
+  if (st != SS_OK) return st;
   const size_t n1 = (size_t)p->C * 2;
   double* o1 = p->d_out;
   double* e1 = o1 + n1;
-  SS_TRY(p, launch_k4_finalize(p->d_acc1, p->C, 1, 1, kLayoutVector, p->groups, p->norm1, o1,
+  SS_TRY(p, launch_k4_finalize(pl.a1, p->C, 1, 1, kLayoutVector, pl.groups, p->norm1, o1,
                                e1, p->stream));
   if (S1) SS_TRY(p, cudaMemcpyAsync(S1, o1, n1 * sizeof(double), cudaMemcpyDefault, p->stream));
   if (S1_err)
@@ -911,12 +981,51 @@ ss_status ss_set_estimator(ss_plan_t p, int estimator) {
     return fail(p, SS_EINVAL, "unknown estimator");
   if (p->groups != 0 || p->carry_n != 0)
     return fail(p, SS_ESTATE, "ss_set_estimator is valid only before the first ss_accumulate");
-  p->estimator = estimator;
-  if (p->oi.img) set_image_scales(p);
+  for (ss_plan_s* q = p; q; q = q->shadow) {
+    q->estimator = estimator;
+    if (q->oi.img) set_image_scales(q);
+  }
+  return SS_OK;
+}
+
+ss_status ss_set_interlace(ss_plan_t p, int on) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (p->groups != 0 || p->carry_n != 0)
+    return fail(p, SS_ESTATE, "ss_set_interlace is valid only before the first ss_accumulate");
+  DeviceGuard guard(p->device);
+  if (!on) {
+    if (p->shadow) {
+      destroy(p->shadow);
+      p->shadow = nullptr;
+    }
+    return SS_OK;
+  }
+  if (p->shadow) return SS_OK;
+  // the same configuration and combinations, fed from T/2 samples on
+  std::vector<int> recs;
+  for (const auto* list : {&p->c2, &p->c3, &p->c4})
+    for (const Combo& cb : *list) {
+      recs.push_back(cb.order);
+      for (int q = 0; q < 4; ++q) recs.push_back(q < cb.order ? cb.c[q] : -1);
+    }
+  ss_plan_t s = nullptr;
+  ss_status st = plan_create(&s, p->C, p->T, p->dt, p->m, p->window, p->win_param, p->orders,
+                             p->dtype, p->precision, recs.empty() ? nullptr : recs.data(),
+                             (int)(recs.size() / 5), p->stream, p->Gb_user);
+  if (st != SS_OK) return fail(p, st, "interlaced window set: " + g_plan_error);
+  s->estimator = p->estimator;
+  if (s->oi.img) set_image_scales(s);
+  s->skip = p->T / 2;
+  p->shadow = s;
   return SS_OK;
 }
 
 ss_status ss_reset(ss_plan_t p) {
+  if (p && p->shadow && !p->broken) {
+    ss_status st = ss_reset(p->shadow);
+    if (st != SS_OK) return fail(p, st, "interlaced window set: " + p->shadow->err);
+    p->shadow->skip = p->T / 2;
+  }
   if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
   if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
   DeviceGuard guard(p->device);
@@ -935,7 +1044,7 @@ ss_status ss_query(ss_plan_t p, ss_info* info) {
   info->n_s4 = (int)p->c4.size();
   info->rows3 = p->rows3;
   info->rows4 = p->rows4;
-  info->groups = p->groups;
+  info->groups = p->groups + (p->shadow ? p->shadow->groups : 0);
   info->samples = p->samples;
   info->carried = p->carry_n;
   info->groups_per_batch = p->Gb_max;
@@ -989,6 +1098,11 @@ ss_status ss_set_batch(ss_plan_t p, int groups_per_batch) {
   DeviceGuard guard(p->device);
   SS_TRY(p, cudaStreamSynchronize(p->stream));
   p->Gb_user = groups_per_batch;
+  if (p->shadow) {
+    p->shadow->Gb_user = groups_per_batch;
+    ss_status st = alloc_spec(p->shadow);
+    if (st != SS_OK) return fail(p, st, "interlaced window set: " + p->shadow->err);
+  }
   return alloc_spec(p);
 }
 
@@ -1019,7 +1133,7 @@ void state_header(const ss_plan_s* p, double* h) {
   h[0] = p->C;
   h[1] = p->T;
   h[2] = p->m;
-  h[3] = p->orders;
+  h[3] = p->orders | (p->shadow ? 1u : 0u);  // bit 0: interlaced
   h[4] = p->precision;
   h[5] = p->window;
   h[6] = p->window == SS_WIN_ACG ? p->win_param : 0.0;
@@ -1048,13 +1162,17 @@ ss_status ss_export_state(ss_plan_t p, double* dst) {
   DeviceGuard guard(p->device);
   ss_status st = check_status(p);
   if (st != SS_OK) return st;
+  Pooled pl;  // with an interlaced window set, the sums of both
+  st = pooled(p, &pl);
+  if (st != SS_OK) return st;
   double h[SS_STATE_HEADER];
   state_header(p, h);
+  h[14] = (double)pl.groups;
+  h[15] = (double)pl.samples;
   SS_TRY(p, cudaMemcpyAsync(dst, h, sizeof(h), cudaMemcpyDefault, p->stream));
   double* o = dst + SS_STATE_HEADER;
   const std::pair<const double*, size_t> parts[4] = {
-      {p->d_acc1, p->n_acc1}, {p->d_acc2, p->n_acc2}, {p->d_acc3, p->n_acc3},
-      {p->d_acc4, p->n_acc4}};
+      {pl.a1, p->n_acc1}, {pl.a2, p->n_acc2}, {pl.a3, p->n_acc3}, {pl.a4, p->n_acc4}};
   for (const auto& pr : parts) {
     if (pr.second)
       SS_TRY(p, cudaMemcpyAsync(o, pr.first, pr.second * sizeof(double), cudaMemcpyDefault,

@@ -75,6 +75,7 @@ def test_null_plan_calls_fail_cleanly():
     assert P.lib.ss_destroy_many(None) == P.SS_OK
     assert P.lib.ss_set_estimator(None, 0) == P.SS_EINVAL
     assert P.lib.ss_finalize_s1(None, None, None) == P.SS_EINVAL
+    assert P.lib.ss_set_interlace(None, 1) == P.SS_EINVAL
     assert P.lib.ss_destroy(None) == P.SS_OK
 
 

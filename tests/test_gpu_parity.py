@@ -372,3 +372,54 @@ def test_estimator_is_fixed_once_data_arrived_and_states_must_agree():
     assert ei.value.status == mod.SS_ESTATE
     a.close()
     b.close()
+
+
+# ---------------------------------------------------------------- interlaced spectra
+@pytest.mark.parametrize("feed", ["device", "host", "pieces"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
+def test_interlaced_spectra(feed, precision):
+    T, m, G = 64, 6, 25
+    z = synth.ar1_quadratic(T * m * G + 2 * T + 5, seed=47)
+    ref = oracle.polyspectra(z, T, 0.5, m, orders=(1, 2, 3, 4), group_chunk=8, interlaced=True)
+    mod = P()
+    plan = mod.Plan(T=T, dt=0.5, m=m, orders=(1, 2, 3, 4), precision=precision, interlaced=True)
+    if feed == "device":
+        plan.accumulate(torch.from_numpy(z).cuda())
+    elif feed == "host":
+        plan.accumulate(z)
+    else:  # pieces shorter than T/2 first: the shift spans several calls
+        cuts = [0, 7, 19, 30, 500, 3001, len(z)]
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            plan.accumulate(torch.from_numpy(np.ascontiguousarray(z[a:b])).cuda(), b - a)
+    out = plan.finalize()
+    tol4, tol4_err = PREC_TOL.get(precision, (TOL, TOL_ERR))
+    compare_single(out, ref, tol4=tol4, tol4_err=tol4_err)
+    check_s1(out["S1"][0], out["S1_err"][0], ref)
+    # a reset restarts both window sets
+    plan.reset()
+    plan.accumulate(torch.from_numpy(z).cuda())
+    again = plan.finalize()
+    for key in ("S2", "S3", "S4"):
+        assert np.allclose(again[key], out[key], rtol=0, atol=1e-12 * np.max(np.abs(out[key])))
+    plan.close()
+
+
+def test_interlaced_natural_and_state_rules():
+    T, m, G = 32, 5, 20
+    z = synth.ar1_quadratic(T * m * G + T, seed=53)
+    ref = oracle.polyspectra(z, T, 1.0, m, orders=(2, 3, 4), interlaced=True, estimator="natural")
+    mod = P()
+    plan = mod.Plan(T=T, m=m, estimator="natural", interlaced=True)
+    plan.accumulate(torch.from_numpy(z).cuda())
+    out = plan.finalize()
+    compare_single(out, ref)
+    assert out["G"] == ref["G"]
+    with pytest.raises(mod.SSError) as ei:  # fixed once data arrived
+        mod.ss_set_interlace(plan.handle, 0)
+    assert ei.value.status == mod.SS_ESTATE
+    plain = mod.Plan(T=T, m=m, estimator="natural")
+    with pytest.raises(mod.SSError) as ei:  # an interlaced state is not a plain one
+        plain.merge_state(plan.export_state())
+    assert ei.value.status == mod.SS_EINVAL
+    plain.close()
+    plan.close()

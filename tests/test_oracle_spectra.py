@@ -199,3 +199,17 @@ def test_running_sums_equal_per_group_statistics():
     assert np.allclose(r["S3_err"][kk, ll, 0], stats.sem(s3.real, axis=0, ddof=1), rtol=1e-8, atol=1e-12)
     assert np.allclose(r["S3_err"][kk, ll, 1], stats.sem(s3.imag, axis=0, ddof=1), rtol=1e-8, atol=1e-12)
     assert np.allclose(r["S3"][kk, ll], s3.mean(axis=0))
+
+
+def test_interlaced_estimate_pools_the_two_window_sets():
+    # with as many shifted groups as unshifted ones, the pooled estimate is the
+    # average of the two spectra; the shifted set is the record without its first
+    # T/2 samples
+    T, m, G = 32, 5, 12
+    z = synth.ar1_quadratic(T * m * G + T // 2, seed=8)
+    both = oracle.polyspectra(z, T, 0.5, m, orders=(1, 2, 3, 4), interlaced=True)
+    a = oracle.polyspectra(z, T, 0.5, m, orders=(1, 2, 3, 4))
+    b = oracle.polyspectra(z[T // 2:], T, 0.5, m, orders=(1, 2, 3, 4))
+    assert both["G"] == a["G"] + b["G"] == 2 * G
+    for key in ("S1", "S2", "S3", "S4"):
+        assert np.allclose(both[key], 0.5 * (a[key] + b[key]), rtol=1e-12, atol=1e-14)
