@@ -438,7 +438,7 @@ def main():
                 "stage_ms_per_step": {nm: float(stage_ms[i] / args.steps)
                                       for i, nm in enumerate(names[:4])},
                 "launch_ms": float(stage_ms[dom] / max(1, launches))}
-    gpu_launches = int(args.steps * (n_batches * (1 + info.n_s3 + info.n_s4) + 3))
+    gpu_launches = int(args.steps * (n_batches * info.kernels_per_batch + 3))
 
     # ---- the S4 stage against its own bound: the tensor pipe in the split modes
     # (useful products of the Gram contraction, K = m(m+1)/2 per grid point and

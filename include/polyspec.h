@@ -103,6 +103,9 @@ typedef struct {
   long long carried;         /* samples per channel waiting for a full group      */
   int groups_per_batch;      /* groups processed per device batch                 */
   size_t device_bytes;       /* device memory held by the plan                    */
+  int kernels_per_batch;     /* kernel launches of one device batch (the K1-K3
+                                stages of this window set; the interlaced set, if
+                                any, launches as many again)                      */
 } ss_info;
 
 /* Per-stage device time, summed over launches since the last reset, measured

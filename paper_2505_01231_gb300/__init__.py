@@ -48,7 +48,7 @@ class ss_info(ctypes.Structure):
                 ("n_s4", ctypes.c_int), ("rows3", ctypes.c_int), ("rows4", ctypes.c_int),
                 ("groups", ctypes.c_longlong), ("samples", ctypes.c_longlong),
                 ("carried", ctypes.c_longlong), ("groups_per_batch", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("kernels_per_batch", ctypes.c_int)]
 
 
 class ss_stats_t(ctypes.Structure):

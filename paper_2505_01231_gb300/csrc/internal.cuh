@@ -142,6 +142,11 @@ inline int work_group_chunk(int G, int n_tiles, int n_cta) {
   return (int)gc;
 }
 
+// K2 for isolated grid points of one channel (pts: n_pts (k, l) pairs)
+cudaError_t launch_k2_points(const float2* spec, int Mp, int G, int m, const int2* pts,
+                             int n_pts, int M, float pref3, double* acc, long long plane,
+                             cudaStream_t stream);
+
 // dynamic shared memory of the pair kernels for FC frames per stage
 size_t k2_smem_bytes(int FC);
 size_t k3_smem_bytes(int FC);

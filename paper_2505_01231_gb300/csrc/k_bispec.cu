@@ -322,6 +322,52 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
   }
 }
 
+// Isolated grid points of one channel (the tiles that hold a single point of
+// the domain, where the edge k + l = M - 1 passes a tile corner): each thread
+// evaluates c3 at one point for one group at a time, reading the centred
+// coefficients from global memory, and the block sums over its groups in
+// float64 before one atomic add per part.
+constexpr int kPointThreads = 128;
+
+__global__ void __launch_bounds__(kPointThreads)
+k2_points(const float2* __restrict__ spec, int Mp, int G, int m, const int2* __restrict__ pts,
+          int M, float pref3, double* __restrict__ acc, long long plane) {
+  __shared__ double red[4][kPointThreads / 32];
+  const int2 pt = pts[blockIdx.x];
+  const int k = pt.x, l = pt.y;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int g = blockIdx.y * kPointThreads + threadIdx.x; g < G;
+       g += gridDim.y * kPointThreads) {
+    const float2* row = spec + (long long)g * m * Mp;
+    float ar = 0.f, ai = 0.f;
+    for (int j = 0; j < m; ++j, row += Mp) {
+      const float2 a = row[k], b = row[l], c = row[k + l];
+      const float px = fmaf(a.x, b.x, -a.y * b.y);
+      const float py = fmaf(a.x, b.y, a.y * b.x);
+      ar = fmaf(px, c.x, fmaf(py, c.y, ar));
+      ai = fmaf(py, c.x, fmaf(-px, c.y, ai));
+    }
+    const double vr = (double)(ar * pref3), vi = (double)(ai * pref3);
+    s[0] += vr;
+    s[1] += vi;
+    s[2] += vr * vr;
+    s[3] += vi * vi;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double v = s[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[q][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0.0;
+    for (int i = 0; i < kPointThreads / 32; ++i) v += red[threadIdx.x][i];
+    atomicAdd(acc + (long long)threadIdx.x * plane + (long long)k * M + l, v);
+  }
+}
+
 }  // namespace
 
 size_t k2_smem_bytes(int FC) { return (size_t)kStages * stage_bytes(FC) + 1024; }
@@ -406,6 +452,16 @@ cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
     default: return launch_k2_t<0>(K2_ARGS);
   }
 #undef K2_ARGS
+}
+
+cudaError_t launch_k2_points(const float2* spec, int Mp, int G, int m, const int2* pts,
+                             int n_pts, int M, float pref3, double* acc, long long plane,
+                             cudaStream_t stream) {
+  if (G <= 0 || n_pts <= 0) return cudaSuccess;
+  const int gy = std::min(256, (G + kPointThreads - 1) / kPointThreads);
+  k2_points<<<dim3((unsigned)n_pts, (unsigned)gy), kPointThreads, 0, stream>>>(
+      spec, Mp, G, m, pts, M, pref3, acc, plane);
+  return cudaGetLastError();
 }
 
 }  // namespace ss

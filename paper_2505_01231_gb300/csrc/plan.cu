@@ -94,6 +94,8 @@ struct ss_plan_s {
   int n_tiles4tc = 0;
   OperandImage oi;                 // K1's second output for the tensor-core S4 kernel
   int n_tiles3 = 0, n_tiles4 = 0;
+  int2* d_pts3 = nullptr;  // isolated S3 grid points of one channel (k2_points)
+  int n_pts3 = 0;
   long long pairs3 = 0, pairs4 = 0;
   void* d_stage[2] = {nullptr, nullptr};
   long long stage_n = 0;
@@ -193,7 +195,12 @@ std::vector<TileInfo> build_tc_tiles(int M) {
 
 // Tiles of 64 x 64 grid points that touch the domain, with the number of
 // their 32 x 16 warp sub-tiles that touch it (the kernels skip the others).
-void build_tiles(ss_plan_s* p, std::vector<TileInfo>& t3, std::vector<TileInfo>& t4) {
+// A one-channel S3 tile holding at most this many domain points (the corner
+// tiles cut by k + l = M - 1) is left to k2_points.
+constexpr int kIsolatedPoints = 8;
+
+void build_tiles(ss_plan_s* p, std::vector<TileInfo>& t3, std::vector<TileInfo>& t4,
+                 std::vector<int2>& pts3) {
   const int M = p->M;
   const bool cross = p->C > 1;
   p->pairs3 = 0;
@@ -217,7 +224,15 @@ void build_tiles(ss_plan_s* p, std::vector<TileInfo>& t3, std::vector<TileInfo>&
   for (int k0 = kmin; k0 < M; k0 += kTile)
     for (int l0 = 0; l0 < M; l0 += kTile) {
       const int w3 = warps(k0, l0, dom3), w4 = warps(k0, l0, dom4);
-      if (w3) t3.push_back(TileInfo{k0, l0, w3, 0});
+      std::vector<int2> in3;
+      if (w3 && !cross)
+        for (int a = 0; a < kTile && (int)in3.size() <= kIsolatedPoints; ++a)
+          for (int b = 0; b < kTile && (int)in3.size() <= kIsolatedPoints; ++b)
+            if (dom3(k0 + a, l0 + b)) in3.push_back(make_int2(k0 + a, l0 + b));
+      if (w3 && !cross && (int)in3.size() <= kIsolatedPoints)
+        pts3.insert(pts3.end(), in3.begin(), in3.end());
+      else if (w3)
+        t3.push_back(TileInfo{k0, l0, w3, 0});
       if (w4) t4.push_back(TileInfo{k0, l0, w4, 0});
     }
   for (int k = -(M - 1); k < M; ++k)
@@ -305,6 +320,11 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
                                      p->C > 1 ? 1 : 0, pref3,
                                      p->d_acc3 + (long long)i * p->rows3 * p->M, plane, p->rows3,
                                      p->nsm, p->d_counter, p->d_status, p->stream));
+          if (p->C == 1 && p->n_pts3 > 0)
+            SS_TRY(p, launch_k2_points(p->d_spec + cb.c[0] * chan_stride, p->Mp, cnt, p->m,
+                                       p->d_pts3, p->n_pts3, p->M, pref3,
+                                       p->d_acc3 + (long long)i * p->rows3 * p->M, plane,
+                                       p->stream));
         }
         record(p, 1, p->stream, false);
       }
@@ -602,6 +622,7 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_s2auto);
   cudaFree(p->d_s2cross);
   cudaFree(p->d_tiles3);
+  cudaFree(p->d_pts3);
   cudaFree(p->d_tiles4);
   cudaFree(p->d_tiles4tc);
   cudaFree(p->d_c4cross);
@@ -740,14 +761,19 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
   }
   p->n_s2cross = (int)s2cross.size();
   std::vector<TileInfo> t3, t4;
-  build_tiles(p, t3, t4);
+  std::vector<int2> pts3;
+  build_tiles(p, t3, t4, pts3);
   std::vector<TileInfo> t4tc;
   if (channels == 1 && !p->c4.empty() && precision != SS_PREC_FP32) t4tc = build_tc_tiles(p->M);
   p->n_tiles4tc = (int)t4tc.size();
-  if (p->c3.empty()) t3.clear();
+  if (p->c3.empty()) {
+    t3.clear();
+    pts3.clear();
+  }
   if (p->c4.empty() || channels > 1) t4.clear();  // several channels: k3_trispec_cross
   p->n_tiles3 = (int)t3.size();
   p->n_tiles4 = (int)t4.size();
+  p->n_pts3 = (int)pts3.size();
 
 #define PLAN_TRY(call)                           \
   do {                                           \
@@ -773,6 +799,7 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
   if (p->n_acc3) PLAN_TRY(dev_alloc(p, &p->d_acc3, p->n_acc3 * sizeof(double)));
   if (p->n_acc4) PLAN_TRY(dev_alloc(p, &p->d_acc4, p->n_acc4 * sizeof(double)));
   if (!t3.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles3, t3.size() * sizeof(TileInfo)));
+  if (!pts3.empty()) PLAN_TRY(dev_alloc(p, &p->d_pts3, pts3.size() * sizeof(int2)));
   if (!t4.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4, t4.size() * sizeof(TileInfo)));
   if (!t4tc.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4tc, t4tc.size() * sizeof(TileInfo)));
   std::vector<int4> c4x;
@@ -794,6 +821,9 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
                         cudaMemcpyHostToDevice));
   if (!t3.empty())
     PLAN_TRY(cudaMemcpy(p->d_tiles3, t3.data(), t3.size() * sizeof(TileInfo),
+                        cudaMemcpyHostToDevice));
+  if (!pts3.empty())
+    PLAN_TRY(cudaMemcpy(p->d_pts3, pts3.data(), pts3.size() * sizeof(int2),
                         cudaMemcpyHostToDevice));
   if (!t4.empty())
     PLAN_TRY(cudaMemcpy(p->d_tiles4, t4.data(), t4.size() * sizeof(TileInfo),
@@ -1049,6 +1079,9 @@ ss_status ss_query(ss_plan_t p, ss_info* info) {
   info->carried = p->carry_n;
   info->groups_per_batch = p->Gb_max;
   info->device_bytes = p->device_bytes;
+  info->kernels_per_batch = 1 + (p->n_s2cross > 0 ? 1 : 0) +
+                            (int)p->c3.size() * (1 + (p->C == 1 && p->n_pts3 > 0 ? 1 : 0)) +
+                            (p->C > 1 ? (p->c4.empty() ? 0 : 1) : (int)p->c4.size());
   return SS_OK;
 }
 
