@@ -147,6 +147,10 @@ cudaError_t launch_k2_points(const float2* spec, int Mp, int G, int m, const int
                              int n_pts, int M, float pref3, double* acc, long long plane,
                              cudaStream_t stream);
 
+// the one-channel S4 cut at l = M - 1 for every k, stored at [l][k]
+cudaError_t launch_k3_column(const float2* spec, int Mp, int G, int m, int M, float pref4a,
+                             float pref4b, double* acc, long long plane, cudaStream_t stream);
+
 // dynamic shared memory of the pair kernels for FC frames per stage
 size_t k2_smem_bytes(int FC);
 size_t k3_smem_bytes(int FC);

@@ -21,6 +21,8 @@
 // k0.. and l0.. arrive by 128-byte-swizzled 3-D TMA box loads into kStages
 // shared-memory stages, |da|^2 is formed once per staged chunk, and each thread
 // evaluates a 4 x 4 micro-tile (quarter-warps of 4 k-threads x 2 l-threads).
+#include <algorithm>
+
 #include "internal.cuh"
 #include "pipeline.cuh"
 
@@ -219,6 +221,58 @@ cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, i
   if (e != cudaSuccess) return e;
   k3_trispec<<<n_cta, kThreadsPair, smem, stream>>>(tm64, row0, G, m, FC, M, tiles, wq, pref4a,
                                                     pref4b, acc, plane, status);
+  return cudaGetLastError();
+}
+
+// The last column l = M - 1 of the one-channel cut for every k (the tensor-core
+// tiles leave it out when it is the only column of its block): one thread per
+// k, the same five length-m sums as above per group, reading the centred
+// coefficients from global memory (consecutive k are consecutive addresses; the
+// bin-l values are the same address across a warp).  Written at [l][k], the
+// layout of the tensor-core kernel's accumulators.
+constexpr int kColThreads = 128;
+
+__global__ void __launch_bounds__(kColThreads)
+k3_column(const float2* __restrict__ spec, int Mp, int G, int m, int M, float pref_a,
+          float pref_b, double* __restrict__ acc, long long plane) {
+  const int k = blockIdx.x * kColThreads + threadIdx.x;
+  const int l = M - 1;
+  if (k >= M) return;
+  float sum = 0.f, sq = 0.f;
+  for (int g = blockIdx.y; g < G; g += gridDim.y) {
+    const float2* row = spec + (long long)g * m * Mp;
+    float q = 0.f, sk = 0.f, sl = 0.f, rr = 0.f, ii = 0.f, xx = 0.f, xt = 0.f;
+    for (int j = 0; j < m; ++j, row += Mp) {
+      const float2 a = __ldg(row + k), b = __ldg(row + l);
+      const float pk = fmaf(a.x, a.x, a.y * a.y), pl = fmaf(b.x, b.x, b.y * b.y);
+      q = fmaf(pk, pl, q);
+      sk += pk;
+      sl += pl;
+      rr = fmaf(a.x, b.x, rr);
+      ii = fmaf(a.y, b.y, ii);
+      xx = fmaf(a.x, b.y, xx);
+      xt = fmaf(a.y, b.x, xt);
+    }
+    float uv = fmaf(rr, rr, ii * ii);
+    uv = fmaf(xx, xx, uv);
+    uv = fmaf(xt, xt, uv);
+    const float pair = fmaf(2.f, uv, sk * sl);
+    const float c4 = fmaf(pref_a, q, -pref_b * pair);
+    sum += c4;
+    sq = fmaf(c4, c4, sq);
+  }
+  const long long o = (long long)l * M + k;
+  atomicAdd(acc + o, (double)sum);
+  atomicAdd(acc + 2 * plane + o, (double)sq);
+}
+
+cudaError_t launch_k3_column(const float2* spec, int Mp, int G, int m, int M, float pref4a,
+                             float pref4b, double* acc, long long plane, cudaStream_t stream) {
+  if (G <= 0 || M <= 0) return cudaSuccess;
+  const int gx = (M + kColThreads - 1) / kColThreads;
+  const int gy = std::min(G, 1024);
+  k3_column<<<dim3((unsigned)gx, (unsigned)gy), kColThreads, 0, stream>>>(
+      spec, Mp, G, m, M, pref4a, pref4b, acc, plane);
   return cudaGetLastError();
 }
 

@@ -95,6 +95,7 @@ struct ss_plan_s {
   OperandImage oi;                 // K1's second output for the tensor-core S4 kernel
   int n_tiles3 = 0, n_tiles4 = 0;
   int2* d_pts3 = nullptr;  // isolated S3 grid points of one channel (k2_points)
+  bool col4 = false;       // the S4 column l = M - 1 is left to k3_column
   int n_pts3 = 0;
   long long pairs3 = 0, pairs4 = 0;
   void* d_stage[2] = {nullptr, nullptr};
@@ -183,11 +184,20 @@ bool in_domain3(int k, int l, int M, bool cross) {
 // Tiles of the tensor-core S4 kernel that touch the upper triangle k <= l < M:
 // 128 k-bins by up to 128 l-bins; the last l-block is cut to the bins left,
 // rounded up to the 16-column granule of the MMA.
-std::vector<TileInfo> build_tc_tiles(int M) {
+// Tensor-core tiles of the upper triangle k <= l.  A last column block that
+// holds only the column l = M - 1 (M = T/2 + 1 with T a multiple of 256) is
+// left to k3_column (*last_col = true): a 16-column tile per k block would
+// cost a full operand load per group for one column.
+std::vector<TileInfo> build_tc_tiles(int M, bool* last_col) {
   std::vector<TileInfo> t;
+  *last_col = false;
   for (int k0 = 0; k0 < M; k0 += kTcTileM)
     for (int l0 = 0; l0 < M; l0 += kTcTileN) {
       const int n = std::min(kTcTileN, (M - l0 + 15) & ~15);
+      if (M - l0 == 1 && M > 1) {
+        *last_col = true;
+        continue;
+      }
       if (k0 <= l0 + n - 1) t.push_back(TileInfo{k0, l0, 8, n});
     }
   return t;
@@ -348,6 +358,11 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
                                            p->d_tiles4tc, p->n_tiles4tc, p->precision,
                                            p->d_acc4 + (long long)i * p->rows4 * p->M, plane,
                                            p->nsm, p->d_counter, p->d_status, p->stream));
+          if (p->precision != SS_PREC_FP32 && p->col4)
+            SS_TRY(p, launch_k3_column(p->d_spec + cb.c[0] * chan_stride, p->Mp, cnt, p->m,
+                                       p->M, pref4a, pref4b,
+                                       p->d_acc4 + (long long)i * p->rows4 * p->M, plane,
+                                       p->stream));
         }
         record(p, 2, p->stream, false);
       }
@@ -771,7 +786,8 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
   std::vector<int2> pts3;
   build_tiles(p, t3, t4, pts3);
   std::vector<TileInfo> t4tc;
-  if (channels == 1 && !p->c4.empty() && precision != SS_PREC_FP32) t4tc = build_tc_tiles(p->M);
+  if (channels == 1 && !p->c4.empty() && precision != SS_PREC_FP32)
+    t4tc = build_tc_tiles(p->M, &p->col4);
   p->n_tiles4tc = (int)t4tc.size();
   if (p->c3.empty()) {
     t3.clear();
@@ -1088,7 +1104,9 @@ ss_status ss_query(ss_plan_t p, ss_info* info) {
   info->device_bytes = p->device_bytes;
   info->kernels_per_batch = 1 + (p->n_s2cross > 0 ? 1 : 0) +
                             (int)p->c3.size() * (1 + (p->C == 1 && p->n_pts3 > 0 ? 1 : 0)) +
-                            (p->C > 1 ? (p->c4.empty() ? 0 : 1) : (int)p->c4.size());
+                            (p->C > 1 ? (p->c4.empty() ? 0 : 1)
+                                      : (int)p->c4.size() *
+                                            (1 + (p->precision != SS_PREC_FP32 && p->col4 ? 1 : 0)));
   return SS_OK;
 }
 
