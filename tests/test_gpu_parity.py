@@ -303,6 +303,76 @@ def test_config2_full_size_sampled_points():
     assert np.max(np.abs(S4.imag)) == 0.0
 
 
+def test_config3_four_channels_full_size_sampled_points():
+    # 4 channels x 2^26 samples, T=512 (257 bins), m=20, 6553 groups, every default
+    # cross combination of S2, S3 and S4 in one plan; the oracle evaluates sampled
+    # grid points of a few combinations, among them each spectrum's peak
+    T, m, n, C = 512, 20, 1 << 26, 4
+    M = T // 2 + 1
+    zs = synth.multichannel_shared(C, n, seed=3)
+    mod = P()
+    plan = mod.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4))
+    recs = plan.combos()
+    plan.close()
+    c2 = [tuple(r[1:3]) for r in recs if r[0] == 2]
+    c3 = [tuple(r[1:4]) for r in recs if r[0] == 3]
+    c4 = [tuple(r[1:5]) for r in recs if r[0] == 4]
+    assert (len(c2), len(c3)) == (10, 20) and len(c4) > 0
+    gpu = run_gpu(zs, T, m, channels=C)
+    assert gpu["G"] == n // (T * m)
+    rng = np.random.default_rng(5)
+    g = oracle.window(T)
+    G = n // (T * m)
+    picks3 = [0, len(c3) // 2, len(c3) - 1]
+    picks4 = [0, len(c4) // 2, len(c4) - 1]
+    pts3, pts4 = {}, {}
+    for i in picks3:
+        S = gpu["S3"][i]
+        peak = np.unravel_index(np.argmax(np.abs(S)), S.shape)
+        k = rng.integers(-(M - 1), M, 40)
+        l = rng.integers(0, M, 40)
+        keep = np.abs(k + l) <= M - 1
+        kk = np.concatenate([k[keep], [peak[0] - (M - 1), -(M - 1), M - 1, 0]])
+        ll = np.concatenate([l[keep], [peak[1], M - 1, 0, M - 1]])
+        pts3[i] = (kk, ll)
+    for i in picks4:
+        S = gpu["S4"][i]
+        peak = np.unravel_index(np.argmax(np.abs(S)), S.shape)
+        kk = np.concatenate([rng.integers(-(M - 1), M, 30), [peak[0] - (M - 1), -(M - 1), M - 1]])
+        ll = np.concatenate([rng.integers(0, M, 30), [peak[1], M - 1, 0]])
+        pts4[i] = (kk, ll)
+    v2 = {i: [] for i in range(len(c2))}
+    v3 = {i: [] for i in picks3}
+    v4 = {i: [] for i in picks4}
+    for g0 in range(0, G, 1024):
+        g1 = min(G, g0 + 1024)
+        X = [oracle.dft_plus(oracle.frame_groups(zs[c], T, m)[g0:g1] * g) for c in range(C)]
+        for i, (a, b) in enumerate(c2):
+            v2[i].append(oracle.s2_groups(X[a], X[b], 1.0, g))
+        for i in picks3:
+            a, b, c = c3[i]
+            v3[i].append(oracle.s3_groups(X[a], X[b], X[c], 1.0, g, *pts3[i]))
+        for i in picks4:
+            a, b, c, d = c4[i]
+            v4[i].append(oracle.s4_groups(X[a], X[b], X[c], X[d], 1.0, g, *pts4[i]))
+    for i in range(len(c2)):
+        ref = oracle.mean_and_stderr(np.concatenate(v2[i]))
+        check({"S2": gpu["S2"][i], "S2_err": gpu["S2_err"][i]},
+              {"S2": ref[0], "S2_err": np.stack([ref[1], ref[2]], -1)}, "S2")
+    for key, vals, pts in (("S3", v3, pts3), ("S4", v4, pts4)):
+        for i, v in vals.items():
+            mean, er, ei = oracle.mean_and_stderr(np.concatenate(v))
+            kk, ll = pts[i]
+            S, E = gpu[key][i][kk + M - 1, ll], gpu[key + "_err"][i][kk + M - 1, ll]
+            scale = np.max(np.abs(mean))
+            # the sampled set holds the GPU grid's peak, and the oracle agrees there
+            assert np.max(np.abs(gpu[key][i])) <= (1 + 2 * TOL) * scale
+            assert np.max(np.abs(S - mean)) <= TOL * scale, (key, i)
+            escale = max(np.max(er), np.max(ei))
+            assert np.max(np.abs(E[:, 0] - er)) <= TOL_ERR * escale, (key, i)
+            assert np.max(np.abs(E[:, 1] - ei)) <= TOL_ERR * escale, (key, i)
+
+
 # ---------------------------------------------------------------- S1 and natural estimators
 def check_s1(gpu_s1, gpu_e1, ref):
     assert abs(gpu_s1 - ref["S1"]) <= TOL * abs(ref["S1"])
