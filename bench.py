@@ -50,6 +50,9 @@ WORKLOADS = {
     # host memory in 256 MiB chunks; 1/16 of the 2^34-sample streamed configuration
     "adc16-2^30-T4096-m10": dict(channels=1, n=1 << 30, T=4096, m=10, seed=5, dtype="i16",
                                  chunk=1 << 27, cpu_groups=3),
+    # four channels sharing an AR(1) component (plus white noise, a quadratic term
+    # and a telegraph signal each), every default cross combination of S2/S3/S4
+    "mc4-2^26-T512-m20": dict(channels=4, n=1 << 26, T=512, m=20, seed=3, cpu_groups=2),
 }
 DEFAULT_WORKLOAD = "ar1q-2^28-T1024-m10"
 
@@ -67,6 +70,8 @@ def make_record(w, rank):
     if w.get("dtype") == "i16":
         return synth.adc_telegraph_int16_parallel(w["n"], seed=w["seed"] + rank,
                                                   processes=min(16, os.cpu_count() or 1))
+    if w["channels"] > 1:
+        return synth.multichannel_shared(w["channels"], w["n"], seed=w["seed"] + rank)
 
     return synth.ar1_quadratic(w["n"], seed=w["seed"] + rank, phi=w["phi"])
 
@@ -183,17 +188,30 @@ def run_reference(args, w, rank, world):
     T, m = w["T"], w["m"]
     groups_per_step = args.ref_groups
     n_step = groups_per_step * m * T
+    C = 1 if z.ndim == 1 else z.shape[0]
+    if C > 1:
+        # the plan's default combinations (listed in the C header): every multiset for
+        # S2 and S3, every unordered pair of unordered channel pairs for the S4 cut
+        pairs = [(a, b) for a in range(C) for b in range(a, C)]
+        sel = {2: pairs,
+               3: [(a, b, c) for a in range(C) for b in range(a, C) for c in range(b, C)],
+               4: [pairs[i] + pairs[j] for i in range(len(pairs)) for j in range(i, len(pairs))]}
     ts = []
     for i in range(args.warmup + args.steps):
-        off = (i * n_step) % max(1, (len(z) - n_step))
+        off = (i * n_step) % max(1, (z.shape[-1] - n_step))
         t0 = time.perf_counter()
-        oracle.polyspectra(z[off:off + n_step], T, 1.0, m, group_chunk=groups_per_step)
+        if C == 1:
+            oracle.polyspectra(z[off:off + n_step], T, 1.0, m, group_chunk=groups_per_step)
+        else:
+            oracle.cross_polyspectra(z[:, off:off + n_step], T, 1.0, m, s2_combos=sel[2],
+                                     s3_combos=sel[3], s4_combos=sel[4],
+                                     group_chunk=groups_per_step)
         if i >= args.warmup:
             ts.append(time.perf_counter() - t0)
     sec = float(np.mean(ts))
-    value = n_step / sec
-    sample = (f"{groups_per_step} groups ({n_step} samples) of the same record per step, "
-              f"full S2/S3/S4 grids, numpy float64")
+    value = C * n_step / sec
+    sample = (f"{groups_per_step} groups ({n_step} samples per channel, {C} channels) of the "
+              f"same record per step, full S2/S3/S4 grids, numpy float64")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -208,17 +226,26 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w, z, groups):
-    """Time the FP64 oracle on a prefix of the record; return the line and its spectra."""
+def cpu_baseline(w, z, groups, combos=None):
+    """Time the FP64 oracle on a prefix of the record; return the line and its spectra.
+    Several channels: the oracle's cross-spectra of every combination in `combos`."""
     import oracle
 
     T, m = w["T"], w["m"]
     n = groups * m * T
     t0 = time.perf_counter()
-    ref = oracle.polyspectra(z[:n], T, 1.0, m, group_chunk=groups)
+    if z.ndim == 1:
+        ref = oracle.polyspectra(z[:n], T, 1.0, m, group_chunk=groups)
+    else:
+        sel = {o: [tuple(r[1:1 + o]) for r in combos if r[0] == o] for o in (2, 3, 4)}
+        ref = oracle.cross_polyspectra(z[:, :n], T, 1.0, m, s2_combos=sel[2],
+                                       s3_combos=sel[3], s4_combos=sel[4], group_chunk=groups)
     sec = time.perf_counter() - t0
-    line = {"value": n / sec, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {groups} groups ({n} samples) of the record, full S2/S3/S4 grids, "
+    what = ("full S2/S3/S4 grids" if z.ndim == 1 else
+            f"{z.shape[0]} channels, full grids of every default combination")
+    line = {"value": (1 if z.ndim == 1 else z.shape[0]) * n / sec, "unit": "samples/s",
+            "cores": 1, "kind": "oracle",
+            "sample": f"first {groups} groups ({n} samples per channel) of the record, {what}, "
                       f"numpy float64 on one host core, {sec:.1f} s"}
     return line, ref
 
@@ -230,15 +257,26 @@ def error_vs_oracle(P, w, z, ref, groups, precision):
 
     T, m = w["T"], w["m"]
     n = groups * m * T
-    plan = P.Plan(channels=1, T=T, dt=1.0, m=m, orders=(2, 3, 4), precision=precision,
+    C = 1 if z.ndim == 1 else z.shape[0]
+    plan = P.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4), precision=precision,
                   dtype=w.get("dtype", "f32"))
-    plan.accumulate(torch.from_numpy(np.ascontiguousarray(z[:n])).cuda(), n)
+    combos = plan.combos()
+    plan.accumulate(torch.from_numpy(np.ascontiguousarray(z[..., :n])).cuda(), n)
     out = plan.finalize()
     plan.close()
     errs = {}
     for key in ("S2", "S3", "S4"):
-        a, b = out[key][0].reshape(ref[key].shape), ref[key]
-        errs[key] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        if C == 1:
+            a, b = out[key][0].reshape(ref[key].shape), ref[key]
+            errs[key] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+            continue
+        o = int(key[1])
+        worst = 0.0
+        for i, c in enumerate([tuple(r[1:1 + o]) for r in combos if r[0] == o]):
+            b = ref[(key, c)][0]
+            a = out[key][i].reshape(b.shape)
+            worst = max(worst, float(np.max(np.abs(a - b)) / np.max(np.abs(b))))
+        errs[key] = worst
     errs["groups"] = groups
     errs["precision"] = precision
     return errs
@@ -408,14 +446,16 @@ def main():
     ms_per_step = elapsed / args.steps * 1e3
     G = info.groups if info.groups else (n // (m * T))
     groups = n // (m * T)
-    value = world * n * args.steps / elapsed
+    value = world * C * n * args.steps / elapsed  # input samples of all channels
 
     # ---- roofline of the dominant kernel (live CUDA events on the plan's stream)
     pk = peaks()
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     st = P.ss_stats(plan.handle)
     frames = groups * m
-    names = ["k1_spectra", "k2_bispec", "k3_trispec", "k4_finalize", "h2d"]
+    # several channels: S4 of every combination on CUDA cores in FP32 (k3_trispec_cross)
+    s4_name = "k3_trispec" if C == 1 else "k3_trispec_cross"
+    names = ["k1_spectra", "k2_bispec", s4_name, "k4_finalize", "h2d"]
     dom = int(np.argmax(stage_ms[:3]))
     n_batches = max(1, int(np.ceil(groups / info.groups_per_batch)))
     launches = stage_launches[dom]
@@ -424,11 +464,12 @@ def main():
         achieved = bytes_per_step * args.steps / (stage_ms[0] / 1e3) / 1e9
         peak, unit, bound = float(pk.get("hbm_gbs", 6800.0)), "GB/s", "hbm"
     elif dom == 1:
-        flops_per_step = 14.0 * st.pairs3 * frames
+        flops_per_step = 14.0 * st.pairs3 * frames * info.n_s3
         achieved = flops_per_step * args.steps / (stage_ms[1] / 1e3) / 1e12
         peak, unit, bound = fp32_peak_tflops(nsm, pk), "TFLOP/s", "alu"
     else:
-        flops_per_step = 10.0 * st.pairs4 * frames
+        # several channels: 40 flop per point and frame (five complex multiply-adds)
+        flops_per_step = (10.0 if C == 1 else 40.0) * st.pairs4 * frames * info.n_s4
         achieved = flops_per_step * args.steps / (stage_ms[2] / 1e3) / 1e12
         peak, unit, bound = fp32_peak_tflops(nsm, pk), "TFLOP/s", "alu"
     roofline = {"bound": bound, "kernel": names[dom], "achieved": achieved, "peak": peak,
@@ -444,8 +485,8 @@ def main():
     # (useful products of the Gram contraction, K = m(m+1)/2 per grid point and
     # group, times the hi/lo passes), the FP32 pipe otherwise
     s4_ms = stage_ms[2] / args.steps
-    if args.precision == "fp32":
-        s4_flops = 10.0 * st.pairs4 * frames
+    if args.precision == "fp32" or C > 1:
+        s4_flops = (10.0 if C == 1 else 40.0) * st.pairs4 * frames * info.n_s4
         s4_peak, s4_unit, s4_bound = fp32_peak_tflops(nsm, pk), "TFLOP/s", "alu"
         s4_src = "derived: SMs x 128 FP32 lanes x 2 flop x max SM clock"
     else:
@@ -464,7 +505,7 @@ def main():
     # 16 products per bin, TF32 4 B, BF16 2 B each part) and the ps values (4 B per bin)
     Mp = ((T // 2 + 1) + 15) // 16 * 16
     k1_bytes = groups * (m * T * z.itemsize * C + m * Mp * 8 * C)
-    if args.precision != "fp32":
+    if args.precision != "fp32" and C == 1:
         nkc = (m + 15) // 16 + (m * (m - 1) // 2 + 15) // 16
         k1_bytes += groups * C * Mp * (nkc * 16 * 2 * (4 if args.precision == "tf32x3" else 2) + 4)
     k1_ms = stage_ms[0] / args.steps
@@ -472,17 +513,18 @@ def main():
     roofline_k1 = {"bound": "hbm", "kernel": "k1_spectra", "achieved": k1_ach,
                    "peak": float(pk.get("hbm_gbs", 6800.0)), "unit": "GB/s",
                    "frac": (k1_ach / float(pk.get("hbm_gbs", 6800.0))) if k1_ach else None,
-                   "traffic": traffic_for("k1_spectra_" + args.precision),
+                   "traffic": (traffic_for("k1_spectra_" + args.precision) if C == 1
+                               else None),
                    "traffic_note": "DRAM bytes per launch (ncu); a step is "
                                    f"{n_batches} launches",
                    "algorithmic_bytes_per_step": k1_bytes,
                    "peak_source": "measured (MEASURED_PEAKS.json)", "ms_per_step": k1_ms}
     s4_ach = s4_flops / (s4_ms / 1e3) / 1e12 if s4_ms > 0 else None
-    roofline_s4 = {"bound": s4_bound, "kernel": "k3_trispec", "achieved": s4_ach,
+    roofline_s4 = {"bound": s4_bound, "kernel": s4_name, "achieved": s4_ach,
                    "peak": s4_peak, "unit": s4_unit,
                    "frac": (s4_ach / s4_peak) if s4_ach else None,
-                   "traffic": traffic_for("k3_trispec_tc" if args.precision != "fp32"
-                                          else "k3_trispec"),
+                   "traffic": traffic_for("k3_trispec_tc" if args.precision != "fp32" and C == 1
+                                          else s4_name),
                    "peak_source": s4_src, "ms_per_step": s4_ms}
 
     # ---- end to end through the same calls with host buffers
@@ -514,13 +556,13 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             he = float(t.item())
         d2h = sum(v.nbytes for v in host_out.values()) + sum(v.nbytes for v in host_err.values())
-        e2e = {"value": world * n * args.steps / he, "unit": "samples/s",
+        e2e = {"value": world * C * n * args.steps / he, "unit": "samples/s",
                "h2d_bytes_per_step": int(z.nbytes), "d2h_bytes_per_step": int(d2h)}
 
     cpu, err_fp64 = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cg = w.get("cpu_groups", args.cpu_groups)
-        cpu, ref = cpu_baseline(w, z, cg)
+        cpu, ref = cpu_baseline(w, z, cg, plan.combos())
         err_fp64 = error_vs_oracle(P, w, z, ref, cg, args.precision)
 
     if rank == 0:
@@ -531,7 +573,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "channels": C, "samples_per_rank": n, "T": T,
                        "M": T // 2 + 1, "m": m, "groups": groups, "window": "hann",
-                       "orders": "S2+S3+S4 full grids", "s4_precision": args.precision,
+                       "orders": "S2+S3+S4 full grids",
+                       "s4_precision": args.precision if C == 1 else "fp32 (several channels)",
                        "dtype_in": w.get("dtype", "f32"),
                        "l2": f"record of {z.nbytes / 2**30:.0f} GiB per step is larger than L2; "
                              "no flush"},
