@@ -531,8 +531,13 @@ def main():
     e2e = None
     if not args.no_e2e:
         hz = torch.from_numpy(z).pin_memory()
-        host_out = {k: np.empty(int(np.prod(v)) * 2, np.float64) for k, v in sh.items()}
-        host_err = {k: np.empty_like(v) for k, v in host_out.items()}
+        # the caller's result buffers in page-locked host memory, so that finalize's
+        # device-to-host copies run as DMA
+        def pinned(count):
+            return torch.empty(count, dtype=torch.float64, pin_memory=True).numpy()
+
+        host_out = {k: pinned(int(np.prod(v)) * 2) for k, v in sh.items()}
+        host_err = {k: pinned(int(np.prod(v)) * 2) for k, v in sh.items()}
 
         chunk = w.get("chunk", n)  # samples per ss_accumulate call (a streaming caller)
 

@@ -19,6 +19,8 @@ constexpr size_t kNoallocScratchBytes = SS_NOALLOC_SCRATCH_BYTES;
 // Tile edge of the bispectrum and trispectrum kernels in (k, l) grid points.
 // shared memory of the resident form of K1 (group coefficients + FFT batch)
 constexpr size_t kK1ResidentBytes = 96u << 10;
+// a tighter budget tried first: three resident CTAs per SM
+constexpr size_t kK1ResidentBytes3 = 74u << 10;
 constexpr int kTile = 64;
 // Threads per CTA of the frame/FFT kernel and of the pair kernels.
 constexpr int kThreadsK1 = 256;
