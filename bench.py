@@ -172,6 +172,16 @@ def traffic_for(kernel):
     return rec["bytes_per_launch"] if h == rec["sha256_16"] else None
 
 
+def default_combos(C):
+    """The plan's default channel combinations (listed in the C header): every
+    multiset for S2 and S3, every unordered pair of unordered channel pairs for the
+    S4 cut C4(a_k, b_k*, c_l, d_l*).  {order: [tuple, ...]} in the plan's order."""
+    pairs = [(a, b) for a in range(C) for b in range(a, C)]
+    return {2: pairs,
+            3: [(a, b, c) for a in range(C) for b in range(a, C) for c in range(b, C)],
+            4: [pairs[i] + pairs[j] for i in range(len(pairs)) for j in range(i, len(pairs))]}
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, w, rank, world):
     if rank != 0:
@@ -190,12 +200,7 @@ def run_reference(args, w, rank, world):
     n_step = groups_per_step * m * T
     C = 1 if z.ndim == 1 else z.shape[0]
     if C > 1:
-        # the plan's default combinations (listed in the C header): every multiset for
-        # S2 and S3, every unordered pair of unordered channel pairs for the S4 cut
-        pairs = [(a, b) for a in range(C) for b in range(a, C)]
-        sel = {2: pairs,
-               3: [(a, b, c) for a in range(C) for b in range(a, C) for c in range(b, C)],
-               4: [pairs[i] + pairs[j] for i in range(len(pairs)) for j in range(i, len(pairs))]}
+        sel = default_combos(C)
     ts = []
     for i in range(args.warmup + args.steps):
         off = (i * n_step) % max(1, (z.shape[-1] - n_step))
