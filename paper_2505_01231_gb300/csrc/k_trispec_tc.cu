@@ -357,7 +357,7 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
     for (uint32_t gc = 0;; ++gc) {
       const int p = gc & (kPsSlots - 1);
       const uint32_t b = gc & 1u;
-      // one verdict per warp: the TMEM accesses below are warp-collective
+      // one decision per warp: the TMEM accesses below are warp-collective
       if (!__all_sync(0xffffffffu,
                       mbar_wait_bounded(&psfull[p], (gc / kPsSlots) & 1u, status))) {
         if (lane == 0) atomicExch(&s_fail, 1);
