@@ -221,6 +221,19 @@ ss_status ss_reset(ss_plan_t plan);
 /* ss_query -- sizes and layout of the plan's outputs (see ss_info). */
 ss_status ss_query(ss_plan_t plan, ss_info* info);
 
+/* ss_layout -- the work decomposition that a plan of this shape uses, computed
+   on the host (no device call, no plan).  S3 (Eq. 28 / Eq. 48 domain): the
+   64 x 64 tiles of (k, l) that K2 takes, as (k0, l0) pairs in s3_tiles, and the
+   grid points left to the point kernel (tiles holding at most 8 domain points,
+   one channel only), as (k, l) pairs in s3_points.  S4 on tensor cores (one
+   channel): the tiles of the upper triangle k <= l as (k0, l0, columns) triples
+   in s4_tiles, and last_col = 1 when the column l = M - 1 is left to the
+   CUDA-core column kernel.  Each array receives at most its max entries (it may
+   be NULL); n3, np and n4 receive the full counts.  Errors: SS_EINVAL for
+   channels outside [1, 4], T not a power of two in [8, 4096], or a NULL count. */
+ss_status ss_layout(int channels, int T, int* s3_tiles, int max3, int* n3, int* s3_points,
+                    int maxp, int* np, int* s4_tiles, int max4, int* n4, int* last_col);
+
 /* ss_combos -- copy the plan's combinations, (n_s2 + n_s3 + n_s4) records of
    five ints {order, c0, c1, c2, c3} in output order; out may hold max_records. */
 ss_status ss_combos(ss_plan_t plan, int* out, int max_records);

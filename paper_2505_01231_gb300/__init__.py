@@ -23,7 +23,7 @@ __all__ = [
     "SSError", "ss_info", "ss_stats_t", "lib", "LIB_PATH",
     "ss_plan", "ss_accumulate", "ss_finalize", "ss_reset", "ss_query", "ss_combos",
     "ss_set_timing", "ss_stats", "ss_set_batch", "ss_destroy", "ss_last_error", "ss_version",
-    "ss_s2_noalloc", "Plan",
+    "ss_s2_noalloc", "ss_layout", "Plan",
 ]
 
 SS_OK, SS_EINVAL, SS_ENOMEM, SS_ECUDA, SS_ESTATE, SS_ETIMEOUT, SS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
@@ -66,6 +66,8 @@ _sig = {
     "ss_reset": (ctypes.c_int, [_P]),
     "ss_query": (ctypes.c_int, [_P, ctypes.POINTER(ss_info)]),
     "ss_combos": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "ss_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P,
+                                 ctypes.c_int, _P, _P, ctypes.c_int, _P, _P]),
     "ss_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_stats": (ctypes.c_int, [_P, ctypes.POINTER(ss_stats_t)]),
     "ss_set_batch": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -171,6 +173,26 @@ def ss_combos(plan):
     buf = (ctypes.c_int * (5 * max(n, 1)))()
     _check(lib.ss_combos(plan, buf, n), plan)
     return [tuple(buf[5 * i:5 * i + 5]) for i in range(n)]
+
+
+def ss_layout(channels, T):
+    """The work decomposition of a plan of this shape (host only): S3 tiles
+    [(k0, l0)], S3 points left to the point kernel [(k, l)], tensor-core S4
+    tiles [(k0, l0, columns)] and whether the column l = M - 1 is left to the
+    column kernel."""
+    n3, np_, n4, col = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.ss_layout(channels, T, None, 0, ctypes.byref(n3), None, 0, ctypes.byref(np_),
+                         None, 0, ctypes.byref(n4), ctypes.byref(col)), None)
+    t3 = (ctypes.c_int * (2 * max(n3.value, 1)))()
+    pts = (ctypes.c_int * (2 * max(np_.value, 1)))()
+    t4 = (ctypes.c_int * (3 * max(n4.value, 1)))()
+    _check(lib.ss_layout(channels, T, t3, n3.value, ctypes.byref(n3), pts, np_.value,
+                         ctypes.byref(np_), t4, n4.value, ctypes.byref(n4), ctypes.byref(col)),
+           None)
+    return ([(t3[2 * i], t3[2 * i + 1]) for i in range(n3.value)],
+            [(pts[2 * i], pts[2 * i + 1]) for i in range(np_.value)],
+            [(t4[3 * i], t4[3 * i + 1], t4[3 * i + 2]) for i in range(n4.value)],
+            bool(col.value))
 
 
 def ss_set_timing(plan, enable):

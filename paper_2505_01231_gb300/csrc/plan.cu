@@ -209,12 +209,10 @@ std::vector<TileInfo> build_tc_tiles(int M, bool* last_col) {
 // tiles cut by k + l = M - 1) is left to k2_points.
 constexpr int kIsolatedPoints = 8;
 
-void build_tiles(ss_plan_s* p, std::vector<TileInfo>& t3, std::vector<TileInfo>& t4,
-                 std::vector<int2>& pts3) {
-  const int M = p->M;
-  const bool cross = p->C > 1;
-  p->pairs3 = 0;
-  p->pairs4 = 0;
+void build_tiles(int M, bool cross, std::vector<TileInfo>& t3, std::vector<TileInfo>& t4,
+                 std::vector<int2>& pts3, long long* pairs3, long long* pairs4) {
+  *pairs3 = 0;
+  *pairs4 = 0;
   auto warps = [&](int k0, int l0, auto in_dom) {
     int w = 0;
     for (int wi = 0; wi < kThreadsPair / 32; ++wi) {
@@ -247,8 +245,8 @@ void build_tiles(ss_plan_s* p, std::vector<TileInfo>& t3, std::vector<TileInfo>&
     }
   for (int k = -(M - 1); k < M; ++k)
     for (int l = 0; l < M; ++l) {
-      if (dom3(k, l)) ++p->pairs3;
-      if (dom4(k, l)) ++p->pairs4;
+      if (dom3(k, l)) ++*pairs3;
+      if (dom4(k, l)) ++*pairs4;
     }
 }
 
@@ -784,7 +782,7 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
   p->n_s2cross = (int)s2cross.size();
   std::vector<TileInfo> t3, t4;
   std::vector<int2> pts3;
-  build_tiles(p, t3, t4, pts3);
+  build_tiles(p->M, channels > 1, t3, t4, pts3, &p->pairs3, &p->pairs4);
   std::vector<TileInfo> t4tc;
   if (channels == 1 && !p->c4.empty() && precision != SS_PREC_FP32)
     t4tc = build_tc_tiles(p->M, &p->col4);
@@ -1107,6 +1105,39 @@ ss_status ss_query(ss_plan_t p, ss_info* info) {
                             (p->C > 1 ? (p->c4.empty() ? 0 : 1)
                                       : (int)p->c4.size() *
                                             (1 + (p->precision != SS_PREC_FP32 && p->col4 ? 1 : 0)));
+  return SS_OK;
+}
+
+ss_status ss_layout(int channels, int T, int* s3_tiles, int max3, int* n3, int* s3_points,
+                    int maxp, int* np, int* s4_tiles, int max4, int* n4, int* last_col) {
+  if (channels < 1 || channels > 4 || T < 8 || T > 4096 || !is_pow2(T))
+    return fail(nullptr, SS_EINVAL, "channels in [1, 4] and T a power of two in [8, 4096]");
+  if (!n3 || !np || !n4 || !last_col) return fail(nullptr, SS_EINVAL, "NULL count argument");
+  const int M = T / 2 + 1;
+  std::vector<TileInfo> t3, t4;
+  std::vector<int2> pts3;
+  long long pairs3 = 0, pairs4 = 0;
+  build_tiles(M, channels > 1, t3, t4, pts3, &pairs3, &pairs4);
+  *n3 = (int)t3.size();
+  *np = (int)pts3.size();
+  for (int i = 0; i < *n3 && i < max3 && s3_tiles; ++i) {
+    s3_tiles[2 * i] = t3[i].k0;
+    s3_tiles[2 * i + 1] = t3[i].l0;
+  }
+  for (int i = 0; i < *np && i < maxp && s3_points; ++i) {
+    s3_points[2 * i] = pts3[i].x;
+    s3_points[2 * i + 1] = pts3[i].y;
+  }
+  bool col = false;
+  std::vector<TileInfo> tc;
+  if (channels == 1) tc = build_tc_tiles(M, &col);
+  *n4 = (int)tc.size();
+  *last_col = col ? 1 : 0;
+  for (int i = 0; i < *n4 && i < max4 && s4_tiles; ++i) {
+    s4_tiles[3 * i] = tc[i].k0;
+    s4_tiles[3 * i + 1] = tc[i].l0;
+    s4_tiles[3 * i + 2] = tc[i].ncols;
+  }
   return SS_OK;
 }
 
