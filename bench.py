@@ -16,12 +16,20 @@ window, groups of m = 10 frames; full S2, S3 and S4 grids.  The record (1 GiB)
 is larger than L2, so no extra L2 flush is done between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank processes its own record (weak scaling, no data-path
-collective); rank 0 prints one JSON line.
+Under torchrun the ranks shard one record of N x 2^28 samples into contiguous
+runs of whole groups (2^28 samples' worth per rank: weak scaling); each rank
+runs its plan on its run, and one step ends with the product's merge: the
+plans' exported states summed by one all-reduce, merged into rank 0's plan and
+finalized there.  Rank 0 prints one JSON line.
+
+Peaks: HBM from MEASURED_PEAKS.json; the FP32-FMA and the tcgen05 TF32 / BF16
+peaks are measured at the start of the run by the microbenchmarks of
+libsspeaks.so, with the SM clock sampled meanwhile.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -44,7 +52,8 @@ WORKLOADS = {
     # same shapes as the default at 1/8 of the length (profiling captures)
     "ar1q-2^25-T1024-m10": dict(channels=1, n=1 << 25, T=1024, m=10, seed=1, phi=0.9),
     # 64 independent recordings, lengths log-uniform in [2^20, 2^26], T from
-    # {128, 256, 512, 1024}, AR coefficients uniform in [0.5, 0.98], one CUDA graph
+    # {128, 256, 512, 1024}, AR coefficients uniform in [0.5, 0.98], one CUDA graph;
+    # refused (REFUSED below) until the cause of its launch failure is fixed
     "many64-2^20..2^26-m10": dict(channels=1, many=64, m=10, seed=100),
     # int16 ADC record (low-passed telegraph plus noise) streamed from page-locked
     # host memory in 256 MiB chunks; 1/16 of the 2^34-sample streamed configuration
@@ -55,6 +64,11 @@ WORKLOADS = {
     "mc4-2^26-T512-m20": dict(channels=4, n=1 << 26, T=512, m=20, seed=3, cpu_groups=2),
 }
 DEFAULT_WORKLOAD = "ar1q-2^28-T1024-m10"
+# workloads this build does not run, with the reason
+REFUSED = {
+    "many64-2^20..2^26-m10": "its last run ended in 'unspecified launch failure' at the first "
+                             "graph launch; it stays off until that cause is fixed",
+}
 
 
 def dist_env():
@@ -148,9 +162,38 @@ def peaks():
 
 def fp32_peak_tflops(nsm, pk):
     # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock, at the maximum
-    # SM clock; no FP32 FMA peak is measured, so this is derived from unit counts
+    # SM clock: the fallback when the FMA microbenchmark could not run
     mhz = float(pk.get("sm_max_mhz", 2070.0))
     return nsm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def measure_peaks(gpu_index):
+    """FP32-FMA and tcgen05 TF32 / BF16 (kind::f16) dense peaks of this GPU, measured
+    now by libsspeaks.so (CUDA events, about 0.1 s each), with the SM clock sampled
+    during the runs.  Returns {} if the library is missing."""
+    path = os.path.join(ROOT, "paper_2505_01231_gb300", "libsspeaks.so")
+    if not os.path.exists(path):
+        return {}
+    lib = ctypes.CDLL(path)
+    lib.ssp_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]
+    lib.ssp_mma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]
+    sec, rate = ctypes.c_double(), ctypes.c_double()
+    out = {}
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.2)
+    if lib.ssp_fma_peak(100000, ctypes.byref(sec), ctypes.byref(rate)) == 0:
+        out["fp32_tflops"] = rate.value / 1e12
+    for kind, key in ((0, "tf32_tflops"), (1, "bf16_tflops")):
+        if lib.ssp_mma_peak(kind, 300000, ctypes.byref(sec), ctypes.byref(rate)) == 0:
+            out[key] = rate.value / 1e12
+    out["clocks"] = clocks.stop()
+    out["how"] = ("libsspeaks.so: FP32 FMA, 2048 threads per SM x 16 independent chains; "
+                  "tcgen05.mma 128x256 (K 8 tf32 / 16 bf16) from shared memory into TMEM, one "
+                  "CTA per SM, one issuing thread; CUDA events, the whole device")
+    return out
 
 
 def traffic_for(kernel):
@@ -182,48 +225,90 @@ def default_combos(C):
             4: [pairs[i] + pairs[j] for i in range(len(pairs)) for j in range(i, len(pairs))]}
 
 
+# ------------------------------------------------------------------ CPU oracle
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_job(z, T, m, combos):
+    """One host core: the FP64 oracle on one slice of whole groups (single-threaded
+    numpy), timed inside the worker."""
+    import oracle
+
+    t0 = time.perf_counter()
+    if z.ndim == 1:
+        ref = oracle.polyspectra(z, T, 1.0, m, group_chunk=64)
+    else:
+        ref = oracle.cross_polyspectra(z, T, 1.0, m, s2_combos=combos[2], s3_combos=combos[3],
+                                       s4_combos=combos[4], group_chunk=64)
+    return time.perf_counter() - t0, ref
+
+
+def oracle_on_cores(z, T, m, groups, cores, combos=None, offset_groups=0):
+    """The oracle as it stands on `cores` host cores at once: core i takes the i-th
+    slice of `groups` whole groups (from `offset_groups` on).  Returns (samples/s
+    over all cores, the slowest core's seconds, the first slice's estimate).  The
+    pool is spawned (no fork after CUDA) and single-threaded per worker."""
+    import multiprocessing as mp
+
+    n = groups * m * T
+    C = 1 if z.ndim == 1 else z.shape[0]
+    avail = (z.shape[-1] // (m * T) - offset_groups) // groups
+    cores = max(1, min(cores, avail))
+    jobs = []
+    for i in range(cores):
+        a = (offset_groups + i * groups) * m * T
+        jobs.append((np.ascontiguousarray(z[..., a:a + n]), T, m, combos))
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_job, jobs)
+    slowest = max(r[0] for r in res)
+    return cores * C * n / slowest, slowest, res[0][1], cores
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
-    import oracle
-
     if "many" in w:  # a bounded sample: the first recording's process, T = 512
         import synth
 
-        z = synth.ar1_quadratic(1 << 20, seed=w["seed"] + 1, phi=0.74)
+        z = synth.ar1_quadratic(1 << 22, seed=w["seed"] + 1, phi=0.74)
         w = dict(w, T=512)
     else:
         z = make_record(w, 0)
     T, m = w["T"], w["m"]
-    groups_per_step = args.ref_groups
-    n_step = groups_per_step * m * T
     C = 1 if z.ndim == 1 else z.shape[0]
-    if C > 1:
-        sel = default_combos(C)
-    ts = []
+    combos = default_combos(C) if C > 1 else None
+    cores = host_cores()
+    ts, vals, used = [], [], 1
     for i in range(args.warmup + args.steps):
-        off = (i * n_step) % max(1, (z.shape[-1] - n_step))
-        t0 = time.perf_counter()
-        if C == 1:
-            oracle.polyspectra(z[off:off + n_step], T, 1.0, m, group_chunk=groups_per_step)
-        else:
-            oracle.cross_polyspectra(z[:, off:off + n_step], T, 1.0, m, s2_combos=sel[2],
-                                     s3_combos=sel[3], s4_combos=sel[4],
-                                     group_chunk=groups_per_step)
+        # each step a fresh stretch of the record (wrapping at its end)
+        span = args.ref_groups * max(1, cores)
+        total = z.shape[-1] // (m * T)
+        off = (i * span) % max(1, total - span)
+        value, sec, _, used = oracle_on_cores(z, T, m, args.ref_groups, cores, combos, off)
         if i >= args.warmup:
-            ts.append(time.perf_counter() - t0)
+            ts.append(sec)
+            vals.append(value)
+    value = float(np.mean(vals))
     sec = float(np.mean(ts))
-    value = C * n_step / sec
-    sample = (f"{groups_per_step} groups ({n_step} samples per channel, {C} channels) of the "
-              f"same record per step, full S2/S3/S4 grids, numpy float64")
+    n_step = args.ref_groups * m * T
+    sample = (f"{args.ref_groups} groups ({n_step} samples per channel, {C} channels) per core "
+              f"and step on {used} host cores at once, full S2/S3/S4 grids"
+              + (", every default combination" if C > 1 else "") + ", numpy float64")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "T": T, "m": m, "samples_per_step": n_step},
-        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+        "config": {"workload": args.workload, "T": T, "m": m,
+                   "samples_per_step": n_step * used * C},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": used, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -232,26 +317,21 @@ def run_reference(args, w, rank, world):
 
 
 def cpu_baseline(w, z, groups, combos=None):
-    """Time the FP64 oracle on a prefix of the record; return the line and its spectra.
-    Several channels: the oracle's cross-spectra of every combination in `combos`."""
-    import oracle
-
+    """The FP64 oracle on all host cores, each on its own prefix slice of `groups`
+    groups; returns the baseline line and the estimate of the first slice (the
+    record's first `groups` groups, for the error check)."""
     T, m = w["T"], w["m"]
-    n = groups * m * T
-    t0 = time.perf_counter()
-    if z.ndim == 1:
-        ref = oracle.polyspectra(z[:n], T, 1.0, m, group_chunk=groups)
-    else:
+    sel = None
+    if z.ndim > 1:
         sel = {o: [tuple(r[1:1 + o]) for r in combos if r[0] == o] for o in (2, 3, 4)}
-        ref = oracle.cross_polyspectra(z[:, :n], T, 1.0, m, s2_combos=sel[2],
-                                       s3_combos=sel[3], s4_combos=sel[4], group_chunk=groups)
-    sec = time.perf_counter() - t0
+    value, sec, ref, used = oracle_on_cores(z, T, m, groups, host_cores(), sel)
     what = ("full S2/S3/S4 grids" if z.ndim == 1 else
             f"{z.shape[0]} channels, full grids of every default combination")
-    line = {"value": (1 if z.ndim == 1 else z.shape[0]) * n / sec, "unit": "samples/s",
-            "cores": 1, "kind": "oracle",
-            "sample": f"first {groups} groups ({n} samples per channel) of the record, {what}, "
-                      f"numpy float64 on one host core, {sec:.1f} s"}
+    line = {"value": value, "unit": "samples/s", "cores": used, "kind": "oracle",
+            "sample": f"{groups} groups ({groups * m * T} samples per channel) per core, the "
+                      f"record's first {groups * used} groups, {what}, numpy float64, one "
+                      f"process per host core ({used} of {os.cpu_count()}), slowest core "
+                      f"{sec:.1f} s"}
     return line, ref
 
 
@@ -358,6 +438,26 @@ def run_many(args, w, rank, world):
 
 
 # ------------------------------------------------------------------ our arm
+def timed_steps(P, plan, step, steps, stream):
+    """Device time of `steps` calls of step() with CUDA events on the plan's stream,
+    and the per-stage event sums of the plan (ss_stats, reset by each ss_reset)."""
+    import torch
+
+    stage_ms = np.zeros(5)
+    stage_launches = np.zeros(5)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+        st = P.ss_stats(plan.handle)   # per-stage event times of this step (reset clears)
+        stage_ms += np.array(st.ms[:])
+        stage_launches += np.array(st.launches[:])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / 1e3, stage_ms, stage_launches
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,10 +465,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-groups", type=int, default=24)
-    ap.add_argument("--ref-groups", type=int, default=4)
+    ap.add_argument("--cpu-groups", type=int, default=16,
+                    help="groups per host core of the CPU oracle baseline")
+    ap.add_argument("--ref-groups", type=int, default=4,
+                    help="groups per host core and step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the peak microbenchmarks")
+    ap.add_argument("--fp32-steps", type=int, default=3,
+                    help="steps of the all-FP32 S4 arm (0 = skip)")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3", "bf16"],
                     help="arithmetic of the S4 moment sums")
     args = ap.parse_args()
@@ -379,6 +484,11 @@ def main():
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return
+    if args.workload in REFUSED:
+        if rank == 0:
+            print(f"bench.py: workload {args.workload} is refused: {REFUSED[args.workload]}",
+                  file=sys.stderr)
+        sys.exit(2)
     if "many" in w:
         if rank == 0:
             run_many(args, w, rank, world)
@@ -387,6 +497,7 @@ def main():
     import torch
 
     import paper_2505_01231_gb300 as P
+    from paper_2505_01231_gb300 import shard
 
     torch.cuda.set_device(local)
     dist = None
@@ -395,30 +506,70 @@ def main():
 
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
-    z = make_record(w, rank)
-    n = z.shape[-1]
     T, m, C = w["T"], w["m"], w["channels"]
+    if world > 1:
+        # one record of world x n samples, sharded into contiguous runs of whole
+        # groups; each rank draws its own run (seed + rank) of the synthetic record
+        ranges = shard.group_ranges(world * w["n"], T, m, world)
+        a, b = ranges[rank]
+        z = make_record(dict(w, n=b - a), rank)
+    else:
+        z = make_record(w, 0)
+    n = z.shape[-1]
+    pk = peaks()
+    measured = {}
+    if not args.no_peaks:
+        measured = measure_peaks(local)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = measured.get("fp32_tflops") or fp32_peak_tflops(nsm, pk)
+    fp32_src = ("measured now (FP32 FMA microbenchmark)" if measured.get("fp32_tflops") else
+                "derived: SMs x 128 FP32 lanes x 2 flop x max SM clock")
+
     stream = torch.cuda.current_stream()
     plan = P.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4), stream=stream,
-                  dtype=w.get("dtype", "f32"),
-                  precision=args.precision)
+                  dtype=w.get("dtype", "f32"), precision=args.precision)
     info = P.ss_query(plan.handle)
     dz = torch.from_numpy(z).cuda()
     sh = plan.shapes()
     outs = {k: torch.empty(int(np.prod(v)) * 2, dtype=torch.float64, device="cuda")
             for k, v in sh.items()}
     errs = {k: torch.empty_like(v) for k, v in outs.items()}
+    state = None
+    if world > 1:
+        state = torch.empty(P.ss_state_size(plan.handle), dtype=torch.float64, device="cuda")
 
-    def step_device():
+    def merge_and_finalize(S, E):
+        # the product's sharded path: export, one sum all-reduce of the states,
+        # merge into rank 0's (reset) plan, finalize there
+        P.ss_export_state(plan.handle, state)
+        shard.reduce_state(state)
+        if rank == 0:
+            P.ss_reset(plan.handle)
+            P.ss_merge_state(plan.handle, state)
+            P.ss_finalize(plan.handle, S["S2"], S["S3"], S["S4"], E["S2"], E["S3"], E["S4"])
+
+    def step_device(merge=True):
         P.ss_reset(plan.handle)
         P.ss_accumulate(plan.handle, dz, n)
-        P.ss_finalize(plan.handle, outs["S2"], outs["S3"], outs["S4"], errs["S2"], errs["S3"],
-                      errs["S4"])
+        if world == 1:
+            P.ss_finalize(plan.handle, outs["S2"], outs["S3"], outs["S4"], errs["S2"],
+                          errs["S3"], errs["S4"])
+        elif merge:
+            merge_and_finalize(outs, errs)
+        else:
+            torch.cuda.current_stream().synchronize()
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
     for _ in range(args.warmup):
         step_device()
@@ -429,108 +580,107 @@ def main():
     clocks.start()
     time.sleep(0.3)
     barrier()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    stage_ms = np.zeros(5)
-    stage_launches = np.zeros(5)
-    for _ in range(args.steps):
-        step_device()
-        st = P.ss_stats(plan.handle)   # per-stage event times of this step (reset clears)
-        stage_ms += np.array(st.ms[:])
-        stage_launches += np.array(st.launches[:])
-    t1.record(stream)
+    elapsed, stage_ms, stage_launches = timed_steps(P, plan, step_device, args.steps, stream)
     barrier()
     clock_info = clocks.stop()
-    elapsed = t0.elapsed_time(t1) / 1e3
     P.ss_set_timing(plan.handle, 0)
-    if dist is not None:
-        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed)
     ms_per_step = elapsed / args.steps * 1e3
-    G = info.groups if info.groups else (n // (m * T))
     groups = n // (m * T)
-    value = world * C * n * args.steps / elapsed  # input samples of all channels
+    value = world * C * n * args.steps / elapsed  # input samples of all channels, all ranks
+    merge_info = None
+    if world > 1:
+        barrier()
+        e2, _, _ = timed_steps(P, plan, lambda: step_device(merge=False), args.steps, stream)
+        e2 = max_over_ranks(e2)
+        merge_info = {"ms_per_step_with_merge": ms_per_step,
+                      "ms_per_step_without_merge": e2 / args.steps * 1e3,
+                      "value_without_merge": world * C * n * args.steps / e2,
+                      "state_doubles": int(state.numel()),
+                      "path": "ss_export_state -> shard.reduce_state (one SUM all-reduce) -> "
+                              "ss_merge_state into rank 0's reset plan -> ss_finalize"}
 
-    # ---- roofline of the dominant kernel (live CUDA events on the plan's stream)
-    pk = peaks()
-    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    # ---- per-stage rooflines (live CUDA events on the plan's stream)
     st = P.ss_stats(plan.handle)
     frames = groups * m
-    # several channels: S4 of every combination on CUDA cores in FP32 (k3_trispec_cross)
+    M = T // 2 + 1
+    Mp = (M + 15) // 16 * 16
     s4_name = "k3_trispec" if C == 1 else "k3_trispec_cross"
+    if C == 1 and args.precision != "fp32":
+        s4_name = "k3_trispec_tc"
     names = ["k1_spectra", "k2_bispec", s4_name, "k4_finalize", "h2d"]
-    dom = int(np.argmax(stage_ms[:3]))
     n_batches = max(1, int(np.ceil(groups / info.groups_per_batch)))
-    launches = stage_launches[dom]
-    if dom == 0:
-        bytes_per_step = frames * (4 * T * C + 8 * (T // 2 + 1) * C)
-        achieved = bytes_per_step * args.steps / (stage_ms[0] / 1e3) / 1e9
-        peak, unit, bound = float(pk.get("hbm_gbs", 6800.0)), "GB/s", "hbm"
-    elif dom == 1:
-        flops_per_step = 14.0 * st.pairs3 * frames * info.n_s3
-        achieved = flops_per_step * args.steps / (stage_ms[1] / 1e3) / 1e12
-        peak, unit, bound = fp32_peak_tflops(nsm, pk), "TFLOP/s", "alu"
-    else:
-        # several channels: 40 flop per point and frame (five complex multiply-adds)
-        flops_per_step = (10.0 if C == 1 else 40.0) * st.pairs4 * frames * info.n_s4
-        achieved = flops_per_step * args.steps / (stage_ms[2] / 1e3) / 1e12
-        peak, unit, bound = fp32_peak_tflops(nsm, pk), "TFLOP/s", "alu"
-    roofline = {"bound": bound, "kernel": names[dom], "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak, "traffic": traffic_for(names[dom]),
-                "peak_source": ("measured (MEASURED_PEAKS.json)" if bound == "hbm" else
-                                "derived: SMs x 128 FP32 lanes x 2 flop x max SM clock"),
-                "stage_ms_per_step": {nm: float(stage_ms[i] / args.steps)
-                                      for i, nm in enumerate(names[:4])},
-                "launch_ms": float(stage_ms[dom] / max(1, launches))}
-    gpu_launches = int(args.steps * (n_batches * info.kernels_per_batch + 3))
+    hbm = float(pk.get("hbm_gbs", 6800.0))
 
-    # ---- the S4 stage against its own bound: the tensor pipe in the split modes
-    # (useful products of the Gram contraction, K = m(m+1)/2 per grid point and
-    # group, times the hi/lo passes), the FP32 pipe otherwise
+    # K1 against HBM on the algorithmic bytes of the step (section (d) of the
+    # design): the samples read and the centred spectra written, M bins per frame;
+    # what the kernel moves beyond that (bins padded to Mp, the tensor-core operand
+    # image and its ps values in the split modes) is reported as overhead
+    k1_ms = stage_ms[0] / args.steps
+    k1_bytes = frames * C * (T * z.itemsize + M * 8)
+    k1_over = frames * C * (Mp - M) * 8
+    if args.precision != "fp32" and C == 1:
+        nkc = (m + 15) // 16 + (m * (m - 1) // 2 + 15) // 16
+        k1_over += groups * C * Mp * (nkc * 16 * 2 * (4 if args.precision == "tf32x3" else 2) + 4)
+    k1_ach = k1_bytes / (k1_ms / 1e3) / 1e9 if k1_ms > 0 else None
+    roofline_k1 = {"bound": "hbm", "kernel": "k1_spectra", "achieved": k1_ach, "peak": hbm,
+                   "unit": "GB/s", "frac": (k1_ach / hbm) if k1_ach else None,
+                   "traffic": (traffic_for("k1_spectra_" + args.precision) if C == 1 else None),
+                   "traffic_note": f"DRAM bytes per launch (ncu); a step is {n_batches} launches",
+                   "algorithmic_bytes_per_step": k1_bytes, "overhead_bytes_per_step": k1_over,
+                   "frac_with_overhead": ((k1_bytes + k1_over) / (k1_ms / 1e3) / 1e9 / hbm)
+                   if k1_ms > 0 else None,
+                   "peak_source": "measured (MEASURED_PEAKS.json, copy)", "ms_per_step": k1_ms}
+
+    # K2 against the FP32 pipe: 14 flop per (grid point, frame)
+    k2_ms = stage_ms[1] / args.steps
+    k2_flops = 14.0 * st.pairs3 * frames * info.n_s3
+    k2_ach = k2_flops / (k2_ms / 1e3) / 1e12 if k2_ms > 0 else None
+    roofline_k2 = {"bound": "alu", "kernel": "k2_bispec", "achieved": k2_ach, "peak": fp32_peak,
+                   "unit": "TFLOP/s", "frac": (k2_ach / fp32_peak) if k2_ach else None,
+                   "traffic": traffic_for("k2_bispec"), "peak_source": fp32_src,
+                   "flop_per_step": k2_flops, "ms_per_step": k2_ms}
+
+    # S4: the tensor pipe in the split modes.  The method's work is one pass of the
+    # Gram contraction, m(m+1) flop per grid point (k <= l) and group; the split
+    # modes issue it three times (hi*hi, hi*lo, lo*hi), padded to whole tiles and K
+    # chunks.  The CUDA-core forms: 10 (one channel) or 40 (several) flop per point
+    # and frame against the FP32 pipe.
     s4_ms = stage_ms[2] / args.steps
     if args.precision == "fp32" or C > 1:
         s4_flops = (10.0 if C == 1 else 40.0) * st.pairs4 * frames * info.n_s4
-        s4_peak, s4_unit, s4_bound = fp32_peak_tflops(nsm, pk), "TFLOP/s", "alu"
-        s4_src = "derived: SMs x 128 FP32 lanes x 2 flop x max SM clock"
+        s4_peak, s4_bound, s4_src, passes = fp32_peak, "alu", fp32_src, 1
     else:
         passes = 1 if args.precision == "bf16" else 3
-        s4_flops = float(st.pairs4) * groups * m * (m + 1) * passes
-        bf16_peak = float(pk.get("bf16_tflops", 1900.0))
-        if args.precision == "tf32x3":
-            s4_peak = bf16_peak * 1.1 / 2.25
+        s4_flops = float(st.pairs4) * groups * m * (m + 1)
+        key = "tf32_tflops" if args.precision == "tf32x3" else "bf16_tflops"
+        if measured.get(key):
+            s4_peak, s4_src = measured[key], f"measured now (tcgen05 {key[:4]} microbenchmark)"
+        elif args.precision == "tf32x3":
+            s4_peak = float(pk.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
             s4_src = "measured bf16 x nominal tf32/bf16 dense ratio (1.1/2.25 PFLOP/s)"
         else:
-            s4_peak, s4_src = bf16_peak, "measured (MEASURED_PEAKS.json, bf16 burst)"
-        s4_unit, s4_bound = "TFLOP/s", "tensor"
-    # ---- K1 against HBM: algorithmic bytes = samples in (4 B), centred spectra out
-    # (8 B per bin and frame, bins padded to a multiple of 16) and, in the split
-    # modes, the operand image (hi and lo of ceil(m/16) + ceil(m(m-1)/2 / 16) chunks of
-    # 16 products per bin, TF32 4 B, BF16 2 B each part) and the ps values (4 B per bin)
-    Mp = ((T // 2 + 1) + 15) // 16 * 16
-    k1_bytes = groups * (m * T * z.itemsize * C + m * Mp * 8 * C)
-    if args.precision != "fp32" and C == 1:
-        nkc = (m + 15) // 16 + (m * (m - 1) // 2 + 15) // 16
-        k1_bytes += groups * C * Mp * (nkc * 16 * 2 * (4 if args.precision == "tf32x3" else 2) + 4)
-    k1_ms = stage_ms[0] / args.steps
-    k1_ach = k1_bytes / (k1_ms / 1e3) / 1e9 if k1_ms > 0 else None
-    roofline_k1 = {"bound": "hbm", "kernel": "k1_spectra", "achieved": k1_ach,
-                   "peak": float(pk.get("hbm_gbs", 6800.0)), "unit": "GB/s",
-                   "frac": (k1_ach / float(pk.get("hbm_gbs", 6800.0))) if k1_ach else None,
-                   "traffic": (traffic_for("k1_spectra_" + args.precision) if C == 1
-                               else None),
-                   "traffic_note": "DRAM bytes per launch (ncu); a step is "
-                                   f"{n_batches} launches",
-                   "algorithmic_bytes_per_step": k1_bytes,
-                   "peak_source": "measured (MEASURED_PEAKS.json)", "ms_per_step": k1_ms}
+            s4_peak, s4_src = float(pk.get("bf16_tflops", 1900.0)), "MEASURED_PEAKS.json bf16"
+        s4_bound = "tensor"
     s4_ach = s4_flops / (s4_ms / 1e3) / 1e12 if s4_ms > 0 else None
-    roofline_s4 = {"bound": s4_bound, "kernel": s4_name, "achieved": s4_ach,
-                   "peak": s4_peak, "unit": s4_unit,
-                   "frac": (s4_ach / s4_peak) if s4_ach else None,
-                   "traffic": traffic_for("k3_trispec_tc" if args.precision != "fp32" and C == 1
-                                          else s4_name),
-                   "peak_source": s4_src, "ms_per_step": s4_ms}
+    roofline_s4 = {"bound": s4_bound, "kernel": s4_name, "achieved": s4_ach, "peak": s4_peak,
+                   "unit": "TFLOP/s", "frac": (s4_ach / s4_peak) if s4_ach else None,
+                   "traffic": traffic_for(s4_name), "peak_source": s4_src,
+                   "flop_per_step": s4_flops, "ms_per_step": s4_ms}
+    if s4_bound == "tensor" and s4_ach:
+        roofline_s4["passes"] = passes
+        roofline_s4["issued_frac"] = s4_ach * passes / s4_peak
+        roofline_s4["note"] = ("frac: the method's one-pass products per second; issued_frac: "
+                               "the split mode's passes, before tile and K-chunk padding")
+
+    # the dominant kernel of the step carries the contract's roofline
+    stage_rl = [roofline_k1, roofline_k2, roofline_s4]
+    dom = int(np.argmax(stage_ms[:3]))
+    roofline = dict(stage_rl[dom])
+    roofline["stage_ms_per_step"] = {nm: float(stage_ms[i] / args.steps)
+                                     for i, nm in enumerate(names[:4])}
+    roofline["launch_ms"] = float(stage_ms[dom] / max(1, stage_launches[dom]))
+    gpu_launches = int(args.steps * (n_batches * info.kernels_per_batch + 3))
 
     # ---- end to end through the same calls with host buffers
     e2e = None
@@ -550,8 +700,11 @@ def main():
             P.ss_reset(plan.handle)
             for a in range(0, n, chunk):
                 P.ss_accumulate(plan.handle, hz[..., a:a + chunk], min(chunk, n - a))
-            P.ss_finalize(plan.handle, host_out["S2"], host_out["S3"], host_out["S4"],
-                          host_err["S2"], host_err["S3"], host_err["S4"])
+            if world == 1:
+                P.ss_finalize(plan.handle, host_out["S2"], host_out["S3"], host_out["S4"],
+                              host_err["S2"], host_err["S3"], host_err["S4"])
+            else:
+                merge_and_finalize(host_out, host_err)
 
         for _ in range(2):
             step_host()
@@ -560,20 +713,38 @@ def main():
         for _ in range(args.steps):
             step_host()
         barrier()
-        he = time.perf_counter() - h0
-        if dist is not None:
-            t = torch.tensor([he], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            he = float(t.item())
+        he = max_over_ranks(time.perf_counter() - h0)
         d2h = sum(v.nbytes for v in host_out.values()) + sum(v.nbytes for v in host_err.values())
         e2e = {"value": world * C * n * args.steps / he, "unit": "samples/s",
-               "h2d_bytes_per_step": int(z.nbytes), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(z.nbytes) * world,
+               "d2h_bytes_per_step": int(d2h)}
 
-    cpu, err_fp64 = None, None
+    cpu, err_fp64, ref, cg = None, None, None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cg = w.get("cpu_groups", args.cpu_groups)
         cpu, ref = cpu_baseline(w, z, cg, plan.combos())
         err_fp64 = error_vs_oracle(P, w, z, ref, cg, args.precision)
+
+    # ---- the all-FP32 CUDA-core form of the same step (S4 on CUDA cores), for the
+    # mixed-precision speed-up at the accuracy each reaches
+    fp32_arm = None
+    if world == 1 and args.precision != "fp32" and C == 1 and args.fp32_steps > 0:
+        plan.close()
+        plan = P.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4), stream=stream,
+                      dtype=w.get("dtype", "f32"), precision="fp32")
+        step_device()
+        torch.cuda.synchronize()
+        P.ss_reset(plan.handle)
+        P.ss_set_timing(plan.handle, 1)
+        e32, ms32, _ = timed_steps(P, plan, step_device, args.fp32_steps, stream)
+        fp32_arm = {"value": C * n * args.fp32_steps / e32, "unit": "samples/s",
+                    "ms_per_step": e32 / args.fp32_steps * 1e3,
+                    "s4_ms_per_step": float(ms32[2] / args.fp32_steps),
+                    "steps": args.fp32_steps}
+        fp32_arm["speedup_of_mixed"] = value / fp32_arm["value"]
+        fp32_arm["s4_speedup_of_mixed"] = fp32_arm["s4_ms_per_step"] / s4_ms if s4_ms else None
+        if ref is not None:
+            fp32_arm["err_vs_fp64"] = error_vs_oracle(P, w, z, ref, cg, "fp32")
 
     if rank == 0:
         line = {
@@ -582,15 +753,18 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "channels": C, "samples_per_rank": n, "T": T,
-                       "M": T // 2 + 1, "m": m, "groups": groups, "window": "hann",
+                       "M": M, "m": m, "groups": groups, "window": "hann",
                        "orders": "S2+S3+S4 full grids",
                        "s4_precision": args.precision if C == 1 else "fp32 (several channels)",
                        "dtype_in": w.get("dtype", "f32"),
+                       "parallelism": (f"dp{world}: one record sharded in whole groups, states "
+                                       "merged by one all-reduce" if world > 1 else "1 GPU"),
                        "l2": f"record of {z.nbytes / 2**30:.0f} GiB per step is larger than L2; "
                              "no flush"},
             "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
-            "roofline_s4": roofline_s4, "roofline_k1": roofline_k1, "err_vs_fp64": err_fp64,
-            "cpu_baseline": cpu, "clocks": clock_info,
+            "roofline_k1": roofline_k1, "roofline_k2": roofline_k2, "roofline_s4": roofline_s4,
+            "peaks_measured": measured or None, "err_vs_fp64": err_fp64, "fp32_arm": fp32_arm,
+            "merge": merge_info, "cpu_baseline": cpu, "clocks": clock_info,
         }
         print(json.dumps(line), flush=True)
     plan.close()

@@ -215,6 +215,22 @@ ss_status ss_set_estimator(ss_plan_t plan, int estimator);
  */
 ss_status ss_set_interlace(ss_plan_t plan, int on);
 
+/*
+ * ss_inject_timeout -- fault-injection hook for testing the timeout path (no
+ *   counterpart in the paper).  Every kernel that waits for its own staged data
+ *   (TMA copies, tensor-core products) bounds each wait by 2 s of %globaltimer;
+ *   a wait that runs out records SS_ETIMEOUT in the plan's device status word,
+ *   and its CTA waits (with the full limit) for the copies it has issued, frees
+ *   its tensor memory and returns, so the device stays usable.  The next
+ *   ss_finalize, ss_finalize_s1 or ss_export_state then returns SS_ETIMEOUT and
+ *   the plan is unusable (SS_ESTATE) from then on.  With on = 1, every
+ *   bispectrum launch of the plan (orders with SS_ORDER3) makes one such wait
+ *   run out: at the first step of its first work item, after that step's copies
+ *   are issued, one thread waits 1 ms on a barrier that nothing completes.  On
+ *   = 0 turns it off.  Nothing faults, traps or hangs.
+ */
+ss_status ss_inject_timeout(ss_plan_t plan, int on);
+
 /* ss_reset -- zero the accumulators, the carry-over and the statistics. */
 ss_status ss_reset(ss_plan_t plan);
 
@@ -337,12 +353,12 @@ const char* ss_version(void);
  * and latency-critical loops that must neither wait for an allocation
  * (cudaMalloc can synchronise the device) nor handle its failure.
  *
- * It computes the same S2 as a one-channel plan with SS_ORDER2 fed the whole
- * record in one ss_accumulate call (Sec. 3, Eq. 23; Sec. 4.1, Eq. 32; error
- * bars Sec. 4.2, Eq. 35-36), with every intermediate (window and twiddle tables,
- * centred spectra, float64 sums) kept in one static device array of
+ * It computes the same S2, with the same error bars, as a one-channel plan with
+ * SS_ORDER2 fed the whole record in one ss_accumulate call, with every
+ * intermediate (window and twiddle tables, built on the device; centred
+ * spectra; float64 sums) kept in one static device array of
  * SS_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the library holds
- * until the process exits.
+ * until the process exits.  The call enqueues kernels and memsets only.
  *   d_signal   device pointer to n_samples float32 samples.
  *   T, dt, m, window, win_param   as for ss_plan (m >= 2).
  *   d_S2       device output, [M] complex128 as interleaved (re, im) doubles.
@@ -352,7 +368,9 @@ const char* ss_version(void);
  * Limit: the centred spectra of all groups must fit the scratch array,
  * floor(n_samples / (m T)) * m * (M rounded up to a multiple of 4) * 8 bytes
  * <= SS_NOALLOC_SCRATCH_BYTES - 128 KiB; longer inputs return SS_EINVAL.
- * Fewer than two groups return SS_ESTATE.  ss_noalloc_last_error() describes
+ * Fewer than two groups return SS_ESTATE.  d_signal, d_S2 and d_S2_err must be
+ * device (or managed) memory: any other pointer returns SS_EINVAL before
+ * anything is enqueued.  ss_noalloc_last_error() describes
  * the last failure of the calling thread.
  * The first call on a device looks up the device address of the static array
  * (cudaGetSymbolAddress, with that device current); make that first call before

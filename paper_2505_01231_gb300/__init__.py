@@ -81,6 +81,7 @@ _sig = {
     "ss_finalize_s1": (ctypes.c_int, [_P, _P, _P]),
     "ss_set_estimator": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_set_interlace": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ss_inject_timeout": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_export_state": (ctypes.c_int, [_P, _P]),
     "ss_merge_state": (ctypes.c_int, [_P, _P]),
     "ss_plan_many": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_double,
@@ -155,6 +156,10 @@ def ss_set_estimator(plan, estimator):
 
 def ss_set_interlace(plan, on):
     _check(lib.ss_set_interlace(plan, int(on)), plan)
+
+
+def ss_inject_timeout(plan, on):
+    _check(lib.ss_inject_timeout(plan, int(bool(on))), plan)
 
 
 def ss_reset(plan):

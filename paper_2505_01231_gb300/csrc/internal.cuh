@@ -22,6 +22,11 @@ constexpr size_t kK1ResidentBytes = 96u << 10;
 // a tighter budget tried first: three resident CTAs per SM
 constexpr size_t kK1ResidentBytes3 = 74u << 10;
 constexpr int kTile = 64;
+// Largest frame length and channel count a plan takes (the kernels' fixed
+// dynamic shared-memory limits are sized for them).
+constexpr int kMaxT = 4096, kMaxChannels = 4;
+// Largest frames per staged chunk of the pair kernels.
+constexpr int kMaxFC = 16;
 // Threads per CTA of the frame/FFT kernel and of the pair kernels.
 constexpr int kThreadsK1 = 256;
 constexpr int kThreadsPair = 256;
@@ -98,7 +103,8 @@ cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G,
 // a device int the launcher zeroes on the stream.  acc points at the
 // combination's first accumulator plane; `plane` is the distance in doubles
 // between the four planes (sum Re, sum Im, sumsq Re, sumsq Im).  `status` is
-// the plan's device status word (a bounded wait that gives up writes to it).
+// the plan's device status word (a bounded wait that gives up writes to it);
+// inject_timeout != 0 makes K2 run one wait out on purpose (timeout test).
 // The tensor maps view the centred spectra as [rows][Mp/16][16] float2 with
 // 128-byte swizzling; tm64 has boxes of 4 blocks (64 bins), tm128 of 8.
 cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
@@ -106,7 +112,7 @@ cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
                              int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
                              const TileInfo* tiles, int n_tiles, int cross, float pref3,
                              double* acc, long long plane, int rows, int nsm, int* counter,
-                             int* status, cudaStream_t stream);
+                             int* status, int inject_timeout, cudaStream_t stream);
 
 cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, int FC, int M,
                               const TileInfo* tiles, int n_tiles, float pref4a, float pref4b,
@@ -134,12 +140,19 @@ cudaError_t launch_k3_trispec_cross(const float2* spec, long long chan_stride, i
                                     long long plane, int nsm, bool natural, cudaStream_t stream);
 int k3tc_stage_chunks(int precision);
 
-// Groups per work item: about 16 items per CTA, whole groups, at least one.
+// Most groups whose per-group estimates a kernel adds up in float32 before the
+// run goes to the float64 accumulators (bounds the float32 rounding of the sums
+// over groups of Sec. 4.2 whatever the record length).
+constexpr int kMaxFp32Groups = 64;
+
+// Groups per work item: about 16 items per CTA, whole groups, at least one, at
+// most kMaxFp32Groups (the pair kernels sum an item's groups in float32).
 inline int work_group_chunk(int G, int n_tiles, int n_cta) {
   const long long units = (long long)G * n_tiles;
   const long long target = 16ll * n_cta;
   long long gc = (units + target - 1) / target;
   if (gc < 1) gc = 1;
+  if (gc > kMaxFp32Groups) gc = kMaxFp32Groups;
   if (gc > G) gc = G;
   return (int)gc;
 }

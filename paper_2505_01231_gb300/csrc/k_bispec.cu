@@ -103,9 +103,10 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
           const float2* __restrict__ sc, int rowA, int rowB, int rowC, int G, int m, int FC_rt,
           int M, int Mp, const TileInfo* __restrict__ tiles, WorkQueue wq, int cross,
           float pref3, double* __restrict__ acc, long long plane, int koff,
-          int* __restrict__ status) {
+          int* __restrict__ status, int inject_timeout) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
   __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ __align__(8) uint64_t never;  // completed by nothing (timeout test)
   __shared__ int s_item;
   __shared__ uint32_t tmem_slot;
   unsigned char* sbase = align1024<unsigned char>(smem_raw);
@@ -129,6 +130,7 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+    mbar_init(&never, 1);
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -214,6 +216,11 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
         }
         __syncthreads();
       }
+      // timeout test (inject_timeout): the CTA that takes the first item waits, at
+      // its first step, on a barrier that nothing completes; the wait runs out and
+      // the CTA stops as after any failed wait (the copies already issued drain)
+      if (inject_timeout && item == 0 && i == 0 && tid == 0)
+        ok = mbar_wait_bounded(&never, 0u, status, kInjectedWaitNs) && ok;
       if (active) {
         auto frame = [&](int j, uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1) {
           const unsigned char* pa = sA + (j & ~1) * 512;
@@ -281,10 +288,13 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
           tmem_st16(tsum + 48, t);
         }
       }
-      // every thread is done with stage s; a failed wait anywhere stops the CTA
+      // every thread is done with stage s; a failed wait anywhere stops the CTA.
+      // Before it gives up, the copies issued so far (steps i .. i + kStages - 1,
+      // the one whose wait ran out included) must have landed: those drain waits
+      // keep the full limit, so no copy is in flight when the CTA exits.
       if (__syncthreads_or(!ok)) {
-        if (use_tma)  // drain copies still in flight before giving up
-          for (int q = i + 1; q < nsteps && q < i + kStages; ++q)
+        if (use_tma)
+          for (int q = i; q < nsteps && q < i + kStages; ++q)
             mbar_wait_bounded(&full[(qbase + q) % kStages], ((qbase + q) / kStages) & 1u, status);
         failed = true;
         break;
@@ -406,10 +416,15 @@ cudaError_t launch_k2_t(const CUtensorMap& tm64, const CUtensorMap& tm128, const
                         const float2* spec_b, const float2* spec_c, int rowA, int rowB, int rowC,
                         int G, int m, int FC, int M, int Mp, const TileInfo* tiles, int n_tiles,
                         int cross, float pref3, double* acc, long long plane, int rows, int nsm,
-                        int* counter, int* status, cudaStream_t stream) {
+                        int* counter, int* status, int inject_timeout,
+                        cudaStream_t stream) {
   const size_t smem = k2_smem_bytes(FC);
+  // one fixed limit per instantiation (the function attribute is shared by all
+  // launches): the chunk size of the instantiation, or the largest one
+  const size_t limit = k2_smem_bytes(kFC > 0 ? kFC : kMaxFC);
+  if (FC < 1 || FC > kMaxFC || smem > limit) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k2_bispec<kFC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
   if (e != cudaSuccess) return e;
   // the whole unified L1 as shared memory, so that two CTAs fit per SM
   e = cudaFuncSetAttribute(k2_bispec<kFC>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -430,7 +445,7 @@ cudaError_t launch_k2_t(const CUtensorMap& tm64, const CUtensorMap& tm128, const
   k2_bispec<kFC><<<n_cta, kThreadsPair, smem, stream>>>(tm64, tm128, spec_a, spec_b, spec_c,
                                                         rowA, rowB, rowC, G, m, FC, M, Mp, tiles,
                                                         wq, cross, pref3, acc, plane, koff,
-                                                        status);
+                                                        status, inject_timeout);
   return cudaGetLastError();
 }
 
@@ -441,10 +456,10 @@ cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
                              int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
                              const TileInfo* tiles, int n_tiles, int cross, float pref3,
                              double* acc, long long plane, int rows, int nsm, int* counter,
-                             int* status, cudaStream_t stream) {
+                             int* status, int inject_timeout, cudaStream_t stream) {
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
 #define K2_ARGS tm64, tm128, spec_a, spec_b, spec_c, rowA, rowB, rowC, G, m, FC, M, Mp, tiles, \
-                n_tiles, cross, pref3, acc, plane, rows, nsm, counter, status, stream
+                n_tiles, cross, pref3, acc, plane, rows, nsm, counter, status, inject_timeout, stream
   switch (FC) {
     case 8: return launch_k2_t<8>(K2_ARGS);
     case 10: return launch_k2_t<10>(K2_ARGS);

@@ -238,6 +238,31 @@ __device__ __forceinline__ void centre_bin(int k, bool valid, float2 mean, int m
   }
 }
 
+// Add the CTA's float32 sums of S2 (and S1) over its last groups to the float64
+// accumulators and clear them.  Each thread flushes the bins it centres (bin k
+// belongs to thread k mod blockDim.x; S1 to thread 0), so no barrier is needed.
+__device__ __forceinline__ void flush_k1_sums(int C, int M, const int* __restrict__ s2_auto,
+                                              double* __restrict__ acc2, int n_s2, float* s2sum,
+                                              float* s2sq, float (*s1s)[4], double* acc1) {
+  const long long plane = (long long)n_s2 * M;
+  for (int c = 0; c < C; ++c) {
+    const int ia = s2_auto[c];
+    if (ia < 0) continue;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+      atomicAdd(acc2 + 0 * plane + (long long)ia * M + k, (double)s2sum[c * M + k]);
+      atomicAdd(acc2 + 2 * plane + (long long)ia * M + k, (double)s2sq[c * M + k]);
+      s2sum[c * M + k] = 0.f;
+      s2sq[c * M + k] = 0.f;
+    }
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < C; ++c)
+      for (int q = 0; q < 4; ++q) {
+        if (acc1) atomicAdd(acc1 + q * C + c, (double)s1s[c][q]);
+        s1s[c][q] = 0.f;
+      }
+}
+
 template <int DTYPE, int FMT>
 __global__ void __launch_bounds__(kThreadsK1)
 k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int M, int Mp,
@@ -257,6 +282,7 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
   for (int i = threadIdx.x; i < 2 * C * M; i += blockDim.x) s2sum[i] = 0.f;
   if (threadIdx.x < 16) s1s[threadIdx.x >> 2][threadIdx.x & 3] = 0.f;
 
+  int ngroups = 0;  // groups in the float32 sums since the last flush
   for (int g = blockIdx.x; g < G; g += gridDim.x) {
     for (int c = 0; c < C; ++c) {
       float2* grow = spec + (long long)c * chan_stride + (long long)g * m * Mp;
@@ -317,21 +343,13 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
             ia >= 0 ? s2sum + c * M : nullptr, ia >= 0 ? s2sq + c * M : nullptr, pref2);
       }
     }
-  }
-  __syncthreads();
-  // flush the CTA's float32 partial sums into the float64 accumulators
-  const long long plane = (long long)n_s2 * M;
-  for (int c = 0; c < C; ++c) {
-    const int ia = s2_auto[c];
-    if (ia < 0) continue;
-    for (int k = threadIdx.x; k < M; k += blockDim.x) {
-      atomicAdd(acc2 + 0 * plane + (long long)ia * M + k, (double)s2sum[c * M + k]);
-      atomicAdd(acc2 + 2 * plane + (long long)ia * M + k, (double)s2sq[c * M + k]);
+    if (++ngroups == kMaxFp32Groups) {
+      flush_k1_sums(C, M, s2_auto, acc2, n_s2, s2sum, s2sq, s1s, acc1);
+      ngroups = 0;
     }
   }
-  if (acc1 && threadIdx.x == 0)  // S1 sums: planes of C values
-    for (int c = 0; c < C; ++c)
-      for (int q = 0; q < 4; ++q) atomicAdd(acc1 + q * C + c, (double)s1s[c][q]);
+  // the CTA's remaining float32 partial sums into the float64 accumulators
+  if (ngroups) flush_k1_sums(C, M, s2_auto, acc2, n_s2, s2sum, s2sq, s1s, acc1);
 }
 
 // Stockham pass over a batch of FB frames of N points (frame f at x + f N);
@@ -395,6 +413,7 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
     wins[i] = __ldg(&win[i]);
   }
 
+  int ngroups = 0;  // groups in the float32 sums since the last flush
   for (int g = blockIdx.x; g < G; g += gridDim.x) {
     for (int c = 0; c < C; ++c) {
       float2* grow = spec + (long long)c * chan_stride + (long long)g * m * Mp;
@@ -527,20 +546,12 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
         }
       }
     }
-  }
-  __syncthreads();
-  const long long plane = (long long)n_s2 * M;
-  for (int c = 0; c < C; ++c) {
-    const int ia = s2_auto[c];
-    if (ia < 0) continue;
-    for (int k = threadIdx.x; k < M; k += blockDim.x) {
-      atomicAdd(acc2 + 0 * plane + (long long)ia * M + k, (double)s2sum[c * M + k]);
-      atomicAdd(acc2 + 2 * plane + (long long)ia * M + k, (double)s2sq[c * M + k]);
+    if (++ngroups == kMaxFp32Groups) {
+      flush_k1_sums(C, M, s2_auto, acc2, n_s2, s2sum, s2sq, s1s, acc1);
+      ngroups = 0;
     }
   }
-  if (acc1 && threadIdx.x == 0)  // S1 sums: planes of C values
-    for (int c = 0; c < C; ++c)
-      for (int q = 0; q < 4; ++q) atomicAdd(acc1 + q * C + c, (double)s1s[c][q]);
+  if (ngroups) flush_k1_sums(C, M, s2_auto, acc2, n_s2, s2sum, s2sq, s1s, acc1);
 }
 
 // Cross-channel S2 (Sec. 7, Eq. 47): c2(a_k, b_k*) = 1/(m-1) sum_j da_jk db_jk*
@@ -581,6 +592,27 @@ __global__ void k1_cross_s2(const float2* __restrict__ spec, long long chan_stri
 
 }  // namespace
 
+// Dynamic shared memory of the frame-at-a-time K1 for T samples and C channels,
+// and its largest value (T = kMaxT, C = kMaxChannels).
+constexpr size_t k1_smem(int T, int C) {
+  return (size_t)(T / 2) * 2 * sizeof(float2) + (size_t)(T / 2 + 1) * sizeof(float2) +
+         (size_t)2 * C * (T / 2 + 1) * sizeof(float);
+}
+constexpr size_t kK1MaxSmem = k1_smem(kMaxT, kMaxChannels);
+
+// The dynamic shared-memory limit of a kernel is an attribute of the function,
+// shared by every plan, stream and captured graph that launches it; each
+// kernel therefore gets one fixed limit, the largest amount any of its
+// launches can ask for, so that no launch depends on which launch set it last.
+template <typename Kern>
+cudaError_t set_smem_limit(Kern kern, size_t limit) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)limit);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              cudaSharedmemCarveoutMaxShared);
+}
+
 template <int DTYPE, int FMT>
 cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C, int T, int m,
                         int M, int Mp, const float* win, const float2* tw, float2* spec,
@@ -598,12 +630,9 @@ cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C
   if (fixed + per_frame <= budget) {
     const int FB = (int)std::min<size_t>((size_t)m, (budget - fixed) / per_frame);
     const size_t rsmem = fixed + (size_t)FB * per_frame;
+    if (rsmem > kK1ResidentBytes) return cudaErrorInvalidValue;  // never: budget <= the limit
     auto kern = k1_spectra_res<DTYPE, FMT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rsmem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = set_smem_limit(kern, kK1ResidentBytes);
     if (e != cudaSuccess) return e;
     // one wave: as many CTAs as are resident at once, from the kernel's own
     // registers and shared memory
@@ -628,8 +657,8 @@ cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C
         pref2, oi, acc1);
     return cudaGetLastError();
   }
-  cudaError_t e = cudaFuncSetAttribute(k1_spectra<DTYPE, FMT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > kK1MaxSmem) return cudaErrorInvalidValue;
+  cudaError_t e = set_smem_limit(k1_spectra<DTYPE, FMT>, kK1MaxSmem);
   if (e != cudaSuccess) return e;
   k1_spectra<DTYPE, FMT><<<grid, kThreadsK1, smem, stream>>>(src, sample0, G, C, T, m, M, Mp, win,
                                                              tw, spec, spec_chan_stride, s2_auto,
@@ -643,8 +672,7 @@ cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G,
                               double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream,
                               const OperandImage& oi, double* acc1) {
   if (G <= 0) return cudaSuccess;
-  const size_t smem = (size_t)(T / 2) * 2 * sizeof(float2) + (size_t)M * sizeof(float2) +
-                      (size_t)2 * C * M * sizeof(float);
+  const size_t smem = k1_smem(T, C);
   if (grid > G) grid = G;
   const bool f32 = src.dtype == SS_F32;
   switch (oi.fmt) {
@@ -679,6 +707,8 @@ cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G,
   const int bx = (M + 127) / 128;
   int splits = std::max(1, (4 * nsm) / std::max(1, bx * n_pairs));
   splits = std::min(splits, std::max(1, G / 8));
+  // at most kMaxFp32Groups groups in a thread's float32 sums (grid y <= 65535)
+  splits = std::min(65535, std::max(splits, (G + kMaxFp32Groups - 1) / kMaxFp32Groups));
   const int gpc = (G + splits - 1) / splits;
   splits = (G + gpc - 1) / gpc;
   dim3 grid(bx, splits, n_pairs);

@@ -205,8 +205,10 @@ cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, i
                               cudaStream_t stream) {
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
   const size_t smem = k3_smem_bytes(FC);
+  // one fixed limit for the function (the attribute is shared by all launches)
+  if (FC < 1 || FC > kMaxFC) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k3_trispec, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+                                       (int)k3_smem_bytes(kMaxFC));
   if (e != cudaSuccess) return e;
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_trispec, kThreadsPair, smem);
@@ -270,7 +272,8 @@ cudaError_t launch_k3_column(const float2* spec, int Mp, int G, int m, int M, fl
                              float pref4b, double* acc, long long plane, cudaStream_t stream) {
   if (G <= 0 || M <= 0) return cudaSuccess;
   const int gx = (M + kColThreads - 1) / kColThreads;
-  const int gy = std::min(G, 1024);
+  // at most kMaxFp32Groups groups in a thread's float32 sums (grid y <= 65535)
+  const int gy = std::min(G, std::min(65535, std::max(1024, (G + kMaxFp32Groups - 1) / kMaxFp32Groups)));
   k3_column<<<dim3((unsigned)gx, (unsigned)gy), kColThreads, 0, stream>>>(
       spec, Mp, G, m, M, pref4a, pref4b, acc, plane);
   return cudaGetLastError();

@@ -12,7 +12,6 @@
 #include <cmath>
 #include <mutex>
 #include <string>
-#include <vector>
 
 #include "internal.cuh"
 
@@ -40,6 +39,51 @@ ss_status fail(ss_status st, const std::string& msg) {
   return st;
 }
 
+// Device or managed memory (checked before anything is enqueued, so that a host
+// pointer is refused instead of reaching a kernel).
+bool on_device(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The window scaled by 1/sqrt(sum g^2) and the twiddles e^{+2 pi j a/T}, built on
+// the device in float64 (the same definitions ss_plan evaluates on the host), so
+// that a call enqueues kernels and memsets only.  One block.
+constexpr int kTableThreads = 256;
+
+__global__ void __launch_bounds__(kTableThreads)
+k0_tables(int T, int window, double sigma, float* __restrict__ win, float2* __restrict__ tw) {
+  __shared__ double red[kTableThreads];
+  auto g_at = [&](int i) {
+    if (window == SS_WIN_HANN) return 0.5 - 0.5 * cospi(2.0 * i / T);
+    const double N = T, c = (N - 1.0) / 2.0, d = 4.0 * N * N * sigma * sigma;
+    auto G = [&](double x) { return exp(-(x - c) * (x - c) / d); };
+    return G(i) - G(-0.5) * (G(i + N) + G(i - N)) / (G(-0.5 + N) + G(-0.5 - N));
+  };
+  double s = 0.0;
+  for (int i = threadIdx.x; i < T; i += kTableThreads) {
+    const double g = g_at(i);
+    s += g * g;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = kTableThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  const double scale = 1.0 / sqrt(red[0]);
+  for (int i = threadIdx.x; i < T; i += kTableThreads) {
+    win[i] = (float)(g_at(i) * scale);
+    double sn, cs;
+    sincospi(2.0 * i / T, &sn, &cs);
+    tw[i] = make_float2((float)cs, (float)sn);
+  }
+}
+
 }  // namespace
 
 const char* noalloc_last_error() { return g_err.c_str(); }
@@ -52,6 +96,8 @@ extern "C" ss_status ss_s2_noalloc(const float* d_signal, size_t n_samples, int 
                                    int m, int window, double win_param, double* d_S2,
                                    double* d_S2_err, void* stream) {
   if (!d_signal || !d_S2) return fail(SS_EINVAL, "d_signal and d_S2 must not be NULL");
+  if (!on_device(d_signal) || !on_device(d_S2) || (d_S2_err && !on_device(d_S2_err)))
+    return fail(SS_EINVAL, "d_signal, d_S2 and d_S2_err must be device (or managed) memory");
   if (T < 8 || T > 4096 || (T & (T - 1))) return fail(SS_EINVAL, "T must be a power of two in [8, 4096]");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SS_EINVAL, "dt must be > 0");
   if (m < 2) return fail(SS_EINVAL, "S2 needs m >= 2 (Eq. 32)");
@@ -88,25 +134,6 @@ extern "C" ss_status ss_s2_noalloc(const float* d_signal, size_t n_samples, int 
     base = static_cast<unsigned char*>(g_addr[dev]);
   }
 
-  // window scaled by 1/sqrt(sum g^2) and twiddles, as ss_plan builds them
-  std::vector<double> g(T);
-  for (int i = 0; i < T; ++i) {
-    if (window == SS_WIN_HANN) {
-      g[i] = 0.5 - 0.5 * std::cos(2.0 * M_PI * i / T);
-    } else {
-      const double N = T, sg = win_param, c = (N - 1.0) / 2.0;
-      auto Gf = [&](double x) { return std::exp(-(x - c) * (x - c) / (4.0 * N * N * sg * sg)); };
-      g[i] = Gf(i) - Gf(-0.5) * (Gf(i + N) + Gf(i - N)) / (Gf(-0.5 + N) + Gf(-0.5 - N));
-    }
-  }
-  double sg2 = 0.0;
-  for (int i = 0; i < T; ++i) sg2 += g[i] * g[i];
-  std::vector<float> gw(T);
-  std::vector<float2> tw(T);
-  for (int i = 0; i < T; ++i) {
-    gw[i] = (float)(g[i] / std::sqrt(sg2));
-    tw[i] = make_float2((float)std::cos(2.0 * M_PI * i / T), (float)std::sin(2.0 * M_PI * i / T));
-  }
   float* d_win = reinterpret_cast<float*>(base + kWinOff);
   float2* d_tw = reinterpret_cast<float2*>(base + kTwOff);
   double* d_acc = reinterpret_cast<double*>(base + kAccOff);
@@ -117,8 +144,8 @@ extern "C" ss_status ss_s2_noalloc(const float* d_signal, size_t n_samples, int 
     cudaError_t e_ = (call);                                                           \
     if (e_ != cudaSuccess) return fail(SS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
-  NA_TRY(cudaMemcpyAsync(d_win, gw.data(), T * sizeof(float), cudaMemcpyHostToDevice, s));
-  NA_TRY(cudaMemcpyAsync(d_tw, tw.data(), T * sizeof(float2), cudaMemcpyHostToDevice, s));
+  k0_tables<<<1, kTableThreads, 0, s>>>(T, window, win_param, d_win, d_tw);
+  NA_TRY(cudaGetLastError());
   // the array keeps the previous call's contents: clear the sums and the index
   NA_TRY(cudaMemsetAsync(d_acc, 0, (size_t)4 * M * sizeof(double), s));
   NA_TRY(cudaMemsetAsync(d_auto, 0, sizeof(int), s));

@@ -14,6 +14,8 @@ enum : int { kStatusOk = 0, kStatusWaitTimeout = 1 };
 
 // A wait on an mbarrier gives up after this many nanoseconds of %globaltimer.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+// Limit of the wait that the timeout test injects (on a barrier nothing completes).
+constexpr unsigned long long kInjectedWaitNs = 1000000ull;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -116,12 +118,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity.  Returns false (and records
-// kStatusWaitTimeout) if the phase does not complete within kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
+// kStatusWaitTimeout) if the phase does not complete within limit_ns
+// nanoseconds (kWaitLimitNs; the injected wait of the timeout test is shorter).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_timer_ns();
   while (!mbar_try_wait(bar, parity)) {
-    if (global_timer_ns() - t0 > kWaitLimitNs) {
+    if (global_timer_ns() - t0 > limit_ns) {
       if (status) atomicExch(status, kStatusWaitTimeout);
       return false;
     }

@@ -85,6 +85,7 @@ struct ss_plan_s {
   int n_s2cross = 0;
   TileInfo *d_tiles3 = nullptr, *d_tiles4 = nullptr;
   int* d_status = nullptr;
+  int inject_timeout = 0;          // timeout test: K2 runs one bounded wait out
   int* d_counter = nullptr;        // work-queue counter of the pair kernels
   int FC = 0;                      // frames per staged chunk of the pair kernels
   CUtensorMap tm64{}, tm128{}, tm48{};  // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
@@ -327,7 +328,8 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
                                      p->FC, p->M, p->Mp, p->d_tiles3, p->n_tiles3,
                                      p->C > 1 ? 1 : 0, pref3,
                                      p->d_acc3 + (long long)i * p->rows3 * p->M, plane, p->rows3,
-                                     p->nsm, p->d_counter, p->d_status, p->stream));
+                                     p->nsm, p->d_counter, p->d_status, p->inject_timeout,
+                                     p->stream));
           if (p->C == 1 && p->n_pts3 > 0)
             SS_TRY(p, launch_k2_points(p->d_spec + cb.c[0] * chan_stride, p->Mp, cnt, p->m,
                                        p->d_pts3, p->n_pts3, p->M, pref3,
@@ -1039,6 +1041,12 @@ ss_status ss_set_estimator(ss_plan_t p, int estimator) {
   return SS_OK;
 }
 
+ss_status ss_inject_timeout(ss_plan_t p, int on) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  for (ss_plan_s* q = p; q; q = q->shadow) q->inject_timeout = on ? 1 : 0;
+  return SS_OK;
+}
+
 ss_status ss_set_interlace(ss_plan_t p, int on) {
   if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
   if (p->groups != 0 || p->carry_n != 0)
@@ -1065,6 +1073,7 @@ ss_status ss_set_interlace(ss_plan_t p, int on) {
                              (int)(recs.size() / 5), p->stream, p->Gb_user);
   if (st != SS_OK) return fail(p, st, "interlaced window set: " + g_plan_error);
   s->estimator = p->estimator;
+  s->inject_timeout = p->inject_timeout;
   if (s->oi.img) set_image_scales(s);
   s->skip = p->T / 2;
   p->shadow = s;

@@ -92,10 +92,12 @@ def test_sizes_and_ragged_tails(T, m, G):
     compare_single(gpu, ref)
 
 
-# tensor-core S4: TF32 3-pass split meets the FP32 bar; BF16 3-pass and plain
-# BF16 are held to the bars their operand precision allows (2^-17 and 2^-9 per
-# product before averaging)
-PREC_TOL = {"tf32x3": (TOL, TOL_ERR), "bf16x3": (5e-5, 5e-4), "bf16": (2e-2, 2e-1)}
+# tensor-core S4: the TF32 3-pass split meets the 1e-5 bar of the FP32 path.
+# BF16 3-pass (operands carried to about 2^-17, each product to about 2^-16)
+# and plain BF16 (2^-9) fall outside that bar; they are reported separately and
+# held here to the bars their operand precision allows
+PREC_TOL = {"fp32": (TOL, TOL_ERR), "tf32x3": (TOL, TOL_ERR), "bf16x3": (5e-5, 5e-4),
+            "bf16": (2e-2, 2e-1)}
 
 
 @pytest.mark.parametrize("precision", ["tf32x3", "bf16x3", "bf16"])
@@ -276,31 +278,71 @@ def oracle_points(z, T, m, dt, s3pts, s4pts, chunk=2048):
     return [oracle.mean_and_stderr(np.concatenate(v)) for v in (v2, v3, v4)], G
 
 
-def test_config2_full_size_sampled_points():
-    # 2^28 samples, T=1024 (513 bins), m=10, 26214 groups, launched as bench.py does
+@pytest.fixture(scope="module")
+def config2():
+    # 2^28 samples, T=1024 (513 bins), m=10, 26214 groups: the oracle at sampled
+    # grid points (the low-frequency block holds each spectrum's peak)
     T, m, n = 1024, 10, 1 << 28
     z = synth.ar1_quadratic(n, seed=1)
-    gpu = run_gpu(z, T, m)
     M = T // 2 + 1
     s3, s4 = sampled_points(M, np.random.default_rng(0))
-    (r2, r3, r4), G = oracle_points(z, T, m, 1.0, s3, s4)
-    assert gpu["G"] == G == 26214
+    refs, G = oracle_points(z, T, m, 1.0, s3, s4)
+    return z, s3, s4, refs, G
+
+
+def check_sampled(gpu, refs, s3, s4, G, tol4=TOL, tol4_err=TOL_ERR):
+    r2, r3, r4 = refs
+    assert gpu["G"] == G
     S2 = gpu["S2"][0]
     assert np.max(np.abs(S2 - r2[0])) <= TOL * np.max(np.abs(r2[0]))
-    for (S, E), ref, pts in (((gpu["S3"][0], gpu["S3_err"][0]), r3, s3),
-                             ((gpu["S4"][0], gpu["S4_err"][0]), r4, s4)):
+    for (S, E), ref, pts, tol, tol_err in (
+            ((gpu["S3"][0], gpu["S3_err"][0]), r3, s3, TOL, TOL_ERR),
+            ((gpu["S4"][0], gpu["S4_err"][0]), r4, s4, tol4, tol4_err)):
         k, l = np.array(pts).T
         scale = np.max(np.abs(ref[0]))
-        # the spectrum's peak lies in the sampled low-frequency block
+        # the spectrum's peak lies among the sampled points
         assert np.max(np.abs(S)) <= 1.001 * scale
-        assert np.max(np.abs(S[k, l] - ref[0])) <= TOL * scale
-        assert np.max(np.abs(E[k, l, 0] - ref[1])) <= TOL_ERR * np.max(ref[1])
-        assert np.max(np.abs(E[k, l, 1] - ref[2])) <= TOL_ERR * max(np.max(ref[1]), np.max(ref[2]))
+        err = np.max(np.abs(S[k, l] - ref[0])) / scale
+        assert err <= tol, f"max rel err {err:.3e} > {tol}"
+        assert np.max(np.abs(E[k, l, 0] - ref[1])) <= tol_err * np.max(ref[1])
+        assert np.max(np.abs(E[k, l, 1] - ref[2])) <= tol_err * max(np.max(ref[1]), np.max(ref[2]))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16x3"])
+def test_config2_full_size_sampled_points(config2, precision):
+    # launched as bench.py does (one plan, the whole record in one call: two batches)
+    z, s3, s4, refs, G = config2
+    assert G == 26214
+    gpu = run_gpu(z, 1024, 10, precision=precision)
+    tol, tol_err = PREC_TOL[precision]
+    check_sampled(gpu, refs, s3, s4, G, tol4=tol, tol4_err=tol_err)
     # estimator-level symmetries of the whole grid (Sec. 9)
     S3, S4 = gpu["S3"][0], gpu["S4"][0]
     assert np.array_equal(S3, S3.T)
     assert np.array_equal(S4, S4.T)
     assert np.max(np.abs(S4.imag)) == 0.0
+
+
+@pytest.mark.parametrize("T,n,precision", [(32, 1 << 27, "fp32"), (16, 1 << 26, "tf32x3")])
+def test_short_frames_long_record_sampled_points(T, n, precision):
+    # 419 430 groups of 10 frames of 32 or 16 samples in one batch, so that a CTA
+    # of every kernel meets more groups than its float32 sums may hold (they go
+    # to the float64 sums every 64 groups at most)
+    m = 10
+    z = synth.ar1_quadratic(n, seed=11)
+    M = T // 2 + 1
+    rng = np.random.default_rng(T)
+    kk3, ll3 = oracle.s3_domain(M)
+    half = np.flatnonzero(kk3 <= ll3)
+    low = [(k, l) for k in range(5) for l in range(k, 5)]   # holds each spectrum's peak
+    s3 = [p for p in low if p[0] + p[1] <= M - 1] + \
+        [(int(kk3[i]), int(ll3[i])) for i in rng.choice(half, 12, replace=False)]
+    s4 = low + [(int(a), int(b)) for a, b in rng.integers(0, M, size=(12, 2))]
+    refs, G = oracle_points(z, T, m, 1.0, s3, s4, chunk=16384)
+    assert G == n // (T * m)
+    gpu = run_gpu(z, T, m, precision=precision)
+    tol, tol_err = PREC_TOL[precision]
+    check_sampled(gpu, refs, s3, s4, G, tol4=tol, tol4_err=tol_err)
 
 
 def test_config3_four_channels_full_size_sampled_points():

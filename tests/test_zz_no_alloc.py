@@ -63,3 +63,19 @@ def test_noalloc_rejects_input_beyond_scratch():
         P.ss_s2_noalloc(dz, n, T, 1.0, m, d_S2=s2)
     assert ei.value.status == P.SS_EINVAL
     assert "scratch" in str(ei.value)
+
+
+def test_noalloc_rejects_host_buffers_before_any_launch():
+    import paper_2505_01231_gb300 as P
+    T, m = 256, 4
+    M = T // 2 + 1
+    z = synth.ar1_quadratic(T * m * 10, seed=32)
+    dz = torch.from_numpy(z).cuda()
+    s2 = torch.empty(M * 2, dtype=torch.float64, device="cuda")
+    host_out = np.empty(M * 2)
+    for sig, out, err in ((z, s2, None), (dz, host_out, None), (dz, s2, np.empty(M * 2))):
+        with pytest.raises(P.SSError) as ei:
+            P.ss_s2_noalloc(sig, z.size, T, 1.0, m, d_S2=out, d_S2_err=err)
+        assert ei.value.status == P.SS_EINVAL
+        assert "device" in str(ei.value)
+    torch.cuda.synchronize()   # nothing was enqueued; the device is intact
