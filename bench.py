@@ -472,6 +472,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the peak microbenchmarks")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the plan's default kernel forms")
+    ap.add_argument("--tuning", default=None,
+                    help="apply this tuning text (ss_set_tuning) instead of autotuning")
     ap.add_argument("--fp32-steps", type=int, default=3,
                     help="steps of the all-FP32 S4 arm (0 = skip)")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3", "bf16"],
@@ -529,6 +533,11 @@ def main():
     plan = P.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4), stream=stream,
                   dtype=w.get("dtype", "f32"), precision=args.precision)
     info = P.ss_query(plan.handle)
+    if args.tuning:
+        P.ss_set_tuning(plan.handle, args.tuning)
+    elif not args.no_autotune:
+        P.ss_autotune(plan.handle)   # the fastest kernel forms for these shapes on this GPU
+    tuning = P.ss_get_tuning(plan.handle)
     dz = torch.from_numpy(z).cuda()
     sh = plan.shapes()
     outs = {k: torch.empty(int(np.prod(v)) * 2, dtype=torch.float64, device="cuda")
@@ -732,6 +741,8 @@ def main():
         plan.close()
         plan = P.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4), stream=stream,
                       dtype=w.get("dtype", "f32"), precision="fp32")
+        if not args.no_autotune:
+            P.ss_autotune(plan.handle)
         step_device()
         torch.cuda.synchronize()
         P.ss_reset(plan.handle)
@@ -763,6 +774,7 @@ def main():
                              "no flush"},
             "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
             "roofline_k1": roofline_k1, "roofline_k2": roofline_k2, "roofline_s4": roofline_s4,
+            "tuning": tuning,
             "peaks_measured": measured or None, "err_vs_fp64": err_fp64, "fp32_arm": fp32_arm,
             "merge": merge_info, "cpu_baseline": cpu, "clocks": clock_info,
         }

@@ -231,6 +231,34 @@ ss_status ss_set_interlace(ss_plan_t plan, int on);
  */
 ss_status ss_inject_timeout(ss_plan_t plan, int on);
 
+/*
+ * Autotuning of the kernel forms (Sec. 10 names autotuning in the style of
+ * FFTW as a direction for the library; the paper gives no procedure).  A plan's
+ * results do not depend on these choices, only its speed: K1 keeps a group's
+ * coefficients in shared memory within a 74 KB or a 96 KB budget or transforms
+ * one frame at a time; K2 uses 4 x 4 micro-tiles in CTAs of 256 threads or
+ * 8 x 4 micro-tiles in CTAs of 128 threads with 2 or 3 pipeline stages.
+ *
+ * ss_autotune   -- time every form of K1 and K2 on this plan's shapes on this
+ *                  GPU (a synthetic Gaussian record of about 16 x SMs groups,
+ *                  generated on the device; one untimed pass and the best of
+ *                  three per form) and keep the fastest.  Valid only before the
+ *                  first ss_accumulate (or after ss_reset); SS_ESTATE otherwise.
+ *                  Allocates and frees that record; synchronises the plan's
+ *                  stream; leaves the plan reset.  best_ms (may be NULL)
+ *                  receives the time of the fastest pass.
+ * ss_get_tuning -- the plan's choices as text: "polyspec-tuning 1 <key> |
+ *                  k1=<auto|r96|frames> k2=<44|84s2|84s3>", where the key names
+ *                  T, m, channels, dtype, precision, SM count and GPU.  out holds
+ *                  cap bytes (SS_EINVAL if too small).
+ * ss_set_tuning -- apply such a text (valid at any time between calls).  A text
+ *                  with a key applies only to a plan of the same key (SS_EINVAL
+ *                  otherwise); "k1=... k2=..." alone applies to any plan.
+ */
+ss_status ss_autotune(ss_plan_t plan, double* best_ms);
+ss_status ss_get_tuning(ss_plan_t plan, char* out, size_t cap);
+ss_status ss_set_tuning(ss_plan_t plan, const char* text);
+
 /* ss_reset -- zero the accumulators, the carry-over and the statistics. */
 ss_status ss_reset(ss_plan_t plan);
 

@@ -82,6 +82,9 @@ _sig = {
     "ss_set_estimator": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_set_interlace": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_inject_timeout": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ss_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "ss_get_tuning": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    "ss_set_tuning": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "ss_export_state": (ctypes.c_int, [_P, _P]),
     "ss_merge_state": (ctypes.c_int, [_P, _P]),
     "ss_plan_many": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, ctypes.c_double,
@@ -160,6 +163,24 @@ def ss_set_interlace(plan, on):
 
 def ss_inject_timeout(plan, on):
     _check(lib.ss_inject_timeout(plan, int(bool(on))), plan)
+
+
+def ss_autotune(plan):
+    """Time every kernel form on this plan's shapes and keep the fastest; returns
+    the best pass time in ms."""
+    ms = ctypes.c_double()
+    _check(lib.ss_autotune(plan, ctypes.byref(ms)), plan)
+    return ms.value
+
+
+def ss_get_tuning(plan):
+    buf = ctypes.create_string_buffer(512)
+    _check(lib.ss_get_tuning(plan, buf, 512), plan)
+    return buf.value.decode()
+
+
+def ss_set_tuning(plan, text):
+    _check(lib.ss_set_tuning(plan, text.encode()), plan)
 
 
 def ss_reset(plan):

@@ -87,12 +87,18 @@ struct OperandImage {
   long long chan_ps = 0;      // Gb_max * Mp floats
 };
 
+// K1 forms (the autotuner's choice per plan): groups resident in shared memory
+// within 74 KB (three CTAs per SM) when they fit, else 96 KB (kK1Auto); always
+// the 96 KB budget (kK1Resident96); one frame at a time (kK1Frames).
+enum { kK1Auto = 0, kK1Resident96 = 1, kK1Frames = 2, kK1Modes = 3 };
+
 // Kernel launchers (each returns the launch status; all work on `stream`).
 cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G, int C, int T,
                               int m, int M, int Mp, const float* win, const float2* tw,
                               float2* spec, long long spec_chan_stride, const int* s2_auto,
                               double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream,
-                              const OperandImage& oi = OperandImage(), double* acc1 = nullptr);
+                              const OperandImage& oi = OperandImage(), double* acc1 = nullptr,
+                              int mode = kK1Auto);
 
 cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G, int m, int M,
                                int Mp, const int4* pairs, int n_pairs, float pref2, double* acc2,
@@ -107,12 +113,16 @@ cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G,
 // inject_timeout != 0 makes K2 run one wait out on purpose (timeout test).
 // The tensor maps view the centred spectra as [rows][Mp/16][16] float2 with
 // 128-byte swizzling; tm64 has boxes of 4 blocks (64 bins), tm128 of 8.
+// K2 tilings (the autotuner's choice per plan): 4 x 4 micro-tiles in CTAs of 256
+// threads with 4 stages, or 8 x 4 micro-tiles in CTAs of 128 threads with 2 or
+// 3 stages; all take the same 64 x 64 tiles and give the same sums.
+enum { kK2Tile44 = 0, kK2Tile84Stages2 = 1, kK2Tile84Stages3 = 2, kK2Variants = 3 };
 cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
                              const float2* spec_a, const float2* spec_b, const float2* spec_c,
                              int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
                              const TileInfo* tiles, int n_tiles, int cross, float pref3,
                              double* acc, long long plane, int rows, int nsm, int* counter,
-                             int* status, int inject_timeout, cudaStream_t stream);
+                             int* status, int inject_timeout, int variant, cudaStream_t stream);
 
 cudaError_t launch_k3_trispec(const CUtensorMap& tm64, int row0, int G, int m, int FC, int M,
                               const TileInfo* tiles, int n_tiles, float pref4a, float pref4b,

@@ -332,6 +332,297 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
   }
 }
 
+// ---------------------------------------------------------------------------
+// K2 with 8 x 4 micro-tiles (k2_bispec84).  Same items, staging and sums as
+// k2_bispec, smaller CTAs: 4 warps of 32 x 32 grid points on the 64 x 64 tile,
+// each thread 8 k-bins x 4 l-bins, so a frame costs 12 shared-memory loads of
+// 16 bytes per 32 points (256 FP instructions) instead of 8 per 16 points: the
+// shared-memory wavefronts per FP instruction drop from 0.25 to 0.19.  Lanes map
+// to (tx, ty) = (lane & 3, bit 3 | bit 2 << 1 | bit 4 << 2 of the lane), which
+// with the 128-byte swizzle puts every quarter-warp's loads of a_k, b_l and
+// c_{k+l} on distinct bank groups (checked with a bank model for every load of a
+// frame).  Warps whose 32 x 32 sub-tile lies outside the domain skip the
+// arithmetic.  The per-item sums of the warp's 32 points (four parts) live in
+// 128 TMEM columns of its lane quadrant.  kSt stages of FC frames.
+constexpr int kThreads84 = 128;
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// resident CTAs per SM the register budget is set for: four with two stages
+// (128 registers), three with three (168)
+template <int kSt>
+constexpr int k84_min_ctas() { return kSt == 2 ? 4 : 3; }
+
+template <int kFC, int kSt>
+__global__ void __launch_bounds__(kThreads84, k84_min_ctas<kSt>())
+k2_bispec84(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUtensorMap tm128,
+            const float2* __restrict__ sa, const float2* __restrict__ sb,
+            const float2* __restrict__ sc, int rowA, int rowB, int rowC, int G, int m,
+            int FC_rt, int M, int Mp, const TileInfo* __restrict__ tiles, WorkQueue wq,
+            int cross, float pref3, double* __restrict__ acc, long long plane, int koff,
+            int* __restrict__ status, int inject_timeout) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
+  __shared__ __align__(8) uint64_t full[kSt];
+  __shared__ __align__(8) uint64_t never;  // completed by nothing (timeout test)
+  __shared__ int s_item;
+  __shared__ uint32_t tmem_slot;
+  unsigned char* sbase = align1024<unsigned char>(smem_raw);
+  const int FC = kFC > 0 ? kFC : FC_rt;
+  const uint32_t sbytes = stage_bytes(FC), a64 = arr64_bytes(FC);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int tx = lane & 3;
+  const int ty = ((lane >> 3) & 1) | (((lane >> 2) & 1) << 1) | (((lane >> 4) & 1) << 2);
+  const int wk = warp & 1, wl = warp >> 1;
+  const int kt = 32 * wk + 8 * tx, lt = 32 * wl + 4 * ty;  // micro-tile origin in the tile
+  const int nch = (m + FC - 1) / FC;
+  // byte offsets of the thread's loads in frame row 0 before the swizzle; the
+  // rows of the 64-bin arrays are 512 bytes, so an odd row flips bit 6 of the
+  // swizzled offset (bit 9 of the row start enters the swizzle), the 1024-byte
+  // rows of c_{k+l} do not
+  const uint32_t oa0 = kt * 8, ob0 = lt * 8, oc0 = (kt + lt) * 8;
+
+  if (tid == 0) {
+    for (int s = 0; s < kSt; ++s) mbar_init(&full[s], 1);
+    mbar_init(&never, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // this warp's 128 columns of per-item sums in its lane quadrant: Re, Im, Re^2,
+  // Im^2 of its 32 points (point q = 4 a + b at column 32 part + q)
+  const uint32_t tsum = tmem_slot + ((uint32_t)(32 * warp) << 16);
+  {
+    float z[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) z[i] = 0.f;
+#pragma unroll
+    for (int part = 0; part < 4; ++part) tmem_st32(tsum + 32 * part, z);
+  }
+  uint32_t qbase = 0;  // TMA steps consumed so far (stage = q % kSt)
+  bool failed = false;
+
+  for (int item; !failed && (item = next_item(wq, &s_item)) >= 0;) {
+    const int t = item % wq.n_tiles;
+    const int ga = (item / wq.n_tiles) * wq.group_chunk;
+    const int gb = min(G, ga + wq.group_chunk);
+    const int k0 = tiles[t].k0, l0 = tiles[t].l0;
+    const bool use_tma = k0 >= 0 && k0 + l0 >= 0;
+    const int kw = k0 + 32 * wk, lw = l0 + 32 * wl;
+    bool active = false;
+    for (int a = 0; a < 32 && !active; ++a)
+      for (int b = 0; b < 32 && !active; ++b) active = in_domain3(kw + a, lw + b, M, cross);
+    const int nsteps = (gb - ga) * nch;
+    auto issue = [&](int i) {
+      const int s = (int)((qbase + i) % kSt);
+      const int g = ga + i / nch, j0 = (i % nch) * FC;
+      unsigned char* st = sbase + (size_t)s * sbytes;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)FC * 256u * 8u);
+      tma_load_3d(st, &tm64, 0, k0 >> 4, rowA + g * m + j0, &full[s]);
+      tma_load_3d(st + a64, &tm64, 0, l0 >> 4, rowB + g * m + j0, &full[s]);
+      tma_load_3d(st + 2 * a64, &tm128, 0, (k0 + l0) >> 4, rowC + g * m + j0, &full[s]);
+    };
+
+    float ar[32], ai[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) ar[i] = ai[i] = 0.f;
+
+    if (use_tma && tid == 0) {
+      fence_async_smem();
+      for (int i = 0; i < kSt && i < nsteps; ++i) issue(i);
+    }
+    bool ok = true;
+    for (int i = 0; i < nsteps; ++i) {
+      const int g = ga + i / nch, ch = i % nch, j0 = ch * FC;
+      const int nf = min(FC, m - j0);
+      const int s = use_tma ? (int)((qbase + i) % kSt) : (i & 1);
+      const unsigned char* sA = sbase + (size_t)s * sbytes;
+      const unsigned char* sB = sA + a64;
+      const unsigned char* sC = sA + 2 * a64;
+      if (use_tma) {
+        ok = mbar_wait_bounded(&full[s], ((qbase + i) / kSt) & 1u, status);
+      } else {
+        unsigned char* w = sbase + (size_t)s * sbytes;
+        for (int idx = tid; idx < nf * 4 * kTile; idx += blockDim.x) {
+          const int j = idx / (4 * kTile);
+          const int e = idx - j * 4 * kTile;
+          const long long rr = ((long long)g * m + j0 + j) * Mp;
+          float2 v;
+          uint32_t off;
+          if (e < kTile) {
+            v = coef(sa + rr, k0 + e, M);
+            off = swz128(j * 512 + e * 8);
+          } else if (e < 2 * kTile) {
+            v = coef(sb + rr, l0 + e - kTile, M);
+            off = a64 + swz128(j * 512 + (e - kTile) * 8);
+          } else {
+            v = coef(sc + rr, k0 + l0 + e - 2 * kTile, M);
+            off = 2 * a64 + swz128(j * 1024 + (e - 2 * kTile) * 8);
+          }
+          *reinterpret_cast<float2*>(w + off) = v;
+        }
+        __syncthreads();
+      }
+      if (inject_timeout && item == 0 && i == 0 && tid == 0)
+        ok = mbar_wait_bounded(&never, 0u, status, kInjectedWaitNs) && ok;
+      if (active) {
+        auto frame = [&](int j) {
+          const unsigned char* pa = sA + j * 512;
+          const unsigned char* pb = sB + j * 512;
+          const unsigned char* pc = sC + j * 1024;
+          const uint32_t odd = (uint32_t)(j & 1) << 6;
+          float2 al[4], ac[12];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float4 v = lds128(pb + (swz128(ob0 + 16 * q) ^ odd));
+            al[2 * q] = make_float2(v.x, v.y);
+            al[2 * q + 1] = make_float2(v.z, v.w);
+          }
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            const float4 v = lds128(pc + swz128(oc0 + 16 * q));
+            ac[2 * q] = make_float2(v.x, v.y);
+            ac[2 * q + 1] = make_float2(v.z, v.w);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 v = lds128(pa + (swz128(oa0 + 16 * q) ^ odd));
+            const float2 ak2[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int a = 2 * q + h;
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                // p = a_k b_l ; accumulate p * conj(c_{k+l})
+                const float px = fmaf(ak2[h].x, al[b].x, -ak2[h].y * al[b].y);
+                const float py = fmaf(ak2[h].x, al[b].y, ak2[h].y * al[b].x);
+                const float2 c = ac[a + b];
+                ar[a * 4 + b] = fmaf(px, c.x, fmaf(py, c.y, ar[a * 4 + b]));
+                ai[a * 4 + b] = fmaf(py, c.x, fmaf(-px, c.y, ai[a * 4 + b]));
+              }
+            }
+          }
+        };
+        if (kFC > 0 && nf == kFC) {
+#pragma unroll 1
+          for (int j = 0; j < kFC; ++j) frame(j);
+        } else {
+          for (int j = 0; j < nf; ++j) frame(j);
+        }
+        if (ch == nch - 1) {  // end of a group: c3 into the per-item sums
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {  // halves of 16 points keep the registers low
+            float tt[16];
+            tmem_ld16(tsum + 16 * h, tt);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) tt[q] = fmaf(ar[16 * h + q], pref3, tt[q]);
+            tmem_st16(tsum + 16 * h, tt);
+            tmem_ld16(tsum + 32 + 16 * h, tt);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) tt[q] = fmaf(ai[16 * h + q], pref3, tt[q]);
+            tmem_st16(tsum + 32 + 16 * h, tt);
+            tmem_ld16(tsum + 64 + 16 * h, tt);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const float v = ar[16 * h + q] * pref3;
+              tt[q] = fmaf(v, v, tt[q]);
+            }
+            tmem_st16(tsum + 64 + 16 * h, tt);
+            tmem_ld16(tsum + 96 + 16 * h, tt);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const float v = ai[16 * h + q] * pref3;
+              tt[q] = fmaf(v, v, tt[q]);
+              ar[16 * h + q] = ai[16 * h + q] = 0.f;
+            }
+            tmem_st16(tsum + 96 + 16 * h, tt);
+          }
+        }
+      }
+      // every thread is done with stage s; a failed wait anywhere stops the CTA
+      // after the copies issued so far (steps i .. i + kSt - 1) have landed
+      if (__syncthreads_or(!ok)) {
+        if (use_tma)
+          for (int q = i; q < nsteps && q < i + kSt; ++q)
+            mbar_wait_bounded(&full[(qbase + q) % kSt], ((qbase + q) / kSt) & 1u, status);
+        failed = true;
+        break;
+      }
+      if (use_tma && tid == 0 && i + kSt < nsteps) {
+        fence_async_smem();
+        issue(i + kSt);
+      }
+    }
+    if (failed) break;
+    if (use_tma) qbase += nsteps;
+    if (!active) continue;
+    // end of the item: the sums of each part go to the float64 accumulators
+#pragma unroll 1
+    for (int part = 0; part < 4; ++part) {
+      float tt[32], z[32];
+      tmem_ld32(tsum + 32 * part, tt);
+      double* dst = acc + (long long)part * plane;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int k = k0 + kt + (q >> 2), l = l0 + lt + (q & 3);
+        if (in_domain3(k, l, M, cross))
+          atomicAdd(dst + (long long)(k + koff) * M + l, (double)tt[q]);
+        z[q] = 0.f;
+      }
+      tmem_st32(tsum + 32 * part, z);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot),
+                 "r"(kTmemCols));
+  }
+}
+
 // Isolated grid points of one channel (the tiles that hold a single point of
 // the domain, where the edge k + l = M - 1 passes a tile corner): each thread
 // evaluates c3 at one point for one group at a time, reading the centred
@@ -384,54 +675,63 @@ size_t k2_smem_bytes(int FC) { return (size_t)kStages * stage_bytes(FC) + 1024; 
 
 namespace {
 
-// resident CTAs per SM of one instantiation, from its registers and shared
-// memory (the occupancy query reports one for these kernels although both
-// limits allow two)
-template <int kFC>
-cudaError_t k2_ctas_per_sm(size_t smem, int* occ_out) {
-  int occ = 0;
-  {
-    cudaFuncAttributes fa;
-    int dev = 0, sm_smem = 0, sm_regs = 0, rsv = 0;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k2_bispec<kFC>);
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess)
-      e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e == cudaSuccess)
-      e = cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    if (e == cudaSuccess)
-      e = cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    if (e != cudaSuccess) return e;
-    const int regs = ((fa.numRegs + 7) & ~7) * kThreadsPair;
-    const int by_regs = regs > 0 ? sm_regs / regs : 1;
-    const int by_smem = sm_smem / (int)(smem + fa.sharedSizeBytes + rsv);
-    occ = std::max(1, std::min(2, std::min(by_regs, by_smem)));
-  }
-  *occ_out = occ;
+// resident CTAs per SM of one kernel, from its registers and shared memory (the
+// occupancy query reports fewer for these kernels than both limits allow),
+// capped at max_ctas (the CTAs whose TMEM allocations fit an SM together)
+template <typename Kern>
+cudaError_t ctas_per_sm(Kern kern, int threads, size_t smem, int max_ctas, int* occ_out) {
+  cudaFuncAttributes fa;
+  int dev = 0, sm_smem = 0, sm_regs = 0, rsv = 0;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e != cudaSuccess) return e;
+  const int regs = ((fa.numRegs + 7) & ~7) * threads;
+  const int by_regs = regs > 0 ? sm_regs / regs : 1;
+  const int by_smem = sm_smem / (int)(smem + fa.sharedSizeBytes + rsv);
+  *occ_out = std::max(1, std::min(max_ctas, std::min(by_regs, by_smem)));
   return cudaSuccess;
 }
 
-template <int kFC>
+// shared memory of the 8 x 4 variant with kSt stages of FC frames
+size_t k84_smem_bytes(int FC, int kSt) { return (size_t)kSt * stage_bytes(FC) + 1024; }
+
+// One launcher for both tilings: kVar = 0 is k2_bispec (4 x 4 micro-tiles, 256
+// threads, 4 stages), kVar = 2 or 3 is k2_bispec84 with that many stages.
+template <int kFC, int kVar>
 cudaError_t launch_k2_t(const CUtensorMap& tm64, const CUtensorMap& tm128, const float2* spec_a,
                         const float2* spec_b, const float2* spec_c, int rowA, int rowB, int rowC,
                         int G, int m, int FC, int M, int Mp, const TileInfo* tiles, int n_tiles,
                         int cross, float pref3, double* acc, long long plane, int rows, int nsm,
                         int* counter, int* status, int inject_timeout,
                         cudaStream_t stream) {
-  const size_t smem = k2_smem_bytes(FC);
+  constexpr bool k44 = kVar == 0;
+  constexpr int kSt = k44 ? kStages : kVar;
+  auto kern = [] {
+    if constexpr (k44) return k2_bispec<kFC>;
+    else return k2_bispec84<kFC, kSt>;
+  }();
+  const int threads = k44 ? kThreadsPair : kThreads84;
+  const size_t smem = k84_smem_bytes(FC, kSt);
   // one fixed limit per instantiation (the function attribute is shared by all
   // launches): the chunk size of the instantiation, or the largest one
-  const size_t limit = k2_smem_bytes(kFC > 0 ? kFC : kMaxFC);
+  const size_t limit = k84_smem_bytes(kFC > 0 ? kFC : kMaxFC, kSt);
   if (FC < 1 || FC > kMaxFC || smem > limit) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k2_bispec<kFC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)limit);
   if (e != cudaSuccess) return e;
-  // the whole unified L1 as shared memory, so that two CTAs fit per SM
-  e = cudaFuncSetAttribute(k2_bispec<kFC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  // the whole unified L1 as shared memory, so that several CTAs fit per SM
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
+  // TMEM: 128 columns per CTA of either tiling, 512 per SM
   int occ = 1;
-  e = k2_ctas_per_sm<kFC>(smem, &occ);
+  e = ctas_per_sm(kern, threads, smem, k44 ? 2 : k84_min_ctas<kSt>(), &occ);
   if (e != cudaSuccess) return e;
   const int n_cta = nsm * occ;
   WorkQueue wq;
@@ -442,11 +742,27 @@ cudaError_t launch_k2_t(const CUtensorMap& tm64, const CUtensorMap& tm128, const
   e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
   const int koff = (rows == M) ? 0 : (M - 1);
-  k2_bispec<kFC><<<n_cta, kThreadsPair, smem, stream>>>(tm64, tm128, spec_a, spec_b, spec_c,
-                                                        rowA, rowB, rowC, G, m, FC, M, Mp, tiles,
-                                                        wq, cross, pref3, acc, plane, koff,
-                                                        status, inject_timeout);
+  kern<<<n_cta, threads, smem, stream>>>(tm64, tm128, spec_a, spec_b, spec_c, rowA, rowB, rowC,
+                                         G, m, FC, M, Mp, tiles, wq, cross, pref3, acc, plane,
+                                         koff, status, inject_timeout);
   return cudaGetLastError();
+}
+
+template <int kVar>
+cudaError_t launch_k2_fc(const CUtensorMap& tm64, const CUtensorMap& tm128, const float2* spec_a,
+                         const float2* spec_b, const float2* spec_c, int rowA, int rowB, int rowC,
+                         int G, int m, int FC, int M, int Mp, const TileInfo* tiles, int n_tiles,
+                         int cross, float pref3, double* acc, long long plane, int rows, int nsm,
+                         int* counter, int* status, int inject_timeout, cudaStream_t stream) {
+#define K2_ARGS tm64, tm128, spec_a, spec_b, spec_c, rowA, rowB, rowC, G, m, FC, M, Mp, tiles, \
+                n_tiles, cross, pref3, acc, plane, rows, nsm, counter, status, inject_timeout, stream
+  switch (FC) {
+    case 8: return launch_k2_t<8, kVar>(K2_ARGS);
+    case 10: return launch_k2_t<10, kVar>(K2_ARGS);
+    case 16: return launch_k2_t<16, kVar>(K2_ARGS);
+    default: return launch_k2_t<0, kVar>(K2_ARGS);
+  }
+#undef K2_ARGS
 }
 
 }  // namespace
@@ -456,15 +772,15 @@ cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
                              int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
                              const TileInfo* tiles, int n_tiles, int cross, float pref3,
                              double* acc, long long plane, int rows, int nsm, int* counter,
-                             int* status, int inject_timeout, cudaStream_t stream) {
+                             int* status, int inject_timeout, int variant, cudaStream_t stream) {
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
 #define K2_ARGS tm64, tm128, spec_a, spec_b, spec_c, rowA, rowB, rowC, G, m, FC, M, Mp, tiles, \
                 n_tiles, cross, pref3, acc, plane, rows, nsm, counter, status, inject_timeout, stream
-  switch (FC) {
-    case 8: return launch_k2_t<8>(K2_ARGS);
-    case 10: return launch_k2_t<10>(K2_ARGS);
-    case 16: return launch_k2_t<16>(K2_ARGS);
-    default: return launch_k2_t<0>(K2_ARGS);
+  switch (variant) {
+    case kK2Tile84Stages2: return launch_k2_fc<2>(K2_ARGS);
+    case kK2Tile84Stages3: return launch_k2_fc<3>(K2_ARGS);
+    case kK2Tile44: return launch_k2_fc<0>(K2_ARGS);
+    default: return cudaErrorInvalidValue;
   }
 #undef K2_ARGS
 }

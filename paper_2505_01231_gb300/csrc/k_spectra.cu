@@ -618,15 +618,18 @@ cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C
                         int M, int Mp, const float* win, const float2* tw, float2* spec,
                         long long spec_chan_stride, const int* s2_auto, double* acc2, int n_s2,
                         float pref2, const OperandImage& oi, int grid, size_t smem,
-                        cudaStream_t stream, double* acc1) {
+                        cudaStream_t stream, double* acc1, int mode) {
   // a group whose coefficients fit beside a batch of FFT buffers stays resident
   const size_t fixed = (size_t)m * Mp * sizeof(float2) + (size_t)2 * C * M * sizeof(float) +
                        (size_t)T * (sizeof(float2) + sizeof(float));  // + twiddles and window
   const size_t per_frame = (size_t)T * sizeof(float2);  // two buffers of T/2 points
-  // three CTAs per SM with a smaller batch of frames beat two with a larger one
-  // (T = 1024, m = 10: 2.59 vs 2.69 ms per step); else the 96 KB budget
-  const size_t budget = fixed + per_frame <= kK1ResidentBytes3 ? kK1ResidentBytes3
-                                                                : kK1ResidentBytes;
+  // kK1Auto: three CTAs per SM with a smaller batch of frames beat two with a
+  // larger one (T = 1024, m = 10: 2.59 vs 2.69 ms per step), else the 96 KB
+  // budget; kK1Resident96: the 96 KB budget; kK1Frames: frame at a time
+  const size_t budget = mode == kK1Frames ? 0
+                        : (mode == kK1Auto && fixed + per_frame <= kK1ResidentBytes3)
+                            ? kK1ResidentBytes3
+                            : kK1ResidentBytes;
   if (fixed + per_frame <= budget) {
     const int FB = (int)std::min<size_t>((size_t)m, (budget - fixed) / per_frame);
     const size_t rsmem = fixed + (size_t)FB * per_frame;
@@ -670,34 +673,26 @@ cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G,
                               int m, int M, int Mp, const float* win, const float2* tw,
                               float2* spec, long long spec_chan_stride, const int* s2_auto,
                               double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream,
-                              const OperandImage& oi, double* acc1) {
+                              const OperandImage& oi, double* acc1, int mode) {
   if (G <= 0) return cudaSuccess;
+  if (mode < kK1Auto || mode > kK1Frames) return cudaErrorInvalidValue;
   const size_t smem = k1_smem(T, C);
   if (grid > G) grid = G;
   const bool f32 = src.dtype == SS_F32;
+#define K1_ARGS src, sample0, G, C, T, m, M, Mp, win, tw, spec, spec_chan_stride, s2_auto, acc2, \
+                n_s2, pref2, oi, grid, smem, stream, acc1, mode
   switch (oi.fmt) {
     case kImageGramTF32:
-      return f32 ? launch_k1_t<SS_F32, kImageGramTF32>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
-                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream, acc1)
-                 : launch_k1_t<SS_I16, kImageGramTF32>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
-                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream, acc1);
+      return f32 ? launch_k1_t<SS_F32, kImageGramTF32>(K1_ARGS)
+                 : launch_k1_t<SS_I16, kImageGramTF32>(K1_ARGS);
     case kImageGramBF16:
-      return f32 ? launch_k1_t<SS_F32, kImageGramBF16>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
-                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream, acc1)
-                 : launch_k1_t<SS_I16, kImageGramBF16>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
-                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream, acc1);
+      return f32 ? launch_k1_t<SS_F32, kImageGramBF16>(K1_ARGS)
+                 : launch_k1_t<SS_I16, kImageGramBF16>(K1_ARGS);
     default:
-      return f32 ? launch_k1_t<SS_F32, kImageNone>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
-                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream, acc1)
-                 : launch_k1_t<SS_I16, kImageNone>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
-                                                   spec_chan_stride, s2_auto, acc2, n_s2, pref2,
-                                                   oi, grid, smem, stream, acc1);
+      return f32 ? launch_k1_t<SS_F32, kImageNone>(K1_ARGS)
+                 : launch_k1_t<SS_I16, kImageNone>(K1_ARGS);
   }
+#undef K1_ARGS
 }
 
 cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G, int m, int M,

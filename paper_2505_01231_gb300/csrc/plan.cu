@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include "internal.cuh"
+#include "plan_state.cuh"
 
 using namespace ss;
 
@@ -43,78 +44,10 @@ struct DeviceGuard {
   }
 };
 
-struct EventPair {
-  cudaEvent_t a = nullptr, b = nullptr;
-};
-
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 }  // namespace
 
-struct ss_plan_s {
-  // configuration
-  int C = 1, T = 0, M = 0, Mp = 0, m = 0, window = 0, dtype = 0, precision = 0;
-  unsigned orders = 0;
-  double dt = 1.0, win_param = 0.14;
-  cudaStream_t stream = nullptr;
-  cudaStream_t copy_stream = nullptr;
-  int device = 0, nsm = 1;
-  size_t elem = 4;
-  std::vector<Combo> c2, c3, c4;
-  int rows3 = 0, rows4 = 0;
-  // normalisation (Eq. 23, 28, 31 with the window scaled by 1/sqrt(sum g^2))
-  double sg2 = 0, sg3 = 0, sg4 = 0, norm2 = 0, norm3 = 0, norm4 = 0;
-  // device tables and buffers
-  float* d_win = nullptr;
-  float2* d_tw = nullptr;
-  void* d_carry = nullptr;
-  long long carry_n = 0;
-  float2* d_spec = nullptr;
-  int Gb_max = 0, Gb_user = 0;
-  double *d_acc1 = nullptr, *d_acc2 = nullptr, *d_acc3 = nullptr, *d_acc4 = nullptr;
-  size_t n_acc1 = 0, n_acc2 = 0, n_acc3 = 0, n_acc4 = 0;
-  int estimator = SS_EST_UNBIASED;
-  // interlaced spectra (Sec. 3): a plan fed the same record without its first
-  // T/2 samples, whose groups are pooled with this plan's at finalize
-  ss_plan_s* shadow = nullptr;
-  long long skip = 0;       // samples still to drop (in the shadow plan)
-  double* d_pool = nullptr;  // pooled accumulators of the two plans
-  double sg1 = 0, norm1 = 0;  // sum g and the S1 scale sqrt(sum g^2) / sum g
-  int* d_s2auto = nullptr;
-  int4* d_s2cross = nullptr;
-  int n_s2cross = 0;
-  TileInfo *d_tiles3 = nullptr, *d_tiles4 = nullptr;
-  int* d_status = nullptr;
-  int inject_timeout = 0;          // timeout test: K2 runs one bounded wait out
-  int* d_counter = nullptr;        // work-queue counter of the pair kernels
-  int FC = 0;                      // frames per staged chunk of the pair kernels
-  CUtensorMap tm64{}, tm128{}, tm48{};  // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
-  CUtensorMap tm_img[4]{};               // 4-D views of each channel's Gram operand image
-  TileInfo* d_tiles4tc = nullptr;  // tiles of the tensor-core S4 kernel (one channel)
-  int4* d_c4cross = nullptr;       // (a, b, c, d) of each S4 combination (several channels)
-  int n_tiles4tc = 0;
-  OperandImage oi;                 // K1's second output for the tensor-core S4 kernel
-  int n_tiles3 = 0, n_tiles4 = 0;
-  int2* d_pts3 = nullptr;  // isolated S3 grid points of one channel (k2_points)
-  bool col4 = false;       // the S4 column l = M - 1 is left to k3_column
-  int n_pts3 = 0;
-  long long pairs3 = 0, pairs4 = 0;
-  void* d_stage[2] = {nullptr, nullptr};
-  long long stage_n = 0;
-  cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
-  double* d_out = nullptr;
-  size_t out_doubles = 0;
-  size_t device_bytes = 0;
-  // progress
-  long long groups = 0, samples = 0;
-  // timing
-  bool timing = false;
-  std::vector<EventPair> ev[5];
-  long long launches[5] = {0, 0, 0, 0, 0};
-  // errors
-  bool broken = false;
-  std::string err;
-};
 
 namespace {
 
@@ -309,7 +242,7 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
       SS_TRY(p, launch_k1_spectra(src, g0 * per_group, cnt, p->C, p->T, p->m, p->M, p->Mp,
                                   p->d_win, p->d_tw, p->d_spec, chan_stride, p->d_s2auto,
                                   p->d_acc2, (int)p->c2.size(), pref2, 4 * p->nsm, p->stream,
-                                  p->oi, p->d_acc1));
+                                  p->oi, p->d_acc1, p->k1_mode));
       if (p->n_s2cross > 0)
         SS_TRY(p, launch_k1_cross_s2(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp,
                                      p->d_s2cross, p->n_s2cross, pref2, p->d_acc2,
@@ -329,7 +262,7 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
                                      p->C > 1 ? 1 : 0, pref3,
                                      p->d_acc3 + (long long)i * p->rows3 * p->M, plane, p->rows3,
                                      p->nsm, p->d_counter, p->d_status, p->inject_timeout,
-                                     p->stream));
+                                     p->k2_variant, p->stream));
           if (p->C == 1 && p->n_pts3 > 0)
             SS_TRY(p, launch_k2_points(p->d_spec + cb.c[0] * chan_stride, p->Mp, cnt, p->m,
                                        p->d_pts3, p->n_pts3, p->M, pref3,
@@ -655,6 +588,14 @@ void destroy(ss_plan_s* p) {
 }
 
 }  // namespace
+
+namespace ss {
+ss_status run_device_chunk(ss_plan_s* p, const void* ptr, long long n, long long stride) {
+  return process_device(p, ptr, n, stride);
+}
+ss_status reset_state(ss_plan_s* p) { return zero_state(p); }
+ss_status plan_fail(ss_plan_s* p, ss_status st, const std::string& msg) { return fail(p, st, msg); }
+}  // namespace ss
 
 extern "C" {
 
