@@ -216,6 +216,34 @@ ss_status ss_set_estimator(ss_plan_t plan, int estimator);
 ss_status ss_set_interlace(ss_plan_t plan, int on);
 
 /*
+ * Sequential spectra (Sec. 8, quasi-polyspectra of non-stationary signals):
+ * besides the whole-record estimate, the short-time estimates of the record,
+ * averaged over blocks of consecutive groups.
+ *
+ * ss_set_sequential -- every block_groups consecutive groups (counted from the
+ *     first group after ss_plan or ss_reset, across ss_accumulate calls), the
+ *     plan writes the block's S2, S3 and S4 -- the mean of the block's
+ *     per-group estimates S_g and its standard error over those groups
+ *     (Eq. 35-36 with the block's groups as the parts), i.e. the estimate of
+ *     that stretch of the record -- to block b of out: ss_sequential_info gives
+ *     the doubles per block, laid out as the six outputs of ss_finalize in the
+ *     order S2, S2_err, S3, S3_err, S4, S4_err.  Blocks b >= max_blocks are
+ *     counted but not written.  out is device memory (SS_EINVAL otherwise); it
+ *     may be NULL with max_blocks = 0.  block_groups = 0 turns the blocks off;
+ *     1 is SS_EINVAL (a block needs two groups for its error bar).  Valid only
+ *     before the first ss_accumulate (or after ss_reset); SS_EUNSUPPORTED with
+ *     interlaced window sets.  Groups after the last whole block enter the
+ *     whole-record estimate only.  Stream-ordered: a block is written when the
+ *     plan's stream passes the ss_accumulate call that completed it.
+ * ss_sequential_info -- the doubles of one block, and the blocks completed since
+ *     the last reset (either pointer may be NULL).
+ * A sweep of m (Sec. 8: quasi-polyspectra that change with m reveal
+ * non-stationarity) is a plan per m over the same record.
+ */
+ss_status ss_set_sequential(ss_plan_t plan, int block_groups, double* out, long long max_blocks);
+ss_status ss_sequential_info(ss_plan_t plan, size_t* block_doubles, long long* blocks_done);
+
+/*
  * ss_inject_timeout -- fault-injection hook for testing the timeout path (no
  *   counterpart in the paper).  Every kernel that waits for its own staged data
  *   (TMA copies, tensor-core products) bounds each wait by 2 s of %globaltimer;

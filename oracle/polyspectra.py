@@ -19,6 +19,8 @@ reordering beyond what the cited formula states:
 * first-order spectrum ..... Sec. 4, S1 = N C1(a_0) / (T sum g); App. G
 * interlaced spectra ....... Sec. 3: the same estimate from windows shifted by T/2, pooled with
                               the unshifted one (the groups of both window sets are the parts)
+* sequential spectra ....... Sec. 8 (quasi-polyspectra): the short-time estimates, each from m
+                              windows, averaged over blocks of consecutive groups
 * natural (biased) estimators, for the paper's unbiased-vs-biased comparison
                               (Sec. 4.1, Fig. 6): the cumulants of the m samples'
                               own empirical distribution, from their central moments
@@ -62,6 +64,7 @@ __all__ = [
     "polyspectra",
     "cross_domain_s3",
     "cross_polyspectra",
+    "sequential_spectra",
 ]
 
 
@@ -451,4 +454,38 @@ def cross_polyspectra(zs, T, dt, m, s2_combos=(), s3_combos=(), s4_combos=(),
         else:
             out[key] = (mean.reshape(2 * M - 1, M),
                         np.stack([er, ei], -1).reshape(2 * M - 1, M, 2))
+    return out
+
+
+# --------------------------------------------------------------------------- sequential spectra
+def sequential_spectra(z, T, dt, m, block_groups, window_kind="hann", sigma_t=0.14,
+                       orders=(2, 3, 4), estimator="unbiased"):
+    """Sequential (short-time) spectra of a single channel (Sec. 8).
+
+    Each group of m consecutive frames gives one short-time estimate S_g (the
+    estimate whose average over all groups is the spectrum, and which for a
+    non-stationary signal is a quasi-polyspectrum of that stretch).  The groups
+    are taken ``block_groups`` at a time, consecutively from the first one; block
+    b is the average of the S_g of groups b*B .. (b+1)*B - 1 with the standard
+    error over those groups (Eq. 35-36 with the block's groups as the parts),
+    i.e. exactly the estimate of that stretch of the record.  Groups after the
+    last whole block form no block.  Returns a dict with 'blocks' and, per
+    order, 'S2' [blocks, M], 'S3'/'S4' [blocks, M, M] and the '*_err' arrays
+    with a trailing (err_re, err_im) axis.
+    """
+    if block_groups < 2:
+        raise ValueError("a block needs at least two groups for its error estimate")
+    z = np.asarray(z)
+    span = block_groups * m * T
+    nb = (z.shape[-1] // (m * T)) // block_groups
+    out = {"blocks": nb}
+    parts = [polyspectra(z[b * span:(b + 1) * span], T, dt, m, window_kind, sigma_t, orders,
+                         group_chunk=max(1, block_groups), estimator=estimator)
+             for b in range(nb)]
+    for n in orders:
+        if n < 2:
+            continue
+        key = f"S{n}"
+        out[key] = np.stack([q[key] for q in parts]) if nb else None
+        out[key + "_err"] = np.stack([q[key + "_err"] for q in parts]) if nb else None
     return out

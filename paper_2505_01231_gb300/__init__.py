@@ -82,6 +82,9 @@ _sig = {
     "ss_set_estimator": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_set_interlace": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_inject_timeout": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ss_set_sequential": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_longlong]),
+    "ss_sequential_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t),
+                                          ctypes.POINTER(ctypes.c_longlong)]),
     "ss_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "ss_get_tuning": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "ss_set_tuning": (ctypes.c_int, [_P, ctypes.c_char_p]),
@@ -163,6 +166,17 @@ def ss_set_interlace(plan, on):
 
 def ss_inject_timeout(plan, on):
     _check(lib.ss_inject_timeout(plan, int(bool(on))), plan)
+
+
+def ss_set_sequential(plan, block_groups, out=None, max_blocks=0):
+    _check(lib.ss_set_sequential(plan, int(block_groups), _addr(out), int(max_blocks)), plan)
+
+
+def ss_sequential_info(plan):
+    """(doubles per block, blocks completed since the last reset)"""
+    n, b = ctypes.c_size_t(), ctypes.c_longlong()
+    _check(lib.ss_sequential_info(plan, ctypes.byref(n), ctypes.byref(b)), plan)
+    return n.value, b.value
 
 
 def ss_autotune(plan):
@@ -440,6 +454,38 @@ class Plan:
     def reset(self):
         ss_reset(self.handle)
 
+    def sequential(self, block_groups, max_blocks):
+        """Turn on sequential spectra (ss_set_sequential) into a device buffer this
+        wrapper owns; ``blocks()`` reads them back."""
+        import torch
+
+        n, _ = ss_sequential_info(self.handle)
+        self._seq = torch.zeros(max(1, n * max_blocks), dtype=torch.float64, device="cuda")
+        self._seq_cap = max_blocks
+        ss_set_sequential(self.handle, block_groups, self._seq, max_blocks)
+
+    def blocks(self):
+        """The written blocks as a list of dicts like ``finalize()`` returns."""
+        import torch
+
+        torch.cuda.synchronize()
+        n, done = ss_sequential_info(self.handle)
+        sh = self.shapes()
+        host = self._seq.cpu().numpy()
+        out = []
+        for b in range(min(done, self._seq_cap)):
+            v, d = host[b * n:(b + 1) * n], {}
+            o = 0
+            for key in ("S2", "S3", "S4"):
+                k = int(np.prod(sh[key])) * 2
+                if k:
+                    mean = v[o:o + k].reshape(sh[key] + (2,))
+                    d[key] = mean[..., 0] + 1j * mean[..., 1]
+                    d[key + "_err"] = v[o + k:o + 2 * k].reshape(sh[key] + (2,))
+                o += 2 * k
+            out.append(d)
+        return out
+
     def export_state(self, out=None):
         """The plan's group sums with their header (float64); a new host array unless
         ``out`` (host or device, ss_state_size doubles) is given."""
@@ -468,3 +514,16 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def sweep_m(record, T, ms, **plan_kw):
+    """Quasi-polyspectra of one record for several group sizes m (Sec. 8: spectra
+    that change with m reveal non-stationarity): one plan per m over the same
+    device record; returns {m: finalize() dict}."""
+    out = {}
+    for m in ms:
+        plan = Plan(T=T, m=m, **plan_kw)
+        plan.accumulate(record)
+        out[m] = plan.finalize()
+        plan.close()
+    return out

@@ -180,9 +180,11 @@ cudaError_t launch_k3_column(const float2* spec, int Mp, int G, int m, int M, fl
 size_t k2_smem_bytes(int FC);
 size_t k3_smem_bytes(int FC);
 
+// K4: mean and standard error over G groups of the float64 sums in acc, or, with
+// prev, of the sums acc - prev (the groups since a snapshot: sequential spectra).
 cudaError_t launch_k4_finalize(const double* acc, int n_combos, int rows, int M, int layout,
                                long long G, double norm, double* out, double* err,
-                               cudaStream_t stream);
+                               cudaStream_t stream, const double* prev = nullptr);
 
 // dst[i] += src[i], i < n (device pointers): merges exported group sums.
 cudaError_t launch_add_f64(double* dst, const double* src, long long n, cudaStream_t stream);

@@ -15,9 +15,9 @@
 namespace ss {
 namespace {
 
-__global__ void k4_finalize(const double* __restrict__ acc, int n_combos, int rows, int M,
-                            int layout, long long G, double norm, double* __restrict__ out,
-                            double* __restrict__ err) {
+__global__ void k4_finalize(const double* __restrict__ acc, const double* __restrict__ prev,
+                            int n_combos, int rows, int M, int layout, long long G, double norm,
+                            double* __restrict__ out, double* __restrict__ err) {
   const long long per = (long long)rows * M;
   const long long total = per * n_combos;
   const long long plane = total;
@@ -40,10 +40,15 @@ __global__ void k4_finalize(const double* __restrict__ acc, int n_combos, int ro
     double mr = 0.0, mi = 0.0, er = 0.0, ei = 0.0;
     if (!zero) {
       const long long o = cmb * per + (long long)r * M + l;
-      mr = norm * acc[o] * invG;
-      mi = norm * acc[plane + o] * invG;
-      const double vr = bessel * (norm * norm * acc[2 * plane + o] * invG - mr * mr);
-      const double vi = bessel * (norm * norm * acc[3 * plane + o] * invG - mi * mi);
+      // the sums of the groups since the snapshot `prev` (a block of sequential
+      // spectra), or of all groups
+      double s[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s[q] = acc[q * plane + o] - (prev ? prev[q * plane + o] : 0.0);
+      mr = norm * s[0] * invG;
+      mi = norm * s[1] * invG;
+      const double vr = bessel * (norm * norm * s[2] * invG - mr * mr);
+      const double vi = bessel * (norm * norm * s[3] * invG - mi * mi);
       er = sqrt(fmax(vr, 0.0) * invG);
       ei = sqrt(fmax(vi, 0.0) * invG);
     }
@@ -70,12 +75,12 @@ cudaError_t launch_add_f64(double* dst, const double* src, long long n, cudaStre
 
 cudaError_t launch_k4_finalize(const double* acc, int n_combos, int rows, int M, int layout,
                                long long G, double norm, double* out, double* err,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, const double* prev) {
   const long long total = (long long)n_combos * rows * M;
   if (total == 0) return cudaSuccess;
   int grid = (int)((total + 255) / 256);
   if (grid > 4096) grid = 4096;
-  k4_finalize<<<grid, 256, 0, stream>>>(acc, n_combos, rows, M, layout, G, norm, out, err);
+  k4_finalize<<<grid, 256, 0, stream>>>(acc, prev, n_combos, rows, M, layout, G, norm, out, err);
   return cudaGetLastError();
 }
 

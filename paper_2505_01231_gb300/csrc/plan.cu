@@ -209,6 +209,51 @@ void clear_events(ss_plan_s* p) {
   for (auto& l : p->launches) l = 0;
 }
 
+// Sequential spectra (Sec. 8): the block of seq_B groups that just ended gives
+// its means and standard errors (the sums since the snapshot, over seq_B groups)
+// in the finalize layout at block index seq_blocks of seq_out; then the snapshot
+// moves to the current sums.
+ss_status emit_block(ss_plan_s* p) {
+  const long long b = p->seq_blocks++;
+  const size_t n2 = p->c2.size() * p->M * 2;
+  const size_t n3 = p->c3.size() * p->rows3 * p->M * 2;
+  const size_t n4 = p->c4.size() * p->rows4 * p->M * 2;
+  if (b < p->seq_cap) {
+    double* o2 = p->seq_out + (size_t)b * 2 * (n2 + n3 + n4);
+    double* e2 = o2 + n2;
+    double* o3 = e2 + n2;
+    double* e3 = o3 + n3;
+    double* o4 = e3 + n3;
+    double* e4 = o4 + n4;
+    const double* q2 = p->d_prev;
+    const double* q3 = q2 + p->n_acc2;
+    const double* q4 = q3 + p->n_acc3;
+    if (n2)
+      SS_TRY(p, launch_k4_finalize(p->d_acc2, (int)p->c2.size(), 1, p->M, kLayoutVector,
+                                   p->seq_B, p->norm2, o2, e2, p->stream, q2));
+    if (n3)
+      SS_TRY(p, launch_k4_finalize(p->d_acc3, (int)p->c3.size(), p->rows3, p->M,
+                                   p->C == 1 ? kLayoutS3Single : kLayoutCross, p->seq_B,
+                                   p->norm3, o3, e3, p->stream, q3));
+    if (n4)
+      SS_TRY(p, launch_k4_finalize(p->d_acc4, (int)p->c4.size(), p->rows4, p->M,
+                                   p->C != 1                        ? kLayoutCross
+                                   : p->precision == SS_PREC_FP32 ? kLayoutS4Single
+                                                                   : kLayoutS4Lower,
+                                   p->seq_B, p->norm4, o4, e4, p->stream, q4));
+  }
+  const std::pair<const double*, size_t> parts[3] = {
+      {p->d_acc2, p->n_acc2}, {p->d_acc3, p->n_acc3}, {p->d_acc4, p->n_acc4}};
+  double* q = p->d_prev;
+  for (const auto& pr : parts) {
+    if (pr.second)
+      SS_TRY(p, cudaMemcpyAsync(q, pr.first, pr.second * sizeof(double),
+                                cudaMemcpyDeviceToDevice, p->stream));
+    q += pr.second;
+  }
+  return SS_OK;
+}
+
 // Process n samples per channel that are already on the device (channel c at
 // ptr + c * stride elements).
 ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long stride) {
@@ -236,8 +281,11 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
     const float pref4a =
         (float)(nat ? 1.0 / md : md * (md + 1) / ((md - 1) * (md - 2) * (md - 3)));
     const float pref4b = (float)(nat ? 1.0 / (md * md) : 1.0 / ((md - 2) * (md - 3)));
-    for (long long g0 = 0; g0 < Gn; g0 += gb) {
-      const int cnt = (int)std::min(gb, Gn - g0);
+    for (long long g0 = 0; g0 < Gn;) {
+      long long take = std::min(gb, Gn - g0);
+      // sequential spectra: a batch ends where a block of seq_B groups ends
+      if (p->seq_B > 0) take = std::min(take, p->seq_B - (p->groups + g0) % p->seq_B);
+      const int cnt = (int)take;
       record(p, 0, p->stream, true);
       SS_TRY(p, launch_k1_spectra(src, g0 * per_group, cnt, p->C, p->T, p->m, p->M, p->Mp,
                                   p->d_win, p->d_tw, p->d_spec, chan_stride, p->d_s2auto,
@@ -298,6 +346,11 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
                                        p->stream));
         }
         record(p, 2, p->stream, false);
+      }
+      g0 += take;
+      if (p->seq_B > 0 && (p->groups + g0) % p->seq_B == 0) {
+        ss_status st = emit_block(p);
+        if (st != SS_OK) return st;
       }
     }
   }
@@ -412,6 +465,10 @@ ss_status zero_state(ss_plan_s* p) {
   if (p->d_acc2) SS_TRY(p, cudaMemsetAsync(p->d_acc2, 0, p->n_acc2 * sizeof(double), p->stream));
   if (p->d_acc3) SS_TRY(p, cudaMemsetAsync(p->d_acc3, 0, p->n_acc3 * sizeof(double), p->stream));
   if (p->d_acc4) SS_TRY(p, cudaMemsetAsync(p->d_acc4, 0, p->n_acc4 * sizeof(double), p->stream));
+  if (p->d_prev)
+    SS_TRY(p, cudaMemsetAsync(p->d_prev, 0,
+                              (p->n_acc2 + p->n_acc3 + p->n_acc4) * sizeof(double), p->stream));
+  p->seq_blocks = 0;
   p->carry_n = 0;
   p->groups = 0;
   p->samples = 0;
@@ -584,6 +641,7 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_status);
   cudaFree(p->d_counter);
   cudaFree(p->d_out);
+  cudaFree(p->d_prev);
   delete p;
 }
 
@@ -982,6 +1040,38 @@ ss_status ss_set_estimator(ss_plan_t p, int estimator) {
   return SS_OK;
 }
 
+ss_status ss_set_sequential(ss_plan_t p, int block_groups, double* out, long long max_blocks) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (block_groups < 0 || block_groups == 1)
+    return fail(p, SS_EINVAL, "block_groups must be 0 (off) or at least 2 (Eq. 35 needs two parts)");
+  if (p->groups != 0 || p->carry_n != 0)
+    return fail(p, SS_ESTATE, "ss_set_sequential is valid only before the first ss_accumulate");
+  if (block_groups > 0 && p->shadow)
+    return fail(p, SS_EUNSUPPORTED, "sequential spectra of interlaced window sets");
+  if (block_groups > 0 && max_blocks > 0 && (!out || !is_device_ptr(out)))
+    return fail(p, SS_EINVAL, "out must be device memory");
+  if (max_blocks < 0) return fail(p, SS_EINVAL, "max_blocks must be >= 0");
+  DeviceGuard guard(p->device);
+  p->seq_B = block_groups;
+  p->seq_out = block_groups > 0 ? out : nullptr;
+  p->seq_cap = block_groups > 0 ? max_blocks : 0;
+  p->seq_blocks = 0;
+  const size_t n = p->n_acc2 + p->n_acc3 + p->n_acc4;
+  if (block_groups > 0 && !p->d_prev && n) SS_TRY(p, dev_alloc(p, &p->d_prev, n * sizeof(double)));
+  if (p->d_prev) SS_TRY(p, cudaMemsetAsync(p->d_prev, 0, n * sizeof(double), p->stream));
+  return SS_OK;
+}
+
+ss_status ss_sequential_info(ss_plan_t p, size_t* block_doubles, long long* blocks_done) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  const size_t n2 = p->c2.size() * p->M * 2;
+  const size_t n3 = p->c3.size() * p->rows3 * p->M * 2;
+  const size_t n4 = p->c4.size() * p->rows4 * p->M * 2;
+  if (block_doubles) *block_doubles = 2 * (n2 + n3 + n4);
+  if (blocks_done) *blocks_done = p->seq_blocks;
+  return SS_OK;
+}
+
 ss_status ss_inject_timeout(ss_plan_t p, int on) {
   if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
   for (ss_plan_s* q = p; q; q = q->shadow) q->inject_timeout = on ? 1 : 0;
@@ -1001,6 +1091,8 @@ ss_status ss_set_interlace(ss_plan_t p, int on) {
     return SS_OK;
   }
   if (p->shadow) return SS_OK;
+  if (p->seq_B > 0)
+    return fail(p, SS_EUNSUPPORTED, "interlaced window sets with sequential spectra");
   // the same configuration and combinations, fed from T/2 samples on
   std::vector<int> recs;
   for (const auto* list : {&p->c2, &p->c3, &p->c4})

@@ -51,6 +51,12 @@ struct ss_plan_s {
   int k2_variant = ss::kK2Tile84Stages2;  // K2 tiling (set by the autotuner or ss_set_tuning)
   int k1_mode = ss::kK1Auto;              // K1 form (likewise)
   float tune_ms[ss::kK1Modes + ss::kK2Variants] = {};  // last ss_autotune: pass ms per form
+  // sequential spectra (Sec. 8): every seq_B groups, the block's means and errors
+  // go to seq_out (blocks past seq_cap are counted, not written)
+  int seq_B = 0;
+  double* seq_out = nullptr;
+  long long seq_cap = 0, seq_blocks = 0;
+  double* d_prev = nullptr;  // the S2/S3/S4 sums at the end of the last block
   int* d_counter = nullptr;        // work-queue counter of the pair kernels
   int FC = 0;                      // frames per staged chunk of the pair kernels
   CUtensorMap tm64{}, tm128{}, tm48{};  // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
