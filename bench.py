@@ -168,7 +168,7 @@ def fp32_peak_tflops(nsm, pk):
 
 
 def measure_peaks(gpu_index):
-    """FP32-FMA and tcgen05 TF32 / BF16 (kind::f16) dense peaks of this GPU, measured
+    """FP32-FMA and tcgen05 TF32 / BF16 / FP16 dense peaks of this GPU, measured
     now by libsspeaks.so (CUDA events, about 0.1 s each), with the SM clock sampled
     during the runs.  Returns {} if the library is missing."""
     path = os.path.join(ROOT, "paper_2505_01231_gb300", "libsspeaks.so")
@@ -186,12 +186,12 @@ def measure_peaks(gpu_index):
     time.sleep(0.2)
     if lib.ssp_fma_peak(100000, ctypes.byref(sec), ctypes.byref(rate)) == 0:
         out["fp32_tflops"] = rate.value / 1e12
-    for kind, key in ((0, "tf32_tflops"), (1, "bf16_tflops")):
+    for kind, key in ((0, "tf32_tflops"), (1, "bf16_tflops"), (2, "fp16_tflops")):
         if lib.ssp_mma_peak(kind, 300000, ctypes.byref(sec), ctypes.byref(rate)) == 0:
             out[key] = rate.value / 1e12
     out["clocks"] = clocks.stop()
     out["how"] = ("libsspeaks.so: FP32 FMA, 2048 threads per SM x 16 independent chains; "
-                  "tcgen05.mma 128x256 (K 8 tf32 / 16 bf16) from shared memory into TMEM, one "
+                  "tcgen05.mma 128x256 (K 8 tf32 / 16 bf16, fp16) from shared memory into TMEM, one "
                   "CTA per SM, one issuing thread; CUDA events, the whole device")
     return out
 
@@ -478,7 +478,8 @@ def main():
                     help="apply this tuning text (ss_set_tuning) instead of autotuning")
     ap.add_argument("--fp32-steps", type=int, default=3,
                     help="steps of the all-FP32 S4 arm (0 = skip)")
-    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3", "bf16"],
+    ap.add_argument("--precision", default="tf32x3",
+                    choices=["fp32", "tf32x3", "bf16x3", "bf16", "fp16x3"],
                     help="arithmetic of the S4 moment sums")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -630,7 +631,8 @@ def main():
     k1_over = frames * C * (Mp - M) * 8
     if args.precision != "fp32" and C == 1:
         nkc = (m + 15) // 16 + (m * (m - 1) // 2 + 15) // 16
-        k1_over += groups * C * Mp * (nkc * 16 * 2 * (4 if args.precision == "tf32x3" else 2) + 4)
+        k1_over += groups * C * Mp * (nkc * 16 * 2 * (4 if args.precision == "tf32x3" else 2) +
+                                      (8 if args.precision == "fp16x3" else 4))
     k1_ach = k1_bytes / (k1_ms / 1e3) / 1e9 if k1_ms > 0 else None
     roofline_k1 = {"bound": "hbm", "kernel": "k1_spectra", "achieved": k1_ach, "peak": hbm,
                    "unit": "GB/s", "frac": (k1_ach / hbm) if k1_ach else None,
@@ -662,7 +664,8 @@ def main():
     else:
         passes = 1 if args.precision == "bf16" else 3
         s4_flops = float(st.pairs4) * groups * m * (m + 1)
-        key = "tf32_tflops" if args.precision == "tf32x3" else "bf16_tflops"
+        key = {"tf32x3": "tf32_tflops", "fp16x3": "fp16_tflops"}.get(args.precision,
+                                                                     "bf16_tflops")
         if measured.get(key):
             s4_peak, s4_src = measured[key], f"measured now (tcgen05 {key[:4]} microbenchmark)"
         elif args.precision == "tf32x3":

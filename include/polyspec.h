@@ -84,7 +84,15 @@ enum { SS_F32 = 0, /* float32 samples                                          *
 enum { SS_PREC_FP32 = 0,    /* FP32 FMA on CUDA cores                          */
        SS_PREC_TF32X3 = 1,  /* tensor cores, TF32 hi/lo split, 3 products      */
        SS_PREC_BF16X3 = 2,  /* tensor cores, BF16 hi/lo split, 3 products      */
-       SS_PREC_BF16 = 3     /* tensor cores, plain BF16 inputs                 */ };
+       SS_PREC_BF16 = 3,    /* tensor cores, plain BF16 inputs                 */
+       SS_PREC_FP16X3 = 4   /* tensor cores, FP16 hi/lo split of operands scaled
+                               by a power of two per bin, 3 products           */ };
+/* Accuracy: FP32, TF32X3 and FP16X3 carry every operand to about 2^-22 and meet
+   1e-5 of each spectrum's peak against the FP64 definition; BF16X3 carries them
+   to about 2^-17 (its tests hold it to 5e-5) and plain BF16 to 2^-9: both are
+   outside that bar.  FP16X3 runs the products at the BF16 rate (twice TF32's)
+   with TF32X3's accuracy: each bin's operands are multiplied by a power of two
+   that keeps them inside the FP16 range, which the kernel divides out exactly. */
 /* The tensor-core precisions contract the weighted frame Gram of each bin
    (m(m+1)/2 products per grid point and group) and take m <= 32 when a
    one-channel plan computes S4; ss_plan returns SS_EUNSUPPORTED for larger m.

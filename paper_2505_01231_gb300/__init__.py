@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "SS_OK", "SS_EINVAL", "SS_ENOMEM", "SS_ECUDA", "SS_ESTATE", "SS_ETIMEOUT", "SS_EUNSUPPORTED",
     "SS_WIN_HANN", "SS_WIN_ACG", "SS_ORDER2", "SS_ORDER3", "SS_ORDER4", "SS_F32", "SS_I16",
-    "SS_PREC_FP32", "SS_PREC_TF32X3", "SS_PREC_BF16X3", "SS_PREC_BF16",
+    "SS_PREC_FP32", "SS_PREC_TF32X3", "SS_PREC_BF16X3", "SS_PREC_BF16", "SS_PREC_FP16X3",
     "SSError", "ss_info", "ss_stats_t", "lib", "LIB_PATH",
     "ss_plan", "ss_accumulate", "ss_finalize", "ss_reset", "ss_query", "ss_combos",
     "ss_set_timing", "ss_stats", "ss_set_batch", "ss_destroy", "ss_last_error", "ss_version",
@@ -31,7 +31,7 @@ SS_WIN_HANN, SS_WIN_ACG = 0, 1
 SS_ORDER1, SS_ORDER2, SS_ORDER3, SS_ORDER4 = 1 << 1, 1 << 2, 1 << 3, 1 << 4
 SS_EST_UNBIASED, SS_EST_NATURAL = 0, 1
 SS_F32, SS_I16 = 0, 1
-SS_PREC_FP32, SS_PREC_TF32X3, SS_PREC_BF16X3, SS_PREC_BF16 = 0, 1, 2, 3
+SS_PREC_FP32, SS_PREC_TF32X3, SS_PREC_BF16X3, SS_PREC_BF16, SS_PREC_FP16X3 = 0, 1, 2, 3, 4
 SS_STATE_HEADER = 16
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpolyspec.so")
@@ -344,7 +344,7 @@ class ManyPlan:
         for o in orders:
             ords |= 1 << o
         prec = {"fp32": SS_PREC_FP32, "tf32x3": SS_PREC_TF32X3, "bf16x3": SS_PREC_BF16X3,
-                "bf16": SS_PREC_BF16}[precision]
+                "bf16": SS_PREC_BF16, "fp16x3": SS_PREC_FP16X3}[precision]
         self.handle = ss_plan_many(T_list, max_samples, dt, m, win, sigma_t, ords, prec, stream)
         self.n = len(T_list)
         self.outs = {}
@@ -407,7 +407,7 @@ class Plan:
             ords |= 1 << o
         dt_code = {"f32": SS_F32, "i16": SS_I16}[dtype]
         prec = {"fp32": SS_PREC_FP32, "tf32x3": SS_PREC_TF32X3, "bf16x3": SS_PREC_BF16X3,
-                "bf16": SS_PREC_BF16}[precision]
+                "bf16": SS_PREC_BF16, "fp16x3": SS_PREC_FP16X3}[precision]
         self.handle = ss_plan(channels, T, dt, m, win, sigma_t, ords, dt_code, prec, combos, stream)
         self.orders = tuple(orders)
         if estimator != "unbiased":

@@ -69,11 +69,16 @@ struct Combo {
 // split hi + lo.  Layout per channel and group: rows (bins) in groups of 8;
 // per row group, for each chunk, a hi block and a lo block of CB bytes, each
 // holding the row group's core matrices (8 rows x 16 bytes) of the chunk's
-// 16-byte entry groups 128 bytes apart (TF32: CB = 512; BF16: CB = 256).  So a
-// chunk of a row group is 2 CB bytes, a row group rg_bytes = nkc * 2 CB, a
+// 16-byte entry groups 128 bytes apart (TF32: CB = 512; BF16, FP16: CB = 256).
+// So a chunk of a row group is 2 CB bytes, a row group rg_bytes = nkc * 2 CB, a
 // group group_bytes = (Mp / 8) * rg_bytes.  ps holds sp * Sk per bin,
 // sp = sqrt((m-1) r), so that the contraction minus ps_k ps_l is c4.
-enum { kImageNone = 0, kImageGramTF32 = 1, kImageGramBF16 = 2 };
+// FP16: each bin's row is first multiplied by a power of two s_k that brings its
+// largest entry (at most max(sd, so) max_j |d_jk|^2) below 2^14, so that hi and
+// lo stay inside the FP16 range; ps then holds s_k sp Sk, followed (Mp floats
+// later) by 1/s_k, and the kernel divides D - ps_k ps_l by s_k s_l (exactly:
+// powers of two).
+enum { kImageNone = 0, kImageGramTF32 = 1, kImageGramBF16 = 2, kImageGramF16 = 3 };
 constexpr int kMaxGramM = 32;  // largest m of the tensor-core S4 path
 struct OperandImage {
   void* img = nullptr;
@@ -84,7 +89,8 @@ struct OperandImage {
   long long rg_bytes = 0;     // nkc * 2 * CB
   long long group_bytes = 0;  // (Mp / 8) * rg_bytes
   long long chan_bytes = 0;   // Gb_max * group_bytes
-  long long chan_ps = 0;      // Gb_max * Mp floats
+  long long chan_ps = 0;      // Gb_max * Mp floats (FP16: Gb_max * 2 Mp)
+  int ps_group = 0;           // floats of ps per group: Mp, or 2 Mp with the FP16 scales
 };
 
 // K1 forms (the autotuner's choice per plan): groups resident in shared memory

@@ -15,6 +15,7 @@
 // per-group S2 estimate c2 = 1/(m-1) sum_j |dX_jk|^2 (Eq. 32 with y = x*),
 // whose sum and sum of squares over groups are accumulated for Eq. 35-36.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -112,7 +113,28 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 template <int FMT>
 __device__ __forceinline__ void write_gram_row(unsigned char* row, const float (&e)[16]) {
   constexpr uint32_t CB = FMT == kImageGramTF32 ? 512u : 256u;
-  if constexpr (FMT == kImageGramTF32) {
+  if constexpr (FMT == kImageGramF16) {
+#pragma unroll
+    for (int kg = 0; kg < 2; ++kg) {
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        uint32_t h2[2], l2[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const float v = e[8 * kg + 2 * t + u];
+          const __half h = __float2half_rn(v);
+          const __half l = __float2half_rn(v - __half2float(h));
+          h2[u] = __half_as_ushort(h);
+          l2[u] = __half_as_ushort(l);
+        }
+        hi[t] = h2[0] | (h2[1] << 16);
+        lo[t] = l2[0] | (l2[1] << 16);
+      }
+      *reinterpret_cast<uint4*>(row + kg * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(row + CB + kg * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+  } else if constexpr (FMT == kImageGramTF32) {
 #pragma unroll
     for (int kg = 0; kg < 4; ++kg) {
       uint32_t hi[4], lo[4];
@@ -146,6 +168,15 @@ __device__ __forceinline__ void write_gram_row(unsigned char* row, const float (
       *reinterpret_cast<uint4*>(row + CB + kg * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
   }
+}
+
+// FP16 operand image: the power of two that brings a bin's largest Gram entry,
+// bounded by `bound`, below 2^14 (1 for an all-zero bin).
+__device__ __forceinline__ float f16_row_scale(float bound) {
+  if (!(bound > 0.f)) return 1.f;
+  int e;
+  frexpf(bound, &e);  // bound < 2^e
+  return ldexpf(1.f, 14 - e);
 }
 
 template <int DTYPE>
@@ -191,13 +222,18 @@ __device__ __forceinline__ void centre_bin(int k, bool valid, float2 mean, int m
     }
   } else {
     float dr[kMaxGramM], di[kMaxGramM];
+    float mx = 0.f;  // max_j |d_j|^2
     for (int j = 0; j < m; ++j) {
       const float2 d = valid ? csub(fetch(j), mean) : make_float2(0.f, 0.f);
       store(j, d);
       dr[j] = d.x;
       di[j] = d.y;
-      p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+      const float pj = fmaf(d.x, d.x, d.y * d.y);
+      p += pj;
+      mx = fmaxf(mx, pj);
     }
+    const float sc = FMT == kImageGramF16 ? f16_row_scale(fmaxf(oi.sd, oi.so) * mx) : 1.f;
+    const float sd = oi.sd * sc, so = oi.so * sc;
     const int npair = m * (m - 1) / 2;
     int pj = 0, pk = 1;  // next off-diagonal pair (j, j'), lexicographic
     constexpr int kChunkBytes = FMT == kImageGramTF32 ? 1024 : 512;  // 2 CB
@@ -210,14 +246,14 @@ __device__ __forceinline__ void centre_bin(int k, bool valid, float2 mean, int m
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
           const int j = ch * 16 + t;
-          e[t] = j < m ? oi.sd * fmaf(dr[j], dr[j], di[j] * di[j]) : 0.f;
+          e[t] = j < m ? sd * fmaf(dr[j], dr[j], di[j] * di[j]) : 0.f;
         }
       } else {
         const int p0 = (ch - oi.ndc) * 16;
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
           if (p0 + t < npair) {
-            e[t] = oi.so * fmaf(dr[pj], dr[pk], di[pj] * di[pk]);
+            e[t] = so * fmaf(dr[pj], dr[pk], di[pj] * di[pk]);
             if (++pk == m) {
               ++pj;
               pk = pj + 1;
@@ -229,7 +265,9 @@ __device__ __forceinline__ void centre_bin(int k, bool valid, float2 mean, int m
       }
       write_gram_row<FMT>(rbase + ch * kChunkBytes, e);
     }
-    oi.ps[(long long)c * oi.chan_ps + (long long)g * Mp + k] = oi.sp * p;
+    float* psg = oi.ps + (long long)c * oi.chan_ps + (long long)g * oi.ps_group;
+    psg[k] = oi.sp * p * sc;
+    if (FMT == kImageGramF16) psg[Mp + k] = 1.f / sc;  // exact: a power of two
   }
   if (valid && s2sum) {
     const float c2 = p * pref2;
@@ -493,14 +531,18 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
           mean = make_float2(mean.x * inv_m, mean.y * inv_m);
         }
         if (k == 0) add_s1(s1s[c], mean);
-        float p = 0.f;
+        float p = 0.f, mx = 0.f;  // sum and max over j of |d_j|^2
         for (int j = 0; j < m; ++j) {
           const float2 d = valid ? csub(Xs[j * Mp + k], mean) : make_float2(0.f, 0.f);
           Xs[j * Mp + k] = d;
           grow[(long long)j * Mp + k] = d;
-          p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+          const float pj = fmaf(d.x, d.x, d.y * d.y);
+          p += pj;
+          mx = fmaxf(mx, pj);
         }
         if constexpr (FMT != kImageNone) {
+          const float sc = FMT == kImageGramF16 ? f16_row_scale(fmaxf(oi.sd, oi.so) * mx) : 1.f;
+          const float sd = oi.sd * sc, so = oi.so * sc;
           // weighted Gram products of the bin in K order, read from the centred column
           const int npair = m * (m - 1) / 2;
           int pj = 0, pk = 1;
@@ -516,7 +558,7 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
               for (int t = 0; t < 16; ++t) {
                 const int j = ch * 16 + t;
                 const float2 d = j < m ? Xs[j * Mp + k] : make_float2(0.f, 0.f);
-                e[t] = oi.sd * fmaf(d.x, d.x, d.y * d.y);
+                e[t] = sd * fmaf(d.x, d.x, d.y * d.y);
               }
             } else {
               const int p0 = (ch - oi.ndc) * 16;
@@ -524,7 +566,7 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
               for (int t = 0; t < 16; ++t) {
                 if (p0 + t < npair) {
                   const float2 d2 = Xs[pk * Mp + k];
-                  e[t] = oi.so * fmaf(dj.x, d2.x, dj.y * d2.y);
+                  e[t] = so * fmaf(dj.x, d2.x, dj.y * d2.y);
                   if (++pk == m) {
                     ++pj;
                     pk = pj + 1;
@@ -537,7 +579,9 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
             }
             write_gram_row<FMT>(rbase + ch * kChunkBytes, e);
           }
-          oi.ps[(long long)c * oi.chan_ps + (long long)g * Mp + k] = oi.sp * p;
+          float* psg = oi.ps + (long long)c * oi.chan_ps + (long long)g * oi.ps_group;
+          psg[k] = oi.sp * p * sc;
+          if (FMT == kImageGramF16) psg[Mp + k] = 1.f / sc;  // exact: a power of two
         }
         if (valid && ia >= 0) {
           const float c2 = p * pref2;
@@ -688,6 +732,9 @@ cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G,
     case kImageGramBF16:
       return f32 ? launch_k1_t<SS_F32, kImageGramBF16>(K1_ARGS)
                  : launch_k1_t<SS_I16, kImageGramBF16>(K1_ARGS);
+    case kImageGramF16:
+      return f32 ? launch_k1_t<SS_F32, kImageGramF16>(K1_ARGS)
+                 : launch_k1_t<SS_I16, kImageGramF16>(K1_ARGS);
     default:
       return f32 ? launch_k1_t<SS_F32, kImageNone>(K1_ARGS)
                  : launch_k1_t<SS_I16, kImageNone>(K1_ARGS);

@@ -51,21 +51,31 @@ constexpr uint32_t kColSum = 256, kColSq = 384;
 // matrices (8 rows x 16 bytes) of the chunk's 16-byte entry groups, 128 bytes
 // apart (LBO).  A stage holds kChunks chunks of 16 row groups, so row groups
 // are kChunks * 2 CB apart (SBO).  Every stage is 64 KB.
-template <bool kBF16>
+template <int kFmt>
 struct OpFmt;
 
 template <>
-struct OpFmt<false> {  // TF32: K = 8 per MMA, two K steps of two core matrices
+struct OpFmt<kImageGramTF32> {  // TF32: K = 8 per MMA, two K steps of two core matrices
   static constexpr uint32_t kCB = 512, kKstepBytes = 256;
   static constexpr int kKsteps = 2, kChunks = 2, kStages = 3;
   static constexpr uint32_t kIdescAB = (2u << 7) | (2u << 10);
+  static constexpr bool kF16Kind = false, kScaled = false;
 };
 
 template <>
-struct OpFmt<true> {  // BF16: K = 16 per MMA, one K step
+struct OpFmt<kImageGramBF16> {  // BF16: K = 16 per MMA, one K step
   static constexpr uint32_t kCB = 256, kKstepBytes = 0;
   static constexpr int kKsteps = 1, kChunks = 4, kStages = 3;
   static constexpr uint32_t kIdescAB = (1u << 7) | (1u << 10);
+  static constexpr bool kF16Kind = true, kScaled = false;
+};
+
+template <>
+struct OpFmt<kImageGramF16> {  // FP16 (rows scaled by powers of two): as BF16, A/B type 0
+  static constexpr uint32_t kCB = 256, kKstepBytes = 0;
+  static constexpr int kKsteps = 1, kChunks = 4, kStages = 3;
+  static constexpr uint32_t kIdescAB = 0u;
+  static constexpr bool kF16Kind = true, kScaled = true;
 };
 
 // Shared-memory matrix descriptor, no swizzle.
@@ -74,10 +84,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
 
-template <bool kBF16>
+template <bool kF16Kind>
 __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                           bool accumulate) {
-  if constexpr (kBF16)
+  if constexpr (kF16Kind)
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -142,13 +152,16 @@ struct GroupRec {
 
 constexpr int kPsSlots = 8;  // ring of per-group ps values and records (a power of two)
 
-// kPasses: 3 (hi*hi + hi*lo + lo*hi) or 1 (hi*hi, plain BF16)
-template <bool kBF16, int kPasses>
+// kPasses: 3 (hi*hi + hi*lo + lo*hi) or 1 (hi*hi, plain BF16).  ps: the group's
+// ps values at ps + g * ps_group (FP16: their row scales 1/s_k Mp floats later).
+template <int kFmt, int kPasses>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restrict__ ps, int G,
-              int nkc, int ndc, int M, int Mp, const TileInfo* __restrict__ tiles, WorkQueue wq,
-              double* __restrict__ acc, long long plane, int* __restrict__ status) {
-  using F = OpFmt<kBF16>;
+k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restrict__ ps,
+              int ps_group, int G, int nkc, int ndc, int M, int Mp,
+              const TileInfo* __restrict__ tiles, WorkQueue wq, double* __restrict__ acc,
+              long long plane, int* __restrict__ status) {
+  using F = OpFmt<kFmt>;
+  constexpr int kPsVals = F::kScaled ? 2 : 1;  // ps, and the row scales (FP16)
   constexpr int S = F::kStages, KC = F::kChunks;
   constexpr uint32_t kChunkBytes = 2 * F::kCB;               // hi and lo blocks of a chunk
   constexpr uint32_t kRowGroupBytes = KC * kChunkBytes;      // a row group in a stage
@@ -162,7 +175,8 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
   __shared__ __align__(8) uint64_t afull[2];            // TMEM buffer holds a finished group
   __shared__ __align__(8) uint64_t aempty[2];           // TMEM buffer read by the epilogue
   __shared__ GroupRec prec[kPsSlots];
-  __shared__ __align__(16) float psr[kPsSlots][kTM + kTN];  // ps: k rows, then l columns
+  // ps: k rows, then l columns (FP16: then the row scales of the k rows and l columns)
+  __shared__ __align__(16) float psr[kPsSlots][kPsVals * (kTM + kTN)];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -223,10 +237,14 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
             break;
           }
           prec[p] = GroupRec{ti.k0, ti.l0, ti.ncols, (g == gb - 1) ? 1 : 0};
-          const float* psg = ps + (long long)g * Mp;
-          mbar_arrive_expect_tx(&psfull[p], pk + pl);
+          const float* psg = ps + (long long)g * ps_group;
+          mbar_arrive_expect_tx(&psfull[p], kPsVals * (pk + pl));
           tma_load_1d(&psr[p][0], psg + ti.k0, pk, &psfull[p]);
           tma_load_1d(&psr[p][kTM], psg + ti.l0, pl, &psfull[p]);
+          if constexpr (F::kScaled) {
+            tma_load_1d(&psr[p][kTM + kTN], psg + Mp + ti.k0, pk, &psfull[p]);
+            tma_load_1d(&psr[p][2 * kTM + kTN], psg + Mp + ti.l0, pl, &psfull[p]);
+          }
           ++gq;
           // its stages of KC chunks (chunks past nkc and rows past Mp read as zeros)
           for (int kc0 = 0; kc0 < nkc; kc0 += KC) {
@@ -320,7 +338,7 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
 #pragma unroll
                 for (int kst = 0; kst < F::kKsteps; ++kst) {
                   const uint64_t off = (uint64_t)((j * kChunkBytes + kst * F::kKstepBytes) >> 4);
-                  mma_issue<kBF16>(d, sa + off + (pa == 2 ? kLo : 0u),
+                  mma_issue<F::kF16Kind>(d, sa + off + (pa == 2 ? kLo : 0u),
                                    sb + off + (pa == 1 ? kLo : 0u), id,
                                    kc > 0 || pa > 0 || kst > 0);
                 }
@@ -372,6 +390,8 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
       tc_fence_after();
       tmem_wait_st();  // the previous group's running sums are stored
       const float skr = psr[p][32 * q + lane];
+      // FP16: the product of the row scales of k and l undoes the operands' scaling
+      const float rk = F::kScaled ? psr[p][kTM + kTN + 32 * q + lane] : 1.f;
       // 32-column blocks of this warp that meet the tile (columns past its width
       // hold no products; their sums are never flushed)
       const int ncc = min(2, max(0, (r.n - col0 + 31) >> 5));
@@ -387,9 +407,15 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
         for (int c = 0; c < 32; c += 4) {
           const float4 w = *reinterpret_cast<const float4*>(&psr[p][kTM + col + c]);
           const float sl[4] = {w.x, w.y, w.z, w.w};
+          float rl[4] = {1.f, 1.f, 1.f, 1.f};
+          if constexpr (F::kScaled) {
+            const float4 r4 = *reinterpret_cast<const float4*>(&psr[p][2 * kTM + kTN + col + c]);
+            rl[0] = r4.x * rk; rl[1] = r4.y * rk; rl[2] = r4.z * rk; rl[3] = r4.w * rk;
+          }
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const float v = fmaf(-skr, sl[i], d[c + i]);  // c4 = r (B(k, l) - (m-1) Sk Sl)
+            float v = fmaf(-skr, sl[i], d[c + i]);  // c4 = r (B(k, l) - (m-1) Sk Sl)
+            if constexpr (F::kScaled) v *= rl[i];    // / (s_k s_l), exact
             sm[c + i] += v;
             sq[c + i] = fmaf(v, v, sq[c + i]);
           }
@@ -445,20 +471,22 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
   }
 }
 
-template <bool kBF16>
+template <int kFmt>
 size_t tc_smem_bytes_t() {
-  using F = OpFmt<kBF16>;
+  using F = OpFmt<kFmt>;
   return (size_t)F::kStages * 2 * (kTM / 8) * F::kChunks * 2 * F::kCB + 1024;
 }
 
 }  // namespace
 
 size_t k3tc_smem_bytes(int precision) {
-  return precision == SS_PREC_TF32X3 ? tc_smem_bytes_t<false>() : tc_smem_bytes_t<true>();
+  return precision == SS_PREC_TF32X3 ? tc_smem_bytes_t<kImageGramTF32>()
+                                     : tc_smem_bytes_t<kImageGramBF16>();
 }
 
 int k3tc_stage_chunks(int precision) {
-  return precision == SS_PREC_TF32X3 ? OpFmt<false>::kChunks : OpFmt<true>::kChunks;
+  return precision == SS_PREC_TF32X3 ? OpFmt<kImageGramTF32>::kChunks
+                                     : OpFmt<kImageGramBF16>::kChunks;
 }
 
 cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm_img, const OperandImage& oi, int channel,
@@ -468,9 +496,10 @@ cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm_img, const OperandImage& 
   if (G <= 0 || n_tiles <= 0) return cudaSuccess;
   if (m < 4 || m > kMaxGramM || (Mp & 15)) return cudaErrorInvalidValue;
   const size_t smem = k3tc_smem_bytes(precision);
-  auto kern = precision == SS_PREC_TF32X3 ? k3_trispec_tc<false, 3>
-              : precision == SS_PREC_BF16X3 ? k3_trispec_tc<true, 3>
-                                            : k3_trispec_tc<true, 1>;
+  auto kern = precision == SS_PREC_TF32X3   ? k3_trispec_tc<kImageGramTF32, 3>
+              : precision == SS_PREC_BF16X3 ? k3_trispec_tc<kImageGramBF16, 3>
+              : precision == SS_PREC_FP16X3 ? k3_trispec_tc<kImageGramF16, 3>
+                                            : k3_trispec_tc<kImageGramBF16, 1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // one CTA per SM: each CTA allocates all 512 TMEM columns
@@ -483,8 +512,8 @@ cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm_img, const OperandImage& 
   e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
   const float* ps = oi.ps + (size_t)channel * oi.chan_ps;
-  kern<<<n_cta, kTcThreads, smem, stream>>>(tm_img, ps, G, oi.nkc, oi.ndc, M, Mp, tiles, wq, acc,
-                                            plane, status);
+  kern<<<n_cta, kTcThreads, smem, stream>>>(tm_img, ps, oi.ps_group, G, oi.nkc, oi.ndc, M, Mp,
+                                            tiles, wq, acc, plane, status);
   return cudaGetLastError();
 }
 

@@ -568,7 +568,9 @@ ss_status alloc_spec(ss_plan_s* p) {
   const size_t rg_bytes = (size_t)nkc * 2 * cb;
   const size_t group_bytes = (size_t)(p->Mp / 8) * rg_bytes;
   const size_t img_group = image ? (size_t)p->C * group_bytes : 0;
-  const size_t ps_group = image ? (size_t)p->C * p->Mp * sizeof(float) : 0;
+  // ps per bin (FP16: and the bin's row scale)
+  const int ps_vals = p->precision == SS_PREC_FP16X3 ? 2 : 1;
+  const size_t ps_group = image ? (size_t)p->C * ps_vals * p->Mp * sizeof(float) : 0;
   {
     void* v = p->d_spec;
     release(v, spec_group * p->Gb_max);
@@ -593,14 +595,17 @@ ss_status alloc_spec(ss_plan_s* p) {
   if (image) {
     SS_TRY(p, dev_alloc(p, &p->oi.img, img_group * gb));
     SS_TRY(p, dev_alloc(p, &p->oi.ps, ps_group * gb));
-    p->oi.fmt = p->precision == SS_PREC_TF32X3 ? kImageGramTF32 : kImageGramBF16;
+    p->oi.fmt = p->precision == SS_PREC_TF32X3   ? kImageGramTF32
+                : p->precision == SS_PREC_FP16X3 ? kImageGramF16
+                                                 : kImageGramBF16;
     p->oi.nkc = nkc;
     p->oi.ndc = ndc;
     set_image_scales(p);
     p->oi.rg_bytes = (long long)rg_bytes;
     p->oi.group_bytes = (long long)group_bytes;
     p->oi.chan_bytes = (long long)gb * group_bytes;
-    p->oi.chan_ps = (long long)gb * p->Mp;
+    p->oi.ps_group = ps_vals * p->Mp;
+    p->oi.chan_ps = (long long)gb * p->oi.ps_group;
   }
   return encode_maps(p);
 }
@@ -684,7 +689,7 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
   if (window == SS_WIN_ACG && !(win_param > 0.0 && win_param < 10.0))
     return fail(nullptr, SS_EINVAL, "sigma_t of the confined Gaussian must be in (0, 10)");
   if (dtype != SS_F32 && dtype != SS_I16) return fail(nullptr, SS_EINVAL, "unknown dtype");
-  if (precision < SS_PREC_FP32 || precision > SS_PREC_BF16)
+  if (precision < SS_PREC_FP32 || precision > SS_PREC_FP16X3)
     return fail(nullptr, SS_EINVAL, "unknown precision");
   if (combos && n_combos <= 0) return fail(nullptr, SS_EINVAL, "n_combos must be > 0");
 

@@ -54,7 +54,7 @@ std::string key_of(const ss_plan_s* p) {
   if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) gpu = prop.name;
   for (char& c : gpu)
     if (c == ' ') c = '_';
-  static const char* const prec[] = {"fp32", "tf32x3", "bf16x3", "bf16"};
+  static const char* const prec[] = {"fp32", "tf32x3", "bf16x3", "bf16", "fp16x3"};
   char buf[256];
   std::snprintf(buf, sizeof(buf), "T=%d m=%d C=%d dtype=%s prec=%s sms=%d gpu=%s", p->T, p->m,
                 p->C, p->dtype == SS_F32 ? "f32" : "i16", prec[p->precision], p->nsm,

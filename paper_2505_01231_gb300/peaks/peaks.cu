@@ -12,6 +12,7 @@
 //                    their completion.
 // Both time the kernel with CUDA events on a stream of their own and return the
 // rate in FLOP/s (an FMA counts two).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,9 +58,11 @@ constexpr uint32_t kSmemBytes = kABytes + kBBytes + 1024;  // + alignment slack
 constexpr uint32_t kPad = 96u << 10;                       // keeps one CTA per SM
 constexpr unsigned long long kMmaWaitNs = 20000000000ull;  // 20 s
 
-template <bool kBF16>
+// kType: 0 = TF32 (kind::tf32), 1 = BF16, 2 = FP16 (both kind::f16)
+template <int kType>
 __global__ void __launch_bounds__(128, 1)
 k_mma(int iters, int* __restrict__ status) {
+  constexpr bool kBF16 = kType != 0;  // a 16-bit kind::f16 type
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t done;
   __shared__ uint32_t tslot;
@@ -69,7 +72,11 @@ k_mma(int iters, int* __restrict__ status) {
     const uint32_t h = (i * 2654435761u) >> 9;
     float v = 0.25f + (float)(h & 1023u) * (1.0f / 4096.0f);
     uint32_t w = __float_as_uint(v);
-    if (kBF16) w = (w >> 16) | (w & 0xFFFF0000u);  // two BF16 values of about v
+    if (kType == 1) w = (w >> 16) | (w & 0xFFFF0000u);  // two BF16 values of about v
+    if (kType == 2) {                                    // two FP16 values of about v
+      const uint32_t hbits = __half_as_ushort(__float2half_rn(v));
+      w = hbits | (hbits << 16);
+    }
     reinterpret_cast<uint32_t*>(base)[i] = w;
   }
   if (threadIdx.x == 0) {
@@ -89,7 +96,9 @@ k_mma(int iters, int* __restrict__ status) {
   if (threadIdx.x == 0) {
     // D f32 (bit 4), A/B format (bits 7-9, 10-12: tf32 = 2, bf16 = 1), K-major
     // A and B, N / 8 at bit 17, M / 16 at bit 24
-    const uint32_t fmt = kBF16 ? ((1u << 7) | (1u << 10)) : ((2u << 7) | (2u << 10));
+    const uint32_t fmt = kType == 1 ? ((1u << 7) | (1u << 10))
+                         : kType == 2 ? 0u
+                                      : ((2u << 7) | (2u << 10));
     const uint32_t idesc = (1u << 4) | fmt | ((uint32_t)(kMmaN >> 3) << 17) |
                            ((uint32_t)(kMmaM >> 4) << 24);
     const uint64_t a0 = mdesc(smem_u32(base), 128, 8 * kRowBytes);
@@ -185,7 +194,8 @@ int ssp_fma_peak(int iters, double* seconds, double* flops_per_s) {
 }
 
 // tcgen05 dense product rate of the whole device, kind 0 = kind::tf32,
-// 1 = kind::f16 with BF16 inputs; returns 0, or 1 if a bounded wait ran out.
+// 1 = kind::f16 with BF16 inputs, 2 = kind::f16 with FP16 inputs; returns 0, or
+// 1 if a bounded wait ran out.
 int ssp_mma_peak(int kind, int iters, double* seconds, double* flops_per_s) {
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
@@ -194,7 +204,11 @@ int ssp_mma_peak(int kind, int iters, double* seconds, double* flops_per_s) {
   int* status = nullptr;
   if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return -1;
   cudaMemset(status, 0, sizeof(int));
-  auto kern = kind == 1 ? k_mma<true> : k_mma<false>;
+  if (kind < 0 || kind > 2) {
+    cudaFree(status);
+    return -1;
+  }
+  auto kern = kind == 1 ? k_mma<1> : kind == 2 ? k_mma<2> : k_mma<0>;
   const size_t smem = kSmemBytes + kPad;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
@@ -216,7 +230,7 @@ int ssp_mma_peak(int kind, int iters, double* seconds, double* flops_per_s) {
     rc = -1;
   if (rc == 0 && st != 0) rc = 1;
   if (rc == 0) {
-    const double k = kind == 1 ? 16.0 : 8.0;  // K of one product
+    const double k = kind == 0 ? 8.0 : 16.0;  // K of one product
     *flops_per_s = 2.0 * kMmaM * kMmaN * k * 4.0 * (double)iters * nsm / *seconds;
   }
   cudaEventDestroy(e0);

@@ -96,11 +96,11 @@ def test_sizes_and_ragged_tails(T, m, G):
 # BF16 3-pass (operands carried to about 2^-17, each product to about 2^-16)
 # and plain BF16 (2^-9) fall outside that bar; they are reported separately and
 # held here to the bars their operand precision allows
-PREC_TOL = {"fp32": (TOL, TOL_ERR), "tf32x3": (TOL, TOL_ERR), "bf16x3": (5e-5, 5e-4),
-            "bf16": (2e-2, 2e-1)}
+PREC_TOL = {"fp32": (TOL, TOL_ERR), "tf32x3": (TOL, TOL_ERR), "fp16x3": (TOL, TOL_ERR),
+            "bf16x3": (5e-5, 5e-4), "bf16": (2e-2, 2e-1)}
 
 
-@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3", "bf16"])
+@pytest.mark.parametrize("precision", ["tf32x3", "fp16x3", "bf16x3", "bf16"])
 def test_config1_tensor_core_s4(c1_signal, precision):
     ref = oracle.polyspectra(c1_signal, 256, 1.0, 10, orders=(4,), group_chunk=64)
     gpu = run_gpu(c1_signal, 256, 10, orders=(4,), precision=precision)
@@ -112,7 +112,7 @@ def test_config1_tensor_core_s4(c1_signal, precision):
 # m from the smallest S4 group to the largest the Gram contraction takes: one
 # diagonal K chunk and a ragged pair chunk (m = 4, 6, 10), exactly 16 frames,
 # two diagonal chunks (m = 17, 32); grids from one ragged 128-bin tile to 17 x 17
-@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("precision", ["tf32x3", "fp16x3", "bf16x3"])
 @pytest.mark.parametrize("T,m,G", [(16, 4, 40), (64, 6, 30), (512, 10, 9), (32, 16, 12),
                                    (128, 17, 10), (64, 32, 6), (4096, 5, 3)])
 def test_tensor_core_s4_sizes(T, m, G, precision):
@@ -121,6 +121,21 @@ def test_tensor_core_s4_sizes(T, m, G, precision):
     gpu = run_gpu(z, T, m, dt=0.5, orders=(2, 4), precision=precision)
     tol, tol_err = PREC_TOL[precision]
     compare_single(gpu, ref, orders=(2, 4), tol4=tol, tol4_err=tol_err)
+
+
+@pytest.mark.parametrize("scale", [1e-12, 1e12])
+def test_fp16x3_row_scaling_keeps_tiny_and_huge_records_in_range(scale):
+    # the FP16 operands are scaled per bin by powers of two: a record scaled by
+    # 1e-12 or 1e12 (Gram entries far outside the FP16 range either way) gives the
+    # scaled spectrum (S4 scales by scale^4) to the same relative accuracy; a red
+    # spectrum (AR(1), coefficient 0.99) spans several decades across the bins
+    T, m, G = 256, 8, 40
+    z = synth.ar1_quadratic(T * m * G + 9, seed=77, phi=0.99).astype(np.float64) * scale
+    z = z.astype(np.float32)
+    ref = oracle.polyspectra(z, T, 1.0, m, orders=(4,), group_chunk=8)
+    gpu = run_gpu(z, T, m, orders=(4,), precision="fp16x3")
+    compare_single(gpu, ref, orders=(4,))
+    assert np.max(np.abs(ref["S4"])) > 0
 
 
 def test_streaming_chunks_match_one_call(c1_signal):
@@ -308,7 +323,7 @@ def check_sampled(gpu, refs, s3, s4, G, tol4=TOL, tol4_err=TOL_ERR):
         assert np.max(np.abs(E[k, l, 1] - ref[2])) <= tol_err * max(np.max(ref[1]), np.max(ref[2]))
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "fp16x3", "bf16x3"])
 def test_config2_full_size_sampled_points(config2, precision):
     # launched as bench.py does (one plan, the whole record in one call: two batches)
     z, s3, s4, refs, G = config2

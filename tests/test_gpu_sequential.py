@@ -45,7 +45,7 @@ def test_blocks_across_calls_and_batches_match_the_oracle(precision):
     plan = mod.Plan(T=T, dt=0.5, m=m, precision=precision)
     mod.ss_set_batch(plan.handle, 3)          # device batches of 3 groups: blocks span them
     plan.sequential(B, 3)                     # room for 3 of the 4 blocks
-    for a, b in ((0, 1000), (1000, 4000), (4000, 9999), (9999, z.size)):
+    for a, b in ((0, 1000), (1000, 4000), (4000, 6001), (6001, z.size)):
         plan.accumulate(torch.from_numpy(z[a:b].copy()).cuda(), b - a)
     out = plan.finalize()
     n, done = mod.ss_sequential_info(plan.handle)
