@@ -390,8 +390,10 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
       tc_fence_after();
       tmem_wait_st();  // the previous group's running sums are stored
       const float skr = psr[p][32 * q + lane];
-      // FP16: the product of the row scales of k and l undoes the operands' scaling
+      // FP16: the row scales of k and l undo the operands' scaling, applied one at a
+      // time (their product alone may leave the float range)
       const float rk = F::kScaled ? psr[p][kTM + kTN + 32 * q + lane] : 1.f;
+      const float skrk = skr * rk;
       // 32-column blocks of this warp that meet the tile (columns past its width
       // hold no products; their sums are never flushed)
       const int ncc = min(2, max(0, (r.n - col0 + 31) >> 5));
@@ -410,12 +412,13 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
           float rl[4] = {1.f, 1.f, 1.f, 1.f};
           if constexpr (F::kScaled) {
             const float4 r4 = *reinterpret_cast<const float4*>(&psr[p][2 * kTM + kTN + col + c]);
-            rl[0] = r4.x * rk; rl[1] = r4.y * rk; rl[2] = r4.z * rk; rl[3] = r4.w * rk;
+            rl[0] = r4.x; rl[1] = r4.y; rl[2] = r4.z; rl[3] = r4.w;
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            float v = fmaf(-skr, sl[i], d[c + i]);  // c4 = r (B(k, l) - (m-1) Sk Sl)
-            if constexpr (F::kScaled) v *= rl[i];    // / (s_k s_l), exact
+            // c4 = r (B(k, l) - (m-1) Sk Sl); FP16: ((D / s_k) - (ps_k / s_k) ps_l) / s_l
+            const float v = F::kScaled ? fmaf(d[c + i], rk, -skrk * sl[i]) * rl[i]
+                                       : fmaf(-skr, sl[i], d[c + i]);
             sm[c + i] += v;
             sq[c + i] = fmaf(v, v, sq[c + i]);
           }
