@@ -19,6 +19,10 @@ reordering beyond what the cited formula states:
 * first-order spectrum ..... Sec. 4, S1 = N C1(a_0) / (T sum g); App. G
 * interlaced spectra ....... Sec. 3: the same estimate from windows shifted by T/2, pooled with
                               the unshifted one (the groups of both window sets are the parts)
+* complex-valued signals ... App. D: the spectra of complex channels from the cumulants of
+                              their own Fourier coefficients at +k and -k (the multilinear
+                              extension of Eq. 47, 48, 50); App. E: planes of the 3-D
+                              trispectrum parallel to the cut, by a shift of s bins
 * sequential spectra ....... Sec. 8 (quasi-polyspectra): the short-time estimates, each from m
                               windows, averaged over blocks of consecutive groups
 * natural (biased) estimators, for the paper's unbiased-vs-biased comparison
@@ -65,6 +69,8 @@ __all__ = [
     "cross_domain_s3",
     "cross_polyspectra",
     "sequential_spectra",
+    "dft_plus_complex",
+    "complex_polyspectra",
 ]
 
 
@@ -488,4 +494,97 @@ def sequential_spectra(z, T, dt, m, block_groups, window_kind="hann", sigma_t=0.
         key = f"S{n}"
         out[key] = np.stack([q[key] for q in parts]) if nb else None
         out[key + "_err"] = np.stack([q[key + "_err"] for q in parts]) if nb else None
+    return out
+
+
+# --------------------------------------------------------------------------- complex signals
+def dft_plus_complex(x: np.ndarray) -> np.ndarray:
+    """X_k = sum_i x_i exp(+2 pi j i k / T) of complex frames, all T bins k = 0..T-1
+    over the last axis (bin T - k is the negative frequency -k).  numpy's inverse
+    FFT uses the same exponent and a factor 1/T, so it serves as the summation
+    step."""
+    x = np.asarray(x, dtype=np.complex128)
+    return np.fft.ifft(x, axis=-1) * x.shape[-1]
+
+
+def _coef_full(X, k, conj):
+    """Coefficient at (signed) bin k of a channel, or of its complex conjugate
+    (the transform of z* at k is the conjugate of z's at -k); bins wrap mod T."""
+    T = X.shape[-1]
+    if conj:
+        return np.conj(X[..., (-np.asarray(k)) % T])
+    return X[..., np.asarray(k) % T]
+
+
+def complex_polyspectra(zs, T, dt, m, s2_combos=(), s3_combos=(), s4_combos=(), s4_shift=0,
+                        window_kind="hann", sigma_t=0.14, group_chunk=8):
+    """Spectra of complex-valued channels (App. D) and shifted S4 planes (App. E).
+
+    zs: [C, n] complex channels.  A combination lists its operands as (channel,
+    conjugate) pairs; operand (c, True) is the conjugate signal z_c*.  With A, B,
+    C, D the Fourier coefficients of the operands (all T bins, Eq. 18 with the
+    positive exponent) and the window sums of Eq. 23, 28, 31:
+      S2(k)    = dt   c2(A(k), B(-k))                       / sum g^2
+      S3(k, l) = dt^2 c3(A(k), B(l), C(-k-l))                / sum g^3
+      S4(k, l) = dt^3 c4(A(k+s), B(-k-s), C(l-s), D(-l+s))   / sum g^4
+    for k, l in [-(M-1), M-1] (M = T/2 + 1; S3 where also |k + l| <= M-1, zero
+    elsewhere), bins taken mod T.  For real channels A(-k) = A(k)*, so these are
+    the spectra of Eq. 47, 48, 50 on the whole plane.  s = s4_shift: the plane
+    of the 3-D trispectrum through (k + s, -k - s, l - s, -l + s), the S4 of the
+    shifted signals z1 e^{+j dw t}, z2 e^{-j dw t}, z3 e^{-j dw t}, z4 e^{+j dw t}
+    with dw = 2 pi s / (T dt) (frames start at multiples of T samples, where
+    e^{j dw t} = 1).  Returns {(order key, combo): (mean, err[..., 2])} and 'G';
+    the arrays are [2M-1] (S2) or [2M-1, 2M-1] (S3, S4), row r holding k = r-(M-1)
+    and column c holding l = c-(M-1).
+    """
+    g = window(T, window_kind, sigma_t)
+    zs = np.asarray(zs)
+    G = zs.shape[-1] // (m * T)
+    frames = zs[:, : G * m * T].astype(np.complex128).reshape(zs.shape[0], G, m, T)
+    M = T // 2 + 1
+    ks = np.arange(-(M - 1), M)
+    kk, ll = [a.ravel() for a in np.meshgrid(ks, ks, indexing="ij")]
+    in3 = np.abs(kk + ll) <= M - 1
+    s = int(s4_shift)
+    accs = {}
+    for cmb in s2_combos:
+        accs[("S2", tuple(cmb))] = _Acc((ks.size,))
+    for cmb in s3_combos:
+        accs[("S3", tuple(cmb))] = _Acc((int(in3.sum()),))
+    for cmb in s4_combos:
+        accs[("S4", tuple(cmb))] = _Acc((kk.size,))
+    k3, l3 = kk[in3], ll[in3]
+    for g0 in range(0, G, group_chunk):
+        X = [dft_plus_complex(frames[c, g0:g0 + group_chunk] * g) for c in range(zs.shape[0])]
+
+        def op(o, k):
+            c, cj = o
+            return _samples_last(_coef_full(X[c], k, cj))
+
+        for cmb in s2_combos:
+            a, b = cmb
+            v = c2(op(a, ks), op(b, -ks))
+            accs[("S2", tuple(cmb))].add(dt * v / np.sum(g ** 2))
+        for cmb in s3_combos:
+            a, b, c = cmb
+            v = c3(op(a, k3), op(b, l3), op(c, -k3 - l3))
+            accs[("S3", tuple(cmb))].add(dt * dt * v / np.sum(g ** 3))
+        for cmb in s4_combos:
+            a, b, c, d = cmb
+            v = c4(op(a, kk + s), op(b, -kk - s), op(c, ll - s), op(d, -ll + s))
+            accs[("S4", tuple(cmb))].add(dt ** 3 * v / np.sum(g ** 4))
+    out = {"G": G}
+    n = 2 * M - 1
+    for key, acc in accs.items():
+        mean, er, ei = acc.result()
+        if key[0] == "S2":
+            out[key] = (mean, np.stack([er, ei], -1))
+        elif key[0] == "S3":
+            S = np.zeros((n, n), np.complex128)
+            E = np.zeros((n, n, 2))
+            S[k3 + M - 1, l3 + M - 1] = mean
+            E[k3 + M - 1, l3 + M - 1, 0], E[k3 + M - 1, l3 + M - 1, 1] = er, ei
+            out[key] = (S, E)
+        else:
+            out[key] = (mean.reshape(n, n), np.stack([er, ei], -1).reshape(n, n, 2))
     return out
