@@ -123,14 +123,14 @@ def test_tensor_core_s4_sizes(T, m, G, precision):
     compare_single(gpu, ref, orders=(2, 4), tol4=tol, tol4_err=tol_err)
 
 
-@pytest.mark.parametrize("scale", [1e-3, 1e3])
+@pytest.mark.parametrize("scale", [1e-2, 30.0])
 def test_fp16x3_row_scaling_keeps_tiny_and_huge_records_in_range(scale):
-    # the FP16 operands are scaled per bin by powers of two: a record scaled by
-    # 1e-3 or 1e3 (Gram entries below the FP16 normal range or above its largest
-    # value, by orders of magnitude) gives the spectrum to the same relative
-    # accuracy; a red spectrum (AR(1), coefficient 0.99) spans several decades
-    # across the bins.  (The scales keep c4 and its square inside the float32
-    # range of the per-group sums, as for every precision.)
+    # the FP16 operands are scaled per bin by powers of two.  A red spectrum (AR(1),
+    # coefficient 0.99) already spans 3e-5 .. 2e6 in |d|^2 across its bins (both
+    # ends outside the FP16 normal range); records scaled by 1e-2 and 30 push the
+    # ends further (about 3e-9 and 2e9) and give the spectrum to the same relative
+    # accuracy.  (Both keep c4 and its square inside the float32 range of the
+    # per-group sums, as for every precision.)
     T, m, G = 256, 8, 40
     z = synth.ar1_quadratic(T * m * G + 9, seed=77, phi=0.99).astype(np.float64) * scale
     z = z.astype(np.float32)
