@@ -252,6 +252,42 @@ ss_status ss_set_sequential(ss_plan_t plan, int block_groups, double* out, long 
 ss_status ss_sequential_info(ss_plan_t plan, size_t* block_doubles, long long* blocks_done);
 
 /*
+ * Complex-valued signals (App. D) and S4 planes off the cut (App. E).
+ *
+ * A complex signal z = x + j y is fed as its two real channels (x and y among
+ * the plan's channels), so any mix of real and complex signals fits in one
+ * plan.  An operand is three ints {re, im, conj}: the real channel carrying the
+ * real part, the one carrying the imaginary part (-1 for a real signal), and 1
+ * for the conjugate signal z* (else 0).  With A, B, C, D the Fourier
+ * coefficients of the operands (Eq. 18, positive exponent) at signed bins, and
+ * the window and dt normalisation of Eq. 23, 28, 31:
+ *   order 2: S2(k)    ~ c2(A(k), B(-k))                        [2M-1]
+ *   order 3: S3(k, l) ~ c3(A(k), B(l), C(-k-l))                [2M-1][2M-1]
+ *   order 4: S4(k, l) ~ c4(A(k+s), B(-k-s), C(l-s), D(-l+s))   [2M-1][2M-1]
+ * with k = row - (M-1), l = column - (M-1), bins mod T, S3 zero where
+ * |k + l| > M-1.  For real operands these are the spectra of Eq. 47, 48, 50 on
+ * the whole plane; for complex ones they are the multilinear combinations that
+ * App. D writes as sums of 4, 8 or 16 real spectra, taken per group, so the
+ * error bars (Eq. 35-36) are those of the combination.  s = s4_shift moves the
+ * S4 plane through the 3-D trispectrum: it is the cut of the signals
+ * z1 e^{j dw t}, z2 e^{-j dw t}, z3 e^{-j dw t}, z4 e^{j dw t}, dw = 2 pi s/(T dt).
+ *
+ * ss_set_complex      -- n records of 13 ints {order, op0 (3 ints), op1, op2,
+ *     op3} (unused operands ignored) and the shift; replaces any earlier set.
+ *     Valid only before the first ss_accumulate (or after ss_reset).
+ *     SS_EINVAL for a bad order, channel or flag; SS_EUNSUPPORTED with
+ *     interlaced window sets.  The sums are not part of exported states.
+ * ss_complex_size     -- doubles of the means of all records (the same again
+ *     for the errors): per record 2 (2M-1) (order 2) or 2 (2M-1)^2.
+ * ss_finalize_complex -- the records' means (complex128 interleaved) and errors
+ *     ((err_re, err_im) pairs), concatenated in record order; host or device
+ *     memory, either may be NULL.  Synchronises the plan's stream.
+ */
+ss_status ss_set_complex(ss_plan_t plan, const int* records, int n_records, int s4_shift);
+ss_status ss_complex_size(ss_plan_t plan, size_t* n_doubles);
+ss_status ss_finalize_complex(ss_plan_t plan, double* S, double* S_err);
+
+/*
  * ss_inject_timeout -- fault-injection hook for testing the timeout path (no
  *   counterpart in the paper).  Every kernel that waits for its own staged data
  *   (TMA copies, tensor-core products) bounds each wait by 2 s of %globaltimer;

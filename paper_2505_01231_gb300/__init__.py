@@ -82,6 +82,9 @@ _sig = {
     "ss_set_estimator": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_set_interlace": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_inject_timeout": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ss_set_complex": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int]),
+    "ss_complex_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "ss_finalize_complex": (ctypes.c_int, [_P, _P, _P]),
     "ss_set_sequential": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_longlong]),
     "ss_sequential_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t),
                                           ctypes.POINTER(ctypes.c_longlong)]),
@@ -177,6 +180,27 @@ def ss_sequential_info(plan):
     n, b = ctypes.c_size_t(), ctypes.c_longlong()
     _check(lib.ss_sequential_info(plan, ctypes.byref(n), ctypes.byref(b)), plan)
     return n.value, b.value
+
+
+def ss_set_complex(plan, records, s4_shift=0):
+    """records: [(order, (re, im, conj), ...)] operands of complex-signal spectra."""
+    flat = []
+    for rec in records:
+        order, ops = rec[0], list(rec[1:])
+        ops += [(-1, -1, 0)] * (4 - len(ops))
+        flat += [int(order)] + [int(v) for op in ops for v in op]
+    arr = (ctypes.c_int * max(1, len(flat)))(*flat)
+    _check(lib.ss_set_complex(plan, arr, len(records), int(s4_shift)), plan)
+
+
+def ss_complex_size(plan):
+    n = ctypes.c_size_t()
+    _check(lib.ss_complex_size(plan, ctypes.byref(n)), plan)
+    return n.value
+
+
+def ss_finalize_complex(plan, S=None, S_err=None):
+    _check(lib.ss_finalize_complex(plan, _addr(S), _addr(S_err)), plan)
 
 
 def ss_autotune(plan):
@@ -453,6 +477,24 @@ class Plan:
 
     def reset(self):
         ss_reset(self.handle)
+
+    def complex_spectra(self, records):
+        """Means and errors of the complex-signal records (ss_set_complex) as a list
+        of (mean, err) numpy arrays in record order."""
+        M = ss_query(self.handle).M
+        nn = 2 * M - 1
+        total = ss_complex_size(self.handle)
+        mean = np.zeros(total)
+        err = np.zeros(total)
+        ss_finalize_complex(self.handle, mean, err)
+        out, o = [], 0
+        for rec in records:
+            shape = (nn,) if rec[0] == 2 else (nn, nn)
+            k = 2 * int(np.prod(shape))
+            v = mean[o:o + k].reshape(shape + (2,))
+            out.append((v[..., 0] + 1j * v[..., 1], err[o:o + k].reshape(shape + (2,))))
+            o += k
+        return out
 
     def sequential(self, block_groups, max_blocks):
         """Turn on sequential spectra (ss_set_sequential) into a device buffer this

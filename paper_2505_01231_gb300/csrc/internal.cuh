@@ -173,6 +173,16 @@ inline int work_group_chunk(int G, int n_tiles, int n_cta) {
   return (int)gc;
 }
 
+// Spectra of complex-valued signals (App. D) and shifted S4 planes (App. E) on
+// the full (k, l) plane: n_combos combinations of `order` operands each, operand
+// i of combination q at ops[order q + i] = (real channel, imaginary channel or
+// -1, sign of j: -1 for the conjugate signal, else 1); accumulated at
+// acc[plane][q][rows][cols] with rows = cols = 2M - 1 (S2: [q][2M - 1]).
+cudaError_t launch_k5_complex(const float2* spec, long long chan_stride, int G, int m, int M,
+                              int Mp, int order, const int4* ops, int n_combos, int shift,
+                              bool natural, double* acc, long long plane, int nsm,
+                              cudaStream_t stream);
+
 // K2 for isolated grid points of one channel (pts: n_pts (k, l) pairs)
 cudaError_t launch_k2_points(const float2* spec, int Mp, int G, int m, const int2* pts,
                              int n_pts, int M, float pref3, double* acc, long long plane,

@@ -347,6 +347,17 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
         }
         record(p, 2, p->stream, false);
       }
+      // spectra of complex-valued signals and shifted S4 planes (App. D, E)
+      for (int o = 0; o < 3; ++o) {
+        if (p->cx_ops[o].empty()) continue;
+        record(p, 2, p->stream, true);
+        const int n_cx = (int)(p->cx_ops[o].size() / (o + 2));
+        const long long cplane = (long long)p->n_cx_acc[o] / kPlanes;
+        SS_TRY(p, launch_k5_complex(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp, o + 2,
+                                    p->d_cx_ops[o], n_cx, p->cx_shift, nat, p->d_cx_acc[o],
+                                    cplane, p->nsm, p->stream));
+        record(p, 2, p->stream, false);
+      }
       g0 += take;
       if (p->seq_B > 0 && (p->groups + g0) % p->seq_B == 0) {
         ss_status st = emit_block(p);
@@ -468,6 +479,9 @@ ss_status zero_state(ss_plan_s* p) {
   if (p->d_prev)
     SS_TRY(p, cudaMemsetAsync(p->d_prev, 0,
                               (p->n_acc2 + p->n_acc3 + p->n_acc4) * sizeof(double), p->stream));
+  for (int o = 0; o < 3; ++o)
+    if (p->d_cx_acc[o])
+      SS_TRY(p, cudaMemsetAsync(p->d_cx_acc[o], 0, p->n_cx_acc[o] * sizeof(double), p->stream));
   p->seq_blocks = 0;
   p->carry_n = 0;
   p->groups = 0;
@@ -647,6 +661,10 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_counter);
   cudaFree(p->d_out);
   cudaFree(p->d_prev);
+  for (int o = 0; o < 3; ++o) {
+    cudaFree(p->d_cx_ops[o]);
+    cudaFree(p->d_cx_acc[o]);
+  }
   delete p;
 }
 
@@ -1077,6 +1095,117 @@ ss_status ss_sequential_info(ss_plan_t p, size_t* block_doubles, long long* bloc
   return SS_OK;
 }
 
+ss_status ss_set_complex(ss_plan_t p, const int* recs, int n, int s4_shift) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (n < 0 || (n > 0 && !recs)) return fail(p, SS_EINVAL, "records missing");
+  if (p->groups != 0 || p->carry_n != 0)
+    return fail(p, SS_ESTATE, "ss_set_complex is valid only before the first ss_accumulate");
+  if (n > 0 && p->shadow)
+    return fail(p, SS_EUNSUPPORTED, "complex-signal spectra of interlaced window sets");
+  std::vector<int4> ops[3];
+  std::vector<int> order;
+  for (int i = 0; i < n; ++i) {
+    const int* r = recs + 13 * i;
+    const int o = r[0];
+    if (o < 2 || o > 4) return fail(p, SS_EINVAL, "record order must be 2, 3 or 4");
+    if (o == 3 && p->m < 3) return fail(p, SS_EINVAL, "S3 needs m >= 3 (Eq. 33)");
+    if (o == 4 && p->m < 4) return fail(p, SS_EINVAL, "S4 needs m >= 4 (Eq. 34)");
+    for (int q = 0; q < o; ++q) {
+      const int re = r[1 + 3 * q], im = r[2 + 3 * q], cj = r[3 + 3 * q];
+      if (re < 0 || re >= p->C || im < -1 || im >= p->C || (cj != 0 && cj != 1))
+        return fail(p, SS_EINVAL, "operand names a channel out of range or a bad conjugate flag");
+      ops[o - 2].push_back(make_int4(re, im, cj ? -1 : 1, 0));
+    }
+    order.push_back(o);
+  }
+  DeviceGuard guard(p->device);
+  const long long nn = 2ll * p->M - 1;
+  for (int o = 0; o < 3; ++o) {
+    cudaFree(p->d_cx_ops[o]);
+    cudaFree(p->d_cx_acc[o]);
+    p->d_cx_ops[o] = nullptr;
+    p->d_cx_acc[o] = nullptr;
+    p->n_cx_acc[o] = 0;
+    p->cx_ops[o] = ops[o];
+    if (ops[o].empty()) continue;
+    const size_t combos = ops[o].size() / (o + 2);
+    p->n_cx_acc[o] = (size_t)kPlanes * combos * (o == 0 ? nn : nn * nn);
+    SS_TRY(p, dev_alloc(p, &p->d_cx_ops[o], ops[o].size() * sizeof(int4)));
+    SS_TRY(p, cudaMemcpy(p->d_cx_ops[o], ops[o].data(), ops[o].size() * sizeof(int4),
+                         cudaMemcpyHostToDevice));
+    SS_TRY(p, dev_alloc(p, &p->d_cx_acc[o], p->n_cx_acc[o] * sizeof(double)));
+    SS_TRY(p, cudaMemsetAsync(p->d_cx_acc[o], 0, p->n_cx_acc[o] * sizeof(double), p->stream));
+  }
+  p->cx_order = order;
+  p->cx_shift = s4_shift;
+  return SS_OK;
+}
+
+ss_status ss_complex_size(ss_plan_t p, size_t* n_doubles) {
+  if (!p || !n_doubles) return fail(p, SS_EINVAL, "NULL argument");
+  const size_t nn = 2 * (size_t)p->M - 1;
+  size_t n = 0;
+  for (int o : p->cx_order) n += 2 * (o == 2 ? nn : nn * nn);
+  *n_doubles = n;
+  return SS_OK;
+}
+
+ss_status ss_finalize_complex(ss_plan_t p, double* S, double* S_err) {
+  if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
+  if (p->broken) return fail(p, SS_ESTATE, "plan is unusable after a CUDA failure: " + p->err);
+  if (p->cx_order.empty()) return fail(p, SS_ESTATE, "no complex-signal combinations set");
+  if (p->groups < 2)
+    return fail(p, SS_ESTATE, "fewer than two groups accumulated: no error estimate (Eq. 35)");
+  DeviceGuard guard(p->device);
+  size_t total = 0;
+  ss_status st = ss_complex_size(p, &total);
+  if (st != SS_OK) return st;
+  // the finalize buffer holds means and errors (grown to fit)
+  if (p->out_doubles < 2 * total) {
+    if (p->d_out) {
+      cudaFree(p->d_out);
+      p->device_bytes -= p->out_doubles * sizeof(double);
+      p->d_out = nullptr;
+      p->out_doubles = 0;
+    }
+    SS_TRY(p, dev_alloc(p, &p->d_out, 2 * total * sizeof(double)));
+    p->out_doubles = 2 * total;
+  }
+  const int nn = 2 * p->M - 1;
+  const double norms[3] = {p->norm2, p->norm3, p->norm4};
+  // each order's combinations in one K4 launch over its block of the buffer
+  double* mean[3];
+  double* err[3];
+  size_t off = 0;
+  for (int o = 0; o < 3; ++o) {
+    const size_t combos = p->cx_ops[o].size() / (o + 2);
+    const size_t per = 2 * (o == 0 ? (size_t)nn : (size_t)nn * nn);
+    mean[o] = p->d_out + off;
+    err[o] = p->d_out + total + off;
+    if (combos)
+      SS_TRY(p, launch_k4_finalize(p->d_cx_acc[o], (int)combos, o == 0 ? 1 : nn, nn,
+                                   kLayoutCross, p->groups, norms[o], mean[o], err[o], p->stream));
+    off += combos * per;
+  }
+  // to the caller in record order
+  size_t seen[3] = {0, 0, 0};
+  size_t out_off = 0;
+  for (int o : p->cx_order) {
+    const size_t per = 2 * (o == 2 ? (size_t)nn : (size_t)nn * nn);
+    const int i = o - 2;
+    if (S)
+      SS_TRY(p, cudaMemcpyAsync(S + out_off, mean[i] + seen[i] * per, per * sizeof(double),
+                                cudaMemcpyDefault, p->stream));
+    if (S_err)
+      SS_TRY(p, cudaMemcpyAsync(S_err + out_off, err[i] + seen[i] * per, per * sizeof(double),
+                                cudaMemcpyDefault, p->stream));
+    ++seen[i];
+    out_off += per;
+  }
+  SS_TRY(p, cudaStreamSynchronize(p->stream));
+  return check_status(p);
+}
+
 ss_status ss_inject_timeout(ss_plan_t p, int on) {
   if (!p) return fail(nullptr, SS_EINVAL, "plan is NULL");
   for (ss_plan_s* q = p; q; q = q->shadow) q->inject_timeout = on ? 1 : 0;
@@ -1098,6 +1227,8 @@ ss_status ss_set_interlace(ss_plan_t p, int on) {
   if (p->shadow) return SS_OK;
   if (p->seq_B > 0)
     return fail(p, SS_EUNSUPPORTED, "interlaced window sets with sequential spectra");
+  if (!p->cx_order.empty())
+    return fail(p, SS_EUNSUPPORTED, "interlaced window sets with complex-signal spectra");
   // the same configuration and combinations, fed from T/2 samples on
   std::vector<int> recs;
   for (const auto* list : {&p->c2, &p->c3, &p->c4})

@@ -57,6 +57,15 @@ struct ss_plan_s {
   double* seq_out = nullptr;
   long long seq_cap = 0, seq_blocks = 0;
   double* d_prev = nullptr;  // the S2/S3/S4 sums at the end of the last block
+  // complex-valued signals (App. D) and shifted S4 planes (App. E): per order
+  // (index order - 2) the operands of its combinations, their float64 sums, and
+  // each record's order and place in the caller's record list
+  std::vector<int4> cx_ops[3];
+  int4* d_cx_ops[3] = {nullptr, nullptr, nullptr};
+  double* d_cx_acc[3] = {nullptr, nullptr, nullptr};
+  size_t n_cx_acc[3] = {0, 0, 0};
+  std::vector<int> cx_order;  // order of each record, in the caller's order
+  int cx_shift = 0;
   int* d_counter = nullptr;        // work-queue counter of the pair kernels
   int FC = 0;                      // frames per staged chunk of the pair kernels
   CUtensorMap tm64{}, tm128{}, tm48{};  // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
