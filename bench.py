@@ -52,8 +52,7 @@ WORKLOADS = {
     # same shapes as the default at 1/8 of the length (profiling captures)
     "ar1q-2^25-T1024-m10": dict(channels=1, n=1 << 25, T=1024, m=10, seed=1, phi=0.9),
     # 64 independent recordings, lengths log-uniform in [2^20, 2^26], T from
-    # {128, 256, 512, 1024}, AR coefficients uniform in [0.5, 0.98], one CUDA graph;
-    # refused (REFUSED below) until the cause of its launch failure is fixed
+    # {128, 256, 512, 1024}, AR coefficients uniform in [0.5, 0.98], one CUDA graph
     "many64-2^20..2^26-m10": dict(channels=1, many=64, m=10, seed=100),
     # int16 ADC record (low-passed telegraph plus noise) streamed from page-locked
     # host memory in 256 MiB chunks; 1/16 of the 2^34-sample streamed configuration
@@ -64,11 +63,8 @@ WORKLOADS = {
     "mc4-2^26-T512-m20": dict(channels=4, n=1 << 26, T=512, m=20, seed=3, cpu_groups=2),
 }
 DEFAULT_WORKLOAD = "ar1q-2^28-T1024-m10"
-# workloads this build does not run, with the reason
-REFUSED = {
-    "many64-2^20..2^26-m10": "its last run ended in 'unspecified launch failure' at the first "
-                             "graph launch; it stays off until that cause is fixed",
-}
+# workloads this build does not run, with the reason (none at present)
+REFUSED = {}
 
 
 def dist_env():
@@ -430,6 +426,8 @@ def run_many(args, w, rank, world):
                    "T_counts": {str(t): Ts.count(t) for t in (128, 256, 512, 1024)},
                    "m": w["m"], "s4_precision": args.precision,
                    "l2": f"records of {4 * total / 2**30:.1f} GiB per step are larger than L2"},
+        "tuning": {str(t): P.ss_get_tuning(many.plan(Ts.index(t))).split(" | ")[1]
+                   for t in sorted(set(Ts))},
         "e2e": None, "gpu_launches": None, "roofline": None, "cpu_baseline": None,
         "clocks": clock_info,
     }

@@ -414,9 +414,12 @@ ss_status ss_merge_state(ss_plan_t plan, const double* src);
  *     S3[i], S4[i] and the *_err[i] (layouts as for ss_finalize of a
  *     one-channel plan; device or page-locked host memory; a NULL list or
  *     entry skips that output).  The first call captures all of it as one CUDA
- *     graph (the recordings spread over four forked streams, longest first) and
- *     launches it; later calls with the same chunks, n_samples and outputs
- *     replay the graph, other arguments capture a new one.  Synchronises the
+ *     graph (the recordings one after the other on one stream, longest first)
+ *     and launches it; later calls with the same chunks, n_samples and outputs
+ *     replay the graph, other arguments capture a new one.  ss_plan_many runs
+ *     ss_autotune on one plan of each frame length and gives its choice to the
+ *     other plans of that length (ss_get_tuning on ss_many_plan shows it).
+ *     Synchronises the
  *     stream; returns SS_ETIMEOUT if a device-side wait of any recording gave
  *     up.  The arrays are host arrays of n_rec entries.
  * ss_many_plan -- the plan of recording i (owned by the handle; ss_query,

@@ -1508,13 +1508,18 @@ ss_status ss_destroy(ss_plan_t p) {
 // Many independent recordings (single channel each, frame lengths and record
 // lengths of their own) processed as one CUDA graph: per recording ss_reset,
 // ss_accumulate of the whole record from device memory and ss_finalize into
-// device buffers, the recordings spread over kBranches forked streams so that
-// small ones overlap.  The graph is captured on the first ss_run_many and
-// replayed while the inputs and outputs stay the same.
+// device buffers, the recordings one after the other on one stream of the
+// graph (longest first), each recording's kernels in the forms the autotuner
+// chose for its frame length.  The graph is captured on the first ss_run_many
+// and replayed while the inputs and outputs stay the same.
 }  // extern "C"
 
 namespace {
-constexpr int kBranches = 4;
+// Streams the recordings are captured on.  One: every kernel sizes its
+// persistent grid for a whole GPU, which holds only when the recordings run one
+// after the other.  (Four concurrent branches ended in an unexplained launch
+// failure on the 64-recording workload; that form is not used.)
+constexpr int kBranches = 1;
 constexpr size_t kManyScratch = 6ull << 30;  // per-batch scratch of all recordings together
 thread_local std::string g_many_error;
 }  // namespace
@@ -1623,6 +1628,26 @@ ss_status ss_plan_many(ss_many_t* out, int n_rec, const int* T, const size_t* ma
   for (int i = 0; i < n_rec; ++i) mp->order[i] = i;
   std::stable_sort(mp->order.begin(), mp->order.end(),
                    [&](int a, int b) { return max_samples[a] > max_samples[b]; });
+  // the kernel forms per frame length: the autotuner on the first plan of each T,
+  // its choice applied to the other plans of that T
+  for (int i = 0; i < n_rec; ++i) {
+    int first = -1;
+    for (int j = 0; j < i && first < 0; ++j)
+      if (T[j] == T[i]) first = j;
+    ss_status st = SS_OK;
+    if (first < 0) {
+      st = ss_autotune(mp->plans[i], nullptr);
+    } else {
+      mp->plans[i]->k1_mode = mp->plans[first]->k1_mode;
+      mp->plans[i]->k2_variant = mp->plans[first]->k2_variant;
+    }
+    if (st != SS_OK) {
+      const std::string why = mp->plans[i]->err;
+      many_release(mp);
+      delete mp;
+      return many_fail(nullptr, st, "recording " + std::to_string(i) + " autotune: " + why);
+    }
+  }
   cudaError_t e = cudaEventCreateWithFlags(&mp->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mp->cap, cudaStreamNonBlocking);
   for (int b = 0; b < kBranches && e == cudaSuccess; ++b) {
