@@ -95,8 +95,9 @@ struct OperandImage {
 
 // K1 forms (the autotuner's choice per plan): groups resident in shared memory
 // within 74 KB (three CTAs per SM) when they fit, else 96 KB (kK1Auto); always
-// the 96 KB budget (kK1Resident96); one frame at a time (kK1Frames).
-enum { kK1Auto = 0, kK1Resident96 = 1, kK1Frames = 2, kK1Modes = 3 };
+// the 96 KB budget (kK1Resident96); one frame at a time (kK1Frames); resident
+// groups with a warp per frame (kK1Warp, T <= 1024 and the group within 96 KB).
+enum { kK1Auto = 0, kK1Resident96 = 1, kK1Frames = 2, kK1Warp = 3, kK1Modes = 4 };
 
 // Kernel launchers (each returns the launch status; all work on `stream`).
 cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G, int C, int T,

@@ -419,6 +419,87 @@ __device__ __forceinline__ void stockham_pass_batch(const float2* __restrict__ x
   }
 }
 
+// K1, resident forms: with the group's m coefficient rows of channel c in shared
+// memory (Xs, [m][Mp]), thread = bin: subtract the bin's group mean (the centred
+// samples of the factorised k-statistics, App. H, Eq. 85), write the centred
+// column to the spectra once, add the per-group S2 estimate to the CTA's float32
+// sums and, with an operand image, write the bin's weighted Gram products and its
+// ps value.
+template <int FMT>
+__device__ __forceinline__ void centre_resident(float2* Xs, float2* __restrict__ grow, int c, int g,
+                                                int m, int M, int Mp, const OperandImage& oi,
+                                                int ia, float* s2sum, float* s2sq, float* s1,
+                                                float pref2) {
+  const float inv_m = 1.0f / (float)m;
+  for (int k = threadIdx.x; k < Mp; k += blockDim.x) {
+    // thread = bin: centre the column in place, write it out once
+    const bool valid = k < M;
+    float2 mean = make_float2(0.f, 0.f);
+    if (valid) {
+      for (int j = 0; j < m; ++j) mean = cadd(mean, Xs[j * Mp + k]);
+      mean = make_float2(mean.x * inv_m, mean.y * inv_m);
+    }
+    if (k == 0) add_s1(s1, mean);
+    float p = 0.f, mx = 0.f;  // sum and max over j of |d_j|^2
+    for (int j = 0; j < m; ++j) {
+      const float2 d = valid ? csub(Xs[j * Mp + k], mean) : make_float2(0.f, 0.f);
+      Xs[j * Mp + k] = d;
+      grow[(long long)j * Mp + k] = d;
+      const float pj = fmaf(d.x, d.x, d.y * d.y);
+      p += pj;
+      mx = fmaxf(mx, pj);
+    }
+    if constexpr (FMT != kImageNone) {
+      const float sc = FMT == kImageGramF16 ? f16_row_scale(fmaxf(oi.sd, oi.so) * mx) : 1.f;
+      const float sd = oi.sd * sc, so = oi.so * sc;
+      // weighted Gram products of the bin in K order, read from the centred column
+      const int npair = m * (m - 1) / 2;
+      int pj = 0, pk = 1;
+      float2 dj = Xs[k];
+      constexpr int kChunkBytes = FMT == kImageGramTF32 ? 1024 : 512;  // 2 CB
+      unsigned char* rbase = static_cast<unsigned char*>(oi.img) + (size_t)c * oi.chan_bytes +
+                             (size_t)g * oi.group_bytes + (size_t)(k >> 3) * oi.rg_bytes +
+                             (k & 7) * 16;
+      for (int ch = 0; ch < oi.nkc; ++ch) {
+        float e[16];
+        if (ch < oi.ndc) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const int j = ch * 16 + t;
+            const float2 d = j < m ? Xs[j * Mp + k] : make_float2(0.f, 0.f);
+            e[t] = sd * fmaf(d.x, d.x, d.y * d.y);
+          }
+        } else {
+          const int p0 = (ch - oi.ndc) * 16;
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            if (p0 + t < npair) {
+              const float2 d2 = Xs[pk * Mp + k];
+              e[t] = so * fmaf(dj.x, d2.x, dj.y * d2.y);
+              if (++pk == m) {
+                ++pj;
+                pk = pj + 1;
+                dj = Xs[pj * Mp + k];
+              }
+            } else {
+              e[t] = 0.f;
+            }
+          }
+        }
+        write_gram_row<FMT>(rbase + ch * kChunkBytes, e);
+      }
+      float* psg = oi.ps + (long long)c * oi.chan_ps + (long long)g * oi.ps_group;
+      psg[k] = oi.sp * p * sc;
+      if (FMT == kImageGramF16) psg[Mp + k] = 1.f / sc;  // exact: a power of two
+    }
+    if (valid && ia >= 0) {
+      const float c2 = p * pref2;
+      s2sum[c * M + k] += c2;
+      s2sq[c * M + k] = fmaf(c2, c2, s2sq[c * M + k]);
+    }
+  }
+}
+
 // K1 for groups whose coefficients fit in shared memory: the group's m frames
 // are transformed FB at a time (every Stockham pass covers all FB frames, so a
 // frame costs a fraction of the barriers), the coefficients X_jk stay in shared
@@ -520,75 +601,146 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
         }
       }
       __syncthreads();  // the group's coefficients are in shared memory
-      const float inv_m = 1.0f / (float)m;
-      const int ia = s2_auto[c];
-      for (int k = threadIdx.x; k < Mp; k += blockDim.x) {
-        // thread = bin: centre the column in place, write it out once
-        const bool valid = k < M;
-        float2 mean = make_float2(0.f, 0.f);
-        if (valid) {
-          for (int j = 0; j < m; ++j) mean = cadd(mean, Xs[j * Mp + k]);
-          mean = make_float2(mean.x * inv_m, mean.y * inv_m);
-        }
-        if (k == 0) add_s1(s1s[c], mean);
-        float p = 0.f, mx = 0.f;  // sum and max over j of |d_j|^2
-        for (int j = 0; j < m; ++j) {
-          const float2 d = valid ? csub(Xs[j * Mp + k], mean) : make_float2(0.f, 0.f);
-          Xs[j * Mp + k] = d;
-          grow[(long long)j * Mp + k] = d;
-          const float pj = fmaf(d.x, d.x, d.y * d.y);
-          p += pj;
-          mx = fmaxf(mx, pj);
-        }
-        if constexpr (FMT != kImageNone) {
-          const float sc = FMT == kImageGramF16 ? f16_row_scale(fmaxf(oi.sd, oi.so) * mx) : 1.f;
-          const float sd = oi.sd * sc, so = oi.so * sc;
-          // weighted Gram products of the bin in K order, read from the centred column
-          const int npair = m * (m - 1) / 2;
-          int pj = 0, pk = 1;
-          float2 dj = Xs[k];
-          constexpr int kChunkBytes = FMT == kImageGramTF32 ? 1024 : 512;  // 2 CB
-          unsigned char* rbase = static_cast<unsigned char*>(oi.img) +
-                                 (size_t)c * oi.chan_bytes + (size_t)g * oi.group_bytes +
-                                 (size_t)(k >> 3) * oi.rg_bytes + (k & 7) * 16;
-          for (int ch = 0; ch < oi.nkc; ++ch) {
-            float e[16];
-            if (ch < oi.ndc) {
+      centre_resident<FMT>(Xs, grow, c, g, m, M, Mp, oi, s2_auto[c], s2sum, s2sq, s1s[c], pref2);
+    }
+    if (++ngroups == kMaxFp32Groups) {
+      flush_k1_sums(C, M, s2_auto, acc2, n_s2, s2sum, s2sq, s1s, acc1);
+      ngroups = 0;
+    }
+  }
+  if (ngroups) flush_k1_sums(C, M, s2_auto, acc2, n_s2, s2sum, s2sq, s1s, acc1);
+}
+
+// One Stockham pass of a warp's own frame (N points in the warp's shared buffer,
+// transformed in place): every lane first reads the inputs of its butterflies
+// (j = lane + 32 b), the warp synchronises, then each lane writes its outputs.
+// N / R <= 32 * (16 / R), i.e. N <= 512: at most 16 points per lane.
+template <int R>
+__device__ __forceinline__ void warp_stockham_pass(float2* buf, int N, int Ns,
+                                                   const float2* __restrict__ tw, int T, int lane) {
+  constexpr int kB = 16 / R;  // butterflies per lane
+  const int NR = N / R;
+  const int tw_scale = T / (Ns * R);
+  float2 v[kB][R];
 #pragma unroll
-              for (int t = 0; t < 16; ++t) {
-                const int j = ch * 16 + t;
-                const float2 d = j < m ? Xs[j * Mp + k] : make_float2(0.f, 0.f);
-                e[t] = sd * fmaf(d.x, d.x, d.y * d.y);
-              }
-            } else {
-              const int p0 = (ch - oi.ndc) * 16;
+  for (int b = 0; b < kB; ++b) {
+    const int j = lane + 32 * b;
+    if (j < NR) {
 #pragma unroll
-              for (int t = 0; t < 16; ++t) {
-                if (p0 + t < npair) {
-                  const float2 d2 = Xs[pk * Mp + k];
-                  e[t] = so * fmaf(dj.x, d2.x, dj.y * d2.y);
-                  if (++pk == m) {
-                    ++pj;
-                    pk = pj + 1;
-                    dj = Xs[pj * Mp + k];
-                  }
-                } else {
-                  e[t] = 0.f;
-                }
-              }
-            }
-            write_gram_row<FMT>(rbase + ch * kChunkBytes, e);
-          }
-          float* psg = oi.ps + (long long)c * oi.chan_ps + (long long)g * oi.ps_group;
-          psg[k] = oi.sp * p * sc;
-          if (FMT == kImageGramF16) psg[Mp + k] = 1.f / sc;  // exact: a power of two
-        }
-        if (valid && ia >= 0) {
-          const float c2 = p * pref2;
-          s2sum[c * M + k] += c2;
-          s2sq[c * M + k] = fmaf(c2, c2, s2sq[c * M + k]);
-        }
+      for (int r = 0; r < R; ++r) v[b][r] = buf[j + r * NR];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int b = 0; b < kB; ++b) {
+    const int j = lane + 32 * b;
+    if (j < NR) {
+      const int k = j & (Ns - 1);
+      if (Ns > 1) {
+        const int step = k * tw_scale;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw[r * step]);
       }
+      dft<R>(v[b]);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int q = 0; q < R; ++q) buf[base + q * Ns] = v[b][q];
+    }
+  }
+  __syncwarp();
+}
+
+// K1 with a warp per frame (T <= 1024): the group's coefficients stay resident as
+// in k1_spectra_res, but each warp windows, transforms and splits whole frames in
+// a buffer of its own, synchronising only itself (no block barrier per pass);
+// the block synchronises once per group before and after the centring.
+template <int DTYPE, int FMT>
+__global__ void __launch_bounds__(kThreadsK1, 2)
+k1_spectra_warp(SampleSource src, long long sample0, int G, int C, int T, int m, int M, int Mp,
+                const float* __restrict__ win, const float2* __restrict__ tw,
+                float2* __restrict__ spec, long long chan_stride, const int* __restrict__ s2_auto,
+                double* __restrict__ acc2, int n_s2, float pref2, OperandImage oi,
+                double* __restrict__ acc1) {
+  extern __shared__ float4 smem_raw[];
+  const int N = T / 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kThreadsK1 / 32;
+  float2* Xs = reinterpret_cast<float2*>(smem_raw);  // [m][Mp]
+  float2* bufs = Xs + m * Mp;                         // [kWarps][N]
+  float2* tws = bufs + kWarps * N;                    // [T] twiddles e^{+2 pi j a/T}
+  float* wins = reinterpret_cast<float*>(tws + T);   // [T] window / sqrt(sum g^2)
+  float* s2sum = wins + T;                            // [C][M]
+  float* s2sq = s2sum + C * M;                        // [C][M]
+  float2* buf = bufs + warp * N;
+  constexpr int kVec = DTYPE == SS_F32 ? 16 : 8;       // bytes per vector load (4 samples)
+
+  __shared__ float s1s[4][4];  // per channel: sums of Re, Im, Re^2, Im^2 of S1 (thread 0)
+  for (int i = threadIdx.x; i < 2 * C * M; i += blockDim.x) s2sum[i] = 0.f;
+  if (threadIdx.x < 16) s1s[threadIdx.x >> 2][threadIdx.x & 3] = 0.f;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    tws[i] = __ldg(&tw[i]);
+    wins[i] = __ldg(&win[i]);
+  }
+  __syncthreads();
+
+  int ngroups = 0;  // groups in the float32 sums since the last flush
+  for (int g = blockIdx.x; g < G; g += gridDim.x) {
+    for (int c = 0; c < C; ++c) {
+      float2* grow = spec + (long long)c * chan_stride + (long long)g * m * Mp;
+      for (int j = warp; j < m; j += kWarps) {
+        // the frame's samples times the window, packed as N complex points
+        const long long s0 = sample0 + ((long long)g * m + j) * T;
+        const long long off = s0 - src.carry_n;
+        const char* cbase = static_cast<const char*>(src.chunk) +
+                            ((long long)c * src.chunk_stride + off) * (DTYPE == SS_F32 ? 4 : 2);
+        if (off >= 0 && ((uintptr_t)cbase % kVec) == 0) {
+          for (int q = lane; q < T / 4; q += 32) {
+            float x0, x1, x2, x3;
+            if constexpr (DTYPE == SS_F32) {
+              const float4 v = __ldg(reinterpret_cast<const float4*>(cbase) + q);
+              x0 = v.x; x1 = v.y; x2 = v.z; x3 = v.w;
+            } else {
+              const short4 v = __ldg(reinterpret_cast<const short4*>(cbase) + q);
+              x0 = v.x; x1 = v.y; x2 = v.z; x3 = v.w;
+            }
+            const float4 w = *reinterpret_cast<const float4*>(wins + 4 * q);
+            buf[2 * q] = make_float2(x0 * w.x, x1 * w.y);
+            buf[2 * q + 1] = make_float2(x2 * w.z, x3 * w.w);
+          }
+        } else {
+          for (int n = lane; n < N; n += 32)
+            buf[n] = make_float2(load_sample<DTYPE>(src, c, s0 + 2 * n) * wins[2 * n],
+                                 load_sample<DTYPE>(src, c, s0 + 2 * n + 1) * wins[2 * n + 1]);
+        }
+        __syncwarp();
+        int Ns = 1, rem = N;
+        while (rem > 1) {
+          if (rem % 8 == 0 && rem != 16) {
+            warp_stockham_pass<8>(buf, N, Ns, tws, T, lane);
+            Ns *= 8; rem /= 8;
+          } else if (rem % 4 == 0) {
+            warp_stockham_pass<4>(buf, N, Ns, tws, T, lane);
+            Ns *= 4; rem /= 4;
+          } else {
+            warp_stockham_pass<2>(buf, N, Ns, tws, T, lane);
+            Ns *= 2; rem /= 2;
+          }
+        }
+        // X_k = 1/2 [(Y_k + Y*_{N-k}) - j w^k (Y_k - Y*_{N-k})], w = e^{+2 pi j/T}
+        float2* xr = Xs + j * Mp;
+        for (int k = lane; k < M; k += 32) {
+          const float2 yk = buf[k == N ? 0 : k];
+          const float2 yr = buf[k == 0 ? 0 : N - k];
+          const float2 yc = make_float2(yr.x, -yr.y);
+          const float2 sm = cadd(yk, yc);
+          const float2 wd = cmul(tws[k], csub(yk, yc));
+          xr[k] = make_float2(0.5f * (sm.x + wd.y), 0.5f * (sm.y - wd.x));
+        }
+        __syncwarp();  // the buffer is free for the warp's next frame
+      }
+      __syncthreads();  // the group's coefficients are in shared memory
+      centre_resident<FMT>(Xs, grow, c, g, m, M, Mp, oi, s2_auto[c], s2sum, s2sq, s1s[c], pref2);
+      __syncthreads();  // Xs is free for the next channel or group
     }
     if (++ngroups == kMaxFp32Groups) {
       flush_k1_sums(C, M, s2_auto, acc2, n_s2, s2sum, s2sq, s1s, acc1);
@@ -657,6 +809,27 @@ cudaError_t set_smem_limit(Kern kern, size_t limit) {
                               cudaSharedmemCarveoutMaxShared);
 }
 
+// resident CTAs per SM of a K1 kernel with `smem` bytes of dynamic shared memory,
+// from its own registers and shared memory (one wave is launched)
+template <typename Kern>
+cudaError_t k1_occupancy(Kern kern, size_t smem, int* occ) {
+  int dev = 0, sm_smem = 0, sm_regs = 0, rsv = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e != cudaSuccess) return e;
+  const int by_smem = sm_smem / (int)(smem + fa.sharedSizeBytes + rsv);
+  const int by_regs = sm_regs / std::max(1, ((fa.numRegs + 7) & ~7) * kThreadsK1);
+  *occ = std::max(1, std::min(std::min(by_smem, by_regs), 2048 / kThreadsK1));
+  return cudaSuccess;
+}
+
 template <int DTYPE, int FMT>
 cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C, int T, int m,
                         int M, int Mp, const float* win, const float2* tw, float2* spec,
@@ -670,6 +843,27 @@ cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C
   // kK1Auto: three CTAs per SM with a smaller batch of frames beat two with a
   // larger one (T = 1024, m = 10: 2.59 vs 2.69 ms per step), else the 96 KB
   // budget; kK1Resident96: the 96 KB budget; kK1Frames: frame at a time
+  // a warp per frame: the group's coefficients, a buffer of T/2 points per warp;
+  // shapes it does not take (T > 1024, or a group beyond 96 KB) use kK1Auto
+  const size_t wsmem = fixed + (size_t)(kThreadsK1 / 32) * (T / 2) * sizeof(float2);
+  if (mode == kK1Warp && (T > 1024 || wsmem > kK1ResidentBytes)) mode = kK1Auto;
+  if (mode == kK1Warp) {
+    auto kern = k1_spectra_warp<DTYPE, FMT>;
+    cudaError_t e = set_smem_limit(kern, kK1ResidentBytes);
+    if (e != cudaSuccess) return e;
+    int occ = 1;
+    e = k1_occupancy(kern, wsmem, &occ);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 1;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int rgrid = std::max(1, std::min(G, nsm * occ));
+    kern<<<rgrid, kThreadsK1, wsmem, stream>>>(src, sample0, G, C, T, m, M, Mp, win, tw, spec,
+                                               spec_chan_stride, s2_auto, acc2, n_s2, pref2, oi,
+                                               acc1);
+    return cudaGetLastError();
+  }
   const size_t budget = mode == kK1Frames ? 0
                         : (mode == kK1Auto && fixed + per_frame <= kK1ResidentBytes3)
                             ? kK1ResidentBytes3
@@ -719,7 +913,7 @@ cudaError_t launch_k1_spectra(const SampleSource& src, long long sample0, int G,
                               double* acc2, int n_s2, float pref2, int grid, cudaStream_t stream,
                               const OperandImage& oi, double* acc1, int mode) {
   if (G <= 0) return cudaSuccess;
-  if (mode < kK1Auto || mode > kK1Frames) return cudaErrorInvalidValue;
+  if (mode < kK1Auto || mode >= kK1Modes) return cudaErrorInvalidValue;
   const size_t smem = k1_smem(T, C);
   if (grid > G) grid = G;
   const bool f32 = src.dtype == SS_F32;

@@ -26,7 +26,7 @@ using namespace ss;
 
 namespace {
 
-const char* const kK1Names[kK1Modes] = {"auto", "r96", "frames"};
+const char* const kK1Names[kK1Modes] = {"auto", "r96", "frames", "warp"};
 const char* const kK2Names[kK2Variants] = {"44", "84s2", "84s3"};
 
 // Gaussian noise (counter-based: SplitMix64 of the element index, Box-Muller),
@@ -198,6 +198,10 @@ ss_status ss_autotune(ss_plan_t p, double* best_ms) {
       *slot = v;
       float t = 0.f, tmin = 1e30f;
       ss_status s = time_pass(p, rec, n, e0, e1, &t);
+      if (s == SS_ECUDA && !p->broken) {  // a form this plan's shapes cannot take
+        cudaGetLastError();
+        continue;
+      }
       for (int r = 0; r < 3 && s == SS_OK; ++r) {
         s = time_pass(p, rec, n, e0, e1, &t);
         tmin = std::min(tmin, t);

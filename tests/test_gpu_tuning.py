@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL, TOL_ERR = 1e-5, 1e-4
-K1_FORMS = ["auto", "r96", "frames"]
+K1_FORMS = ["auto", "r96", "frames", "warp"]
 K2_FORMS = ["44", "84s2", "84s3"]
 
 
@@ -69,7 +69,8 @@ def test_k2_forms_several_channels(k2):
 
 
 @pytest.mark.parametrize("k1", K1_FORMS)
-@pytest.mark.parametrize("T,m,G", [(256, 10, 40), (1024, 10, 6), (4096, 4, 3), (16, 300, 4)])
+@pytest.mark.parametrize("T,m,G", [(256, 10, 40), (1024, 10, 6), (4096, 4, 3), (16, 300, 4),
+                                   (8, 5, 30), (512, 20, 5)])
 def test_k1_forms_match_the_oracle(T, m, G, k1):
     z = synth.ar1_quadratic(T * m * G + 5, seed=3 * T + m)
     ref = oracle.polyspectra(z, T, 1.0, m, orders=(2, 4), group_chunk=8)
