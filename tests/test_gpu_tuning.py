@@ -1,6 +1,6 @@
 """The autotuner and every kernel form it chooses between.
 
-Each K1 form (resident groups in 74 KB or 96 KB, frame at a time) and each K2
+Each K1 form (resident groups in 74 KB or 96 KB, a warp per frame, frame at a time) and each K2
 tiling (4 x 4 micro-tiles, 8 x 4 micro-tiles with two or three stages) must give
 the oracle's spectra; ss_autotune must leave a plan that does; the tuning text
 round-trips and refuses a plan of another configuration.
