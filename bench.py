@@ -52,7 +52,8 @@ WORKLOADS = {
     # same shapes as the default at 1/8 of the length (profiling captures)
     "ar1q-2^25-T1024-m10": dict(channels=1, n=1 << 25, T=1024, m=10, seed=1, phi=0.9),
     # 64 independent recordings, lengths log-uniform in [2^20, 2^26], T from
-    # {128, 256, 512, 1024}, AR coefficients uniform in [0.5, 0.98], one CUDA graph
+    # {128, 256, 512, 1024}, AR coefficients uniform in [0.5, 0.98], one CUDA graph;
+    # refused (REFUSED below)
     "many64-2^20..2^26-m10": dict(channels=1, many=64, m=10, seed=100),
     # int16 ADC record (low-passed telegraph plus noise) streamed from page-locked
     # host memory in 256 MiB chunks; 1/16 of the 2^34-sample streamed configuration
@@ -63,8 +64,13 @@ WORKLOADS = {
     "mc4-2^26-T512-m20": dict(channels=4, n=1 << 26, T=512, m=20, seed=3, cpu_groups=2),
 }
 DEFAULT_WORKLOAD = "ar1q-2^28-T1024-m10"
-# workloads this build does not run, with the reason (none at present)
-REFUSED = {}
+# workloads this build does not run, with the reason
+REFUSED = {
+    "many64-2^20..2^26-m10": "its runs ended in a fault (first an 'unspecified launch failure' "
+                             "at the first graph launch with four concurrent branches, then a "
+                             "host segfault with GPU Xid 43 with one stream); the cause is not "
+                             "found, so it stays off",
+}
 
 
 def dist_env():
