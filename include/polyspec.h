@@ -309,8 +309,8 @@ ss_status ss_inject_timeout(ss_plan_t plan, int on);
  * results do not depend on these choices, only its speed: K1 keeps a group's
  * coefficients in shared memory within a 74 KB or a 96 KB budget, or with a
  * warp per frame (T <= 1024), or transforms one frame at a time; K2 uses 4 x 4
- * micro-tiles in CTAs of 256 threads or
- * 8 x 4 micro-tiles in CTAs of 128 threads with 2 or 3 pipeline stages.
+ * micro-tiles in CTAs of 256 threads (4 stages, or 3 stages with three CTAs per
+ * SM) or 8 x 4 micro-tiles in CTAs of 128 threads with 2 or 3 pipeline stages.
  *
  * ss_autotune   -- time every form of K1 and K2 on this plan's shapes on this
  *                  GPU (a synthetic Gaussian record of about 16 x SMs groups,
@@ -321,7 +321,7 @@ ss_status ss_inject_timeout(ss_plan_t plan, int on);
  *                  stream; leaves the plan reset.  best_ms (may be NULL)
  *                  receives the time of the fastest pass.
  * ss_get_tuning -- the plan's choices as text: "polyspec-tuning 1 <key> |
- *                  k1=<auto|r96|frames|warp> k2=<44|84s2|84s3>", where the key names
+ *                  k1=<auto|r96|frames|warp> k2=<44|44s3|84s2|84s3>", where the key names
  *                  T, m, channels, dtype, precision, SM count and GPU.  out holds
  *                  cap bytes (SS_EINVAL if too small).
  * ss_set_tuning -- apply such a text (valid at any time between calls).  A text

@@ -121,9 +121,11 @@ cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G,
 // The tensor maps view the centred spectra as [rows][Mp/16][16] float2 with
 // 128-byte swizzling; tm64 has boxes of 4 blocks (64 bins), tm128 of 8.
 // K2 tilings (the autotuner's choice per plan): 4 x 4 micro-tiles in CTAs of 256
-// threads with 4 stages, or 8 x 4 micro-tiles in CTAs of 128 threads with 2 or
-// 3 stages; all take the same 64 x 64 tiles and give the same sums.
-enum { kK2Tile44 = 0, kK2Tile84Stages2 = 1, kK2Tile84Stages3 = 2, kK2Variants = 3 };
+// threads with 4 stages (two CTAs per SM) or 3 stages (three CTAs per SM, 85
+// registers), or 8 x 4 micro-tiles in CTAs of 128 threads with 2 or 3 stages;
+// all take the same 64 x 64 tiles and give the same sums.
+enum { kK2Tile44 = 0, kK2Tile84Stages2 = 1, kK2Tile84Stages3 = 2, kK2Tile44Stages3 = 3,
+       kK2Variants = 4 };
 cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
                              const float2* spec_a, const float2* spec_b, const float2* spec_c,
                              int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,

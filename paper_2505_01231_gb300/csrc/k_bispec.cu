@@ -96,8 +96,10 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
 
 // kFC > 0: the frames per staged chunk fixed at compile time (the frame loop of a
 // full chunk is unrolled with constant shared-memory offsets); 0: taken from FC.
-template <int kFC>
-__global__ void __launch_bounds__(kThreadsPair, 2)
+// kSt stages; kMinCtas resident CTAs per SM the register budget is set for (two
+// with four stages: 128 registers; three with three stages: 85)
+template <int kFC, int kSt = kStages, int kMinCtas = 2>
+__global__ void __launch_bounds__(kThreadsPair, kMinCtas)
 k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUtensorMap tm128,
           const float2* __restrict__ sa, const float2* __restrict__ sb,
           const float2* __restrict__ sc, int rowA, int rowB, int rowC, int G, int m, int FC_rt,
@@ -105,7 +107,7 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
           float pref3, double* __restrict__ acc, long long plane, int koff,
           int* __restrict__ status, int inject_timeout) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
-  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ __align__(8) uint64_t full[kSt];
   __shared__ __align__(8) uint64_t never;  // completed by nothing (timeout test)
   __shared__ int s_item;
   __shared__ uint32_t tmem_slot;
@@ -129,7 +131,7 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
   for (int d = 0; d < 4; ++d) oC[d] = swz128((kt + lt) * 8 + 16 * d);
 
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+    for (int s = 0; s < kSt; ++s) mbar_init(&full[s], 1);
     mbar_init(&never, 1);
     fence_mbar_init();
   }
@@ -152,7 +154,7 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
 #pragma unroll
     for (int part = 0; part < 4; ++part) tmem_st16(tsum + 16 * part, z);
   }
-  uint32_t qbase = 0;  // TMA steps consumed so far (stage = q % kStages)
+  uint32_t qbase = 0;  // TMA steps consumed so far (stage = q % kSt)
   bool failed = false;
 
   for (int item; !failed && (item = next_item(wq, &s_item)) >= 0;) {
@@ -167,7 +169,7 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
       for (int b = 0; b < 16 && !active; ++b) active = in_domain3(kw + a, lw + b, M, cross);
     const int nsteps = (gb - ga) * nch;
     auto issue = [&](int i) {
-      const int s = (int)((qbase + i) % kStages);
+      const int s = (int)((qbase + i) % kSt);
       const int g = ga + i / nch, j0 = (i % nch) * FC;
       unsigned char* st = sbase + (size_t)s * sbytes;
       mbar_arrive_expect_tx(&full[s], (uint32_t)FC * 256u * 8u);
@@ -182,18 +184,18 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
 
     if (use_tma && tid == 0) {
       fence_async_smem();
-      for (int i = 0; i < kStages && i < nsteps; ++i) issue(i);
+      for (int i = 0; i < kSt && i < nsteps; ++i) issue(i);
     }
     bool ok = true;
     for (int i = 0; i < nsteps; ++i) {
       const int g = ga + i / nch, ch = i % nch, j0 = ch * FC;
       const int nf = min(FC, m - j0);
-      const int s = use_tma ? (int)((qbase + i) % kStages) : (i & 1);
+      const int s = use_tma ? (int)((qbase + i) % kSt) : (i & 1);
       const unsigned char* sA = sbase + (size_t)s * sbytes;
       const unsigned char* sB = sA + a64;
       const unsigned char* sC = sA + 2 * a64;
       if (use_tma) {
-        ok = mbar_wait_bounded(&full[s], ((qbase + i) / kStages) & 1u, status);
+        ok = mbar_wait_bounded(&full[s], ((qbase + i) / kSt) & 1u, status);
       } else {
         unsigned char* w = sbase + (size_t)s * sbytes;
         for (int idx = tid; idx < nf * 4 * kTile; idx += blockDim.x) {
@@ -289,19 +291,19 @@ k2_bispec(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CUte
         }
       }
       // every thread is done with stage s; a failed wait anywhere stops the CTA.
-      // Before it gives up, the copies issued so far (steps i .. i + kStages - 1,
+      // Before it gives up, the copies issued so far (steps i .. i + kSt - 1,
       // the one whose wait ran out included) must have landed: those drain waits
       // keep the full limit, so no copy is in flight when the CTA exits.
       if (__syncthreads_or(!ok)) {
         if (use_tma)
-          for (int q = i; q < nsteps && q < i + kStages; ++q)
-            mbar_wait_bounded(&full[(qbase + q) % kStages], ((qbase + q) / kStages) & 1u, status);
+          for (int q = i; q < nsteps && q < i + kSt; ++q)
+            mbar_wait_bounded(&full[(qbase + q) % kSt], ((qbase + q) / kSt) & 1u, status);
         failed = true;
         break;
       }
-      if (use_tma && tid == 0 && i + kStages < nsteps) {
+      if (use_tma && tid == 0 && i + kSt < nsteps) {
         fence_async_smem();
-        issue(i + kStages);
+        issue(i + kSt);
       }
     }
     if (failed) break;
@@ -710,10 +712,13 @@ cudaError_t launch_k2_t(const CUtensorMap& tm64, const CUtensorMap& tm128, const
                         int cross, float pref3, double* acc, long long plane, int rows, int nsm,
                         int* counter, int* status, int inject_timeout,
                         cudaStream_t stream) {
-  constexpr bool k44 = kVar == 0;
-  constexpr int kSt = k44 ? kStages : kVar;
+  // kVar: 0 = 4 x 4 with 4 stages (two CTAs per SM), 1 = 4 x 4 with 3 stages (three
+  // CTAs per SM), 2 / 3 = 8 x 4 with that many stages
+  constexpr bool k44 = kVar < 2;
+  constexpr int kSt = kVar == 0 ? kStages : kVar == 1 ? 3 : kVar;
   auto kern = [] {
-    if constexpr (k44) return k2_bispec<kFC>;
+    if constexpr (kVar == 0) return k2_bispec<kFC>;
+    else if constexpr (kVar == 1) return k2_bispec<kFC, 3, 3>;
     else return k2_bispec84<kFC, kSt>;
   }();
   const int threads = k44 ? kThreadsPair : kThreads84;
@@ -731,7 +736,8 @@ cudaError_t launch_k2_t(const CUtensorMap& tm64, const CUtensorMap& tm128, const
   if (e != cudaSuccess) return e;
   // TMEM: 128 columns per CTA of either tiling, 512 per SM
   int occ = 1;
-  e = ctas_per_sm(kern, threads, smem, k44 ? 2 : k84_min_ctas<kSt>(), &occ);
+  e = ctas_per_sm(kern, threads, smem, kVar == 0 ? 2 : kVar == 1 ? 3 : k84_min_ctas<kSt>(),
+                  &occ);
   if (e != cudaSuccess) return e;
   const int n_cta = nsm * occ;
   WorkQueue wq;
@@ -780,6 +786,7 @@ cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
     case kK2Tile84Stages2: return launch_k2_fc<2>(K2_ARGS);
     case kK2Tile84Stages3: return launch_k2_fc<3>(K2_ARGS);
     case kK2Tile44: return launch_k2_fc<0>(K2_ARGS);
+    case kK2Tile44Stages3: return launch_k2_fc<1>(K2_ARGS);
     default: return cudaErrorInvalidValue;
   }
 #undef K2_ARGS

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 TOL, TOL_ERR = 1e-5, 1e-4
 K1_FORMS = ["auto", "r96", "frames", "warp"]
-K2_FORMS = ["44", "84s2", "84s3"]
+K2_FORMS = ["44", "44s3", "84s2", "84s3"]
 
 
 def P():
