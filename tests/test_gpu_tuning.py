@@ -74,7 +74,10 @@ def test_k2_forms_several_channels(k2):
 def test_k1_forms_match_the_oracle(T, m, G, k1):
     z = synth.ar1_quadratic(T * m * G + 5, seed=3 * T + m)
     ref = oracle.polyspectra(z, T, 1.0, m, orders=(2, 4), group_chunk=8)
-    out = run(z, T, m, f"k1={k1}", orders=(2, 4), precision="tf32x3" if m <= 32 else "fp32")
+    # the operand image of the tensor-core S4 is part of K1: written in TF32x3 at the
+    # larger T (at T = 8 the split modes stay above 1e-5 of the S4 peak, see the
+    # tensor-core size tests), FP32 otherwise
+    out = run(z, T, m, f"k1={k1}", orders=(2, 4), precision="tf32x3" if T >= 256 else "fp32")
     for key in ("S2", "S4"):
         a = out[key][0].reshape(ref[key].shape)
         assert close(a, ref[key], TOL), key
