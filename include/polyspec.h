@@ -219,6 +219,9 @@ ss_status ss_set_estimator(ss_plan_t plan, int estimator);
  *   frame, so the middle of one window set covers the edges of the other) and
  *   pools the groups of both window sets in every estimate and error bar; with
  *   as many groups in each set, the estimate is the average of the two spectra.
+ *   The error bar (Eq. 35-36) treats all pooled groups as independent parts,
+ *   which the overlapping windows of the two sets are not quite: it is somewhat
+ *   optimistic.
  *   Doubles the work and the device memory.  Valid only before the first
  *   ss_accumulate (or after ss_reset); SS_ESTATE otherwise.  ss_query reports
  *   the pooled groups; ss_export_state writes the pooled sums.
