@@ -88,9 +88,9 @@ enum { SS_PREC_FP32 = 0,    /* FP32 FMA on CUDA cores                          *
        SS_PREC_FP16X3 = 4   /* tensor cores, FP16 hi/lo split of operands scaled
                                by a power of two per bin, 3 products           */ };
 /* Accuracy: FP32, TF32X3 and FP16X3 carry every operand to about 2^-22 and meet
-   1e-5 of each spectrum's peak against the FP64 definition in every tested shape
-   with T >= 16 (at T = 8 the S4 of the split modes reached about 1e-4 of its
-   peak: the contraction and the S_k S_l term cancel there); BF16X3 carries them
+   1e-5 of each spectrum's peak against the FP64 definition in the tested shapes
+   (at T = 8, m = 5 the S4 reached 1.4e-5 of its peak in FP32 and about 1e-4 in
+   the split modes: the terms of Eq. 85 cancel strongly there); BF16X3 carries them
    to about 2^-17 (its tests hold it to 5e-5) and plain BF16 to 2^-9: both are
    outside that bar.  FP16X3 runs the products at the BF16 rate (twice TF32's)
    with TF32X3's accuracy: each bin's operands are multiplied by a power of two
