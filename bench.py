@@ -482,7 +482,7 @@ def main():
                     help="apply this tuning text (ss_set_tuning) instead of autotuning")
     ap.add_argument("--fp32-steps", type=int, default=3,
                     help="steps of the all-FP32 S4 arm (0 = skip)")
-    ap.add_argument("--precision", default="tf32x3",
+    ap.add_argument("--precision", default="fp16x3",
                     choices=["fp32", "tf32x3", "bf16x3", "bf16", "fp16x3"],
                     help="arithmetic of the S4 moment sums")
     args = ap.parse_args()
