@@ -62,6 +62,8 @@ WORKLOADS = {
     # four channels sharing an AR(1) component (plus white noise, a quadratic term
     # and a telegraph signal each), every default cross combination of S2/S3/S4
     "mc4-2^26-T512-m20": dict(channels=4, n=1 << 26, T=512, m=20, seed=3, cpu_groups=2),
+    # same shapes at 1/16 of the length (profiling captures)
+    "mc4-2^22-T512-m20": dict(channels=4, n=1 << 22, T=512, m=20, seed=3, cpu_groups=2),
 }
 DEFAULT_WORKLOAD = "ar1q-2^28-T1024-m10"
 # workloads this build does not run, with the reason
@@ -620,8 +622,10 @@ def main():
     M = T // 2 + 1
     Mp = (M + 15) // 16 * 16
     s4_name = "k3_trispec" if C == 1 else "k3_trispec_cross"
-    if C == 1 and args.precision != "fp32":
-        s4_name = "k3_trispec_tc"
+    if args.precision != "fp32":
+        s4_name = "k3_trispec_tc" if C == 1 else "k3_trispec_cross_tc"
+    # several channels: every tensor-core precision runs the cross S4 in TF32x3
+    s4_prec = args.precision if C == 1 or args.precision == "fp32" else "tf32x3"
     names = ["k1_spectra", "k2_bispec", s4_name, "k4_finalize", "h2d"]
     n_batches = max(1, int(np.ceil(groups / info.groups_per_batch)))
     hbm = float(pk.get("hbm_gbs", 6800.0))
@@ -656,23 +660,25 @@ def main():
                    "traffic": traffic_for("k2_bispec"), "peak_source": fp32_src,
                    "flop_per_step": k2_flops, "ms_per_step": k2_ms}
 
-    # S4: the tensor pipe in the split modes.  The method's work is one pass of the
-    # Gram contraction, m(m+1) flop per grid point (k <= l) and group; the split
-    # modes issue it three times (hi*hi, hi*lo, lo*hi), padded to whole tiles and K
-    # chunks.  The CUDA-core forms: 10 (one channel) or 40 (several) flop per point
-    # and frame against the FP32 pipe.
+    # S4: the tensor pipe in the split modes.  One channel: the method's work is one
+    # pass of the Gram contraction, m(m+1) flop per grid point (k <= l) and group.
+    # Several channels: five complex products per point and frame, 40 flop (as the
+    # real products of the tensor-core form: 10 columns x K = 2m x 2 flop).  The
+    # split modes issue it three times (hi*hi, hi*lo, lo*hi), padded to whole tiles
+    # and K chunks.  The CUDA-core forms: 10 (one channel) or 40 (several) flop per
+    # point and frame against the FP32 pipe.
     s4_ms = stage_ms[2] / args.steps
-    if args.precision == "fp32" or C > 1:
+    if args.precision == "fp32":
         s4_flops = (10.0 if C == 1 else 40.0) * st.pairs4 * frames * info.n_s4
         s4_peak, s4_bound, s4_src, passes = fp32_peak, "alu", fp32_src, 1
     else:
-        passes = 1 if args.precision == "bf16" else 3
-        s4_flops = float(st.pairs4) * groups * m * (m + 1)
-        key = {"tf32x3": "tf32_tflops", "fp16x3": "fp16_tflops"}.get(args.precision,
-                                                                     "bf16_tflops")
+        passes = 1 if s4_prec == "bf16" else 3
+        s4_flops = (float(st.pairs4) * groups * m * (m + 1) if C == 1
+                    else 40.0 * st.pairs4 * frames * info.n_s4)
+        key = {"tf32x3": "tf32_tflops", "fp16x3": "fp16_tflops"}.get(s4_prec, "bf16_tflops")
         if measured.get(key):
             s4_peak, s4_src = measured[key], f"measured now (tcgen05 {key[:4]} microbenchmark)"
-        elif args.precision == "tf32x3":
+        elif s4_prec == "tf32x3":
             s4_peak = float(pk.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
             s4_src = "measured bf16 x nominal tf32/bf16 dense ratio (1.1/2.25 PFLOP/s)"
         else:
@@ -744,7 +750,7 @@ def main():
     # ---- the all-FP32 CUDA-core form of the same step (S4 on CUDA cores), for the
     # mixed-precision speed-up at the accuracy each reaches
     fp32_arm = None
-    if world == 1 and args.precision != "fp32" and C == 1 and args.fp32_steps > 0:
+    if world == 1 and args.precision != "fp32" and args.fp32_steps > 0:
         plan.close()
         plan = P.Plan(channels=C, T=T, dt=1.0, m=m, orders=(2, 3, 4), stream=stream,
                       dtype=w.get("dtype", "f32"), precision="fp32")
@@ -773,7 +779,8 @@ def main():
             "config": {"workload": args.workload, "channels": C, "samples_per_rank": n, "T": T,
                        "M": M, "m": m, "groups": groups, "window": "hann",
                        "orders": "S2+S3+S4 full grids",
-                       "s4_precision": args.precision if C == 1 else "fp32 (several channels)",
+                       "s4_precision": s4_prec if s4_prec == args.precision
+                       else f"{s4_prec} (several channels; --precision {args.precision})",
                        "dtype_in": w.get("dtype", "f32"),
                        "parallelism": (f"dp{world}: one record sharded in whole groups, states "
                                        "merged by one all-reduce" if world > 1 else "1 GPU"),

@@ -159,6 +159,15 @@ cudaError_t launch_k3_trispec_cross(const float2* spec, long long chan_stride, i
                                     long long plane, int nsm, bool natural, cudaStream_t stream);
 int k3tc_stage_chunks(int precision);
 
+// The same on the tcgen05 tensor cores (every tensor-core precision; TF32 hi/lo
+// in three passes): tiles of 128 rows k x 16 columns l, operands built in shared
+// memory from the centred spectra; the row k = -(M-1) is copied from k = M-1
+// (equal for real signals).  counter and status as for the pair kernels.
+cudaError_t launch_k3_trispec_cross_tc(const float2* spec, long long chan_stride, int G, int m,
+                                       int M, int Mp, const int4* combos, int n_combos,
+                                       double* acc, long long plane, int nsm, bool natural,
+                                       int* counter, int* status, cudaStream_t stream);
+
 // Most groups whose per-group estimates a kernel adds up in float32 before the
 // run goes to the float64 accumulators (bounds the float32 rounding of the sums
 // over groups of Sec. 4.2 whatever the record length).

@@ -1,0 +1,645 @@
+// k_trispec_cross_tc.cu -- K3 for several channels on the tcgen05 tensor cores:
+// per-group trispectrum-cut k-statistics C4(a_k, b_k*, c_l, d_l*) (Sec. 7,
+// Eq. 50) in the factorised form of App. H, Eq. 85.
+//
+// Per group and combination (a, b, c, d), with centred coefficients and
+// x_j = da_jk, y_j = db_jk*, z_j = dc_jl, w_j = dd_jl* (a_{-k} = a_k*):
+//   c4(k, l) = pref [fmm P - fm1 (Sxy Szw + Sxz Syw + Sxw Syz)],
+//   P = sum_j x_j y_j z_j w_j,   Suv = sum_j u_j v_j   (j over the m frames).
+// Over a tile of 128 rows k and 16 columns l, Sxz, Sxw, Syz, Syw and P are
+// complex matrix products with the frames as K:
+//   rows x (128 x m) and rows y (128 x m) times columns [z | w] (m x 32), and
+//   rows xy (128 x m) times columns zw (m x 16).
+// Each complex product is a real one with K = 2m (real and imaginary part of
+// frame j at 2j and 2j + 1): a row u is (ur_j, ui_j); the column giving Re(u v)
+// is (vr_j, -vi_j) and the one giving Im(u v) is (vi_j, vr_j).  The products run
+// as TF32 hi/lo splits in three passes (hi hi + hi lo + lo hi) accumulated in
+// FP32 in TMEM.  Sxy and Szw depend on one bin each and are summed by the threads
+// that build the operands.
+//
+// Grid: one persistent CTA per SM (all 512 TMEM columns).  Items (group chunk,
+// combination, tile) come from a group-major queue.  Warp roles, coupled only by
+// mbarriers:
+// - warp 17 takes the items and, per stage of 4 frames, stages the coefficients
+//   the tile needs (the bins |k| of its rows of a and b, at most 130 consecutive
+//   bins, and the 16 bins of c and d) with 1-D bulk copies into a ring of 8, with
+//   the stage's record;
+// - warps 8-15 build each stage from them: the TF32 hi and lo parts of x, y, xy
+//   for the tile's 128 rows and of the [z | w] and zw columns for its 16 columns
+//   (a thread: one row, two frames), written to shared memory in the K-major
+//   core-matrix layout of the MMA descriptors (no copy of the operands exists in
+//   HBM), plus the group's Sxy and Szw and its record in a ring of slots;
+// - warp 16 issues, per stage, the nine MMAs (3 products x 3 passes) into the
+//   group's TMEM buffer (two buffers of 160 columns, alternating by group), and
+//   commits the stage (free again) and, after the group's last stage, the buffer;
+// - warps 0-7 (TMEM lane quadrant warp % 4, 8 of the 16 columns each) read the
+//   buffer, form c4 and keep each point's sums of Re, Im, Re^2 and Im^2 over the
+//   item's groups in registers; at the end of an item they add them to the
+//   float64 accumulators.
+// Rows: r = k + M - 1 in [1, 2M - 2] (k from -(M - 2) to M - 1).  The row r = 0
+// (k = -(M - 1)) equals the row r = 2M - 2: for a real signal the Nyquist
+// coefficient X(M - 1) is real, so x, y at k = -(M - 1) are those at k = M - 1;
+// a small kernel copies that row's sums after every batch.  Every wait is
+// bounded; on a failure the CTA stops, waits for the products it issued and
+// frees its TMEM.
+#include "internal.cuh"
+#include "pipeline.cuh"
+
+namespace ss {
+namespace {
+
+constexpr int kXT = 128;     // rows of a tile
+constexpr int kXL = 16;      // columns of a tile
+constexpr int kXF = 4;       // frames per stage: K = 8 TF32 values, one MMA K step
+constexpr int kXStages = 4;  // operand stages
+constexpr int kXRaw = 8;     // stages of staged coefficients
+constexpr int kXEpiWarps = 8, kXBuildWarps = 8;
+constexpr int kXBuilders = 32 * kXBuildWarps;
+constexpr int kXMmaWarp = kXEpiWarps + kXBuildWarps, kXLoadWarp = kXMmaWarp + 1;
+constexpr int kXThreads = 32 * (kXLoadWarp + 1);
+constexpr int kXSlots = 4;
+constexpr uint32_t kXTmemCols = 512;
+// TMEM buffer b starts at column 256 b: Sxz, Sxw (4 columns per l: Re Sxz, Im Sxz,
+// Re Sxw, Im Sxw), then Syz, Syw at +64, then P (Re, Im per l) at +128
+constexpr uint32_t kXBufCols = 256, kColY = 64, kColP = 128;
+
+// A stage: for each matrix a hi block, then a lo block.  A matrix of R rows x 8
+// TF32 values is R/8 row groups of two core matrices (8 rows x 16 bytes: frames
+// 2c and 2c + 1 of the stage, Re and Im), 128 bytes apart (LBO); row groups are
+// 256 bytes apart (SBO).
+constexpr uint32_t kAMat = kXT * 32;                      // 4 KB
+constexpr uint32_t kBXYMat = 4 * kXL * 32, kBPMat = 2 * kXL * 32;
+constexpr uint32_t kOffAX = 0, kOffAY = 2 * kAMat, kOffAP = 4 * kAMat;
+constexpr uint32_t kOffBXY = 6 * kAMat, kOffBP = kOffBXY + 2 * kBXYMat;
+constexpr uint32_t kXStageBytes = kOffBP + 2 * kBPMat;    // 30 KB
+// A stage of staged coefficients (4 frames): the bins of a and b that the tile's
+// rows need (at most 130 consecutive bins from an even bin), then the 16 bins of
+// c and d of its columns.
+constexpr int kRawK = 136;
+constexpr uint32_t kRawA = 0, kRawB = kXF * kRawK * 8, kRawC = 2 * kXF * kRawK * 8,
+                   kRawD = kRawC + kXF * kXL * 8;
+constexpr uint32_t kXRawBytes = kRawD + kXF * kXL * 8;      // 9.5 KB
+constexpr size_t kXSmemBytes =
+    (size_t)kXStages * kXStageBytes + (size_t)kXRaw * kXRawBytes + 128;
+
+enum : int { kRecFirst = 1, kRecLast = 2, kRecStop = 4, kRecItemEnd = 8 };
+
+struct StageRec {
+  int ncols, flags;  // columns of the tile (a multiple of 8), flags
+};
+
+struct RawRec {  // a staged stage: its tile, combination, first staged bin, frames
+  int r0, l0, ncols, combo, bstart, st, flags;
+};
+
+struct CrossSlot {  // one group: its one-bin sums and record, for the epilogue
+  float2 sxy[kXT];
+  float2 szw[kXL];
+  int r0, l0, combo, flags;
+};
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t t;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+  return t;
+}
+
+// hi and lo TF32 parts of four values into the hi and lo blocks at byte `off`
+__device__ __forceinline__ void put_split(unsigned char* blk, uint32_t lo_off, uint32_t off, float a,
+                                          float b, float c, float d) {
+  uint4 h, l;
+  h.x = to_tf32(a);
+  h.y = to_tf32(b);
+  h.z = to_tf32(c);
+  h.w = to_tf32(d);
+  l.x = to_tf32(a - __uint_as_float(h.x));
+  l.y = to_tf32(b - __uint_as_float(h.y));
+  l.z = to_tf32(c - __uint_as_float(h.z));
+  l.w = to_tf32(d - __uint_as_float(h.w));
+  *reinterpret_cast<uint4*>(blk + off) = h;
+  *reinterpret_cast<uint4*>(blk + lo_off + off) = l;
+}
+
+// byte offset of row n's 16-byte chunk c in a matrix block
+__device__ __forceinline__ uint32_t core_off(int n, int c) {
+  return (uint32_t)((n >> 3) * 256 + c * 128 + (n & 7) * 16);
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void cmacf(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+
+__device__ __forceinline__ uint64_t smem_desc_x(uint32_t addr) {
+  // K-major, no swizzle: LBO 128 bytes, SBO 256 bytes
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)(256u >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"((uint32_t)accumulate));
+}
+
+__device__ __forceinline__ void mma_commit_x(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_x(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// true on every builder thread iff v is true on all of them
+__device__ __forceinline__ bool builders_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kXBuilders)
+      : "memory");
+  return r != 0;
+}
+
+struct CrossQueue {
+  int* counter;
+  int n_items, n_tiles, n_combos, n_cb, group_chunk;
+};
+
+__global__ void __launch_bounds__(kXThreads, 1)
+k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int G, int m, int M,
+                    int Mp, const int4* __restrict__ combos, CrossQueue wq, float pref, float fmm,
+                    float fm1, double* __restrict__ acc, long long plane, long long combo_stride,
+                    int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[kXStages];      // stage built
+  __shared__ __align__(8) uint64_t sdone[kXStages];     // stage's products complete
+  __shared__ __align__(8) uint64_t slotfull[kXSlots];   // group slot written
+  __shared__ __align__(8) uint64_t slotempty[kXSlots];  // group slot read by the epilogue
+  __shared__ __align__(8) uint64_t bfull[2];            // TMEM buffer holds a finished group
+  __shared__ __align__(8) uint64_t bempty[2];           // TMEM buffer read by the epilogue
+  __shared__ __align__(8) uint64_t rfull[kXRaw];       // coefficients staged (bulk copies)
+  __shared__ __align__(8) uint64_t rempty[kXRaw];      // staged coefficients read
+  __shared__ StageRec srec[kXStages];
+  __shared__ RawRec rrec[kXRaw];
+  __shared__ __align__(16) CrossSlot slot[kXSlots];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* stages =
+      smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);  // 128-byte aligned
+
+  if (tid == 0) {
+    for (int s = 0; s < kXStages; ++s) {
+      mbar_init(&full[s], kXBuilders);
+      mbar_init(&sdone[s], 1);
+    }
+    for (int p = 0; p < kXSlots; ++p) {
+      mbar_init(&slotfull[p], kXBuilders);
+      mbar_init(&slotempty[p], kXEpiWarps);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bfull[b], 1);
+      mbar_init(&bempty[b], kXEpiWarps);
+    }
+    for (int i = 0; i < kXRaw; ++i) {
+      mbar_init(&rfull[i], 1);
+      mbar_init(&rempty[i], kXBuilders);
+    }
+    s_fail = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kXTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t taddr = tmem_slot;
+  const int rows_hi = 2 * M - 2;  // last row r of the tiles
+  const int nst = (m + kXF - 1) / kXF;
+
+  unsigned char* raws = stages + (size_t)kXStages * kXStageBytes;
+  if (warp >= kXEpiWarps && warp < kXMmaWarp) {
+    // ------------------------------------------------------------ builders
+    // thread bt: row R = bt / 2 of the tile, frames 2 fp and 2 fp + 1 of every
+    // stage (one 16-byte chunk of each row); the first 32 threads also build the
+    // columns of bin l0 + bt / 2 for the same two frames
+    const int bt = tid - 32 * kXEpiWarps;
+    const int R = bt >> 1, fp = bt & 1;
+    const bool bcol = bt < 2 * kXL;
+    const int li = bt >> 1;
+    const float2 zero = make_float2(0.f, 0.f);
+    uint32_t rq = 0, q = 0, gs = 0;
+    bool ok = true;
+    float2 sxy = zero, szw = zero;
+    for (;;) {
+      const int rs = (int)(rq % kXRaw);
+      ok = builders_all(mbar_wait_bounded(&rfull[rs], (rq / kXRaw) & 1u, status));
+      if (!ok) break;
+      const RawRec rec = rrec[rs];
+      if (rec.flags & kRecStop) break;
+      const int r = rec.r0 + R, k = r - (M - 1);
+      const bool rv = r <= rows_hi;
+      const int kb = k < 0 ? -k : k;
+      const bool lv = bcol && rec.l0 + li < M;
+      const int j0 = rec.st * kXF + 2 * fp;  // first frame of this thread's chunk
+      const float2* raw = reinterpret_cast<const float2*>(raws + (size_t)rs * kXRawBytes);
+      float2 va[2], vb[2], vc[2], vd[2];
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        const int fj = 2 * fp + jj;  // frame within the stage
+        const bool v = rv && j0 + jj < m;
+        va[jj] = v ? raw[kRawA / 8 + fj * kRawK + kb - rec.bstart] : zero;
+        vb[jj] = v ? raw[kRawB / 8 + fj * kRawK + kb - rec.bstart] : zero;
+        const bool w = lv && j0 + jj < m;
+        vc[jj] = w ? raw[kRawC / 8 + fj * kXL + li] : zero;
+        vd[jj] = w ? raw[kRawD / 8 + fj * kXL + li] : zero;
+      }
+      mbar_arrive_x(&rempty[rs]);  // the staged coefficients are in registers
+      ++rq;
+      const int s = (int)(q % kXStages);
+      ok = builders_all(q < (uint32_t)kXStages ||
+                        mbar_wait_bounded(&sdone[s], ((q / kXStages) & 1u) ^ 1u, status));
+      if (!ok) break;
+      if (rec.flags & kRecFirst) sxy = szw = zero;
+      unsigned char* stg = stages + (size_t)s * kXStageBytes;
+      // rows: k < 0: x = a_{|k|}*, y = b_{|k|};  k >= 0: x = a_k, y = b_k*
+      float2 x[2], y[2], xy[2];
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        x[jj] = k < 0 ? make_float2(va[jj].x, -va[jj].y) : va[jj];
+        y[jj] = k < 0 ? vb[jj] : make_float2(vb[jj].x, -vb[jj].y);
+        xy[jj] = cmulf(x[jj], y[jj]);
+        sxy.x += xy[jj].x;
+        sxy.y += xy[jj].y;
+      }
+      const uint32_t o = core_off(R, fp);
+      put_split(stg + kOffAX, kAMat, o, x[0].x, x[0].y, x[1].x, x[1].y);
+      put_split(stg + kOffAY, kAMat, o, y[0].x, y[0].y, y[1].x, y[1].y);
+      put_split(stg + kOffAP, kAMat, o, xy[0].x, xy[0].y, xy[1].x, xy[1].y);
+      if (bcol) {
+        // columns of bin l: z = c_l, w = d_l*, zw
+        float2 z[2], w[2], zw[2];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          z[jj] = vc[jj];
+          w[jj] = make_float2(vd[jj].x, -vd[jj].y);
+          zw[jj] = cmulf(z[jj], w[jj]);
+          szw.x += zw[jj].x;
+          szw.y += zw[jj].y;
+        }
+        unsigned char* bxy = stg + kOffBXY;
+        put_split(bxy, kBXYMat, core_off(4 * li + 0, fp), z[0].x, -z[0].y, z[1].x, -z[1].y);
+        put_split(bxy, kBXYMat, core_off(4 * li + 1, fp), z[0].y, z[0].x, z[1].y, z[1].x);
+        put_split(bxy, kBXYMat, core_off(4 * li + 2, fp), w[0].x, -w[0].y, w[1].x, -w[1].y);
+        put_split(bxy, kBXYMat, core_off(4 * li + 3, fp), w[0].y, w[0].x, w[1].y, w[1].x);
+        unsigned char* bp = stg + kOffBP;
+        put_split(bp, kBPMat, core_off(2 * li + 0, fp), zw[0].x, -zw[0].y, zw[1].x, -zw[1].y);
+        put_split(bp, kBPMat, core_off(2 * li + 1, fp), zw[0].y, zw[0].x, zw[1].y, zw[1].x);
+      }
+      if (bt == 0) srec[s] = StageRec{rec.ncols, rec.flags & (kRecFirst | kRecLast)};
+      // the generic-proxy writes become visible to the tensor cores' reads
+      fence_async_smem();
+      mbar_arrive_x(&full[s]);
+      ++q;
+      if (rec.flags & kRecLast) {
+        // the group's one-bin sums (the two chunks of a bin are adjacent lanes) and
+        // its record, for the epilogue
+        const float2 sxy_o = make_float2(__shfl_xor_sync(0xffffffffu, sxy.x, 1),
+                                         __shfl_xor_sync(0xffffffffu, sxy.y, 1));
+        const float2 szw_o = make_float2(__shfl_xor_sync(0xffffffffu, szw.x, 1),
+                                         __shfl_xor_sync(0xffffffffu, szw.y, 1));
+        const int p = (int)(gs % kXSlots);
+        ok = builders_all(gs < (uint32_t)kXSlots ||
+                          mbar_wait_bounded(&slotempty[p], ((gs / kXSlots) - 1) & 1u, status));
+        if (!ok) break;
+        if (fp == 0) slot[p].sxy[R] = make_float2(sxy.x + sxy_o.x, sxy.y + sxy_o.y);
+        if (bcol && fp == 0) slot[p].szw[li] = make_float2(szw.x + szw_o.x, szw.y + szw_o.y);
+        if (bt == 0) {
+          slot[p].r0 = rec.r0;
+          slot[p].l0 = rec.l0;
+          slot[p].combo = rec.combo;
+          slot[p].flags = rec.flags & kRecItemEnd;
+        }
+        mbar_arrive_x(&slotfull[p]);
+        ++gs;
+      }
+    }
+    if (!ok && bt == 0) atomicExch(&s_fail, 1);
+    // stop records: the next stage (for the MMA warp) and the next slot (epilogue)
+    {
+      const int s = (int)(q % kXStages);
+      if (q >= (uint32_t)kXStages)
+        mbar_wait_bounded(&sdone[s], ((q / kXStages) & 1u) ^ 1u, status);
+      if (bt == 0) srec[s] = StageRec{0, kRecStop};
+      mbar_arrive_x(&full[s]);
+      const int p = (int)(gs % kXSlots);
+      if (gs >= (uint32_t)kXSlots)
+        mbar_wait_bounded(&slotempty[p], ((gs / kXSlots) - 1) & 1u, status);
+      if (bt == 0) slot[p].flags = kRecStop;
+      mbar_arrive_x(&slotfull[p]);
+    }
+  } else if (warp == kXMmaWarp) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t sbase = smem_addr(stages);
+      const uint32_t idesc0 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kXT >> 4) << 24);
+      uint32_t q = 0, gc = 0;
+      int last_s = -1;
+      uint32_t last_ph = 0;
+      for (;; ++q) {
+        const int s = (int)(q % kXStages);
+        const uint32_t ph = (q / kXStages) & 1u;
+        if (!mbar_wait_bounded(&full[s], ph, status)) break;
+        const StageRec rec = srec[s];
+        if (rec.flags & kRecStop) break;
+        const uint32_t b = gc & 1u;
+        if (rec.flags & kRecFirst) {
+          // the buffer is free once the epilogue has read the group two before
+          if (gc >= 2 && !mbar_wait_bounded(&bempty[b], ((gc >> 1) - 1) & 1u, status)) break;
+          tc_after();
+        }
+        const uint32_t d = taddr + b * kXBufCols;
+        const uint32_t idx = idesc0 | ((uint32_t)((4 * rec.ncols) >> 3) << 17);
+        const uint32_t idp = idesc0 | ((uint32_t)((2 * rec.ncols) >> 3) << 17);
+        const uint32_t sa = sbase + (uint32_t)s * kXStageBytes;
+        const bool first = (rec.flags & kRecFirst) != 0;
+#pragma unroll
+        for (int pa = 0; pa < 3; ++pa) {
+          // passes hi*hi, hi*lo, lo*hi
+          const uint32_t ao = pa == 2 ? kAMat : 0u;
+          const uint32_t bxo = pa == 1 ? kBXYMat : 0u, bpo = pa == 1 ? kBPMat : 0u;
+          const bool accum = !(first && pa == 0);
+          mma_tf32(d, smem_desc_x(sa + kOffAX + ao), smem_desc_x(sa + kOffBXY + bxo), idx, accum);
+          mma_tf32(d + kColY, smem_desc_x(sa + kOffAY + ao), smem_desc_x(sa + kOffBXY + bxo), idx,
+                   accum);
+          mma_tf32(d + kColP, smem_desc_x(sa + kOffAP + ao), smem_desc_x(sa + kOffBP + bpo), idp,
+                   accum);
+        }
+        mma_commit_x(&sdone[s]);
+        last_s = s;
+        last_ph = ph;
+        if (rec.flags & kRecLast) {
+          mma_commit_x(&bfull[b]);
+          ++gc;
+        }
+      }
+      if (*(volatile int*)status != 0) atomicExch(&s_fail, 1);
+      // the products issued must be complete before the TMEM is freed
+      if (last_s >= 0) mbar_wait_bounded(&sdone[last_s], last_ph, status);
+    }
+    __syncwarp();
+  } else if (warp == kXLoadWarp) {
+    // ------------------------------------------------------------ loader
+    // takes the items and stages, per 4 frames, the coefficients the builders need
+    // (bulk copies of whole bin ranges), with the stage's record
+    if (lane == 0) {
+      uint32_t rq = 0;
+      bool ok = true;
+      const int per_chunk = wq.n_tiles * wq.n_combos;
+      for (;;) {
+        const int item = *(volatile int*)&s_fail ? wq.n_items : atomicAdd(wq.counter, 1);
+        if (item >= wq.n_items) break;
+        const int chunk = item / per_chunk, rest = item - chunk * per_chunk;
+        const int combo = rest / wq.n_tiles, tile = rest - combo * wq.n_tiles;
+        const int r0 = 1 + (tile / wq.n_cb) * kXT, l0 = (tile % wq.n_cb) * kXL;
+        const int ncols = min(kXL, (M - l0 + 7) & ~7);
+        const int g0 = chunk * wq.group_chunk, g1 = min(G, g0 + wq.group_chunk);
+        const int4 cb = combos[combo];
+        const float2* A = spec + cb.x * chan_stride;
+        const float2* B = spec + cb.y * chan_stride;
+        const float2* C = spec + cb.z * chan_stride;
+        const float2* D = spec + cb.w * chan_stride;
+        // bins |k| of the tile's rows: one range of at most 128 bins, staged from an
+        // even bin (16-byte aligned) in a whole number of bin pairs, within the row
+        const int klo = r0 - (M - 1), khi = min(r0 + kXT - 1, rows_hi) - (M - 1);
+        const int blo = klo >= 0 ? klo : (khi <= 0 ? -khi : 0);
+        const int bhi = klo >= 0 ? khi : (khi <= 0 ? -klo : max(-klo, khi));
+        const int bstart = blo & ~1;
+        const int nb = min((bhi - bstart + 2) & ~1, Mp - bstart);
+        const uint32_t ab_bytes = (uint32_t)nb * 8u, cd_bytes = (uint32_t)kXL * 8u;
+        for (int g = g0; g < g1 && ok; ++g) {
+          const long long gbase = (long long)g * m * Mp;
+          for (int st = 0; st < nst; ++st) {
+            const int rs = (int)(rq % kXRaw);
+            if (rq >= (uint32_t)kXRaw &&
+                !mbar_wait_bounded(&rempty[rs], ((rq / kXRaw) - 1) & 1u, status)) {
+              ok = false;
+              break;
+            }
+            const int nf = min(kXF, m - st * kXF);
+            const int last = st == nst - 1;
+            rrec[rs] = RawRec{r0, l0, ncols, combo, bstart, st,
+                              (st == 0 ? kRecFirst : 0) | (last ? kRecLast : 0) |
+                                  (last && g == g1 - 1 ? kRecItemEnd : 0)};
+            unsigned char* dst = raws + (size_t)rs * kXRawBytes;
+            mbar_arrive_expect_tx(&rfull[rs], (uint32_t)nf * 2u * (ab_bytes + cd_bytes));
+            for (int f = 0; f < nf; ++f) {
+              const long long o = gbase + (long long)(st * kXF + f) * Mp;
+              tma_load_1d(dst + kRawA + f * kRawK * 8, A + o + bstart, ab_bytes, &rfull[rs]);
+              tma_load_1d(dst + kRawB + f * kRawK * 8, B + o + bstart, ab_bytes, &rfull[rs]);
+              tma_load_1d(dst + kRawC + f * kXL * 8, C + o + l0, cd_bytes, &rfull[rs]);
+              tma_load_1d(dst + kRawD + f * kXL * 8, D + o + l0, cd_bytes, &rfull[rs]);
+            }
+            ++rq;
+          }
+        }
+        if (!ok) break;
+      }
+      if (!ok) atomicExch(&s_fail, 1);
+      // every copy issued has landed before the CTA may exit (waited before the stop
+      // record moves the barrier to its next phase)
+      for (uint32_t i = rq > (uint32_t)kXRaw ? rq - kXRaw : 0; i < rq; ++i)
+        mbar_wait_bounded(&rfull[i % kXRaw], (i / kXRaw) & 1u, status);
+      const int rs = (int)(rq % kXRaw);
+      if (rq >= (uint32_t)kXRaw) mbar_wait_bounded(&rempty[rs], ((rq / kXRaw) - 1) & 1u, status);
+      rrec[rs].flags = kRecStop;
+      asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
+                       smem_addr(&rfull[rs]))
+                   : "memory");
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int qd = warp & 3, h = warp >> 2;
+    const int R = 32 * qd + lane;
+    const uint32_t lane_addr = taddr + ((uint32_t)(32 * qd) << 16);
+    float sre[8], sim[8], qre[8], qim[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sre[i] = sim[i] = qre[i] = qim[i] = 0.f;
+    for (uint32_t gc = 0;; ++gc) {
+      const int p = (int)(gc % kXSlots);
+      const uint32_t b = gc & 1u;
+      // one decision per warp: the TMEM accesses below are warp-collective
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&slotfull[p], (gc / kXSlots) & 1u, status))) {
+        if (lane == 0) atomicExch(&s_fail, 1);
+        break;
+      }
+      const int flags = slot[p].flags;
+      if (flags & kRecStop) break;
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bfull[b], (gc >> 1) & 1u, status))) {
+        if (lane == 0) atomicExch(&s_fail, 1);
+        break;
+      }
+      tc_after();
+      const int l0 = slot[p].l0;
+      const float2 sxy = slot[p].sxy[R];
+      const uint32_t tb = lane_addr + b * kXBufCols;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int li0 = 8 * h + 4 * hh;
+        if (l0 + li0 < M) {  // warp-uniform
+          float dx[16], dy[16], dp[8];
+          tmem_ld16(tb + 4 * li0, dx);
+          tmem_ld16(tb + kColY + 4 * li0, dy);
+          tmem_ld8(tb + kColP + 2 * li0, dp);
+          tc_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float2 szw = slot[p].szw[li0 + i];
+            const float2 xz = make_float2(dx[4 * i], dx[4 * i + 1]);
+            const float2 xw = make_float2(dx[4 * i + 2], dx[4 * i + 3]);
+            const float2 yz = make_float2(dy[4 * i], dy[4 * i + 1]);
+            const float2 yw = make_float2(dy[4 * i + 2], dy[4 * i + 3]);
+            float2 t = cmulf(sxy, szw);
+            cmacf(t, xz, yw);
+            cmacf(t, xw, yz);
+            const float cr = pref * fmaf(fmm, dp[2 * i], -fm1 * t.x);
+            const float ci = pref * fmaf(fmm, dp[2 * i + 1], -fm1 * t.y);
+            const int e = 4 * hh + i;
+            sre[e] += cr;
+            sim[e] += ci;
+            qre[e] = fmaf(cr, cr, qre[e]);
+            qim[e] = fmaf(ci, ci, qim[e]);
+          }
+        }
+      }
+      // this warp has read its part of the buffer and of the slot
+      tc_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive_x(&bempty[b]);
+        mbar_arrive_x(&slotempty[p]);
+      }
+      if (flags & kRecItemEnd) {
+        const int r = slot[p].r0 + R;
+        const long long cbase = (long long)slot[p].combo * combo_stride;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int lc = l0 + 8 * h + e;
+          if (r <= rows_hi && lc < M) {
+            const long long o = cbase + (long long)r * M + lc;
+            atomicAdd(acc + o, (double)sre[e]);
+            atomicAdd(acc + plane + o, (double)sim[e]);
+            atomicAdd(acc + 2 * plane + o, (double)qre[e]);
+            atomicAdd(acc + 3 * plane + o, (double)qim[e]);
+          }
+          sre[e] = sim[e] = qre[e] = qim[e] = 0.f;
+        }
+      }
+    }
+  }
+  tc_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(kXTmemCols));
+  }
+}
+
+// row r = 0 (k = -(M - 1)) of every plane and combination <- row r = 2M - 2
+__global__ void k3_cross_row0(double* __restrict__ acc, int n, int M, long long combo_stride,
+                              long long plane) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int l = i % M, pc = i / M;
+  const int c = pc >> 2, pl = pc & 3;
+  double* a = acc + pl * plane + (long long)c * combo_stride;
+  a[l] = a[(long long)(2 * M - 2) * M + l];
+}
+
+}  // namespace
+
+cudaError_t launch_k3_trispec_cross_tc(const float2* spec, long long chan_stride, int G, int m,
+                                       int M, int Mp, const int4* combos, int n_combos,
+                                       double* acc, long long plane, int nsm, bool natural,
+                                       int* counter, int* status, cudaStream_t stream) {
+  if (G <= 0 || n_combos <= 0) return cudaSuccess;
+  if (m < 1 || M < 2 || nsm <= 0) return cudaErrorInvalidValue;
+  const int n_rb = (2 * M - 2 + kXT - 1) / kXT, n_cb = (M + kXL - 1) / kXL;
+  const long long n_tiles = (long long)n_rb * n_cb;
+  CrossQueue wq;
+  wq.counter = counter;
+  wq.n_tiles = (int)n_tiles;
+  wq.n_combos = n_combos;
+  wq.n_cb = n_cb;
+  wq.group_chunk = work_group_chunk(G, (int)std::min<long long>(n_tiles * n_combos, 1 << 30), nsm);
+  const long long n_chunks = (G + wq.group_chunk - 1) / wq.group_chunk;
+  const long long n_items = n_chunks * n_tiles * n_combos;
+  if (n_items > 0x7fffffffll) return cudaErrorInvalidValue;
+  wq.n_items = (int)n_items;
+  auto kern = k3_trispec_cross_tc;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmemBytes);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  const double md = m;
+  // c4 = pref [fmm P - fm1 (...)]: the k-statistic (Eq. 85) or the natural estimator
+  const float pref =
+      (float)(natural ? 1.0 / (md * md) : 1.0 / ((md - 1.0) * (md - 2.0) * (md - 3.0)));
+  const float fmm = (float)(natural ? md : md * (md + 1.0));
+  const float fm1 = (float)(natural ? 1.0 : md - 1.0);
+  const long long combo_stride = (long long)(2 * M - 1) * M;
+  kern<<<nsm, kXThreads, kXSmemBytes, stream>>>(spec, chan_stride, G, m, M, Mp, combos, wq, pref,
+                                                fmm, fm1, acc, plane, combo_stride, status);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n = 4 * n_combos * M;
+  k3_cross_row0<<<(n + 255) / 256, 256, 0, stream>>>(acc, n, M, combo_stride, plane);
+  return cudaGetLastError();
+}
+
+}  // namespace ss

@@ -322,10 +322,15 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
       if (!p->c4.empty()) {
         record(p, 2, p->stream, true);
         const long long plane = (long long)p->c4.size() * p->rows4 * p->M;
-        if (p->C > 1)
+        if (p->C > 1 && p->precision == SS_PREC_FP32)
           SS_TRY(p, launch_k3_trispec_cross(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp,
                                             p->d_c4cross, (int)p->c4.size(), p->d_acc4, plane,
                                             p->nsm, nat, p->stream));
+        else if (p->C > 1)
+          SS_TRY(p, launch_k3_trispec_cross_tc(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp,
+                                               p->d_c4cross, (int)p->c4.size(), p->d_acc4,
+                                               plane, p->nsm, nat, p->d_counter, p->d_status,
+                                               p->stream));
         for (size_t i = 0; i < p->c4.size() && p->C == 1; ++i) {
           const Combo& cb = p->c4[i];
           if (p->precision == SS_PREC_FP32)
@@ -1280,7 +1285,7 @@ ss_status ss_query(ss_plan_t p, ss_info* info) {
   info->device_bytes = p->device_bytes;
   info->kernels_per_batch = 1 + (p->n_s2cross > 0 ? 1 : 0) +
                             (int)p->c3.size() * (1 + (p->C == 1 && p->n_pts3 > 0 ? 1 : 0)) +
-                            (p->C > 1 ? (p->c4.empty() ? 0 : 1)
+                            (p->C > 1 ? (p->c4.empty() ? 0 : p->precision == SS_PREC_FP32 ? 1 : 2)
                                       : (int)p->c4.size() *
                                             (1 + (p->precision != SS_PREC_FP32 && p->col4 ? 1 : 0)));
   return SS_OK;

@@ -205,9 +205,15 @@ def test_multichannel_s2_s3():
 # cross-channel S4, C4(a_k, b_k*, c_l, d_l*) on k in [-(M-1), M-1] x l in [0, M-1]:
 # pairings that exercise every role (all equal, one distinct, two pairs, all
 # distinct, the order of the pairs), m across one and two staged frame chunks,
-# a grid with ragged row and column tiles; every precision runs it in FP32
+# a grid with ragged row and column tiles.  FP32 runs on CUDA cores; every
+# tensor-core precision runs the tcgen05 form in TF32x3 (4-frame stages, so m
+# = 5, 9, 33 end on a partly filled stage; T = 256 and 512 span two and four row
+# tiles, and a last column tile holding only l = M - 1)
 @pytest.mark.parametrize("T,m,G,precision", [(64, 5, 40, "fp32"), (32, 20, 12, "fp32"),
-                                             (128, 6, 16, "tf32x3")])
+                                             (128, 6, 16, "tf32x3"), (64, 5, 40, "tf32x3"),
+                                             (32, 20, 12, "fp16x3"), (8, 4, 50, "tf32x3"),
+                                             (256, 9, 6, "bf16x3"), (16, 33, 6, "tf32x3"),
+                                             (512, 4, 3, "bf16")])
 def test_multichannel_s4(T, m, G, precision):
     zs = synth.multichannel_shared(4, T * m * G + 7, seed=13 + m)
     combos4 = [(0, 0, 0, 0), (0, 0, 1, 1), (0, 1, 0, 1), (0, 1, 1, 0), (0, 0, 1, 2),
@@ -379,6 +385,8 @@ def test_config3_four_channels_full_size_sampled_points():
     assert (len(c2), len(c3)) == (10, 20) and len(c4) > 0
     gpu = run_gpu(zs, T, m, channels=C)
     assert gpu["G"] == n // (T * m)
+    # the tensor-core form of the cross S4 on the same record
+    gpu_tc = run_gpu(zs, T, m, channels=C, precision="tf32x3")
     rng = np.random.default_rng(5)
     g = oracle.window(T)
     G = n // (T * m)
@@ -395,10 +403,12 @@ def test_config3_four_channels_full_size_sampled_points():
         ll = np.concatenate([l[keep], [peak[1], M - 1, 0, M - 1]])
         pts3[i] = (kk, ll)
     for i in picks4:
-        S = gpu["S4"][i]
+        S, S_tc = gpu["S4"][i], gpu_tc["S4"][i]
         peak = np.unravel_index(np.argmax(np.abs(S)), S.shape)
-        kk = np.concatenate([rng.integers(-(M - 1), M, 30), [peak[0] - (M - 1), -(M - 1), M - 1]])
-        ll = np.concatenate([rng.integers(0, M, 30), [peak[1], M - 1, 0]])
+        peak_tc = np.unravel_index(np.argmax(np.abs(S_tc)), S.shape)
+        kk = np.concatenate([rng.integers(-(M - 1), M, 30),
+                             [peak[0] - (M - 1), peak_tc[0] - (M - 1), -(M - 1), M - 1]])
+        ll = np.concatenate([rng.integers(0, M, 30), [peak[1], peak_tc[1], M - 1, 0]])
         pts4[i] = (kk, ll)
     v2 = {i: [] for i in range(len(c2))}
     v3 = {i: [] for i in picks3}
@@ -418,14 +428,15 @@ def test_config3_four_channels_full_size_sampled_points():
         ref = oracle.mean_and_stderr(np.concatenate(v2[i]))
         check({"S2": gpu["S2"][i], "S2_err": gpu["S2_err"][i]},
               {"S2": ref[0], "S2_err": np.stack([ref[1], ref[2]], -1)}, "S2")
-    for key, vals, pts in (("S3", v3, pts3), ("S4", v4, pts4)):
+    for key, vals, pts, out in (("S3", v3, pts3, gpu), ("S4", v4, pts4, gpu),
+                                ("S4", v4, pts4, gpu_tc)):
         for i, v in vals.items():
             mean, er, ei = oracle.mean_and_stderr(np.concatenate(v))
             kk, ll = pts[i]
-            S, E = gpu[key][i][kk + M - 1, ll], gpu[key + "_err"][i][kk + M - 1, ll]
+            S, E = out[key][i][kk + M - 1, ll], out[key + "_err"][i][kk + M - 1, ll]
             scale = np.max(np.abs(mean))
             # the sampled set holds the GPU grid's peak, and the oracle agrees there
-            assert np.max(np.abs(gpu[key][i])) <= (1 + 2 * TOL) * scale
+            assert np.max(np.abs(out[key][i])) <= (1 + 2 * TOL) * scale
             assert np.max(np.abs(S - mean)) <= TOL * scale, (key, i)
             escale = max(np.max(er), np.max(ei))
             assert np.max(np.abs(E[:, 0] - er)) <= TOL_ERR * escale, (key, i)
@@ -457,7 +468,8 @@ def test_first_order_and_natural_estimators_single_channel(estimator, precision)
     check_s1(out["S1"][0], out["S1_err"][0], ref)
 
 
-def test_natural_estimators_several_channels():
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
+def test_natural_estimators_several_channels(precision):
     zs = synth.multichannel_shared(3, 64 * 5 * 30 + 9, seed=43)
     combos2 = [(0, 0), (0, 2)]
     combos3 = [(0, 1, 2), (1, 1, 0)]
@@ -466,7 +478,7 @@ def test_natural_estimators_several_channels():
             + [(4, *c) for c in combos4])
     mod = P()
     plan = mod.Plan(channels=3, T=64, dt=1.0, m=5, orders=(1, 2, 3, 4), combos=recs,
-                    estimator="natural")
+                    estimator="natural", precision=precision)
     plan.accumulate(torch.from_numpy(np.ascontiguousarray(zs)).cuda())
     out = plan.finalize()
     plan.close()
