@@ -161,12 +161,17 @@ int k3tc_stage_chunks(int precision);
 
 // The same on the tcgen05 tensor cores (every tensor-core precision; TF32 hi/lo
 // in three passes): tiles of 128 rows k x 16 columns l, operands built in shared
-// memory from the centred spectra; the row k = -(M-1) is copied from k = M-1
+// memory from the centred spectra, read through two 2-D views [rows][Mp] of
+// them (8-byte elements, no swizzle): tm_ab with boxes of 4 rows x
+// min(kCrossBoxBins, Mp) bins, tm_cd with boxes of 4 rows x 16 bins; a channel's
+// rows start at channel x chan_rows.  The row k = -(M-1) is copied from k = M-1
 // (equal for real signals).  counter and status as for the pair kernels.
-cudaError_t launch_k3_trispec_cross_tc(const float2* spec, long long chan_stride, int G, int m,
-                                       int M, int Mp, const int4* combos, int n_combos,
-                                       double* acc, long long plane, int nsm, bool natural,
-                                       int* counter, int* status, cudaStream_t stream);
+constexpr int kCrossBoxBins = 140;
+cudaError_t launch_k3_trispec_cross_tc(const CUtensorMap& tm_ab, const CUtensorMap& tm_cd,
+                                       int chan_rows, int G, int m, int M, int Mp,
+                                       const int4* combos, int n_combos, double* acc,
+                                       long long plane, int nsm, bool natural, int* counter,
+                                       int* status, cudaStream_t stream);
 
 // Most groups whose per-group estimates a kernel adds up in float32 before the
 // run goes to the float64 accumulators (bounds the float32 rounding of the sums

@@ -54,13 +54,13 @@ constexpr int kXF = 4;       // frames per stage: K = 8 TF32 values, one MMA K s
 constexpr int kXStages = 4;  // operand stages
 constexpr int kXRaw = 8;     // stages of staged coefficients
 constexpr int kXEpiWarps = 8, kXBuildWarps = 8;
-constexpr int kXBuilders = 32 * kXBuildWarps;
 constexpr int kXMmaWarp = kXEpiWarps + kXBuildWarps, kXLoadWarp = kXMmaWarp + 1;
 constexpr int kXThreads = 32 * (kXLoadWarp + 1);
 constexpr int kXSlots = 4;
 constexpr uint32_t kXTmemCols = 512;
-// TMEM buffer b starts at column 256 b: Sxz, Sxw (4 columns per l: Re Sxz, Im Sxz,
-// Re Sxw, Im Sxw), then Syz, Syw at +64, then P (Re, Im per l) at +128
+// TMEM buffer b starts at column 256 b: 16 columns (one per l) each of Re Sxz,
+// Im Sxz, Re Sxw, Im Sxw, then of Re Syz, Im Syz, Re Syw, Im Syw at +64, then of
+// Re P, Im P at +128 (the B rows are ordered the same way: type-major)
 constexpr uint32_t kXBufCols = 256, kColY = 64, kColP = 128;
 
 // A stage: for each matrix a hi block, then a lo block.  A matrix of R rows x 8
@@ -73,9 +73,10 @@ constexpr uint32_t kOffAX = 0, kOffAY = 2 * kAMat, kOffAP = 4 * kAMat;
 constexpr uint32_t kOffBXY = 6 * kAMat, kOffBP = kOffBXY + 2 * kBXYMat;
 constexpr uint32_t kXStageBytes = kOffBP + 2 * kBPMat;    // 30 KB
 // A stage of staged coefficients (4 frames): the bins of a and b that the tile's
-// rows need (at most 130 consecutive bins from an even bin), then the 16 bins of
-// c and d of its columns.
-constexpr int kRawK = 136;
+// rows need (at most 130 consecutive bins from an even bin; a box of 4 rows x
+// min(kRawK, Mp) bins, rows rawk bins apart), then the 16 bins of c and d of its
+// columns.
+constexpr int kRawK = kCrossBoxBins;
 constexpr uint32_t kRawA = 0, kRawB = kXF * kRawK * 8, kRawC = 2 * kXF * kRawK * 8,
                    kRawD = kRawC + kXF * kXL * 8;
 constexpr uint32_t kXRawBytes = kRawD + kXF * kXL * 8;      // 9.5 KB
@@ -85,11 +86,11 @@ constexpr size_t kXSmemBytes =
 enum : int { kRecFirst = 1, kRecLast = 2, kRecStop = 4, kRecItemEnd = 8 };
 
 struct StageRec {
-  int ncols, flags;  // columns of the tile (a multiple of 8), flags
+  int flags;
 };
 
 struct RawRec {  // a staged stage: its tile, combination, first staged bin, frames
-  int r0, l0, ncols, combo, bstart, st, flags;
+  int r0, l0, combo, bstart, st, flags;
 };
 
 struct CrossSlot {  // one group: its one-bin sums and record, for the epilogue
@@ -178,6 +179,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -186,28 +196,17 @@ __device__ __forceinline__ void mbar_arrive_x(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// true on every builder thread iff v is true on all of them
-__device__ __forceinline__ bool builders_all(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)v), "n"(kXBuilders)
-      : "memory");
-  return r != 0;
-}
-
 struct CrossQueue {
   int* counter;
   int n_items, n_tiles, n_combos, n_cb, group_chunk;
 };
 
 __global__ void __launch_bounds__(kXThreads, 1)
-k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int G, int m, int M,
-                    int Mp, const int4* __restrict__ combos, CrossQueue wq, float pref, float fmm,
-                    float fm1, double* __restrict__ acc, long long plane, long long combo_stride,
-                    int* __restrict__ status) {
+k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
+                    const __grid_constant__ CUtensorMap tm_cd, int chan_rows, int rawk, int G,
+                    int m, int M, int Mp, const int4* __restrict__ combos, CrossQueue wq,
+                    float pref, float fmm, float fm1, double* __restrict__ acc, long long plane,
+                    long long combo_stride, int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kXStages];      // stage built
   __shared__ __align__(8) uint64_t sdone[kXStages];     // stage's products complete
@@ -228,11 +227,11 @@ k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int 
 
   if (tid == 0) {
     for (int s = 0; s < kXStages; ++s) {
-      mbar_init(&full[s], kXBuilders);
+      mbar_init(&full[s], kXBuildWarps);
       mbar_init(&sdone[s], 1);
     }
     for (int p = 0; p < kXSlots; ++p) {
-      mbar_init(&slotfull[p], kXBuilders);
+      mbar_init(&slotfull[p], kXBuildWarps);
       mbar_init(&slotempty[p], kXEpiWarps);
     }
     for (int b = 0; b < 2; ++b) {
@@ -241,7 +240,7 @@ k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int 
     }
     for (int i = 0; i < kXRaw; ++i) {
       mbar_init(&rfull[i], 1);
-      mbar_init(&rempty[i], kXBuilders);
+      mbar_init(&rempty[i], kXBuildWarps);
     }
     s_fail = 0;
     fence_mbar_init();
@@ -262,20 +261,23 @@ k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int 
   unsigned char* raws = stages + (size_t)kXStages * kXStageBytes;
   if (warp >= kXEpiWarps && warp < kXMmaWarp) {
     // ------------------------------------------------------------ builders
-    // thread bt: row R = bt / 2 of the tile, frames 2 fp and 2 fp + 1 of every
-    // stage (one 16-byte chunk of each row); the first 32 threads also build the
-    // columns of bin l0 + bt / 2 for the same two frames
-    const int bt = tid - 32 * kXEpiWarps;
-    const int R = bt >> 1, fp = bt & 1;
-    const bool bcol = bt < 2 * kXL;
-    const int li = bt >> 1;
+    // Builder warp wb, lane: row R = 16 wb + lane % 8 + 8 (lane / 16) of the tile,
+    // frames 2 fp and 2 fp + 1 of every stage, fp = lane / 8 % 2 (one 16-byte chunk
+    // of the row), so that 8 consecutive lanes fill one 128-byte core matrix.  Warps
+    // 0-5 also write column type wb (Re and Im columns of z, of w, of zw) of bin
+    // l0 + li, li = lane % 16, for frames 2 fq and 2 fq + 1, fq = lane / 16.  Each
+    // warp waits and arrives on its own.
+    const int bt = tid - 32 * kXEpiWarps, wb = bt >> 5;
+    const int R = 16 * wb + (lane & 7) + 8 * (lane >> 4), fp = (lane >> 3) & 1;
+    const int li = lane & 15, fq = lane >> 4;
+    const bool bcol = wb < 6;
     const float2 zero = make_float2(0.f, 0.f);
     uint32_t rq = 0, q = 0, gs = 0;
     bool ok = true;
     float2 sxy = zero, szw = zero;
     for (;;) {
       const int rs = (int)(rq % kXRaw);
-      ok = builders_all(mbar_wait_bounded(&rfull[rs], (rq / kXRaw) & 1u, status));
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&rfull[rs], (rq / kXRaw) & 1u, status));
       if (!ok) break;
       const RawRec rec = rrec[rs];
       if (rec.flags & kRecStop) break;
@@ -283,24 +285,26 @@ k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int 
       const bool rv = r <= rows_hi;
       const int kb = k < 0 ? -k : k;
       const bool lv = bcol && rec.l0 + li < M;
-      const int j0 = rec.st * kXF + 2 * fp;  // first frame of this thread's chunk
+      const int j0 = rec.st * kXF;  // first frame of the stage
       const float2* raw = reinterpret_cast<const float2*>(raws + (size_t)rs * kXRawBytes);
       float2 va[2], vb[2], vc[2], vd[2];
 #pragma unroll
       for (int jj = 0; jj < 2; ++jj) {
-        const int fj = 2 * fp + jj;  // frame within the stage
-        const bool v = rv && j0 + jj < m;
-        va[jj] = v ? raw[kRawA / 8 + fj * kRawK + kb - rec.bstart] : zero;
-        vb[jj] = v ? raw[kRawB / 8 + fj * kRawK + kb - rec.bstart] : zero;
-        const bool w = lv && j0 + jj < m;
-        vc[jj] = w ? raw[kRawC / 8 + fj * kXL + li] : zero;
-        vd[jj] = w ? raw[kRawD / 8 + fj * kXL + li] : zero;
+        const int fj = 2 * fp + jj, fk = 2 * fq + jj;  // frames within the stage
+        const bool v = rv && j0 + fj < m;
+        va[jj] = v ? raw[kRawA / 8 + fj * rawk + kb - rec.bstart] : zero;
+        vb[jj] = v ? raw[kRawB / 8 + fj * rawk + kb - rec.bstart] : zero;
+        const bool w = lv && j0 + fk < m;
+        vc[jj] = w ? raw[kRawC / 8 + fk * kXL + li] : zero;
+        vd[jj] = w ? raw[kRawD / 8 + fk * kXL + li] : zero;
       }
-      mbar_arrive_x(&rempty[rs]);  // the staged coefficients are in registers
+      __syncwarp();
+      if (lane == 0) mbar_arrive_x(&rempty[rs]);  // the warp's coefficients are in registers
       ++rq;
       const int s = (int)(q % kXStages);
-      ok = builders_all(q < (uint32_t)kXStages ||
-                        mbar_wait_bounded(&sdone[s], ((q / kXStages) & 1u) ^ 1u, status));
+      ok = __all_sync(0xffffffffu, q < (uint32_t)kXStages ||
+                                       mbar_wait_bounded(&sdone[s], ((q / kXStages) & 1u) ^ 1u,
+                                                         status));
       if (!ok) break;
       if (rec.flags & kRecFirst) sxy = szw = zero;
       unsigned char* stg = stages + (size_t)s * kXStageBytes;
@@ -319,66 +323,73 @@ k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int 
       put_split(stg + kOffAY, kAMat, o, y[0].x, y[0].y, y[1].x, y[1].y);
       put_split(stg + kOffAP, kAMat, o, xy[0].x, xy[0].y, xy[1].x, xy[1].y);
       if (bcol) {
-        // columns of bin l: z = c_l, w = d_l*, zw
-        float2 z[2], w[2], zw[2];
+        // column row wb of bin l: z = c_l (wb 0, 1), w = d_l* (2, 3), zw (4, 5); an
+        // even wb gives the Re column (ur, -ui), an odd one the Im column (ui, ur)
+        float2 u[2];
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
-          z[jj] = vc[jj];
-          w[jj] = make_float2(vd[jj].x, -vd[jj].y);
-          zw[jj] = cmulf(z[jj], w[jj]);
-          szw.x += zw[jj].x;
-          szw.y += zw[jj].y;
+          const float2 z = vc[jj], w = make_float2(vd[jj].x, -vd[jj].y);
+          const float2 zw = cmulf(z, w);
+          if (wb == 4) {
+            szw.x += zw.x;
+            szw.y += zw.y;
+          }
+          u[jj] = wb < 2 ? z : (wb < 4 ? w : zw);
         }
-        unsigned char* bxy = stg + kOffBXY;
-        put_split(bxy, kBXYMat, core_off(4 * li + 0, fp), z[0].x, -z[0].y, z[1].x, -z[1].y);
-        put_split(bxy, kBXYMat, core_off(4 * li + 1, fp), z[0].y, z[0].x, z[1].y, z[1].x);
-        put_split(bxy, kBXYMat, core_off(4 * li + 2, fp), w[0].x, -w[0].y, w[1].x, -w[1].y);
-        put_split(bxy, kBXYMat, core_off(4 * li + 3, fp), w[0].y, w[0].x, w[1].y, w[1].x);
-        unsigned char* bp = stg + kOffBP;
-        put_split(bp, kBPMat, core_off(2 * li + 0, fp), zw[0].x, -zw[0].y, zw[1].x, -zw[1].y);
-        put_split(bp, kBPMat, core_off(2 * li + 1, fp), zw[0].y, zw[0].x, zw[1].y, zw[1].x);
+        const uint32_t co = wb < 4 ? kOffBXY + core_off(kXL * wb + li, fq)
+                                   : kOffBP + core_off(kXL * (wb - 4) + li, fq);
+        const uint32_t lo = wb < 4 ? kBXYMat : kBPMat;
+        if (wb & 1)
+          put_split(stg, lo, co, u[0].y, u[0].x, u[1].y, u[1].x);
+        else
+          put_split(stg, lo, co, u[0].x, -u[0].y, u[1].x, -u[1].y);
       }
-      if (bt == 0) srec[s] = StageRec{rec.ncols, rec.flags & (kRecFirst | kRecLast)};
+      if (bt == 0) srec[s] = StageRec{rec.flags & (kRecFirst | kRecLast)};
       // the generic-proxy writes become visible to the tensor cores' reads
       fence_async_smem();
-      mbar_arrive_x(&full[s]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive_x(&full[s]);
       ++q;
       if (rec.flags & kRecLast) {
-        // the group's one-bin sums (the two chunks of a bin are adjacent lanes) and
-        // its record, for the epilogue
-        const float2 sxy_o = make_float2(__shfl_xor_sync(0xffffffffu, sxy.x, 1),
-                                         __shfl_xor_sync(0xffffffffu, sxy.y, 1));
-        const float2 szw_o = make_float2(__shfl_xor_sync(0xffffffffu, szw.x, 1),
-                                         __shfl_xor_sync(0xffffffffu, szw.y, 1));
+        // the group's one-bin sums (the two chunks of a bin are lanes 8, for the
+        // columns 16, apart) and its record, for the epilogue
+        const float2 sxy_o = make_float2(__shfl_xor_sync(0xffffffffu, sxy.x, 8),
+                                         __shfl_xor_sync(0xffffffffu, sxy.y, 8));
+        const float2 szw_o = make_float2(__shfl_xor_sync(0xffffffffu, szw.x, 16),
+                                         __shfl_xor_sync(0xffffffffu, szw.y, 16));
         const int p = (int)(gs % kXSlots);
-        ok = builders_all(gs < (uint32_t)kXSlots ||
-                          mbar_wait_bounded(&slotempty[p], ((gs / kXSlots) - 1) & 1u, status));
+        ok = __all_sync(0xffffffffu, gs < (uint32_t)kXSlots ||
+                                         mbar_wait_bounded(&slotempty[p],
+                                                           ((gs / kXSlots) - 1) & 1u, status));
         if (!ok) break;
         if (fp == 0) slot[p].sxy[R] = make_float2(sxy.x + sxy_o.x, sxy.y + sxy_o.y);
-        if (bcol && fp == 0) slot[p].szw[li] = make_float2(szw.x + szw_o.x, szw.y + szw_o.y);
+        if (wb == 4 && fq == 0) slot[p].szw[li] = make_float2(szw.x + szw_o.x, szw.y + szw_o.y);
         if (bt == 0) {
           slot[p].r0 = rec.r0;
           slot[p].l0 = rec.l0;
           slot[p].combo = rec.combo;
           slot[p].flags = rec.flags & kRecItemEnd;
         }
-        mbar_arrive_x(&slotfull[p]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive_x(&slotfull[p]);
         ++gs;
       }
     }
-    if (!ok && bt == 0) atomicExch(&s_fail, 1);
+    if (!ok && lane == 0) atomicExch(&s_fail, 1);
     // stop records: the next stage (for the MMA warp) and the next slot (epilogue)
     {
       const int s = (int)(q % kXStages);
       if (q >= (uint32_t)kXStages)
         mbar_wait_bounded(&sdone[s], ((q / kXStages) & 1u) ^ 1u, status);
-      if (bt == 0) srec[s] = StageRec{0, kRecStop};
-      mbar_arrive_x(&full[s]);
+      if (bt == 0) srec[s] = StageRec{kRecStop};
+      __syncwarp();
+      if (lane == 0) mbar_arrive_x(&full[s]);
       const int p = (int)(gs % kXSlots);
       if (gs >= (uint32_t)kXSlots)
         mbar_wait_bounded(&slotempty[p], ((gs / kXSlots) - 1) & 1u, status);
       if (bt == 0) slot[p].flags = kRecStop;
-      mbar_arrive_x(&slotfull[p]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive_x(&slotfull[p]);
     }
   } else if (warp == kXMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
@@ -401,8 +412,10 @@ k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int 
           tc_after();
         }
         const uint32_t d = taddr + b * kXBufCols;
-        const uint32_t idx = idesc0 | ((uint32_t)((4 * rec.ncols) >> 3) << 17);
-        const uint32_t idp = idesc0 | ((uint32_t)((2 * rec.ncols) >> 3) << 17);
+        // N = 64 ([z | w] columns) and 32 (zw), whatever the tile's width (columns
+        // of bins past M - 1 are zero)
+        const uint32_t idx = idesc0 | ((uint32_t)((4 * kXL) >> 3) << 17);
+        const uint32_t idp = idesc0 | ((uint32_t)((2 * kXL) >> 3) << 17);
         const uint32_t sa = sbase + (uint32_t)s * kXStageBytes;
         const bool first = (rec.flags & kRecFirst) != 0;
 #pragma unroll
@@ -444,23 +457,15 @@ k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int 
         const int chunk = item / per_chunk, rest = item - chunk * per_chunk;
         const int combo = rest / wq.n_tiles, tile = rest - combo * wq.n_tiles;
         const int r0 = 1 + (tile / wq.n_cb) * kXT, l0 = (tile % wq.n_cb) * kXL;
-        const int ncols = min(kXL, (M - l0 + 7) & ~7);
         const int g0 = chunk * wq.group_chunk, g1 = min(G, g0 + wq.group_chunk);
         const int4 cb = combos[combo];
-        const float2* A = spec + cb.x * chan_stride;
-        const float2* B = spec + cb.y * chan_stride;
-        const float2* C = spec + cb.z * chan_stride;
-        const float2* D = spec + cb.w * chan_stride;
         // bins |k| of the tile's rows: one range of at most 128 bins, staged from an
-        // even bin (16-byte aligned) in a whole number of bin pairs, within the row
+        // even bin (x 8 bytes a multiple of 16: the boxes' alignment rule)
         const int klo = r0 - (M - 1), khi = min(r0 + kXT - 1, rows_hi) - (M - 1);
         const int blo = klo >= 0 ? klo : (khi <= 0 ? -khi : 0);
-        const int bhi = klo >= 0 ? khi : (khi <= 0 ? -klo : max(-klo, khi));
         const int bstart = blo & ~1;
-        const int nb = min((bhi - bstart + 2) & ~1, Mp - bstart);
-        const uint32_t ab_bytes = (uint32_t)nb * 8u, cd_bytes = (uint32_t)kXL * 8u;
+        const uint32_t stage_bytes = 2u * 4u * 8u * (uint32_t)(rawk + kXL);
         for (int g = g0; g < g1 && ok; ++g) {
-          const long long gbase = (long long)g * m * Mp;
           for (int st = 0; st < nst; ++st) {
             const int rs = (int)(rq % kXRaw);
             if (rq >= (uint32_t)kXRaw &&
@@ -468,20 +473,19 @@ k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int 
               ok = false;
               break;
             }
-            const int nf = min(kXF, m - st * kXF);
             const int last = st == nst - 1;
-            rrec[rs] = RawRec{r0, l0, ncols, combo, bstart, st,
+            rrec[rs] = RawRec{r0, l0, combo, bstart, st,
                               (st == 0 ? kRecFirst : 0) | (last ? kRecLast : 0) |
                                   (last && g == g1 - 1 ? kRecItemEnd : 0)};
             unsigned char* dst = raws + (size_t)rs * kXRawBytes;
-            mbar_arrive_expect_tx(&rfull[rs], (uint32_t)nf * 2u * (ab_bytes + cd_bytes));
-            for (int f = 0; f < nf; ++f) {
-              const long long o = gbase + (long long)(st * kXF + f) * Mp;
-              tma_load_1d(dst + kRawA + f * kRawK * 8, A + o + bstart, ab_bytes, &rfull[rs]);
-              tma_load_1d(dst + kRawB + f * kRawK * 8, B + o + bstart, ab_bytes, &rfull[rs]);
-              tma_load_1d(dst + kRawC + f * kXL * 8, C + o + l0, cd_bytes, &rfull[rs]);
-              tma_load_1d(dst + kRawD + f * kXL * 8, D + o + l0, cd_bytes, &rfull[rs]);
-            }
+            // 4 frame rows of each channel (rows past the group's m frames are not
+            // used; rows and bins past the spectra read as zeros)
+            const int fr = g * m + st * kXF;
+            mbar_arrive_expect_tx(&rfull[rs], stage_bytes);
+            tma_load_2d(dst + kRawA, &tm_ab, bstart, cb.x * chan_rows + fr, &rfull[rs]);
+            tma_load_2d(dst + kRawB, &tm_ab, bstart, cb.y * chan_rows + fr, &rfull[rs]);
+            tma_load_2d(dst + kRawC, &tm_cd, l0, cb.z * chan_rows + fr, &rfull[rs]);
+            tma_load_2d(dst + kRawD, &tm_cd, l0, cb.w * chan_rows + fr, &rfull[rs]);
             ++rq;
           }
         }
@@ -530,23 +534,21 @@ k3_trispec_cross_tc(const float2* __restrict__ spec, long long chan_stride, int 
       for (int hh = 0; hh < 2; ++hh) {
         const int li0 = 8 * h + 4 * hh;
         if (l0 + li0 < M) {  // warp-uniform
-          float dx[16], dy[16], dp[8];
-          tmem_ld16(tb + 4 * li0, dx);
-          tmem_ld16(tb + kColY + 4 * li0, dy);
-          tmem_ld8(tb + kColP + 2 * li0, dp);
+          // columns li0 .. li0 + 3 of each of the ten product types
+          float d[10][4];
+#pragma unroll
+          for (int t = 0; t < 10; ++t) tmem_ld4(tb + kXL * t + li0, d[t]);
           tc_wait_ld();
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const float2 szw = slot[p].szw[li0 + i];
-            const float2 xz = make_float2(dx[4 * i], dx[4 * i + 1]);
-            const float2 xw = make_float2(dx[4 * i + 2], dx[4 * i + 3]);
-            const float2 yz = make_float2(dy[4 * i], dy[4 * i + 1]);
-            const float2 yw = make_float2(dy[4 * i + 2], dy[4 * i + 3]);
+            const float2 xz = make_float2(d[0][i], d[1][i]), xw = make_float2(d[2][i], d[3][i]);
+            const float2 yz = make_float2(d[4][i], d[5][i]), yw = make_float2(d[6][i], d[7][i]);
             float2 t = cmulf(sxy, szw);
             cmacf(t, xz, yw);
             cmacf(t, xw, yz);
-            const float cr = pref * fmaf(fmm, dp[2 * i], -fm1 * t.x);
-            const float ci = pref * fmaf(fmm, dp[2 * i + 1], -fm1 * t.y);
+            const float cr = pref * fmaf(fmm, d[8][i], -fm1 * t.x);
+            const float ci = pref * fmaf(fmm, d[9][i], -fm1 * t.y);
             const int e = 4 * hh + i;
             sre[e] += cr;
             sim[e] += ci;
@@ -602,12 +604,13 @@ __global__ void k3_cross_row0(double* __restrict__ acc, int n, int M, long long 
 
 }  // namespace
 
-cudaError_t launch_k3_trispec_cross_tc(const float2* spec, long long chan_stride, int G, int m,
-                                       int M, int Mp, const int4* combos, int n_combos,
-                                       double* acc, long long plane, int nsm, bool natural,
-                                       int* counter, int* status, cudaStream_t stream) {
+cudaError_t launch_k3_trispec_cross_tc(const CUtensorMap& tm_ab, const CUtensorMap& tm_cd,
+                                       int chan_rows, int G, int m, int M, int Mp,
+                                       const int4* combos, int n_combos, double* acc,
+                                       long long plane, int nsm, bool natural, int* counter,
+                                       int* status, cudaStream_t stream) {
   if (G <= 0 || n_combos <= 0) return cudaSuccess;
-  if (m < 1 || M < 2 || nsm <= 0) return cudaErrorInvalidValue;
+  if (m < 1 || M < 2 || nsm <= 0 || (Mp & 15) || Mp < M) return cudaErrorInvalidValue;
   const int n_rb = (2 * M - 2 + kXT - 1) / kXT, n_cb = (M + kXL - 1) / kXL;
   const long long n_tiles = (long long)n_rb * n_cb;
   CrossQueue wq;
@@ -633,8 +636,10 @@ cudaError_t launch_k3_trispec_cross_tc(const float2* spec, long long chan_stride
   const float fmm = (float)(natural ? md : md * (md + 1.0));
   const float fm1 = (float)(natural ? 1.0 : md - 1.0);
   const long long combo_stride = (long long)(2 * M - 1) * M;
-  kern<<<nsm, kXThreads, kXSmemBytes, stream>>>(spec, chan_stride, G, m, M, Mp, combos, wq, pref,
-                                                fmm, fm1, acc, plane, combo_stride, status);
+  const int rawk = std::min(kRawK, Mp);  // the box width of tm_ab
+  kern<<<nsm, kXThreads, kXSmemBytes, stream>>>(tm_ab, tm_cd, chan_rows, rawk, G, m, M, Mp,
+                                                combos, wq, pref, fmm, fm1, acc, plane,
+                                                combo_stride, status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int n = 4 * n_combos * M;

@@ -327,10 +327,10 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
                                             p->d_c4cross, (int)p->c4.size(), p->d_acc4, plane,
                                             p->nsm, nat, p->stream));
         else if (p->C > 1)
-          SS_TRY(p, launch_k3_trispec_cross_tc(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp,
-                                               p->d_c4cross, (int)p->c4.size(), p->d_acc4,
-                                               plane, p->nsm, nat, p->d_counter, p->d_status,
-                                               p->stream));
+          SS_TRY(p, launch_k3_trispec_cross_tc(p->tmx_ab, p->tmx_cd, p->Gb_max * p->m, cnt,
+                                               p->m, p->M, p->Mp, p->d_c4cross,
+                                               (int)p->c4.size(), p->d_acc4, plane, p->nsm, nat,
+                                               p->d_counter, p->d_status, p->stream));
         for (size_t i = 0; i < p->c4.size() && p->C == 1; ++i) {
           const Combo& cb = p->c4[i];
           if (p->precision == SS_PREC_FP32)
@@ -523,6 +523,24 @@ ss_status encode_maps(ss_plan_s* p) {
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
       return fail(p, SS_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string(r));
+  }
+  if (p->C > 1) {
+    // 2-D views [rows][Mp] for the tensor-core cross S4: boxes of 4 frame rows by
+    // min(kCrossBoxBins, Mp) bins (rows of a and b) or by 16 bins (c and d)
+    const cuuint64_t d2[2] = {(cuuint64_t)p->Mp, rows};
+    const cuuint64_t s2[1] = {(cuuint64_t)p->Mp * sizeof(float2)};
+    const cuuint32_t e2[2] = {1, 1};
+    const cuuint32_t bab[2] = {(cuuint32_t)std::min(kCrossBoxBins, p->Mp), 4};
+    const cuuint32_t bcd[2] = {16, 4};
+    for (int i = 0; i < 2; ++i) {
+      CUresult r = encode(i == 0 ? &p->tmx_ab : &p->tmx_cd, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                          p->d_spec, d2, s2, i == 0 ? bab : bcd, e2,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(p, SS_ECUDA,
+                    "cuTensorMapEncodeTiled (cross views) failed with code " + std::to_string(r));
+    }
   }
   if (p->oi.img) {
     // Gram operand image of each channel as [group][row group][chunk][2 CB bytes]
