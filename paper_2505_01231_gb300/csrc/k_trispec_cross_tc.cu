@@ -49,19 +49,20 @@ namespace ss {
 namespace {
 
 constexpr int kXT = 128;     // rows of a tile
-constexpr int kXL = 16;      // columns of a tile
+constexpr int kXL = kCrossTileCols;  // columns of a tile (24)
+constexpr int kXLw = kXL / 2;        // columns of an epilogue warp
 constexpr int kXF = 4;       // frames per stage: K = 8 TF32 values, one MMA K step
 constexpr int kXStages = 4;  // operand stages
-constexpr int kXRaw = 8;     // stages of staged coefficients
+constexpr int kXRaw = 6;     // stages of staged coefficients
 constexpr int kXEpiWarps = 8, kXBuildWarps = 8;
 constexpr int kXMmaWarp = kXEpiWarps + kXBuildWarps, kXLoadWarp = kXMmaWarp + 1;
 constexpr int kXThreads = 32 * (kXLoadWarp + 1);
 constexpr int kXSlots = 4;
 constexpr uint32_t kXTmemCols = 512;
-// TMEM buffer b starts at column 256 b: 16 columns (one per l) each of Re Sxz,
-// Im Sxz, Re Sxw, Im Sxw, then of Re Syz, Im Syz, Re Syw, Im Syw at +64, then of
-// Re P, Im P at +128 (the B rows are ordered the same way: type-major)
-constexpr uint32_t kXBufCols = 256, kColY = 64, kColP = 128;
+// TMEM buffer b starts at column 256 b: 24 columns (one per l) each of Re Sxz,
+// Im Sxz, Re Sxw, Im Sxw, then of Re Syz, Im Syz, Re Syw, Im Syw at +96, then of
+// Re P, Im P at +192 (the B rows are ordered the same way: type-major)
+constexpr uint32_t kXBufCols = 256, kColY = 4 * kXL, kColP = 8 * kXL;
 
 // A stage: for each matrix a hi block, then a lo block.  A matrix of R rows x 8
 // TF32 values is R/8 row groups of two core matrices (8 rows x 16 bytes: frames
@@ -95,7 +96,7 @@ struct RawRec {  // a staged stage: its tile, combination, first staged bin, fra
 
 struct CrossSlot {  // one group: its one-bin sums and record, for the epilogue
   float2 sxy[kXT];
-  float2 szw[kXL];
+  float2 szw[2][kXL];  // over frames 4i, 4i + 1 and over 4i + 2, 4i + 3
   int r0, l0, combo, flags;
 };
 
@@ -155,37 +156,13 @@ __device__ __forceinline__ void mma_commit_x(uint64_t* bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
-  uint32_t r[4];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float (&v)[2]) {
+  uint32_t r[2];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
                : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+  v[0] = __uint_as_float(r[0]);
+  v[1] = __uint_as_float(r[1]);
 }
 
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -263,18 +240,26 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
     // ------------------------------------------------------------ builders
     // Builder warp wb, lane: row R = 16 wb + lane % 8 + 8 (lane / 16) of the tile,
     // frames 2 fp and 2 fp + 1 of every stage, fp = lane / 8 % 2 (one 16-byte chunk
-    // of the row), so that 8 consecutive lanes fill one 128-byte core matrix.  Warps
-    // 0-5 also write column type wb (Re and Im columns of z, of w, of zw) of bin
-    // l0 + li, li = lane % 16, for frames 2 fq and 2 fq + 1, fq = lane / 16.  Each
-    // warp waits and arrives on its own.
+    // of the row), so that 8 consecutive lanes fill one 128-byte core matrix.  The
+    // column rows are 6 types (Re and Im columns of z, of w, of zw) x 24 bins x 2
+    // chunks = 288 tasks: thread bt takes tasks bt and bt + 256, task i being type
+    // i / 48, chunk i / 24 % 2, bin i % 24 (8 consecutive tasks fill one core
+    // matrix).  Each warp waits and arrives on its own.
+    constexpr int kTasks = 6 * 2 * kXL;
     const int bt = tid - 32 * kXEpiWarps, wb = bt >> 5;
     const int R = 16 * wb + (lane & 7) + 8 * (lane >> 4), fp = (lane >> 3) & 1;
-    const int li = lane & 15, fq = lane >> 4;
-    const bool bcol = wb < 6;
+    int tt[2], tli[2], tfq[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = bt + u * 32 * kXBuildWarps;
+      tt[u] = i < kTasks ? i / (2 * kXL) : -1;
+      tli[u] = i % kXL;
+      tfq[u] = (i / kXL) & 1;
+    }
     const float2 zero = make_float2(0.f, 0.f);
     uint32_t rq = 0, q = 0, gs = 0;
     bool ok = true;
-    float2 sxy = zero, szw = zero;
+    float2 sxy = zero, szw = zero;  // szw: the task of type 4 (Re zw), if any
     for (;;) {
       const int rs = (int)(rq % kXRaw);
       ok = __all_sync(0xffffffffu, mbar_wait_bounded(&rfull[rs], (rq / kXRaw) & 1u, status));
@@ -284,19 +269,22 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
       const int r = rec.r0 + R, k = r - (M - 1);
       const bool rv = r <= rows_hi;
       const int kb = k < 0 ? -k : k;
-      const bool lv = bcol && rec.l0 + li < M;
       const int j0 = rec.st * kXF;  // first frame of the stage
       const float2* raw = reinterpret_cast<const float2*>(raws + (size_t)rs * kXRawBytes);
-      float2 va[2], vb[2], vc[2], vd[2];
+      float2 va[2], vb[2], vc[2][2], vd[2][2];
 #pragma unroll
       for (int jj = 0; jj < 2; ++jj) {
-        const int fj = 2 * fp + jj, fk = 2 * fq + jj;  // frames within the stage
+        const int fj = 2 * fp + jj;  // frame within the stage
         const bool v = rv && j0 + fj < m;
         va[jj] = v ? raw[kRawA / 8 + fj * rawk + kb - rec.bstart] : zero;
         vb[jj] = v ? raw[kRawB / 8 + fj * rawk + kb - rec.bstart] : zero;
-        const bool w = lv && j0 + fk < m;
-        vc[jj] = w ? raw[kRawC / 8 + fk * kXL + li] : zero;
-        vd[jj] = w ? raw[kRawD / 8 + fk * kXL + li] : zero;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int fk = 2 * tfq[u] + jj;
+          const bool w = tt[u] >= 0 && rec.l0 + tli[u] < M && j0 + fk < m;
+          vc[u][jj] = w ? raw[kRawC / 8 + fk * kXL + tli[u]] : zero;
+          vd[u][jj] = w ? raw[kRawD / 8 + fk * kXL + tli[u]] : zero;
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive_x(&rempty[rs]);  // the warp's coefficients are in registers
@@ -322,27 +310,30 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
       put_split(stg + kOffAX, kAMat, o, x[0].x, x[0].y, x[1].x, x[1].y);
       put_split(stg + kOffAY, kAMat, o, y[0].x, y[0].y, y[1].x, y[1].y);
       put_split(stg + kOffAP, kAMat, o, xy[0].x, xy[0].y, xy[1].x, xy[1].y);
-      if (bcol) {
-        // column row wb of bin l: z = c_l (wb 0, 1), w = d_l* (2, 3), zw (4, 5); an
-        // even wb gives the Re column (ur, -ui), an odd one the Im column (ui, ur)
-        float2 u[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int t = tt[u];
+        if (t < 0) continue;
+        // column row of type t of bin l: z = c_l (t 0, 1), w = d_l* (2, 3), zw (4, 5);
+        // an even t gives the Re column (ur, -ui), an odd one the Im column (ui, ur)
+        float2 v[2];
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
-          const float2 z = vc[jj], w = make_float2(vd[jj].x, -vd[jj].y);
+          const float2 z = vc[u][jj], w = make_float2(vd[u][jj].x, -vd[u][jj].y);
           const float2 zw = cmulf(z, w);
-          if (wb == 4) {
+          if (t == 4) {
             szw.x += zw.x;
             szw.y += zw.y;
           }
-          u[jj] = wb < 2 ? z : (wb < 4 ? w : zw);
+          v[jj] = t < 2 ? z : (t < 4 ? w : zw);
         }
-        const uint32_t co = wb < 4 ? kOffBXY + core_off(kXL * wb + li, fq)
-                                   : kOffBP + core_off(kXL * (wb - 4) + li, fq);
-        const uint32_t lo = wb < 4 ? kBXYMat : kBPMat;
-        if (wb & 1)
-          put_split(stg, lo, co, u[0].y, u[0].x, u[1].y, u[1].x);
+        const uint32_t co = t < 4 ? kOffBXY + core_off(kXL * t + tli[u], tfq[u])
+                                  : kOffBP + core_off(kXL * (t - 4) + tli[u], tfq[u]);
+        const uint32_t lo = t < 4 ? kBXYMat : kBPMat;
+        if (t & 1)
+          put_split(stg, lo, co, v[0].y, v[0].x, v[1].y, v[1].x);
         else
-          put_split(stg, lo, co, u[0].x, -u[0].y, u[1].x, -u[1].y);
+          put_split(stg, lo, co, v[0].x, -v[0].y, v[1].x, -v[1].y);
       }
       if (bt == 0) srec[s] = StageRec{rec.flags & (kRecFirst | kRecLast)};
       // the generic-proxy writes become visible to the tensor cores' reads
@@ -351,19 +342,17 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
       if (lane == 0) mbar_arrive_x(&full[s]);
       ++q;
       if (rec.flags & kRecLast) {
-        // the group's one-bin sums (the two chunks of a bin are lanes 8, for the
-        // columns 16, apart) and its record, for the epilogue
+        // the group's one-bin sums (the two chunks of a row are lanes 8 apart; the
+        // column sums go per chunk) and its record, for the epilogue
         const float2 sxy_o = make_float2(__shfl_xor_sync(0xffffffffu, sxy.x, 8),
                                          __shfl_xor_sync(0xffffffffu, sxy.y, 8));
-        const float2 szw_o = make_float2(__shfl_xor_sync(0xffffffffu, szw.x, 16),
-                                         __shfl_xor_sync(0xffffffffu, szw.y, 16));
         const int p = (int)(gs % kXSlots);
         ok = __all_sync(0xffffffffu, gs < (uint32_t)kXSlots ||
                                          mbar_wait_bounded(&slotempty[p],
                                                            ((gs / kXSlots) - 1) & 1u, status));
         if (!ok) break;
         if (fp == 0) slot[p].sxy[R] = make_float2(sxy.x + sxy_o.x, sxy.y + sxy_o.y);
-        if (wb == 4 && fq == 0) slot[p].szw[li] = make_float2(szw.x + szw_o.x, szw.y + szw_o.y);
+        if (tt[0] == 4) slot[p].szw[tfq[0]][tli[0]] = szw;
         if (bt == 0) {
           slot[p].r0 = rec.r0;
           slot[p].l0 = rec.l0;
@@ -509,9 +498,9 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
     const int qd = warp & 3, h = warp >> 2;
     const int R = 32 * qd + lane;
     const uint32_t lane_addr = taddr + ((uint32_t)(32 * qd) << 16);
-    float sre[8], sim[8], qre[8], qim[8];
+    float sre[kXLw], sim[kXLw], qre[kXLw], qim[kXLw];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) sre[i] = sim[i] = qre[i] = qim[i] = 0.f;
+    for (int i = 0; i < kXLw; ++i) sre[i] = sim[i] = qre[i] = qim[i] = 0.f;
     for (uint32_t gc = 0;; ++gc) {
       const int p = (int)(gc % kXSlots);
       const uint32_t b = gc & 1u;
@@ -531,17 +520,18 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
       const float2 sxy = slot[p].sxy[R];
       const uint32_t tb = lane_addr + b * kXBufCols;
 #pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const int li0 = 8 * h + 4 * hh;
+      for (int hh = 0; hh < kXLw / 2; ++hh) {
+        const int li0 = kXLw * h + 2 * hh;
         if (l0 + li0 < M) {  // warp-uniform
-          // columns li0 .. li0 + 3 of each of the ten product types
-          float d[10][4];
+          // columns li0, li0 + 1 of each of the ten product types
+          float d[10][2];
 #pragma unroll
-          for (int t = 0; t < 10; ++t) tmem_ld4(tb + kXL * t + li0, d[t]);
+          for (int t = 0; t < 10; ++t) tmem_ld2(tb + kXL * t + li0, d[t]);
           tc_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float2 szw = slot[p].szw[li0 + i];
+          for (int i = 0; i < 2; ++i) {
+            const float2 szw = make_float2(slot[p].szw[0][li0 + i].x + slot[p].szw[1][li0 + i].x,
+                                           slot[p].szw[0][li0 + i].y + slot[p].szw[1][li0 + i].y);
             const float2 xz = make_float2(d[0][i], d[1][i]), xw = make_float2(d[2][i], d[3][i]);
             const float2 yz = make_float2(d[4][i], d[5][i]), yw = make_float2(d[6][i], d[7][i]);
             float2 t = cmulf(sxy, szw);
@@ -549,7 +539,7 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
             cmacf(t, xw, yz);
             const float cr = pref * fmaf(fmm, d[8][i], -fm1 * t.x);
             const float ci = pref * fmaf(fmm, d[9][i], -fm1 * t.y);
-            const int e = 4 * hh + i;
+            const int e = 2 * hh + i;
             sre[e] += cr;
             sim[e] += ci;
             qre[e] = fmaf(cr, cr, qre[e]);
@@ -568,8 +558,8 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
         const int r = slot[p].r0 + R;
         const long long cbase = (long long)slot[p].combo * combo_stride;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int lc = l0 + 8 * h + e;
+        for (int e = 0; e < kXLw; ++e) {
+          const int lc = l0 + kXLw * h + e;
           if (r <= rows_hi && lc < M) {
             const long long o = cbase + (long long)r * M + lc;
             atomicAdd(acc + o, (double)sre[e]);
