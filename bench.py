@@ -200,6 +200,35 @@ def measure_peaks(gpu_index):
     return out
 
 
+def mma_shapes(gpu_index):
+    """tcgen05 product rate against N (M = 128; K = 8 TF32 or 16 BF16 per product),
+    the measurement behind the cross-channel S4 tile width: narrow products are
+    paced by their operand reads from shared memory, not by the multipliers."""
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2505_01231_gb300", "libsspeaks.so"))
+    lib.ssp_mma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    import torch
+    nsm = torch.cuda.get_device_properties(gpu_index).multi_processor_count
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.2)
+    iters, out = 100000, {}
+    for kind, name in ((0, "tf32"), (1, "bf16")):
+        for n in (32, 64, 96, 128, 256):
+            sec, rate = ctypes.c_double(), ctypes.c_double()
+            if lib.ssp_mma_rate(kind, n, iters, ctypes.byref(sec), ctypes.byref(rate)) != 0:
+                continue
+            per_product = sec.value / (iters * 4)              # one SM's products are serial
+            kbytes = 128 * 32 / 1024 + n * 32 / 1024           # A and B read per product (KB)
+            out[f"{name}_n{n}"] = {"tflops": rate.value / 1e12, "ns_per_product": per_product * 1e9,
+                                   "operand_kb_per_product": kbytes,
+                                   "operand_gb_s_per_sm": kbytes * 1024 / per_product / 1e9}
+    info = clocks.stop()
+    return {"mma_shapes": out, "sms": nsm, "clocks": info,
+            "how": "libsspeaks.so ssp_mma_rate: one CTA per SM, one thread issuing 128 x N products "
+                   "from shared memory (K-major, no swizzle) into two TMEM accumulators; CUDA events"}
+
+
 def traffic_for(kernel):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is
     unchanged since the capture (source hash recorded beside the figure)."""
@@ -484,6 +513,8 @@ def main():
                     help="apply this tuning text (ss_set_tuning) instead of autotuning")
     ap.add_argument("--fp32-steps", type=int, default=3,
                     help="steps of the all-FP32 S4 arm (0 = skip)")
+    ap.add_argument("--mma-shapes", action="store_true",
+                    help="print the tcgen05 product rate against N and exit")
     ap.add_argument("--precision", default="fp16x3",
                     choices=["fp32", "tf32x3", "bf16x3", "bf16", "fp16x3"],
                     help="arithmetic of the S4 moment sums")
@@ -494,6 +525,11 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, w, rank, world)
+        return
+    if args.mma_shapes:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(mma_shapes(local)), flush=True)
         return
     if args.workload in REFUSED:
         if rank == 0:

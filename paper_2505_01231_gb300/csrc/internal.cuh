@@ -163,10 +163,11 @@ int k3tc_stage_chunks(int precision);
 // in three passes): tiles of 128 rows k x 24 columns l, operands built in shared
 // memory from the centred spectra, read through two 2-D views [rows][Mp] of
 // them (8-byte elements, no swizzle): tm_ab with boxes of 4 rows x
-// min(kCrossBoxBins, Mp) bins, tm_cd with boxes of 4 rows x kCrossTileCols bins; a channel's
+// min(kCrossBoxBins, Mp) bins, tm_cd with boxes of 4 rows x kCrossColBox bins; a channel's
 // rows start at channel x chan_rows.  The row k = -(M-1) is copied from k = M-1
 // (equal for real signals).  counter and status as for the pair kernels.
-constexpr int kCrossBoxBins = 140, kCrossTileCols = 24;
+// (the c, d box is 4 bins wider than a tile, so that its rows fall on other banks)
+constexpr int kCrossBoxBins = 140, kCrossTileCols = 24, kCrossColBox = 28;
 cudaError_t launch_k3_trispec_cross_tc(const CUtensorMap& tm_ab, const CUtensorMap& tm_cd,
                                        int chan_rows, int G, int m, int M, int Mp,
                                        const int4* combos, int n_combos, double* acc,

@@ -6,33 +6,40 @@
 // x_j = da_jk, y_j = db_jk*, z_j = dc_jl, w_j = dd_jl* (a_{-k} = a_k*):
 //   c4(k, l) = pref [fmm P - fm1 (Sxy Szw + Sxz Syw + Sxw Syz)],
 //   P = sum_j x_j y_j z_j w_j,   Suv = sum_j u_j v_j   (j over the m frames).
-// Over a tile of 128 rows k and 16 columns l, Sxz, Sxw, Syz, Syw and P are
+// Over a tile of 128 rows k and 24 columns l, Sxz, Sxw, Syz, Syw and P are
 // complex matrix products with the frames as K:
-//   rows x (128 x m) and rows y (128 x m) times columns [z | w] (m x 32), and
-//   rows xy (128 x m) times columns zw (m x 16).
+//   rows x (128 x m) and rows y (128 x m) times columns [z | w] (m x 48), and
+//   rows xy (128 x m) times columns zw (m x 24).
 // Each complex product is a real one with K = 2m (real and imaginary part of
 // frame j at 2j and 2j + 1): a row u is (ur_j, ui_j); the column giving Re(u v)
-// is (vr_j, -vi_j) and the one giving Im(u v) is (vi_j, vr_j).  The products run
-// as TF32 hi/lo splits in three passes (hi hi + hi lo + lo hi) accumulated in
-// FP32 in TMEM.  Sxy and Szw depend on one bin each and are summed by the threads
-// that build the operands.
+// is (vr_j, -vi_j) and the one giving Im(u v) is (vi_j, vr_j), so [z | w] is 96
+// real columns and zw 48.  The products run as TF32 hi/lo splits in three passes
+// (hi hi + hi lo + lo hi) accumulated in FP32 in TMEM.  Sxy and Szw depend on one
+// bin each and are summed by the threads that build the operands.
+//
+// The products are bound by shared-memory bandwidth: an M = 128, N <= 128 TF32
+// product reads its operands at about 120 bytes per clock, the port's rate, so
+// the tile is as wide as two TMEM buffers allow and every other shared-memory
+// access (staging, building) is kept to one pass, free of bank conflicts.
 //
 // Grid: one persistent CTA per SM (all 512 TMEM columns).  Items (group chunk,
 // combination, tile) come from a group-major queue.  Warp roles, coupled only by
 // mbarriers:
 // - warp 17 takes the items and, per stage of 4 frames, stages the coefficients
-//   the tile needs (the bins |k| of its rows of a and b, at most 130 consecutive
-//   bins, and the 16 bins of c and d) with 1-D bulk copies into a ring of 8, with
-//   the stage's record;
+//   the tile needs with four 2-D tensor-map boxes (4 frame rows of a and of b over
+//   the bins |k| of the tile's rows, at most 130 consecutive bins from an even
+//   bin; 4 frame rows of c and of d over its 24 bins) into a ring of 6, with the
+//   stage's record;
 // - warps 8-15 build each stage from them: the TF32 hi and lo parts of x, y, xy
-//   for the tile's 128 rows and of the [z | w] and zw columns for its 16 columns
-//   (a thread: one row, two frames), written to shared memory in the K-major
-//   core-matrix layout of the MMA descriptors (no copy of the operands exists in
-//   HBM), plus the group's Sxy and Szw and its record in a ring of slots;
+//   for the tile's 128 rows (a thread: one row, two frames) and of the [z | w]
+//   and zw columns (288 tasks of one column row and two frames), written to
+//   shared memory in the K-major core-matrix layout of the MMA descriptors (no
+//   copy of the operands exists in HBM), plus the group's Sxy and Szw and its
+//   record in a ring of slots;
 // - warp 16 issues, per stage, the nine MMAs (3 products x 3 passes) into the
-//   group's TMEM buffer (two buffers of 160 columns, alternating by group), and
+//   group's TMEM buffer (two buffers of 240 columns, alternating by group), and
 //   commits the stage (free again) and, after the group's last stage, the buffer;
-// - warps 0-7 (TMEM lane quadrant warp % 4, 8 of the 16 columns each) read the
+// - warps 0-7 (TMEM lane quadrant warp % 4, 12 of the 24 columns each) read the
 //   buffer, form c4 and keep each point's sums of Re, Im, Re^2 and Im^2 over the
 //   item's groups in registers; at the end of an item they add them to the
 //   float64 accumulators.
@@ -40,8 +47,8 @@
 // (k = -(M - 1)) equals the row r = 2M - 2: for a real signal the Nyquist
 // coefficient X(M - 1) is real, so x, y at k = -(M - 1) are those at k = M - 1;
 // a small kernel copies that row's sums after every batch.  Every wait is
-// bounded; on a failure the CTA stops, waits for the products it issued and
-// frees its TMEM.
+// bounded; on a failure the CTA stops, waits for the copies and products it
+// issued and frees its TMEM.
 #include "internal.cuh"
 #include "pipeline.cuh"
 
@@ -75,12 +82,12 @@ constexpr uint32_t kOffBXY = 6 * kAMat, kOffBP = kOffBXY + 2 * kBXYMat;
 constexpr uint32_t kXStageBytes = kOffBP + 2 * kBPMat;    // 30 KB
 // A stage of staged coefficients (4 frames): the bins of a and b that the tile's
 // rows need (at most 130 consecutive bins from an even bin; a box of 4 rows x
-// min(kRawK, Mp) bins, rows rawk bins apart), then the 16 bins of c and d of its
-// columns.
+// min(kRawK, Mp) bins, rows rawk bins apart), then the 24 bins of c and d of its
+// columns (boxes of 4 rows x kCrossColBox bins).
 constexpr int kRawK = kCrossBoxBins;
 constexpr uint32_t kRawA = 0, kRawB = kXF * kRawK * 8, kRawC = 2 * kXF * kRawK * 8,
-                   kRawD = kRawC + kXF * kXL * 8;
-constexpr uint32_t kXRawBytes = kRawD + kXF * kXL * 8;      // 9.5 KB
+                   kRawD = kRawC + kXF * kCrossColBox * 8;
+constexpr uint32_t kXRawBytes = kRawD + kXF * kCrossColBox * 8;  // 10.5 KB
 constexpr size_t kXSmemBytes =
     (size_t)kXStages * kXStageBytes + (size_t)kXRaw * kXRawBytes + 128;
 
@@ -282,8 +289,8 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
         for (int u = 0; u < 2; ++u) {
           const int fk = 2 * tfq[u] + jj;
           const bool w = tt[u] >= 0 && rec.l0 + tli[u] < M && j0 + fk < m;
-          vc[u][jj] = w ? raw[kRawC / 8 + fk * kXL + tli[u]] : zero;
-          vd[u][jj] = w ? raw[kRawD / 8 + fk * kXL + tli[u]] : zero;
+          vc[u][jj] = w ? raw[kRawC / 8 + fk * kCrossColBox + tli[u]] : zero;
+          vd[u][jj] = w ? raw[kRawD / 8 + fk * kCrossColBox + tli[u]] : zero;
         }
       }
       __syncwarp();
@@ -453,7 +460,7 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
         const int klo = r0 - (M - 1), khi = min(r0 + kXT - 1, rows_hi) - (M - 1);
         const int blo = klo >= 0 ? klo : (khi <= 0 ? -khi : 0);
         const int bstart = blo & ~1;
-        const uint32_t stage_bytes = 2u * 4u * 8u * (uint32_t)(rawk + kXL);
+        const uint32_t stage_bytes = 2u * 4u * 8u * (uint32_t)(rawk + kCrossColBox);
         for (int g = g0; g < g1 && ok; ++g) {
           for (int st = 0; st < nst; ++st) {
             const int rs = (int)(rq % kXRaw);
@@ -516,7 +523,8 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
         break;
       }
       tc_after();
-      const int l0 = slot[p].l0;
+      // the whole record is read before the slot is released below
+      const int l0 = slot[p].l0, r0 = slot[p].r0, combo = slot[p].combo;
       const float2 sxy = slot[p].sxy[R];
       const uint32_t tb = lane_addr + b * kXBufCols;
 #pragma unroll
@@ -555,8 +563,8 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
         mbar_arrive_x(&slotempty[p]);
       }
       if (flags & kRecItemEnd) {
-        const int r = slot[p].r0 + R;
-        const long long cbase = (long long)slot[p].combo * combo_stride;
+        const int r = r0 + R;
+        const long long cbase = (long long)combo * combo_stride;
 #pragma unroll
         for (int e = 0; e < kXLw; ++e) {
           const int lc = l0 + kXLw * h + e;

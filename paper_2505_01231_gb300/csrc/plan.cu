@@ -526,12 +526,12 @@ ss_status encode_maps(ss_plan_s* p) {
   }
   if (p->C > 1) {
     // 2-D views [rows][Mp] for the tensor-core cross S4: boxes of 4 frame rows by
-    // min(kCrossBoxBins, Mp) bins (rows of a and b) or by kCrossTileCols bins (c and d)
+    // min(kCrossBoxBins, Mp) bins (rows of a and b) or by kCrossColBox bins (c and d)
     const cuuint64_t d2[2] = {(cuuint64_t)p->Mp, rows};
     const cuuint64_t s2[1] = {(cuuint64_t)p->Mp * sizeof(float2)};
     const cuuint32_t e2[2] = {1, 1};
     const cuuint32_t bab[2] = {(cuuint32_t)std::min(kCrossBoxBins, p->Mp), 4};
-    const cuuint32_t bcd[2] = {(cuuint32_t)kCrossTileCols, 4};
+    const cuuint32_t bcd[2] = {(cuuint32_t)kCrossColBox, 4};
     for (int i = 0; i < 2; ++i) {
       CUresult r = encode(i == 0 ? &p->tmx_ab : &p->tmx_cd, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
                           p->d_spec, d2, s2, i == 0 ? bab : bcd, e2,

@@ -10,6 +10,9 @@
 //                    from shared-memory operands (K-major, no swizzle) into two
 //                    alternating TMEM accumulators, then waits (bounded) for
 //                    their completion.
+//   ssp_mma_rate  -- the same with N = 32, 64, 96, 128 or 256: the rate of narrow
+//                    products, whose operand reads from shared memory rather
+//                    than the multipliers set the pace.
 // Both time the kernel with CUDA events on a stream of their own and return the
 // rate in FLOP/s (an FMA counts two).
 #include <cuda_fp16.h>
@@ -50,18 +53,17 @@ __device__ __forceinline__ uint64_t mdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
 
-constexpr int kMmaM = 128, kMmaN = 256;
+constexpr int kMmaM = 128;
 constexpr uint32_t kRowBytes = 128;                       // K bytes per operand row
 constexpr uint32_t kABytes = kMmaM * kRowBytes;            // 16 KB
-constexpr uint32_t kBBytes = kMmaN * kRowBytes;            // 32 KB
-constexpr uint32_t kSmemBytes = kABytes + kBBytes + 1024;  // + alignment slack
 constexpr uint32_t kPad = 96u << 10;                       // keeps one CTA per SM
 constexpr unsigned long long kMmaWaitNs = 20000000000ull;  // 20 s
 
-// kType: 0 = TF32 (kind::tf32), 1 = BF16, 2 = FP16 (both kind::f16)
-template <int kType>
+// kType: 0 = TF32 (kind::tf32), 1 = BF16, 2 = FP16 (both kind::f16); kMmaN: N
+template <int kType, int kMmaN>
 __global__ void __launch_bounds__(128, 1)
 k_mma(int iters, int* __restrict__ status) {
+  constexpr uint32_t kBBytes = kMmaN * kRowBytes;
   constexpr bool kBF16 = kType != 0;  // a 16-bit kind::f16 type
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t done;
@@ -193,23 +195,30 @@ int ssp_fma_peak(int iters, double* seconds, double* flops_per_s) {
   return rc;
 }
 
-// tcgen05 dense product rate of the whole device, kind 0 = kind::tf32,
-// 1 = kind::f16 with BF16 inputs, 2 = kind::f16 with FP16 inputs; returns 0, or
-// 1 if a bounded wait ran out.
-int ssp_mma_peak(int kind, int iters, double* seconds, double* flops_per_s) {
+// tcgen05 dense product rate of the whole device for products of M = 128 and the
+// given N, kind 0 = kind::tf32, 1 = kind::f16 with BF16 inputs, 2 = kind::f16 with
+// FP16 inputs; returns 0, 1 if a bounded wait ran out, -1 on an error (or an N
+// other than 32, 64, 96, 128, 256).
+int ssp_mma_rate(int kind, int n, int iters, double* seconds, double* flops_per_s) {
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
   if (iters < 2) iters = 2;
+  if (kind < 0 || kind > 2) return -1;
+  void (*kern)(int, int*) = nullptr;
+#define SSP_PICK(N)                                                              \
+  if (n == N) kern = kind == 1 ? k_mma<1, N> : kind == 2 ? k_mma<2, N> : k_mma<0, N>;
+  SSP_PICK(32)
+  SSP_PICK(64)
+  SSP_PICK(96)
+  SSP_PICK(128)
+  SSP_PICK(256)
+#undef SSP_PICK
+  if (!kern) return -1;
   int* status = nullptr;
   if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) return -1;
   cudaMemset(status, 0, sizeof(int));
-  if (kind < 0 || kind > 2) {
-    cudaFree(status);
-    return -1;
-  }
-  auto kern = kind == 1 ? k_mma<1> : kind == 2 ? k_mma<2> : k_mma<0>;
-  const size_t smem = kSmemBytes + kPad;
+  const size_t smem = kABytes + (size_t)n * kRowBytes + 1024 + kPad;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaFree(status);
@@ -231,13 +240,18 @@ int ssp_mma_peak(int kind, int iters, double* seconds, double* flops_per_s) {
   if (rc == 0 && st != 0) rc = 1;
   if (rc == 0) {
     const double k = kind == 0 ? 8.0 : 16.0;  // K of one product
-    *flops_per_s = 2.0 * kMmaM * kMmaN * k * 4.0 * (double)iters * nsm / *seconds;
+    *flops_per_s = 2.0 * kMmaM * n * k * 4.0 * (double)iters * nsm / *seconds;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(s);
   cudaFree(status);
   return rc;
+}
+
+// the dense peak: products of M = 128, N = 256
+int ssp_mma_peak(int kind, int iters, double* seconds, double* flops_per_s) {
+  return ssp_mma_rate(kind, 256, iters, seconds, flops_per_s);
 }
 
 }  // extern "C"
