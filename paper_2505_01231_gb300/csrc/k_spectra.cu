@@ -119,17 +119,13 @@ __device__ __forceinline__ void write_gram_row(unsigned char* row, const float (
       uint32_t hi[4], lo[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        uint32_t h2[2], l2[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const float v = e[8 * kg + 2 * t + u];
-          const __half h = __float2half_rn(v);
-          const __half l = __float2half_rn(v - __half2float(h));
-          h2[u] = __half_as_ushort(h);
-          l2[u] = __half_as_ushort(l);
-        }
-        hi[t] = h2[0] | (h2[1] << 16);
-        lo[t] = l2[0] | (l2[1] << 16);
+        // two entries per conversion (each rounded to nearest, as one at a time)
+        const float v0 = e[8 * kg + 2 * t], v1 = e[8 * kg + 2 * t + 1];
+        const __half2 h = __floats2half2_rn(v0, v1);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+        hi[t] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[t] = *reinterpret_cast<const uint32_t*>(&l);
       }
       *reinterpret_cast<uint4*>(row + kg * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(row + CB + kg * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
@@ -152,17 +148,12 @@ __device__ __forceinline__ void write_gram_row(unsigned char* row, const float (
       uint32_t hi[4], lo[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        uint32_t h2[2], l2[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const float v = e[8 * kg + 2 * t + u];
-          const __nv_bfloat16 h = __float2bfloat16_rn(v);
-          const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-          h2[u] = __bfloat16_as_ushort(h);
-          l2[u] = __bfloat16_as_ushort(l);
-        }
-        hi[t] = h2[0] | (h2[1] << 16);
-        lo[t] = l2[0] | (l2[1] << 16);
+        const float v0 = e[8 * kg + 2 * t], v1 = e[8 * kg + 2 * t + 1];
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+        hi[t] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[t] = *reinterpret_cast<const uint32_t*>(&l);
       }
       *reinterpret_cast<uint4*>(row + kg * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(row + CB + kg * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
