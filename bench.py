@@ -660,8 +660,9 @@ def main():
     s4_name = "k3_trispec" if C == 1 else "k3_trispec_cross"
     if args.precision != "fp32":
         s4_name = "k3_trispec_tc" if C == 1 else "k3_trispec_cross_tc"
-    # several channels: every tensor-core precision runs the cross S4 in TF32x3
-    s4_prec = args.precision if C == 1 or args.precision == "fp32" else "tf32x3"
+    # several channels: the cross S4 runs FP16x3 with fp16x3, TF32x3 with the other
+    # tensor-core precisions
+    s4_prec = (args.precision if C == 1 or args.precision in ("fp32", "fp16x3") else "tf32x3")
     names = ["k1_spectra", "k2_bispec", s4_name, "k4_finalize", "h2d"]
     n_batches = max(1, int(np.ceil(groups / info.groups_per_batch)))
     hbm = float(pk.get("hbm_gbs", 6800.0))

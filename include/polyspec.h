@@ -99,10 +99,11 @@ enum { SS_PREC_FP32 = 0,    /* FP32 FMA on CUDA cores                          *
    (m(m+1)/2 products per grid point and group) and take m <= 32 when a
    one-channel plan computes S4; ss_plan returns SS_EUNSUPPORTED for larger m.
    Plans of several channels compute every S4 combination C4(a_k, b_k*, c_l,
-   d_l*) in FP32 on CUDA cores with SS_PREC_FP32, and with every tensor-core
-   precision on the tensor cores in TF32X3 (five complex frame products per
-   combination and group, Sec. 7, Eq. 50, App. H, Eq. 85; any m), so their
-   accuracy is TF32X3's whichever tensor-core precision is named.  All precisions
+   d_l*) in FP32 on CUDA cores with SS_PREC_FP32, and on the tensor cores (five
+   complex frame products per combination and group, Sec. 7, Eq. 50, App. H,
+   Eq. 85; any m) in FP16X3 with SS_PREC_FP16X3 (each bin's operands scaled by a
+   power of two per group) and in TF32X3 with the other tensor-core precisions,
+   so their accuracy is that of FP16X3 or TF32X3.  All precisions
    keep the per-group c4 values and their per-item sums in FP32: inputs whose
    |c4| exceeds about 1e18 overflow the sum of squares. */
 

@@ -91,6 +91,11 @@ struct OperandImage {
   long long chan_bytes = 0;   // Gb_max * group_bytes
   long long chan_ps = 0;      // Gb_max * Mp floats (FP16: Gb_max * 2 Mp)
   int ps_group = 0;           // floats of ps per group: Mp, or 2 Mp with the FP16 scales
+  // several channels in FP16X3: per channel, group and bin the power of two that
+  // brings the bin's coefficients over the group's frames below 2^14 (within
+  // [2^-60, 2^60]; 1 for a zero bin), at rmax[channel * chan_rmax + group * Mp + bin]
+  float* rmax = nullptr;
+  long long chan_rmax = 0;
 };
 
 // K1 forms (the autotuner's choice per plan): groups resident in shared memory
@@ -159,17 +164,31 @@ cudaError_t launch_k3_trispec_cross(const float2* spec, long long chan_stride, i
                                     long long plane, int nsm, bool natural, cudaStream_t stream);
 int k3tc_stage_chunks(int precision);
 
-// The same on the tcgen05 tensor cores (every tensor-core precision; TF32 hi/lo
-// in three passes): tiles of 128 rows k x 24 columns l, operands built in shared
-// memory from the centred spectra, read through two 2-D views [rows][Mp] of
-// them (8-byte elements, no swizzle): tm_ab with boxes of 4 rows x
-// min(kCrossBoxBins, Mp) bins, tm_cd with boxes of 4 rows x kCrossColBox bins; a channel's
-// rows start at channel x chan_rows.  The row k = -(M-1) is copied from k = M-1
-// (equal for real signals).  counter and status as for the pair kernels.
-// (the c, d box is 4 bins wider than a tile, so that its rows fall on other banks)
-constexpr int kCrossBoxBins = 140, kCrossTileCols = 24, kCrossColBox = 28;
-cudaError_t launch_k3_trispec_cross_tc(const CUtensorMap& tm_ab, const CUtensorMap& tm_cd,
-                                       int chan_rows, int G, int m, int M, int Mp,
+// The same on the tcgen05 tensor cores: tiles of 128 rows k x 24 columns l,
+// operands built in shared memory from the centred spectra.  TF32 hi/lo in three
+// passes for SS_PREC_TF32X3, SS_PREC_BF16X3 and SS_PREC_BF16; with SS_PREC_FP16X3
+// FP16 hi/lo in three passes of operands scaled per bin by powers of two, the
+// bins' row scales per group that K1 writes (OperandImage::rmax).
+// The spectra are read through 2-D views [rows][Mp] (8-byte elements, no swizzle):
+// tm_ab with boxes of kF rows x min(box bins, Mp) bins, tm_cd with boxes of kF
+// rows x col box bins (kF = 4 frames, 8 for FP16); a channel's rows start at
+// channel x chan_rows.  FP16 also reads the row scales [channel x grp_rows +
+// group][Mp] (float) through tm_sab (boxes of min(kCrossScaleBins, Mp) bins) and
+// tm_scd (kCrossScaleCols bins).  The row k = -(M-1) is copied from k = M-1 (equal
+// for real signals).  counter and status as for the pair kernels.
+// Box widths (bins) of tm_ab and tm_cd, TF32 and FP16 forms: wider than the bins
+// used, so that the rows of a thread's two frame chunks fall on other banks.
+constexpr int kCrossBoxBins = 140, kCrossBoxBinsH = 142, kCrossColBox = 28, kCrossColBoxH = 30;
+constexpr int kCrossTileCols = 24, kCrossScaleBins = 144, kCrossScaleCols = 28;
+struct CrossViews {
+  const CUtensorMap* tm_ab = nullptr;
+  const CUtensorMap* tm_cd = nullptr;
+  const CUtensorMap* tm_sab = nullptr;
+  const CUtensorMap* tm_scd = nullptr;
+  int chan_rows = 0, grp_rows = 0;
+  bool f16 = false;
+};
+cudaError_t launch_k3_trispec_cross_tc(const CrossViews& v, int G, int m, int M, int Mp,
                                        const int4* combos, int n_combos, double* acc,
                                        long long plane, int nsm, bool natural, int* counter,
                                        int* status, cudaStream_t stream);

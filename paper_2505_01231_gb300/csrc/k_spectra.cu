@@ -161,6 +161,16 @@ __device__ __forceinline__ void write_gram_row(unsigned char* row, const float (
   }
 }
 
+// Several channels in FP16X3: the row scale of a bin whose largest |d_j|^2 over
+// the group is mx2, a power of two that brings sqrt(mx2) below 2^14, within
+// [2^-60, 2^60] (1 for a zero bin).
+__device__ __forceinline__ float cross_row_scale(float mx2) {
+  if (!(mx2 > 0.f)) return 1.f;
+  int e;
+  frexpf(sqrtf(mx2), &e);  // sqrt(mx2) < 2^e
+  return ldexpf(1.f, min(60, max(-60, 14 - e)));
+}
+
 // FP16 operand image: the power of two that brings a bin's largest Gram entry,
 // bounded by `bound`, below 2^14 (1 for an all-zero bin).
 __device__ __forceinline__ float f16_row_scale(float bound) {
@@ -206,11 +216,14 @@ __device__ __forceinline__ void centre_bin(int k, bool valid, float2 mean, int m
                                            Store store, float* s2sum, float* s2sq, float pref2) {
   float p = 0.f;
   if constexpr (FMT == kImageNone) {
+    float mx = 0.f;  // max_j |d_j|^2 (several channels in FP16X3: the bin's row scale)
     for (int j = 0; j < m; ++j) {
       const float2 d = valid ? csub(fetch(j), mean) : make_float2(0.f, 0.f);
       store(j, d);
       p = fmaf(d.x, d.x, fmaf(d.y, d.y, p));
+      mx = fmaxf(mx, fmaf(d.x, d.x, d.y * d.y));
     }
+    if (oi.rmax) oi.rmax[(long long)c * oi.chan_rmax + (long long)g * Mp + k] = cross_row_scale(mx);
   } else {
     float dr[kMaxGramM], di[kMaxGramM];
     float mx = 0.f;  // max_j |d_j|^2
@@ -440,6 +453,8 @@ __device__ __forceinline__ void centre_resident(float2* Xs, float2* __restrict__
       p += pj;
       mx = fmaxf(mx, pj);
     }
+    // several channels in FP16X3: the bin's row scale
+    if (oi.rmax) oi.rmax[(long long)c * oi.chan_rmax + (long long)g * Mp + k] = cross_row_scale(mx);
     if constexpr (FMT != kImageNone) {
       const float sc = FMT == kImageGramF16 ? f16_row_scale(fmaxf(oi.sd, oi.so) * mx) : 1.f;
       const float sd = oi.sd * sc, so = oi.so * sc;

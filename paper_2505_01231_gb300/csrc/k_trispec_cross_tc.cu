@@ -49,6 +49,8 @@
 // a small kernel copies that row's sums after every batch.  Every wait is
 // bounded; on a failure the CTA stops, waits for the copies and products it
 // issued and frees its TMEM.
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 #include "pipeline.cuh"
 
@@ -58,9 +60,6 @@ namespace {
 constexpr int kXT = 128;     // rows of a tile
 constexpr int kXL = kCrossTileCols;  // columns of a tile (24)
 constexpr int kXLw = kXL / 2;        // columns of an epilogue warp
-constexpr int kXF = 4;       // frames per stage: K = 8 TF32 values, one MMA K step
-constexpr int kXStages = 4;  // operand stages
-constexpr int kXRaw = 6;     // stages of staged coefficients
 constexpr int kXEpiWarps = 8, kXBuildWarps = 8;
 constexpr int kXMmaWarp = kXEpiWarps + kXBuildWarps, kXLoadWarp = kXMmaWarp + 1;
 constexpr int kXThreads = 32 * (kXLoadWarp + 1);
@@ -71,25 +70,47 @@ constexpr uint32_t kXTmemCols = 512;
 // Re P, Im P at +192 (the B rows are ordered the same way: type-major)
 constexpr uint32_t kXBufCols = 256, kColY = 4 * kXL, kColP = 8 * kXL;
 
-// A stage: for each matrix a hi block, then a lo block.  A matrix of R rows x 8
-// TF32 values is R/8 row groups of two core matrices (8 rows x 16 bytes: frames
-// 2c and 2c + 1 of the stage, Re and Im), 128 bytes apart (LBO); row groups are
-// 256 bytes apart (SBO).
+// A stage: for each matrix a hi block, then a lo block.  A matrix of R rows and
+// 32 bytes of K per row is R/8 row groups of two core matrices (8 rows x 16
+// bytes: the first and the second half of the stage's frames, Re and Im), 128
+// bytes apart (LBO); row groups are 256 bytes apart (SBO).  TF32: 4 frames per
+// stage (K = 8); FP16: 8 frames (K = 16).
 constexpr uint32_t kAMat = kXT * 32;                      // 4 KB
 constexpr uint32_t kBXYMat = 4 * kXL * 32, kBPMat = 2 * kXL * 32;
 constexpr uint32_t kOffAX = 0, kOffAY = 2 * kAMat, kOffAP = 4 * kAMat;
 constexpr uint32_t kOffBXY = 6 * kAMat, kOffBP = kOffBXY + 2 * kBXYMat;
-constexpr uint32_t kXStageBytes = kOffBP + 2 * kBPMat;    // 30 KB
-// A stage of staged coefficients (4 frames): the bins of a and b that the tile's
-// rows need (at most 130 consecutive bins from an even bin; a box of 4 rows x
-// min(kRawK, Mp) bins, rows rawk bins apart), then the 24 bins of c and d of its
-// columns (boxes of 4 rows x kCrossColBox bins).
-constexpr int kRawK = kCrossBoxBins;
-constexpr uint32_t kRawA = 0, kRawB = kXF * kRawK * 8, kRawC = 2 * kXF * kRawK * 8,
-                   kRawD = kRawC + kXF * kCrossColBox * 8;
-constexpr uint32_t kXRawBytes = kRawD + kXF * kCrossColBox * 8;  // 10.5 KB
-constexpr size_t kXSmemBytes =
-    (size_t)kXStages * kXStageBytes + (size_t)kXRaw * kXRawBytes + 128;
+constexpr uint32_t kXStageBytes = kOffBP + 2 * kBPMat;    // 33 KB
+
+// Operand formats.  TF32 hi/lo of the values; FP16 hi/lo of the values scaled
+// by a power of two per row (bin and operand) that keeps them below 2^14.
+// A stage of staged coefficients holds kF frames: the bins of a and b that the
+// tile's rows need (at most 131 consecutive bins from a bin that is a multiple
+// of 4; boxes of kF rows x min(kRawK, Mp) bins, rows rawk bins apart), then the
+// 24 bins of c and d (boxes of kF rows x kColBox bins) and, for FP16, the
+// group's row scales of each of those bins (boxes of one row).  The box widths
+// put the rows of a thread's two frame chunks (kHalf frames apart) 64 bytes
+// apart modulo 128: on other banks.
+template <bool kF16>
+struct XFmt {
+  static constexpr int kF = kF16 ? 8 : 4;           // frames per stage
+  static constexpr int kHalf = kF / 2;              // frames per 16-byte chunk of a row
+  static constexpr int kStages = kF16 ? 3 : 4;      // operand stages
+  static constexpr int kRaw = kF16 ? 4 : 6;         // staged-coefficient stages
+  static constexpr int kRawK = kF16 ? kCrossBoxBinsH : kCrossBoxBins;
+  static constexpr int kColBox = kF16 ? kCrossColBoxH : kCrossColBox;
+  static constexpr uint32_t kRawA = 0, kRawB = kF * kRawK * 8, kRawC = 2 * kF * kRawK * 8,
+                            kRawD = kRawC + kF * kColBox * 8, kRawEnd = kRawD + kF * kColBox * 8;
+  static constexpr uint32_t kRawSA = kRawEnd, kRawSB = kRawSA + 640, kRawSC = kRawSB + 640,
+                            kRawSD = kRawSC + 128;
+  static constexpr uint32_t kRawBytes = kF16 ? kRawSD + 128 : kRawEnd;
+  static constexpr size_t kSmem = (size_t)kStages * kXStageBytes + (size_t)kRaw * kRawBytes + 128;
+};
+static_assert(XFmt<false>::kRawBytes % 128 == 0 && XFmt<true>::kRawBytes % 128 == 0 &&
+                  XFmt<true>::kRawSA % 128 == 0 && XFmt<true>::kRawSB % 128 == 0 &&
+                  XFmt<true>::kRawSC % 128 == 0 && XFmt<true>::kRawSD % 128 == 0,
+              "staging regions start on 128-byte boundaries");
+static_assert(XFmt<false>::kSmem <= 227 * 1024 - 12 * 1024 && XFmt<true>::kSmem <= 227 * 1024 - 12 * 1024,
+              "shared memory");
 
 enum : int { kRecFirst = 1, kRecLast = 2, kRecStop = 4, kRecItemEnd = 8 };
 
@@ -101,9 +122,11 @@ struct RawRec {  // a staged stage: its tile, combination, first staged bin, fra
   int r0, l0, combo, bstart, st, flags;
 };
 
-struct CrossSlot {  // one group: its one-bin sums and record, for the epilogue
+struct CrossSlot {  // one group: its one-bin sums, scales and record, for the epilogue
   float2 sxy[kXT];
-  float2 szw[2][kXL];  // over frames 4i, 4i + 1 and over 4i + 2, 4i + 3
+  float2 szw[2][kXL];   // over the first and the second half of each stage's frames
+  float2 rxy[kXT];      // FP16: 1 / (row scales of x and y)
+  float2 rzw[kXL];      // FP16: 1 / (column scales of z and w)
   int r0, l0, combo, flags;
 };
 
@@ -127,6 +150,27 @@ __device__ __forceinline__ void put_split(unsigned char* blk, uint32_t lo_off, u
   l.w = to_tf32(d - __uint_as_float(h.w));
   *reinterpret_cast<uint4*>(blk + off) = h;
   *reinterpret_cast<uint4*>(blk + lo_off + off) = l;
+}
+
+// hi and lo FP16 parts of eight values (two at a time, each rounded to nearest)
+__device__ __forceinline__ void put_split16(unsigned char* blk, uint32_t lo_off, uint32_t off,
+                                            const float (&v)[8]) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const __half2 hh = __floats2half2_rn(v[2 * t], v[2 * t + 1]);
+    const float2 hf = __half22float2(hh);
+    const __half2 ll = __floats2half2_rn(v[2 * t] - hf.x, v[2 * t + 1] - hf.y);
+    h[t] = *reinterpret_cast<const uint32_t*>(&hh);
+    l[t] = *reinterpret_cast<const uint32_t*>(&ll);
+  }
+  *reinterpret_cast<uint4*>(blk + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(blk + lo_off + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// 1 / s for a normal power of two s (exact): the exponent field mirrored
+__device__ __forceinline__ float pow2_inv(float s) {
+  return __int_as_float((254 << 23) - __float_as_int(s));
 }
 
 // byte offset of row n's 16-byte chunk c in a matrix block
@@ -153,6 +197,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"((uint32_t)accumulate));
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"((uint32_t)accumulate));
 }
 
@@ -185,23 +237,30 @@ struct CrossQueue {
   int n_items, n_tiles, n_combos, n_cb, group_chunk;
 };
 
+template <bool kF16>
 __global__ void __launch_bounds__(kXThreads, 1)
 k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
-                    const __grid_constant__ CUtensorMap tm_cd, int chan_rows, int rawk, int G,
-                    int m, int M, int Mp, const int4* __restrict__ combos, CrossQueue wq,
-                    float pref, float fmm, float fm1, double* __restrict__ acc, long long plane,
-                    long long combo_stride, int* __restrict__ status) {
+                    const __grid_constant__ CUtensorMap tm_cd,
+                    const __grid_constant__ CUtensorMap tm_sab,
+                    const __grid_constant__ CUtensorMap tm_scd, int chan_rows, int grp_rows,
+                    int rawk, int sabk, int G, int m, int M, int Mp,
+                    const int4* __restrict__ combos, CrossQueue wq, float pref, float fmm,
+                    float fm1, double* __restrict__ acc, long long plane, long long combo_stride,
+                    int* __restrict__ status) {
+  using F = XFmt<kF16>;
+  constexpr int kSt = F::kStages, kRw = F::kRaw, kH = F::kHalf;
+  constexpr float kPairScale = 1.f / 16384.f;  // FP16: products of two scaled values x 2^-14
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[kXStages];      // stage built
-  __shared__ __align__(8) uint64_t sdone[kXStages];     // stage's products complete
+  __shared__ __align__(8) uint64_t full[kSt];           // stage built
+  __shared__ __align__(8) uint64_t sdone[kSt];          // stage's products complete
   __shared__ __align__(8) uint64_t slotfull[kXSlots];   // group slot written
   __shared__ __align__(8) uint64_t slotempty[kXSlots];  // group slot read by the epilogue
   __shared__ __align__(8) uint64_t bfull[2];            // TMEM buffer holds a finished group
   __shared__ __align__(8) uint64_t bempty[2];           // TMEM buffer read by the epilogue
-  __shared__ __align__(8) uint64_t rfull[kXRaw];       // coefficients staged (bulk copies)
-  __shared__ __align__(8) uint64_t rempty[kXRaw];      // staged coefficients read
-  __shared__ StageRec srec[kXStages];
-  __shared__ RawRec rrec[kXRaw];
+  __shared__ __align__(8) uint64_t rfull[kRw];          // coefficients staged (tensor copies)
+  __shared__ __align__(8) uint64_t rempty[kRw];         // staged coefficients read
+  __shared__ StageRec srec[kSt];
+  __shared__ RawRec rrec[kRw];
   __shared__ __align__(16) CrossSlot slot[kXSlots];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
@@ -210,7 +269,7 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
       smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);  // 128-byte aligned
 
   if (tid == 0) {
-    for (int s = 0; s < kXStages; ++s) {
+    for (int s = 0; s < kSt; ++s) {
       mbar_init(&full[s], kXBuildWarps);
       mbar_init(&sdone[s], 1);
     }
@@ -222,7 +281,7 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
       mbar_init(&bfull[b], 1);
       mbar_init(&bempty[b], kXEpiWarps);
     }
-    for (int i = 0; i < kXRaw; ++i) {
+    for (int i = 0; i < kRw; ++i) {
       mbar_init(&rfull[i], 1);
       mbar_init(&rempty[i], kXBuildWarps);
     }
@@ -240,73 +299,77 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
   tc_after();
   const uint32_t taddr = tmem_slot;
   const int rows_hi = 2 * M - 2;  // last row r of the tiles
-  const int nst = (m + kXF - 1) / kXF;
+  const int nst = (m + F::kF - 1) / F::kF;
 
-  unsigned char* raws = stages + (size_t)kXStages * kXStageBytes;
+  unsigned char* raws = stages + (size_t)kSt * kXStageBytes;
   if (warp >= kXEpiWarps && warp < kXMmaWarp) {
     // ------------------------------------------------------------ builders
     // Builder warp wb, lane: row R = 16 wb + lane % 8 + 8 (lane / 16) of the tile,
-    // frames 2 fp and 2 fp + 1 of every stage, fp = lane / 8 % 2 (one 16-byte chunk
-    // of the row), so that 8 consecutive lanes fill one 128-byte core matrix.  The
-    // column rows are 6 types (Re and Im columns of z, of w, of zw) x 24 bins x 2
-    // chunks = 288 tasks: thread bt takes tasks bt and bt + 256, task i being type
-    // i / 48, chunk i / 24 % 2, bin i % 24 (8 consecutive tasks fill one core
-    // matrix).  Each warp waits and arrives on its own.
-    constexpr int kTasks = 6 * 2 * kXL;
+    // the first or second half of every stage's frames, fp = lane / 8 % 2 (one
+    // 16-byte chunk of the row), so that 8 consecutive lanes fill one 128-byte core
+    // matrix.  The column rows: 3 operands (z, w, zw) x 24 bins x 2 chunks = 144
+    // tasks, thread bt < 144 taking task bt: operand bt / 48, chunk bt / 24 % 2, bin
+    // bt % 24; a task writes the operand's Re and Im columns (8 consecutive tasks
+    // fill one core matrix).  Each warp waits and arrives on its own.
+    constexpr int kTasks = 3 * 2 * kXL;
     const int bt = tid - 32 * kXEpiWarps, wb = bt >> 5;
     const int R = 16 * wb + (lane & 7) + 8 * (lane >> 4), fp = (lane >> 3) & 1;
-    int tt[2], tli[2], tfq[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int i = bt + u * 32 * kXBuildWarps;
-      tt[u] = i < kTasks ? i / (2 * kXL) : -1;
-      tli[u] = i % kXL;
-      tfq[u] = (i / kXL) & 1;
-    }
+    const int top = bt < kTasks ? bt / (2 * kXL) : -1;  // 0: z, 1: w, 2: zw; -1: none
+    const int tli = bt % kXL, tfq = (bt / kXL) & 1;
     const float2 zero = make_float2(0.f, 0.f);
     uint32_t rq = 0, q = 0, gs = 0;
     bool ok = true;
-    float2 sxy = zero, szw = zero;  // szw: the task of type 4 (Re zw), if any
+    float2 sxy = zero, szw = zero;  // szw: the zw task, if any
+    // FP16: the current group's scales of this thread's row (x, y) and column (z, w)
+    float sx = 1.f, sy = 1.f, tz = 1.f, tw = 1.f;
     for (;;) {
-      const int rs = (int)(rq % kXRaw);
-      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&rfull[rs], (rq / kXRaw) & 1u, status));
+      const int rs = (int)(rq % kRw);
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&rfull[rs], (rq / kRw) & 1u, status));
       if (!ok) break;
       const RawRec rec = rrec[rs];
       if (rec.flags & kRecStop) break;
       const int r = rec.r0 + R, k = r - (M - 1);
       const bool rv = r <= rows_hi;
       const int kb = k < 0 ? -k : k;
-      const int j0 = rec.st * kXF;  // first frame of the stage
-      const float2* raw = reinterpret_cast<const float2*>(raws + (size_t)rs * kXRawBytes);
-      float2 va[2], vb[2], vc[2][2], vd[2][2];
+      const int j0 = rec.st * F::kF;  // first frame of the stage
+      const unsigned char* rbase = raws + (size_t)rs * F::kRawBytes;
+      const float2* raw = reinterpret_cast<const float2*>(rbase);
+      float2 va[kH], vb[kH], vc[kH], vd[kH];
+      const bool lv = top >= 0 && rec.l0 + tli < M;
 #pragma unroll
-      for (int jj = 0; jj < 2; ++jj) {
-        const int fj = 2 * fp + jj;  // frame within the stage
+      for (int jj = 0; jj < kH; ++jj) {
+        const int fj = kH * fp + jj;  // frame within the stage
         const bool v = rv && j0 + fj < m;
-        va[jj] = v ? raw[kRawA / 8 + fj * rawk + kb - rec.bstart] : zero;
-        vb[jj] = v ? raw[kRawB / 8 + fj * rawk + kb - rec.bstart] : zero;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int fk = 2 * tfq[u] + jj;
-          const bool w = tt[u] >= 0 && rec.l0 + tli[u] < M && j0 + fk < m;
-          vc[u][jj] = w ? raw[kRawC / 8 + fk * kCrossColBox + tli[u]] : zero;
-          vd[u][jj] = w ? raw[kRawD / 8 + fk * kCrossColBox + tli[u]] : zero;
+        va[jj] = v ? raw[F::kRawA / 8 + fj * rawk + kb - rec.bstart] : zero;
+        vb[jj] = v ? raw[F::kRawB / 8 + fj * rawk + kb - rec.bstart] : zero;
+        const int fk = kH * tfq + jj;
+        const bool w = lv && j0 + fk < m;
+        vc[jj] = w && top != 1 ? raw[F::kRawC / 8 + fk * F::kColBox + tli] : zero;
+        vd[jj] = w && top != 0 ? raw[F::kRawD / 8 + fk * F::kColBox + tli] : zero;
+      }
+      if constexpr (kF16) {
+        if (rec.flags & kRecFirst) {  // the group's row scales, staged with its first stage
+          const float* ssc = reinterpret_cast<const float*>(rbase);
+          sx = rv ? ssc[F::kRawSA / 4 + kb - rec.bstart] : 1.f;
+          sy = rv ? ssc[F::kRawSB / 4 + kb - rec.bstart] : 1.f;
+          tz = lv ? ssc[F::kRawSC / 4 + tli] : 1.f;
+          tw = lv ? ssc[F::kRawSD / 4 + tli] : 1.f;
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive_x(&rempty[rs]);  // the warp's coefficients are in registers
       ++rq;
-      const int s = (int)(q % kXStages);
-      ok = __all_sync(0xffffffffu, q < (uint32_t)kXStages ||
-                                       mbar_wait_bounded(&sdone[s], ((q / kXStages) & 1u) ^ 1u,
-                                                         status));
+      const int s = (int)(q % kSt);
+      ok = __all_sync(0xffffffffu,
+                      q < (uint32_t)kSt ||
+                          mbar_wait_bounded(&sdone[s], ((q / kSt) & 1u) ^ 1u, status));
       if (!ok) break;
       if (rec.flags & kRecFirst) sxy = szw = zero;
       unsigned char* stg = stages + (size_t)s * kXStageBytes;
       // rows: k < 0: x = a_{|k|}*, y = b_{|k|};  k >= 0: x = a_k, y = b_k*
-      float2 x[2], y[2], xy[2];
+      float2 x[kH], y[kH], xy[kH];
 #pragma unroll
-      for (int jj = 0; jj < 2; ++jj) {
+      for (int jj = 0; jj < kH; ++jj) {
         x[jj] = k < 0 ? make_float2(va[jj].x, -va[jj].y) : va[jj];
         y[jj] = k < 0 ? vb[jj] : make_float2(vb[jj].x, -vb[jj].y);
         xy[jj] = cmulf(x[jj], y[jj]);
@@ -314,33 +377,71 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
         sxy.y += xy[jj].y;
       }
       const uint32_t o = core_off(R, fp);
-      put_split(stg + kOffAX, kAMat, o, x[0].x, x[0].y, x[1].x, x[1].y);
-      put_split(stg + kOffAY, kAMat, o, y[0].x, y[0].y, y[1].x, y[1].y);
-      put_split(stg + kOffAP, kAMat, o, xy[0].x, xy[0].y, xy[1].x, xy[1].y);
+      if constexpr (!kF16) {
+        put_split(stg + kOffAX, kAMat, o, x[0].x, x[0].y, x[1].x, x[1].y);
+        put_split(stg + kOffAY, kAMat, o, y[0].x, y[0].y, y[1].x, y[1].y);
+        put_split(stg + kOffAP, kAMat, o, xy[0].x, xy[0].y, xy[1].x, xy[1].y);
+      } else {
+        // scaled rows: x sx, y sy and (x sx)(y sy) 2^-14, each below 2^14
+        float ex[8], ey[8], ep[8];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int t = tt[u];
-        if (t < 0) continue;
-        // column row of type t of bin l: z = c_l (t 0, 1), w = d_l* (2, 3), zw (4, 5);
-        // an even t gives the Re column (ur, -ui), an odd one the Im column (ui, ur)
-        float2 v[2];
+        for (int jj = 0; jj < kH; ++jj) {
+          const float2 xs = make_float2(x[jj].x * sx, x[jj].y * sx);
+          const float2 ys = make_float2(y[jj].x * sy, y[jj].y * sy);
+          const float2 ps = cmulf(xs, ys);
+          ex[2 * jj] = xs.x;
+          ex[2 * jj + 1] = xs.y;
+          ey[2 * jj] = ys.x;
+          ey[2 * jj + 1] = ys.y;
+          ep[2 * jj] = ps.x * kPairScale;
+          ep[2 * jj + 1] = ps.y * kPairScale;
+        }
+        put_split16(stg + kOffAX, kAMat, o, ex);
+        put_split16(stg + kOffAY, kAMat, o, ey);
+        put_split16(stg + kOffAP, kAMat, o, ep);
+      }
+      if (top >= 0) {
+        // operand top of bin l: z = c_l, w = d_l*, zw; its Re column (ur, -ui) and
+        // its Im column (ui, ur)
+        float2 v[kH];
 #pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-          const float2 z = vc[u][jj], w = make_float2(vd[u][jj].x, -vd[u][jj].y);
-          const float2 zw = cmulf(z, w);
-          if (t == 4) {
+        for (int jj = 0; jj < kH; ++jj) {
+          float2 z = vc[jj], w = make_float2(vd[jj].x, -vd[jj].y);
+          if (top == 2) {
+            const float2 zw = cmulf(z, w);
             szw.x += zw.x;
             szw.y += zw.y;
           }
-          v[jj] = t < 2 ? z : (t < 4 ? w : zw);
+          if constexpr (kF16) {
+            z = make_float2(z.x * tz, z.y * tz);
+            w = make_float2(w.x * tw, w.y * tw);
+            const float2 zws = cmulf(z, w);
+            v[jj] = top == 0 ? z
+                             : (top == 1 ? w : make_float2(zws.x * kPairScale, zws.y * kPairScale));
+          } else {
+            v[jj] = top == 0 ? z : (top == 1 ? w : cmulf(z, w));
+          }
         }
-        const uint32_t co = t < 4 ? kOffBXY + core_off(kXL * t + tli[u], tfq[u])
-                                  : kOffBP + core_off(kXL * (t - 4) + tli[u], tfq[u]);
-        const uint32_t lo = t < 4 ? kBXYMat : kBPMat;
-        if (t & 1)
-          put_split(stg, lo, co, v[0].y, v[0].x, v[1].y, v[1].x);
-        else
-          put_split(stg, lo, co, v[0].x, -v[0].y, v[1].x, -v[1].y);
+        const uint32_t cre = top < 2 ? kOffBXY + core_off(kXL * (2 * top) + tli, tfq)
+                                     : kOffBP + core_off(tli, tfq);
+        const uint32_t cim = top < 2 ? kOffBXY + core_off(kXL * (2 * top + 1) + tli, tfq)
+                                     : kOffBP + core_off(kXL + tli, tfq);
+        const uint32_t lo = top < 2 ? kBXYMat : kBPMat;
+        if constexpr (!kF16) {
+          put_split(stg, lo, cre, v[0].x, -v[0].y, v[1].x, -v[1].y);
+          put_split(stg, lo, cim, v[0].y, v[0].x, v[1].y, v[1].x);
+        } else {
+          float er[8], ei[8];
+#pragma unroll
+          for (int jj = 0; jj < kH; ++jj) {
+            er[2 * jj] = v[jj].x;
+            er[2 * jj + 1] = -v[jj].y;
+            ei[2 * jj] = v[jj].y;
+            ei[2 * jj + 1] = v[jj].x;
+          }
+          put_split16(stg, lo, cre, er);
+          put_split16(stg, lo, cim, ei);
+        }
       }
       if (bt == 0) srec[s] = StageRec{rec.flags & (kRecFirst | kRecLast)};
       // the generic-proxy writes become visible to the tensor cores' reads
@@ -350,7 +451,7 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
       ++q;
       if (rec.flags & kRecLast) {
         // the group's one-bin sums (the two chunks of a row are lanes 8 apart; the
-        // column sums go per chunk) and its record, for the epilogue
+        // column sums go per chunk), its scales and its record, for the epilogue
         const float2 sxy_o = make_float2(__shfl_xor_sync(0xffffffffu, sxy.x, 8),
                                          __shfl_xor_sync(0xffffffffu, sxy.y, 8));
         const int p = (int)(gs % kXSlots);
@@ -359,7 +460,11 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
                                                            ((gs / kXSlots) - 1) & 1u, status));
         if (!ok) break;
         if (fp == 0) slot[p].sxy[R] = make_float2(sxy.x + sxy_o.x, sxy.y + sxy_o.y);
-        if (tt[0] == 4) slot[p].szw[tfq[0]][tli[0]] = szw;
+        if (top == 2) slot[p].szw[tfq][tli] = szw;
+        if constexpr (kF16) {
+          if (fp == 0) slot[p].rxy[R] = make_float2(pow2_inv(sx), pow2_inv(sy));
+          if (top == 2 && tfq == 0) slot[p].rzw[tli] = make_float2(pow2_inv(tz), pow2_inv(tw));
+        }
         if (bt == 0) {
           slot[p].r0 = rec.r0;
           slot[p].l0 = rec.l0;
@@ -374,9 +479,8 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
     if (!ok && lane == 0) atomicExch(&s_fail, 1);
     // stop records: the next stage (for the MMA warp) and the next slot (epilogue)
     {
-      const int s = (int)(q % kXStages);
-      if (q >= (uint32_t)kXStages)
-        mbar_wait_bounded(&sdone[s], ((q / kXStages) & 1u) ^ 1u, status);
+      const int s = (int)(q % kSt);
+      if (q >= (uint32_t)kSt) mbar_wait_bounded(&sdone[s], ((q / kSt) & 1u) ^ 1u, status);
       if (bt == 0) srec[s] = StageRec{kRecStop};
       __syncwarp();
       if (lane == 0) mbar_arrive_x(&full[s]);
@@ -391,13 +495,15 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t sbase = smem_addr(stages);
-      const uint32_t idesc0 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kXT >> 4) << 24);
+      // D FP32; A, B TF32 (format 2) or FP16 (format 0 of kind::f16); K-major
+      const uint32_t fmt = kF16 ? 0u : ((2u << 7) | (2u << 10));
+      const uint32_t idesc0 = (1u << 4) | fmt | ((uint32_t)(kXT >> 4) << 24);
       uint32_t q = 0, gc = 0;
       int last_s = -1;
       uint32_t last_ph = 0;
       for (;; ++q) {
-        const int s = (int)(q % kXStages);
-        const uint32_t ph = (q / kXStages) & 1u;
+        const int s = (int)(q % kSt);
+        const uint32_t ph = (q / kSt) & 1u;
         if (!mbar_wait_bounded(&full[s], ph, status)) break;
         const StageRec rec = srec[s];
         if (rec.flags & kRecStop) break;
@@ -408,7 +514,7 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
           tc_after();
         }
         const uint32_t d = taddr + b * kXBufCols;
-        // N = 64 ([z | w] columns) and 32 (zw), whatever the tile's width (columns
+        // N = 96 ([z | w] columns) and 48 (zw), whatever the tile's width (columns
         // of bins past M - 1 are zero)
         const uint32_t idx = idesc0 | ((uint32_t)((4 * kXL) >> 3) << 17);
         const uint32_t idp = idesc0 | ((uint32_t)((2 * kXL) >> 3) << 17);
@@ -420,11 +526,18 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
           const uint32_t ao = pa == 2 ? kAMat : 0u;
           const uint32_t bxo = pa == 1 ? kBXYMat : 0u, bpo = pa == 1 ? kBPMat : 0u;
           const bool accum = !(first && pa == 0);
-          mma_tf32(d, smem_desc_x(sa + kOffAX + ao), smem_desc_x(sa + kOffBXY + bxo), idx, accum);
-          mma_tf32(d + kColY, smem_desc_x(sa + kOffAY + ao), smem_desc_x(sa + kOffBXY + bxo), idx,
-                   accum);
-          mma_tf32(d + kColP, smem_desc_x(sa + kOffAP + ao), smem_desc_x(sa + kOffBP + bpo), idp,
-                   accum);
+          const uint64_t ax = smem_desc_x(sa + kOffAX + ao), ay = smem_desc_x(sa + kOffAY + ao);
+          const uint64_t ap = smem_desc_x(sa + kOffAP + ao);
+          const uint64_t bxy = smem_desc_x(sa + kOffBXY + bxo), bp = smem_desc_x(sa + kOffBP + bpo);
+          if constexpr (kF16) {
+            mma_f16(d, ax, bxy, idx, accum);
+            mma_f16(d + kColY, ay, bxy, idx, accum);
+            mma_f16(d + kColP, ap, bp, idp, accum);
+          } else {
+            mma_tf32(d, ax, bxy, idx, accum);
+            mma_tf32(d + kColY, ay, bxy, idx, accum);
+            mma_tf32(d + kColP, ap, bp, idp, accum);
+          }
         }
         mma_commit_x(&sdone[s]);
         last_s = s;
@@ -441,8 +554,9 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
     __syncwarp();
   } else if (warp == kXLoadWarp) {
     // ------------------------------------------------------------ loader
-    // takes the items and stages, per 4 frames, the coefficients the builders need
-    // (bulk copies of whole bin ranges), with the stage's record
+    // takes the items and stages, per stage of kF frames, the coefficients the
+    // builders need (tensor-map boxes of whole bin ranges) with the stage's record;
+    // FP16: with a group's first stage also the bins' largest |coefficient|^2
     if (lane == 0) {
       uint32_t rq = 0;
       bool ok = true;
@@ -455,17 +569,19 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
         const int r0 = 1 + (tile / wq.n_cb) * kXT, l0 = (tile % wq.n_cb) * kXL;
         const int g0 = chunk * wq.group_chunk, g1 = min(G, g0 + wq.group_chunk);
         const int4 cb = combos[combo];
-        // bins |k| of the tile's rows: one range of at most 128 bins, staged from an
-        // even bin (x 8 bytes a multiple of 16: the boxes' alignment rule)
+        // bins |k| of the tile's rows: one range of at most 128 bins, staged from a
+        // multiple of 4 (x times 8 bytes, and times 4 for the maxima, a multiple of
+        // 16: the boxes' alignment rule)
         const int klo = r0 - (M - 1), khi = min(r0 + kXT - 1, rows_hi) - (M - 1);
         const int blo = klo >= 0 ? klo : (khi <= 0 ? -khi : 0);
-        const int bstart = blo & ~1;
-        const uint32_t stage_bytes = 2u * 4u * 8u * (uint32_t)(rawk + kCrossColBox);
+        const int bstart = blo & ~3;
+        const uint32_t stage_bytes = 2u * (uint32_t)F::kF * 8u * (uint32_t)(rawk + F::kColBox);
+        const uint32_t scale_bytes = kF16 ? 2u * 4u * (uint32_t)(sabk + kCrossScaleCols) : 0u;
         for (int g = g0; g < g1 && ok; ++g) {
           for (int st = 0; st < nst; ++st) {
-            const int rs = (int)(rq % kXRaw);
-            if (rq >= (uint32_t)kXRaw &&
-                !mbar_wait_bounded(&rempty[rs], ((rq / kXRaw) - 1) & 1u, status)) {
+            const int rs = (int)(rq % kRw);
+            if (rq >= (uint32_t)kRw &&
+                !mbar_wait_bounded(&rempty[rs], ((rq / kRw) - 1) & 1u, status)) {
               ok = false;
               break;
             }
@@ -473,15 +589,21 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
             rrec[rs] = RawRec{r0, l0, combo, bstart, st,
                               (st == 0 ? kRecFirst : 0) | (last ? kRecLast : 0) |
                                   (last && g == g1 - 1 ? kRecItemEnd : 0)};
-            unsigned char* dst = raws + (size_t)rs * kXRawBytes;
-            // 4 frame rows of each channel (rows past the group's m frames are not
+            unsigned char* dst = raws + (size_t)rs * F::kRawBytes;
+            // kF frame rows of each channel (rows past the group's m frames are not
             // used; rows and bins past the spectra read as zeros)
-            const int fr = g * m + st * kXF;
-            mbar_arrive_expect_tx(&rfull[rs], stage_bytes);
-            tma_load_2d(dst + kRawA, &tm_ab, bstart, cb.x * chan_rows + fr, &rfull[rs]);
-            tma_load_2d(dst + kRawB, &tm_ab, bstart, cb.y * chan_rows + fr, &rfull[rs]);
-            tma_load_2d(dst + kRawC, &tm_cd, l0, cb.z * chan_rows + fr, &rfull[rs]);
-            tma_load_2d(dst + kRawD, &tm_cd, l0, cb.w * chan_rows + fr, &rfull[rs]);
+            const int fr = g * m + st * F::kF;
+            mbar_arrive_expect_tx(&rfull[rs], stage_bytes + (st == 0 ? scale_bytes : 0u));
+            tma_load_2d(dst + F::kRawA, &tm_ab, bstart, cb.x * chan_rows + fr, &rfull[rs]);
+            tma_load_2d(dst + F::kRawB, &tm_ab, bstart, cb.y * chan_rows + fr, &rfull[rs]);
+            tma_load_2d(dst + F::kRawC, &tm_cd, l0, cb.z * chan_rows + fr, &rfull[rs]);
+            tma_load_2d(dst + F::kRawD, &tm_cd, l0, cb.w * chan_rows + fr, &rfull[rs]);
+            if (kF16 && st == 0) {
+              tma_load_2d(dst + F::kRawSA, &tm_sab, bstart, cb.x * grp_rows + g, &rfull[rs]);
+              tma_load_2d(dst + F::kRawSB, &tm_sab, bstart, cb.y * grp_rows + g, &rfull[rs]);
+              tma_load_2d(dst + F::kRawSC, &tm_scd, l0, cb.z * grp_rows + g, &rfull[rs]);
+              tma_load_2d(dst + F::kRawSD, &tm_scd, l0, cb.w * grp_rows + g, &rfull[rs]);
+            }
             ++rq;
           }
         }
@@ -490,10 +612,10 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
       if (!ok) atomicExch(&s_fail, 1);
       // every copy issued has landed before the CTA may exit (waited before the stop
       // record moves the barrier to its next phase)
-      for (uint32_t i = rq > (uint32_t)kXRaw ? rq - kXRaw : 0; i < rq; ++i)
-        mbar_wait_bounded(&rfull[i % kXRaw], (i / kXRaw) & 1u, status);
-      const int rs = (int)(rq % kXRaw);
-      if (rq >= (uint32_t)kXRaw) mbar_wait_bounded(&rempty[rs], ((rq / kXRaw) - 1) & 1u, status);
+      for (uint32_t i = rq > (uint32_t)kRw ? rq - kRw : 0; i < rq; ++i)
+        mbar_wait_bounded(&rfull[i % kRw], (i / kRw) & 1u, status);
+      const int rs = (int)(rq % kRw);
+      if (rq >= (uint32_t)kRw) mbar_wait_bounded(&rempty[rs], ((rq / kRw) - 1) & 1u, status);
       rrec[rs].flags = kRecStop;
       asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
                        smem_addr(&rfull[rs]))
@@ -505,6 +627,8 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
     const int qd = warp & 3, h = warp >> 2;
     const int R = 32 * qd + lane;
     const uint32_t lane_addr = taddr + ((uint32_t)(32 * qd) << 16);
+    // FP16: P' carries the two factors 2^-14 of the scaled products xy and zw
+    const float fmm_p = kF16 ? fmm * 268435456.f : fmm;  // 2^28
     float sre[kXLw], sim[kXLw], qre[kXLw], qim[kXLw];
 #pragma unroll
     for (int i = 0; i < kXLw; ++i) sre[i] = sim[i] = qre[i] = qim[i] = 0.f;
@@ -526,6 +650,7 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
       // the whole record is read before the slot is released below
       const int l0 = slot[p].l0, r0 = slot[p].r0, combo = slot[p].combo;
       const float2 sxy = slot[p].sxy[R];
+      const float2 rxy = kF16 ? slot[p].rxy[R] : make_float2(1.f, 1.f);
       const uint32_t tb = lane_addr + b * kXBufCols;
 #pragma unroll
       for (int hh = 0; hh < kXLw / 2; ++hh) {
@@ -542,11 +667,27 @@ k3_trispec_cross_tc(const __grid_constant__ CUtensorMap tm_ab,
                                            slot[p].szw[0][li0 + i].y + slot[p].szw[1][li0 + i].y);
             const float2 xz = make_float2(d[0][i], d[1][i]), xw = make_float2(d[2][i], d[3][i]);
             const float2 yz = make_float2(d[4][i], d[5][i]), yw = make_float2(d[6][i], d[7][i]);
-            float2 t = cmulf(sxy, szw);
-            cmacf(t, xz, yw);
-            cmacf(t, xw, yz);
-            const float cr = pref * fmaf(fmm, d[8][i], -fm1 * t.x);
-            const float ci = pref * fmaf(fmm, d[9][i], -fm1 * t.y);
+            float cr, ci;
+            if constexpr (kF16) {
+              // the scaled products: [fmm P - fm1 (Sxz Syw + Sxw Syz)] sx sy tz tw, undone
+              // one power of two at a time (their product alone may leave the float
+              // range); Sxy Szw is unscaled
+              float2 t = cmulf(xz, yw);
+              cmacf(t, xw, yz);
+              const float2 rzw = slot[p].rzw[li0 + i];
+              float ur = fmaf(fmm_p, d[8][i], -fm1 * t.x), ui = fmaf(fmm_p, d[9][i], -fm1 * t.y);
+              ur = ur * rxy.x * rxy.y * rzw.x * rzw.y;
+              ui = ui * rxy.x * rxy.y * rzw.x * rzw.y;
+              const float2 u = cmulf(sxy, szw);
+              cr = pref * fmaf(-fm1, u.x, ur);
+              ci = pref * fmaf(-fm1, u.y, ui);
+            } else {
+              float2 t = cmulf(sxy, szw);
+              cmacf(t, xz, yw);
+              cmacf(t, xw, yz);
+              cr = pref * fmaf(fmm_p, d[8][i], -fm1 * t.x);
+              ci = pref * fmaf(fmm_p, d[9][i], -fm1 * t.y);
+            }
             const int e = 2 * hh + i;
             sre[e] += cr;
             sim[e] += ci;
@@ -602,13 +743,13 @@ __global__ void k3_cross_row0(double* __restrict__ acc, int n, int M, long long 
 
 }  // namespace
 
-cudaError_t launch_k3_trispec_cross_tc(const CUtensorMap& tm_ab, const CUtensorMap& tm_cd,
-                                       int chan_rows, int G, int m, int M, int Mp,
+cudaError_t launch_k3_trispec_cross_tc(const CrossViews& v, int G, int m, int M, int Mp,
                                        const int4* combos, int n_combos, double* acc,
                                        long long plane, int nsm, bool natural, int* counter,
                                        int* status, cudaStream_t stream) {
   if (G <= 0 || n_combos <= 0) return cudaSuccess;
   if (m < 1 || M < 2 || nsm <= 0 || (Mp & 15) || Mp < M) return cudaErrorInvalidValue;
+  if (v.f16 && (!v.tm_sab || !v.tm_scd)) return cudaErrorInvalidValue;
   const int n_rb = (2 * M - 2 + kXT - 1) / kXT, n_cb = (M + kXL - 1) / kXL;
   const long long n_tiles = (long long)n_rb * n_cb;
   CrossQueue wq;
@@ -621,9 +762,9 @@ cudaError_t launch_k3_trispec_cross_tc(const CUtensorMap& tm_ab, const CUtensorM
   const long long n_items = n_chunks * n_tiles * n_combos;
   if (n_items > 0x7fffffffll) return cudaErrorInvalidValue;
   wq.n_items = (int)n_items;
-  auto kern = k3_trispec_cross_tc;
-  cudaError_t e =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXSmemBytes);
+  auto kern = v.f16 ? k3_trispec_cross_tc<true> : k3_trispec_cross_tc<false>;
+  const size_t smem = v.f16 ? XFmt<true>::kSmem : XFmt<false>::kSmem;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
@@ -634,10 +775,13 @@ cudaError_t launch_k3_trispec_cross_tc(const CUtensorMap& tm_ab, const CUtensorM
   const float fmm = (float)(natural ? md : md * (md + 1.0));
   const float fm1 = (float)(natural ? 1.0 : md - 1.0);
   const long long combo_stride = (long long)(2 * M - 1) * M;
-  const int rawk = std::min(kRawK, Mp);  // the box width of tm_ab
-  kern<<<nsm, kXThreads, kXSmemBytes, stream>>>(tm_ab, tm_cd, chan_rows, rawk, G, m, M, Mp,
-                                                combos, wq, pref, fmm, fm1, acc, plane,
-                                                combo_stride, status);
+  const int rawk = std::min(v.f16 ? XFmt<true>::kRawK : XFmt<false>::kRawK, Mp);  // tm_ab's box
+  const int sabk = std::min(kCrossScaleBins, Mp);    // the box width of tm_sab
+  const CUtensorMap& tsab = v.f16 ? *v.tm_sab : *v.tm_ab;  // not read by the TF32 form
+  const CUtensorMap& tscd = v.f16 ? *v.tm_scd : *v.tm_cd;
+  kern<<<nsm, kXThreads, smem, stream>>>(*v.tm_ab, *v.tm_cd, tsab, tscd, v.chan_rows, v.grp_rows,
+                                         rawk, sabk, G, m, M, Mp, combos, wq, pref, fmm, fm1, acc,
+                                         plane, combo_stride, status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int n = 4 * n_combos * M;

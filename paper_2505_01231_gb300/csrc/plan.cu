@@ -326,11 +326,19 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
           SS_TRY(p, launch_k3_trispec_cross(p->d_spec, chan_stride, cnt, p->m, p->M, p->Mp,
                                             p->d_c4cross, (int)p->c4.size(), p->d_acc4, plane,
                                             p->nsm, nat, p->stream));
-        else if (p->C > 1)
-          SS_TRY(p, launch_k3_trispec_cross_tc(p->tmx_ab, p->tmx_cd, p->Gb_max * p->m, cnt,
-                                               p->m, p->M, p->Mp, p->d_c4cross,
+        else if (p->C > 1) {
+          CrossViews v;
+          v.tm_ab = &p->tmx_ab;
+          v.tm_cd = &p->tmx_cd;
+          v.tm_sab = p->oi.rmax ? &p->tmx_sab : nullptr;
+          v.tm_scd = p->oi.rmax ? &p->tmx_scd : nullptr;
+          v.chan_rows = p->Gb_max * p->m;
+          v.grp_rows = p->Gb_max;
+          v.f16 = p->oi.rmax != nullptr;
+          SS_TRY(p, launch_k3_trispec_cross_tc(v, cnt, p->m, p->M, p->Mp, p->d_c4cross,
                                                (int)p->c4.size(), p->d_acc4, plane, p->nsm, nat,
                                                p->d_counter, p->d_status, p->stream));
+        }
         for (size_t i = 0; i < p->c4.size() && p->C == 1; ++i) {
           const Combo& cb = p->c4[i];
           if (p->precision == SS_PREC_FP32)
@@ -525,13 +533,16 @@ ss_status encode_maps(ss_plan_s* p) {
       return fail(p, SS_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string(r));
   }
   if (p->C > 1) {
-    // 2-D views [rows][Mp] for the tensor-core cross S4: boxes of 4 frame rows by
-    // min(kCrossBoxBins, Mp) bins (rows of a and b) or by kCrossColBox bins (c and d)
+    // 2-D views [rows][Mp] for the tensor-core cross S4: boxes of 4 frame rows (8 for
+    // FP16X3) by min(box bins, Mp) bins (rows of a and b) or by the column box
+    // (c and d); the widths differ between the two forms
+    const cuuint32_t fr = p->precision == SS_PREC_FP16X3 ? 8 : 4;
     const cuuint64_t d2[2] = {(cuuint64_t)p->Mp, rows};
     const cuuint64_t s2[1] = {(cuuint64_t)p->Mp * sizeof(float2)};
     const cuuint32_t e2[2] = {1, 1};
-    const cuuint32_t bab[2] = {(cuuint32_t)std::min(kCrossBoxBins, p->Mp), 4};
-    const cuuint32_t bcd[2] = {(cuuint32_t)kCrossColBox, 4};
+    const bool h = p->precision == SS_PREC_FP16X3;
+    const cuuint32_t bab[2] = {(cuuint32_t)std::min(h ? kCrossBoxBinsH : kCrossBoxBins, p->Mp), fr};
+    const cuuint32_t bcd[2] = {(cuuint32_t)(h ? kCrossColBoxH : kCrossColBox), fr};
     for (int i = 0; i < 2; ++i) {
       CUresult r = encode(i == 0 ? &p->tmx_ab : &p->tmx_cd, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
                           p->d_spec, d2, s2, i == 0 ? bab : bcd, e2,
@@ -540,6 +551,23 @@ ss_status encode_maps(ss_plan_s* p) {
       if (r != CUDA_SUCCESS)
         return fail(p, SS_ECUDA,
                     "cuTensorMapEncodeTiled (cross views) failed with code " + std::to_string(r));
+    }
+  }
+  if (p->oi.rmax) {
+    // the bins' row scales: [channel x Gb_max + group][Mp] floats, boxes of one row
+    const cuuint64_t d2[2] = {(cuuint64_t)p->Mp, (cuuint64_t)p->C * p->Gb_max};
+    const cuuint64_t s2[1] = {(cuuint64_t)p->Mp * sizeof(float)};
+    const cuuint32_t e2[2] = {1, 1};
+    const cuuint32_t bab[2] = {(cuuint32_t)std::min(kCrossScaleBins, p->Mp), 1};
+    const cuuint32_t bcd[2] = {(cuuint32_t)kCrossScaleCols, 1};
+    for (int i = 0; i < 2; ++i) {
+      CUresult r = encode(i == 0 ? &p->tmx_sab : &p->tmx_scd, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                          p->oi.rmax, d2, s2, i == 0 ? bab : bcd, e2,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(p, SS_ECUDA,
+                    "cuTensorMapEncodeTiled (cross maxima) failed with code " + std::to_string(r));
     }
   }
   if (p->oi.img) {
@@ -608,7 +636,13 @@ ss_status alloc_spec(ss_plan_s* p) {
   // ps per bin (FP16: and the bin's row scale)
   const int ps_vals = p->precision == SS_PREC_FP16X3 ? 2 : 1;
   const size_t ps_group = image ? (size_t)p->C * ps_vals * p->Mp * sizeof(float) : 0;
+  // several channels in FP16X3: the bins' row scales per group
+  const bool cross16 = p->C > 1 && !p->c4.empty() && p->precision == SS_PREC_FP16X3;
+  const size_t rmax_group = cross16 ? (size_t)p->C * p->Mp * sizeof(float) : 0;
   {
+    void* r = p->oi.rmax;
+    release(r, rmax_group * p->Gb_max);
+    p->oi.rmax = nullptr;
     void* v = p->d_spec;
     release(v, spec_group * p->Gb_max);
     p->d_spec = nullptr;
@@ -617,7 +651,7 @@ ss_status alloc_spec(ss_plan_s* p) {
     release(w, ps_group * p->Gb_max);
     p->oi.ps = nullptr;
   }
-  const size_t per_group = spec_group + img_group + ps_group;
+  const size_t per_group = spec_group + img_group + ps_group + rmax_group;
   int gb = p->Gb_user;
   if (gb <= 0) {
     // about 4 GiB of per-batch scratch, at least one group
@@ -644,6 +678,10 @@ ss_status alloc_spec(ss_plan_s* p) {
     p->oi.ps_group = ps_vals * p->Mp;
     p->oi.chan_ps = (long long)gb * p->oi.ps_group;
   }
+  if (cross16) {
+    SS_TRY(p, dev_alloc(p, &p->oi.rmax, rmax_group * gb));
+    p->oi.chan_rmax = (long long)gb * p->Mp;
+  }
   return encode_maps(p);
 }
 
@@ -669,6 +707,7 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_spec);
   cudaFree(p->oi.img);
   cudaFree(p->oi.ps);
+  cudaFree(p->oi.rmax);
   cudaFree(p->d_acc1);
   cudaFree(p->d_acc2);
   cudaFree(p->d_acc3);

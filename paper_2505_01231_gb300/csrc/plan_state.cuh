@@ -70,6 +70,7 @@ struct ss_plan_s {
   int FC = 0;                      // frames per staged chunk of the pair kernels
   CUtensorMap tm64{}, tm128{}, tm48{};  // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
   CUtensorMap tmx_ab{}, tmx_cd{};        // 2-D views [rows][Mp] (several channels, tensor cores)
+  CUtensorMap tmx_sab{}, tmx_scd{};      // FP16X3: views of the bins' maxima [rows][Mp]
   CUtensorMap tm_img[4]{};               // 4-D views of each channel's Gram operand image
   ss::TileInfo* d_tiles4tc = nullptr;  // tiles of the tensor-core S4 kernel (one channel)
   int4* d_c4cross = nullptr;       // (a, b, c, d) of each S4 combination (several channels)

@@ -213,7 +213,9 @@ def test_multichannel_s2_s3():
                                              (128, 6, 16, "tf32x3"), (64, 5, 40, "tf32x3"),
                                              (32, 20, 12, "fp16x3"), (8, 4, 50, "tf32x3"),
                                              (256, 9, 6, "bf16x3"), (16, 33, 6, "tf32x3"),
-                                             (512, 4, 3, "bf16")])
+                                             (512, 4, 3, "bf16"), (64, 5, 40, "fp16x3"),
+                                             (256, 9, 6, "fp16x3"), (8, 4, 50, "fp16x3"),
+                                             (512, 17, 3, "fp16x3"), (16, 33, 6, "fp16x3")])
 def test_multichannel_s4(T, m, G, precision):
     zs = synth.multichannel_shared(4, T * m * G + 7, seed=13 + m)
     combos4 = [(0, 0, 0, 0), (0, 0, 1, 1), (0, 1, 0, 1), (0, 1, 1, 0), (0, 0, 1, 2),
@@ -222,6 +224,23 @@ def test_multichannel_s4(T, m, G, precision):
     gpu = run_gpu(zs, T, m, dt=0.5, orders=(4,), channels=4, combos=recs, precision=precision)
     ref = oracle.cross_polyspectra(zs, T, 0.5, m, s4_combos=combos4)
     assert gpu["G"] == ref["G"] == G
+    for i, c in enumerate(combos4):
+        check({"S4": gpu["S4"][i], "S4_err": gpu["S4_err"][i]},
+              {"S4": ref[("S4", c)][0], "S4_err": ref[("S4", c)][1]}, "S4")
+
+
+@pytest.mark.parametrize("scale", [1e-2, 30.0])
+def test_multichannel_s4_fp16x3_row_scaling(scale):
+    # the FP16 form scales every operand row by a power of two from the group's
+    # largest coefficient of that bin; records far from unit scale (and channels
+    # of different scales) must give the oracle's spectra all the same
+    T, m, G = 64, 6, 30
+    zs = synth.multichannel_shared(3, T * m * G + 5, seed=77)
+    zs = zs * np.array([scale, 1.0, 1.0 / scale], dtype=zs.dtype)[:, None]
+    combos4 = [(0, 0, 1, 1), (0, 1, 2, 0), (2, 2, 2, 2), (0, 2, 1, 1)]
+    recs = [(4, *c) for c in combos4]
+    gpu = run_gpu(zs, T, m, dt=0.5, orders=(4,), channels=3, combos=recs, precision="fp16x3")
+    ref = oracle.cross_polyspectra(zs.astype(np.float64), T, 0.5, m, s4_combos=combos4)
     for i, c in enumerate(combos4):
         check({"S4": gpu["S4"][i], "S4_err": gpu["S4_err"][i]},
               {"S4": ref[("S4", c)][0], "S4_err": ref[("S4", c)][1]}, "S4")
@@ -385,8 +404,9 @@ def test_config3_four_channels_full_size_sampled_points():
     assert (len(c2), len(c3)) == (10, 20) and len(c4) > 0
     gpu = run_gpu(zs, T, m, channels=C)
     assert gpu["G"] == n // (T * m)
-    # the tensor-core form of the cross S4 on the same record
+    # the tensor-core forms of the cross S4 on the same record
     gpu_tc = run_gpu(zs, T, m, channels=C, precision="tf32x3")
+    gpu_f16 = run_gpu(zs, T, m, channels=C, precision="fp16x3")
     rng = np.random.default_rng(5)
     g = oracle.window(T)
     G = n // (T * m)
@@ -429,7 +449,7 @@ def test_config3_four_channels_full_size_sampled_points():
         check({"S2": gpu["S2"][i], "S2_err": gpu["S2_err"][i]},
               {"S2": ref[0], "S2_err": np.stack([ref[1], ref[2]], -1)}, "S2")
     for key, vals, pts, out in (("S3", v3, pts3, gpu), ("S4", v4, pts4, gpu),
-                                ("S4", v4, pts4, gpu_tc)):
+                                ("S4", v4, pts4, gpu_tc), ("S4", v4, pts4, gpu_f16)):
         for i, v in vals.items():
             mean, er, ei = oracle.mean_and_stderr(np.concatenate(v))
             kk, ll = pts[i]
@@ -468,7 +488,7 @@ def test_first_order_and_natural_estimators_single_channel(estimator, precision)
     check_s1(out["S1"][0], out["S1_err"][0], ref)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "fp16x3"])
 def test_natural_estimators_several_channels(precision):
     zs = synth.multichannel_shared(3, 64 * 5 * 30 + 9, seed=43)
     combos2 = [(0, 0), (0, 2)]
