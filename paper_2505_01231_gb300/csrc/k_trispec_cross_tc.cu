@@ -13,29 +13,34 @@
 // Each complex product is a real one with K = 2m (real and imaginary part of
 // frame j at 2j and 2j + 1): a row u is (ur_j, ui_j); the column giving Re(u v)
 // is (vr_j, -vi_j) and the one giving Im(u v) is (vi_j, vr_j), so [z | w] is 96
-// real columns and zw 48.  The products run as TF32 hi/lo splits in three passes
-// (hi hi + hi lo + lo hi) accumulated in FP32 in TMEM.  Sxy and Szw depend on one
-// bin each and are summed by the threads that build the operands.
+// real columns and zw 48.  The products run in three passes (hi hi + hi lo + lo
+// hi) accumulated in FP32 in TMEM, as TF32 hi/lo (kind::tf32, stages of 4 frames)
+// or, for FP16X3, as FP16 hi/lo (kind::f16, stages of 8 frames) of operands
+// scaled per group and bin by powers of two that keep them below 2^14: x sx,
+// y sy, (x sx)(y sy) 2^-14 and z tz, w tw, (z tz)(w tw) 2^-14, with the scales
+// written by K1; the epilogue undoes them one power of two at a time.  Sxy and
+// Szw depend on one bin each and are summed, unscaled, by the threads that build
+// the operands.
 //
-// The products are bound by shared-memory bandwidth: an M = 128, N <= 128 TF32
-// product reads its operands at about 120 bytes per clock, the port's rate, so
-// the tile is as wide as two TMEM buffers allow and every other shared-memory
-// access (staging, building) is kept to one pass, free of bank conflicts.
+// Building the operands is the limit: an M = 128, N <= 128 product reads its
+// operands from shared memory at about 120 bytes per clock, so the tile is as
+// wide as two TMEM buffers allow, and the builders' staging reads and operand
+// stores are kept to one pass each, free of bank conflicts.
 //
 // Grid: one persistent CTA per SM (all 512 TMEM columns).  Items (group chunk,
 // combination, tile) come from a group-major queue.  Warp roles, coupled only by
 // mbarriers:
-// - warp 17 takes the items and, per stage of 4 frames, stages the coefficients
-//   the tile needs with four 2-D tensor-map boxes (4 frame rows of a and of b over
-//   the bins |k| of the tile's rows, at most 130 consecutive bins from an even
-//   bin; 4 frame rows of c and of d over its 24 bins) into a ring of 6, with the
-//   stage's record;
-// - warps 8-15 build each stage from them: the TF32 hi and lo parts of x, y, xy
-//   for the tile's 128 rows (a thread: one row, two frames) and of the [z | w]
-//   and zw columns (288 tasks of one column row and two frames), written to
-//   shared memory in the K-major core-matrix layout of the MMA descriptors (no
-//   copy of the operands exists in HBM), plus the group's Sxy and Szw and its
-//   record in a ring of slots;
+// - warp 17 takes the items and, per stage, stages the coefficients the tile
+//   needs with four 2-D tensor-map boxes (the stage's frame rows of a and of b
+//   over the bins |k| of the tile's rows, at most 131 consecutive bins from a
+//   multiple of 4; of c and of d over its 24 bins) into a ring, with the stage's
+//   record; FP16: with a group's first stage also the bins' row scales;
+// - warps 8-15 build each stage from them: the hi and lo parts of x, y, xy for
+//   the tile's 128 rows (a thread: one row, half the stage's frames) and of the
+//   [z | w] and zw columns (144 tasks of one operand, one bin and half the
+//   frames, writing its Re and Im columns), in the K-major core-matrix layout of
+//   the MMA descriptors (no copy of the operands exists in HBM), plus the group's
+//   Sxy, Szw, scales and record in a ring of slots;
 // - warp 16 issues, per stage, the nine MMAs (3 products x 3 passes) into the
 //   group's TMEM buffer (two buffers of 240 columns, alternating by group), and
 //   commits the stage (free again) and, after the group's last stage, the buffer;
