@@ -513,7 +513,7 @@ __device__ __forceinline__ void centre_resident(float2* Xs, float2* __restrict__
 // results as k1_spectra; the samples of a batch are contiguous and are read
 // with 16-byte (float32) or 8-byte (int16) loads when aligned.
 template <int DTYPE, int FMT>
-__global__ void __launch_bounds__(kThreadsK1)
+__global__ void __launch_bounds__(kThreadsK1, 3)
 k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, int M, int Mp,
                int FB, const float* __restrict__ win, const float2* __restrict__ tw,
                float2* __restrict__ spec, long long chan_stride, const int* __restrict__ s2_auto,
@@ -538,6 +538,27 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
     wins[i] = __ldg(&win[i]);
   }
 
+  // float32 samples of the next batch, loaded into registers while the current
+  // batch is transformed (when the batch is aligned, past the carry-over, and at
+  // most kPre vectors per thread)
+  constexpr int kPre = 4;
+  float4 pre[kPre];
+  auto prefetch = [&](int gg, int cc, int jj) -> bool {
+    if constexpr (DTYPE != SS_F32) return false;
+    const int nq = min(FB, m - jj) * T / 4;
+    if (nq > kPre * (int)blockDim.x) return false;
+    const long long off = sample0 + ((long long)gg * m + jj) * T - src.carry_n;
+    const float4* p4 = reinterpret_cast<const float4*>(
+        static_cast<const float*>(src.chunk) + (long long)cc * src.chunk_stride + off);
+    if (off < 0 || ((uintptr_t)p4 % 16) != 0) return false;
+#pragma unroll
+    for (int r = 0; r < kPre; ++r) {
+      const int q = threadIdx.x + r * blockDim.x;
+      if (q < nq) pre[r] = __ldg(p4 + q);
+    }
+    return true;
+  };
+  bool have = blockIdx.x < G && prefetch(blockIdx.x, 0, 0);  // pre holds the batch's samples
   int ngroups = 0;  // groups in the float32 sums since the last flush
   for (int g = blockIdx.x; g < G; g += gridDim.x) {
     for (int c = 0; c < C; ++c) {
@@ -549,7 +570,19 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
         const long long off = s0 - src.carry_n;
         const char* cbase = static_cast<const char*>(src.chunk) +
                             ((long long)c * src.chunk_stride + off) * (DTYPE == SS_F32 ? 4 : 2);
-        if (off >= 0 && ((uintptr_t)cbase % kVec) == 0) {
+        if (have) {
+#pragma unroll
+          for (int r = 0; r < kPre; ++r) {
+            const int q = threadIdx.x + r * blockDim.x;
+            if (q < nf * T / 4) {
+              const int i = (4 * q) & (T - 1), f = (4 * q) / T;
+              const float4 w = *reinterpret_cast<const float4*>(wins + i);
+              float2* d = bufA + f * N + i / 2;
+              d[0] = make_float2(pre[r].x * w.x, pre[r].y * w.y);
+              d[1] = make_float2(pre[r].z * w.z, pre[r].w * w.w);
+            }
+          }
+        } else if (off >= 0 && ((uintptr_t)cbase % kVec) == 0) {
           for (int q = threadIdx.x; q < nf * T / 4; q += blockDim.x) {
             const int i = (4 * q) & (T - 1), f = (4 * q) / T;
             float x0, x1, x2, x3;
@@ -572,6 +605,17 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
             bufA[q] = make_float2(load_sample<DTYPE>(src, c, si) * wins[2 * n],
                                   load_sample<DTYPE>(src, c, si + 1) * wins[2 * n + 1]);
           }
+        }
+        {  // the next batch: this group's next frames, the next channel or the next group
+          int gn = g, cn = c, jn = j0 + FB;
+          if (jn >= m) {
+            jn = 0;
+            if (++cn == C) {
+              cn = 0;
+              gn += gridDim.x;
+            }
+          }
+          have = gn < G && prefetch(gn, cn, jn);
         }
         __syncthreads();
         float2* x = bufA;
