@@ -91,6 +91,8 @@ struct OperandImage {
   long long chan_bytes = 0;   // Gb_max * group_bytes
   long long chan_ps = 0;      // Gb_max * Mp floats (FP16: Gb_max * 2 Mp)
   int ps_group = 0;           // floats of ps per group: Mp, or 2 Mp with the FP16 scales
+  int img_bins = 0;           // bins whose image rows and ps values the tensor-core S4 reads
+                              // (M - 1 when k3_column takes the last column, else Mp)
   // several channels in FP16X3: per channel, group and bin the power of two that
   // brings the bin's coefficients over the group's frames below 2^14 (within
   // [2^-60, 2^60]; 1 for a zero bin), at rmax[channel * chan_rmax + group * Mp + bin]

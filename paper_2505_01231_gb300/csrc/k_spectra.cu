@@ -240,38 +240,40 @@ __device__ __forceinline__ void centre_bin(int k, bool valid, float2 mean, int m
     const float sd = oi.sd * sc, so = oi.so * sc;
     const int npair = m * (m - 1) / 2;
     int pj = 0, pk = 1;  // next off-diagonal pair (j, j'), lexicographic
-    constexpr int kChunkBytes = FMT == kImageGramTF32 ? 1024 : 512;  // 2 CB
-    unsigned char* rbase = static_cast<unsigned char*>(oi.img) + (size_t)c * oi.chan_bytes +
-                           (size_t)g * oi.group_bytes + (size_t)(k >> 3) * oi.rg_bytes +
-                           (k & 7) * 16;
-    for (int ch = 0; ch < oi.nkc; ++ch) {
-      float e[16];
-      if (ch < oi.ndc) {
+    if (k < oi.img_bins) {  // rows the tensor-core S4 reads
+      constexpr int kChunkBytes = FMT == kImageGramTF32 ? 1024 : 512;  // 2 CB
+      unsigned char* rbase = static_cast<unsigned char*>(oi.img) + (size_t)c * oi.chan_bytes +
+                             (size_t)g * oi.group_bytes + (size_t)(k >> 3) * oi.rg_bytes +
+                             (k & 7) * 16;
+      for (int ch = 0; ch < oi.nkc; ++ch) {
+        float e[16];
+        if (ch < oi.ndc) {
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int j = ch * 16 + t;
-          e[t] = j < m ? sd * fmaf(dr[j], dr[j], di[j] * di[j]) : 0.f;
-        }
-      } else {
-        const int p0 = (ch - oi.ndc) * 16;
+          for (int t = 0; t < 16; ++t) {
+            const int j = ch * 16 + t;
+            e[t] = j < m ? sd * fmaf(dr[j], dr[j], di[j] * di[j]) : 0.f;
+          }
+        } else {
+          const int p0 = (ch - oi.ndc) * 16;
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          if (p0 + t < npair) {
-            e[t] = so * fmaf(dr[pj], dr[pk], di[pj] * di[pk]);
-            if (++pk == m) {
-              ++pj;
-              pk = pj + 1;
+          for (int t = 0; t < 16; ++t) {
+            if (p0 + t < npair) {
+              e[t] = so * fmaf(dr[pj], dr[pk], di[pj] * di[pk]);
+              if (++pk == m) {
+                ++pj;
+                pk = pj + 1;
+              }
+            } else {
+              e[t] = 0.f;
             }
-          } else {
-            e[t] = 0.f;
           }
         }
+        write_gram_row<FMT>(rbase + ch * kChunkBytes, e);
       }
-      write_gram_row<FMT>(rbase + ch * kChunkBytes, e);
+      float* psg = oi.ps + (long long)c * oi.chan_ps + (long long)g * oi.ps_group;
+      psg[k] = oi.sp * p * sc;
+      if (FMT == kImageGramF16) psg[Mp + k] = 1.f / sc;  // exact: a power of two
     }
-    float* psg = oi.ps + (long long)c * oi.chan_ps + (long long)g * oi.ps_group;
-    psg[k] = oi.sp * p * sc;
-    if (FMT == kImageGramF16) psg[Mp + k] = 1.f / sc;  // exact: a power of two
   }
   if (valid && s2sum) {
     const float c2 = p * pref2;
@@ -455,7 +457,7 @@ __device__ __forceinline__ void centre_resident(float2* Xs, float2* __restrict__
     }
     // several channels in FP16X3: the bin's row scale
     if (oi.rmax) oi.rmax[(long long)c * oi.chan_rmax + (long long)g * Mp + k] = cross_row_scale(mx);
-    if constexpr (FMT != kImageNone) {
+    if (FMT != kImageNone && k < oi.img_bins) {  // rows the tensor-core S4 reads
       const float sc = FMT == kImageGramF16 ? f16_row_scale(fmaxf(oi.sd, oi.so) * mx) : 1.f;
       const float sd = oi.sd * sc, so = oi.so * sc;
       // weighted Gram products of the bin in K order, read from the centred column

@@ -677,6 +677,8 @@ ss_status alloc_spec(ss_plan_s* p) {
     p->oi.chan_bytes = (long long)gb * group_bytes;
     p->oi.ps_group = ps_vals * p->Mp;
     p->oi.chan_ps = (long long)gb * p->oi.ps_group;
+    // no tile reads the rows of bins from M - 1 on when k3_column takes that column
+    p->oi.img_bins = p->col4 ? p->M - 1 : p->Mp;
   }
   if (cross16) {
     SS_TRY(p, dev_alloc(p, &p->oi.rmax, rmax_group * gb));
