@@ -670,14 +670,17 @@ def main():
     # K1 against HBM on the algorithmic bytes of the step (section (d) of the
     # design): the samples read and the centred spectra written, M bins per frame;
     # what the kernel moves beyond that (bins padded to Mp, the tensor-core operand
-    # image and its ps values in the split modes) is reported as overhead
+    # image and its FP16 row scales in the split modes) is reported as overhead
     k1_ms = stage_ms[0] / args.steps
     k1_bytes = frames * C * (T * z.itemsize + M * 8)
     k1_over = frames * C * (Mp - M) * 8
     if args.precision != "fp32" and C == 1:
-        nkc = (m + 15) // 16 + (m * (m - 1) // 2 + 15) // 16
-        k1_over += groups * C * Mp * (nkc * 16 * 2 * (4 if args.precision == "tf32x3" else 2) +
-                                      (8 if args.precision == "fp16x3" else 4))
+        # K chunks: the diagonal entries, then the pairs and ps; image rows for the
+        # bins the tiles read (up to M - 2 when the last column has a kernel of its own)
+        nkc = (m + 15) // 16 + (m * (m - 1) // 2 + 16) // 16
+        img_bins = M - 1 if (M - 1) % 128 == 0 else Mp
+        k1_over += groups * C * img_bins * (nkc * 16 * 2 * (4 if args.precision == "tf32x3" else 2) +
+                                            (4 if args.precision == "fp16x3" else 0))
     k1_ach = k1_bytes / (k1_ms / 1e3) / 1e9 if k1_ms > 0 else None
     roofline_k1 = {"bound": "hbm", "kernel": "k1_spectra", "achieved": k1_ach, "peak": hbm,
                    "unit": "GB/s", "frac": (k1_ach / hbm) if k1_ach else None,

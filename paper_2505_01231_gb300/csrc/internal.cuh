@@ -64,34 +64,33 @@ struct Combo {
 // one real contraction over K = m(m+1)/2, and c4 = r [that - (m-1) Sk Sl] with
 // r = 1/((m-1)(m-2)(m-3)), Sk = sum_j |d_jk|^2.  The K entries come in chunks
 // of 16: the diagonal chunks first, scaled by sd = sqrt(w_jj r), then the pairs
-// j < j' in lexicographic order, scaled by so = sqrt(4(m-1) r) (the
-// tensor-core kernel negates the pair chunks), zero-padded.  Each entry is
-// split hi + lo.  Layout per channel and group: rows (bins) in groups of 8;
-// per row group, for each chunk, a hi block and a lo block of CB bytes, each
-// holding the row group's core matrices (8 rows x 16 bytes) of the chunk's
-// 16-byte entry groups 128 bytes apart (TF32: CB = 512; BF16, FP16: CB = 256).
-// So a chunk of a row group is 2 CB bytes, a row group rg_bytes = nkc * 2 CB, a
-// group group_bytes = (Mp / 8) * rg_bytes.  ps holds sp * Sk per bin,
-// sp = sqrt((m-1) r), so that the contraction minus ps_k ps_l is c4.
+// j < j' in lexicographic order, scaled by so = sqrt(4(m-1) r), then one entry
+// ps_k = sp Sk, sp = sqrt((m-1) r), zero-padded (the tensor-core kernel negates
+// the pair chunks, so ps_k ps_l is subtracted with them and the contraction is
+// c4 itself; K = m(m+1)/2 + 1).  Each entry is split hi + lo.  Layout per
+// channel and group: rows (bins) in groups of 8; per row group, for each chunk,
+// a hi block and a lo block of CB bytes, each holding the row group's core
+// matrices (8 rows x 16 bytes) of the chunk's 16-byte entry groups 128 bytes
+// apart (TF32: CB = 512; BF16, FP16: CB = 256).  So a chunk of a row group is
+// 2 CB bytes, a row group rg_bytes = nkc * 2 CB, a group group_bytes =
+// (Mp / 8) * rg_bytes.
 // FP16: each bin's row is first multiplied by a power of two s_k that brings its
-// largest entry (at most max(sd, so) max_j |d_jk|^2) below 2^14, so that hi and
-// lo stay inside the FP16 range; ps then holds s_k sp Sk, followed (Mp floats
-// later) by 1/s_k, and the kernel divides D - ps_k ps_l by s_k s_l (exactly:
-// powers of two).
+// largest entry (at most max(max(sd, so) max_j |d_jk|^2, sp Sk)) below 2^14, so
+// that hi and lo stay inside the FP16 range; rsc holds 1/s_k per group and bin,
+// and the kernel divides D by s_k and by s_l (exactly: powers of two).
 enum { kImageNone = 0, kImageGramTF32 = 1, kImageGramBF16 = 2, kImageGramF16 = 3 };
 constexpr int kMaxGramM = 32;  // largest m of the tensor-core S4 path
 struct OperandImage {
   void* img = nullptr;
-  float* ps = nullptr;
+  float* rsc = nullptr;       // FP16: per group and bin, 1 / the bin's row scale
   int fmt = kImageNone;
   int nkc = 0, ndc = 0;       // K chunks, of which diagonal
   float sd = 0.f, so = 0.f, sp = 0.f;
   long long rg_bytes = 0;     // nkc * 2 * CB
   long long group_bytes = 0;  // (Mp / 8) * rg_bytes
   long long chan_bytes = 0;   // Gb_max * group_bytes
-  long long chan_ps = 0;      // Gb_max * Mp floats (FP16: Gb_max * 2 Mp)
-  int ps_group = 0;           // floats of ps per group: Mp, or 2 Mp with the FP16 scales
-  int img_bins = 0;           // bins whose image rows and ps values the tensor-core S4 reads
+  long long chan_rsc = 0;     // Gb_max * Mp floats (FP16)
+  int img_bins = 0;           // bins whose image rows and scales the tensor-core S4 reads
                               // (M - 1 when k3_column takes the last column, else Mp)
   // several channels in FP16X3: per channel, group and bin the power of two that
   // brings the bin's coefficients over the group's frames below 2^14 (within

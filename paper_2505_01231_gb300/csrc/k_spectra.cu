@@ -171,8 +171,9 @@ __device__ __forceinline__ float cross_row_scale(float mx2) {
   return ldexpf(1.f, min(60, max(-60, 14 - e)));
 }
 
-// FP16 operand image: the power of two that brings a bin's largest Gram entry,
-// bounded by `bound`, below 2^14 (1 for an all-zero bin).
+// FP16 operand image: the power of two that brings a bin's largest entry (the
+// weighted Gram products and ps), bounded by `bound`, below 2^14 (1 for an
+// all-zero bin).
 __device__ __forceinline__ float f16_row_scale(float bound) {
   if (!(bound > 0.f)) return 1.f;
   int e;
@@ -236,8 +237,9 @@ __device__ __forceinline__ void centre_bin(int k, bool valid, float2 mean, int m
       p += pj;
       mx = fmaxf(mx, pj);
     }
-    const float sc = FMT == kImageGramF16 ? f16_row_scale(fmaxf(oi.sd, oi.so) * mx) : 1.f;
-    const float sd = oi.sd * sc, so = oi.so * sc;
+    const float sc =
+        FMT == kImageGramF16 ? f16_row_scale(fmaxf(fmaxf(oi.sd, oi.so) * mx, oi.sp * p)) : 1.f;
+    const float sd = oi.sd * sc, so = oi.so * sc, sps = oi.sp * p * sc;
     const int npair = m * (m - 1) / 2;
     int pj = 0, pk = 1;  // next off-diagonal pair (j, j'), lexicographic
     if (k < oi.img_bins) {  // rows the tensor-core S4 reads
@@ -264,15 +266,14 @@ __device__ __forceinline__ void centre_bin(int k, bool valid, float2 mean, int m
                 pk = pj + 1;
               }
             } else {
-              e[t] = 0.f;
+              e[t] = p0 + t == npair ? sps : 0.f;  // ps after the pairs (negated with them)
             }
           }
         }
         write_gram_row<FMT>(rbase + ch * kChunkBytes, e);
       }
-      float* psg = oi.ps + (long long)c * oi.chan_ps + (long long)g * oi.ps_group;
-      psg[k] = oi.sp * p * sc;
-      if (FMT == kImageGramF16) psg[Mp + k] = 1.f / sc;  // exact: a power of two
+      if (FMT == kImageGramF16)  // exact: a power of two
+        oi.rsc[(long long)c * oi.chan_rsc + (long long)g * Mp + k] = 1.f / sc;
     }
   }
   if (valid && s2sum) {
@@ -458,8 +459,9 @@ __device__ __forceinline__ void centre_resident(float2* Xs, float2* __restrict__
     // several channels in FP16X3: the bin's row scale
     if (oi.rmax) oi.rmax[(long long)c * oi.chan_rmax + (long long)g * Mp + k] = cross_row_scale(mx);
     if (FMT != kImageNone && k < oi.img_bins) {  // rows the tensor-core S4 reads
-      const float sc = FMT == kImageGramF16 ? f16_row_scale(fmaxf(oi.sd, oi.so) * mx) : 1.f;
-      const float sd = oi.sd * sc, so = oi.so * sc;
+      const float sc =
+        FMT == kImageGramF16 ? f16_row_scale(fmaxf(fmaxf(oi.sd, oi.so) * mx, oi.sp * p)) : 1.f;
+      const float sd = oi.sd * sc, so = oi.so * sc, sps = oi.sp * p * sc;
       // weighted Gram products of the bin in K order, read from the centred column
       const int npair = m * (m - 1) / 2;
       int pj = 0, pk = 1;
@@ -490,15 +492,14 @@ __device__ __forceinline__ void centre_resident(float2* Xs, float2* __restrict__
                 dj = Xs[pj * Mp + k];
               }
             } else {
-              e[t] = 0.f;
+              e[t] = p0 + t == npair ? sps : 0.f;  // ps after the pairs (negated with them)
             }
           }
         }
         write_gram_row<FMT>(rbase + ch * kChunkBytes, e);
       }
-      float* psg = oi.ps + (long long)c * oi.chan_ps + (long long)g * oi.ps_group;
-      psg[k] = oi.sp * p * sc;
-      if (FMT == kImageGramF16) psg[Mp + k] = 1.f / sc;  // exact: a power of two
+      if (FMT == kImageGramF16)  // exact: a power of two
+        oi.rsc[(long long)c * oi.chan_rsc + (long long)g * Mp + k] = 1.f / sc;
     }
     if (valid && ia >= 0) {
       const float c2 = p * pref2;

@@ -10,29 +10,31 @@
 // with P = |d|^2, U = sum_j d_jk d_jl, V = sum_j d_jk d_jl* (the cross terms of
 // |U|^2 + |V|^2 regroup as 2 sum_{j,j'} G^k_jj' G^l_jj'), and
 //   c4 = [B(k, l) - (m-1) Sk Sl] / ((m-1)(m-2)(m-3)),  Sk = sum_j P_jk.
-// K1 writes the operand image of sqrt(|w| r) G (K = m(m+1)/2 entries in
-// chunks of 16, see OperandImage), r = 1/((m-1)(m-2)(m-3)), and
-// ps = sqrt((m-1) r) Sk, so that D - ps_k ps_l is c4 itself.  This kernel forms
-// D = A_k A_l^T over K for every 128 x 128 tile of (k, l), negating the pair
-// chunks through the MMA's negate-A bit, in FP32 accumulators in TMEM.
+// K1 writes the operand image of sqrt(|w| r) G (m(m+1)/2 entries in chunks of
+// 16, see OperandImage), r = 1/((m-1)(m-2)(m-3)), followed by the entry
+// ps = sqrt((m-1) r) Sk.  This kernel forms D = A_k A_l^T over K for every
+// 128 x 128 tile of (k, l), negating the pair chunks (and with them ps_k ps_l)
+// through the MMA's negate-A bit, in FP32 accumulators in TMEM: D is c4 itself
+// (FP16: times s_k s_l, the rows' scales).
 // Operands are split hi + lo (TF32 or BF16) and each chunk takes three MMAs
 // hi*hi + hi*lo + lo*hi (one in the plain BF16 mode).
 //
-// Warp roles (352 threads), coupled only by mbarriers.  Warp 8, TMA: takes
-// (group chunk, tile) items from the queue; per group it loads the group's ps
-// values for the tile into a ring of kPsSlots slots with a record of the group,
+// Warp roles (608 threads), coupled only by mbarriers.  Warp 16, TMA: takes
+// (group chunk, tile) items from the queue; per group it writes a record of the
+// group into a ring of kPsSlots slots (FP16: with the tile's row scales),
 // and per stage (group, kChunks consecutive K chunks) it loads two boxes of the
 // operand image through a 4-D tensor map: the 16 row groups of the k-block and
-// the 16 of the l-block.  Warps 9 and 10, MMA: warp 9 + w takes every other
+// the 16 of the l-block.  Warps 17 and 18, MMA: warp 17 + w takes every other
 // group (w = group index mod 2, TMEM buffer w of 128 columns), reads the group's
 // record from the ring, and per stage issues the MMAs of its chunks, commits
 // them to the stage's barrier (the stage is then free for the next load) and,
 // after the group's last stage, to the buffer's barrier; one warp's waits and
-// commits overlap the other's products.  Warps 0-7, the
-// epilogue: TMEM lane quadrant warp % 4, column half warp / 4.  For each group
-// they read D, form c4 and update the running sum and sum of squares of their
-// 64 grid points, which stay in TMEM columns 256-511; at the end of an item they
-// add them to the float64 accumulators.  Tiles of the last l-block are as
+// commits overlap the other's products.  Warps 0-15, the epilogue: TMEM lane
+// quadrant warp % 4, columns 32 (warp / 4) .. + 31.  For each group they read D
+// in two halves of 16 columns (FP16: divided by the scales) and update the
+// running sums of their 32 grid points, held in registers, and the running sums
+// of squares, held in TMEM columns 256-383; at the end of an item they add both
+// to the float64 accumulators.  Tiles of the last l-block are as
 // narrow as the bins left (N a multiple of 16).  Every wait is bounded; on a
 // failure the CTA stops, drains its copies and products and frees its TMEM.
 #include "internal.cuh"
@@ -41,10 +43,11 @@
 namespace ss {
 namespace {
 
-constexpr int kTM = 128, kTN = 128, kEpiWarps = 8, kMmaWarps = 2;
+constexpr int kTM = 128, kTN = 128, kEpiWarps = 16, kMmaWarps = 2;
 constexpr int kTcThreads = 32 * (kEpiWarps + 1 + kMmaWarps);
-constexpr uint32_t kTmemCols = 512;  // D0 | D1 | running sum | running sum of squares
-constexpr uint32_t kColSum = 256, kColSq = 384;
+constexpr uint32_t kTmemCols = 512;  // D0 | D1 | running sum of squares | (unused)
+constexpr uint32_t kColSq = 256;
+constexpr int kEpiCols = kTN / (kEpiWarps / 4);  // columns of an epilogue warp (32)
 
 // Operand formats.  In the image and in a stage, a row group (8 bins) holds,
 // per K chunk, a hi block and a lo block of CB bytes; a block holds the core
@@ -106,37 +109,29 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(
-          taddr),
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16};" ::"r"(taddr),
       "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
       "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
       "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
       "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
       "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
-      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
-      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
-      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
-      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
-      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      "r"(__float_as_uint(v[15]))
       : "memory");
 }
 
@@ -145,23 +140,22 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Record of a group for the epilogue, delivered with its ps values.
+// Record of a group for the MMA warps and the epilogue (FP16: with its row scales).
 struct GroupRec {
   int k0, l0, n, flags;  // n = tile columns; flags: 1 = last group of its item, 2 = stop
 };
 
-constexpr int kPsSlots = 8;  // ring of per-group ps values and records (a power of two)
+constexpr int kPsSlots = 8;  // ring of per-group records (a power of two)
 
-// kPasses: 3 (hi*hi + hi*lo + lo*hi) or 1 (hi*hi, plain BF16).  ps: the group's
-// ps values at ps + g * ps_group (FP16: their row scales 1/s_k Mp floats later).
+// kPasses: 3 (hi*hi + hi*lo + lo*hi) or 1 (hi*hi, plain BF16).  rsc (FP16): the
+// group's row scales 1/s_k at rsc + g * Mp.
 template <int kFmt, int kPasses>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restrict__ ps,
-              int ps_group, int G, int nkc, int ndc, int M, int Mp,
+k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restrict__ rsc,
+              int G, int nkc, int ndc, int M, int Mp,
               const TileInfo* __restrict__ tiles, WorkQueue wq, double* __restrict__ acc,
               long long plane, int* __restrict__ status) {
   using F = OpFmt<kFmt>;
-  constexpr int kPsVals = F::kScaled ? 2 : 1;  // ps, and the row scales (FP16)
   constexpr int S = F::kStages, KC = F::kChunks;
   constexpr uint32_t kChunkBytes = 2 * F::kCB;               // hi and lo blocks of a chunk
   constexpr uint32_t kRowGroupBytes = KC * kChunkBytes;      // a row group in a stage
@@ -170,13 +164,13 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
   extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
   __shared__ __align__(8) uint64_t full[S];             // stage loaded (TMA)
   __shared__ __align__(8) uint64_t sdone[S];            // stage's products complete
-  __shared__ __align__(8) uint64_t psfull[kPsSlots];    // ps slot loaded (TMA)
-  __shared__ __align__(8) uint64_t psempty[kPsSlots];   // ps slot read by the epilogue
+  __shared__ __align__(8) uint64_t psfull[kPsSlots];    // group slot written (FP16: scales loaded)
+  __shared__ __align__(8) uint64_t psempty[kPsSlots];   // group slot read by the epilogue
   __shared__ __align__(8) uint64_t afull[2];            // TMEM buffer holds a finished group
   __shared__ __align__(8) uint64_t aempty[2];           // TMEM buffer read by the epilogue
   __shared__ GroupRec prec[kPsSlots];
-  // ps: k rows, then l columns (FP16: then the row scales of the k rows and l columns)
-  __shared__ __align__(16) float psr[kPsSlots][kPsVals * (kTM + kTN)];
+  // FP16: the row scales 1/s of the tile's k rows, then of its l columns
+  __shared__ __align__(16) float psr[kPsSlots][F::kScaled ? kTM + kTN : 4];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -229,7 +223,7 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
         const uint32_t pk = (uint32_t)min(kTM, Mp - ti.k0) * 4u;
         const uint32_t pl = (uint32_t)min(ti.ncols, Mp - ti.l0) * 4u;
         for (int g = ga; g < gb && ok; ++g) {
-          // the group's ps values and record
+          // the group's record (FP16: and the tile's row scales)
           const int p = gq & (kPsSlots - 1);
           if (gq >= kPsSlots &&
               !mbar_wait_bounded(&psempty[p], ((gq / kPsSlots) - 1) & 1u, status)) {
@@ -237,13 +231,15 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
             break;
           }
           prec[p] = GroupRec{ti.k0, ti.l0, ti.ncols, (g == gb - 1) ? 1 : 0};
-          const float* psg = ps + (long long)g * ps_group;
-          mbar_arrive_expect_tx(&psfull[p], kPsVals * (pk + pl));
-          tma_load_1d(&psr[p][0], psg + ti.k0, pk, &psfull[p]);
-          tma_load_1d(&psr[p][kTM], psg + ti.l0, pl, &psfull[p]);
           if constexpr (F::kScaled) {
-            tma_load_1d(&psr[p][kTM + kTN], psg + Mp + ti.k0, pk, &psfull[p]);
-            tma_load_1d(&psr[p][2 * kTM + kTN], psg + Mp + ti.l0, pl, &psfull[p]);
+            const float* rg = rsc + (long long)g * Mp;
+            mbar_arrive_expect_tx(&psfull[p], pk + pl);
+            tma_load_1d(&psr[p][0], rg + ti.k0, pk, &psfull[p]);
+            tma_load_1d(&psr[p][kTM], rg + ti.l0, pl, &psfull[p]);
+          } else {
+            asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(
+                             smem_addr(&psfull[p]))
+                         : "memory");
           }
           ++gq;
           // its stages of KC chunks (chunks past nkc and rows past Mp read as zeros)
@@ -361,16 +357,18 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3, h = warp >> 2;
     const uint32_t lane_addr = taddr + ((uint32_t)(32 * q) << 16);
-    const int col0 = 64 * h;  // this warp's 64 columns of the tile
+    const int col0 = kEpiCols * h;  // this warp's 32 columns of the tile
+    // running sums over the item's groups of this thread's 32 points (row
+    // 32 q + lane, columns col0 ..); their squares are in TMEM
+    float sm[kEpiCols];
+#pragma unroll
+    for (int i = 0; i < kEpiCols; ++i) sm[i] = 0.f;
     {
-      float z[32];
+      float z[16];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) z[i] = 0.f;
+      for (int i = 0; i < 16; ++i) z[i] = 0.f;
 #pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        tmem_st32(lane_addr + kColSum + col0 + 32 * cc, z);
-        tmem_st32(lane_addr + kColSq + col0 + 32 * cc, z);
-      }
+      for (int hh = 0; hh < kEpiCols / 16; ++hh) tmem_st16(lane_addr + kColSq + col0 + 16 * hh, z);
     }
     for (uint32_t gc = 0;; ++gc) {
       const int p = gc & (kPsSlots - 1);
@@ -388,43 +386,38 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
         break;
       }
       tc_fence_after();
-      tmem_wait_st();  // the previous group's running sums are stored
-      const float skr = psr[p][32 * q + lane];
+      tmem_wait_st();  // the previous group's sums of squares are stored
       // FP16: the row scales of k and l undo the operands' scaling, applied one at a
       // time (their product alone may leave the float range)
-      const float rk = F::kScaled ? psr[p][kTM + kTN + 32 * q + lane] : 1.f;
-      const float skrk = skr * rk;
-      // 32-column blocks of this warp that meet the tile (columns past its width
-      // hold no products; their sums are never flushed)
-      const int ncc = min(2, max(0, (r.n - col0 + 31) >> 5));
-#pragma unroll 1
-      for (int cc = 0; cc < ncc; ++cc) {
-        const uint32_t col = col0 + 32 * cc;
-        float d[32], sm[32], sq[32];
-        tmem_ld32(lane_addr + b * kTN + col, d);
-        tmem_ld32(lane_addr + kColSum + col, sm);
-        tmem_ld32(lane_addr + kColSq + col, sq);
-        tmem_wait_ld();
+      const float rk = F::kScaled ? psr[p][32 * q + lane] : 1.f;
+      // 16-column halves of this warp that meet the tile (the tile width is a
+      // multiple of 16; columns past it hold no products and are never flushed)
+      const int nh = min(kEpiCols / 16, max(0, (r.n - col0) >> 4));
 #pragma unroll
-        for (int c = 0; c < 32; c += 4) {
-          const float4 w = *reinterpret_cast<const float4*>(&psr[p][kTM + col + c]);
-          const float sl[4] = {w.x, w.y, w.z, w.w};
-          float rl[4] = {1.f, 1.f, 1.f, 1.f};
-          if constexpr (F::kScaled) {
-            const float4 r4 = *reinterpret_cast<const float4*>(&psr[p][2 * kTM + kTN + col + c]);
-            rl[0] = r4.x; rl[1] = r4.y; rl[2] = r4.z; rl[3] = r4.w;
-          }
+      for (int hh = 0; hh < kEpiCols / 16; ++hh) {
+        if (hh < nh) {
+          const uint32_t col = col0 + 16 * hh;
+          float d[16], sq[16];
+          tmem_ld16(lane_addr + b * kTN + col, d);
+          tmem_ld16(lane_addr + kColSq + col, sq);
+          tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            // c4 = r (B(k, l) - (m-1) Sk Sl); FP16: ((D / s_k) - (ps_k / s_k) ps_l) / s_l
-            const float v = F::kScaled ? fmaf(d[c + i], rk, -skrk * sl[i]) * rl[i]
-                                       : fmaf(-skr, sl[i], d[c + i]);
-            sm[c + i] += v;
-            sq[c + i] = fmaf(v, v, sq[c + i]);
+          for (int c = 0; c < 16; c += 4) {
+            float rl[4] = {1.f, 1.f, 1.f, 1.f};
+            if constexpr (F::kScaled) {
+              const float4 r4 = *reinterpret_cast<const float4*>(&psr[p][kTM + col + c]);
+              rl[0] = r4.x; rl[1] = r4.y; rl[2] = r4.z; rl[3] = r4.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              // c4 = D (FP16: D / s_k / s_l)
+              const float v = F::kScaled ? (d[c + i] * rk) * rl[i] : d[c + i];
+              sm[16 * hh + c + i] += v;
+              sq[c + i] = fmaf(v, v, sq[c + i]);
+            }
           }
+          tmem_st16(lane_addr + kColSq + col, sq);
         }
-        tmem_st32(lane_addr + kColSum + col, sm);
-        tmem_st32(lane_addr + kColSq + col, sq);
       }
       // this warp has read its part of the buffer and of the ps slot
       tc_fence_before();
@@ -441,25 +434,26 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
         // doubles.
         tmem_wait_st();
         const int k = r.k0 + 32 * q + lane;
-#pragma unroll 1
-        for (int cc = 0; cc < ncc; ++cc) {
-          const uint32_t col = col0 + 32 * cc;
-          float sm[32], sq[32];
-          tmem_ld32(lane_addr + kColSum + col, sm);
-          tmem_ld32(lane_addr + kColSq + col, sq);
-          tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int l = r.l0 + (int)col + i;
-            if (k <= l && l < M) {
-              const long long o = (long long)l * M + k;
-              atomicAdd(acc + o, (double)sm[i]);
-              atomicAdd(acc + 2 * plane + o, (double)sq[i]);
+        for (int hh = 0; hh < kEpiCols / 16; ++hh) {
+          if (hh < nh) {
+            const uint32_t col = col0 + 16 * hh;
+            float sq[16];
+            tmem_ld16(lane_addr + kColSq + col, sq);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int l = r.l0 + (int)col + i;
+              if (k <= l && l < M) {
+                const long long o = (long long)l * M + k;
+                atomicAdd(acc + o, (double)sm[16 * hh + i]);
+                atomicAdd(acc + 2 * plane + o, (double)sq[i]);
+              }
+              sm[16 * hh + i] = 0.f;
+              sq[i] = 0.f;
             }
-            sm[i] = 0.f;
+            tmem_st16(lane_addr + kColSq + col, sq);
           }
-          tmem_st32(lane_addr + kColSum + col, sm);
-          tmem_st32(lane_addr + kColSq + col, sm);
         }
       }
     }
@@ -514,8 +508,8 @@ cudaError_t launch_k3_trispec_tc(const CUtensorMap& tm_img, const OperandImage& 
   wq.n_items = n_tiles * ((G + wq.group_chunk - 1) / wq.group_chunk);
   e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
-  const float* ps = oi.ps + (size_t)channel * oi.chan_ps;
-  kern<<<n_cta, kTcThreads, smem, stream>>>(tm_img, ps, oi.ps_group, G, oi.nkc, oi.ndc, M, Mp,
+  const float* rsc = oi.rsc ? oi.rsc + (size_t)channel * oi.chan_rsc : nullptr;
+  kern<<<n_cta, kTcThreads, smem, stream>>>(tm_img, rsc, G, oi.nkc, oi.ndc, M, Mp,
                                             tiles, wq, acc, plane, status);
   return cudaGetLastError();
 }

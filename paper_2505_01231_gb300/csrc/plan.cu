@@ -626,16 +626,17 @@ ss_status alloc_spec(ss_plan_s* p) {
   };
   const size_t spec_group = (size_t)p->C * p->m * p->Mp * sizeof(float2);
   const bool image = p->C == 1 && !p->c4.empty() && p->precision != SS_PREC_FP32;
-  // Gram image: ceil(m/16) diagonal chunks, then ceil(m(m-1)/2 / 16) pair chunks
+  // Gram image: ceil(m/16) diagonal chunks, then ceil((m(m-1)/2 + 1) / 16) chunks
+  // of the pairs and ps
   const int ndc = (p->m + 15) / 16;
-  const int nkc = ndc + (p->m * (p->m - 1) / 2 + 15) / 16;
+  const int nkc = ndc + (p->m * (p->m - 1) / 2 + 16) / 16;
   const size_t cb = p->precision == SS_PREC_TF32X3 ? 512 : 256;
   const size_t rg_bytes = (size_t)nkc * 2 * cb;
   const size_t group_bytes = (size_t)(p->Mp / 8) * rg_bytes;
   const size_t img_group = image ? (size_t)p->C * group_bytes : 0;
-  // ps per bin (FP16: and the bin's row scale)
-  const int ps_vals = p->precision == SS_PREC_FP16X3 ? 2 : 1;
-  const size_t ps_group = image ? (size_t)p->C * ps_vals * p->Mp * sizeof(float) : 0;
+  // FP16: the bins' row scales per group
+  const bool scaled = image && p->precision == SS_PREC_FP16X3;
+  const size_t rsc_group = scaled ? (size_t)p->C * p->Mp * sizeof(float) : 0;
   // several channels in FP16X3: the bins' row scales per group
   const bool cross16 = p->C > 1 && !p->c4.empty() && p->precision == SS_PREC_FP16X3;
   const size_t rmax_group = cross16 ? (size_t)p->C * p->Mp * sizeof(float) : 0;
@@ -647,11 +648,11 @@ ss_status alloc_spec(ss_plan_s* p) {
     release(v, spec_group * p->Gb_max);
     p->d_spec = nullptr;
     release(p->oi.img, img_group * p->Gb_max);
-    void* w = p->oi.ps;
-    release(w, ps_group * p->Gb_max);
-    p->oi.ps = nullptr;
+    void* w = p->oi.rsc;
+    release(w, rsc_group * p->Gb_max);
+    p->oi.rsc = nullptr;
   }
-  const size_t per_group = spec_group + img_group + ps_group + rmax_group;
+  const size_t per_group = spec_group + img_group + rsc_group + rmax_group;
   int gb = p->Gb_user;
   if (gb <= 0) {
     // about 4 GiB of per-batch scratch, at least one group
@@ -665,7 +666,7 @@ ss_status alloc_spec(ss_plan_s* p) {
   p->oi = OperandImage();
   if (image) {
     SS_TRY(p, dev_alloc(p, &p->oi.img, img_group * gb));
-    SS_TRY(p, dev_alloc(p, &p->oi.ps, ps_group * gb));
+    if (scaled) SS_TRY(p, dev_alloc(p, &p->oi.rsc, rsc_group * gb));
     p->oi.fmt = p->precision == SS_PREC_TF32X3   ? kImageGramTF32
                 : p->precision == SS_PREC_FP16X3 ? kImageGramF16
                                                  : kImageGramBF16;
@@ -675,8 +676,7 @@ ss_status alloc_spec(ss_plan_s* p) {
     p->oi.rg_bytes = (long long)rg_bytes;
     p->oi.group_bytes = (long long)group_bytes;
     p->oi.chan_bytes = (long long)gb * group_bytes;
-    p->oi.ps_group = ps_vals * p->Mp;
-    p->oi.chan_ps = (long long)gb * p->oi.ps_group;
+    p->oi.chan_rsc = (long long)gb * p->Mp;
     // no tile reads the rows of bins from M - 1 on when k3_column takes that column
     p->oi.img_bins = p->col4 ? p->M - 1 : p->Mp;
   }
@@ -708,7 +708,7 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_carry);
   cudaFree(p->d_spec);
   cudaFree(p->oi.img);
-  cudaFree(p->oi.ps);
+  cudaFree(p->oi.rsc);
   cudaFree(p->oi.rmax);
   cudaFree(p->d_acc1);
   cudaFree(p->d_acc2);
