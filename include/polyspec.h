@@ -322,7 +322,7 @@ ss_status ss_inject_timeout(ss_plan_t plan, int on);
  * SM) or 8 x 4 micro-tiles in CTAs of 128 threads with 2 or 3 pipeline stages.
  *
  * ss_autotune   -- time every form of K1 and K2 on this plan's shapes on this
- *                  GPU (a synthetic Gaussian record of about 16 x SMs groups,
+ *                  GPU (a synthetic Gaussian record of about 64 x SMs groups,
  *                  generated on the device; one untimed pass and the best of
  *                  three per form) and keep the fastest.  Valid only before the
  *                  first ss_accumulate (or after ss_reset); SS_ESTATE otherwise.

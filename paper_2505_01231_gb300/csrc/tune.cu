@@ -165,9 +165,12 @@ ss_status ss_autotune(ss_plan_t p, double* best_ms) {
       if (dev >= 0) cudaSetDevice(dev);
     }
   } restore{prev};
-  // enough groups for several waves of every kernel, within one batch
+  // enough groups for several waves of every kernel, within one batch: 64 per SM,
+  // so that the pair kernels' items hold about as many groups as in a full batch
+  // (with 16 per SM, the items of the 128-thread tilings were a fifth of their
+  // full-batch size and their float64 flushes weighed several times more)
   const long long per_group = (long long)p->m * p->T;
-  const long long G = std::min<long long>(p->Gb_max, std::max(8, 16 * p->nsm));
+  const long long G = std::min<long long>(p->Gb_max, std::max(8, 64 * p->nsm));
   const long long n = G * per_group;
   void* rec = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
