@@ -25,7 +25,8 @@
 // and per stage (group, kChunks consecutive K chunks) it loads two boxes of the
 // operand image through a 4-D tensor map: the 16 row groups of the k-block and
 // the 16 of the l-block.  Warps 17 and 18, MMA: warp 17 + w takes every other
-// group (w = group index mod 2, TMEM buffer w of 128 columns), reads the group's
+// group (w = group index mod 2; TMEM buffer group index mod 3 of 128 columns, so
+// the products run up to two groups ahead of the epilogue), reads the group's
 // record from the ring, and per stage issues the MMAs of its chunks, commits
 // them to the stage's barrier (the stage is then free for the next load) and,
 // after the group's last stage, to the buffer's barrier; one warp's waits and
@@ -45,8 +46,11 @@ namespace {
 
 constexpr int kTM = 128, kTN = 128, kEpiWarps = 16, kMmaWarps = 2;
 constexpr int kTcThreads = 32 * (kEpiWarps + 1 + kMmaWarps);
-constexpr uint32_t kTmemCols = 512;  // D0 | D1 | running sum of squares | (unused)
+constexpr uint32_t kTmemCols = 512;  // D0 | D1 | running sum of squares | D2
 constexpr uint32_t kColSq = 256;
+constexpr int kBufs = 3;  // TMEM accumulator buffers: group g uses buffer g mod 3
+
+__device__ __forceinline__ uint32_t buf_col(uint32_t b) { return b == 2 ? 384u : b * kTN; }
 constexpr int kEpiCols = kTN / (kEpiWarps / 4);  // columns of an epilogue warp (32)
 
 // Operand formats.  In the image and in a stage, a row group (8 bins) holds,
@@ -166,8 +170,8 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
   __shared__ __align__(8) uint64_t sdone[S];            // stage's products complete
   __shared__ __align__(8) uint64_t psfull[kPsSlots];    // group slot written (FP16: scales loaded)
   __shared__ __align__(8) uint64_t psempty[kPsSlots];   // group slot read by the epilogue
-  __shared__ __align__(8) uint64_t afull[2];            // TMEM buffer holds a finished group
-  __shared__ __align__(8) uint64_t aempty[2];           // TMEM buffer read by the epilogue
+  __shared__ __align__(8) uint64_t afull[kBufs];        // TMEM buffer holds a finished group
+  __shared__ __align__(8) uint64_t aempty[kBufs];       // TMEM buffer read by the epilogue
   __shared__ GroupRec prec[kPsSlots];
   // FP16: the row scales 1/s of the tile's k rows, then of its l columns
   __shared__ __align__(16) float psr[kPsSlots][F::kScaled ? kTM + kTN : 4];
@@ -185,7 +189,7 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
       mbar_init(&psfull[p], 1);
       mbar_init(&psempty[p], kEpiWarps);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kBufs; ++b) {
       mbar_init(&afull[b], 1);
       mbar_init(&aempty[b], kEpiWarps);
     }
@@ -299,11 +303,11 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
         if (!mbar_wait_bounded(&psfull[p], (gc / kPsSlots) & 1u, status)) break;
         const GroupRec r = prec[p];
         if (r.flags & 2) break;
-        const uint32_t d = taddr + w * kTN;
+        const uint32_t b = gc % kBufs;
+        const uint32_t d = taddr + buf_col(b);
         const uint32_t idesc = idesc0 | ((uint32_t)(r.n >> 3) << 17);
-        // the buffer is free once the epilogue has read this warp's previous group
-        if (gc >= kMmaWarps &&
-            !mbar_wait_bounded(&aempty[w], ((gc / kMmaWarps) - 1) & 1u, status))
+        // the buffer is free once the epilogue has read its previous group, gc - 3
+        if (gc >= kBufs && !mbar_wait_bounded(&aempty[b], ((gc / kBufs) - 1) & 1u, status))
           break;
         // order the group's products after the epilogue's reads of the buffer; the
         // staged operands need no fence (TMA writes and MMA reads are both
@@ -346,7 +350,7 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
           last_ph = ph;
         }
         if (stop) break;
-        mma_commit(&afull[w]);  // arrives when the group's products are complete
+        mma_commit(&afull[b]);  // arrives when the group's products are complete
       }
       if (*(volatile int*)status != 0) atomicExch(&s_fail, 1);
       // the products issued must be complete before the TMEM is freed
@@ -372,7 +376,7 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
     }
     for (uint32_t gc = 0;; ++gc) {
       const int p = gc & (kPsSlots - 1);
-      const uint32_t b = gc & 1u;
+      const uint32_t b = gc % kBufs;
       // one decision per warp: the TMEM accesses below are warp-collective
       if (!__all_sync(0xffffffffu,
                       mbar_wait_bounded(&psfull[p], (gc / kPsSlots) & 1u, status))) {
@@ -381,7 +385,7 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
       }
       const GroupRec r = prec[p];
       if (r.flags & 2) break;
-      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&afull[b], (gc >> 1) & 1u, status))) {
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&afull[b], (gc / kBufs) & 1u, status))) {
         if (lane == 0) atomicExch(&s_fail, 1);
         break;
       }
@@ -398,7 +402,7 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
         if (hh < nh) {
           const uint32_t col = col0 + 16 * hh;
           float d[16], sq[16];
-          tmem_ld16(lane_addr + b * kTN + col, d);
+          tmem_ld16(lane_addr + buf_col(b) + col, d);
           tmem_ld16(lane_addr + kColSq + col, sq);
           tmem_wait_ld();
 #pragma unroll
