@@ -397,19 +397,20 @@ k1_spectra(SampleSource src, long long sample0, int G, int C, int T, int m, int 
   if (ngroups) flush_k1_sums(C, M, s2_auto, acc2, n_s2, s2sum, s2sq, s1s, acc1);
 }
 
-// Stockham pass over a batch of FB frames of N points (frame f at x + f N);
-// all threads share the FB * N/R butterflies of the pass.
+// Stockham pass over a batch of FB frames of N points (frame f at x + f sx, its
+// output at y + f sy); all threads share the FB * N/R butterflies of the pass.
 template <int R>
 __device__ __forceinline__ void stockham_pass_batch(const float2* __restrict__ x,
                                                     float2* __restrict__ y, int N, int Ns,
-                                                    const float2* __restrict__ tw, int T, int FB) {
+                                                    const float2* __restrict__ tw, int T, int FB,
+                                                    int sx, int sy) {
   const int NR = N / R;
   const int lg = __ffs(NR) - 1;  // NR is a power of two
   const int tw_scale = T / (Ns * R);
   for (int idx = threadIdx.x; idx < FB * NR; idx += blockDim.x) {
     const int f = idx >> lg, j = idx & (NR - 1);
-    const float2* xf = x + f * N;
-    float2* yf = y + f * N;
+    const float2* xf = x + f * sx;
+    float2* yf = y + f * sy;
     const int k = j & (Ns - 1);
     float2 v[R];
 #pragma unroll
@@ -512,7 +513,11 @@ __device__ __forceinline__ void centre_resident(float2* Xs, float2* __restrict__
 // K1 for groups whose coefficients fit in shared memory: the group's m frames
 // are transformed FB at a time (every Stockham pass covers all FB frames, so a
 // frame costs a fraction of the barriers), the coefficients X_jk stay in shared
-// memory, and the centred coefficients are written to the spectra once.  Same
+// memory, and the centred coefficients are written to the spectra once.  The
+// passes of a batch alternate between the batch's own coefficient rows and one
+// buffer of FB frames (a second buffer would halve FB within the same shared
+// memory); the split into X_k reads the last pass's output and writes the rows,
+// in place (one thread per pair k, N - k) when the rows hold that output.  Same
 // results as k1_spectra; the samples of a batch are contiguous and are read
 // with 16-byte (float32) or 8-byte (int16) loads when aligned.
 template <int DTYPE, int FMT>
@@ -524,9 +529,8 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
            double* __restrict__ acc1) {
   extern __shared__ float4 smem_raw[];
   const int N = T / 2;
-  float2* bufA = reinterpret_cast<float2*>(smem_raw);  // [FB][N]
-  float2* bufB = bufA + FB * N;                        // [FB][N]
-  float2* Xs = bufB + FB * N;                          // [m][Mp]
+  float2* buf = reinterpret_cast<float2*>(smem_raw);  // [FB][N]
+  float2* Xs = buf + FB * N;                          // [m][Mp]
   float2* tws = Xs + m * Mp;                           // [T] twiddles e^{+2 pi j a/T}
   float* wins = reinterpret_cast<float*>(tws + T);     // [T] window / sqrt(sum g^2)
   float* s2sum = wins + T;                             // [C][M]
@@ -580,7 +584,7 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
             if (q < nf * T / 4) {
               const int i = (4 * q) & (T - 1), f = (4 * q) / T;
               const float4 w = *reinterpret_cast<const float4*>(wins + i);
-              float2* d = bufA + f * N + i / 2;
+              float2* d = Xs + (j0 + f) * Mp + i / 2;
               d[0] = make_float2(pre[r].x * w.x, pre[r].y * w.y);
               d[1] = make_float2(pre[r].z * w.z, pre[r].w * w.w);
             }
@@ -597,7 +601,7 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
               x0 = v.x; x1 = v.y; x2 = v.z; x3 = v.w;
             }
             const float4 w = *reinterpret_cast<const float4*>(wins + i);
-            float2* d = bufA + f * N + i / 2;
+            float2* d = Xs + (j0 + f) * Mp + i / 2;
             d[0] = make_float2(x0 * w.x, x1 * w.y);
             d[1] = make_float2(x2 * w.z, x3 * w.w);
           }
@@ -605,8 +609,8 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
           for (int q = threadIdx.x; q < nf * N; q += blockDim.x) {
             const int f = q / N, n = q - f * N;
             const long long si = s0 + (long long)f * T + 2 * n;
-            bufA[q] = make_float2(load_sample<DTYPE>(src, c, si) * wins[2 * n],
-                                  load_sample<DTYPE>(src, c, si + 1) * wins[2 * n + 1]);
+            Xs[(j0 + f) * Mp + n] = make_float2(load_sample<DTYPE>(src, c, si) * wins[2 * n],
+                                                load_sample<DTYPE>(src, c, si + 1) * wins[2 * n + 1]);
           }
         }
         {  // the next batch: this group's next frames, the next channel or the next group
@@ -621,36 +625,44 @@ k1_spectra_res(SampleSource src, long long sample0, int G, int C, int T, int m, 
           have = gn < G && prefetch(gn, cn, jn);
         }
         __syncthreads();
-        float2* x = bufA;
-        float2* y = bufB;
+        float2* rows = Xs + j0 * Mp;
+        float2* x = rows;  // the pass input and its frame stride
+        float2* y = buf;
+        int sx = Mp, sy = N;
         int Ns = 1;
         int rem = N;
         while (rem > 1) {
           if (rem % 8 == 0 && rem != 16) {
-            stockham_pass_batch<8>(x, y, N, Ns, tws, T, nf);
+            stockham_pass_batch<8>(x, y, N, Ns, tws, T, nf, sx, sy);
             Ns *= 8; rem /= 8;
           } else if (rem % 4 == 0) {
-            stockham_pass_batch<4>(x, y, N, Ns, tws, T, nf);
+            stockham_pass_batch<4>(x, y, N, Ns, tws, T, nf, sx, sy);
             Ns *= 4; rem /= 4;
           } else {
-            stockham_pass_batch<2>(x, y, N, Ns, tws, T, nf);
+            stockham_pass_batch<2>(x, y, N, Ns, tws, T, nf, sx, sy);
             Ns *= 2; rem /= 2;
           }
           __syncthreads();
           float2* t = x; x = y; y = t;
+          const int ts = sx; sx = sy; sy = ts;
         }
-        // X_k = 1/2 [(Y_k + Y*_{N-k}) - j w^k (Y_k - Y*_{N-k})], w = e^{+2 pi j/T}
-        for (int f = 0; f < nf; ++f) {
-          const float2* xf = x + f * N;
-          float2* xr = Xs + (j0 + f) * Mp;
-          for (int k = threadIdx.x; k < M; k += blockDim.x) {
-            const float2 yk = xf[k == N ? 0 : k];
-            const float2 yr = xf[k == 0 ? 0 : N - k];
-            const float2 yc = make_float2(yr.x, -yr.y);
-            const float2 sm = cadd(yk, yc);
-            const float2 wd = cmul(tws[k], csub(yk, yc));
-            xr[k] = make_float2(0.5f * (sm.x + wd.y), 0.5f * (sm.y - wd.x));
-          }
+        // X_k = 1/2 [(Y_k + Y*_{N-k}) - j w^k (Y_k - Y*_{N-k})], w = e^{+2 pi j/T},
+        // Y_N = Y_0: each thread takes a pair k, N - k (k = 0 also gives X_N from
+        // Y_0), reads both Y and writes both X, so the split may work in place
+        auto split = [&](float2 yk, float2 yr, int k) {
+          const float2 yc = make_float2(yr.x, -yr.y);
+          const float2 sm = cadd(yk, yc);
+          const float2 wd = cmul(tws[k], csub(yk, yc));
+          return make_float2(0.5f * (sm.x + wd.y), 0.5f * (sm.y - wd.x));
+        };
+        const int NH = N / 2 + 1;  // pairs per frame
+        for (int idx = threadIdx.x; idx < nf * NH; idx += blockDim.x) {
+          const int f = idx / NH, k = idx - f * NH;
+          const float2* xf = x + f * sx;
+          float2* xr = rows + f * Mp;
+          const float2 a = xf[k], b = xf[k == 0 ? 0 : N - k];
+          xr[k] = split(a, b, k);
+          xr[N - k] = split(b, a, N - k);
         }
       }
       __syncthreads();  // the group's coefficients are in shared memory
@@ -892,7 +904,7 @@ cudaError_t launch_k1_t(const SampleSource& src, long long sample0, int G, int C
   // a group whose coefficients fit beside a batch of FFT buffers stays resident
   const size_t fixed = (size_t)m * Mp * sizeof(float2) + (size_t)2 * C * M * sizeof(float) +
                        (size_t)T * (sizeof(float2) + sizeof(float));  // + twiddles and window
-  const size_t per_frame = (size_t)T * sizeof(float2);  // two buffers of T/2 points
+  const size_t per_frame = (size_t)(T / 2) * sizeof(float2);  // one buffer of T/2 points
   // kK1Auto: three CTAs per SM with a smaller batch of frames beat two with a
   // larger one (T = 1024, m = 10: 2.59 vs 2.69 ms per step), else the 96 KB
   // budget; kK1Resident96: the 96 KB budget; kK1Frames: frame at a time
