@@ -319,7 +319,9 @@ ss_status ss_inject_timeout(ss_plan_t plan, int on);
  * coefficients in shared memory within a 74 KB or a 96 KB budget, or with a
  * warp per frame (T <= 1024), or transforms one frame at a time; K2 uses 4 x 4
  * micro-tiles in CTAs of 256 threads (4 stages, or 3 stages with three CTAs per
- * SM) or 8 x 4 micro-tiles in CTAs of 128 threads with 2 or 3 pipeline stages.
+ * SM), 8 x 4 micro-tiles in CTAs of 128 threads with 2 or 3 pipeline stages, or
+ * (one channel) 8 x 4 micro-tiles in warps that each take their own 32 x 32
+ * sub-tiles and stage their own frames, with no block barrier.
  *
  * ss_autotune   -- time every form of K1 and K2 on this plan's shapes on this
  *                  GPU (a synthetic Gaussian record of about 64 x SMs groups,
@@ -330,7 +332,7 @@ ss_status ss_inject_timeout(ss_plan_t plan, int on);
  *                  stream; leaves the plan reset.  best_ms (may be NULL)
  *                  receives the time of the fastest pass.
  * ss_get_tuning -- the plan's choices as text: "polyspec-tuning 1 <key> |
- *                  k1=<auto|r96|frames|warp> k2=<44|44s3|84s2|84s3>", where the key names
+ *                  k1=<auto|r96|frames|warp> k2=<44|44s3|84s2|84s3|84w>", where the key names
  *                  T, m, channels, dtype, precision, SM count and GPU.  out holds
  *                  cap bytes (SS_EINVAL if too small).
  * ss_set_tuning -- apply such a text (valid at any time between calls).  A text

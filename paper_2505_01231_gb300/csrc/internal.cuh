@@ -129,9 +129,11 @@ cudaError_t launch_k1_cross_s2(const float2* spec, long long chan_stride, int G,
 // K2 tilings (the autotuner's choice per plan): 4 x 4 micro-tiles in CTAs of 256
 // threads with 4 stages (two CTAs per SM) or 3 stages (three CTAs per SM, 85
 // registers), or 8 x 4 micro-tiles in CTAs of 128 threads with 2 or 3 stages;
-// all take the same 64 x 64 tiles and give the same sums.
+// all take the same 64 x 64 tiles and give the same sums.  kK2Warp84 (one channel;
+// the plan takes kK2Tile84Stages2 for several) runs k2_bispec84w: 8 x 4 micro-tiles
+// in warps that work independently on 32 x 32 sub-tiles, each with its own stages.
 enum { kK2Tile44 = 0, kK2Tile84Stages2 = 1, kK2Tile84Stages3 = 2, kK2Tile44Stages3 = 3,
-       kK2Variants = 4 };
+       kK2Warp84 = 4, kK2Variants = 5 };
 cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
                              const float2* spec_a, const float2* spec_b, const float2* spec_c,
                              int rowA, int rowB, int rowC, int G, int m, int FC, int M, int Mp,
@@ -222,6 +224,14 @@ cudaError_t launch_k5_complex(const float2* spec, long long chan_stride, int G, 
                               cudaStream_t stream);
 
 // K2 for isolated grid points of one channel (pts: n_pts (k, l) pairs)
+// One channel: independent warps on 32 x 32 sub-tiles (the plan's list of those
+// with more than 8 points of the domain; k2_points takes the others' points).
+// tm32 / tm64w: boxes of 2 / 4 blocks (32 / 64 bins) x kFrames84w frame rows.
+constexpr int kFrames84w = 4;
+cudaError_t launch_k2_bispec84w(const CUtensorMap& tm32, const CUtensorMap& tm64w, int row0,
+                                int G, int m, int M, const TileInfo* tiles, int n_tiles,
+                                float pref3, double* acc, long long plane, int nsm, int* counter,
+                                int* status, int inject_timeout, cudaStream_t stream);
 cudaError_t launch_k2_points(const float2* spec, int Mp, int G, int m, const int2* pts,
                              int n_pts, int M, float pref3, double* acc, long long plane,
                              cudaStream_t stream);

@@ -625,6 +625,221 @@ k2_bispec84(const __grid_constant__ CUtensorMap tm64, const __grid_constant__ CU
   }
 }
 
+// ---------------------------------------------------------------------------
+// K2 with independent warps (k2_bispec84w, one channel).  Each warp of a
+// 128-thread CTA is a worker of its own: it takes (group chunk, 32 x 32
+// sub-tile) items from the queue, stages the item's frame rows kFS84w at a
+// time into its own ring of kSt84w stages (a: 32 bins, b: 32 bins, c: 64 bins
+// per frame, three 3-D TMA boxes with 128-byte swizzling, refilled by its lane
+// 0 as soon as the warp leaves a stage) and evaluates 8 x 4 micro-tiles as
+// k2_bispec84 does, with the same lane layout (conflict-free for these 256- and
+// 512-byte frame rows too, checked with a bank model).  No block barrier: a warp
+// never waits for another.  The frames of an item's groups are contiguous rows,
+// so the stages run across group boundaries and a group ends at the frame where
+// its m-th row is consumed.  Per-item sums: 128 TMEM columns of the warp's lane
+// quadrant; four CTAs per SM fill the 512 columns.
+constexpr int kThreads84w = 128;
+constexpr int kFS84w = kFrames84w;  // frames per stage
+constexpr int kSt84w = 3;   // stages per warp
+constexpr uint32_t kStage84w = kFS84w * (256u + 256u + 512u);  // a | b | c
+constexpr uint32_t kRing84w = kSt84w * kStage84w;
+
+__global__ void __launch_bounds__(kThreads84w, 4)
+k2_bispec84w(const __grid_constant__ CUtensorMap tm32, const __grid_constant__ CUtensorMap tm64,
+             int row0, int m, int M, int G, const TileInfo* __restrict__ tiles, WorkQueue wq,
+             float pref3, double* __restrict__ acc, long long plane, int* __restrict__ status,
+             int inject_timeout) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];  // + 1024 spare bytes
+  __shared__ __align__(8) uint64_t full[kThreads84w / 32][kSt84w];
+  __shared__ __align__(8) uint64_t never;  // completed by nothing (timeout test)
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned char* ring = align1024<unsigned char>(smem_raw) + (size_t)warp * kRing84w;
+  const int tx = lane & 3;
+  const int ty = ((lane >> 3) & 1) | (((lane >> 2) & 1) << 1) | (((lane >> 4) & 1) << 2);
+  const int kt = 8 * tx, lt = 4 * ty;  // micro-tile origin in the sub-tile
+  // byte offsets of the thread's loads in frame 0 of a stage, before the swizzle:
+  // frame f of a or b (256-byte rows) flips bits 5-6 by 2f, of c (512-byte rows)
+  // bit 6 by f
+  const uint32_t oa0 = kt * 8, ob0 = lt * 8, oc0 = (kt + lt) * 8;
+
+  if (tid == 0) {
+    for (int w = 0; w < kThreads84w / 32; ++w)
+      for (int s = 0; s < kSt84w; ++s) mbar_init(&full[w][s], 1);
+    mbar_init(&never, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tsum = tmem_slot + ((uint32_t)(32 * warp) << 16);
+  {
+    float z[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) z[i] = 0.f;
+#pragma unroll
+    for (int part = 0; part < 4; ++part) tmem_st32(tsum + 32 * part, z);
+  }
+  uint32_t qb = 0;  // stages this warp has consumed (stage = q % kSt84w)
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(wq.counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= wq.n_items) break;
+    const int t = item % wq.n_tiles;
+    const int ga = (item / wq.n_tiles) * wq.group_chunk;
+    const int gb = min(G, ga + wq.group_chunk);
+    const int k0 = tiles[t].k0, l0 = tiles[t].l0;
+    const int rows = (gb - ga) * m;  // the item's frames, consecutive rows from r0
+    const int r0 = row0 + ga * m;
+    const int nst = (rows + kFS84w - 1) / kFS84w;
+    auto issue = [&](int i) {  // lane 0: stage of step i (kFS84w rows from r0 + i kFS84w)
+      const int s = (int)((qb + i) % kSt84w);
+      unsigned char* st = ring + (size_t)s * kStage84w;
+      const int r = r0 + i * kFS84w;
+      mbar_arrive_expect_tx(&full[warp][s], kStage84w);
+      tma_load_3d(st, &tm32, 0, k0 >> 4, r, &full[warp][s]);
+      tma_load_3d(st + kFS84w * 256, &tm32, 0, l0 >> 4, r, &full[warp][s]);
+      tma_load_3d(st + kFS84w * 512, &tm64, 0, (k0 + l0) >> 4, r, &full[warp][s]);
+    };
+    float ar[32], ai[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) ar[i] = ai[i] = 0.f;
+    if (lane == 0) {
+      fence_async_smem();
+      for (int i = 0; i < kSt84w && i < nst; ++i) issue(i);
+    }
+    __syncwarp();
+    bool ok = true;
+    int jg = 0;  // frames of the current group consumed
+    for (int i = 0; i < nst && ok; ++i) {
+      const int s = (int)((qb + i) % kSt84w);
+      ok = mbar_wait_bounded(&full[warp][s], ((qb + i) / kSt84w) & 1u, status);
+      // timeout test: the warp that takes the first item waits, at its first
+      // step, on a barrier that nothing completes
+      if (inject_timeout && item == 0 && i == 0 && lane == 0)
+        ok = mbar_wait_bounded(&never, 0u, status, kInjectedWaitNs) && ok;
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        // the copies issued and not consumed (steps i .. i + kSt84w - 1) land
+        // before the warp stops; those waits keep the full limit
+        if (lane == 0)
+          for (int q = i; q < nst && q < i + kSt84w; ++q)
+            mbar_wait_bounded(&full[warp][(qb + q) % kSt84w], ((qb + q) / kSt84w) & 1u, status);
+        break;
+      }
+      const unsigned char* sA = ring + (size_t)s * kStage84w;
+      const unsigned char* sB = sA + kFS84w * 256;
+      const unsigned char* sC = sA + kFS84w * 512;
+      const int nf = min(kFS84w, rows - i * kFS84w);
+#pragma unroll 1
+      for (int f = 0; f < nf; ++f) {
+        const unsigned char* pa = sA + f * 256;
+        const unsigned char* pb = sB + f * 256;
+        const unsigned char* pc = sC + f * 512;
+        const uint32_t fab = (uint32_t)f << 5, fc = (uint32_t)(f & 1) << 6;
+        float2 al[4], ac[12];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float4 v = lds128(pb + (swz128(ob0 + 16 * q) ^ fab));
+          al[2 * q] = make_float2(v.x, v.y);
+          al[2 * q + 1] = make_float2(v.z, v.w);
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const float4 v = lds128(pc + (swz128(oc0 + 16 * q) ^ fc));
+          ac[2 * q] = make_float2(v.x, v.y);
+          ac[2 * q + 1] = make_float2(v.z, v.w);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 v = lds128(pa + (swz128(oa0 + 16 * q) ^ fab));
+          const float2 ak2[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int a = 2 * q + h;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              // p = a_k b_l ; accumulate p * conj(c_{k+l})
+              const float px = fmaf(ak2[h].x, al[b].x, -ak2[h].y * al[b].y);
+              const float py = fmaf(ak2[h].x, al[b].y, ak2[h].y * al[b].x);
+              const float2 c = ac[a + b];
+              ar[a * 4 + b] = fmaf(px, c.x, fmaf(py, c.y, ar[a * 4 + b]));
+              ai[a * 4 + b] = fmaf(py, c.x, fmaf(-px, c.y, ai[a * 4 + b]));
+            }
+          }
+        }
+        if (++jg == m) {  // end of a group: c3 into the per-item sums
+          jg = 0;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {  // halves of 16 points keep the registers low
+            float tt[16];
+            tmem_ld16(tsum + 16 * h, tt);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) tt[q] = fmaf(ar[16 * h + q], pref3, tt[q]);
+            tmem_st16(tsum + 16 * h, tt);
+            tmem_ld16(tsum + 32 + 16 * h, tt);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) tt[q] = fmaf(ai[16 * h + q], pref3, tt[q]);
+            tmem_st16(tsum + 32 + 16 * h, tt);
+            tmem_ld16(tsum + 64 + 16 * h, tt);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const float v = ar[16 * h + q] * pref3;
+              tt[q] = fmaf(v, v, tt[q]);
+            }
+            tmem_st16(tsum + 64 + 16 * h, tt);
+            tmem_ld16(tsum + 96 + 16 * h, tt);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const float v = ai[16 * h + q] * pref3;
+              tt[q] = fmaf(v, v, tt[q]);
+              ar[16 * h + q] = ai[16 * h + q] = 0.f;
+            }
+            tmem_st16(tsum + 96 + 16 * h, tt);
+          }
+        }
+      }
+      // the warp is done with stage s: its lane 0 loads the stage's next step
+      __syncwarp();
+      if (lane == 0 && i + kSt84w < nst) {
+        fence_async_smem();
+        issue(i + kSt84w);
+      }
+    }
+    if (!ok) break;
+    qb += nst;
+    // end of the item: the sums of each part go to the float64 accumulators
+#pragma unroll 1
+    for (int part = 0; part < 4; ++part) {
+      float tt[32], z[32];
+      tmem_ld32(tsum + 32 * part, tt);
+      double* dst = acc + (long long)part * plane;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int k = k0 + kt + (q >> 2), l = l0 + lt + (q & 3);
+        if (in_domain3(k, l, M, 0)) atomicAdd(dst + (long long)k * M + l, (double)tt[q]);
+        z[q] = 0.f;
+      }
+      tmem_st32(tsum + 32 * part, z);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot),
+                 "r"(kTmemCols));
+  }
+}
+
 // Isolated grid points of one channel (the tiles that hold a single point of
 // the domain, where the edge k + l = M - 1 passes a tile corner): each thread
 // evaluates c3 at one point for one group at a time, reading the centred
@@ -772,6 +987,35 @@ cudaError_t launch_k2_fc(const CUtensorMap& tm64, const CUtensorMap& tm128, cons
 }
 
 }  // namespace
+
+cudaError_t launch_k2_bispec84w(const CUtensorMap& tm32, const CUtensorMap& tm64w, int row0,
+                                int G, int m, int M, const TileInfo* tiles, int n_tiles,
+                                float pref3, double* acc, long long plane, int nsm, int* counter,
+                                int* status, int inject_timeout, cudaStream_t stream) {
+  if (G <= 0 || n_tiles <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(kThreads84w / 32) * kRing84w + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k2_bispec84w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k2_bispec84w, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  // TMEM: 128 columns per CTA, 512 per SM
+  int occ = 1;
+  e = ctas_per_sm(k2_bispec84w, kThreads84w, smem, 4, &occ);
+  if (e != cudaSuccess) return e;
+  const int n_cta = nsm * occ;
+  WorkQueue wq;  // items per warp
+  wq.counter = counter;
+  wq.n_tiles = n_tiles;
+  wq.group_chunk = work_group_chunk(G, n_tiles, n_cta * (kThreads84w / 32));
+  wq.n_items = n_tiles * ((G + wq.group_chunk - 1) / wq.group_chunk);
+  e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  k2_bispec84w<<<n_cta, kThreads84w, smem, stream>>>(tm32, tm64w, row0, m, M, G, tiles, wq,
+                                                     pref3, acc, plane, status, inject_timeout);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_k2_bispec(const CUtensorMap& tm64, const CUtensorMap& tm128,
                              const float2* spec_a, const float2* spec_b, const float2* spec_c,

@@ -184,6 +184,25 @@ void build_tiles(int M, bool cross, std::vector<TileInfo>& t3, std::vector<TileI
     }
 }
 
+// One channel, k2_bispec84w: the 32 x 32 sub-tiles that hold more than
+// kIsolatedPoints points of the S3 domain (0 <= k <= l, k + l <= M - 1), and the
+// points of the others (where the edge k + l = M - 1 passes a sub-tile corner),
+// which k2_points evaluates.
+void build_warp_tiles(int M, std::vector<TileInfo>& t, std::vector<int2>& pts) {
+  constexpr int kW = 32;
+  for (int k0 = 0; k0 < M; k0 += kW)
+    for (int l0 = 0; l0 < M; l0 += kW) {
+      std::vector<int2> in;
+      for (int a = 0; a < kW && (int)in.size() <= kIsolatedPoints; ++a)
+        for (int b = 0; b < kW && (int)in.size() <= kIsolatedPoints; ++b)
+          if (in_domain3(k0 + a, l0 + b, M, 0)) in.push_back(make_int2(k0 + a, l0 + b));
+      if ((int)in.size() > kIsolatedPoints)
+        t.push_back(TileInfo{k0, l0, 1, kW});
+      else
+        pts.insert(pts.end(), in.begin(), in.end());
+    }
+}
+
 void record(ss_plan_s* p, int stage, cudaStream_t s, bool start) {
   if (!p->timing) return;
   if (start) {
@@ -302,20 +321,29 @@ ss_status process_device(ss_plan_s* p, const void* ptr, long long n, long long s
         for (size_t i = 0; i < p->c3.size(); ++i) {
           const Combo& cb = p->c3[i];
           const int row_stride = p->Gb_max * p->m;
-          SS_TRY(p, launch_k2_bispec(p->tm64, p->tm128, p->d_spec + cb.c[0] * chan_stride,
-                                     p->d_spec + cb.c[1] * chan_stride,
-                                     p->d_spec + cb.c[2] * chan_stride, cb.c[0] * row_stride,
-                                     cb.c[1] * row_stride, cb.c[2] * row_stride, cnt, p->m,
-                                     p->FC, p->M, p->Mp, p->d_tiles3, p->n_tiles3,
-                                     p->C > 1 ? 1 : 0, pref3,
-                                     p->d_acc3 + (long long)i * p->rows3 * p->M, plane, p->rows3,
-                                     p->nsm, p->d_counter, p->d_status, p->inject_timeout,
-                                     p->k2_variant, p->stream));
-          if (p->C == 1 && p->n_pts3 > 0)
-            SS_TRY(p, launch_k2_points(p->d_spec + cb.c[0] * chan_stride, p->Mp, cnt, p->m,
-                                       p->d_pts3, p->n_pts3, p->M, pref3,
-                                       p->d_acc3 + (long long)i * p->rows3 * p->M, plane,
+          double* acc3 = p->d_acc3 + (long long)i * p->rows3 * p->M;
+          const bool warps = p->k2_variant == kK2Warp84 && p->C == 1;
+          if (warps)
+            SS_TRY(p, launch_k2_bispec84w(p->tm32w, p->tm64w, cb.c[0] * row_stride, cnt, p->m,
+                                          p->M, p->d_tiles3w, p->n_tiles3w, pref3, acc3, plane,
+                                          p->nsm, p->d_counter, p->d_status, p->inject_timeout,
+                                          p->stream));
+          else
+            SS_TRY(p, launch_k2_bispec(p->tm64, p->tm128, p->d_spec + cb.c[0] * chan_stride,
+                                       p->d_spec + cb.c[1] * chan_stride,
+                                       p->d_spec + cb.c[2] * chan_stride, cb.c[0] * row_stride,
+                                       cb.c[1] * row_stride, cb.c[2] * row_stride, cnt, p->m,
+                                       p->FC, p->M, p->Mp, p->d_tiles3, p->n_tiles3,
+                                       p->C > 1 ? 1 : 0, pref3, acc3, plane, p->rows3, p->nsm,
+                                       p->d_counter, p->d_status, p->inject_timeout,
+                                       p->k2_variant == kK2Warp84 ? kK2Tile84Stages2
+                                                                  : p->k2_variant,
                                        p->stream));
+          const int2* pts = warps ? p->d_pts3w : p->d_pts3;
+          const int npts = warps ? p->n_pts3w : p->n_pts3;
+          if (p->C == 1 && npts > 0)
+            SS_TRY(p, launch_k2_points(p->d_spec + cb.c[0] * chan_stride, p->Mp, cnt, p->m, pts,
+                                       npts, p->M, pref3, acc3, plane, p->stream));
         }
         record(p, 1, p->stream, false);
       }
@@ -532,6 +560,15 @@ ss_status encode_maps(ss_plan_s* p) {
     if (r != CUDA_SUCCESS)
       return fail(p, SS_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string(r));
   }
+  for (int blocks : {2, 4}) {  // boxes of kFrames84w rows for k2_bispec84w
+    const cuuint32_t box[3] = {16, (cuuint32_t)blocks, (cuuint32_t)kFrames84w};
+    CUresult r = encode(blocks == 2 ? &p->tm32w : &p->tm64w, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                        p->d_spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(p, SS_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string(r));
+  }
   if (p->C > 1) {
     // 2-D views [rows][Mp] for the tensor-core cross S4: boxes of 4 frame rows (8 for
     // FP16X3) by min(box bins, Mp) bins (rows of a and b) or by the column box
@@ -718,6 +755,8 @@ void destroy(ss_plan_s* p) {
   cudaFree(p->d_s2cross);
   cudaFree(p->d_tiles3);
   cudaFree(p->d_pts3);
+  cudaFree(p->d_tiles3w);
+  cudaFree(p->d_pts3w);
   cudaFree(p->d_tiles4);
   cudaFree(p->d_tiles4tc);
   cudaFree(p->d_c4cross);
@@ -880,9 +919,14 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
     pts3.clear();
   }
   if (p->c4.empty() || channels > 1) t4.clear();  // several channels: k3_trispec_cross
+  std::vector<TileInfo> t3w;
+  std::vector<int2> pts3w;
+  if (channels == 1 && !p->c3.empty()) build_warp_tiles(p->M, t3w, pts3w);
   p->n_tiles3 = (int)t3.size();
   p->n_tiles4 = (int)t4.size();
   p->n_pts3 = (int)pts3.size();
+  p->n_tiles3w = (int)t3w.size();
+  p->n_pts3w = (int)pts3w.size();
 
 #define PLAN_TRY(call)                           \
   do {                                           \
@@ -909,6 +953,8 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
   if (p->n_acc4) PLAN_TRY(dev_alloc(p, &p->d_acc4, p->n_acc4 * sizeof(double)));
   if (!t3.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles3, t3.size() * sizeof(TileInfo)));
   if (!pts3.empty()) PLAN_TRY(dev_alloc(p, &p->d_pts3, pts3.size() * sizeof(int2)));
+  if (!t3w.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles3w, t3w.size() * sizeof(TileInfo)));
+  if (!pts3w.empty()) PLAN_TRY(dev_alloc(p, &p->d_pts3w, pts3w.size() * sizeof(int2)));
   if (!t4.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4, t4.size() * sizeof(TileInfo)));
   if (!t4tc.empty()) PLAN_TRY(dev_alloc(p, &p->d_tiles4tc, t4tc.size() * sizeof(TileInfo)));
   std::vector<int4> c4x;
@@ -933,6 +979,12 @@ static ss_status plan_create(ss_plan_t* out, int channels, int T, double dt, int
                         cudaMemcpyHostToDevice));
   if (!pts3.empty())
     PLAN_TRY(cudaMemcpy(p->d_pts3, pts3.data(), pts3.size() * sizeof(int2),
+                        cudaMemcpyHostToDevice));
+  if (!t3w.empty())
+    PLAN_TRY(cudaMemcpy(p->d_tiles3w, t3w.data(), t3w.size() * sizeof(TileInfo),
+                        cudaMemcpyHostToDevice));
+  if (!pts3w.empty())
+    PLAN_TRY(cudaMemcpy(p->d_pts3w, pts3w.data(), pts3w.size() * sizeof(int2),
                         cudaMemcpyHostToDevice));
   if (!t4.empty())
     PLAN_TRY(cudaMemcpy(p->d_tiles4, t4.data(), t4.size() * sizeof(TileInfo),

@@ -69,6 +69,7 @@ struct ss_plan_s {
   int* d_counter = nullptr;        // work-queue counter of the pair kernels
   int FC = 0;                      // frames per staged chunk of the pair kernels
   CUtensorMap tm64{}, tm128{}, tm48{};  // 3-D views [rows = C*Gb_max*m][Mp/16][16] of the spectra
+  CUtensorMap tm32w{}, tm64w{};          // the same with boxes of kFrames84w rows (k2_bispec84w)
   CUtensorMap tmx_ab{}, tmx_cd{};        // 2-D views [rows][Mp] (several channels, tensor cores)
   CUtensorMap tmx_sab{}, tmx_scd{};      // FP16X3: views of the bins' maxima [rows][Mp]
   CUtensorMap tm_img[4]{};               // 4-D views of each channel's Gram operand image
@@ -78,6 +79,10 @@ struct ss_plan_s {
   ss::OperandImage oi;                 // K1's second output for the tensor-core S4 kernel
   int n_tiles3 = 0, n_tiles4 = 0;
   int2* d_pts3 = nullptr;  // isolated S3 grid points of one channel (k2_points)
+  // the independent-warp K2 form: its 32 x 32 sub-tiles and their isolated points
+  ss::TileInfo* d_tiles3w = nullptr;
+  int2* d_pts3w = nullptr;
+  int n_tiles3w = 0, n_pts3w = 0;
   bool col4 = false;       // the S4 column l = M - 1 is left to k3_column
   int n_pts3 = 0;
   long long pairs3 = 0, pairs4 = 0;

@@ -27,7 +27,7 @@ using namespace ss;
 namespace {
 
 const char* const kK1Names[kK1Modes] = {"auto", "r96", "frames", "warp"};
-const char* const kK2Names[kK2Variants] = {"44", "84s2", "84s3", "44s3"};
+const char* const kK2Names[kK2Variants] = {"44", "84s2", "84s3", "44s3", "84w"};
 
 // Gaussian noise (counter-based: SplitMix64 of the element index, Box-Muller),
 // float32 or int16 (scaled by 1000, saturated), for timing only.

@@ -1,7 +1,8 @@
 """The autotuner and every kernel form it chooses between.
 
 Each K1 form (resident groups in 74 KB or 96 KB, a warp per frame, frame at a time) and each K2
-tiling (4 x 4 micro-tiles, 8 x 4 micro-tiles with two or three stages) must give
+tiling (4 x 4 micro-tiles, 8 x 4 micro-tiles with two or three stages or in independent warps)
+must give
 the oracle's spectra; ss_autotune must leave a plan that does; the tuning text
 round-trips and refuses a plan of another configuration.
 Tolerance as in the parity tests: 1e-5 of each spectrum's peak, 1e-4 for the
@@ -18,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 TOL, TOL_ERR = 1e-5, 1e-4
 K1_FORMS = ["auto", "r96", "frames", "warp"]
-K2_FORMS = ["44", "44s3", "84s2", "84s3"]
+K2_FORMS = ["44", "44s3", "84s2", "84s3", "84w"]
 
 
 def P():
@@ -51,6 +52,18 @@ def test_k2_forms_match_the_oracle(T, m, G, k2):
     out = run(z, T, m, f"k2={k2}", orders=(3,))
     a = out["S3"][0].reshape(ref["S3"].shape)
     assert close(a, ref["S3"], TOL)
+    assert close(out["S3_err"][0].reshape(ref["S3_err"].shape), ref["S3_err"], TOL_ERR)
+
+
+# the independent-warp form streams an item's frames four at a time across group
+# boundaries: m = 10 (the bench's shape), 13 and 6 (groups ending inside a stage),
+# 16 at T = 2048; ragged tails
+@pytest.mark.parametrize("T,m,G", [(1024, 10, 20), (1024, 13, 7), (2048, 16, 4), (512, 6, 33)])
+def test_k2_independent_warps_match_the_oracle(T, m, G):
+    z = synth.ar1_quadratic(T * m * G + 3 * T + 7, seed=T + m)
+    ref = oracle.polyspectra(z, T, 1.0, m, orders=(3,), group_chunk=8)
+    out = run(z, T, m, "k2=84w", orders=(3,))
+    assert close(out["S3"][0].reshape(ref["S3"].shape), ref["S3"], TOL)
     assert close(out["S3_err"][0].reshape(ref["S3_err"].shape), ref["S3_err"], TOL_ERR)
 
 
