@@ -25,17 +25,16 @@
 // and per stage (group, kChunks consecutive K chunks) it loads two boxes of the
 // operand image through a 4-D tensor map: the 16 row groups of the k-block and
 // the 16 of the l-block.  Warps 17 and 18, MMA: warp 17 + w takes every other
-// group (w = group index mod 2; TMEM buffer group index mod 3 of 128 columns, so
-// the products run up to two groups ahead of the epilogue), reads the group's
+// group (w = group index mod 2; TMEM buffer group index mod 4 of 128 columns, so
+// the products run up to three groups ahead of the epilogue), reads the group's
 // record from the ring, and per stage issues the MMAs of its chunks, commits
 // them to the stage's barrier (the stage is then free for the next load) and,
 // after the group's last stage, to the buffer's barrier; one warp's waits and
 // commits overlap the other's products.  Warps 0-15, the epilogue: TMEM lane
 // quadrant warp % 4, columns 32 (warp / 4) .. + 31.  For each group they read D
 // in two halves of 16 columns (FP16: divided by the scales) and update the
-// running sums of their 32 grid points, held in registers, and the running sums
-// of squares, held in TMEM columns 256-383; at the end of an item they add both
-// to the float64 accumulators.  Tiles of the last l-block are as
+// running sums and sums of squares of their 32 grid points, held in registers;
+// at the end of an item they add both to the float64 accumulators.  Tiles of the last l-block are as
 // narrow as the bins left (N a multiple of 16).  Every wait is bounded; on a
 // failure the CTA stops, drains its copies and products and frees its TMEM.
 #include "internal.cuh"
@@ -46,11 +45,10 @@ namespace {
 
 constexpr int kTM = 128, kTN = 128, kEpiWarps = 16, kMmaWarps = 2;
 constexpr int kTcThreads = 32 * (kEpiWarps + 1 + kMmaWarps);
-constexpr uint32_t kTmemCols = 512;  // D0 | D1 | running sum of squares | D2
-constexpr uint32_t kColSq = 256;
-constexpr int kBufs = 3;  // TMEM accumulator buffers: group g uses buffer g mod 3
+constexpr uint32_t kTmemCols = 512;  // D0 | D1 | D2 | D3
+constexpr int kBufs = 4;  // TMEM accumulator buffers: group g uses buffer g mod 4
 
-__device__ __forceinline__ uint32_t buf_col(uint32_t b) { return b == 2 ? 384u : b * kTN; }
+__device__ __forceinline__ uint32_t buf_col(uint32_t b) { return b * kTN; }
 constexpr int kEpiCols = kTN / (kEpiWarps / 4);  // columns of an epilogue warp (32)
 
 // Operand formats.  In the image and in a stage, a row group (8 bins) holds,
@@ -362,18 +360,11 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
     const int q = warp & 3, h = warp >> 2;
     const uint32_t lane_addr = taddr + ((uint32_t)(32 * q) << 16);
     const int col0 = kEpiCols * h;  // this warp's 32 columns of the tile
-    // running sums over the item's groups of this thread's 32 points (row
-    // 32 q + lane, columns col0 ..); their squares are in TMEM
-    float sm[kEpiCols];
+    // running sums and sums of squares over the item's groups of this thread's
+    // 32 points (row 32 q + lane, columns col0 ..)
+    float sm[kEpiCols], sq[kEpiCols];
 #pragma unroll
-    for (int i = 0; i < kEpiCols; ++i) sm[i] = 0.f;
-    {
-      float z[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) z[i] = 0.f;
-#pragma unroll
-      for (int hh = 0; hh < kEpiCols / 16; ++hh) tmem_st16(lane_addr + kColSq + col0 + 16 * hh, z);
-    }
+    for (int i = 0; i < kEpiCols; ++i) sm[i] = sq[i] = 0.f;
     for (uint32_t gc = 0;; ++gc) {
       const int p = gc & (kPsSlots - 1);
       const uint32_t b = gc % kBufs;
@@ -390,7 +381,6 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
         break;
       }
       tc_fence_after();
-      tmem_wait_st();  // the previous group's sums of squares are stored
       // FP16: the row scales of k and l undo the operands' scaling, applied one at a
       // time (their product alone may leave the float range)
       const float rk = F::kScaled ? psr[p][32 * q + lane] : 1.f;
@@ -401,9 +391,8 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
       for (int hh = 0; hh < kEpiCols / 16; ++hh) {
         if (hh < nh) {
           const uint32_t col = col0 + 16 * hh;
-          float d[16], sq[16];
+          float d[16];
           tmem_ld16(lane_addr + buf_col(b) + col, d);
-          tmem_ld16(lane_addr + kColSq + col, sq);
           tmem_wait_ld();
 #pragma unroll
           for (int c = 0; c < 16; c += 4) {
@@ -417,10 +406,9 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
               // c4 = D (FP16: D / s_k / s_l)
               const float v = F::kScaled ? (d[c + i] * rk) * rl[i] : d[c + i];
               sm[16 * hh + c + i] += v;
-              sq[c + i] = fmaf(v, v, sq[c + i]);
+              sq[16 * hh + c + i] = fmaf(v, v, sq[16 * hh + c + i]);
             }
           }
-          tmem_st16(lane_addr + kColSq + col, sq);
         }
       }
       // this warp has read its part of the buffer and of the ps slot
@@ -436,32 +424,19 @@ k3_trispec_tc(const __grid_constant__ CUtensorMap tm_img, const float* __restric
         // end of an item: add the sums to the float64 accumulators.  Point (k, l),
         // k <= l, is stored at [l][k], so a warp's 32 rows k are 32 consecutive
         // doubles.
-        tmem_wait_st();
         const int k = r.k0 + 32 * q + lane;
 #pragma unroll
-        for (int hh = 0; hh < kEpiCols / 16; ++hh) {
-          if (hh < nh) {
-            const uint32_t col = col0 + 16 * hh;
-            float sq[16];
-            tmem_ld16(lane_addr + kColSq + col, sq);
-            tmem_wait_ld();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int l = r.l0 + (int)col + i;
-              if (k <= l && l < M) {
-                const long long o = (long long)l * M + k;
-                atomicAdd(acc + o, (double)sm[16 * hh + i]);
-                atomicAdd(acc + 2 * plane + o, (double)sq[i]);
-              }
-              sm[16 * hh + i] = 0.f;
-              sq[i] = 0.f;
-            }
-            tmem_st16(lane_addr + kColSq + col, sq);
+        for (int i = 0; i < kEpiCols; ++i) {
+          const int l = r.l0 + col0 + i;
+          if (i < 16 * nh && k <= l && l < M) {
+            const long long o = (long long)l * M + k;
+            atomicAdd(acc + o, (double)sm[i]);
+            atomicAdd(acc + 2 * plane + o, (double)sq[i]);
           }
+          sm[i] = sq[i] = 0.f;
         }
       }
     }
-    tmem_wait_st();
   }
   tc_fence_before();
   __syncthreads();
