@@ -663,6 +663,12 @@ def main():
     # several channels: the cross S4 runs FP16x3 with fp16x3, TF32x3 with the other
     # tensor-core precisions
     s4_prec = (args.precision if C == 1 or args.precision in ("fp32", "fp16x3") else "tf32x3")
+    # the K2 form the autotuner (or --tuning) chose: its kernel's name; the
+    # independent-warp form runs only with one channel (the plan takes the 8 x 4
+    # tiling for several)
+    k2_form = (tuning.split(" k2=")[1].split()[0] if " k2=" in tuning else "44")
+    k2_name = {"84s2": "k2_bispec84", "84s3": "k2_bispec84",
+               "84w": "k2_bispec84w" if C == 1 else "k2_bispec84"}.get(k2_form, "k2_bispec")
     names = ["k1_spectra", "k2_bispec", s4_name, "k4_finalize", "h2d"]
     n_batches = max(1, int(np.ceil(groups / info.groups_per_batch)))
     hbm = float(pk.get("hbm_gbs", 6800.0))
@@ -695,9 +701,9 @@ def main():
     k2_ms = stage_ms[1] / args.steps
     k2_flops = 14.0 * st.pairs3 * frames * info.n_s3
     k2_ach = k2_flops / (k2_ms / 1e3) / 1e12 if k2_ms > 0 else None
-    roofline_k2 = {"bound": "alu", "kernel": "k2_bispec", "achieved": k2_ach, "peak": fp32_peak,
+    roofline_k2 = {"bound": "alu", "kernel": k2_name, "achieved": k2_ach, "peak": fp32_peak,
                    "unit": "TFLOP/s", "frac": (k2_ach / fp32_peak) if k2_ach else None,
-                   "traffic": traffic_for("k2_bispec"), "peak_source": fp32_src,
+                   "traffic": traffic_for(k2_name), "peak_source": fp32_src,
                    "flop_per_step": k2_flops, "ms_per_step": k2_ms}
 
     # S4: the tensor pipe in the split modes.  One channel: the method's work is one
