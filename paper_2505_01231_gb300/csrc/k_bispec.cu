@@ -64,6 +64,15 @@ __device__ __forceinline__ float4 lds128(const unsigned char* p) {
   return *reinterpret_cast<const float4*>(p);
 }
 
+// 16-byte load from a shared-memory address (the .shared window, 32 bits)
+__device__ __forceinline__ float4 lds128_s(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+
 constexpr uint32_t kTmemCols = 128;  // per CTA: 2 warps per lane quadrant x 64 columns
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -658,10 +667,17 @@ k2_bispec84w(const __grid_constant__ CUtensorMap tm32, const __grid_constant__ C
   const int tx = lane & 3;
   const int ty = ((lane >> 3) & 1) | (((lane >> 2) & 1) << 1) | (((lane >> 4) & 1) << 2);
   const int kt = 8 * tx, lt = 4 * ty;  // micro-tile origin in the sub-tile
-  // byte offsets of the thread's loads in frame 0 of a stage, before the swizzle:
-  // frame f of a or b (256-byte rows) flips bits 5-6 by 2f, of c (512-byte rows)
-  // bit 6 by f
-  const uint32_t oa0 = kt * 8, ob0 = lt * 8, oc0 = (kt + lt) * 8;
+  // Swizzled byte offsets of the thread's loads in frame 0 of an array: frame f of
+  // a or b (256-byte rows) XORs them with 32 f, of c (512-byte rows) with 64 (f & 1).
+  // For a and b the q-th 16-byte load of a thread stays in the 128-byte row of the
+  // first (their chunk is 0 or 4, resp. even), so its offset is the first's XOR 16 q;
+  // with array and frame bases free of the offset bits, an address is the frame
+  // base XOR one per-thread constant, one logic operation a load.
+  const uint32_t sa0 = swz128(kt * 8), sb0 = swz128(lt * 8);
+  uint32_t sc[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) sc[q] = swz128((kt + lt) * 8 + 16 * q);
+  const uint32_t ring_s = smem_addr(ring);
 
   if (tid == 0) {
     for (int w = 0; w < kThreads84w / 32; ++w)
@@ -735,32 +751,32 @@ k2_bispec84w(const __grid_constant__ CUtensorMap tm32, const __grid_constant__ C
             mbar_wait_bounded(&full[warp][(qb + q) % kSt84w], ((qb + q) / kSt84w) & 1u, status);
         break;
       }
-      const unsigned char* sA = ring + (size_t)s * kStage84w;
-      const unsigned char* sB = sA + kFS84w * 256;
-      const unsigned char* sC = sA + kFS84w * 512;
+      const uint32_t sA = ring_s + (uint32_t)s * kStage84w;  // 1024-byte aligned
+      const uint32_t sB = sA + kFS84w * 256;
+      const uint32_t sC = sA + kFS84w * 512;
       const int nf = min(kFS84w, rows - i * kFS84w);
 #pragma unroll 1
       for (int f = 0; f < nf; ++f) {
-        const unsigned char* pa = sA + f * 256;
-        const unsigned char* pb = sB + f * 256;
-        const unsigned char* pc = sC + f * 512;
         const uint32_t fab = (uint32_t)f << 5, fc = (uint32_t)(f & 1) << 6;
+        const uint32_t pa = (sA + f * 256) | (sa0 ^ fab);
+        const uint32_t pb = (sB + f * 256) | (sb0 ^ fab);
+        const uint32_t pc = (sC + f * 512) ^ fc;
         float2 al[4], ac[12];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const float4 v = lds128(pb + (swz128(ob0 + 16 * q) ^ fab));
+          const float4 v = lds128_s(pb ^ (16u * q));
           al[2 * q] = make_float2(v.x, v.y);
           al[2 * q + 1] = make_float2(v.z, v.w);
         }
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-          const float4 v = lds128(pc + (swz128(oc0 + 16 * q) ^ fc));
+          const float4 v = lds128_s(pc ^ sc[q]);
           ac[2 * q] = make_float2(v.x, v.y);
           ac[2 * q + 1] = make_float2(v.z, v.w);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const float4 v = lds128(pa + (swz128(oa0 + 16 * q) ^ fab));
+          const float4 v = lds128_s(pa ^ (16u * q));
           const float2 ak2[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
