@@ -1024,7 +1024,9 @@ cudaError_t launch_k2_bispec84w(const CUtensorMap& tm32, const CUtensorMap& tm64
   WorkQueue wq;  // items per warp
   wq.counter = counter;
   wq.n_tiles = n_tiles;
-  wq.group_chunk = work_group_chunk(G, n_tiles, n_cta * (kThreads84w / 32));
+  // about 8 items per warp (half the pair kernels' 16): each item ends with a
+  // flush of its warp's 32 x 32 sub-tile, so longer items halve the atomics
+  wq.group_chunk = work_group_chunk(G, n_tiles, n_cta * (kThreads84w / 32) / 2);
   wq.n_items = n_tiles * ((G + wq.group_chunk - 1) / wq.group_chunk);
   e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
