@@ -483,17 +483,15 @@ ss_status process_host(ss_plan_s* p, const void* chunk, long long n) {
   const size_t e = p->elem;
   // pieces of about a quarter of the call in whole groups (at least 32 Mi
   // samples, at most a staging buffer), so that the copies of all but the first
-  // piece overlap the kernels of the one before; the first piece is a quarter of
-  // that (whole groups), since nothing hides its copy
+  // piece overlap the kernels of the one before
   const long long per_group = (long long)p->m * p->T;
   long long step = (n + 3) / 4;
   step = (step + per_group - 1) / per_group * per_group;
   step = std::min(p->stage_n, std::max(step, std::min(p->stage_n, (32ll << 20) / p->C)));
-  const long long first = std::max(per_group, (step / 4) / per_group * per_group);
   int piece = 0;
-  for (long long off = 0, len = 0; off < n; off += len, ++piece) {
+  for (long long off = 0; off < n; off += step, ++piece) {
     const int b = piece & 1;
-    len = std::min(piece == 0 ? first : step, n - off);
+    const long long len = std::min(step, n - off);
     SS_TRY(p, cudaStreamWaitEvent(p->copy_stream, p->ev_free[b], 0));
     record(p, 4, p->copy_stream, true);
     for (int c = 0; c < p->C; ++c)
