@@ -362,6 +362,16 @@ ss_status ss_query(ss_plan_t plan, ss_info* info);
 ss_status ss_layout(int channels, int T, int* s3_tiles, int max3, int* n3, int* s3_points,
                     int maxp, int* np, int* s4_tiles, int max4, int* n4, int* last_col);
 
+/* ss_layout_warps -- the S3 decomposition of the independent-warp K2 form (one
+   channel; host only, no device call): the 32 x 32 sub-tiles of (k, l) that hold
+   more than 8 points of the domain 0 <= k <= l, k + l <= M - 1 (Eq. 28), as
+   (k0, l0) pairs in tiles, and the domain points of the other sub-tiles, left to
+   the point kernel, as (k, l) pairs in points.  Each array receives at most its
+   max entries (it may be NULL); n and np receive the full counts.  Errors:
+   SS_EINVAL for T not a power of two in [8, 4096], or a NULL count. */
+ss_status ss_layout_warps(int T, int* tiles, int max_tiles, int* n, int* points, int maxp,
+                          int* np);
+
 /* ss_combos -- copy the plan's combinations, (n_s2 + n_s3 + n_s4) records of
    five ints {order, c0, c1, c2, c3} in output order; out may hold max_records. */
 ss_status ss_combos(ss_plan_t plan, int* out, int max_records);

@@ -23,7 +23,7 @@ __all__ = [
     "SSError", "ss_info", "ss_stats_t", "lib", "LIB_PATH",
     "ss_plan", "ss_accumulate", "ss_finalize", "ss_reset", "ss_query", "ss_combos",
     "ss_set_timing", "ss_stats", "ss_set_batch", "ss_destroy", "ss_last_error", "ss_version",
-    "ss_s2_noalloc", "ss_layout", "Plan",
+    "ss_s2_noalloc", "ss_layout", "ss_layout_warps", "Plan",
 ]
 
 SS_OK, SS_EINVAL, SS_ENOMEM, SS_ECUDA, SS_ESTATE, SS_ETIMEOUT, SS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
@@ -68,6 +68,8 @@ _sig = {
     "ss_combos": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "ss_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P,
                                  ctypes.c_int, _P, _P, ctypes.c_int, _P, _P]),
+    "ss_layout_warps": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int, _P, _P, ctypes.c_int,
+                                       _P]),
     "ss_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "ss_stats": (ctypes.c_int, [_P, ctypes.POINTER(ss_stats_t)]),
     "ss_set_batch": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -257,6 +259,20 @@ def ss_layout(channels, T):
             [(pts[2 * i], pts[2 * i + 1]) for i in range(np_.value)],
             [(t4[3 * i], t4[3 * i + 1], t4[3 * i + 2]) for i in range(n4.value)],
             bool(col.value))
+
+
+def ss_layout_warps(T):
+    """The S3 decomposition of the independent-warp K2 form (one channel, host
+    only): 32 x 32 sub-tiles [(k0, l0)] and the points left to the point kernel
+    [(k, l)]."""
+    n, np_ = ctypes.c_int(), ctypes.c_int()
+    _check(lib.ss_layout_warps(T, None, 0, ctypes.byref(n), None, 0, ctypes.byref(np_)), None)
+    t = (ctypes.c_int * (2 * max(n.value, 1)))()
+    pts = (ctypes.c_int * (2 * max(np_.value, 1)))()
+    _check(lib.ss_layout_warps(T, t, n.value, ctypes.byref(n), pts, np_.value,
+                               ctypes.byref(np_)), None)
+    return ([(t[2 * i], t[2 * i + 1]) for i in range(n.value)],
+            [(pts[2 * i], pts[2 * i + 1]) for i in range(np_.value)])
 
 
 def ss_set_timing(plan, enable):

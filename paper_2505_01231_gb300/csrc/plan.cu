@@ -1435,6 +1435,27 @@ ss_status ss_layout(int channels, int T, int* s3_tiles, int max3, int* n3, int* 
   return SS_OK;
 }
 
+ss_status ss_layout_warps(int T, int* tiles, int max_tiles, int* n, int* points, int maxp,
+                          int* np) {
+  if (T < 8 || T > 4096 || !is_pow2(T))
+    return fail(nullptr, SS_EINVAL, "T a power of two in [8, 4096]");
+  if (!n || !np) return fail(nullptr, SS_EINVAL, "NULL count argument");
+  std::vector<TileInfo> t;
+  std::vector<int2> pts;
+  build_warp_tiles(T / 2 + 1, t, pts);
+  *n = (int)t.size();
+  *np = (int)pts.size();
+  for (int i = 0; i < *n && i < max_tiles && tiles; ++i) {
+    tiles[2 * i] = t[i].k0;
+    tiles[2 * i + 1] = t[i].l0;
+  }
+  for (int i = 0; i < *np && i < maxp && points; ++i) {
+    points[2 * i] = pts[i].x;
+    points[2 * i + 1] = pts[i].y;
+  }
+  return SS_OK;
+}
+
 ss_status ss_combos(ss_plan_t p, int* out, int max_records) {
   if (!p || (!out && max_records > 0)) return fail(p, SS_EINVAL, "NULL argument");
   int r = 0;

@@ -1,5 +1,6 @@
-"""Host logic of the work decomposition (ss_layout, no GPU): the S3 tiles of K2 and
-the points left to the point kernel cover the bispectrum domain (Eq. 28 / Eq. 48)
+"""Host logic of the work decomposition (ss_layout, ss_layout_warps; no GPU): the S3
+tiles of K2 (64 x 64 tiles, or the 32 x 32 sub-tiles of the independent-warp form)
+and the points left to the point kernel cover the bispectrum domain (Eq. 28 / Eq. 48)
 exactly once; the tensor-core S4 tiles and the column left to the column kernel
 cover the upper triangle k <= l of the trispectrum cut exactly once."""
 import numpy as np
@@ -44,6 +45,37 @@ def test_s3_tiles_and_points_cover_the_domain_once(T, channels):
         assert dom3(kp, lp, M, cross)
         cover[kp + M - 1, lp] += 1
     assert np.array_equal(cover, want.astype(int))
+
+
+@pytest.mark.parametrize("T", TS)
+def test_independent_warp_subtiles_and_points_cover_the_domain_once(T):
+    mod = P()
+    M = T // 2 + 1
+    tiles, pts = mod.ss_layout_warps(T)
+    k = np.arange(M)[:, None]
+    l = np.arange(M)[None, :]
+    want = ((k <= l) & (k + l < M)).astype(int)
+    cover = np.zeros((M, M), int)
+    for k0, l0 in tiles:
+        assert k0 % 32 == 0 and l0 % 32 == 0 and 0 <= k0 < M and 0 <= l0 < M
+        inside = want[k0:k0 + 32, l0:l0 + 32]
+        assert inside.sum() > 8, (k0, l0)
+        cover[k0:k0 + 32, l0:l0 + 32] += inside
+    for kp, lp in pts:
+        assert dom3(kp, lp, M, False)
+        # a point of the list lies in a sub-tile with at most 8 domain points
+        k0, l0 = kp // 32 * 32, lp // 32 * 32
+        assert want[k0:k0 + 32, l0:l0 + 32].sum() <= 8 and (k0, l0) not in tiles
+        cover[kp, lp] += 1
+    assert np.array_equal(cover, want)
+
+
+def test_layout_warps_rejects_bad_shapes():
+    mod = P()
+    for T in (4, 100, 8192):
+        with pytest.raises(mod.SSError) as ei:
+            mod.ss_layout_warps(T)
+        assert ei.value.status == mod.SS_EINVAL
 
 
 @pytest.mark.parametrize("T", TS)
